@@ -1,0 +1,14 @@
+"""Seeded synthetic inputs shared by the oracle and the CUDA path.
+
+This package holds only input generation (permeability fields, boundary
+data, sources).  It contains none of the method's arithmetic, so the oracle
+and the CUDA path can both draw their inputs from it without sharing any
+part of the computation.
+"""
+from .fields import gaussian_random_field, lognormal_permeability
+from .problems import (Problem, darcy_problem, config_64, config_1024,
+                       config_4096, NEUMANN, DIRICHLET)
+
+__all__ = ["gaussian_random_field", "lognormal_permeability", "Problem",
+           "darcy_problem", "config_64", "config_1024", "config_4096",
+           "NEUMANN", "DIRICHLET"]

@@ -1,0 +1,134 @@
+"""Local Robin problems on one leaf and its MMBFs (oracle side).
+
+Eqs. (11.2)-(12.2) restricted to one subdomain Omega^i with lumped RT0
+(two-point fluxes, see oracle.fine).  On a skeleton face e inside segment t
+the Robin term of Eq. (11.2), with the half-cell Darcy law
+u.n^i = 2K_c (p_c - p_e)/h_d, gives the outward integrated flux
+
+    F_e = rho_e (p_c - lambda^i_t),   rho_e = |e| / (h_d/(2K_c) + beta_t),
+    lambda^i_t = P_t - beta_t U_t (n_t . n^i),
+
+so the interface data (U_H, P_H) enter only through lambda.  Domain
+boundary faces carry the Dirichlet / Neumann data of Eqs. (ellip.2-3).
+
+MMBFs (Section 3.1, Eqs. 11Hhatbasisa and 11Hhatbasisb): for each segment j
+of the leaf, one solve with U_H = phi^j, P_H = 0 (lambda_j = -beta_j
+n_j.n^i) and one with P_H = psi^j, U_H = 0 (lambda_j = 1), both with zero
+source and zero external data; the particular solution has lambda = 0 and
+the source / external data (Eqs. addu, addp).
+"""
+import numpy as np
+
+from inputs.problems import DIRICHLET
+
+
+class LeafProblem:
+    def __init__(self, dec, leaf_id):
+        prob = dec.prob
+        lf = dec.leaves[leaf_id]
+        self.dec, self.leaf = dec, lf
+        self.i0, self.i1, self.j0, self.j1 = lf["i0"], lf["i1"], lf["j0"], lf["j1"]
+        w, h = self.i1 - self.i0, self.j1 - self.j0
+        self.w, self.h, self.n = w, h, w * h
+        self.segs = lf["segs"]
+        self.seg_pos = {t: k for k, t in enumerate(self.segs)}
+        K, hx, hy = prob.K, prob.hx, prob.hy
+        A = np.zeros((self.n, self.n))
+        bbar = np.zeros(self.n)
+        loc = lambda i, j: (i - self.i0) + w * (j - self.j0)
+        # faces of the leaf: ("x", j, i) is the x-face i of row j, ("y", j, i)
+        # the y-face j of column i.  Each entry records how its flux follows
+        # from the cell pressures.
+        self.faces = {}
+        bcs = prob.bc_slices()
+        for j in range(self.j0, self.j1):
+            for i in range(self.i0, self.i1):
+                c = loc(i, j)
+                bbar[c] += prob.q[j, i]
+                for d, (fkey, ni, nj, outsign) in enumerate([
+                        (("x", j, i), i - 1, j, -1.0), (("x", j, i + 1), i + 1, j, +1.0),
+                        (("y", j, i), i, j - 1, -1.0), (("y", j + 1, i), i, j + 1, +1.0)]):
+                    axis = 0 if d < 2 else 1
+                    hn, area = (hx, hy) if axis == 0 else (hy, hx)
+                    inside = self.i0 <= ni < self.i1 and self.j0 <= nj < self.j1
+                    in_domain = 0 <= ni < prob.nx and 0 <= nj < prob.ny
+                    if inside:
+                        T = area / (hn / (2 * K[j, i]) + hn / (2 * K[nj, ni]))
+                        A[c, c] += T
+                        A[c, loc(ni, nj)] -= T
+                        if outsign > 0:
+                            self.faces[fkey] = ("int", c, loc(ni, nj), T)
+                    elif in_domain:
+                        t = (dec.xface_seg[fkey[1], fkey[2]] if axis == 0
+                             else dec.yface_seg[fkey[1], fkey[2]])
+                        beta = dec.segments[t]["beta"]
+                        rho = area / (hn / (2 * K[j, i]) + beta)
+                        A[c, c] += rho
+                        self.faces[fkey] = ("robin", c, int(t), rho, outsign)
+                    else:
+                        side = (0 if outsign < 0 else 1) if axis == 0 else (2 if outsign < 0 else 3)
+                        k = j if axis == 0 else i
+                        gval = prob.bc_val[bcs[side]][k]
+                        if prob.bc_type[side] == DIRICHLET:
+                            tau = 2.0 * K[j, i] * area / hn
+                            A[c, c] += tau
+                            bbar[c] += tau * gval
+                            self.faces[fkey] = ("dir", c, tau, gval, outsign)
+                        else:
+                            bbar[c] -= area * gval
+                            self.faces[fkey] = ("neu", c, area * gval, outsign)
+        self.A = A
+        self.bbar = bbar
+        # Robin load matrix: column k is the right-hand side of a unit lambda
+        # on segment segs[k]
+        self.B = np.zeros((self.n, len(self.segs)))
+        for f in self.faces.values():
+            if f[0] == "robin":
+                _, c, t, rho, _ = f
+                self.B[c, self.seg_pos[t]] += rho
+
+    def solve(self, lam, with_data):
+        """Solve the local problem for Robin data lam (one value per segment
+        of the leaf, in self.segs order) with or without the source and
+        external boundary data.  Several data sets may be passed as the
+        columns of lam (shape (m, k)).  Returns (p[n, k], outward segment
+        fluxes [m, k], face flux dict in +axis direction)."""
+        lam = np.asarray(lam, dtype=np.float64)
+        single = lam.ndim == 1
+        if single:
+            lam = lam[:, None]
+        rhs = self.B @ lam
+        if with_data:
+            rhs = rhs + self.bbar[:, None]
+        p = np.linalg.solve(self.A, rhs)
+        seg_flux = np.zeros_like(lam)
+        faces = {}
+        for key, f in self.faces.items():
+            kind = f[0]
+            if kind == "int":
+                _, c, c2, T = f
+                faces[key] = T * (p[c] - p[c2])
+            elif kind == "robin":
+                _, c, t, rho, outsign = f
+                out = rho * (p[c] - lam[self.seg_pos[t]])
+                seg_flux[self.seg_pos[t]] += out
+                faces[key] = outsign * out
+            elif kind == "dir":
+                _, c, tau, gval, outsign = f
+                out = tau * (p[c] - (gval if with_data else 0.0))
+                faces[key] = outsign * out
+            else:
+                _, c, flux, outsign = f
+                out = flux if with_data else 0.0
+                faces[key] = outsign * out * np.ones(p.shape[1])
+        if single:
+            p, seg_flux = p[:, 0], seg_flux[:, 0]
+            faces = {k: v[0] for k, v in faces.items()}
+        return p, seg_flux, faces
+
+    def robin_to_flux(self):
+        """R[t, s] = outward flux through segment t for lambda = e_s, no data
+        (the P_H = psi^s MMBF traces), and rbar = particular flux traces."""
+        _, R, _ = self.solve(np.eye(len(self.segs)), with_data=False)
+        _, rbar, _ = self.solve(np.zeros(len(self.segs)), with_data=True)
+        return R, rbar
