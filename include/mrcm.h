@@ -1,0 +1,237 @@
+/*
+ * mrcm.h -- C ABI of the GB300 Recursive MRCM library (libmrcm.so).
+ *
+ * Method: the Multiscale Robin Coupled Method for Darcy flow
+ *     div u = f,  u = -K grad p  in Omega,  p = g_D / u.n = g_N on the boundary
+ * (arXiv 2009.07965, Eqs. ellip.1-ellip.3), discretised with lowest-order
+ * Raviart-Thomas elements in their lumped (two-point flux) form on a
+ * Cartesian grid, with the global interface problem replaced by the binary
+ * hierarchy of two-subdomain interface systems of the Recursive MRCM
+ * (Section 3, Algorithm 1), in the MuMM specialisation of Section 4:
+ * piecewise-constant interface unknowns on segments of H-bar fine faces and
+ * one Robin coefficient per segment, beta = alpha * H-bar / K_eff
+ * (Eqs. robin.beta, permeff).
+ *
+ * Every computation behind these calls runs in CUDA kernels on the calling
+ * process's current device; there is no CPU fallback.
+ *
+ * Conventions shared by all calls
+ *   - Arrays are float64, x fastest (cell (i, j) at i + nx*j).
+ *   - *_dev arguments are device pointers owned by the caller; the library
+ *     never frees them.  Host arguments are read before the call returns.
+ *   - Face fluxes are integrated over the face (per unit depth in 2D) and
+ *     positive in the +axis direction.  Fx has (nx+1)*ny entries, face i of
+ *     row j at i + (nx+1)*j; Fy has nx*(ny+1) entries, face j of column i at
+ *     i + nx*j.
+ *   - Boundary values bc_val: x- faces (ny, by j), x+ faces (ny), y- faces
+ *     (nx, by i), y+ faces (nx).  A Dirichlet side holds g_D, a Neumann side
+ *     the outward normal flux density g_N.
+ *   - Sources q are integrated per cell (q_c = f_c |c|).
+ *   - Calls are asynchronous on the stream given to mrcm_setup, except that
+ *     each call ends with one stream synchronisation to read the device
+ *     status word, so errors are returned by the call that raised them.
+ *   - Return value: MRCM_OK or a negative MRCM_ERR_* code; after an error
+ *     the context stays valid unless mrcm_setup itself failed.
+ */
+#ifndef MRCM_H
+#define MRCM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mrcm_ctx mrcm_ctx; /* opaque, owned by the library */
+
+typedef struct {
+    int dim;       /* 2; 3 is reserved and returns MRCM_ERR_UNSUPPORTED */
+    int n[3];      /* cells per axis (n[2] ignored in 2D) */
+    double L[3];   /* domain extent per axis; h_d = L[d] / n[d] */
+} mrcm_grid;
+
+enum { MRCM_BC_NEUMANN = 0, MRCM_BC_DIRICHLET = 1 };
+enum { MRCM_FP64 = 0, MRCM_MIXED = 1, MRCM_SURROGATE = 2 };
+
+enum {
+    MRCM_OK = 0,
+    MRCM_ERR_INVALID_ARG = -1, /* null pointer, bad size, alpha <= 0, ...  */
+    MRCM_ERR_SHAPE = -2,       /* segment does not divide the leaf side, or
+                                  leaf larger than 16x16 cells              */
+    MRCM_ERR_BAD_K = -3,       /* a permeability is <= 0 or not finite      */
+    MRCM_ERR_NOT_BUILT = -4,   /* mrcm_solve before mrcm_build_basis         */
+    MRCM_ERR_SINGULAR = -5,    /* zero / tiny pivot in a local or interface
+                                  factorisation                             */
+    MRCM_ERR_CUDA = -6,        /* a CUDA runtime call failed                 */
+    MRCM_ERR_OOM = -7,         /* device allocation failed                   */
+    MRCM_ERR_TIMEOUT = -8,     /* a bounded device wait gave up              */
+    MRCM_ERR_UNSUPPORTED = -9  /* valid request not implemented (3D, mixed
+                                  precision, surrogate, single-leaf pure
+                                  Neumann)                                  */
+};
+
+/*
+ * mrcm_setup -- plan the decomposition and copy the permeability.
+ *
+ * Section 2 (Eqs. decomp.1-2) and Section 3.1 (Eqs. dd.l, dd.2,
+ * interface.1): the grid is cut into leaves of sub_cells[0] x sub_cells[1]
+ * cells (the last leaf of a row / column is truncated when n is not a
+ * multiple); every leaf side shared with another leaf is cut into segments
+ * of seg_cells[1] cells (x-normal sides) or seg_cells[0] cells (y-normal
+ * sides), the last one shorter on truncated sides (Section 4, intermediate
+ * scale H-bar).  The hierarchy bisects the box of leaves along the axis with
+ * more leaves (x on ties), the lower half taking ceil(count/2).
+ *
+ *   out        receives the new context (NULL on failure)
+ *   g          grid; g->dim must be 2
+ *   K_dev      device array, n[0]*n[1] permeabilities (> 0); copied, the
+ *              caller may free it when the call returns
+ *   sub_cells  leaf shape in cells, each in [1, 16]
+ *   seg_cells  segment length in cells; must divide sub_cells per axis
+ *   alpha      dimensionless Robin parameter of Eq. (robin.beta), > 0
+ *   bc_type    per side (x-, x+, y-, y+, z-, z+): MRCM_BC_NEUMANN or
+ *              MRCM_BC_DIRICHLET (z entries ignored in 2D).  All-Neumann
+ *              problems are solved with zero-mean pressure.
+ *   precision  MRCM_FP64 (others return MRCM_ERR_UNSUPPORTED)
+ *   cuda_stream  cudaStream_t to run on (NULL = legacy default stream)
+ * The context allocates and owns all device workspace.
+ */
+int mrcm_setup(mrcm_ctx** out, const mrcm_grid* g, const double* K_dev,
+               const int sub_cells[3], const int seg_cells[3], double alpha,
+               const int bc_type[6], int precision, void* cuda_stream);
+
+/*
+ * mrcm_set_permeability -- replace K (same grid), invalidating the basis.
+ * K_dev: device array of n[0]*n[1] values > 0, copied.
+ */
+int mrcm_set_permeability(mrcm_ctx* ctx, const double* K_dev);
+
+/*
+ * mrcm_build_basis -- the data-dependent part that depends only on K, alpha
+ * and the boundary-condition types.
+ *
+ *   1. Robin coefficients per segment, Eqs. (robin.beta) and (permeff).
+ *   2. Every leaf's local Robin problem, Eqs. (11.2)-(12.2) with the MMBF
+ *      data of Eqs. (11Hhatbasisa)/(11Hhatbasisb): the leaf's pressure
+ *      matrix is factored (LDL^T) and its Robin-to-flux map R (one response
+ *      per interface segment) is formed.
+ *   3. The recursive merge of Algorithm 1, one batched step per tree height:
+ *      each pair of siblings solves its interface system on gamma (Eq.
+ *      linsys restricted to gamma, rows from Eqs. 13.2 and 14.2) and passes
+ *      the merged map up (Eqs. new_bfs.1-2, coefficient tracking remark of
+ *      Section 3.2).
+ * Errors: MRCM_ERR_BAD_K, MRCM_ERR_SINGULAR, MRCM_ERR_CUDA.
+ */
+int mrcm_build_basis(mrcm_ctx* ctx);
+
+/*
+ * mrcm_solve -- sources and boundary values -> pressures and fluxes.
+ *
+ *   1. Each leaf's particular solution (Eqs. addu/addp) and its interface
+ *      flux traces; up-sweep of the particular data (Eqs. particular.1-2).
+ *   2. Root interface system, then top-down recovery of every interface
+ *      unknown (Algorithm 1).
+ *   3. Final local solutions, Eq. (final): cell pressures and face fluxes.
+ *
+ *   q_dev      n[0]*n[1] integrated sources (all-Neumann problems need
+ *              sum(q) + boundary inflow = 0 up to rounding)
+ *   bc_val_dev 2*(n[0]+n[1]) boundary values (layout in the header comment)
+ *   p_dev      out: n[0]*n[1] cell pressures
+ *   Fx_dev     out: (n[0]+1)*n[1] x-face fluxes; skeleton faces hold the
+ *              mean of the two one-sided values
+ *   Fy_dev     out: n[0]*(n[1]+1) y-face fluxes
+ *   Fz_dev     must be NULL in 2D
+ *   iface_dev  optional out (NULL to skip): one-sided fluxes, 2*((n[0]+1)*n[1]
+ *              + n[0]*(n[1]+1)) values laid out as [Fa_x, Fb_x, Fa_y, Fb_y],
+ *              each face-shaped like Fx / Fy; side a is the lower-coordinate
+ *              leaf, side b the upper one, both in the +axis direction; off
+ *              the skeleton both equal the face flux.
+ * Errors: MRCM_ERR_NOT_BUILT, MRCM_ERR_INVALID_ARG, MRCM_ERR_CUDA.
+ */
+int mrcm_solve(mrcm_ctx* ctx, const double* q_dev, const double* bc_val_dev,
+               double* p_dev, double* Fx_dev, double* Fy_dev, double* Fz_dev,
+               double* iface_dev);
+
+/* Keys of mrcm_query. */
+enum {
+    MRCM_Q_LEAVES = 0,        /* number of leaves                            */
+    MRCM_Q_SEGMENTS = 1,      /* number of interface segments                */
+    MRCM_Q_LEVELS = 2,        /* tree height (merge steps from leaf to root) */
+    MRCM_Q_NODES = 3,         /* tree nodes, leaves included                 */
+    MRCM_Q_WORKSPACE_BYTES = 4,
+    MRCM_Q_MAX_GAMMA = 5,     /* largest interface system size 2g            */
+    MRCM_Q_BUILD_FLOPS = 6,   /* algorithmic FP64 flops of mrcm_build_basis  */
+    MRCM_Q_SOLVE_FLOPS = 7,   /* algorithmic FP64 flops of mrcm_solve        */
+    MRCM_Q_LEAF_FLOPS = 8,    /* part of BUILD_FLOPS in the leaf kernel      */
+    MRCM_Q_KERNEL_LAUNCHES_BUILD = 9, /* kernels launched by one build call  */
+    MRCM_Q_KERNEL_LAUNCHES_SOLVE = 10 /* kernels launched by one solve call  */
+};
+
+/* mrcm_query -- integer facts about a context.  value: host out pointer. */
+int mrcm_query(const mrcm_ctx* ctx, int what, long long* value);
+
+/*
+ * mrcm_plan_query -- the same integer facts as mrcm_query (keys
+ * MRCM_Q_LEAVES .. MRCM_Q_LEAF_FLOPS except WORKSPACE_BYTES, which is 0),
+ * computed from the decomposition alone on the host: no device, no CUDA
+ * call.  Arguments as in mrcm_setup; value: host out pointer.
+ */
+int mrcm_plan_query(const mrcm_grid* g, const int sub_cells[3], const int seg_cells[3],
+                    const int bc_type[6], int what, long long* value);
+
+/* Phases timed by mrcm_phase_times. */
+enum {
+    MRCM_PHASE_COEF = 0,        /* permeability check, Robin and face coefficients */
+    MRCM_PHASE_LEAF_BUILD = 1,  /* leaf factorisation and Robin-to-flux maps      */
+    MRCM_PHASE_MERGE_BUILD = 2, /* all interface merges of the build              */
+    MRCM_PHASE_LEAF_PART = 3,   /* leaf particular solutions (solve)              */
+    MRCM_PHASE_TREE_SOLVE = 4,  /* up-sweep, root, down-sweep (solve)             */
+    MRCM_PHASE_LEAF_FINAL = 5,  /* final leaf pressures and fluxes (solve)        */
+    MRCM_PHASE_FINISH = 6,      /* skeleton fluxes and mean shift (solve)         */
+    MRCM_PHASE_COUNT = 7
+};
+
+/*
+ * mrcm_enable_timing -- on != 0: record a CUDA event pair around every phase
+ * of the following build / solve calls (on the context's stream).
+ * mrcm_phase_times -- ms[MRCM_PHASE_COUNT] (host) receives the durations of
+ * the phases of the most recent build and solve (0 where not run).  Only
+ * valid after a call made with timing enabled.
+ */
+int mrcm_enable_timing(mrcm_ctx* ctx, int on);
+int mrcm_phase_times(mrcm_ctx* ctx, double* ms);
+
+/*
+ * Introspection for tests (host buffers, synchronous).
+ *
+ * mrcm_node_info: info[0] = height (0 for leaves), info[1] = m (outer
+ * segments), info[2] = g (segments on the node's internal interface gamma,
+ * 0 for leaves), info[3], info[4] = children (-1 for leaves), info[5] =
+ * parent (-1 for the root), info[6] = leaf index or -1, info[7..10] = leaf
+ * box I0, I1, J0, J1 (half-open).  Nodes 0..leaves-1 are the leaves.
+ *
+ * mrcm_node_segments: seg_ids[m] = the node's outer segments in the order
+ * its R uses.
+ *
+ * mrcm_segment_info: info[0] = axis of the normal, info[1] = face line
+ * (x-face index for axis 0, y-face index for axis 1), info[2] = first cell
+ * along the segment, info[3] = number of faces, info[4] = leaf on side a,
+ * info[5] = leaf on side b.
+ *
+ * mrcm_node_operator: R_host[m*m] (row-major) = the node's Robin-to-flux
+ * map (outward segment fluxes per unit Robin datum) after mrcm_build_basis;
+ * rbar_host[m] (may be NULL) = its particular fluxes after mrcm_solve.
+ */
+int mrcm_node_info(const mrcm_ctx* ctx, int node, int info[11]);
+int mrcm_node_segments(const mrcm_ctx* ctx, int node, int* seg_ids);
+int mrcm_segment_info(const mrcm_ctx* ctx, int seg, int info[6]);
+int mrcm_node_operator(mrcm_ctx* ctx, int node, double* R_host, double* rbar_host);
+
+/* mrcm_destroy -- free all device and host resources (NULL is a no-op). */
+void mrcm_destroy(mrcm_ctx* ctx);
+
+/* mrcm_error_string -- static text for an MRCM_* code. */
+const char* mrcm_error_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MRCM_H */

@@ -1,0 +1,16 @@
+"""GB300-native Recursive MRCM (arXiv 2009.07965) for 2D Darcy flow.
+
+The compute path is libmrcm.so (hand-written sm_103a CUDA behind the C ABI
+of include/mrcm.h); this package only builds it and marshals arguments.
+"""
+from .binding import (mrcm_setup, mrcm_plan_query, mrcm_set_permeability, mrcm_build_basis, mrcm_solve,
+                      mrcm_query, mrcm_node_info, mrcm_node_segments, mrcm_segment_info,
+                      mrcm_node_operator, mrcm_destroy, mrcm_error_string, mrcm_enable_timing,
+                      mrcm_phase_times, MrcmError, PHASES,
+                      EXPORTS, LIB_PATH)
+from .solver import Solver
+
+__all__ = ["mrcm_setup", "mrcm_plan_query", "mrcm_set_permeability", "mrcm_build_basis", "mrcm_solve", "mrcm_query",
+           "mrcm_node_info", "mrcm_node_segments", "mrcm_segment_info", "mrcm_node_operator",
+           "mrcm_destroy", "mrcm_error_string", "mrcm_enable_timing", "mrcm_phase_times",
+           "MrcmError", "PHASES", "EXPORTS", "LIB_PATH", "Solver"]

@@ -1,0 +1,190 @@
+"""ctypes binding of libmrcm (include/mrcm.h): argument marshalling only.
+
+The functions below carry the C names and pass plain pointers and sizes
+through; device buffers are torch CUDA tensors (float64, contiguous).  The
+library must have been built (paper_2009_07965_gb300.build.build()); there
+is no fallback path.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmrcm.so")
+
+MRCM_BC_NEUMANN, MRCM_BC_DIRICHLET = 0, 1
+MRCM_FP64, MRCM_MIXED, MRCM_SURROGATE = 0, 1, 2
+ERRORS = {0: "MRCM_OK", -1: "MRCM_ERR_INVALID_ARG", -2: "MRCM_ERR_SHAPE", -3: "MRCM_ERR_BAD_K",
+          -4: "MRCM_ERR_NOT_BUILT", -5: "MRCM_ERR_SINGULAR", -6: "MRCM_ERR_CUDA",
+          -7: "MRCM_ERR_OOM", -8: "MRCM_ERR_TIMEOUT", -9: "MRCM_ERR_UNSUPPORTED"}
+Q = dict(LEAVES=0, SEGMENTS=1, LEVELS=2, NODES=3, WORKSPACE_BYTES=4, MAX_GAMMA=5,
+         BUILD_FLOPS=6, SOLVE_FLOPS=7, LEAF_FLOPS=8, KERNEL_LAUNCHES_BUILD=9,
+         KERNEL_LAUNCHES_SOLVE=10)
+
+# every symbol include/mrcm.h declares
+EXPORTS = ["mrcm_setup", "mrcm_plan_query", "mrcm_set_permeability", "mrcm_build_basis", "mrcm_solve", "mrcm_query",
+           "mrcm_node_info", "mrcm_node_segments", "mrcm_segment_info", "mrcm_node_operator",
+           "mrcm_destroy", "mrcm_error_string", "mrcm_enable_timing", "mrcm_phase_times"]
+PHASES = ["coef", "leaf_build", "merge_build", "leaf_particular", "tree_solve", "leaf_final", "finish"]
+
+
+class MrcmError(RuntimeError):
+    def __init__(self, code, call):
+        self.code = code
+        super().__init__(f"{call} failed: {ERRORS.get(code, code)} ({_lib().mrcm_error_string(code).decode()})")
+
+
+class mrcm_grid(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("L", ctypes.c_double * 3)]
+
+
+_LIB = None
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with paper_2009_07965_gb300.build.build()")
+        lib = ctypes.CDLL(LIB_PATH)
+        P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        IP = ctypes.POINTER(ctypes.c_int)
+        lib.mrcm_setup.argtypes = [ctypes.POINTER(P), ctypes.POINTER(mrcm_grid), P, IP, IP, D, IP, I, P]
+        lib.mrcm_setup.restype = I
+        lib.mrcm_plan_query.argtypes = [ctypes.POINTER(mrcm_grid), IP, IP, IP, I,
+                                        ctypes.POINTER(ctypes.c_longlong)]
+        lib.mrcm_plan_query.restype = I
+        lib.mrcm_set_permeability.argtypes = [P, P]
+        lib.mrcm_set_permeability.restype = I
+        lib.mrcm_build_basis.argtypes = [P]
+        lib.mrcm_build_basis.restype = I
+        lib.mrcm_solve.argtypes = [P, P, P, P, P, P, P, P]
+        lib.mrcm_solve.restype = I
+        lib.mrcm_query.argtypes = [P, I, ctypes.POINTER(ctypes.c_longlong)]
+        lib.mrcm_query.restype = I
+        lib.mrcm_node_info.argtypes = [P, I, IP]
+        lib.mrcm_node_info.restype = I
+        lib.mrcm_node_segments.argtypes = [P, I, IP]
+        lib.mrcm_node_segments.restype = I
+        lib.mrcm_segment_info.argtypes = [P, I, IP]
+        lib.mrcm_segment_info.restype = I
+        lib.mrcm_node_operator.argtypes = [P, I, P, P]
+        lib.mrcm_node_operator.restype = I
+        lib.mrcm_enable_timing.argtypes = [P, I]
+        lib.mrcm_enable_timing.restype = I
+        lib.mrcm_phase_times.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
+        lib.mrcm_phase_times.restype = I
+        lib.mrcm_destroy.argtypes = [P]
+        lib.mrcm_destroy.restype = None
+        lib.mrcm_error_string.argtypes = [I]
+        lib.mrcm_error_string.restype = ctypes.c_char_p
+        _LIB = lib
+    return _LIB
+
+
+def _check(code, call):
+    if code != 0:
+        raise MrcmError(code, call)
+
+
+def _ptr(t):
+    """Device (or host) address of a tensor / array, or None."""
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    if hasattr(t, "ctypes"):
+        return t.ctypes.data
+    return int(t)
+
+
+def _ints(vals, n):
+    vals = list(vals) + [0] * (n - len(vals))
+    return (ctypes.c_int * n)(*vals)
+
+
+def mrcm_setup(n, L, K, sub_cells=(16, 16), seg_cells=(4, 4), alpha=1.0,
+               bc_type=(1, 1, 0, 0), precision=MRCM_FP64, stream=0):
+    g = mrcm_grid(2, (ctypes.c_int * 3)(n[0], n[1], 1), (ctypes.c_double * 3)(L[0], L[1], 1.0))
+    ctx = ctypes.c_void_p()
+    _check(_lib().mrcm_setup(ctypes.byref(ctx), ctypes.byref(g), _ptr(K), _ints(sub_cells, 3),
+                             _ints(seg_cells, 3), float(alpha), _ints(bc_type, 6), int(precision),
+                             stream), "mrcm_setup")
+    return ctx
+
+
+def mrcm_plan_query(n, L, sub_cells, seg_cells, bc_type, what):
+    g = mrcm_grid(2, (ctypes.c_int * 3)(n[0], n[1], 1), (ctypes.c_double * 3)(L[0], L[1], 1.0))
+    v = ctypes.c_longlong()
+    key = Q[what] if isinstance(what, str) else int(what)
+    _check(_lib().mrcm_plan_query(ctypes.byref(g), _ints(sub_cells, 3), _ints(seg_cells, 3),
+                                  _ints(bc_type, 6), key, ctypes.byref(v)), "mrcm_plan_query")
+    return v.value
+
+
+def mrcm_set_permeability(ctx, K):
+    _check(_lib().mrcm_set_permeability(ctx, _ptr(K)), "mrcm_set_permeability")
+
+
+def mrcm_build_basis(ctx):
+    _check(_lib().mrcm_build_basis(ctx), "mrcm_build_basis")
+
+
+def mrcm_solve(ctx, q, bc_val, p, Fx, Fy, Fz=None, iface=None):
+    _check(_lib().mrcm_solve(ctx, _ptr(q), _ptr(bc_val), _ptr(p), _ptr(Fx), _ptr(Fy), _ptr(Fz),
+                             _ptr(iface)), "mrcm_solve")
+
+
+def mrcm_query(ctx, what):
+    v = ctypes.c_longlong()
+    key = Q[what] if isinstance(what, str) else int(what)
+    _check(_lib().mrcm_query(ctx, key, ctypes.byref(v)), "mrcm_query")
+    return v.value
+
+
+def mrcm_node_info(ctx, node):
+    info = (ctypes.c_int * 11)()
+    _check(_lib().mrcm_node_info(ctx, node, info), "mrcm_node_info")
+    keys = ["height", "m", "g", "c1", "c2", "parent", "leaf", "I0", "I1", "J0", "J1"]
+    return dict(zip(keys, list(info)))
+
+
+def mrcm_node_segments(ctx, node):
+    m = mrcm_node_info(ctx, node)["m"]
+    buf = (ctypes.c_int * max(m, 1))()
+    _check(_lib().mrcm_node_segments(ctx, node, buf), "mrcm_node_segments")
+    return list(buf)[:m]
+
+
+def mrcm_segment_info(ctx, seg):
+    info = (ctypes.c_int * 6)()
+    _check(_lib().mrcm_segment_info(ctx, seg, info), "mrcm_segment_info")
+    return dict(zip(["axis", "line", "lo", "len", "a", "b"], list(info)))
+
+
+def mrcm_node_operator(ctx, node, with_rbar=False):
+    import numpy as np
+    m = mrcm_node_info(ctx, node)["m"]
+    R = np.zeros((m, m))
+    rbar = np.zeros(m) if with_rbar else None
+    _check(_lib().mrcm_node_operator(ctx, node, R.ctypes.data if m else R.ctypes.data,
+                                     rbar.ctypes.data if with_rbar else None), "mrcm_node_operator")
+    return (R, rbar) if with_rbar else R
+
+
+def mrcm_enable_timing(ctx, on=True):
+    _check(_lib().mrcm_enable_timing(ctx, 1 if on else 0), "mrcm_enable_timing")
+
+
+def mrcm_phase_times(ctx):
+    ms = (ctypes.c_double * len(PHASES))()
+    _check(_lib().mrcm_phase_times(ctx, ms), "mrcm_phase_times")
+    return dict(zip(PHASES, list(ms)))
+
+
+def mrcm_destroy(ctx):
+    if ctx:
+        _lib().mrcm_destroy(ctx)
+
+
+def mrcm_error_string(code):
+    return _lib().mrcm_error_string(code).decode()

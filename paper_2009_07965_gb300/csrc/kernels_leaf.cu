@@ -1,0 +1,485 @@
+// Leaf kernels: the local Robin problems of every finest-level subdomain.
+//
+// arXiv 2009.07965, Eqs. (11.2)-(12.2) on one leaf with lumped RT0 (two-point
+// fluxes).  On a skeleton face e of segment t the Robin term gives the
+// outward flux F_e = rho_e (p_c - lambda_t), lambda_t = P_t - beta_t U_t
+// (n_t . n^i), so the interface data of the MMBF problems (Eqs.
+// 11Hhatbasisa / 11Hhatbasisb) enter only through one Robin datum per
+// segment.  With the leaf pressure matrix A (SPD: two-point couplings plus
+// the Robin / Dirichlet diagonal) and B[c, s] = rho_e for the face e of cell
+// c in segment s:
+//     p = A^-1 (bbar + B lambda),   F_s = (B^T A^-1 B - W) lambda + B^T A^-1 bbar,
+// W_s = sum_{e in s} rho_e.  The Robin-to-flux map R = B^T A^-1 B - W holds
+// the traces of all MMBFs of the leaf (coefficient-tracking remark, Section
+// 3.2); bbar carries the source and external boundary data (Eqs. addu, addp).
+//
+// Layout and mapping.  16 threads own one leaf (two leaves per warp); cells
+// are ordered x fastest, so A is banded with half-bandwidth w (leaf width).
+// A = L D L^T is factored right-looking over a circular window of w+2 band
+// rows in shared memory; each step also advances the multi-right-hand-side
+// forward solve Z = L^-1 B and accumulates R += z_k z_k^T / d_k, so no
+// column of L is read twice.  The multipliers L, 1/d and Z are written to
+// global memory for the solve phase.  Every FP64 instruction does useful
+// work on all 16 lanes except the pivot reciprocal.
+#include "mrcm_internal.h"
+
+namespace mrcm {
+namespace {
+
+constexpr int kWin = kMaxLeafSide + 2;   // circular window rows
+
+template <int MMAX>
+struct LeafBuildSmem {
+    double win[kWin][kMaxLeafSide + 1];  // win[row % (w+2)][o] = A[row][row - o]
+    double zw[kWin][MMAX];               // rows of Z being updated
+    double R[MMAX][MMAX];                // lower triangle of B^T A^-1 B
+    double W[MMAX];                      // sum of rho per segment
+    double lcol[kMaxLeafSide];           // column k of L below the diagonal
+    double zk[MMAX];                     // row k of Z
+    double uk[MMAX];                     // row k of Z / d_k
+};
+
+// (row, col) of entry idx of a lower triangle stored row by row.
+__device__ __forceinline__ void tri_index(int idx, int& r, int& c) {
+    r = (int)((sqrtf(8.0f * idx + 1.0f) - 1.0f) * 0.5f);
+    while ((r + 1) * (r + 2) / 2 <= idx) ++r;
+    while (r * (r + 1) / 2 > idx) --r;
+    c = idx - r * (r + 1) / 2;
+}
+
+// Face coefficients around local cell (i, j) of leaf L.
+struct CellFaces {
+    double w_, e_, s_, n_;   // coefficient seen from the cell: west, east, south, north
+    double tx, ty;           // couplings to the west / south neighbour inside the leaf
+};
+
+__device__ __forceinline__ CellFaces cell_faces(const DevView& v, const LeafDesc& L, int i, int j) {
+    const int gi = L.i0 + i, gj = L.j0 + j;
+    const long long fx = gi + (long long)(v.nx + 1) * gj;
+    const long long fy = gi + (long long)v.nx * gj;
+    CellFaces c;
+    c.w_ = v.cxU[fx];
+    c.e_ = v.cxL[fx + 1];
+    c.s_ = v.cyU[fy];
+    c.n_ = v.cyL[fy + v.nx];
+    c.tx = (i > 0) ? v.cxL[fx] : 0.0;
+    c.ty = (j > 0) ? v.cyL[fy] : 0.0;
+    return c;
+}
+
+// Local segments of the Robin faces of cell (i, j), -1 where the face is not
+// on the skeleton.
+__device__ __forceinline__ void cell_robin_segments(const DevView& v, const LeafDesc& L, int i, int j,
+                                                    int& sw, int& se, int& ss, int& sn) {
+    sw = (i == 0 && L.side_off[0] >= 0) ? L.side_off[0] + j / v.gy : -1;
+    se = (i == L.w - 1 && L.side_off[1] >= 0) ? L.side_off[1] + j / v.gy : -1;
+    ss = (j == 0 && L.side_off[2] >= 0) ? L.side_off[2] + i / v.gx : -1;
+    sn = (j == L.h - 1 && L.side_off[3] >= 0) ? L.side_off[3] + i / v.gx : -1;
+}
+
+template <int MMAX>
+__device__ __forceinline__ void init_row(const DevView& v, const LeafDesc& L, LeafBuildSmem<MMAX>& S,
+                                         int row, int t, double* Wacc) {
+    const int w = L.w, m = L.m;
+    const int i = row % w, j = row / w;
+    const int slot = row % (w + 2);
+    const CellFaces f = cell_faces(v, L, i, j);
+    for (int o = t; o <= w; o += kLeafThreads) {
+        double a = 0.0;
+        if (o == 0) a = (f.w_ + f.e_) + (f.s_ + f.n_);
+        if (o == 1 && i > 0) a = -f.tx;
+        if (o == w && j > 0) a = -f.ty;   // w == 1: the y neighbour sits at offset 1
+        S.win[slot][o] = a;
+    }
+    int sw, se, ss, sn;
+    cell_robin_segments(v, L, i, j, sw, se, ss, sn);
+    int q = 0;
+    for (int s = t; s < m; s += kLeafThreads, ++q) {
+        double b = 0.0;
+        if (s == sw) b = f.w_;
+        if (s == se) b = f.e_;
+        if (s == ss) b = f.s_;
+        if (s == sn) b = f.n_;
+        S.zw[slot][s] = b;
+        Wacc[q] += b;
+    }
+}
+
+template <int MMAX, int LPB>
+__global__ void __launch_bounds__(kLeafThreads * LPB)
+leaf_build_kernel(DevView v) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int t = threadIdx.x & (kLeafThreads - 1);
+    const int slot_leaf = threadIdx.x / kLeafThreads;
+    const int leaf = blockIdx.x * LPB + slot_leaf;
+    if (leaf >= v.nleaf) return;     // uniform over the 16 threads of the leaf
+    const unsigned mask = 0xFFFFu << (threadIdx.x & 16);
+    LeafBuildSmem<MMAX>& S = reinterpret_cast<LeafBuildSmem<MMAX>*>(smem_raw)[slot_leaf];
+    const LeafDesc L = v.leaves[leaf];
+    const int w = L.w, n = L.w * L.h, m = L.m, W2 = L.w + 2;
+    double* Lg = v.leafL + L.L_off;          // n x 16 multipliers
+    double* Dg = Lg + (long long)n * kLeafThreads;   // n reciprocal pivots
+    double* Zg = v.leafZ + L.Z_off;          // n x m
+
+    constexpr int NQ = (MMAX + kLeafThreads - 1) / kLeafThreads;
+    double Wacc[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) Wacc[q] = 0.0;
+    for (int idx = t; idx < m * m; idx += kLeafThreads) S.R[idx / m][idx % m] = 0.0;
+    const int first = min(w, n - 1);
+    for (int r = 0; r <= first; ++r) init_row(v, L, S, r, t, Wacc);
+    __syncwarp(mask);
+
+    bool bad_pivot = false;
+    const int ntri_m = m * (m + 1) / 2;
+    for (int k = 0; k < n; ++k) {
+        // ---- phase A: pivot, multipliers, row k of Z -------------------------
+        const int sk = k % W2;
+        const double dk = S.win[sk][0];
+        bad_pivot |= !(dk > 0.0);
+        const double rcp = 1.0 / dk;
+        const int wk = min(w, n - 1 - k);
+        if (t < wk) {
+            const double l = S.win[(k + 1 + t) % W2][1 + t] * rcp;
+            S.lcol[t] = l;
+            Lg[(long long)k * kLeafThreads + t] = l;
+        }
+        if (t == 0) Dg[k] = rcp;
+        for (int s = t; s < m; s += kLeafThreads) {
+            const double z = S.zw[sk][s];
+            S.zk[s] = z;
+            S.uk[s] = z * rcp;
+            Zg[(long long)k * m + s] = z;
+        }
+        __syncwarp(mask);
+        // ---- phase B: trailing band update, Z update, R update, new row -----
+        const int ntri_w = wk * (wk + 1) / 2;
+        for (int idx = t; idx < ntri_w; idx += kLeafThreads) {
+            int a, b;
+            tri_index(idx, a, b);
+            S.win[(k + 1 + a) % W2][a - b] -= S.lcol[a] * S.win[(k + 1 + b) % W2][1 + b];
+        }
+        for (int s = t; s < m; s += kLeafThreads) {
+            const double z = S.zk[s];
+            for (int a = 0; a < wk; ++a) S.zw[(k + 1 + a) % W2][s] -= S.lcol[a] * z;
+        }
+        for (int idx = t; idx < ntri_m; idx += kLeafThreads) {
+            int r, c;
+            tri_index(idx, r, c);
+            S.R[r][c] += S.zk[r] * S.uk[c];
+        }
+        if (k + w + 1 < n) init_row(v, L, S, k + w + 1, t, Wacc);
+        __syncwarp(mask);
+    }
+    if (bad_pivot) atomicOr(v.status, kStatusSingular);
+    {
+        int q = 0;
+        for (int s = t; s < m; s += kLeafThreads, ++q) S.W[s] = Wacc[q];
+    }
+    __syncwarp(mask);
+    double* Rg = v.R + L.R_off;
+    for (int idx = t; idx < m * m; idx += kLeafThreads) {
+        const int r = idx / m, c = idx % m;
+        double val = (r >= c) ? S.R[r][c] : S.R[c][r];
+        if (r == c) val -= S.W[r];
+        Rg[idx] = val;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Solve phase.  Right-hand side of the particular problem (Eqs. addu/addp):
+// source plus Dirichlet and Neumann data of the leaf's domain-boundary faces.
+__device__ __forceinline__ double particular_rhs(const DevView& v, const LeafDesc& L, const double* q,
+                                                 const double* bc_val, int row) {
+    const int i = row % L.w, j = row / L.w;
+    const int gi = L.i0 + i, gj = L.j0 + j;
+    double b = q[(long long)gj * v.nx + gi];
+    if (gi == 0) {
+        const double g = bc_val[gj];
+        b += v.bc[0] ? v.cxU[(long long)(v.nx + 1) * gj] * g : -v.hy * g;
+    }
+    if (gi == v.nx - 1) {
+        const double g = bc_val[v.ny + gj];
+        b += v.bc[1] ? v.cxL[v.nx + (long long)(v.nx + 1) * gj] * g : -v.hy * g;
+    }
+    if (gj == 0) {
+        const double g = bc_val[2 * v.ny + gi];
+        b += v.bc[2] ? v.cyU[gi] * g : -v.hx * g;
+    }
+    if (gj == v.ny - 1) {
+        const double g = bc_val[2 * v.ny + v.nx + gi];
+        b += v.bc[3] ? v.cyL[gi + (long long)v.nx * v.ny] * g : -v.hx * g;
+    }
+    return b;
+}
+
+struct LeafSolveSmem {
+    double buf[kWin];                                  // circular sweep rows
+    double y[kMaxLeafSide * kMaxLeafSide];             // D^-1 z (or the pressures)
+};
+
+template <int LPB>
+__global__ void __launch_bounds__(kLeafThreads * LPB)
+leaf_particular_kernel(DevView v, const double* __restrict__ q, const double* __restrict__ bc_val) {
+    __shared__ LeafSolveSmem smem[LPB];
+    const int t = threadIdx.x & (kLeafThreads - 1);
+    const int slot_leaf = threadIdx.x / kLeafThreads;
+    const int leaf = blockIdx.x * LPB + slot_leaf;
+    if (leaf >= v.nleaf) return;
+    const unsigned mask = 0xFFFFu << (threadIdx.x & 16);
+    LeafSolveSmem& S = smem[slot_leaf];
+    const LeafDesc L = v.leaves[leaf];
+    const int w = L.w, n = L.w * L.h, m = L.m, W2 = L.w + 2;
+    const double* Lg = v.leafL + L.L_off;
+    const double* Dg = Lg + (long long)n * kLeafThreads;
+    const double* Zg = v.leafZ + L.Z_off;
+    double* zb = v.leafzb + L.zb_off;
+
+    // forward sweep zbar = L^-1 bbar (unit lower band)
+    const int first = min(w, n - 1);
+    for (int r = t; r <= first; r += kLeafThreads) S.buf[r % W2] = particular_rhs(v, L, q, bc_val, r);
+    __syncwarp(mask);
+    for (int k = 0; k < n; ++k) {
+        const double zk = S.buf[k % W2];
+        const int wk = min(w, n - 1 - k);
+        if (t < wk) S.buf[(k + 1 + t) % W2] -= Lg[(long long)k * kLeafThreads + t] * zk;
+        if (t == 0) {
+            zb[k] = zk;
+            if (k + w + 1 < n) S.buf[(k + w + 1) % W2] = particular_rhs(v, L, q, bc_val, k + w + 1);
+        }
+        __syncwarp(mask);
+    }
+    // y = D^-1 zbar ; rbar = Z^T y  (= B^T A^-1 bbar)
+    for (int k = t; k < n; k += kLeafThreads) S.y[k] = zb[k] * Dg[k];
+    __syncwarp(mask);
+    double* rb = v.rbar + L.r_off;
+    for (int s = t; s < m; s += kLeafThreads) {
+        double acc = 0.0;
+        for (int k = 0; k < n; ++k) acc += Zg[(long long)k * m + s] * S.y[k];
+        rb[s] = acc;
+    }
+}
+
+template <int LPB>
+__global__ void __launch_bounds__(kLeafThreads * LPB)
+leaf_final_kernel(DevView v, const double* __restrict__ q, const double* __restrict__ bc_val,
+                  double* __restrict__ p, double* __restrict__ Fx, double* __restrict__ Fy) {
+    __shared__ LeafSolveSmem smem[LPB];
+    __shared__ double lam_s[LPB][64];
+    const int t = threadIdx.x & (kLeafThreads - 1);
+    const int slot_leaf = threadIdx.x / kLeafThreads;
+    const int leaf = blockIdx.x * LPB + slot_leaf;
+    if (leaf >= v.nleaf) return;
+    const unsigned mask = 0xFFFFu << (threadIdx.x & 16);
+    LeafSolveSmem& S = smem[slot_leaf];
+    double* lam = lam_s[slot_leaf];
+    const LeafDesc L = v.leaves[leaf];
+    const int w = L.w, h = L.h, n = L.w * L.h, m = L.m, W2 = L.w + 2;
+    const double* Lg = v.leafL + L.L_off;
+    const double* Dg = Lg + (long long)n * kLeafThreads;
+    const double* Zg = v.leafZ + L.Z_off;
+    const double* zb = v.leafzb + L.zb_off;
+    for (int s = t; s < m; s += kLeafThreads) lam[s] = v.lam[L.r_off + s];
+    __syncwarp(mask);
+    // y = D^-1 (zbar + Z lambda)
+    for (int k = t; k < n; k += kLeafThreads) {
+        double acc = zb[k];
+        for (int s = 0; s < m; ++s) acc += Zg[(long long)k * m + s] * lam[s];
+        S.y[k] = acc * Dg[k];
+    }
+    __syncwarp(mask);
+    // backward sweep L^T p = y, right-looking from the last row
+    const int first = min(w, n - 1);
+    for (int r = t; r <= first; r += kLeafThreads) S.buf[(n - 1 - r) % W2] = S.y[n - 1 - r];
+    __syncwarp(mask);
+    for (int k = n - 1; k >= 0; --k) {
+        const double pk = S.buf[k % W2];
+        const int wk = min(w, k);
+        if (t < wk) {
+            const int i = k - 1 - t;   // row of L^T: entry L[k][i] = multiplier (i, k - i - 1)
+            S.buf[i % W2] -= Lg[(long long)i * kLeafThreads + t] * pk;
+        }
+        if (t == 0) {
+            S.y[k] = pk;   // y[k] is no longer needed: keep p in its place
+            if (k - w - 1 >= 0) S.buf[(k - w - 1) % W2] = S.y[k - w - 1];
+        }
+        __syncwarp(mask);
+    }
+    // pressures
+    for (int k = t; k < n; k += kLeafThreads) {
+        const int i = k % w, j = k / w;
+        p[(long long)(L.j0 + j) * v.nx + L.i0 + i] = S.y[k];
+    }
+    // x faces of the leaf: i = 0..w (local), rows j
+    const long long nxf1 = v.nx + 1;
+    for (int idx = t; idx < (w + 1) * h; idx += kLeafThreads) {
+        const int i = idx % (w + 1), j = idx / (w + 1);
+        const int gi = L.i0 + i, gj = L.j0 + j;
+        const long long f = gi + nxf1 * gj;
+        if (i > 0 && i < w) {
+            Fx[f] = v.cxL[f] * (S.y[j * w + i - 1] - S.y[j * w + i]);
+        } else if (gi == 0) {
+            const double g = bc_val[gj];
+            const double out = v.bc[0] ? v.cxU[f] * (S.y[j * w] - g) : v.hy * g;
+            Fx[f] = -out;
+        } else if (gi == v.nx) {
+            const double g = bc_val[v.ny + gj];
+            const double out = v.bc[1] ? v.cxL[f] * (S.y[j * w + w - 1] - g) : v.hy * g;
+            Fx[f] = out;
+        } else {
+            // skeleton face: one-sided flux of this leaf, +x direction
+            const bool side_a = (i == w);
+            const int s = side_a ? L.side_off[1] + j / v.gy : L.side_off[0] + j / v.gy;
+            const int seg = v.leaf_segs[L.seg_off + s];
+            const int e = gj - v.seg_lo[seg];
+            const double pc = S.y[j * w + (side_a ? w - 1 : 0)];
+            const double out = (side_a ? v.cxL[f] : v.cxU[f]) * (pc - lam[s]);
+            v.skel[2 * (long long)(v.seg_face_off[seg] + e) + (side_a ? 0 : 1)] = side_a ? out : -out;
+        }
+    }
+    // y faces: j = 0..h, columns i
+    const long long nxl = v.nx;
+    for (int idx = t; idx < w * (h + 1); idx += kLeafThreads) {
+        const int i = idx % w, j = idx / w;
+        const int gi = L.i0 + i, gj = L.j0 + j;
+        const long long f = gi + nxl * gj;
+        if (j > 0 && j < h) {
+            Fy[f] = v.cyL[f] * (S.y[(j - 1) * w + i] - S.y[j * w + i]);
+        } else if (gj == 0) {
+            const double g = bc_val[2 * v.ny + gi];
+            const double out = v.bc[2] ? v.cyU[f] * (S.y[i] - g) : v.hx * g;
+            Fy[f] = -out;
+        } else if (gj == v.ny) {
+            const double g = bc_val[2 * v.ny + v.nx + gi];
+            const double out = v.bc[3] ? v.cyL[f] * (S.y[(h - 1) * w + i] - g) : v.hx * g;
+            Fy[f] = out;
+        } else {
+            const bool side_a = (j == h);
+            const int s = side_a ? L.side_off[3] + i / v.gx : L.side_off[2] + i / v.gx;
+            const int seg = v.leaf_segs[L.seg_off + s];
+            const int e = gi - v.seg_lo[seg];
+            const double pc = S.y[(side_a ? h - 1 : 0) * w + i];
+            const double out = (side_a ? v.cyL[f] : v.cyU[f]) * (pc - lam[s]);
+            v.skel[2 * (long long)(v.seg_face_off[seg] + e) + (side_a ? 0 : 1)] = side_a ? out : -out;
+        }
+    }
+}
+
+// Skeleton faces: mean of the two one-sided values; optional one-sided
+// output [Fa_x, Fb_x, Fa_y, Fb_y] (off the skeleton both equal F).
+__global__ void skeleton_flux_kernel(DevView v, double* Fx, double* Fy, double* iface) {
+    const long long nxf = (long long)(v.nx + 1) * v.ny;
+    const long long nyf = (long long)v.nx * (v.ny + 1);
+    long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (f >= nxf + nyf) return;
+    const bool xface = f < nxf;
+    const long long fl = xface ? f : f - nxf;
+    int axis, line, k;
+    if (xface) { axis = 0; line = (int)(fl % (v.nx + 1)); k = (int)(fl / (v.nx + 1)); }
+    else { axis = 1; k = (int)(fl % v.nx); line = (int)(fl / v.nx); }
+    const int nline = axis == 0 ? v.nx : v.ny;
+    const int sub = axis == 0 ? v.sx : v.sy;
+    double* F = xface ? Fx : Fy;
+    const bool skel = line > 0 && line < nline && line % sub == 0;
+    double fa, fb;
+    if (skel) {
+        // segment: carried by the + side of the leaf below the line
+        int leaf, side, pos;
+        const int nlx = (v.nx + v.sx - 1) / v.sx;
+        if (axis == 0) { leaf = (line / v.sx - 1) + nlx * (k / v.sy); side = 1; }
+        else { leaf = (k / v.sx) + nlx * (line / v.sy - 1); side = 3; }
+        const LeafDesc& L = v.leaves[leaf];
+        pos = axis == 0 ? (k - L.j0) / v.gy : (k - L.i0) / v.gx;
+        const int seg = v.leaf_segs[L.seg_off + L.side_off[side] + pos];
+        const long long e = v.seg_face_off[seg] + (k - v.seg_lo[seg]);
+        fa = v.skel[2 * e];
+        fb = v.skel[2 * e + 1];
+        F[fl] = 0.5 * (fa + fb);
+    } else {
+        if (!iface) return;
+        fa = fb = F[fl];
+    }
+    if (iface) {
+        if (xface) { iface[fl] = fa; iface[nxf + fl] = fb; }
+        else { iface[2 * nxf + fl] = fa; iface[2 * nxf + nyf + fl] = fb; }
+    }
+}
+
+constexpr int kRedBlocks = 256;
+
+__global__ void mean_partial_kernel(const double* __restrict__ p, long long n, double* red) {
+    __shared__ double sh[256];
+    double acc = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        acc += p[i];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) red[blockIdx.x] = sh[0];
+}
+
+__global__ void mean_subtract_kernel(double* __restrict__ p, long long n, const double* red) {
+    __shared__ double mean;
+    if (threadIdx.x == 0) {
+        double acc = 0.0;   // same order in every block: identical mean
+        for (int b = 0; b < kRedBlocks; ++b) acc += red[b];
+        mean = acc / (double)n;
+    }
+    __syncthreads();
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        p[i] -= mean;
+}
+
+}  // namespace
+
+cudaError_t launch_leaf_build(const DevView& v, int max_m, cudaStream_t s) {
+    if (max_m <= 16) {
+        constexpr int LPB = 8;
+        const size_t sm = sizeof(LeafBuildSmem<16>) * LPB;
+        cudaFuncSetAttribute(leaf_build_kernel<16, LPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        leaf_build_kernel<16, LPB><<<(v.nleaf + LPB - 1) / LPB, kLeafThreads * LPB, sm, s>>>(v);
+    } else {
+        constexpr int LPB = 2;
+        const size_t sm = sizeof(LeafBuildSmem<64>) * LPB;
+        cudaFuncSetAttribute(leaf_build_kernel<64, LPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        leaf_build_kernel<64, LPB><<<(v.nleaf + LPB - 1) / LPB, kLeafThreads * LPB, sm, s>>>(v);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_leaf_particular(const DevView& v, const double* q, const double* bc_val, int,
+                                   cudaStream_t s) {
+    constexpr int LPB = 8;
+    leaf_particular_kernel<LPB><<<(v.nleaf + LPB - 1) / LPB, kLeafThreads * LPB, 0, s>>>(v, q, bc_val);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_leaf_final(const DevView& v, const double* q, const double* bc_val, double* p,
+                              double* Fx, double* Fy, int, cudaStream_t s) {
+    constexpr int LPB = 8;
+    leaf_final_kernel<LPB><<<(v.nleaf + LPB - 1) / LPB, kLeafThreads * LPB, 0, s>>>(v, q, bc_val, p, Fx, Fy);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_skeleton_fluxes(const DevView& v, double* Fx, double* Fy, double* iface,
+                                   cudaStream_t s) {
+    const long long nf = (long long)(v.nx + 1) * v.ny + (long long)v.nx * (v.ny + 1);
+    skeleton_flux_kernel<<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(v, Fx, Fy, iface);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mean_shift(const DevView& v, double* p, cudaStream_t s) {
+    const long long n = (long long)v.nx * v.ny;
+    mean_partial_kernel<<<kRedBlocks, 256, 0, s>>>(p, n, v.red);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    mean_subtract_kernel<<<kRedBlocks, 256, 0, s>>>(p, n, v.red);
+    return cudaGetLastError();
+}
+
+}  // namespace mrcm

@@ -1,0 +1,147 @@
+// Permeability check, Robin coefficients and face coefficients (build step 1).
+//
+// Robin coefficient per segment t, Eqs. (robin.beta) and (permeff) of
+// arXiv 2009.07965 (Section 5.1):
+//     Keff_t = (1/N) sum_{e in t} 2 K_a K_b / (K_a + K_b),
+//     beta_t = alpha * Hbar_t / Keff_t,   Hbar_t = |t| (segment length),
+// and the coupling of the two Robin sides D_t = |t| / (2 beta_t).
+//
+// Face coefficients of the lumped RT0 (two-point flux) local operators,
+// seen from each of the two cells of a face:
+//     interior face:   T   = |e| / (h/(2K_a) + h/(2K_b))       (both sides)
+//     skeleton face:   rho = |e| / (h/(2K_c) + beta_t)         (Eq. 11.2, lumped)
+//     Dirichlet face:  tau = 2 K_c |e| / h,   Neumann face: 0.
+#include "mrcm_internal.h"
+
+namespace mrcm {
+namespace {
+
+__global__ void check_K_kernel(const double* __restrict__ K, long long n, int* status) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long stride = (long long)gridDim.x * blockDim.x;
+    bool bad = false;
+    for (; i < n; i += stride) {
+        double k = K[i];
+        // k > 0 is false for NaN; the upper bound rejects +inf
+        bad |= !(k > 0.0 && k < 1.0e300);
+    }
+    if (bad) atomicOr(status, kStatusBadK);
+}
+
+__global__ void seg_beta_kernel(DevView v) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= v.nseg) return;
+    const int axis = v.seg_axis[t], line = v.seg_line[t], lo = v.seg_lo[t], len = v.seg_len[t];
+    double sum = 0.0;
+    for (int e = 0; e < len; ++e) {
+        double ka, kb;
+        if (axis == 0) {
+            const long long row = (long long)(lo + e) * v.nx;
+            ka = v.K[row + line - 1];
+            kb = v.K[row + line];
+        } else {
+            ka = v.K[(long long)(line - 1) * v.nx + lo + e];
+            kb = v.K[(long long)line * v.nx + lo + e];
+        }
+        sum += 2.0 * ka * kb / (ka + kb);
+    }
+    const double keff = sum / len;
+    const double length = len * (axis == 0 ? v.hy : v.hx);
+    v.seg_beta[t] = v.alpha * length / keff;
+    // D = |t| / (2 beta) = Keff / (2 alpha)
+    v.seg_D[t] = keff / (2.0 * v.alpha);
+}
+
+// Global segment id and position of the skeleton face (axis, line, k), where
+// k is the cell index along the face; the leaf below the face (side a)
+// carries the segment on its + side.
+__device__ __forceinline__ int skeleton_segment(const DevView& v, int axis, int line, int k) {
+    int leaf, side, pos;
+    if (axis == 0) {
+        const int I = line / v.sx - 1, J = k / v.sy;
+        leaf = I + ((v.nx + v.sx - 1) / v.sx) * J;
+        side = 1;
+        pos = (k - v.leaves[leaf].j0) / v.gy;
+    } else {
+        const int I = k / v.sx, J = line / v.sy - 1;
+        leaf = I + ((v.nx + v.sx - 1) / v.sx) * J;
+        side = 3;
+        pos = (k - v.leaves[leaf].i0) / v.gx;
+    }
+    const LeafDesc& L = v.leaves[leaf];
+    return v.leaf_segs[L.seg_off + L.side_off[side] + pos];
+}
+
+__global__ void face_coef_kernel(DevView v) {
+    const long long nxf = (long long)(v.nx + 1) * v.ny;
+    const long long nyf = (long long)v.nx * (v.ny + 1);
+    long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (f < nxf) {
+        const int i = (int)(f % (v.nx + 1)), j = (int)(f / (v.nx + 1));
+        const double area = v.hy, hn = v.hx;
+        double cl = 0.0, cu = 0.0;
+        if (i == 0) {
+            if (v.bc[0]) cu = 2.0 * v.K[(long long)j * v.nx] * area / hn;
+        } else if (i == v.nx) {
+            if (v.bc[1]) cl = 2.0 * v.K[(long long)j * v.nx + v.nx - 1] * area / hn;
+        } else {
+            const double ka = v.K[(long long)j * v.nx + i - 1], kb = v.K[(long long)j * v.nx + i];
+            if (i % v.sx == 0) {
+                const double beta = v.seg_beta[skeleton_segment(v, 0, i, j)];
+                cl = 2.0 * ka * area / (hn + 2.0 * ka * beta);
+                cu = 2.0 * kb * area / (hn + 2.0 * kb * beta);
+            } else {
+                cl = cu = (2.0 * area / hn) * ka * kb / (ka + kb);
+            }
+        }
+        v.cxL[f] = cl;
+        v.cxU[f] = cu;
+        return;
+    }
+    f -= nxf;
+    if (f < nyf) {
+        const int i = (int)(f % v.nx), j = (int)(f / v.nx);
+        const double area = v.hx, hn = v.hy;
+        double cl = 0.0, cu = 0.0;
+        if (j == 0) {
+            if (v.bc[2]) cu = 2.0 * v.K[i] * area / hn;
+        } else if (j == v.ny) {
+            if (v.bc[3]) cl = 2.0 * v.K[(long long)(v.ny - 1) * v.nx + i] * area / hn;
+        } else {
+            const double ka = v.K[(long long)(j - 1) * v.nx + i], kb = v.K[(long long)j * v.nx + i];
+            if (j % v.sy == 0) {
+                const double beta = v.seg_beta[skeleton_segment(v, 1, j, i)];
+                cl = 2.0 * ka * area / (hn + 2.0 * ka * beta);
+                cu = 2.0 * kb * area / (hn + 2.0 * kb * beta);
+            } else {
+                cl = cu = (2.0 * area / hn) * ka * kb / (ka + kb);
+            }
+        }
+        v.cyL[f] = cl;
+        v.cyU[f] = cu;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_check_K(const DevView& v, cudaStream_t s) {
+    const long long n = (long long)v.nx * v.ny;
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    check_K_kernel<<<blocks, 256, 0, s>>>(v.K, n, v.status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seg_beta(const DevView& v, cudaStream_t s) {
+    if (v.nseg == 0) return cudaSuccess;
+    seg_beta_kernel<<<(v.nseg + 127) / 128, 128, 0, s>>>(v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_face_coef(const DevView& v, cudaStream_t s) {
+    const long long nf = (long long)(v.nx + 1) * v.ny + (long long)v.nx * (v.ny + 1);
+    face_coef_kernel<<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(v);
+    return cudaGetLastError();
+}
+
+}  // namespace mrcm

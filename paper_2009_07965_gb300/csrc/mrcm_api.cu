@@ -1,0 +1,692 @@
+// libmrcm: C ABI, planning of the decomposition and launch orchestration.
+//
+// Host side of the Recursive MRCM (arXiv 2009.07965): leaves and interface
+// segments (Section 2, Eqs. decomp.1-2; Section 4, intermediate scale
+// H-bar), the binary hierarchy of Section 3.1 (Eqs. dd.l, dd.2, interface.1)
+// and the order of the batched kernel launches that carry out Algorithm 1.
+// All arithmetic on problem data happens in the kernels.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <unordered_map>
+#include <vector>
+
+#include "mrcm_internal.h"
+#include "../../include/mrcm.h"
+
+using namespace mrcm;
+
+namespace {
+
+struct Plan {
+    int nx = 0, ny = 0;
+    double hx = 0, hy = 0, alpha = 0;
+    int sx = 0, sy = 0, gx = 0, gy = 0;
+    int bc[4] = {0, 0, 0, 0};
+    bool pure_neumann = false;
+    int Nlx = 0, Nly = 0, nleaf = 0;
+    std::vector<LeafDesc> leaves;
+    std::vector<int> leaf_segs;
+    // segments
+    std::vector<int> seg_axis, seg_line, seg_lo, seg_len, seg_a, seg_b, seg_face_off;
+    int nseg = 0;
+    long long nskel_faces = 0;
+    // tree (nodes 0..nleaf-1 are the leaves)
+    struct Node {
+        int box[4];
+        int height = 0, c1 = -1, c2 = -1, parent = -1, leaf = -1;
+        std::vector<int> segs;   // outer segments in R order
+        std::vector<int> gamma;  // gamma segments (internal nodes)
+        std::vector<int> map;    // gpos1, gpos2, opos1, opos2
+        int o1 = 0;
+    };
+    std::vector<Node> nodes;
+    int root = -1, height = 0;
+    std::vector<MergeDesc> merges;       // grouped by height (ascending)
+    std::vector<int> level_first, level_count, level_max_g2;  // index by height-1
+    std::vector<int> node_map, gamma_segs;
+    int max_m_leaf = 0, max_g2 = 0;
+    // storage sizes (doubles / ints)
+    long long nR = 0, nr = 0, nLU = 0, npiv = 0, nX = 0, nxb = 0, nL = 0, nZ = 0, nzb = 0;
+    std::vector<long long> node_R_off, node_r_off;
+    // flop model
+    long long leaf_flops = 0, merge_flops = 0, solve_flops = 0;
+};
+
+inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+int make_plan(Plan& P) {
+    P.Nlx = ceil_div(P.nx, P.sx);
+    P.Nly = ceil_div(P.ny, P.sy);
+    P.nleaf = P.Nlx * P.Nly;
+    P.leaves.resize(P.nleaf);
+    std::vector<int> xplus_first(P.nleaf, -1), yplus_first(P.nleaf, -1);
+    // leaves and the segments on their + sides
+    for (int J = 0; J < P.Nly; ++J)
+        for (int I = 0; I < P.Nlx; ++I) {
+            const int id = I + P.Nlx * J;
+            LeafDesc& L = P.leaves[id];
+            std::memset(&L, 0, sizeof(L));
+            L.i0 = I * P.sx;
+            L.j0 = J * P.sy;
+            L.w = std::min(P.sx, P.nx - L.i0);
+            L.h = std::min(P.sy, P.ny - L.j0);
+        }
+    for (int id = 0; id < P.nleaf; ++id) {
+        const int I = id % P.Nlx, J = id / P.Nlx;
+        const LeafDesc& L = P.leaves[id];
+        if (I + 1 < P.Nlx) {
+            xplus_first[id] = P.nseg;
+            for (int lo = 0; lo < L.h; lo += P.gy) {
+                P.seg_axis.push_back(0);
+                P.seg_line.push_back(L.i0 + L.w);
+                P.seg_lo.push_back(L.j0 + lo);
+                P.seg_len.push_back(std::min(P.gy, L.h - lo));
+                P.seg_a.push_back(id);
+                P.seg_b.push_back(id + 1);
+                ++P.nseg;
+            }
+        }
+        if (J + 1 < P.Nly) {
+            yplus_first[id] = P.nseg;
+            for (int lo = 0; lo < L.w; lo += P.gx) {
+                P.seg_axis.push_back(1);
+                P.seg_line.push_back(L.j0 + L.h);
+                P.seg_lo.push_back(L.i0 + lo);
+                P.seg_len.push_back(std::min(P.gx, L.w - lo));
+                P.seg_a.push_back(id);
+                P.seg_b.push_back(id + P.Nlx);
+                ++P.nseg;
+            }
+        }
+    }
+    P.seg_face_off.resize(P.nseg + 1);
+    P.seg_face_off[0] = 0;
+    for (int t = 0; t < P.nseg; ++t) P.seg_face_off[t + 1] = P.seg_face_off[t] + P.seg_len[t];
+    P.nskel_faces = P.seg_face_off[P.nseg];
+    // leaf segment lists: x-, x+, y-, y+ sides
+    for (int id = 0; id < P.nleaf; ++id) {
+        const int I = id % P.Nlx, J = id / P.Nlx;
+        LeafDesc& L = P.leaves[id];
+        L.seg_off = (int)P.leaf_segs.size();
+        const int nx_side = ceil_div(L.h, P.gy), ny_side = ceil_div(L.w, P.gx);
+        int cnt = 0;
+        auto add_side = [&](int s, int first, int count) {
+            if (first < 0) { L.side_off[s] = -1; return; }
+            L.side_off[s] = cnt;
+            for (int k = 0; k < count; ++k) P.leaf_segs.push_back(first + k);
+            cnt += count;
+        };
+        add_side(0, I > 0 ? xplus_first[id - 1] : -1, nx_side);
+        add_side(1, xplus_first[id], nx_side);
+        add_side(2, J > 0 ? yplus_first[id - P.Nlx] : -1, ny_side);
+        add_side(3, yplus_first[id], ny_side);
+        L.m = cnt;
+        P.max_m_leaf = std::max(P.max_m_leaf, cnt);
+    }
+    // tree by recursive bisection of the leaf box
+    P.nodes.resize(P.nleaf);
+    for (int id = 0; id < P.nleaf; ++id) {
+        Plan::Node& nd = P.nodes[id];
+        const int I = id % P.Nlx, J = id / P.Nlx;
+        nd.box[0] = I; nd.box[1] = I + 1; nd.box[2] = J; nd.box[3] = J + 1;
+        nd.leaf = id;
+        const LeafDesc& L = P.leaves[id];
+        nd.segs.assign(P.leaf_segs.begin() + L.seg_off, P.leaf_segs.begin() + L.seg_off + L.m);
+    }
+    struct Rec {
+        Plan& P;
+        int build(int I0, int I1, int J0, int J1) {
+            const int nxl = I1 - I0, nyl = J1 - J0;
+            if (nxl == 1 && nyl == 1) return I0 + P.Nlx * J0;
+            int c1, c2;
+            if (nxl >= nyl) {
+                const int mid = I0 + (nxl + 1) / 2;
+                c1 = build(I0, mid, J0, J1);
+                c2 = build(mid, I1, J0, J1);
+            } else {
+                const int mid = J0 + (nyl + 1) / 2;
+                c1 = build(I0, I1, J0, mid);
+                c2 = build(I0, I1, mid, J1);
+            }
+            Plan::Node nd;
+            nd.box[0] = I0; nd.box[1] = I1; nd.box[2] = J0; nd.box[3] = J1;
+            nd.c1 = c1; nd.c2 = c2;
+            nd.height = 1 + std::max(P.nodes[c1].height, P.nodes[c2].height);
+            const std::vector<int>& s1 = P.nodes[c1].segs;
+            const std::vector<int>& s2 = P.nodes[c2].segs;
+            std::unordered_map<int, int> pos2;
+            for (int k = 0; k < (int)s2.size(); ++k) pos2[s2[k]] = k;
+            std::vector<int> gpos1, gpos2, opos1, opos2;
+            std::vector<char> in_gamma2(s2.size(), 0);
+            for (int k = 0; k < (int)s1.size(); ++k) {
+                auto it = pos2.find(s1[k]);
+                if (it != pos2.end()) {
+                    nd.gamma.push_back(s1[k]);
+                    gpos1.push_back(k);
+                    gpos2.push_back(it->second);
+                    in_gamma2[it->second] = 1;
+                } else {
+                    opos1.push_back(k);
+                    nd.segs.push_back(s1[k]);
+                }
+            }
+            nd.o1 = (int)opos1.size();
+            for (int k = 0; k < (int)s2.size(); ++k)
+                if (!in_gamma2[k]) { opos2.push_back(k); nd.segs.push_back(s2[k]); }
+            nd.map = gpos1;
+            nd.map.insert(nd.map.end(), gpos2.begin(), gpos2.end());
+            nd.map.insert(nd.map.end(), opos1.begin(), opos1.end());
+            nd.map.insert(nd.map.end(), opos2.begin(), opos2.end());
+            const int id = (int)P.nodes.size();
+            P.nodes.push_back(nd);
+            P.nodes[c1].parent = id;
+            P.nodes[c2].parent = id;
+            return id;
+        }
+    } rec{P};
+    P.root = rec.build(0, P.Nlx, 0, P.Nly);
+    P.height = P.nodes[P.root].height;
+    // storage offsets per node
+    const int nnode = (int)P.nodes.size();
+    P.node_R_off.resize(nnode);
+    P.node_r_off.resize(nnode);
+    for (int v = 0; v < nnode; ++v) {
+        const long long m = (long long)P.nodes[v].segs.size();
+        P.node_R_off[v] = P.nR;
+        P.nR += m * m;
+        P.node_r_off[v] = P.nr;
+        P.nr += m;
+    }
+    for (int id = 0; id < P.nleaf; ++id) {
+        LeafDesc& L = P.leaves[id];
+        const long long n = (long long)L.w * L.h;
+        L.L_off = P.nL;
+        P.nL += n * (kLeafThreads + 1);
+        L.Z_off = P.nZ;
+        P.nZ += n * L.m;
+        L.zb_off = P.nzb;
+        P.nzb += n;
+        L.R_off = P.node_R_off[id];
+        L.r_off = P.node_r_off[id];
+        L.fs_off = 0;
+        // flop model of the leaf kernel: LDL^T band steps, forward solve of
+        // the m Robin columns, SYRK of the lower triangle (FMA = 2 flops)
+        long long f = 0;
+        for (long long k = 0; k < n; ++k) {
+            const long long wk = std::min<long long>(L.w, n - 1 - k);
+            f += wk + wk * (wk + 1);                  // multipliers + trailing update
+            f += 2 * wk * L.m;                        // Z update
+            f += L.m + (long long)L.m * (L.m + 1);    // scaling + R update
+        }
+        P.leaf_flops += f;
+        // solve phase per leaf: forward sweep, Z^T y, Z lambda, backward sweep
+        P.solve_flops += 2 * n * L.w * 2 + 2 * n * L.m * 2 + 2 * n;
+    }
+    // merges grouped by height
+    std::vector<std::vector<int>> by_h(P.height + 1);
+    for (int v = P.nleaf; v < nnode; ++v) by_h[P.nodes[v].height].push_back(v);
+    P.level_first.assign(P.height, 0);
+    P.level_count.assign(P.height, 0);
+    P.level_max_g2.assign(P.height, 0);
+    for (int h = 1; h <= P.height; ++h) {
+        P.level_first[h - 1] = (int)P.merges.size();
+        P.level_count[h - 1] = (int)by_h[h].size();
+        for (int v : by_h[h]) {
+            Plan::Node& nd = P.nodes[v];
+            MergeDesc D;
+            std::memset(&D, 0, sizeof(D));
+            D.node = v;
+            D.c1 = nd.c1;
+            D.c2 = nd.c2;
+            D.g = (int)nd.gamma.size();
+            D.m = (int)nd.segs.size();
+            D.o1 = nd.o1;
+            D.m1 = (int)P.nodes[nd.c1].segs.size();
+            D.m2 = (int)P.nodes[nd.c2].segs.size();
+            D.map_off = (int)P.node_map.size();
+            P.node_map.insert(P.node_map.end(), nd.map.begin(), nd.map.end());
+            D.gamma_off = (int)P.gamma_segs.size();
+            P.gamma_segs.insert(P.gamma_segs.end(), nd.gamma.begin(), nd.gamma.end());
+            D.pinned = (v == P.root && P.pure_neumann) ? 1 : 0;
+            D.R_off = P.node_R_off[v];
+            D.R1_off = P.node_R_off[nd.c1];
+            D.R2_off = P.node_R_off[nd.c2];
+            D.r_off = P.node_r_off[v];
+            D.r1_off = P.node_r_off[nd.c1];
+            D.r2_off = P.node_r_off[nd.c2];
+            const long long g2 = 2LL * D.g, m = D.m;
+            D.LU_off = P.nLU;  P.nLU += g2 * g2;
+            D.piv_off = P.npiv; P.npiv += g2;
+            D.X_off = P.nX;    P.nX += g2 * m;
+            D.xb_off = P.nxb;  P.nxb += g2;
+            P.merges.push_back(D);
+            P.level_max_g2[h - 1] = std::max(P.level_max_g2[h - 1], (int)g2);
+            P.max_g2 = std::max(P.max_g2, (int)g2);
+            // flop model: LU (2/3 N^3), X solve (2 N^2 m), R update (2 g m^2)
+            const double N = (double)g2;
+            P.merge_flops += (long long)(2.0 / 3.0 * N * N * N) + 2LL * g2 * g2 * m + 2LL * D.g * m * m;
+            P.solve_flops += 2LL * g2 * g2 + 2LL * D.g * m + 2LL * g2 * m;
+        }
+    }
+    return MRCM_OK;
+}
+
+}  // namespace
+
+struct mrcm_ctx {
+    Plan P;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    bool built = false;
+    bool solved = false;
+    DevView v{};
+    std::vector<void*> allocs;
+    size_t bytes = 0;
+    double* K = nullptr;
+    int launches_build = 0, launches_solve = 0;
+    bool timing = false;
+    cudaEvent_t ev[2 * MRCM_PHASE_COUNT] = {};
+    bool ev_used[MRCM_PHASE_COUNT] = {};
+};
+
+namespace {
+
+int cuda_err(cudaError_t e) {
+    if (e == cudaSuccess) return MRCM_OK;
+    if (e == cudaErrorMemoryAllocation) return MRCM_ERR_OOM;
+    return MRCM_ERR_CUDA;
+}
+
+template <class T>
+int dev_alloc(mrcm_ctx* c, T** p, long long count) {
+    *p = nullptr;
+    if (count <= 0) count = 1;
+    void* ptr = nullptr;
+    cudaError_t e = cudaMalloc(&ptr, sizeof(T) * (size_t)count);
+    if (e != cudaSuccess) return cuda_err(e);
+    c->allocs.push_back(ptr);
+    c->bytes += sizeof(T) * (size_t)count;
+    *p = static_cast<T*>(ptr);
+    return MRCM_OK;
+}
+
+template <class T>
+int upload(mrcm_ctx* c, const T** out, const std::vector<T>& h) {
+    T* d = nullptr;
+    int rc = dev_alloc(c, &d, (long long)h.size());
+    if (rc) return rc;
+    if (!h.empty()) {
+        cudaError_t e = cudaMemcpy(d, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_err(e);
+    }
+    *out = d;
+    return MRCM_OK;
+}
+
+int read_status(mrcm_ctx* c) {
+    int st = 0;
+    cudaError_t e = cudaMemcpyAsync(&st, c->v.status, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_err(e);
+    if (st & kStatusBadK) return MRCM_ERR_BAD_K;
+    if (st & kStatusSingular) return MRCM_ERR_SINGULAR;
+    if (st & kStatusTimeout) return MRCM_ERR_TIMEOUT;
+    if (st & kStatusBadIndex) return MRCM_ERR_INVALID_ARG;
+    return MRCM_OK;
+}
+
+struct PhaseScope {
+    mrcm_ctx* c;
+    int phase;
+    PhaseScope(mrcm_ctx* c_, int p) : c(c_), phase(p) {
+        if (c->timing) {
+            cudaEventRecord(c->ev[2 * p], c->stream);
+            c->ev_used[p] = true;
+        }
+    }
+    ~PhaseScope() {
+        if (c->timing) cudaEventRecord(c->ev[2 * phase + 1], c->stream);
+    }
+};
+
+}  // namespace
+
+#define TRY(x) do { int rc_ = (x); if (rc_ != MRCM_OK) return rc_; } while (0)
+#define TRYC(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) return cuda_err(e_); } while (0)
+
+extern "C" {
+
+const char* mrcm_error_string(int code) {
+    switch (code) {
+        case MRCM_OK: return "ok";
+        case MRCM_ERR_INVALID_ARG: return "invalid argument";
+        case MRCM_ERR_SHAPE: return "segment length does not divide the leaf side, or leaf too large";
+        case MRCM_ERR_BAD_K: return "permeability not positive and finite";
+        case MRCM_ERR_NOT_BUILT: return "basis not built (call mrcm_build_basis first)";
+        case MRCM_ERR_SINGULAR: return "singular local or interface system";
+        case MRCM_ERR_CUDA: return "CUDA runtime error";
+        case MRCM_ERR_OOM: return "device out of memory";
+        case MRCM_ERR_TIMEOUT: return "bounded device wait timed out";
+        case MRCM_ERR_UNSUPPORTED: return "unsupported configuration";
+        default: return "unknown error";
+    }
+}
+
+static int validate(const mrcm_grid* g, const int sub_cells[3], const int seg_cells[3],
+                    const int bc_type[6]) {
+    if (!g || !sub_cells || !seg_cells || !bc_type) return MRCM_ERR_INVALID_ARG;
+    if (g->dim == 3) return MRCM_ERR_UNSUPPORTED;
+    if (g->dim != 2) return MRCM_ERR_INVALID_ARG;
+    if (g->n[0] < 1 || g->n[1] < 1 || !(g->L[0] > 0) || !(g->L[1] > 0)) return MRCM_ERR_INVALID_ARG;
+    if ((long long)g->n[0] * g->n[1] > (1LL << 31)) return MRCM_ERR_INVALID_ARG;
+    for (int s = 0; s < 4; ++s)
+        if (bc_type[s] != MRCM_BC_NEUMANN && bc_type[s] != MRCM_BC_DIRICHLET) return MRCM_ERR_INVALID_ARG;
+    for (int d = 0; d < 2; ++d) {
+        if (sub_cells[d] < 1 || seg_cells[d] < 1) return MRCM_ERR_INVALID_ARG;
+        if (sub_cells[d] > kMaxLeafSide) return MRCM_ERR_SHAPE;
+        if (seg_cells[d] > sub_cells[d] || sub_cells[d] % seg_cells[d] != 0) return MRCM_ERR_SHAPE;
+    }
+    return MRCM_OK;
+}
+
+static void fill_plan_inputs(Plan& P, const mrcm_grid* g, const int sub[3], const int seg[3],
+                             double alpha, const int bc_type[6]) {
+    P.nx = g->n[0];
+    P.ny = g->n[1];
+    P.hx = g->L[0] / g->n[0];
+    P.hy = g->L[1] / g->n[1];
+    P.alpha = alpha;
+    P.sx = sub[0]; P.sy = sub[1];
+    P.gx = seg[0]; P.gy = seg[1];
+    for (int s = 0; s < 4; ++s) P.bc[s] = bc_type[s];
+    P.pure_neumann = !(P.bc[0] || P.bc[1] || P.bc[2] || P.bc[3]);
+}
+
+static int plan_value(const Plan& P, int what, long long* value) {
+    switch (what) {
+        case MRCM_Q_LEAVES: *value = P.nleaf; break;
+        case MRCM_Q_SEGMENTS: *value = P.nseg; break;
+        case MRCM_Q_LEVELS: *value = P.height; break;
+        case MRCM_Q_NODES: *value = (long long)P.nodes.size(); break;
+        case MRCM_Q_MAX_GAMMA: *value = P.max_g2; break;
+        case MRCM_Q_BUILD_FLOPS: *value = P.leaf_flops + P.merge_flops; break;
+        case MRCM_Q_SOLVE_FLOPS: *value = P.solve_flops; break;
+        case MRCM_Q_LEAF_FLOPS: *value = P.leaf_flops; break;
+        default: return MRCM_ERR_INVALID_ARG;
+    }
+    return MRCM_OK;
+}
+
+int mrcm_plan_query(const mrcm_grid* g, const int sub_cells[3], const int seg_cells[3],
+                    const int bc_type[6], int what, long long* value) {
+    if (!value) return MRCM_ERR_INVALID_ARG;
+    TRY(validate(g, sub_cells, seg_cells, bc_type));
+    if (what == MRCM_Q_WORKSPACE_BYTES) { *value = 0; return MRCM_OK; }
+    Plan P;
+    fill_plan_inputs(P, g, sub_cells, seg_cells, 1.0, bc_type);
+    TRY(make_plan(P));
+    return plan_value(P, what, value);
+}
+
+static int setup_impl(mrcm_ctx* c, const mrcm_grid* g, const double* K_dev, const int sub[3],
+                      const int seg[3], double alpha, const int bc_type[6], void* stream) {
+    Plan& P = c->P;
+    fill_plan_inputs(P, g, sub, seg, alpha, bc_type);
+    c->stream = static_cast<cudaStream_t>(stream);
+    TRYC(cudaGetDevice(&c->device));
+    TRY(make_plan(P));
+    if (P.pure_neumann && P.nleaf == 1) return MRCM_ERR_UNSUPPORTED;
+    DevView& v = c->v;
+    v.nx = P.nx; v.ny = P.ny; v.hx = P.hx; v.hy = P.hy; v.alpha = P.alpha;
+    for (int s = 0; s < 4; ++s) v.bc[s] = P.bc[s];
+    v.nleaf = P.nleaf; v.nseg = P.nseg;
+    v.sx = P.sx; v.sy = P.sy; v.gx = P.gx; v.gy = P.gy;
+    const long long ncell = (long long)P.nx * P.ny;
+    const long long nxf = (long long)(P.nx + 1) * P.ny, nyf = (long long)P.nx * (P.ny + 1);
+    TRY(dev_alloc(c, &c->K, ncell));
+    v.K = c->K;
+    TRY(dev_alloc(c, &v.seg_beta, P.nseg));
+    TRY(dev_alloc(c, &v.seg_D, P.nseg));
+    TRY(dev_alloc(c, &v.cxL, nxf));
+    TRY(dev_alloc(c, &v.cxU, nxf));
+    TRY(dev_alloc(c, &v.cyL, nyf));
+    TRY(dev_alloc(c, &v.cyU, nyf));
+    TRY(upload(c, &v.seg_axis, P.seg_axis));
+    TRY(upload(c, &v.seg_line, P.seg_line));
+    TRY(upload(c, &v.seg_lo, P.seg_lo));
+    TRY(upload(c, &v.seg_len, P.seg_len));
+    TRY(upload(c, &v.seg_a, P.seg_a));
+    TRY(upload(c, &v.seg_b, P.seg_b));
+    TRY(upload(c, &v.seg_face_off, P.seg_face_off));
+    TRY(upload(c, &v.leaves, P.leaves));
+    TRY(upload(c, &v.leaf_segs, P.leaf_segs));
+    TRY(upload(c, &v.merges, P.merges));
+    TRY(upload(c, &v.node_map, P.node_map));
+    TRY(upload(c, &v.gamma_segs, P.gamma_segs));
+    TRY(dev_alloc(c, &v.leafL, P.nL));
+    TRY(dev_alloc(c, &v.leafZ, P.nZ));
+    TRY(dev_alloc(c, &v.leafzb, P.nzb));
+    TRY(dev_alloc(c, &v.R, P.nR));
+    TRY(dev_alloc(c, &v.rbar, P.nr));
+    TRY(dev_alloc(c, &v.lam, P.nr));
+    TRY(dev_alloc(c, &v.LU, P.nLU));
+    TRY(dev_alloc(c, &v.piv, P.npiv));
+    TRY(dev_alloc(c, &v.X, P.nX));
+    TRY(dev_alloc(c, &v.xbar, P.nxb));
+    TRY(dev_alloc(c, &v.skel, 2 * P.nskel_faces));
+    TRY(dev_alloc(c, &v.red, 1024));
+    TRY(dev_alloc(c, &v.status, 4));
+    TRYC(cudaMemcpyAsync(c->K, K_dev, sizeof(double) * ncell, cudaMemcpyDefault, c->stream));
+    // the root's lambda has no entries; lambda of every other node is written
+    // top-down before it is read
+    TRYC(cudaMemsetAsync(v.status, 0, sizeof(int), c->stream));
+    TRYC(cudaStreamSynchronize(c->stream));
+    return MRCM_OK;
+}
+
+int mrcm_setup(mrcm_ctx** out, const mrcm_grid* g, const double* K_dev, const int sub_cells[3],
+               const int seg_cells[3], double alpha, const int bc_type[6], int precision,
+               void* cuda_stream) {
+    if (!out) return MRCM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!K_dev) return MRCM_ERR_INVALID_ARG;
+    TRY(validate(g, sub_cells, seg_cells, bc_type));
+    if (precision != MRCM_FP64) return MRCM_ERR_UNSUPPORTED;
+    if (!(alpha > 0) || !std::isfinite(alpha)) return MRCM_ERR_INVALID_ARG;
+    mrcm_ctx* c = new (std::nothrow) mrcm_ctx();
+    if (!c) return MRCM_ERR_OOM;
+    int rc = setup_impl(c, g, K_dev, sub_cells, seg_cells, alpha, bc_type, cuda_stream);
+    if (rc != MRCM_OK) {
+        mrcm_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return MRCM_OK;
+}
+
+int mrcm_set_permeability(mrcm_ctx* c, const double* K_dev) {
+    if (!c || !K_dev) return MRCM_ERR_INVALID_ARG;
+    TRYC(cudaMemcpyAsync(c->K, K_dev, sizeof(double) * (size_t)c->P.nx * c->P.ny, cudaMemcpyDefault,
+                         c->stream));
+    c->built = false;
+    c->solved = false;
+    TRYC(cudaStreamSynchronize(c->stream));
+    return MRCM_OK;
+}
+
+int mrcm_build_basis(mrcm_ctx* c) {
+    if (!c) return MRCM_ERR_INVALID_ARG;
+    const Plan& P = c->P;
+    const DevView& v = c->v;
+    cudaStream_t s = c->stream;
+    c->built = false;
+    c->solved = false;
+    int launches = 0;
+    for (int p = 0; p < MRCM_PHASE_COUNT; ++p) c->ev_used[p] = false;
+    TRYC(cudaMemsetAsync(v.status, 0, sizeof(int), s));
+    {
+        PhaseScope ps(c, MRCM_PHASE_COEF);
+        TRYC(launch_check_K(v, s)); ++launches;
+        TRYC(launch_seg_beta(v, s)); launches += P.nseg > 0;
+        TRYC(launch_face_coef(v, s)); ++launches;
+    }
+    {
+        PhaseScope ps(c, MRCM_PHASE_LEAF_BUILD);
+        TRYC(launch_leaf_build(v, P.max_m_leaf, s)); ++launches;
+    }
+    {
+        PhaseScope ps(c, MRCM_PHASE_MERGE_BUILD);
+        for (int h = 1; h <= P.height; ++h) {
+            TRYC(launch_merge_build(v, P.level_first[h - 1], P.level_count[h - 1], P.level_max_g2[h - 1],
+                                    0, s));
+            ++launches;
+        }
+    }
+    c->launches_build = launches;
+    TRY(read_status(c));
+    c->built = true;
+    return MRCM_OK;
+}
+
+int mrcm_solve(mrcm_ctx* c, const double* q_dev, const double* bc_val_dev, double* p_dev, double* Fx_dev,
+               double* Fy_dev, double* Fz_dev, double* iface_dev) {
+    if (!c) return MRCM_ERR_INVALID_ARG;
+    if (!c->built) return MRCM_ERR_NOT_BUILT;
+    if (!q_dev || !bc_val_dev || !p_dev || !Fx_dev || !Fy_dev || Fz_dev) return MRCM_ERR_INVALID_ARG;
+    const Plan& P = c->P;
+    const DevView& v = c->v;
+    cudaStream_t s = c->stream;
+    int launches = 0;
+    for (int p = MRCM_PHASE_LEAF_PART; p < MRCM_PHASE_COUNT; ++p) c->ev_used[p] = false;
+    TRYC(cudaMemsetAsync(v.status, 0, sizeof(int), s));
+    {
+        PhaseScope ps(c, MRCM_PHASE_LEAF_PART);
+        TRYC(launch_leaf_particular(v, q_dev, bc_val_dev, P.max_m_leaf, s)); ++launches;
+    }
+    {
+        PhaseScope ps(c, MRCM_PHASE_TREE_SOLVE);
+        for (int h = 1; h <= P.height; ++h) {
+            TRYC(launch_merge_up(v, P.level_first[h - 1], P.level_count[h - 1], P.level_max_g2[h - 1], s));
+            ++launches;
+        }
+        for (int h = P.height; h >= 1; --h) {
+            TRYC(launch_merge_down(v, P.level_first[h - 1], P.level_count[h - 1], P.level_max_g2[h - 1], s));
+            ++launches;
+        }
+    }
+    {
+        PhaseScope ps(c, MRCM_PHASE_LEAF_FINAL);
+        TRYC(launch_leaf_final(v, q_dev, bc_val_dev, p_dev, Fx_dev, Fy_dev, P.max_m_leaf, s)); ++launches;
+    }
+    {
+        PhaseScope ps(c, MRCM_PHASE_FINISH);
+        if (P.nseg > 0 || iface_dev) {
+            TRYC(launch_skeleton_fluxes(v, Fx_dev, Fy_dev, iface_dev, s));
+            ++launches;
+        }
+        if (P.pure_neumann) {
+            TRYC(launch_mean_shift(v, p_dev, s));
+            launches += 2;
+        }
+    }
+    c->launches_solve = launches;
+    TRY(read_status(c));
+    c->solved = true;
+    return MRCM_OK;
+}
+
+int mrcm_query(const mrcm_ctx* c, int what, long long* value) {
+    if (!c || !value) return MRCM_ERR_INVALID_ARG;
+    switch (what) {
+        case MRCM_Q_WORKSPACE_BYTES: *value = (long long)c->bytes; return MRCM_OK;
+        case MRCM_Q_KERNEL_LAUNCHES_BUILD: *value = c->launches_build; return MRCM_OK;
+        case MRCM_Q_KERNEL_LAUNCHES_SOLVE: *value = c->launches_solve; return MRCM_OK;
+        default: return plan_value(c->P, what, value);
+    }
+}
+
+int mrcm_node_info(const mrcm_ctx* c, int node, int info[11]) {
+    if (!c || !info || node < 0 || node >= (int)c->P.nodes.size()) return MRCM_ERR_INVALID_ARG;
+    const Plan::Node& nd = c->P.nodes[node];
+    info[0] = nd.height;
+    info[1] = (int)nd.segs.size();
+    info[2] = (int)nd.gamma.size();
+    info[3] = nd.c1;
+    info[4] = nd.c2;
+    info[5] = nd.parent;
+    info[6] = nd.leaf;
+    for (int k = 0; k < 4; ++k) info[7 + k] = nd.box[k];
+    return MRCM_OK;
+}
+
+int mrcm_node_segments(const mrcm_ctx* c, int node, int* seg_ids) {
+    if (!c || !seg_ids || node < 0 || node >= (int)c->P.nodes.size()) return MRCM_ERR_INVALID_ARG;
+    const std::vector<int>& s = c->P.nodes[node].segs;
+    std::copy(s.begin(), s.end(), seg_ids);
+    return MRCM_OK;
+}
+
+int mrcm_segment_info(const mrcm_ctx* c, int seg, int info[6]) {
+    if (!c || !info || seg < 0 || seg >= c->P.nseg) return MRCM_ERR_INVALID_ARG;
+    const Plan& P = c->P;
+    info[0] = P.seg_axis[seg];
+    info[1] = P.seg_line[seg];
+    info[2] = P.seg_lo[seg];
+    info[3] = P.seg_len[seg];
+    info[4] = P.seg_a[seg];
+    info[5] = P.seg_b[seg];
+    return MRCM_OK;
+}
+
+int mrcm_node_operator(mrcm_ctx* c, int node, double* R_host, double* rbar_host) {
+    if (!c || !R_host || node < 0 || node >= (int)c->P.nodes.size()) return MRCM_ERR_INVALID_ARG;
+    if (!c->built) return MRCM_ERR_NOT_BUILT;
+    if (rbar_host && !c->solved) return MRCM_ERR_NOT_BUILT;
+    const long long m = (long long)c->P.nodes[node].segs.size();
+    if (m > 0) {
+        TRYC(cudaMemcpyAsync(R_host, c->v.R + c->P.node_R_off[node], sizeof(double) * m * m,
+                             cudaMemcpyDeviceToHost, c->stream));
+        if (rbar_host)
+            TRYC(cudaMemcpyAsync(rbar_host, c->v.rbar + c->P.node_r_off[node], sizeof(double) * m,
+                                 cudaMemcpyDeviceToHost, c->stream));
+    }
+    TRYC(cudaStreamSynchronize(c->stream));
+    return MRCM_OK;
+}
+
+int mrcm_enable_timing(mrcm_ctx* c, int on) {
+    if (!c) return MRCM_ERR_INVALID_ARG;
+    if (on && !c->ev[0]) {
+        for (int k = 0; k < 2 * MRCM_PHASE_COUNT; ++k) TRYC(cudaEventCreate(&c->ev[k]));
+    }
+    c->timing = on != 0;
+    return MRCM_OK;
+}
+
+int mrcm_phase_times(mrcm_ctx* c, double* ms) {
+    if (!c || !ms) return MRCM_ERR_INVALID_ARG;
+    TRYC(cudaStreamSynchronize(c->stream));
+    for (int p = 0; p < MRCM_PHASE_COUNT; ++p) {
+        ms[p] = 0.0;
+        if (c->ev[0] && c->ev_used[p]) {
+            float t = 0.f;
+            TRYC(cudaEventElapsedTime(&t, c->ev[2 * p], c->ev[2 * p + 1]));
+            ms[p] = t;
+        }
+    }
+    return MRCM_OK;
+}
+
+void mrcm_destroy(mrcm_ctx* c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    for (int k = 0; k < 2 * MRCM_PHASE_COUNT; ++k)
+        if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+    for (void* p : c->allocs) cudaFree(p);
+    delete c;
+}
+
+}  // extern "C"

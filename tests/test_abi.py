@@ -1,0 +1,81 @@
+"""The C-ABI library loads and exports what include/mrcm.h declares; host-only
+calls (error strings, planning) work without a GPU."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import inputs
+from oracle.geometry import Decomposition
+from oracle.recursive import build_tree
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "mrcm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mrcm_[a-z_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(mrcm_lib):
+    import ctypes
+    lib = ctypes.CDLL(mrcm_lib.LIB_PATH)
+    declared = _declared()
+    assert len(declared) >= 12
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert sorted(mrcm_lib.EXPORTS) == declared
+
+
+def test_error_strings(mrcm_lib):
+    for code in range(-9, 1):
+        assert mrcm_lib.mrcm_error_string(code)
+    assert mrcm_lib.mrcm_error_string(-5).startswith("singular")
+
+
+def _tree_height(node):
+    if not node.children:
+        return 0
+    return 1 + max(_tree_height(c) for c in node.children)
+
+
+@pytest.mark.parametrize("n,sub,seg,bc", [((64, 64), (16, 16), (4, 4), (1, 1, 0, 0)),
+                                          ((40, 36), (16, 16), (4, 4), (0, 0, 0, 0)),
+                                          ((50, 30), (8, 16), (2, 4), (1, 1, 0, 0)),
+                                          ((48, 48), (16, 16), (1, 1), (1, 1, 0, 0)),
+                                          ((1024, 1024), (16, 16), (4, 4), (0, 0, 0, 0))])
+def test_plan_matches_oracle_decomposition(mrcm_lib, n, sub, seg, bc):
+    q = lambda k: mrcm_lib.mrcm_plan_query(n, (1.0, 1.0), sub, seg, bc, k)
+    prob = inputs.darcy_problem(n[0], n[1], sigma2=0.0, sub=sub, seg=seg)
+    dec = Decomposition(prob) if n[0] * n[1] <= 4096 else None
+    nl = -(-n[0] // sub[0]) * -(-n[1] // sub[1])
+    assert q("LEAVES") == nl
+    assert q("NODES") == 2 * nl - 1
+    if dec is not None:
+        assert q("SEGMENTS") == len(dec.segments)
+        assert q("LEVELS") == _tree_height(build_tree(dec))
+    assert q("BUILD_FLOPS") > q("LEAF_FLOPS") > 0
+
+
+def test_plan_counts_for_the_paper_layout(mrcm_lib):
+    # 2D analogue of Table ntmmbfs: interior segments per leaf side = H/Hbar
+    for (a, b) in [(4, 8), (8, 8), (16, 32)]:
+        for r in (1, 4):
+            segs = mrcm_lib.mrcm_plan_query((16 * a, 16 * b), (1, 1), (16, 16), (16 // r, 16 // r),
+                                            (1, 1, 0, 0), "SEGMENTS")
+            assert segs == r * ((a - 1) * b + a * (b - 1))
+
+
+def test_setup_rejects_bad_shapes_without_a_device(mrcm_lib):
+    from paper_2009_07965_gb300.binding import MrcmError
+    with pytest.raises(MrcmError) as e:
+        mrcm_lib.mrcm_plan_query((64, 64), (1, 1), (16, 16), (3, 4), (1, 1, 0, 0), "LEAVES")
+    assert e.value.code == -2
+    with pytest.raises(MrcmError) as e:
+        mrcm_lib.mrcm_plan_query((64, 64), (1, 1), (32, 32), (4, 4), (1, 1, 0, 0), "LEAVES")
+    assert e.value.code == -2
+    with pytest.raises(MrcmError) as e:
+        mrcm_lib.mrcm_plan_query((64, 64), (1, 1), (16, 16), (4, 4), (1, 2, 0, 0), "LEAVES")
+    assert e.value.code == -1

@@ -1,0 +1,179 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerance: relative L2 <= 1e-10 in pressure and in each flux array (the
+FP64 target), on problems that span several leaves, ragged (truncated)
+leaves, both boundary-condition families, one-face segments (64 Robin
+responses per leaf) and per-node Robin-to-flux maps.
+"""
+import numpy as np
+import pytest
+
+import inputs
+from oracle.fine import solve_fine
+from oracle.geometry import Decomposition
+from oracle.local import LeafProblem
+from oracle.mrcm import solve_mrcm
+from oracle.recursive import RecursiveMRCM
+from conftest import gpu_solve, rel
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+KEYS = ("p", "Fx", "Fy", "Fa_x", "Fb_x", "Fa_y", "Fb_y")
+
+
+def _compare(g, o, keys=KEYS, tol=TOL):
+    errs = {k: rel(g[k], o[k]) for k in keys}
+    bad = {k: e for k, e in errs.items() if not e <= tol}
+    assert not bad, errs
+    return errs
+
+
+def test_square64_left_right(mrcm_lib):
+    prob = inputs.config_64()
+    _compare(gpu_solve(prob), solve_mrcm(prob))
+
+
+@pytest.mark.parametrize("bc", ["left_right", "quarter_five_spot"])
+def test_ragged_leaves(mrcm_lib, bc):
+    prob = inputs.darcy_problem(40, 36, sigma2=2.0, corr=0.15, seed=31, bc=bc)
+    _compare(gpu_solve(prob), solve_mrcm(prob))
+
+
+@pytest.mark.parametrize("bc", ["left_right", "quarter_five_spot"])
+def test_one_face_segments_equal_fine(mrcm_lib, bc):
+    # 64 Robin responses per 16x16 leaf; MRCM then equals the fine solution
+    prob = inputs.darcy_problem(48, 40, sigma2=2.0, corr=0.2, seed=3, bc=bc, seg=(1, 1), alpha=5.0)
+    g = gpu_solve(prob)
+    _compare(g, solve_mrcm(prob))
+    f = solve_fine(prob)
+    for k in ("p", "Fx", "Fy"):
+        assert rel(g[k], f[k]) < 1e-10
+
+
+def test_rectangular_leaves_and_segments(mrcm_lib):
+    prob = inputs.darcy_problem(50, 30, sigma2=1.5, corr=0.1, seed=5, bc="left_right",
+                                sub=(8, 16), seg=(2, 4), alpha=0.3, Lx=2.0, Ly=0.7)
+    _compare(gpu_solve(prob), solve_mrcm(prob))
+
+
+@pytest.mark.parametrize("alpha", [1e-3, 1e3])
+def test_alpha_range(mrcm_lib, alpha):
+    prob = inputs.darcy_problem(64, 48, sigma2=1.0, corr=0.1, seed=7, bc="quarter_five_spot",
+                                alpha=alpha)
+    _compare(gpu_solve(prob), solve_mrcm(prob), tol=1e-9 if alpha > 1 else TOL)
+
+
+def test_tiny_leaves(mrcm_lib):
+    prob = inputs.darcy_problem(12, 10, sigma2=1.0, corr=0.3, seed=2, bc="left_right",
+                                sub=(1, 2), seg=(1, 1), alpha=2.0)
+    _compare(gpu_solve(prob), solve_mrcm(prob))
+
+
+def _oracle_seg_key(dec, t):
+    s = dec.segments[t]
+    return (s["axis"], s["line"], s["lo"])
+
+
+def test_node_maps_match_recursive_oracle(mrcm_lib):
+    prob = inputs.darcy_problem(64, 48, sigma2=2.0, corr=0.1, seed=17, bc="left_right")
+    g = gpu_solve(prob, want_iface=False)
+    ctx = g["solver"].ctx
+    rm = RecursiveMRCM(prob)
+    rm.solve()
+    dec = rm.dec
+    by_box = {}
+    stack = [rm.root]
+    while stack:
+        nd = stack.pop()
+        stack += nd.children
+        by_box[tuple(nd.box)] = nd
+    nnodes = mrcm_lib.mrcm_query(ctx, "NODES")
+    assert nnodes == len(by_box)
+    checked = 0
+    for v in range(nnodes):
+        info = mrcm_lib.mrcm_node_info(ctx, v)
+        nd = by_box[(info["I0"], info["I1"], info["J0"], info["J1"])]
+        if info["parent"] < 0:
+            continue
+        R_gpu, rbar_gpu = mrcm_lib.mrcm_node_operator(ctx, v, with_rbar=True)
+        keys = []
+        for t in mrcm_lib.mrcm_node_segments(ctx, v):
+            si = mrcm_lib.mrcm_segment_info(ctx, t)
+            keys.append((si["axis"], si["line"], si["lo"]))
+        okey = {_oracle_seg_key(dec, t): k for k, t in enumerate(nd.segs)}
+        perm = [okey[k] for k in keys]
+        R_o = nd.R[np.ix_(perm, perm)]
+        assert rel(R_gpu, R_o) < 1e-11, (v, rel(R_gpu, R_o))
+        assert rel(rbar_gpu, nd.rbar[perm]) < 1e-10
+        checked += 1
+    assert checked == nnodes - 1
+
+
+def test_leaf_maps_match_oracle(mrcm_lib):
+    prob = inputs.config_64()
+    g = gpu_solve(prob, want_iface=False)
+    ctx = g["solver"].ctx
+    dec = Decomposition(prob)
+    for leaf in range(len(dec.leaves)):
+        lp = LeafProblem(dec, leaf)
+        R_o, _ = lp.robin_to_flux()
+        R_g = mrcm_lib.mrcm_node_operator(ctx, leaf)
+        keys = []
+        for t in mrcm_lib.mrcm_node_segments(ctx, leaf):
+            si = mrcm_lib.mrcm_segment_info(ctx, t)
+            keys.append((si["axis"], si["line"], si["lo"]))
+        okey = {_oracle_seg_key(dec, t): k for k, t in enumerate(lp.segs)}
+        perm = [okey[k] for k in keys]
+        assert rel(R_g, R_o[np.ix_(perm, perm)]) < 1e-12
+        # symmetric and annihilating constants on Dirichlet-free leaves
+        assert np.abs(R_g - R_g.T).max() < 1e-12 * np.abs(R_g).max()
+
+
+def test_repeat_solves_bitwise_identical(mrcm_lib):
+    import torch
+    prob = inputs.darcy_problem(64, 64, sigma2=2.0, corr=0.1, seed=9, bc="quarter_five_spot")
+    g = gpu_solve(prob, want_iface=False)
+    s = g["solver"]
+    q = torch.from_numpy(prob.q).cuda()
+    bc = torch.from_numpy(prob.bc_val).cuda()
+    s.build_basis()
+    p2, fx2, fy2 = [x.cpu().numpy() for x in s.solve(q, bc)]
+    assert np.array_equal(p2, g["p"]) and np.array_equal(fx2, g["Fx"]) and np.array_equal(fy2, g["Fy"])
+
+
+def test_errors_are_reported(mrcm_lib):
+    import torch
+    from paper_2009_07965_gb300 import Solver, MrcmError
+    K = torch.ones(32, 32, dtype=torch.float64, device="cuda")
+    s = Solver(K)
+    q = torch.zeros(32, 32, dtype=torch.float64, device="cuda")
+    bc = torch.zeros(2 * 64, dtype=torch.float64, device="cuda")
+    with pytest.raises(MrcmError) as e:
+        s.solve(q, bc)
+    assert e.value.code == -4            # NOT_BUILT
+    K[3, 5] = -1.0
+    s.set_permeability(K)
+    with pytest.raises(MrcmError) as e:
+        s.build_basis()
+    assert e.value.code == -3            # BAD_K
+    K[3, 5] = float("nan")
+    s.set_permeability(K)
+    with pytest.raises(MrcmError) as e:
+        s.build_basis()
+    assert e.value.code == -3
+    K[3, 5] = 1.0
+    s.set_permeability(K)
+    s.build_basis()
+    s.solve(q, bc)                       # the context stays usable
+    with pytest.raises(MrcmError) as e:
+        Solver(K, sub=(16, 16), seg=(3, 4))
+    assert e.value.code == -2            # SHAPE
+
+
+@pytest.mark.slow
+def test_square1024_quarter_five_spot_full_size(mrcm_lib):
+    # the benchmark workload (1024^2, sigma^2 = 4, 4096 leaves, 12 levels)
+    prob = inputs.config_1024()
+    g = gpu_solve(prob, want_iface=True)
+    errs = _compare(g, solve_mrcm(prob))
+    print("1024^2 rel errors", errs)
