@@ -225,6 +225,50 @@ int mrcm_node_segments(const mrcm_ctx* ctx, int node, int* seg_ids);
 int mrcm_segment_info(const mrcm_ctx* ctx, int seg, int info[6]);
 int mrcm_node_operator(mrcm_ctx* ctx, int node, double* R_host, double* rbar_host);
 
+/*
+ * mrcm_merge_pair_noalloc -- merge two Robin-to-flux maps along their common
+ * interface without allocating device memory.
+ *
+ * The paper has no counterpart to this call; it exists for callers that
+ * cannot call cudaMalloc where they need a merge: code running inside
+ * another framework's execution step (an inference-engine plugin's enqueue,
+ * a solver callback) whose framework owns all device memory, and
+ * latency-bound loops that cannot absorb the device synchronisation an
+ * allocation implies.  It computes what one merge of mrcm_build_basis
+ * computes for one node, from caller-owned buffers only:
+ *     M = [[R1_gg + D, -D], [-D, R2_gg + D]]  (2g x 2g, partial-pivot LU),
+ *     X = -M^-1 blockdiag(R1_go, R2_go),
+ *     R = blockdiag(R1_oo, R2_oo) + blockdiag(R1_og, R2_og) X.
+ *
+ *   R1_dev, R2_dev  children's maps, m1 x m1 and m2 x m2, row-major (device)
+ *   map_dev   device ints, 2g + m values: gpos1[g], gpos2[g] (positions of
+ *             the gamma segments in child 1 / child 2, same gamma order),
+ *             opos1[m1-g], opos2[m2-g] (the children's other positions, in
+ *             the order the merged map uses); out-of-range entries make the
+ *             call return MRCM_ERR_INVALID_ARG without touching R or X
+ *   g         gamma segments, 1 <= 2g <= MRCM_NOALLOC_MAX_G2
+ *   D_dev     g values |t| / (2 beta_t) of the gamma segments (device)
+ *   R_dev     out: merged map, m x m with m = m1 + m2 - 2g (device)
+ *   X_dev     out: coefficients, 2g x m (device)
+ *   cuda_stream  stream to run on
+ *
+ * Workspace: the LU factors, pivots and a status word live in one
+ * file-scope device array sized for 2g = MRCM_NOALLOC_MAX_G2 (about 513 KB),
+ * which every GPU that loads the library holds until the process exits.
+ * The first call on a device looks up that array's device address (once
+ * per device, with that device current); make that first call before any
+ * stream capture.  Every call reuses the same array and clears the status
+ * word itself, so calls that overlap on the GPU (different streams or
+ * devices sharing a context) race: serialise them.  The call synchronises
+ * its stream once to read the status.  Larger systems return
+ * MRCM_ERR_INVALID_ARG.  Errors: MRCM_ERR_INVALID_ARG, MRCM_ERR_SINGULAR,
+ * MRCM_ERR_CUDA.
+ */
+#define MRCM_NOALLOC_MAX_G2 256
+int mrcm_merge_pair_noalloc(const double* R1_dev, int m1, const double* R2_dev, int m2,
+                            const int* map_dev, int g, const double* D_dev,
+                            double* R_dev, double* X_dev, void* cuda_stream);
+
 /* mrcm_destroy -- free all device and host resources (NULL is a no-op). */
 void mrcm_destroy(mrcm_ctx* ctx);
 

@@ -23,7 +23,8 @@ Q = dict(LEAVES=0, SEGMENTS=1, LEVELS=2, NODES=3, WORKSPACE_BYTES=4, MAX_GAMMA=5
 # every symbol include/mrcm.h declares
 EXPORTS = ["mrcm_setup", "mrcm_plan_query", "mrcm_set_permeability", "mrcm_build_basis", "mrcm_solve", "mrcm_query",
            "mrcm_node_info", "mrcm_node_segments", "mrcm_segment_info", "mrcm_node_operator",
-           "mrcm_destroy", "mrcm_error_string", "mrcm_enable_timing", "mrcm_phase_times"]
+           "mrcm_destroy", "mrcm_error_string", "mrcm_enable_timing", "mrcm_phase_times",
+           "mrcm_merge_pair_noalloc"]
 PHASES = ["coef", "leaf_build", "merge_build", "leaf_particular", "tree_solve", "leaf_final", "finish"]
 
 
@@ -73,6 +74,8 @@ def _lib():
         lib.mrcm_enable_timing.restype = I
         lib.mrcm_phase_times.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
         lib.mrcm_phase_times.restype = I
+        lib.mrcm_merge_pair_noalloc.argtypes = [P, I, P, I, P, I, P, P, P, P]
+        lib.mrcm_merge_pair_noalloc.restype = I
         lib.mrcm_destroy.argtypes = [P]
         lib.mrcm_destroy.restype = None
         lib.mrcm_error_string.argtypes = [I]
@@ -188,3 +191,10 @@ def mrcm_destroy(ctx):
 
 def mrcm_error_string(code):
     return _lib().mrcm_error_string(code).decode()
+
+
+def mrcm_merge_pair_noalloc(R1, m1, R2, m2, index_map, g, D, R_out, X_out, stream=0):
+    """Allocation-free merge of two maps (device tensors in, device tensors out)."""
+    _check(_lib().mrcm_merge_pair_noalloc(_ptr(R1), int(m1), _ptr(R2), int(m2), _ptr(index_map),
+                                          int(g), _ptr(D), _ptr(R_out), _ptr(X_out), stream),
+           "mrcm_merge_pair_noalloc")
