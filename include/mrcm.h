@@ -129,7 +129,10 @@ int mrcm_build_basis(mrcm_ctx* ctx);
  *      flux traces; up-sweep of the particular data (Eqs. particular.1-2).
  *   2. Root interface system, then top-down recovery of every interface
  *      unknown (Algorithm 1).
- *   3. Final local solutions, Eq. (final): cell pressures and face fluxes.
+ *   3. Final local solutions, Eq. (final): cell pressures.
+ *   4. Iterative refinement (mrcm_set_refinement), then the zero-mean shift
+ *      of all-Neumann problems and the face fluxes from the cell pressures
+ *      and the interface unknowns.
  *
  *   q_dev      n[0]*n[1] integrated sources (all-Neumann problems need
  *              sum(q) + boundary inflow = 0 up to rounding)
@@ -184,10 +187,33 @@ enum {
     MRCM_PHASE_MERGE_BUILD = 2, /* all interface merges of the build              */
     MRCM_PHASE_LEAF_PART = 3,   /* leaf particular solutions (solve)              */
     MRCM_PHASE_TREE_SOLVE = 4,  /* up-sweep, root, down-sweep (solve)             */
-    MRCM_PHASE_LEAF_FINAL = 5,  /* final leaf pressures and fluxes (solve)        */
-    MRCM_PHASE_FINISH = 6,      /* skeleton fluxes and mean shift (solve)         */
-    MRCM_PHASE_COUNT = 7
+    MRCM_PHASE_LEAF_FINAL = 5,  /* leaf pressures and interface unknowns (solve)  */
+    MRCM_PHASE_FINISH = 6,      /* mean shift and face fluxes (solve)             */
+    MRCM_PHASE_RESIDUAL = 7,    /* refinement residuals (solve)                   */
+    MRCM_PHASE_COUNT = 8
 };
+
+/*
+ * mrcm_set_refinement -- iterative refinement of mrcm_solve (default 2 steps).
+ *
+ * The discrete MRCM solution is the exact solution of Eqs. (11.2)-(14.2)
+ * (lumped RT0); a direct FP64 solve meets it only to the conditioning of the
+ * problem times the rounding unit, which high-contrast permeability makes
+ * far larger than 1e-10.  Each step evaluates the residual of those
+ * equations in double-double arithmetic and solves for the correction with
+ * the factored basis (Wilkinson's iterative refinement); the result then
+ * matches the discrete solution to near FP64 accuracy when the conditioning
+ * is below 1/u.
+ *   steps  0..16 refinement steps per mrcm_solve
+ *   check  != 0: evaluate the residual once more after the last step (for
+ *          mrcm_residual_history)
+ *
+ * mrcm_residual_history -- out[k] (host) = max |residual| of the k-th
+ * evaluation in the last mrcm_solve (cell balances, Eq. 13.2 and 14.2 rows,
+ * unscaled); returns the number of evaluations (>= 0) or an error code.
+ */
+int mrcm_set_refinement(mrcm_ctx* ctx, int steps, int check);
+int mrcm_residual_history(mrcm_ctx* ctx, double* out, int cap);
 
 /*
  * mrcm_enable_timing -- on != 0: record a CUDA event pair around every phase

@@ -18,6 +18,7 @@ source and zero external data; the particular solution has lambda = 0 and
 the source / external data (Eqs. addu, addp).
 """
 import numpy as np
+import scipy.linalg as sla
 
 from inputs.problems import DIRICHLET
 
@@ -86,13 +87,38 @@ class LeafProblem:
             if f[0] == "robin":
                 _, c, t, rho, _ = f
                 self.B[c, self.seg_pos[t]] += rho
+        # face tables by kind, for vectorised flux evaluation
+        keys = {k: [] for k in ("int", "robin", "dir", "neu")}
+        for key, f in self.faces.items():
+            keys[f[0]].append((key, f))
+        self.kind_keys = {k: [kf[0] for kf in v] for k, v in keys.items()}
+        fi = [kf[1] for kf in keys["int"]]
+        self.int_c = np.array([f[1] for f in fi], dtype=np.int64)
+        self.int_c2 = np.array([f[2] for f in fi], dtype=np.int64)
+        self.int_T = np.array([f[3] for f in fi])
+        fr = [kf[1] for kf in keys["robin"]]
+        self.rob_c = np.array([f[1] for f in fr], dtype=np.int64)
+        self.rob_k = np.array([self.seg_pos[f[2]] for f in fr], dtype=np.int64)
+        self.rob_rho = np.array([f[3] for f in fr])
+        self.rob_sign = np.array([f[4] for f in fr])
+        fd = [kf[1] for kf in keys["dir"]]
+        self.dir_c = np.array([f[1] for f in fd], dtype=np.int64)
+        self.dir_tau = np.array([f[2] for f in fd])
+        self.dir_g = np.array([f[3] for f in fd])
+        self.dir_sign = np.array([f[4] for f in fd])
+        fn = [kf[1] for kf in keys["neu"]]
+        self.neu_flux = np.array([f[2] for f in fn])
+        self.neu_sign = np.array([f[3] for f in fn])
+        self._lu = None
 
-    def solve(self, lam, with_data):
+    def solve(self, lam, with_data, source=None, want_faces=True):
         """Solve the local problem for Robin data lam (one value per segment
         of the leaf, in self.segs order) with or without the source and
         external boundary data.  Several data sets may be passed as the
-        columns of lam (shape (m, k)).  Returns (p[n, k], outward segment
-        fluxes [m, k], face flux dict in +axis direction)."""
+        columns of lam (shape (m, k)).  `source` (h x w) adds a cell source
+        without external data (used for residual corrections).  Returns
+        (p[n, k], outward segment fluxes [m, k], face flux dict in +axis
+        direction, or None when want_faces is false)."""
         lam = np.asarray(lam, dtype=np.float64)
         single = lam.ndim == 1
         if single:
@@ -100,35 +126,35 @@ class LeafProblem:
         rhs = self.B @ lam
         if with_data:
             rhs = rhs + self.bbar[:, None]
-        p = np.linalg.solve(self.A, rhs)
+        if source is not None:
+            rhs = rhs + np.asarray(source, dtype=np.float64).reshape(-1)[:, None]
+        if self._lu is None:
+            self._lu = sla.lu_factor(self.A)
+        p = sla.lu_solve(self._lu, rhs)
+        # Robin faces: outward flux rho (p_c - lambda_t)
+        rob = self.rob_rho[:, None] * (p[self.rob_c] - lam[self.rob_k])
         seg_flux = np.zeros_like(lam)
-        faces = {}
-        for key, f in self.faces.items():
-            kind = f[0]
-            if kind == "int":
-                _, c, c2, T = f
-                faces[key] = T * (p[c] - p[c2])
-            elif kind == "robin":
-                _, c, t, rho, outsign = f
-                out = rho * (p[c] - lam[self.seg_pos[t]])
-                seg_flux[self.seg_pos[t]] += out
-                faces[key] = outsign * out
-            elif kind == "dir":
-                _, c, tau, gval, outsign = f
-                out = tau * (p[c] - (gval if with_data else 0.0))
-                faces[key] = outsign * out
-            else:
-                _, c, flux, outsign = f
-                out = flux if with_data else 0.0
-                faces[key] = outsign * out * np.ones(p.shape[1])
+        np.add.at(seg_flux, self.rob_k, rob)
+        faces = None
+        if want_faces:
+            k = p.shape[1]
+            vals = {}
+            fint = self.int_T[:, None] * (p[self.int_c] - p[self.int_c2])
+            vals.update(zip(self.kind_keys["int"], fint))
+            vals.update(zip(self.kind_keys["robin"], self.rob_sign[:, None] * rob))
+            g = self.dir_g[:, None] if with_data else 0.0
+            fdir = self.dir_sign[:, None] * (self.dir_tau[:, None] * (p[self.dir_c] - g))
+            vals.update(zip(self.kind_keys["dir"], fdir))
+            fneu = self.neu_sign[:, None] * (self.neu_flux[:, None] if with_data else np.zeros((len(self.neu_flux), 1)))
+            vals.update(zip(self.kind_keys["neu"], fneu * np.ones((1, k))))
+            faces = {key: (v[0] if single else v) for key, v in vals.items()}
         if single:
             p, seg_flux = p[:, 0], seg_flux[:, 0]
-            faces = {k: v[0] for k, v in faces.items()}
         return p, seg_flux, faces
 
     def robin_to_flux(self):
         """R[t, s] = outward flux through segment t for lambda = e_s, no data
         (the P_H = psi^s MMBF traces), and rbar = particular flux traces."""
-        _, R, _ = self.solve(np.eye(len(self.segs)), with_data=False)
-        _, rbar, _ = self.solve(np.zeros(len(self.segs)), with_data=True)
+        _, R, _ = self.solve(np.eye(len(self.segs)), with_data=False, want_faces=False)
+        _, rbar, _ = self.solve(np.zeros(len(self.segs)), with_data=True, want_faces=False)
         return R, rbar

@@ -20,6 +20,11 @@ the children's fluxes written through their R, rbar.  Solving gives gamma's
 (U, P) as X lambda_outer + Xbar, and the node's map follows by substitution
 (Eqs. new_bfs / particular.1-2, read as: basis responses are purely
 homogeneous, the particular part combines as in Eq. particular).
+
+The homogeneous part (R, X) is built once; solve_rhs() runs the particular
+up-sweep and the top-down pass for any data (source, external boundary data
+on or off, right-hand sides of the Eq. 13.2 / 14.2 rows), which also serves
+iterative refinement (oracle.refine).
 """
 import numpy as np
 
@@ -77,20 +82,21 @@ class RecursiveMRCM:
         self.dec = Decomposition(prob)
         self.root = build_tree(self.dec, tie)
         self.leaf_problems = {}
+        self._build(self.root)
 
-    # ---- upward pass: leaves via MFEM, then merges ---------------------
-    def _up(self, node):
+    # ---- homogeneous part: leaves via MFEM, merges -------------------------
+    def _build(self, node):
         dec = self.dec
         node.segs = outer_segments(dec, node.box)
         if node.leaf is not None:
             lp = LeafProblem(dec, node.leaf)
             self.leaf_problems[node.leaf] = lp
             assert lp.segs == node.segs
-            node.R, node.rbar = lp.robin_to_flux()
+            node.R, _ = lp.robin_to_flux()
             return
         c1, c2 = node.children
-        self._up(c1)
-        self._up(c2)
+        self._build(c1)
+        self._build(c2)
         gamma = [t for t in c1.segs if t in set(c2.segs)]
         node.gamma = gamma
         g = len(gamma)
@@ -102,6 +108,7 @@ class RecursiveMRCM:
         node.o1, node.o2 = o1, o2
         beta = np.array([dec.segments[t]["beta"] for t in gamma])
         length = np.array([dec.segments[t]["length"] for t in gamma])
+        node.beta = beta
         # c1 lies on side a of every gamma segment (lower coordinate)
         for t in gamma:
             assert _in_box(dec, dec.segments[t]["a"], c1.box)
@@ -111,6 +118,7 @@ class RecursiveMRCM:
         L2 = np.hstack([np.diag(beta), np.eye(g)])
         ig1 = [p1[t] for t in gamma]; ig2 = [p2[t] for t in gamma]
         io1 = [p1[t] for t in o1]; io2 = [p2[t] for t in o2]
+        node.ig1, node.ig2, node.io1, node.io2 = ig1, ig2, io1, io2
         # fluxes of each child through gamma: F^c_gamma = R^c_gg L^c Y + R^c_go lam_o + rbar^c_g
         Fy1 = c1.R[np.ix_(ig1, ig1)] @ L1
         Fy2 = c2.R[np.ix_(ig2, ig2)] @ L2
@@ -122,32 +130,63 @@ class RecursiveMRCM:
         Ucol = np.hstack([np.diag(length), np.zeros((g, g))])
         E = np.vstack([beta[:, None] * (Fy1 - Fy2 - 2 * Ucol), Fy1 + Fy2])
         G = -np.vstack([beta[:, None] * (Fo1 - Fo2), Fo1 + Fo2])
-        h = -np.vstack([(beta * (c1.rbar[ig1] - c2.rbar[ig2]))[:, None],
-                        (c1.rbar[ig1] + c2.rbar[ig2])[:, None]])[:, 0]
-        node.E, node.G, node.h = E, G, h
+        node.E, node.G = E, G
         node.L1, node.L2 = L1, L2
         if node is self.root:
+            if self.prob.pure_neumann:
+                # replace the Eq. (13.2) row of the first gamma segment by P = 0
+                E = E.copy()
+                E[g, :] = 0.0
+                E[g, g] = 1.0
+                node.E = E
             return
         X = np.linalg.solve(E, G)
-        Xbar = np.linalg.solve(E, h)
-        node.X, node.Xbar = X, Xbar
+        node.X = X
         # node map on o = o1 + o2
-        R = np.zeros((no, no)); rbar = np.zeros(no)
+        R = np.zeros((no, no))
         n1 = len(o1)
         R[:n1, :n1] = c1.R[np.ix_(io1, io1)]
         R[n1:, n1:] = c2.R[np.ix_(io2, io2)]
         R[:n1, :] += c1.R[np.ix_(io1, ig1)] @ L1 @ X
         R[n1:, :] += c2.R[np.ix_(io2, ig2)] @ L2 @ X
-        rbar[:n1] = c1.rbar[io1] + c1.R[np.ix_(io1, ig1)] @ L1 @ Xbar
-        rbar[n1:] = c2.rbar[io2] + c2.R[np.ix_(io2, ig2)] @ L2 @ Xbar
         # reorder o1 + o2 into sorted segment order
         order = np.argsort(o1 + o2)
         node.perm = order
         node.R = R[np.ix_(order, order)]
-        node.rbar = rbar[order]
 
-    # ---- downward pass ----------------------------------------------------
-    def _down(self, node, lam):
+    # ---- particular part for given data -----------------------------------
+    def _up(self, node, data):
+        if node.leaf is not None:
+            lp = self.leaf_problems[node.leaf]
+            src = data["source"]
+            src = None if src is None else src[lp.j0:lp.j1, lp.i0:lp.i1]
+            _, node.rbar, _ = lp.solve(np.zeros(len(lp.segs)), with_data=data["with_bc"], source=src,
+                                       want_faces=False)
+            return
+        c1, c2 = node.children
+        self._up(c1, data)
+        self._up(c2, data)
+        g = len(node.gamma)
+        r1 = c1.rbar[node.ig1]
+        r2 = c2.rbar[node.ig2]
+        h = -np.concatenate([node.beta * (r1 - r2), r1 + r2])
+        if data["rhs14"] is not None:
+            h[:g] += node.beta * data["rhs14"][node.gamma]
+        if data["rhs13"] is not None:
+            h[g:] += data["rhs13"][node.gamma]
+        if node is self.root:
+            if self.prob.pure_neumann:
+                h[g] = 0.0
+            node.h = h
+            return
+        node.Xbar = np.linalg.solve(node.E, h)
+        n1 = len(node.o1)
+        rbar = np.zeros(len(node.o1) + len(node.o2))
+        rbar[:n1] = c1.rbar[node.io1] + c1.R[np.ix_(node.io1, node.ig1)] @ node.L1 @ node.Xbar
+        rbar[n1:] = c2.rbar[node.io2] + c2.R[np.ix_(node.io2, node.ig2)] @ node.L2 @ node.Xbar
+        node.rbar = rbar[node.perm]
+
+    def _down(self, node, lam, UP):
         """lam: Robin data on node.segs (this node's side)."""
         if node.leaf is not None:
             node.lam = lam
@@ -155,17 +194,13 @@ class RecursiveMRCM:
         c1, c2 = node.children
         g = len(node.gamma)
         if node is self.root:
-            E, h = node.E.copy(), node.h.copy()
-            if self.prob.pure_neumann:
-                # replace the Eq. (13.2) row of the first gamma segment by P = 0
-                E[g, :] = 0.0
-                E[g, g] = 1.0
-                h[g] = 0.0
-            Y = np.linalg.solve(E, h)
+            Y = np.linalg.solve(node.E, node.h)
         else:
             lam_o = np.zeros(len(node.o1) + len(node.o2))
             lam_o[node.perm] = lam
             Y = node.X @ lam_o + node.Xbar
+        UP[0][node.gamma] = Y[:g]
+        UP[1][node.gamma] = Y[g:]
         lam1 = dict(zip(node.gamma, node.L1 @ Y))
         lam2 = dict(zip(node.gamma, node.L2 @ Y))
         pos = {t: k for k, t in enumerate(node.segs)}
@@ -173,23 +208,53 @@ class RecursiveMRCM:
             lam1[t] = lam[pos[t]]
         for t in node.o2:
             lam2[t] = lam[pos[t]]
-        self._down(c1, np.array([lam1[t] for t in c1.segs]))
-        self._down(c2, np.array([lam2[t] for t in c2.segs]))
+        self._down(c1, np.array([lam1[t] for t in c1.segs]), UP)
+        self._down(c2, np.array([lam2[t] for t in c2.segs]), UP)
 
-    def solve(self):
-        prob = self.prob
-        self._up(self.root)
-        self._down(self.root, np.zeros(0))
-        nx, ny = prob.nx, prob.ny
-        p = np.zeros((ny, nx))
-        Fa_x = np.zeros((ny, nx + 1)); Fb_x = np.zeros((ny, nx + 1))
-        Fa_y = np.zeros((ny + 1, nx)); Fb_y = np.zeros((ny + 1, nx))
+    def _leaves(self):
         stack = [self.root]
         while stack:
             node = stack.pop()
             if node.leaf is None:
                 stack += node.children
-                continue
+            else:
+                yield node
+
+    def solve_rhs(self, with_bc=True, source=None, rhs13=None, rhs14=None):
+        """(p[ny, nx], U, P) for the given data."""
+        prob = self.prob
+        data = dict(with_bc=with_bc, source=source, rhs13=rhs13, rhs14=rhs14)
+        nseg = len(self.dec.segments)
+        UP = (np.zeros(nseg), np.zeros(nseg))
+        self._up(self.root, data)
+        self._down(self.root, np.zeros(0), UP)
+        p = np.zeros((prob.ny, prob.nx))
+        for node in self._leaves():
+            lp = self.leaf_problems[node.leaf]
+            src = None if source is None else source[lp.j0:lp.j1, lp.i0:lp.i1]
+            pl, _, _ = lp.solve(node.lam, with_data=with_bc, source=src, want_faces=False)
+            p[lp.j0:lp.j1, lp.i0:lp.i1] = pl.reshape(lp.h, lp.w)
+        return p, UP[0], UP[1]
+
+    def solve(self, refine=0):
+        prob = self.prob
+        if refine > 0:
+            from .refine import refine_solution, fluxes_from_state, shift_mean
+            p, U, P = self.solve_rhs()
+            state, hist = refine_solution(prob, self.dec, self.solve_rhs, p, U, P, refine)
+            if prob.pure_neumann:
+                state = shift_mean(prob, state)
+            out = fluxes_from_state(prob, self.dec, state)
+            out["refine_history"] = hist
+            return out
+        self._up(self.root, dict(with_bc=True, source=None, rhs13=None, rhs14=None))
+        nseg = len(self.dec.segments)
+        self._down(self.root, np.zeros(0), (np.zeros(nseg), np.zeros(nseg)))
+        nx, ny = prob.nx, prob.ny
+        p = np.zeros((ny, nx))
+        Fa_x = np.zeros((ny, nx + 1)); Fb_x = np.zeros((ny, nx + 1))
+        Fa_y = np.zeros((ny + 1, nx)); Fb_y = np.zeros((ny + 1, nx))
+        for node in self._leaves():
             lp = self.leaf_problems[node.leaf]
             pl, _, faces = lp.solve(node.lam, with_data=True)
             p[lp.j0:lp.j1, lp.i0:lp.i1] = pl.reshape(lp.h, lp.w)
@@ -208,5 +273,5 @@ class RecursiveMRCM:
                     Fa_x=Fa_x, Fb_x=Fb_x, Fa_y=Fa_y, Fb_y=Fb_y)
 
 
-def solve_recursive(prob, tie="x"):
-    return RecursiveMRCM(prob, tie).solve()
+def solve_recursive(prob, tie="x", refine=0):
+    return RecursiveMRCM(prob, tie).solve(refine=refine)

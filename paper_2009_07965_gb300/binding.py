@@ -24,8 +24,9 @@ Q = dict(LEAVES=0, SEGMENTS=1, LEVELS=2, NODES=3, WORKSPACE_BYTES=4, MAX_GAMMA=5
 EXPORTS = ["mrcm_setup", "mrcm_plan_query", "mrcm_set_permeability", "mrcm_build_basis", "mrcm_solve", "mrcm_query",
            "mrcm_node_info", "mrcm_node_segments", "mrcm_segment_info", "mrcm_node_operator",
            "mrcm_destroy", "mrcm_error_string", "mrcm_enable_timing", "mrcm_phase_times",
-           "mrcm_merge_pair_noalloc"]
-PHASES = ["coef", "leaf_build", "merge_build", "leaf_particular", "tree_solve", "leaf_final", "finish"]
+           "mrcm_merge_pair_noalloc", "mrcm_set_refinement", "mrcm_residual_history"]
+PHASES = ["coef", "leaf_build", "merge_build", "leaf_particular", "tree_solve", "leaf_final", "finish",
+          "residual"]
 
 
 class MrcmError(RuntimeError):
@@ -76,6 +77,10 @@ def _lib():
         lib.mrcm_phase_times.restype = I
         lib.mrcm_merge_pair_noalloc.argtypes = [P, I, P, I, P, I, P, P, P, P]
         lib.mrcm_merge_pair_noalloc.restype = I
+        lib.mrcm_set_refinement.argtypes = [P, I, I]
+        lib.mrcm_set_refinement.restype = I
+        lib.mrcm_residual_history.argtypes = [P, ctypes.POINTER(ctypes.c_double), I]
+        lib.mrcm_residual_history.restype = I
         lib.mrcm_destroy.argtypes = [P]
         lib.mrcm_destroy.restype = None
         lib.mrcm_error_string.argtypes = [I]
@@ -182,6 +187,18 @@ def mrcm_phase_times(ctx):
     ms = (ctypes.c_double * len(PHASES))()
     _check(_lib().mrcm_phase_times(ctx, ms), "mrcm_phase_times")
     return dict(zip(PHASES, list(ms)))
+
+
+def mrcm_set_refinement(ctx, steps, check=False):
+    _check(_lib().mrcm_set_refinement(ctx, int(steps), 1 if check else 0), "mrcm_set_refinement")
+
+
+def mrcm_residual_history(ctx, cap=17):
+    buf = (ctypes.c_double * cap)()
+    n = _lib().mrcm_residual_history(ctx, buf, cap)
+    if n < 0:
+        raise MrcmError(n, "mrcm_residual_history")
+    return list(buf)[:min(n, cap)]
 
 
 def mrcm_destroy(ctx):

@@ -194,6 +194,7 @@ __device__ __forceinline__ double particular_rhs(const DevView& v, const LeafDes
     const int i = row % L.w, j = row / L.w;
     const int gi = L.i0 + i, gj = L.j0 + j;
     double b = q[(long long)gj * v.nx + gi];
+    if (!bc_val) return b;
     if (gi == 0) {
         const double g = bc_val[gj];
         b += v.bc[0] ? v.cxU[(long long)(v.nx + 1) * gj] * g : -v.hy * g;
@@ -220,7 +221,8 @@ struct LeafSolveSmem {
 
 template <int LPB>
 __global__ void __launch_bounds__(kLeafThreads * LPB)
-leaf_particular_kernel(DevView v, const double* __restrict__ q, const double* __restrict__ bc_val) {
+leaf_particular_kernel(DevView v, const double* __restrict__ q, const double* __restrict__ bc_val,
+                       bool with_sadj) {
     __shared__ LeafSolveSmem smem[LPB];
     const int t = threadIdx.x & (kLeafThreads - 1);
     const int slot_leaf = threadIdx.x / kLeafThreads;
@@ -256,14 +258,18 @@ leaf_particular_kernel(DevView v, const double* __restrict__ q, const double* __
     for (int s = t; s < m; s += kLeafThreads) {
         double acc = 0.0;
         for (int k = 0; k < n; ++k) acc += Zg[(long long)k * m + s] * S.y[k];
+        // a right-hand side sigma on this segment's interface row,
+        // F - D (lambda_other - lambda_own) = sigma, acts as rbar - sigma
+        if (with_sadj) acc -= v.sadj[L.r_off + s];
         rb[s] = acc;
     }
 }
 
+// p = A^-1 (bbar + B lambda) = L^-T D^-1 (zbar + Z lambda), written into the
+// state (p_hi, p_lo) or added to it in double-double (refinement corrections).
 template <int LPB>
 __global__ void __launch_bounds__(kLeafThreads * LPB)
-leaf_final_kernel(DevView v, const double* __restrict__ q, const double* __restrict__ bc_val,
-                  double* __restrict__ p, double* __restrict__ Fx, double* __restrict__ Fy) {
+leaf_pressure_kernel(DevView v, bool accumulate) {
     __shared__ LeafSolveSmem smem[LPB];
     __shared__ double lam_s[LPB][64];
     const int t = threadIdx.x & (kLeafThreads - 1);
@@ -274,7 +280,7 @@ leaf_final_kernel(DevView v, const double* __restrict__ q, const double* __restr
     LeafSolveSmem& S = smem[slot_leaf];
     double* lam = lam_s[slot_leaf];
     const LeafDesc L = v.leaves[leaf];
-    const int w = L.w, h = L.h, n = L.w * L.h, m = L.m, W2 = L.w + 2;
+    const int w = L.w, n = L.w * L.h, m = L.m, W2 = L.w + 2;
     const double* Lg = v.leafL + L.L_off;
     const double* Dg = Lg + (long long)n * kLeafThreads;
     const double* Zg = v.leafZ + L.Z_off;
@@ -305,114 +311,29 @@ leaf_final_kernel(DevView v, const double* __restrict__ q, const double* __restr
         }
         __syncwarp(mask);
     }
-    // pressures
     for (int k = t; k < n; k += kLeafThreads) {
         const int i = k % w, j = k / w;
-        p[(long long)(L.j0 + j) * v.nx + L.i0 + i] = S.y[k];
-    }
-    // x faces of the leaf: i = 0..w (local), rows j
-    const long long nxf1 = v.nx + 1;
-    for (int idx = t; idx < (w + 1) * h; idx += kLeafThreads) {
-        const int i = idx % (w + 1), j = idx / (w + 1);
-        const int gi = L.i0 + i, gj = L.j0 + j;
-        const long long f = gi + nxf1 * gj;
-        if (i > 0 && i < w) {
-            Fx[f] = v.cxL[f] * (S.y[j * w + i - 1] - S.y[j * w + i]);
-        } else if (gi == 0) {
-            const double g = bc_val[gj];
-            const double out = v.bc[0] ? v.cxU[f] * (S.y[j * w] - g) : v.hy * g;
-            Fx[f] = -out;
-        } else if (gi == v.nx) {
-            const double g = bc_val[v.ny + gj];
-            const double out = v.bc[1] ? v.cxL[f] * (S.y[j * w + w - 1] - g) : v.hy * g;
-            Fx[f] = out;
+        const long long c = (long long)(L.j0 + j) * v.nx + L.i0 + i;
+        if (accumulate) {
+            const DD x = dd_add(DD{v.p_hi[c], v.p_lo[c]}, DD{S.y[k], 0.0});
+            v.p_hi[c] = x.h;
+            v.p_lo[c] = x.l;
         } else {
-            // skeleton face: one-sided flux of this leaf, +x direction
-            const bool side_a = (i == w);
-            const int s = side_a ? L.side_off[1] + j / v.gy : L.side_off[0] + j / v.gy;
-            const int seg = v.leaf_segs[L.seg_off + s];
-            const int e = gj - v.seg_lo[seg];
-            const double pc = S.y[j * w + (side_a ? w - 1 : 0)];
-            const double out = (side_a ? v.cxL[f] : v.cxU[f]) * (pc - lam[s]);
-            v.skel[2 * (long long)(v.seg_face_off[seg] + e) + (side_a ? 0 : 1)] = side_a ? out : -out;
+            v.p_hi[c] = S.y[k];
+            v.p_lo[c] = 0.0;
         }
-    }
-    // y faces: j = 0..h, columns i
-    const long long nxl = v.nx;
-    for (int idx = t; idx < w * (h + 1); idx += kLeafThreads) {
-        const int i = idx % w, j = idx / w;
-        const int gi = L.i0 + i, gj = L.j0 + j;
-        const long long f = gi + nxl * gj;
-        if (j > 0 && j < h) {
-            Fy[f] = v.cyL[f] * (S.y[(j - 1) * w + i] - S.y[j * w + i]);
-        } else if (gj == 0) {
-            const double g = bc_val[2 * v.ny + gi];
-            const double out = v.bc[2] ? v.cyU[f] * (S.y[i] - g) : v.hx * g;
-            Fy[f] = -out;
-        } else if (gj == v.ny) {
-            const double g = bc_val[2 * v.ny + v.nx + gi];
-            const double out = v.bc[3] ? v.cyL[f] * (S.y[(h - 1) * w + i] - g) : v.hx * g;
-            Fy[f] = out;
-        } else {
-            const bool side_a = (j == h);
-            const int s = side_a ? L.side_off[3] + i / v.gx : L.side_off[2] + i / v.gx;
-            const int seg = v.leaf_segs[L.seg_off + s];
-            const int e = gi - v.seg_lo[seg];
-            const double pc = S.y[(side_a ? h - 1 : 0) * w + i];
-            const double out = (side_a ? v.cyL[f] : v.cyU[f]) * (pc - lam[s]);
-            v.skel[2 * (long long)(v.seg_face_off[seg] + e) + (side_a ? 0 : 1)] = side_a ? out : -out;
-        }
-    }
-}
-
-// Skeleton faces: mean of the two one-sided values; optional one-sided
-// output [Fa_x, Fb_x, Fa_y, Fb_y] (off the skeleton both equal F).
-__global__ void skeleton_flux_kernel(DevView v, double* Fx, double* Fy, double* iface) {
-    const long long nxf = (long long)(v.nx + 1) * v.ny;
-    const long long nyf = (long long)v.nx * (v.ny + 1);
-    long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (f >= nxf + nyf) return;
-    const bool xface = f < nxf;
-    const long long fl = xface ? f : f - nxf;
-    int axis, line, k;
-    if (xface) { axis = 0; line = (int)(fl % (v.nx + 1)); k = (int)(fl / (v.nx + 1)); }
-    else { axis = 1; k = (int)(fl % v.nx); line = (int)(fl / v.nx); }
-    const int nline = axis == 0 ? v.nx : v.ny;
-    const int sub = axis == 0 ? v.sx : v.sy;
-    double* F = xface ? Fx : Fy;
-    const bool skel = line > 0 && line < nline && line % sub == 0;
-    double fa, fb;
-    if (skel) {
-        // segment: carried by the + side of the leaf below the line
-        int leaf, side, pos;
-        const int nlx = (v.nx + v.sx - 1) / v.sx;
-        if (axis == 0) { leaf = (line / v.sx - 1) + nlx * (k / v.sy); side = 1; }
-        else { leaf = (k / v.sx) + nlx * (line / v.sy - 1); side = 3; }
-        const LeafDesc& L = v.leaves[leaf];
-        pos = axis == 0 ? (k - L.j0) / v.gy : (k - L.i0) / v.gx;
-        const int seg = v.leaf_segs[L.seg_off + L.side_off[side] + pos];
-        const long long e = v.seg_face_off[seg] + (k - v.seg_lo[seg]);
-        fa = v.skel[2 * e];
-        fb = v.skel[2 * e + 1];
-        F[fl] = 0.5 * (fa + fb);
-    } else {
-        if (!iface) return;
-        fa = fb = F[fl];
-    }
-    if (iface) {
-        if (xface) { iface[fl] = fa; iface[nxf + fl] = fb; }
-        else { iface[2 * nxf + fl] = fa; iface[2 * nxf + nyf + fl] = fb; }
     }
 }
 
 constexpr int kRedBlocks = 256;
 
-__global__ void mean_partial_kernel(const double* __restrict__ p, long long n, double* red) {
+__global__ void mean_partial_kernel(const double* __restrict__ ph, const double* __restrict__ pl, long long n,
+                                    double* red) {
     __shared__ double sh[256];
     double acc = 0.0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)
-        acc += p[i];
+        acc += ph[i] + pl[i];
     sh[threadIdx.x] = acc;
     __syncthreads();
     for (int s = 128; s > 0; s >>= 1) {
@@ -422,17 +343,31 @@ __global__ void mean_partial_kernel(const double* __restrict__ p, long long n, d
     if (threadIdx.x == 0) red[blockIdx.x] = sh[0];
 }
 
-__global__ void mean_subtract_kernel(double* __restrict__ p, long long n, const double* red) {
+// Subtracts the mean of the rounded cell pressures from p and P, in
+// double-double (the shift is exact up to its own rounding).
+__global__ void mean_subtract_kernel(DevView v, long long n) {
     __shared__ double mean;
-    if (threadIdx.x == 0) {
-        double acc = 0.0;   // same order in every block: identical mean
-        for (int b = 0; b < kRedBlocks; ++b) acc += red[b];
-        mean = acc / (double)n;
+    if (threadIdx.x < 32) {
+        // fixed-order warp reduction of the block partial sums: every block
+        // obtains the identical mean
+        double acc = 0.0;
+        for (int b = threadIdx.x; b < kRedBlocks; b += 32) acc += v.red[b];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (threadIdx.x == 0) mean = acc / (double)n;
     }
     __syncthreads();
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x)
-        p[i] -= mean;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) {
+        const DD x = dd_add(DD{v.p_hi[i], v.p_lo[i]}, DD{-mean, 0.0});
+        v.p_hi[i] = x.h;
+        v.p_lo[i] = x.l;
+    }
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < v.nseg; i += stride) {
+        const DD x = dd_add(DD{v.segP[i], v.segP_lo[i]}, DD{-mean, 0.0});
+        v.segP[i] = x.h;
+        v.segP_lo[i] = x.l;
+    }
 }
 
 }  // namespace
@@ -452,33 +387,26 @@ cudaError_t launch_leaf_build(const DevView& v, int max_m, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_leaf_particular(const DevView& v, const double* q, const double* bc_val, int,
-                                   cudaStream_t s) {
+cudaError_t launch_leaf_particular(const DevView& v, const double* q, const double* bc_val,
+                                   bool with_sadj, cudaStream_t s) {
     constexpr int LPB = 8;
-    leaf_particular_kernel<LPB><<<(v.nleaf + LPB - 1) / LPB, kLeafThreads * LPB, 0, s>>>(v, q, bc_val);
+    leaf_particular_kernel<LPB><<<(v.nleaf + LPB - 1) / LPB, kLeafThreads * LPB, 0, s>>>(v, q, bc_val,
+                                                                                          with_sadj);
     return cudaGetLastError();
 }
 
-cudaError_t launch_leaf_final(const DevView& v, const double* q, const double* bc_val, double* p,
-                              double* Fx, double* Fy, int, cudaStream_t s) {
+cudaError_t launch_leaf_pressure(const DevView& v, bool accumulate, cudaStream_t s) {
     constexpr int LPB = 8;
-    leaf_final_kernel<LPB><<<(v.nleaf + LPB - 1) / LPB, kLeafThreads * LPB, 0, s>>>(v, q, bc_val, p, Fx, Fy);
+    leaf_pressure_kernel<LPB><<<(v.nleaf + LPB - 1) / LPB, kLeafThreads * LPB, 0, s>>>(v, accumulate);
     return cudaGetLastError();
 }
 
-cudaError_t launch_skeleton_fluxes(const DevView& v, double* Fx, double* Fy, double* iface,
-                                   cudaStream_t s) {
-    const long long nf = (long long)(v.nx + 1) * v.ny + (long long)v.nx * (v.ny + 1);
-    skeleton_flux_kernel<<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(v, Fx, Fy, iface);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_mean_shift(const DevView& v, double* p, cudaStream_t s) {
+cudaError_t launch_mean_shift(const DevView& v, cudaStream_t s) {
     const long long n = (long long)v.nx * v.ny;
-    mean_partial_kernel<<<kRedBlocks, 256, 0, s>>>(p, n, v.red);
+    mean_partial_kernel<<<kRedBlocks, 256, 0, s>>>(v.p_hi, v.p_lo, n, v.red);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    mean_subtract_kernel<<<kRedBlocks, 256, 0, s>>>(p, n, v.red);
+    mean_subtract_kernel<<<kRedBlocks, 256, 0, s>>>(v, n);
     return cudaGetLastError();
 }
 

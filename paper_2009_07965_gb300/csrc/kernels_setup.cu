@@ -7,10 +7,12 @@
 // and the coupling of the two Robin sides D_t = |t| / (2 beta_t).
 //
 // Face coefficients of the lumped RT0 (two-point flux) local operators,
-// seen from each of the two cells of a face:
-//     interior face:   T   = |e| / (h/(2K_a) + h/(2K_b))       (both sides)
-//     skeleton face:   rho = |e| / (h/(2K_c) + beta_t)         (Eq. 11.2, lumped)
+// seen from each of the two cells of a face, with r_c = h/(2K_c):
+//     interior face:   T   = |e| / (r_a + r_b)                 (both sides)
+//     skeleton face:   rho = |e| / (r_c + beta_t)              (Eq. 11.2, lumped)
 //     Dirichlet face:  tau = 2 K_c |e| / h,   Neumann face: 0.
+// Each coefficient is evaluated in this exact order (no fused operations),
+// so that the discrete system is defined to the last bit.
 #include "mrcm_internal.h"
 
 namespace mrcm {
@@ -26,6 +28,17 @@ __global__ void check_K_kernel(const double* __restrict__ K, long long n, int* s
         bad |= !(k > 0.0 && k < 1.0e300);
     }
     if (bad) atomicOr(status, kStatusBadK);
+}
+
+// Half-cell resistances r = h_d / (2 K_c), the building block of every face
+// coefficient below (evaluated once per cell, in this order).
+__global__ void cell_resist_kernel(DevView v) {
+    const long long n = (long long)v.nx * v.ny;
+    const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    const double k2 = 2.0 * v.K[c];
+    v.rx[c] = v.hx / k2;
+    v.ry[c] = v.hy / k2;
 }
 
 __global__ void seg_beta_kernel(DevView v) {
@@ -52,26 +65,6 @@ __global__ void seg_beta_kernel(DevView v) {
     v.seg_D[t] = keff / (2.0 * v.alpha);
 }
 
-// Global segment id and position of the skeleton face (axis, line, k), where
-// k is the cell index along the face; the leaf below the face (side a)
-// carries the segment on its + side.
-__device__ __forceinline__ int skeleton_segment(const DevView& v, int axis, int line, int k) {
-    int leaf, side, pos;
-    if (axis == 0) {
-        const int I = line / v.sx - 1, J = k / v.sy;
-        leaf = I + ((v.nx + v.sx - 1) / v.sx) * J;
-        side = 1;
-        pos = (k - v.leaves[leaf].j0) / v.gy;
-    } else {
-        const int I = k / v.sx, J = line / v.sy - 1;
-        leaf = I + ((v.nx + v.sx - 1) / v.sx) * J;
-        side = 3;
-        pos = (k - v.leaves[leaf].i0) / v.gx;
-    }
-    const LeafDesc& L = v.leaves[leaf];
-    return v.leaf_segs[L.seg_off + L.side_off[side] + pos];
-}
-
 __global__ void face_coef_kernel(DevView v) {
     const long long nxf = (long long)(v.nx + 1) * v.ny;
     const long long nyf = (long long)v.nx * (v.ny + 1);
@@ -79,19 +72,20 @@ __global__ void face_coef_kernel(DevView v) {
     if (f < nxf) {
         const int i = (int)(f % (v.nx + 1)), j = (int)(f / (v.nx + 1));
         const double area = v.hy, hn = v.hx;
+        const long long row = (long long)j * v.nx;
         double cl = 0.0, cu = 0.0;
         if (i == 0) {
-            if (v.bc[0]) cu = 2.0 * v.K[(long long)j * v.nx] * area / hn;
+            if (v.bc[0]) cu = 2.0 * v.K[row] * area / hn;
         } else if (i == v.nx) {
-            if (v.bc[1]) cl = 2.0 * v.K[(long long)j * v.nx + v.nx - 1] * area / hn;
+            if (v.bc[1]) cl = 2.0 * v.K[row + v.nx - 1] * area / hn;
         } else {
-            const double ka = v.K[(long long)j * v.nx + i - 1], kb = v.K[(long long)j * v.nx + i];
+            const double ra = v.rx[row + i - 1], rb = v.rx[row + i];
             if (i % v.sx == 0) {
                 const double beta = v.seg_beta[skeleton_segment(v, 0, i, j)];
-                cl = 2.0 * ka * area / (hn + 2.0 * ka * beta);
-                cu = 2.0 * kb * area / (hn + 2.0 * kb * beta);
+                cl = area / (ra + beta);
+                cu = area / (rb + beta);
             } else {
-                cl = cu = (2.0 * area / hn) * ka * kb / (ka + kb);
+                cl = cu = area / (ra + rb);
             }
         }
         v.cxL[f] = cl;
@@ -108,13 +102,13 @@ __global__ void face_coef_kernel(DevView v) {
         } else if (j == v.ny) {
             if (v.bc[3]) cl = 2.0 * v.K[(long long)(v.ny - 1) * v.nx + i] * area / hn;
         } else {
-            const double ka = v.K[(long long)(j - 1) * v.nx + i], kb = v.K[(long long)j * v.nx + i];
+            const double ra = v.ry[(long long)(j - 1) * v.nx + i], rb = v.ry[(long long)j * v.nx + i];
             if (j % v.sy == 0) {
                 const double beta = v.seg_beta[skeleton_segment(v, 1, j, i)];
-                cl = 2.0 * ka * area / (hn + 2.0 * ka * beta);
-                cu = 2.0 * kb * area / (hn + 2.0 * kb * beta);
+                cl = area / (ra + beta);
+                cu = area / (rb + beta);
             } else {
-                cl = cu = (2.0 * area / hn) * ka * kb / (ka + kb);
+                cl = cu = area / (ra + rb);
             }
         }
         v.cyL[f] = cl;
@@ -129,6 +123,12 @@ cudaError_t launch_check_K(const DevView& v, cudaStream_t s) {
     int blocks = (int)((n + 255) / 256);
     if (blocks > 152 * 8) blocks = 152 * 8;
     check_K_kernel<<<blocks, 256, 0, s>>>(v.K, n, v.status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cell_resist(const DevView& v, cudaStream_t s) {
+    const long long n = (long long)v.nx * v.ny;
+    cell_resist_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(v);
     return cudaGetLastError();
 }
 

@@ -20,6 +20,8 @@ using namespace mrcm;
 
 namespace {
 
+constexpr int kMaxRefine = 16;
+
 struct Plan {
     int nx = 0, ny = 0;
     double hx = 0, hy = 0, alpha = 0;
@@ -51,6 +53,7 @@ struct Plan {
     // storage sizes (doubles / ints)
     long long nR = 0, nr = 0, nLU = 0, npiv = 0, nX = 0, nxb = 0, nL = 0, nZ = 0, nzb = 0;
     std::vector<long long> node_R_off, node_r_off;
+    std::vector<long long> seg_lam_a, seg_lam_b;   // lam offsets of each segment in its two leaves
     // flop model
     long long leaf_flops = 0, merge_flops = 0, solve_flops = 0;
 };
@@ -211,7 +214,6 @@ int make_plan(Plan& P) {
         P.nzb += n;
         L.R_off = P.node_R_off[id];
         L.r_off = P.node_r_off[id];
-        L.fs_off = 0;
         // flop model of the leaf kernel: LDL^T band steps, forward solve of
         // the m Robin columns, SYRK of the lower triangle (FMA = 2 flops)
         long long f = 0;
@@ -224,6 +226,17 @@ int make_plan(Plan& P) {
         P.leaf_flops += f;
         // solve phase per leaf: forward sweep, Z^T y, Z lambda, backward sweep
         P.solve_flops += 2 * n * L.w * 2 + 2 * n * L.m * 2 + 2 * n;
+    }
+    // offsets of each segment inside the Robin-data arrays of its two leaves
+    P.seg_lam_a.assign(P.nseg, -1);
+    P.seg_lam_b.assign(P.nseg, -1);
+    for (int id = 0; id < P.nleaf; ++id) {
+        const LeafDesc& L = P.leaves[id];
+        for (int k = 0; k < L.m; ++k) {
+            const int t = P.leaf_segs[L.seg_off + k];
+            if (P.seg_a[t] == id) P.seg_lam_a[t] = L.r_off + k;
+            else P.seg_lam_b[t] = L.r_off + k;
+        }
     }
     // merges grouped by height
     std::vector<std::vector<int>> by_h(P.height + 1);
@@ -288,8 +301,11 @@ struct mrcm_ctx {
     double* K = nullptr;
     int launches_build = 0, launches_solve = 0;
     bool timing = false;
-    cudaEvent_t ev[2 * MRCM_PHASE_COUNT] = {};
-    bool ev_used[MRCM_PHASE_COUNT] = {};
+    cudaEvent_t ev[2 * MRCM_PHASE_COUNT * (kMaxRefine + 2)] = {};
+    int ev_count[MRCM_PHASE_COUNT] = {};
+    int refine_steps = 2;
+    int refine_check = 0;
+    int hist_count = 0;
 };
 
 namespace {
@@ -338,17 +354,20 @@ int read_status(mrcm_ctx* c) {
     return MRCM_OK;
 }
 
+// Records a CUDA event pair around one occurrence of a phase; the phase time
+// of a call is the sum over its occurrences.
+constexpr int kMaxOcc = kMaxRefine + 2;
 struct PhaseScope {
     mrcm_ctx* c;
-    int phase;
-    PhaseScope(mrcm_ctx* c_, int p) : c(c_), phase(p) {
-        if (c->timing) {
-            cudaEventRecord(c->ev[2 * p], c->stream);
-            c->ev_used[p] = true;
+    int slot = -1;
+    PhaseScope(mrcm_ctx* c_, int p) : c(c_) {
+        if (c->timing && c->ev_count[p] < kMaxOcc) {
+            slot = 2 * (p * kMaxOcc + c->ev_count[p]++);
+            cudaEventRecord(c->ev[slot], c->stream);
         }
     }
     ~PhaseScope() {
-        if (c->timing) cudaEventRecord(c->ev[2 * phase + 1], c->stream);
+        if (slot >= 0) cudaEventRecord(c->ev[slot + 1], c->stream);
     }
 };
 
@@ -413,7 +432,7 @@ static int plan_value(const Plan& P, int what, long long* value) {
         case MRCM_Q_NODES: *value = (long long)P.nodes.size(); break;
         case MRCM_Q_MAX_GAMMA: *value = P.max_g2; break;
         case MRCM_Q_BUILD_FLOPS: *value = P.leaf_flops + P.merge_flops; break;
-        case MRCM_Q_SOLVE_FLOPS: *value = P.solve_flops; break;
+        case MRCM_Q_SOLVE_FLOPS: *value = P.solve_flops; break;  // one solve pass
         case MRCM_Q_LEAF_FLOPS: *value = P.leaf_flops; break;
         default: return MRCM_ERR_INVALID_ARG;
     }
@@ -448,6 +467,8 @@ static int setup_impl(mrcm_ctx* c, const mrcm_grid* g, const double* K_dev, cons
     const long long nxf = (long long)(P.nx + 1) * P.ny, nyf = (long long)P.nx * (P.ny + 1);
     TRY(dev_alloc(c, &c->K, ncell));
     v.K = c->K;
+    TRY(dev_alloc(c, &v.rx, ncell));
+    TRY(dev_alloc(c, &v.ry, ncell));
     TRY(dev_alloc(c, &v.seg_beta, P.nseg));
     TRY(dev_alloc(c, &v.seg_D, P.nseg));
     TRY(dev_alloc(c, &v.cxL, nxf));
@@ -461,6 +482,8 @@ static int setup_impl(mrcm_ctx* c, const mrcm_grid* g, const double* K_dev, cons
     TRY(upload(c, &v.seg_a, P.seg_a));
     TRY(upload(c, &v.seg_b, P.seg_b));
     TRY(upload(c, &v.seg_face_off, P.seg_face_off));
+    TRY(upload(c, &v.seg_lam_a, P.seg_lam_a));
+    TRY(upload(c, &v.seg_lam_b, P.seg_lam_b));
     TRY(upload(c, &v.leaves, P.leaves));
     TRY(upload(c, &v.leaf_segs, P.leaf_segs));
     TRY(upload(c, &v.merges, P.merges));
@@ -476,7 +499,15 @@ static int setup_impl(mrcm_ctx* c, const mrcm_grid* g, const double* K_dev, cons
     TRY(dev_alloc(c, &v.piv, P.npiv));
     TRY(dev_alloc(c, &v.X, P.nX));
     TRY(dev_alloc(c, &v.xbar, P.nxb));
-    TRY(dev_alloc(c, &v.skel, 2 * P.nskel_faces));
+    TRY(dev_alloc(c, &v.segP, P.nseg));
+    TRY(dev_alloc(c, &v.segU, P.nseg));
+    TRY(dev_alloc(c, &v.segP_lo, P.nseg));
+    TRY(dev_alloc(c, &v.segU_lo, P.nseg));
+    TRY(dev_alloc(c, &v.p_hi, ncell));
+    TRY(dev_alloc(c, &v.p_lo, ncell));
+    TRY(dev_alloc(c, &v.rcell, ncell));
+    TRY(dev_alloc(c, &v.sadj, P.nr));
+    TRY(dev_alloc(c, &v.res_max, kMaxRefine + 1));
     TRY(dev_alloc(c, &v.red, 1024));
     TRY(dev_alloc(c, &v.status, 4));
     TRYC(cudaMemcpyAsync(c->K, K_dev, sizeof(double) * ncell, cudaMemcpyDefault, c->stream));
@@ -525,11 +556,12 @@ int mrcm_build_basis(mrcm_ctx* c) {
     c->built = false;
     c->solved = false;
     int launches = 0;
-    for (int p = 0; p < MRCM_PHASE_COUNT; ++p) c->ev_used[p] = false;
+    for (int p = 0; p < MRCM_PHASE_COUNT; ++p) c->ev_count[p] = 0;
     TRYC(cudaMemsetAsync(v.status, 0, sizeof(int), s));
     {
         PhaseScope ps(c, MRCM_PHASE_COEF);
         TRYC(launch_check_K(v, s)); ++launches;
+        TRYC(launch_cell_resist(v, s)); ++launches;
         TRYC(launch_seg_beta(v, s)); launches += P.nseg > 0;
         TRYC(launch_face_coef(v, s)); ++launches;
     }
@@ -551,20 +583,17 @@ int mrcm_build_basis(mrcm_ctx* c) {
     return MRCM_OK;
 }
 
-int mrcm_solve(mrcm_ctx* c, const double* q_dev, const double* bc_val_dev, double* p_dev, double* Fx_dev,
-               double* Fy_dev, double* Fz_dev, double* iface_dev) {
-    if (!c) return MRCM_ERR_INVALID_ARG;
-    if (!c->built) return MRCM_ERR_NOT_BUILT;
-    if (!q_dev || !bc_val_dev || !p_dev || !Fx_dev || !Fy_dev || Fz_dev) return MRCM_ERR_INVALID_ARG;
+// One pass of the solve phase for the data (q, bc) -- or, with bc == nullptr
+// and with_sadj, for a refinement residual: leaf particular solutions,
+// up-sweep and root, down-sweep, leaf pressures, interface unknowns.
+static int solve_pass(mrcm_ctx* c, const double* q, const double* bc, bool with_sadj, bool accumulate,
+                      int& launches) {
     const Plan& P = c->P;
     const DevView& v = c->v;
     cudaStream_t s = c->stream;
-    int launches = 0;
-    for (int p = MRCM_PHASE_LEAF_PART; p < MRCM_PHASE_COUNT; ++p) c->ev_used[p] = false;
-    TRYC(cudaMemsetAsync(v.status, 0, sizeof(int), s));
     {
         PhaseScope ps(c, MRCM_PHASE_LEAF_PART);
-        TRYC(launch_leaf_particular(v, q_dev, bc_val_dev, P.max_m_leaf, s)); ++launches;
+        TRYC(launch_leaf_particular(v, q, bc, with_sadj, s)); ++launches;
     }
     {
         PhaseScope ps(c, MRCM_PHASE_TREE_SOLVE);
@@ -579,23 +608,73 @@ int mrcm_solve(mrcm_ctx* c, const double* q_dev, const double* bc_val_dev, doubl
     }
     {
         PhaseScope ps(c, MRCM_PHASE_LEAF_FINAL);
-        TRYC(launch_leaf_final(v, q_dev, bc_val_dev, p_dev, Fx_dev, Fy_dev, P.max_m_leaf, s)); ++launches;
+        TRYC(launch_leaf_pressure(v, accumulate, s)); ++launches;
+        TRYC(launch_lam_to_PU(v, accumulate, s)); launches += P.nseg > 0;
     }
+    return MRCM_OK;
+}
+
+int mrcm_solve(mrcm_ctx* c, const double* q_dev, const double* bc_val_dev, double* p_dev, double* Fx_dev,
+               double* Fy_dev, double* Fz_dev, double* iface_dev) {
+    if (!c) return MRCM_ERR_INVALID_ARG;
+    if (!c->built) return MRCM_ERR_NOT_BUILT;
+    if (!q_dev || !bc_val_dev || !p_dev || !Fx_dev || !Fy_dev || Fz_dev) return MRCM_ERR_INVALID_ARG;
+    const Plan& P = c->P;
+    const DevView& v = c->v;
+    cudaStream_t s = c->stream;
+    int launches = 0;
+    for (int p = MRCM_PHASE_LEAF_PART; p < MRCM_PHASE_COUNT; ++p) c->ev_count[p] = 0;
+    TRYC(cudaMemsetAsync(v.status, 0, sizeof(int), s));
+    const int steps = c->refine_steps, nres = steps + (c->refine_check ? 1 : 0);
+    if (nres > 0) TRYC(cudaMemsetAsync(v.res_max, 0, sizeof(unsigned long long) * nres, s));
+    TRY(solve_pass(c, q_dev, bc_val_dev, false, false, launches));
+    for (int it = 0; it < steps; ++it) {
+        {
+            PhaseScope ps(c, MRCM_PHASE_RESIDUAL);
+            TRYC(launch_residual(v, q_dev, bc_val_dev, it, s));
+            launches += 1 + (P.nseg > 0);
+        }
+        TRY(solve_pass(c, v.rcell, nullptr, true, true, launches));
+    }
+    if (c->refine_check) {
+        TRYC(launch_residual(v, q_dev, bc_val_dev, steps, s));
+        launches += 1 + (P.nseg > 0);
+    }
+    c->hist_count = nres;
     {
         PhaseScope ps(c, MRCM_PHASE_FINISH);
-        if (P.nseg > 0 || iface_dev) {
-            TRYC(launch_skeleton_fluxes(v, Fx_dev, Fy_dev, iface_dev, s));
-            ++launches;
-        }
         if (P.pure_neumann) {
-            TRYC(launch_mean_shift(v, p_dev, s));
+            TRYC(launch_mean_shift(v, s));
             launches += 2;
         }
+        TRYC(launch_face_fluxes(v, bc_val_dev, p_dev, Fx_dev, Fy_dev, iface_dev, s));
+        ++launches;
     }
     c->launches_solve = launches;
     TRY(read_status(c));
     c->solved = true;
     return MRCM_OK;
+}
+
+int mrcm_set_refinement(mrcm_ctx* c, int steps, int check) {
+    if (!c || steps < 0 || steps > kMaxRefine) return MRCM_ERR_INVALID_ARG;
+    c->refine_steps = steps;
+    c->refine_check = check ? 1 : 0;
+    return MRCM_OK;
+}
+
+int mrcm_residual_history(mrcm_ctx* c, double* out, int cap) {
+    if (!c || !out || cap < 0) return MRCM_ERR_INVALID_ARG;
+    if (!c->solved) return MRCM_ERR_NOT_BUILT;
+    const int n = std::min(cap, c->hist_count);
+    unsigned long long bits[kMaxRefine + 1];
+    if (n > 0) {
+        TRYC(cudaMemcpyAsync(bits, c->v.res_max, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost,
+                             c->stream));
+        TRYC(cudaStreamSynchronize(c->stream));
+    }
+    for (int k = 0; k < n; ++k) std::memcpy(&out[k], &bits[k], sizeof(double));
+    return c->hist_count;
 }
 
 int mrcm_query(const mrcm_ctx* c, int what, long long* value) {
@@ -660,7 +739,7 @@ int mrcm_node_operator(mrcm_ctx* c, int node, double* R_host, double* rbar_host)
 int mrcm_enable_timing(mrcm_ctx* c, int on) {
     if (!c) return MRCM_ERR_INVALID_ARG;
     if (on && !c->ev[0]) {
-        for (int k = 0; k < 2 * MRCM_PHASE_COUNT; ++k) TRYC(cudaEventCreate(&c->ev[k]));
+        for (int k = 0; k < 2 * MRCM_PHASE_COUNT * kMaxOcc; ++k) TRYC(cudaEventCreate(&c->ev[k]));
     }
     c->timing = on != 0;
     return MRCM_OK;
@@ -671,10 +750,12 @@ int mrcm_phase_times(mrcm_ctx* c, double* ms) {
     TRYC(cudaStreamSynchronize(c->stream));
     for (int p = 0; p < MRCM_PHASE_COUNT; ++p) {
         ms[p] = 0.0;
-        if (c->ev[0] && c->ev_used[p]) {
+        if (!c->ev[0]) continue;
+        for (int o = 0; o < c->ev_count[p]; ++o) {
             float t = 0.f;
-            TRYC(cudaEventElapsedTime(&t, c->ev[2 * p], c->ev[2 * p + 1]));
-            ms[p] = t;
+            const int slot = 2 * (p * kMaxOcc + o);
+            TRYC(cudaEventElapsedTime(&t, c->ev[slot], c->ev[slot + 1]));
+            ms[p] += t;
         }
     }
     return MRCM_OK;
@@ -683,7 +764,7 @@ int mrcm_phase_times(mrcm_ctx* c, double* ms) {
 void mrcm_destroy(mrcm_ctx* c) {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
-    for (int k = 0; k < 2 * MRCM_PHASE_COUNT; ++k)
+    for (int k = 0; k < 2 * MRCM_PHASE_COUNT * kMaxOcc; ++k)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
     for (void* p : c->allocs) cudaFree(p);
     delete c;

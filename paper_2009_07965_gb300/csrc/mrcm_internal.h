@@ -32,7 +32,6 @@ struct LeafDesc {
     long long zb_off;  // particular forward solve: n values
     long long R_off;   // node R (m x m) of the leaf
     long long r_off;   // node rbar / lambda (m values each, separate arrays)
-    long long fs_off;  // unused
 };
 
 // One internal tree node (a merge of two children).
@@ -63,6 +62,8 @@ struct DevView {
     int sx, sy, gx, gy;
     // inputs copied / derived
     const double* K;        // nx*ny
+    double* rx;             // nx*ny half-cell resistances hx / (2 K)
+    double* ry;             //                               hy / (2 K)
     double* seg_beta;       // nseg
     double* seg_D;          // nseg: |t| / (2 beta_t)
     double* cxL;            // (nx+1)*ny face coefficient seen from the lower cell
@@ -72,6 +73,8 @@ struct DevView {
     // segment geometry
     const int* seg_axis; const int* seg_line; const int* seg_lo; const int* seg_len;
     const int* seg_a; const int* seg_b; const int* seg_face_off;
+    const long long* seg_lam_a;   // offset in lam of segment t in the leaf on side a
+    const long long* seg_lam_b;   //                                   ... side b
     // leaves and tree
     const LeafDesc* leaves;
     const int* leaf_segs;
@@ -89,23 +92,97 @@ struct DevView {
     int* piv;
     double* X;
     double* xbar;
-    double* skel;       // one-sided skeleton fluxes: 2 per skeleton face
+    double* segP;       // refined interface unknowns P_t, U_t (high parts)
+    double* segU;
+    double* segP_lo;    // ... and low parts of the double-double state
+    double* segU_lo;
+    double* p_hi;       // refined cell pressures, double-double
+    double* p_lo;
+    double* rcell;      // cell residuals (refinement)
+    double* sadj;       // per leaf segment: right-hand side of its interface row
     double* red;        // reduction scratch (mean pressure)
+    unsigned long long* res_max;  // max |residual| per refinement step (double bits)
     int* status;        // device status word
 };
 
+#ifdef __CUDACC__
+// Global segment id of the skeleton face (axis, line, k): line is the face
+// index along the normal, k the cell index along the face.  The segment is
+// listed on the + side of the leaf below the line.
+__device__ __forceinline__ int skeleton_segment(const DevView& v, int axis, int line, int k) {
+    const int nlx = (v.nx + v.sx - 1) / v.sx;
+    int leaf, side, pos;
+    if (axis == 0) {
+        leaf = (line / v.sx - 1) + nlx * (k / v.sy);
+        side = 1;
+        pos = (k - v.leaves[leaf].j0) / v.gy;
+    } else {
+        leaf = (k / v.sx) + nlx * (line / v.sy - 1);
+        side = 3;
+        pos = (k - v.leaves[leaf].i0) / v.gx;
+    }
+    const LeafDesc& L = v.leaves[leaf];
+    return v.leaf_segs[L.seg_off + L.side_off[side] + pos];
+}
+
+// Double-double arithmetic: TwoSum (Knuth) and FMA-based TwoProd are
+// error-free; a value is the unevaluated sum h + l with |l| <= ulp(h)/2.
+struct DD {
+    double h, l;
+};
+__device__ __forceinline__ DD dd_two_sum(double a, double b) {
+    const double s = __dadd_rn(a, b);
+    const double bb = __dsub_rn(s, a);
+    const double e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
+    return {s, e};
+}
+__device__ __forceinline__ DD dd_two_prod(double a, double b) {
+    const double p = __dmul_rn(a, b);
+    return {p, __fma_rn(a, b, -p)};
+}
+__device__ __forceinline__ DD dd_add(DD x, DD y) {
+    const DD s = dd_two_sum(x.h, y.h);
+    return dd_two_sum(s.h, __dadd_rn(s.l, __dadd_rn(x.l, y.l)));
+}
+__device__ __forceinline__ DD dd_mul_d(DD x, double b) {
+    const DD p = dd_two_prod(x.h, b);
+    return dd_two_sum(p.h, __fma_rn(x.l, b, p.l));
+}
+__device__ __forceinline__ DD dd_neg(DD x) { return {-x.h, -x.l}; }
+__device__ __forceinline__ double dd_round(DD x) { return __dadd_rn(x.h, x.l); }
+
+// x-face (i, j) / y-face (i, j) lies on the skeleton
+__device__ __forceinline__ bool x_skeleton(const DevView& v, int i) {
+    return i > 0 && i < v.nx && i % v.sx == 0;
+}
+__device__ __forceinline__ bool y_skeleton(const DevView& v, int j) {
+    return j > 0 && j < v.ny && j % v.sy == 0;
+}
+#endif
+
 // ---- launchers (return cudaGetLastError() of the launch) -----------------
 cudaError_t launch_check_K(const DevView& v, cudaStream_t s);
+cudaError_t launch_cell_resist(const DevView& v, cudaStream_t s);
 cudaError_t launch_seg_beta(const DevView& v, cudaStream_t s);
 cudaError_t launch_face_coef(const DevView& v, cudaStream_t s);
 cudaError_t launch_leaf_build(const DevView& v, int max_m, cudaStream_t s);
+// particular solve: q and bc_val are the data; bc_val == nullptr means zero
+// external data; with_sadj subtracts the interface right-hand sides.
 cudaError_t launch_leaf_particular(const DevView& v, const double* q, const double* bc_val,
-                                   int max_m, cudaStream_t s);
-cudaError_t launch_leaf_final(const DevView& v, const double* q, const double* bc_val,
-                              double* p, double* Fx, double* Fy, int max_m, cudaStream_t s);
-cudaError_t launch_skeleton_fluxes(const DevView& v, double* Fx, double* Fy, double* iface,
-                                   cudaStream_t s);
-cudaError_t launch_mean_shift(const DevView& v, double* p, cudaStream_t s);
+                                   bool with_sadj, cudaStream_t s);
+// p = A^-1 (bbar + B lambda) per leaf into the double-double state
+// (p_hi, p_lo): set, or accumulate (double-double add of the correction).
+cudaError_t launch_leaf_pressure(const DevView& v, bool accumulate, cudaStream_t s);
+// interface unknowns from the two Robin data of each segment (set or add)
+cudaError_t launch_lam_to_PU(const DevView& v, bool accumulate, cudaStream_t s);
+// residual of the discrete equations in double-double; fills rcell, sadj
+cudaError_t launch_residual(const DevView& v, const double* q, const double* bc_val, int step,
+                            cudaStream_t s);
+// cell pressures and face fluxes from the double-double state; iface optional
+cudaError_t launch_face_fluxes(const DevView& v, const double* bc_val, double* p, double* Fx,
+                               double* Fy, double* iface, cudaStream_t s);
+// zero-mean shift of the state's p and P (all-Neumann problems)
+cudaError_t launch_mean_shift(const DevView& v, cudaStream_t s);
 cudaError_t launch_merge_build(const DevView& v, int first, int count, int max_g2, int max_m,
                                cudaStream_t s);
 cudaError_t launch_merge_up(const DevView& v, int first, int count, int max_g2, cudaStream_t s);

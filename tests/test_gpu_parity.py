@@ -3,7 +3,11 @@
 Tolerance: relative L2 <= 1e-10 in pressure and in each flux array (the
 FP64 target), on problems that span several leaves, ragged (truncated)
 leaves, both boundary-condition families, one-face segments (64 Robin
-responses per leaf) and per-node Robin-to-flux maps.
+responses per leaf) and per-node Robin-to-flux maps.  Both sides refine
+their solution with residuals of Eqs. 11.2-14.2 evaluated in double-double
+arithmetic, so both approximate the same discrete solution to near FP64
+accuracy even where the permeability contrast makes a plain FP64 solve
+accurate to only ~1e-6 in the fluxes.
 """
 import numpy as np
 import pytest
@@ -12,13 +16,18 @@ import inputs
 from oracle.fine import solve_fine
 from oracle.geometry import Decomposition
 from oracle.local import LeafProblem
-from oracle.mrcm import solve_mrcm
+from oracle.mrcm import solve_mrcm as _solve_mrcm
 from oracle.recursive import RecursiveMRCM
 from conftest import gpu_solve, rel
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-10
 KEYS = ("p", "Fx", "Fy", "Fa_x", "Fb_x", "Fa_y", "Fb_y")
+REFINE = 3
+
+
+def solve_mrcm(prob):
+    return _solve_mrcm(prob, refine=REFINE)
 
 
 def _compare(g, o, keys=KEYS, tol=TOL):
@@ -75,9 +84,14 @@ def _oracle_seg_key(dec, t):
 
 
 def test_node_maps_match_recursive_oracle(mrcm_lib):
+    import torch
     prob = inputs.darcy_problem(64, 48, sigma2=2.0, corr=0.1, seed=17, bc="left_right")
     g = gpu_solve(prob, want_iface=False)
     ctx = g["solver"].ctx
+    # node particular fluxes of the plain solve (refinement passes overwrite
+    # them with those of the correction data)
+    mrcm_lib.mrcm_set_refinement(ctx, 0)
+    g["solver"].solve(torch.from_numpy(prob.q).cuda(), torch.from_numpy(prob.bc_val).cuda())
     rm = RecursiveMRCM(prob)
     rm.solve()
     dec = rm.dec
@@ -168,6 +182,29 @@ def test_errors_are_reported(mrcm_lib):
     with pytest.raises(MrcmError) as e:
         Solver(K, sub=(16, 16), seg=(3, 4))
     assert e.value.code == -2            # SHAPE
+
+
+def test_refinement_converges(mrcm_lib):
+    import paper_2009_07965_gb300 as mr
+    import torch
+    prob = inputs.darcy_problem(256, 256, sigma2=4.0, corr=0.05, seed=2000, bc="quarter_five_spot")
+    s = mr.Solver(torch.from_numpy(prob.K).cuda(), sub=prob.sub, seg=prob.seg, alpha=prob.alpha,
+                  bc_type=prob.bc_type)
+    mr.mrcm_set_refinement(s.ctx, 3, check=True)
+    s.build_basis()
+    s.solve(torch.from_numpy(prob.q).cuda(), torch.from_numpy(prob.bc_val).cuda())
+    hist = mr.mrcm_residual_history(s.ctx)
+    assert len(hist) == 4
+    assert hist[-1] < 1e-13 and hist[-1] <= hist[0], hist
+    g = {k: v.cpu().numpy() for k, v in zip(("p", "Fx", "Fy"), (s.p, s.Fx, s.Fy))}
+    _compare(g, solve_mrcm(prob), keys=("p", "Fx", "Fy"))
+
+
+def test_square512_same_recipe_as_benchmark(mrcm_lib):
+    # the benchmark recipe (sigma^2 = 4, corr 0.05, quarter-five-spot) at
+    # 512^2: 1024 leaves, 10 levels, interface systems up to 2g = 256
+    prob = inputs.darcy_problem(512, 512, sigma2=4.0, corr=0.05, seed=2000, bc="quarter_five_spot")
+    _compare(gpu_solve(prob), solve_mrcm(prob))
 
 
 @pytest.mark.slow

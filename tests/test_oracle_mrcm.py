@@ -196,3 +196,28 @@ def test_error_falls_with_alpha():
                         np.concatenate([f["Fx"].ravel(), f["Fy"].ravel()])))
     ratios = np.array(errs[:-1]) / np.array(errs[1:])
     assert np.all(ratios > 5.0) and np.all(ratios < 20.0), errs
+
+
+@pytest.mark.parametrize("bc", BCS)
+def test_refinement_reaches_the_discrete_solution(bc):
+    # Iterative refinement with double-double residuals of Eqs. 11.2-14.2:
+    # the global system (O2) and the recursion (Algorithm 1) are different
+    # FP64 solvers whose plain results differ at high contrast; refined, both
+    # must give the same discrete solution to about one rounding unit, and
+    # the residual must fall to the double-double level.
+    prob = inputs.darcy_problem(96, 80, sigma2=4.0, corr=0.05, seed=77, bc=bc)
+    m0, r0 = solve_mrcm(prob), solve_recursive(prob)
+    m, r = solve_mrcm(prob, refine=3), solve_recursive(prob, refine=3)
+    assert m["refine_history"][-1] < 1e-24 and r["refine_history"][-1] < 1e-24
+    for key in ("p", "Fx", "Fy", "Fa_x", "Fb_y"):
+        assert rel(m[key], r[key]) < 1e-14, key
+        # the plain solves agree with the refined one only to their accuracy
+        assert rel(m0[key], m[key]) < 1e-8
+
+
+def test_refined_one_face_segments_equal_fine():
+    prob = inputs.darcy_problem(24, 20, sigma2=3.0, corr=0.2, seed=4, bc="quarter_five_spot",
+                                sub=(6, 5), seg=(1, 1), alpha=2.0)
+    f, m = solve_fine(prob), solve_mrcm(prob, refine=2)
+    for key in ("p", "Fx", "Fy"):
+        assert rel(m[key], f[key]) < 1e-11
