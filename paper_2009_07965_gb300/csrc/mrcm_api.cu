@@ -47,7 +47,7 @@ struct Plan {
     std::vector<Node> nodes;
     int root = -1, height = 0;
     std::vector<MergeDesc> merges;       // grouped by height (ascending)
-    std::vector<int> level_first, level_count, level_max_g2;  // index by height-1
+    std::vector<int> level_first, level_count, level_max_g2, level_max_m;  // index by height-1
     std::vector<int> node_map, gamma_segs;
     int max_m_leaf = 0, max_g2 = 0;
     // storage sizes (doubles / ints)
@@ -244,6 +244,7 @@ int make_plan(Plan& P) {
     P.level_first.assign(P.height, 0);
     P.level_count.assign(P.height, 0);
     P.level_max_g2.assign(P.height, 0);
+    P.level_max_m.assign(P.height, 0);
     for (int h = 1; h <= P.height; ++h) {
         P.level_first[h - 1] = (int)P.merges.size();
         P.level_count[h - 1] = (int)by_h[h].size();
@@ -277,6 +278,7 @@ int make_plan(Plan& P) {
             D.xb_off = P.nxb;  P.nxb += g2;
             P.merges.push_back(D);
             P.level_max_g2[h - 1] = std::max(P.level_max_g2[h - 1], (int)g2);
+            P.level_max_m[h - 1] = std::max(P.level_max_m[h - 1], (int)m);
             P.max_g2 = std::max(P.max_g2, (int)g2);
             // flop model: LU (2/3 N^3), X solve (2 N^2 m), R update (2 g m^2)
             const double N = (double)g2;
@@ -302,6 +304,7 @@ struct mrcm_ctx {
     int launches_build = 0, launches_solve = 0;
     bool timing = false;
     cudaEvent_t ev[2 * MRCM_PHASE_COUNT * (kMaxRefine + 2)] = {};
+    unsigned long long* amax_bits = nullptr;
     int ev_count[MRCM_PHASE_COUNT] = {};
     int refine_steps = 2;
     int refine_check = 0;
@@ -509,6 +512,11 @@ static int setup_impl(mrcm_ctx* c, const mrcm_grid* g, const double* K_dev, cons
     TRY(dev_alloc(c, &v.sadj, P.nr));
     TRY(dev_alloc(c, &v.res_max, kMaxRefine + 1));
     TRY(dev_alloc(c, &v.red, 1024));
+    {
+        int maxc = 1;
+        for (int n : P.level_count) maxc = std::max(maxc, n);
+        TRY(dev_alloc(c, &c->amax_bits, maxc));
+    }
     TRY(dev_alloc(c, &v.status, 4));
     TRYC(cudaMemcpyAsync(c->K, K_dev, sizeof(double) * ncell, cudaMemcpyDefault, c->stream));
     // the root's lambda has no entries; lambda of every other node is written
@@ -573,8 +581,7 @@ int mrcm_build_basis(mrcm_ctx* c) {
         PhaseScope ps(c, MRCM_PHASE_MERGE_BUILD);
         for (int h = 1; h <= P.height; ++h) {
             TRYC(launch_merge_build(v, P.level_first[h - 1], P.level_count[h - 1], P.level_max_g2[h - 1],
-                                    0, s));
-            ++launches;
+                                    P.level_max_m[h - 1], c->amax_bits, s, &launches));
         }
     }
     c->launches_build = launches;

@@ -183,8 +183,11 @@ cudaError_t launch_face_fluxes(const DevView& v, const double* bc_val, double* p
                                double* Fy, double* iface, cudaStream_t s);
 // zero-mean shift of the state's p and P (all-Neumann problems)
 cudaError_t launch_mean_shift(const DevView& v, cudaStream_t s);
+// one tree height of merges; amax_bits: scratch of `count` entries;
+// *launches is increased by the number of kernels launched
 cudaError_t launch_merge_build(const DevView& v, int first, int count, int max_g2, int max_m,
-                               cudaStream_t s);
+                               unsigned long long* amax_bits, cudaStream_t s, int* launches);
+bool merge_level_blocked(int count, int max_g2);
 cudaError_t launch_merge_up(const DevView& v, int first, int count, int max_g2, cudaStream_t s);
 cudaError_t launch_merge_down(const DevView& v, int first, int count, int max_g2, cudaStream_t s);
 
