@@ -13,14 +13,17 @@
 // the traces of all MMBFs of the leaf (coefficient-tracking remark, Section
 // 3.2); bbar carries the source and external boundary data (Eqs. addu, addp).
 //
-// Layout and mapping.  16 threads own one leaf (two leaves per warp); cells
-// are ordered x fastest, so A is banded with half-bandwidth w (leaf width).
-// A = L D L^T is factored right-looking over a circular window of w+2 band
-// rows in shared memory; each step also advances the multi-right-hand-side
-// forward solve Z = L^-1 B and accumulates R += z_k z_k^T / d_k, so no
-// column of L is read twice.  The multipliers L, 1/d and Z are written to
-// global memory for the solve phase.  Every FP64 instruction does useful
-// work on all 16 lanes except the pivot reciprocal.
+// Layout and mapping.  16 threads own one leaf (two leaves per warp, four
+// per CTA so that a 64 x 64-leaf grid fits in one wave); cells are ordered x
+// fastest, so A is banded with half-bandwidth w (leaf width).  A = L D L^T
+// is factored right-looking over a circular window of w+2 band rows in
+// shared memory; each step also advances the multi-right-hand-side forward
+// solve Z = L^-1 B and accumulates R += z_k z_k^T / d_k, so no column of L is
+// read twice.  The columns of B are taken in the order of their first
+// nonzero row, so the structurally zero upper part of Z is skipped and the
+// remaining work is spread evenly over the 16 lanes (a masked FP64 lane
+// costs as much as a busy one).  The multipliers L, 1/d and Z are written to
+// global memory for the solve phase.
 #include "mrcm_internal.h"
 
 namespace mrcm {
@@ -31,12 +34,15 @@ constexpr int kWin = kMaxLeafSide + 2;   // circular window rows
 template <int MMAX>
 struct LeafBuildSmem {
     double win[kWin][kMaxLeafSide + 1];  // win[row % (w+2)][o] = A[row][row - o]
-    double zw[kWin][MMAX];               // rows of Z being updated
-    double R[MMAX][MMAX];                // lower triangle of B^T A^-1 B
-    double W[MMAX];                      // sum of rho per segment
+    double zw[kWin][MMAX + 1];           // rows of Z being updated (ordered columns)
+    double R[MMAX][MMAX + 1];            // lower triangle of B^T A^-1 B (ordered)
+    double W[MMAX];                      // sum of rho per segment (ordered)
     double lcol[kMaxLeafSide];           // column k of L below the diagonal
-    double zk[MMAX];                     // row k of Z
-    double uk[MMAX];                     // row k of Z / d_k
+    double zk[MMAX];                     // row k of Z (ordered)
+    double uk[MMAX];                     // row k of Z / d_k (ordered)
+    int order[MMAX];                     // ordered column q -> local segment
+    int pos[MMAX];                       // local segment -> ordered column
+    int start[MMAX];                     // first row with a nonzero, per ordered column
 };
 
 // (row, col) of entry idx of a lower triangle stored row by row.
@@ -93,16 +99,27 @@ __device__ __forceinline__ void init_row(const DevView& v, const LeafDesc& L, Le
     }
     int sw, se, ss, sn;
     cell_robin_segments(v, L, i, j, sw, se, ss, sn);
-    int q = 0;
-    for (int s = t; s < m; s += kLeafThreads, ++q) {
+    int qq = 0;
+    for (int q = t; q < m; q += kLeafThreads, ++qq) {
+        const int s = S.order[q];
         double b = 0.0;
         if (s == sw) b = f.w_;
         if (s == se) b = f.e_;
         if (s == ss) b = f.s_;
         if (s == sn) b = f.n_;
-        S.zw[slot][s] = b;
-        Wacc[q] += b;
+        S.zw[slot][q] = b;
+        Wacc[qq] += b;
     }
+}
+
+// First row of the leaf whose cell touches local segment s (the first
+// nonzero of column s of B).
+__device__ __forceinline__ int segment_start_row(const DevView& v, const LeafDesc& L, int s) {
+    const int w = L.w, h = L.h;
+    if (L.side_off[3] >= 0 && s >= L.side_off[3]) return (h - 1) * w + (s - L.side_off[3]) * v.gx;
+    if (L.side_off[2] >= 0 && s >= L.side_off[2]) return (s - L.side_off[2]) * v.gx;
+    if (L.side_off[1] >= 0 && s >= L.side_off[1]) return (s - L.side_off[1]) * v.gy * w + w - 1;
+    return (s - L.side_off[0]) * v.gy * w;
 }
 
 template <int MMAX, int LPB>
@@ -119,20 +136,40 @@ leaf_build_kernel(DevView v) {
     const int w = L.w, n = L.w * L.h, m = L.m, W2 = L.w + 2;
     double* Lg = v.leafL + L.L_off;          // n x 16 multipliers
     double* Dg = Lg + (long long)n * kLeafThreads;   // n reciprocal pivots
-    double* Zg = v.leafZ + L.Z_off;          // n x m
+    double* Zg = v.leafZ + L.Z_off;          // n x m (local segment order)
+
+    // Columns of B ordered by their first nonzero row: column q of Z stays
+    // zero above start[q], so only the first c_k ordered columns take part
+    // in step k of the forward solve and of the R accumulation.
+    if (t == 0) {
+        for (int s = 0; s < m; ++s) {
+            const int st = segment_start_row(v, L, s);
+            int q = s;
+            while (q > 0 && S.start[q - 1] > st) {
+                S.start[q] = S.start[q - 1];
+                S.order[q] = S.order[q - 1];
+                --q;
+            }
+            S.start[q] = st;
+            S.order[q] = s;
+        }
+        for (int q = 0; q < m; ++q) S.pos[S.order[q]] = q;
+    }
+    __syncwarp(mask);
 
     constexpr int NQ = (MMAX + kLeafThreads - 1) / kLeafThreads;
     double Wacc[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) Wacc[q] = 0.0;
-    for (int idx = t; idx < m * m; idx += kLeafThreads) S.R[idx / m][idx % m] = 0.0;
+    for (int idx = t; idx < m * (MMAX + 1); idx += kLeafThreads) S.R[idx / (MMAX + 1)][idx % (MMAX + 1)] = 0.0;
     const int first = min(w, n - 1);
     for (int r = 0; r <= first; ++r) init_row(v, L, S, r, t, Wacc);
     __syncwarp(mask);
 
     bool bad_pivot = false;
-    const int ntri_m = m * (m + 1) / 2;
+    int ck = 0;                      // active ordered columns
     for (int k = 0; k < n; ++k) {
+        while (ck < m && S.start[ck] <= k) ++ck;
         // ---- phase A: pivot, multipliers, row k of Z -------------------------
         const int sk = k % W2;
         const double dk = S.win[sk][0];
@@ -145,13 +182,16 @@ leaf_build_kernel(DevView v) {
             Lg[(long long)k * kLeafThreads + t] = l;
         }
         if (t == 0) Dg[k] = rcp;
-        for (int s = t; s < m; s += kLeafThreads) {
-            const double z = S.zw[sk][s];
-            S.zk[s] = z;
-            S.uk[s] = z * rcp;
-            Zg[(long long)k * m + s] = z;
+        for (int q = t; q < ck; q += kLeafThreads) {
+            const double z = S.zw[sk][q];
+            S.zk[q] = z;
+            S.uk[q] = z * rcp;
         }
         __syncwarp(mask);
+        for (int s = t; s < m; s += kLeafThreads) {
+            const int q = S.pos[s];
+            Zg[(long long)k * m + s] = q < ck ? S.zk[q] : 0.0;
+        }
         // ---- phase B: trailing band update, Z update, R update, new row -----
         const int ntri_w = wk * (wk + 1) / 2;
         for (int idx = t; idx < ntri_w; idx += kLeafThreads) {
@@ -159,10 +199,12 @@ leaf_build_kernel(DevView v) {
             tri_index(idx, a, b);
             S.win[(k + 1 + a) % W2][a - b] -= S.lcol[a] * S.win[(k + 1 + b) % W2][1 + b];
         }
-        for (int s = t; s < m; s += kLeafThreads) {
-            const double z = S.zk[s];
-            for (int a = 0; a < wk; ++a) S.zw[(k + 1 + a) % W2][s] -= S.lcol[a] * z;
+        const int nz = wk * ck;
+        for (int idx = t; idx < nz; idx += kLeafThreads) {
+            const int a = idx / ck, q = idx - a * ck;
+            S.zw[(k + 1 + a) % W2][q] -= S.lcol[a] * S.zk[q];
         }
+        const int ntri_m = ck * (ck + 1) / 2;
         for (int idx = t; idx < ntri_m; idx += kLeafThreads) {
             int r, c;
             tri_index(idx, r, c);
@@ -173,13 +215,13 @@ leaf_build_kernel(DevView v) {
     }
     if (bad_pivot) atomicOr(v.status, kStatusSingular);
     {
-        int q = 0;
-        for (int s = t; s < m; s += kLeafThreads, ++q) S.W[s] = Wacc[q];
+        int qq = 0;
+        for (int q = t; q < m; q += kLeafThreads, ++qq) S.W[q] = Wacc[qq];
     }
     __syncwarp(mask);
     double* Rg = v.R + L.R_off;
     for (int idx = t; idx < m * m; idx += kLeafThreads) {
-        const int r = idx / m, c = idx % m;
+        const int r = S.pos[idx / m], c = S.pos[idx % m];
         double val = (r >= c) ? S.R[r][c] : S.R[c][r];
         if (r == c) val -= S.W[r];
         Rg[idx] = val;
@@ -374,7 +416,7 @@ __global__ void mean_subtract_kernel(DevView v, long long n) {
 
 cudaError_t launch_leaf_build(const DevView& v, int max_m, cudaStream_t s) {
     if (max_m <= 16) {
-        constexpr int LPB = 8;
+        constexpr int LPB = 4;
         const size_t sm = sizeof(LeafBuildSmem<16>) * LPB;
         cudaFuncSetAttribute(leaf_build_kernel<16, LPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         leaf_build_kernel<16, LPB><<<(v.nleaf + LPB - 1) / LPB, kLeafThreads * LPB, sm, s>>>(v);

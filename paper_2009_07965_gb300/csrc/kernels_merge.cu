@@ -133,7 +133,7 @@ __device__ __forceinline__ double block_max(double val, double* sv) {
 // shared through *s_rcp.
 template <int NT>
 __device__ __forceinline__ void lu_step(double* M, int n, int k, int cstart, int cend, double thresh, int* piv,
-                                        double* sv, int* si, double* s_rcp, bool& singular) {
+                                        double* dinv, double* sv, int* si, double* s_rcp, bool& singular) {
     const int tid = threadIdx.x;
     double best = -1.0;
     int bi = k;
@@ -160,6 +160,7 @@ __device__ __forceinline__ void lu_step(double* M, int n, int k, int cstart, int
         const double pivot = col[b];
         if (!(fabs(pivot) > thresh)) singular = true;
         *s_rcp = 1.0 / pivot;
+        dinv[k] = *s_rcp;
     }
     __syncthreads();
     const int p = si[0];
@@ -210,7 +211,7 @@ __global__ void __launch_bounds__(NT) merge_small_kernel(DevView v, int first) {
     const double thresh = 1e-14 * block_max<NT>(amax, sv);
     bool singular = false;
     for (int k = 0; k < g2; ++k)
-        lu_step<NT>(M, g2, k, (k / kNB) * kNB, g2, thresh, piv, sv, si, &s_rcp, singular);
+        lu_step<NT>(M, g2, k, (k / kNB) * kNB, g2, thresh, piv, v.udinv + D.xb_off, sv, si, &s_rcp, singular);
     if (singular && tid == 0) atomicOr(v.status, kStatusSingular);
     // X = -M^-1 C, one column per thread (forward with the exchanges, backward)
     for (int j = tid; j < m; j += NT) {
@@ -270,63 +271,144 @@ __global__ void __launch_bounds__(256) merge_assemble_kernel(DevView v, int firs
         atomicMax(amax_bits + (node - first), (unsigned long long)__double_as_longlong(amax));
 }
 
-// Panel factorisation of columns [k0, k0+NB) (rows k0..2g-1), one CTA per node.
+// Panel factorisation of columns [k0, k0+NB) (rows k0..2g-1), one CTA per
+// node; the panel is staged in shared memory when it fits (smem_rows).
 template <int NT>
 __global__ void __launch_bounds__(NT) lu_panel_kernel(DevView v, int first, int k0,
-                                                      const unsigned long long* amax_bits) {
+                                                      const unsigned long long* amax_bits, int smem_rows) {
+    extern __shared__ __align__(16) double Ps[];
     __shared__ double sv[NT / 32];
     __shared__ int si[NT / 32];
     __shared__ double s_rcp;
+    __shared__ int s_p;
     const MergeDesc D = v.merges[first + blockIdx.x];
     const int g2 = 2 * D.g;
     if (k0 >= g2) return;
-    const int kend = min(k0 + kNB, g2);
-    double* M = v.LU + D.LU_off;
+    const int nb = min(kNB, g2 - k0), rows = g2 - k0;
+    double* Mg = v.LU + D.LU_off;
     int* piv = v.piv + D.piv_off;
+    double* dinv = v.udinv + D.xb_off;
+    const int tid = threadIdx.x;
+    const bool staged = rows <= smem_rows;
+    double* P = staged ? Ps : Mg + (long long)k0 * g2 + k0;   // entry (i, c) at P[c * ld + i]
+    const int ld = staged ? rows : g2;
+    if (staged) {
+        for (int idx = tid; idx < rows * nb; idx += NT) {
+            const int i = idx % rows, c = idx / rows;
+            Ps[idx] = Mg[(long long)(k0 + c) * g2 + k0 + i];
+        }
+        __syncthreads();
+    }
     const double thresh = 1e-14 * __longlong_as_double((long long)amax_bits[blockIdx.x]);
     bool singular = false;
-    for (int k = k0; k < kend; ++k) lu_step<NT>(M, g2, k, k0, kend, thresh, piv, sv, si, &s_rcp, singular);
-    if (singular && threadIdx.x == 0) atomicOr(v.status, kStatusSingular);
+    for (int kk = 0; kk < nb; ++kk) {
+        double best = -1.0;
+        int bi = kk;
+        const double* col = P + (long long)kk * ld;
+        for (int i = kk + tid; i < rows; i += NT) {
+            const double a = fabs(col[i]);
+            if (a > best) { best = a; bi = i; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_down_sync(0xffffffffu, best, o);
+            const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+            if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+        }
+        if ((tid & 31) == 0) { sv[tid >> 5] = best; si[tid >> 5] = bi; }
+        __syncthreads();
+        if (tid == 0) {
+            double bv = sv[0];
+            int b = si[0];
+            for (int w = 1; w < NT / 32; ++w)
+                if (sv[w] > bv || (sv[w] == bv && si[w] < b)) { bv = sv[w]; b = si[w]; }
+            s_p = b;
+            piv[k0 + kk] = k0 + b;
+            const double pivot = col[b];
+            if (!(fabs(pivot) > thresh)) singular = true;
+            s_rcp = 1.0 / pivot;
+            dinv[k0 + kk] = s_rcp;
+        }
+        __syncthreads();
+        const int p = s_p;
+        if (p != kk && tid < nb) {                       // exchange within the panel
+            double* cc = P + (long long)tid * ld;
+            const double a = cc[kk];
+            cc[kk] = cc[p];
+            cc[p] = a;
+        }
+        __syncthreads();
+        const double rcp = s_rcp;
+        for (int i = kk + 1 + tid; i < rows; i += NT) {  // multipliers and rank-1 update
+            const double l = col[i] * rcp;
+            P[(long long)kk * ld + i] = l;
+            for (int c = kk + 1; c < nb; ++c) P[(long long)c * ld + i] -= l * P[(long long)c * ld + kk];
+        }
+        __syncthreads();
+    }
+    if (singular && tid == 0) atomicOr(v.status, kStatusSingular);
+    if (staged) {
+        for (int idx = tid; idx < rows * nb; idx += NT) {
+            const int i = idx % rows, c = idx / rows;
+            Mg[(long long)(k0 + c) * g2 + k0 + i] = Ps[idx];
+        }
+    }
 }
 
-// Block row of U: apply the panel's exchanges to columns [kend, 2g) and
-// solve U12 = L11^-1 A12; one thread per column.
-__global__ void __launch_bounds__(64) lu_trsm_kernel(DevView v, int first, int k0) {
+// Block row of U: the panel's exchanges applied to columns [kend, 2g) (as one
+// composed permutation of the touched rows), then U12 = L11^-1 A12 with one
+// warp per column (lane r holds row k0 + r).
+constexpr int kTrsmWarps = 8;
+__global__ void __launch_bounds__(32 * kTrsmWarps) lu_trsm_kernel(DevView v, int first, int k0) {
     __shared__ double L11[kNB][kNB + 1];
-    __shared__ int pv[kNB];
+    __shared__ int rows_touched[2 * kNB];
+    __shared__ int src_row[2 * kNB];
+    __shared__ int n_touched;
     const MergeDesc D = v.merges[first + blockIdx.x];
     const int g2 = 2 * D.g;
     const int kend = min(k0 + kNB, g2);
-    const int j = kend + blockIdx.y * 64 + threadIdx.x;
-    if (kend >= g2 || kend + blockIdx.y * 64 >= g2) return;   // uniform per CTA
+    if (kend >= g2 || kend + (int)blockIdx.y * kTrsmWarps >= g2) return;   // uniform per CTA
     double* M = v.LU + D.LU_off;
+    const int* piv = v.piv + D.piv_off;
     const int nb = kend - k0;
-    for (int idx = threadIdx.x; idx < kNB * kNB; idx += 64) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int idx = tid; idx < kNB * kNB; idx += 32 * kTrsmWarps) {
         const int r = idx % kNB, c = idx / kNB;
         L11[r][c] = (r < nb && c < nb) ? M[(long long)(k0 + c) * g2 + k0 + r] : 0.0;
     }
-    for (int idx = threadIdx.x; idx < nb; idx += 64) pv[idx] = v.piv[D.piv_off + k0 + idx];
+    if (tid == 0) {
+        // rows touched by the exchanges and, after all of them, the original
+        // row whose value each touched row holds
+        int n = 0;
+        for (int c = 0; c < nb; ++c) { rows_touched[n] = k0 + c; src_row[n] = k0 + c; ++n; }
+        for (int c = 0; c < nb; ++c) {
+            const int p = piv[k0 + c];
+            int ip = -1;
+            for (int q = 0; q < n; ++q) if (rows_touched[q] == p) ip = q;
+            if (ip < 0) { rows_touched[n] = p; src_row[n] = p; ip = n; ++n; }
+            const int t = src_row[c];
+            src_row[c] = src_row[ip];
+            src_row[ip] = t;
+        }
+        n_touched = n;
+    }
     __syncthreads();
+    const int j = kend + blockIdx.y * kTrsmWarps + warp;
     if (j >= g2) return;
     double* col = M + (long long)j * g2;
+    const int nt = n_touched;
+    double g0 = lane < nt ? col[src_row[lane]] : 0.0;
+    double g1 = lane + 32 < nt ? col[src_row[lane + 32]] : 0.0;
+    __syncwarp();
+    if (lane < nt) col[rows_touched[lane]] = g0;
+    if (lane + 32 < nt) col[rows_touched[lane + 32]] = g1;
+    __syncwarp();
+    double u = lane < nb ? col[k0 + lane] : 0.0;
     for (int c = 0; c < nb; ++c) {
-        const int p = pv[c];
-        if (p != k0 + c) {
-            const double a = col[k0 + c];
-            col[k0 + c] = col[p];
-            col[p] = a;
-        }
+        const double xc = __shfl_sync(0xffffffffu, u, c);
+        if (lane > c && lane < nb) u -= L11[lane][c] * xc;
     }
-    double u[kNB];
-#pragma unroll
-    for (int r = 0; r < kNB; ++r) u[r] = r < nb ? col[k0 + r] : 0.0;
-#pragma unroll
-    for (int c = 0; c < kNB; ++c)
-#pragma unroll
-        for (int r = c + 1; r < kNB; ++r) u[r] -= L11[r][c] * u[c];
-#pragma unroll
-    for (int r = 0; r < kNB; ++r)
-        if (r < nb) col[k0 + r] = u[r];
+    if (lane < nb) col[k0 + lane] = u;
 }
 
 // Trailing update A22 -= L21 U12 on kGemmTile^2 tiles; 256 threads, 4x4 each.
@@ -452,16 +534,19 @@ __global__ void __launch_bounds__(256) merge_rupdate_kernel(DevView v, int first
 
 // ---------------------------------------------------------------------------
 // Solve phase, bottom-up: xbar = -M^-1 [rbar^a_gamma; rbar^b_gamma] and the
-// node's particular fluxes (Eqs. particular.1-2).
+// node's particular fluxes (Eqs. particular.1-2).  Blocked triangular
+// solves: warp 0 solves each 32 x 32 diagonal block with shuffles, the CTA
+// updates the remaining rows (a matrix-vector product per block).
 template <int NT>
 __global__ void __launch_bounds__(NT) merge_up_kernel(DevView v, int first) {
     extern __shared__ __align__(16) double rhs[];
     const MergeDesc D = v.merges[first + blockIdx.x];
     const NodeRefs N = node_refs(v, D);
     const int g = N.g, g2 = N.g2, m = N.m, o1 = N.o1;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const double* M = v.LU + D.LU_off;
     const int* piv = v.piv + D.piv_off;
+    const double* dinv = v.udinv + D.xb_off;
     const double* rb1 = v.rbar + D.r1_off;
     const double* rb2 = v.rbar + D.r2_off;
     for (int r = tid; r < g2; r += NT) rhs[r] = -(r < g ? rb1[N.gpos1[r]] : rb2[N.gpos2[r - g]]);
@@ -472,74 +557,111 @@ __global__ void __launch_bounds__(NT) merge_up_kernel(DevView v, int first) {
         rhs[0] = 0.0;
     }
     __syncthreads();
+    // forward: per panel, its exchanges, the unit lower diagonal block, then
+    // the rows below
     for (int k0 = 0; k0 < g2; k0 += kNB) {
-        const int kend = min(k0 + kNB, g2);
-        if (tid == 0) {
-            for (int k = k0; k < kend; ++k) {
-                const int p = piv[k];
-                if (p != k) { const double a = rhs[p]; rhs[p] = rhs[k]; rhs[k] = a; }
+        const int nb = min(kNB, g2 - k0);
+        if (warp == 0) {
+            if (lane == 0) {
+                for (int k = k0; k < k0 + nb; ++k) {
+                    const int p = piv[k];
+                    if (p != k) { const double a = rhs[p]; rhs[p] = rhs[k]; rhs[k] = a; }
+                }
             }
+            __syncwarp();
+            double val = lane < nb ? rhs[k0 + lane] : 0.0;
+            for (int c = 0; c < nb; ++c) {
+                const double xc = __shfl_sync(0xffffffffu, val, c);
+                if (lane > c && lane < nb) val -= M[(long long)(k0 + c) * g2 + k0 + lane] * xc;
+            }
+            if (lane < nb) rhs[k0 + lane] = val;
         }
         __syncthreads();
-        for (int k = k0; k < kend; ++k) {
-            const double xk = rhs[k];
-            const double* ck = M + (long long)k * g2;
-            for (int i = k + 1 + tid; i < g2; i += NT) rhs[i] -= ck[i] * xk;
-            __syncthreads();
+        for (int i = k0 + nb + tid; i < g2; i += NT) {
+            double acc = 0.0;
+            for (int c = 0; c < nb; ++c) acc += M[(long long)(k0 + c) * g2 + i] * rhs[k0 + c];
+            rhs[i] -= acc;
         }
+        __syncthreads();
     }
-    for (int k = g2 - 1; k >= 0; --k) {
-        const double* ck = M + (long long)k * g2;
-        if (tid == 0) rhs[k] /= ck[k];
+    // backward: U with the stored reciprocals of its diagonal, blocks from
+    // the bottom
+    for (int blk = (g2 - 1) / kNB; blk >= 0; --blk) {
+        const int k0 = blk * kNB, nb = min(kNB, g2 - k0);
+        if (warp == 0) {
+            double val = lane < nb ? rhs[k0 + lane] : 0.0;
+            for (int c = nb - 1; c >= 0; --c) {
+                if (lane == c) val *= dinv[k0 + c];
+                const double xc = __shfl_sync(0xffffffffu, val, c);
+                if (lane < c) val -= M[(long long)(k0 + c) * g2 + k0 + lane] * xc;
+            }
+            if (lane < nb) rhs[k0 + lane] = val;
+        }
         __syncthreads();
-        const double xk = rhs[k];
-        for (int i = tid; i < k; i += NT) rhs[i] -= ck[i] * xk;
+        for (int i = tid; i < k0; i += NT) {
+            double acc = 0.0;
+            for (int c = 0; c < nb; ++c) acc += M[(long long)(k0 + c) * g2 + i] * rhs[k0 + c];
+            rhs[i] -= acc;
+        }
         __syncthreads();
     }
     double* xb = v.xbar + D.xb_off;
     for (int r = tid; r < g2; r += NT) xb[r] = rhs[r];
+    // rbar of the node: one warp per output, lanes split the gamma sum
     double* rbp = v.rbar + D.r_off;
-    for (int i = tid; i < m; i += NT) {
-        double acc;
-        if (i < o1) {
-            const double* row = N.R1 + N.opos1[i] * N.m1;
-            acc = rb1[N.opos1[i]];
-            for (int k = 0; k < g; ++k) acc += row[N.gpos1[k]] * rhs[k];
-        } else {
-            const double* row = N.R2 + N.opos2[i - o1] * N.m2;
-            acc = rb2[N.opos2[i - o1]];
-            for (int k = 0; k < g; ++k) acc += row[N.gpos2[k]] * rhs[g + k];
-        }
-        rbp[i] = acc;
+    for (int i = warp; i < m; i += NT / 32) {
+        const bool first_child = i < o1;
+        const double* row = first_child ? N.R1 + N.opos1[i] * N.m1 : N.R2 + N.opos2[i - o1] * N.m2;
+        const int* gpos = first_child ? N.gpos1 : N.gpos2;
+        const double* x = first_child ? rhs : rhs + g;
+        double acc = 0.0;
+        for (int k = lane; k < g; k += 32) acc += row[gpos[k]] * x[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) acc += first_child ? rb1[N.opos1[i]] : rb2[N.opos2[i - o1]];
+        if (lane == 0) rbp[i] = acc;
     }
 }
 
 // Solve phase, top-down: lambda_gamma = X lambda_o + xbar, scattered into the
-// children's Robin data together with the node's own outer data.
-template <int NT>
-__global__ void __launch_bounds__(NT) merge_down_kernel(DevView v, int first) {
+// children's Robin data together with the node's own outer data.  A CTA
+// covers 64 rows of gamma; four thread groups split the sum over the outer
+// segments.
+constexpr int kDownRows = 64;
+__global__ void __launch_bounds__(256) merge_down_kernel(DevView v, int first) {
+    __shared__ double part[4][kDownRows];
     const MergeDesc D = v.merges[first + blockIdx.x];
     const NodeRefs N = node_refs(v, D);
     const int g = N.g, g2 = N.g2, m = N.m, o1 = N.o1;
-    const int tid = threadIdx.x;
+    const int r0 = blockIdx.y * kDownRows;
+    if (r0 >= g2) return;                                // uniform per CTA
+    const int tid = threadIdx.x, rl = tid % kDownRows, grp = tid / kDownRows;
     const double* lam_o = v.lam + D.r_off;
     const double* X = v.X + D.X_off;
-    const double* xb = v.xbar + D.xb_off;
     double* l1 = v.lam + D.r1_off;
     double* l2 = v.lam + D.r2_off;
-    for (int r = tid; r < g2; r += NT) {
-        double acc = xb[r];
-        for (int j = 0; j < m; ++j) acc += X[(long long)j * g2 + r] * lam_o[j];
-        if (r < g) l1[N.gpos1[r]] = acc;
-        else l2[N.gpos2[r - g]] = acc;
+    const int r = r0 + rl;
+    double acc = 0.0;
+    if (r < g2)
+        for (int j = grp; j < m; j += 4) acc += X[(long long)j * g2 + r] * lam_o[j];
+    part[grp][rl] = acc;
+    __syncthreads();
+    if (grp == 0 && r < g2) {
+        const double lg = v.xbar[D.xb_off + r] + ((part[0][rl] + part[1][rl]) + (part[2][rl] + part[3][rl]));
+        if (r < g) l1[N.gpos1[r]] = lg;
+        else l2[N.gpos2[r - g]] = lg;
     }
-    for (int j = tid; j < m; j += NT) {
-        if (j < o1) l1[N.opos1[j]] = lam_o[j];
-        else l2[N.opos2[j - o1]] = lam_o[j];
+    if (blockIdx.y == 0) {
+        for (int j = tid; j < m; j += 256) {
+            if (j < o1) l1[N.opos1[j]] = lam_o[j];
+            else l2[N.opos2[j - o1]] = lam_o[j];
+        }
     }
 }
 
 constexpr int kMergeThreads = 256;
+constexpr int kPanelThreads = 512;
+constexpr int kPanelSmemBytes = 200 * 1024;
 constexpr int kSmemG2 = 128;          // fused path: M in shared memory up to 128 x 128
 constexpr int kBlockedBelow = 304;    // levels with fewer nodes take the blocked path
 
@@ -570,13 +692,20 @@ cudaError_t launch_merge_build(const DevView& v, int first, int count, int max_g
         ++*launches;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
+    const int smem_rows = kPanelSmemBytes / (kNB * (int)sizeof(double));
+    e = cudaFuncSetAttribute(lu_panel_kernel<kPanelThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kPanelSmemBytes);
+    if (e != cudaSuccess) return e;
     for (int k0 = 0; k0 < max_g2; k0 += kNB) {
-        lu_panel_kernel<kMergeThreads><<<count, kMergeThreads, 0, s>>>(v, first, k0, amax_bits);
+        const int rows = max_g2 - k0;
+        const size_t psm = rows <= smem_rows ? (size_t)rows * kNB * sizeof(double) : 0;
+        lu_panel_kernel<kPanelThreads><<<count, kPanelThreads, psm, s>>>(v, first, k0, amax_bits,
+                                                                          psm ? smem_rows : 0);
         ++*launches;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         const int rest = max_g2 - min(k0 + kNB, max_g2);
         if (rest <= 0) break;
-        lu_trsm_kernel<<<dim3(count, (rest + 63) / 64), 64, 0, s>>>(v, first, k0);
+        lu_trsm_kernel<<<dim3(count, (rest + kTrsmWarps - 1) / kTrsmWarps), 32 * kTrsmWarps, 0, s>>>(v, first, k0);
         ++*launches;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         const int tiles = (rest + kGemmTile - 1) / kGemmTile;
@@ -605,9 +734,9 @@ cudaError_t launch_merge_up(const DevView& v, int first, int count, int max_g2, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_merge_down(const DevView& v, int first, int count, int, cudaStream_t s) {
+cudaError_t launch_merge_down(const DevView& v, int first, int count, int max_g2, cudaStream_t s) {
     if (count == 0) return cudaSuccess;
-    merge_down_kernel<kMergeThreads><<<count, kMergeThreads, 0, s>>>(v, first);
+    merge_down_kernel<<<dim3(count, (max_g2 + kDownRows - 1) / kDownRows), 256, 0, s>>>(v, first);
     return cudaGetLastError();
 }
 

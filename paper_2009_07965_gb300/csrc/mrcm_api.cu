@@ -215,13 +215,26 @@ int make_plan(Plan& P) {
         L.R_off = P.node_R_off[id];
         L.r_off = P.node_r_off[id];
         // flop model of the leaf kernel: LDL^T band steps, forward solve of
-        // the m Robin columns, SYRK of the lower triangle (FMA = 2 flops)
+        // the Robin columns from their first nonzero row on, SYRK of the
+        // lower triangle of the active columns (FMA = 2 flops)
+        std::vector<int> starts;
+        for (int s = 0; s < L.m; ++s) {
+            int st;
+            if (L.side_off[3] >= 0 && s >= L.side_off[3]) st = (L.h - 1) * L.w + (s - L.side_off[3]) * P.gx;
+            else if (L.side_off[2] >= 0 && s >= L.side_off[2]) st = (s - L.side_off[2]) * P.gx;
+            else if (L.side_off[1] >= 0 && s >= L.side_off[1]) st = (s - L.side_off[1]) * P.gy * L.w + L.w - 1;
+            else st = (s - L.side_off[0]) * P.gy * L.w;
+            starts.push_back(st);
+        }
+        std::sort(starts.begin(), starts.end());
         long long f = 0;
+        int ck = 0;
         for (long long k = 0; k < n; ++k) {
+            while (ck < L.m && starts[ck] <= k) ++ck;
             const long long wk = std::min<long long>(L.w, n - 1 - k);
             f += wk + wk * (wk + 1);                  // multipliers + trailing update
-            f += 2 * wk * L.m;                        // Z update
-            f += L.m + (long long)L.m * (L.m + 1);    // scaling + R update
+            f += 2 * wk * ck;                         // Z update
+            f += ck + (long long)ck * (ck + 1);       // scaling + R update
         }
         P.leaf_flops += f;
         // solve phase per leaf: forward sweep, Z^T y, Z lambda, backward sweep
@@ -502,6 +515,7 @@ static int setup_impl(mrcm_ctx* c, const mrcm_grid* g, const double* K_dev, cons
     TRY(dev_alloc(c, &v.piv, P.npiv));
     TRY(dev_alloc(c, &v.X, P.nX));
     TRY(dev_alloc(c, &v.xbar, P.nxb));
+    TRY(dev_alloc(c, &v.udinv, P.nxb));
     TRY(dev_alloc(c, &v.segP, P.nseg));
     TRY(dev_alloc(c, &v.segU, P.nseg));
     TRY(dev_alloc(c, &v.segP_lo, P.nseg));

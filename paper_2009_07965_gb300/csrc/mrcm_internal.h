@@ -92,6 +92,7 @@ struct DevView {
     int* piv;
     double* X;
     double* xbar;
+    double* udinv;      // reciprocals of the U diagonal per merge (xb_off layout)
     double* segP;       // refined interface unknowns P_t, U_t (high parts)
     double* segU;
     double* segP_lo;    // ... and low parts of the double-double state
