@@ -279,17 +279,24 @@ leaf_particular_kernel(DevView v, const double* __restrict__ q, const double* __
     const double* Zg = v.leafZ + L.Z_off;
     double* zb = v.leafzb + L.zb_off;
 
-    // forward sweep zbar = L^-1 bbar (unit lower band)
-    const int first = min(w, n - 1);
-    for (int r = t; r <= first; r += kLeafThreads) S.buf[r % W2] = particular_rhs(v, L, q, bc_val, r);
+    // forward sweep zbar = L^-1 bbar (unit lower band); the right-hand side
+    // is formed for all rows first, and each step's multiplier is loaded one
+    // step ahead so that no global load sits on the sequential chain
+    for (int r = t; r < n; r += kLeafThreads) S.y[r] = particular_rhs(v, L, q, bc_val, r);
     __syncwarp(mask);
+    const int first = min(w, n - 1);
+    for (int r = t; r <= first; r += kLeafThreads) S.buf[r % W2] = S.y[r];
+    __syncwarp(mask);
+    double lnext = (t < min(w, n - 1)) ? Lg[t] : 0.0;
     for (int k = 0; k < n; ++k) {
+        const double lk = lnext;
+        if (k + 1 < n && t < min(w, n - 2 - k)) lnext = Lg[(long long)(k + 1) * kLeafThreads + t];
         const double zk = S.buf[k % W2];
         const int wk = min(w, n - 1 - k);
-        if (t < wk) S.buf[(k + 1 + t) % W2] -= Lg[(long long)k * kLeafThreads + t] * zk;
+        if (t < wk) S.buf[(k + 1 + t) % W2] -= lk * zk;
         if (t == 0) {
             zb[k] = zk;
-            if (k + w + 1 < n) S.buf[(k + w + 1) % W2] = particular_rhs(v, L, q, bc_val, k + w + 1);
+            if (k + w + 1 < n) S.buf[(k + w + 1) % W2] = S.y[k + w + 1];
         }
         __syncwarp(mask);
     }
@@ -336,16 +343,20 @@ leaf_pressure_kernel(DevView v, bool accumulate) {
         S.y[k] = acc * Dg[k];
     }
     __syncwarp(mask);
-    // backward sweep L^T p = y, right-looking from the last row
+    // backward sweep L^T p = y, right-looking from the last row; the
+    // multiplier of each step is loaded one step ahead
     const int first = min(w, n - 1);
     for (int r = t; r <= first; r += kLeafThreads) S.buf[(n - 1 - r) % W2] = S.y[n - 1 - r];
     __syncwarp(mask);
+    double lnext = (t < min(w, n - 1)) ? Lg[(long long)(n - 2 - t) * kLeafThreads + t] : 0.0;
     for (int k = n - 1; k >= 0; --k) {
+        const double lk = lnext;
+        if (k >= 1 && t < min(w, k - 1)) lnext = Lg[(long long)(k - 2 - t) * kLeafThreads + t];
         const double pk = S.buf[k % W2];
         const int wk = min(w, k);
         if (t < wk) {
             const int i = k - 1 - t;   // row of L^T: entry L[k][i] = multiplier (i, k - i - 1)
-            S.buf[i % W2] -= Lg[(long long)i * kLeafThreads + t] * pk;
+            S.buf[i % W2] -= lk * pk;
         }
         if (t == 0) {
             S.y[k] = pk;   // y[k] is no longer needed: keep p in its place

@@ -29,11 +29,20 @@
 // solve therefore takes the panels in order: apply the panel's exchanges,
 // then eliminate its columns.  X is column-major too (2g x m).
 //
+// The build also forms W = M^-1 explicitly; X = -W C then exploits the block
+// structure of C, and every solve pass is a pair of matrix-vector products
+// per node instead of two triangular solves: M is symmetric (R^a, R^b
+// symmetric, D diagonal), so blockdiag(R_og) xbar = -C^T M^-1 rbar_gamma
+// = X^T rbar_gamma, giving the up-sweep rbar = rbar_o + X^T rbar_gamma, and
+// the down-sweep lambda_gamma = X lambda_o + W (-rbar_gamma).  Iterative
+// refinement (kernels_refine.cu) absorbs the different rounding of an
+// inverse-based solve.
+//
 // Two launch shapes.  Levels with many nodes: one CTA per node, M in shared
 // memory (merge_small_kernel).  Levels with few, large nodes: a blocked
 // right-looking LU across many CTAs -- a panel kernel (NB columns, one CTA
 // per node), a TRSM kernel for the block row of U and a tiled FP64 GEMM for
-// the trailing update -- then X by column blocks and R by output tiles.
+// the trailing update -- then W by column blocks, X and R by output tiles.
 #include "mrcm_internal.h"
 
 namespace mrcm {
@@ -207,15 +216,17 @@ __global__ void __launch_bounds__(NT) merge_small_kernel(DevView v, int first) {
         M[idx] = val;
         amax = fmax(amax, fabs(val));
     }
-    for (int idx = tid; idx < g2 * m; idx += NT) X[idx] = -c_entry(N, idx % g2, idx / g2);
     const double thresh = 1e-14 * block_max<NT>(amax, sv);
     bool singular = false;
     for (int k = 0; k < g2; ++k)
         lu_step<NT>(M, g2, k, (k / kNB) * kNB, g2, thresh, piv, v.udinv + D.xb_off, sv, si, &s_rcp, singular);
     if (singular && tid == 0) atomicOr(v.status, kStatusSingular);
-    // X = -M^-1 C, one column per thread (forward with the exchanges, backward)
-    for (int j = tid; j < m; j += NT) {
-        double* x = X + (long long)j * g2;
+    // W = M^-1, one column per thread (per panel: exchanges, unit lower
+    // columns; then the upper triangle)
+    double* Wg = v.W + D.LU_off;
+    for (int j = tid; j < g2; j += NT) {
+        double* x = Wg + (long long)j * g2;
+        for (int i = 0; i < g2; ++i) x[i] = (i == j) ? 1.0 : 0.0;
         for (int k0 = 0; k0 < g2; k0 += kNB) {
             const int kend = min(k0 + kNB, g2);
             for (int k = k0; k < kend; ++k) {
@@ -236,34 +247,41 @@ __global__ void __launch_bounds__(NT) merge_small_kernel(DevView v, int first) {
         }
     }
     __syncthreads();
+    // X = -W C: C is block diagonal, so column j uses one half of W
+    for (int idx = tid; idx < g2 * m; idx += NT) {
+        const int r = idx % g2, j = idx / g2;
+        double acc = 0.0;
+        if (j < N.o1) {
+            const double* crow = N.R1 + N.opos1[j];
+            for (int k = 0; k < N.g; ++k) acc += Wg[(long long)k * g2 + r] * crow[N.gpos1[k] * N.m1];
+        } else {
+            const double* crow = N.R2 + N.opos2[j - N.o1];
+            for (int k = 0; k < N.g; ++k)
+                acc += Wg[(long long)(N.g + k) * g2 + r] * crow[N.gpos2[k] * N.m2];
+        }
+        X[idx] = -acc;
+    }
+    __syncthreads();
     double* Rp = v.R + D.R_off;
     for (int idx = tid; idx < m * m; idx += NT) Rp[idx] = r_entry(N, X, idx / m, idx % m);
-    double* Mg = v.LU + D.LU_off;
-    for (int idx = tid; idx < g2 * g2; idx += NT) Mg[idx] = M[idx];
 }
 
 // ---------------------------------------------------------------------------
 // Blocked path.
-// Assembly of M (column-major, pinned rows applied) and of -C into X.
+// Assembly of M (column-major, pinned rows applied).
 __global__ void __launch_bounds__(256) merge_assemble_kernel(DevView v, int first, unsigned long long* amax_bits) {
     const int node = first + blockIdx.x;
     const MergeDesc D = v.merges[node];
     const NodeRefs N = node_refs(v, D);
     const int g2 = N.g2, m = N.m;
     double* M = v.LU + D.LU_off;
-    double* X = v.X + D.X_off;
-    const long long nM = (long long)g2 * g2, nX = (long long)g2 * m;
+    const long long nM = (long long)g2 * g2;
     double amax = 0.0;
-    for (long long idx = blockIdx.y * 256LL + threadIdx.x; idx < nM + nX; idx += (long long)gridDim.y * 256) {
-        if (idx < nM) {
-            const int r = (int)(idx % g2), c = (int)(idx / g2);
-            const double val = m_entry_pinned(v, D, N, r, c);
-            M[idx] = val;
-            amax = fmax(amax, fabs(val));
-        } else {
-            const long long x = idx - nM;
-            X[x] = -c_entry(N, (int)(x % g2), (int)(x / g2));
-        }
+    for (long long idx = blockIdx.y * 256LL + threadIdx.x; idx < nM; idx += (long long)gridDim.y * 256) {
+        const int r = (int)(idx % g2), c = (int)(idx / g2);
+        const double val = m_entry_pinned(v, D, N, r, c);
+        M[idx] = val;
+        amax = fmax(amax, fabs(val));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
@@ -277,10 +295,10 @@ template <int NT>
 __global__ void __launch_bounds__(NT) lu_panel_kernel(DevView v, int first, int k0,
                                                       const unsigned long long* amax_bits, int smem_rows) {
     extern __shared__ __align__(16) double Ps[];
-    __shared__ double sv[NT / 32];
+    __shared__ unsigned long long skey[NT / 32];
     __shared__ int si[NT / 32];
-    __shared__ double s_rcp;
     __shared__ int s_p;
+    __shared__ double prow[kNB], krow[kNB];
     const MergeDesc D = v.merges[first + blockIdx.x];
     const int g2 = 2 * D.g;
     if (k0 >= g2) return;
@@ -302,47 +320,63 @@ __global__ void __launch_bounds__(NT) lu_panel_kernel(DevView v, int first, int 
     const double thresh = 1e-14 * __longlong_as_double((long long)amax_bits[blockIdx.x]);
     bool singular = false;
     for (int kk = 0; kk < nb; ++kk) {
-        double best = -1.0;
+        // pivot search on the bit patterns of |a| (ordered like the values)
+        unsigned long long best = 0ull;
         int bi = kk;
         const double* col = P + (long long)kk * ld;
         for (int i = kk + tid; i < rows; i += NT) {
-            const double a = fabs(col[i]);
-            if (a > best) { best = a; bi = i; }
+            const unsigned long long a = (unsigned long long)__double_as_longlong(col[i]) & 0x7fffffffffffffffull;
+            if (a > best || (a == best && i < bi)) { best = a; bi = i; }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            const double ov = __shfl_down_sync(0xffffffffu, best, o);
+            const unsigned long long ov = __shfl_down_sync(0xffffffffu, best, o);
             const int oi = __shfl_down_sync(0xffffffffu, bi, o);
             if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
         }
-        if ((tid & 31) == 0) { sv[tid >> 5] = best; si[tid >> 5] = bi; }
+        if ((tid & 31) == 0) { skey[tid >> 5] = best; si[tid >> 5] = bi; }
         __syncthreads();
-        if (tid == 0) {
-            double bv = sv[0];
-            int b = si[0];
-            for (int w = 1; w < NT / 32; ++w)
-                if (sv[w] > bv || (sv[w] == bv && si[w] < b)) { bv = sv[w]; b = si[w]; }
-            s_p = b;
-            piv[k0 + kk] = k0 + b;
-            const double pivot = col[b];
-            if (!(fabs(pivot) > thresh)) singular = true;
-            s_rcp = 1.0 / pivot;
-            dinv[k0 + kk] = s_rcp;
+        if (tid < 32) {
+            unsigned long long kv = tid < NT / 32 ? skey[tid] : 0ull;
+            int ki = tid < NT / 32 ? si[tid] : 0x7fffffff;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long ov = __shfl_down_sync(0xffffffffu, kv, o);
+                const int oi = __shfl_down_sync(0xffffffffu, ki, o);
+                if (ov > kv || (ov == kv && oi < ki)) { kv = ov; ki = oi; }
+            }
+            ki = __shfl_sync(0xffffffffu, ki, 0);
+            // the pivot row (old row p) and the old row kk, all panel columns
+            if (tid < nb) {
+                prow[tid] = P[(long long)tid * ld + ki];
+                krow[tid] = P[(long long)tid * ld + kk];
+            }
+            if (tid == 0) {
+                s_p = ki;
+                piv[k0 + kk] = k0 + ki;
+            }
         }
         __syncthreads();
         const int p = s_p;
-        if (p != kk && tid < nb) {                       // exchange within the panel
-            double* cc = P + (long long)tid * ld;
-            const double a = cc[kk];
-            cc[kk] = cc[p];
-            cc[p] = a;
+        const double pivot = prow[kk];
+        const double rcp = 1.0 / pivot;
+        if (tid == 0) {
+            if (!(fabs(pivot) > thresh)) singular = true;
+            dinv[k0 + kk] = rcp;
         }
-        __syncthreads();
-        const double rcp = s_rcp;
-        for (int i = kk + 1 + tid; i < rows; i += NT) {  // multipliers and rank-1 update
-            const double l = col[i] * rcp;
+        if (tid < nb) P[(long long)tid * ld + kk] = prow[tid];       // row kk <- pivot row
+        // rows below: row p takes the old row kk (all panel columns), then
+        // every row gets its multiplier and the rank-1 update
+        for (int i = kk + 1 + tid; i < rows; i += NT) {
+            const bool is_p = (i == p);
+            if (is_p)
+                for (int c = 0; c < kk; ++c) P[(long long)c * ld + i] = krow[c];
+            const double l = (is_p ? krow[kk] : col[i]) * rcp;
             P[(long long)kk * ld + i] = l;
-            for (int c = kk + 1; c < nb; ++c) P[(long long)c * ld + i] -= l * P[(long long)c * ld + kk];
+            for (int c = kk + 1; c < nb; ++c) {
+                const double a = is_p ? krow[c] : P[(long long)c * ld + i];
+                P[(long long)c * ld + i] = a - l * prow[c];
+            }
         }
         __syncthreads();
     }
@@ -464,56 +498,153 @@ __global__ void __launch_bounds__(256) lu_gemm_kernel(DevView v, int first, int 
     }
 }
 
-// X = -M^-1 C for kXCols columns per CTA, columns staged in shared memory.
-__global__ void __launch_bounds__(256) merge_xsolve_kernel(DevView v, int first) {
+// W = M^-1 for kXCols columns per CTA (identity columns staged in shared
+// memory).  Blocked like the factorisation: per 32-row block, warp j solves
+// the diagonal block for column j with shuffles (block rows preloaded into
+// registers), then every thread updates one remaining row for all columns.
+__global__ void __launch_bounds__(32 * kXCols) merge_inverse_kernel(DevView v, int first) {
     extern __shared__ __align__(16) double xs[];   // kXCols x 2g
     const MergeDesc D = v.merges[first + blockIdx.x];
-    const int g2 = 2 * D.g, m = D.m;
+    const int g2 = 2 * D.g;
     const int j0 = blockIdx.y * kXCols;
-    if (j0 >= m) return;                              // uniform per CTA
-    const int nc = min(kXCols, m - j0);
+    if (j0 >= g2) return;                             // uniform per CTA
+    const int nc = min(kXCols, g2 - j0);
     const double* M = v.LU + D.LU_off;
     const int* piv = v.piv + D.piv_off;
-    double* X = v.X + D.X_off;
-    const int tid = threadIdx.x;
-    for (int idx = tid; idx < nc * g2; idx += 256) xs[idx] = X[(long long)j0 * g2 + idx];
+    const double* dinv = v.udinv + D.xb_off;
+    double* X = v.W + D.LU_off;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NT = 32 * kXCols;
+    for (int idx = tid; idx < nc * g2; idx += NT) xs[idx] = (idx % g2 == j0 + idx / g2) ? 1.0 : 0.0;
     __syncthreads();
-    // forward: per panel, its exchanges, then its columns of the unit lower L
+    // forward: per panel, its exchanges, the unit lower diagonal block, then
+    // the rows below
     for (int k0 = 0; k0 < g2; k0 += kNB) {
-        const int kend = min(k0 + kNB, g2);
-        if (tid < nc) {
-            for (int k = k0; k < kend; ++k) {
-                const int p = piv[k];
-                if (p != k) {
-                    const double a = xs[tid * g2 + k];
-                    xs[tid * g2 + k] = xs[tid * g2 + p];
-                    xs[tid * g2 + p] = a;
+        const int nb = min(kNB, g2 - k0);
+        if (warp < nc) {
+            double* x = xs + warp * g2;
+            double Lr[kNB];
+#pragma unroll
+            for (int c = 0; c < kNB; ++c)
+                Lr[c] = (c < nb && lane < nb) ? M[(long long)(k0 + c) * g2 + k0 + lane] : 0.0;
+            if (lane == 0) {
+                for (int k = k0; k < k0 + nb; ++k) {
+                    const int p = piv[k];
+                    if (p != k) { const double a = x[p]; x[p] = x[k]; x[k] = a; }
+                }
+            }
+            __syncwarp();
+            double val = lane < nb ? x[k0 + lane] : 0.0;
+#pragma unroll
+            for (int c = 0; c < kNB; ++c) {
+                const double xc = __shfl_sync(0xffffffffu, val, c);
+                if (lane > c) val -= Lr[c] * xc;
+            }
+            if (lane < nb) x[k0 + lane] = val;
+        }
+        __syncthreads();
+        for (int i = k0 + nb + tid; i < g2; i += NT) {
+            double Li[kNB];
+#pragma unroll
+            for (int c = 0; c < kNB; ++c) Li[c] = c < nb ? M[(long long)(k0 + c) * g2 + i] : 0.0;
+            for (int j = 0; j < nc; ++j) {
+                const double* x = xs + j * g2 + k0;
+                double acc = 0.0;
+#pragma unroll
+                for (int c = 0; c < kNB; ++c) acc += Li[c] * (c < nb ? x[c] : 0.0);
+                xs[j * g2 + i] -= acc;
+            }
+        }
+        __syncthreads();
+    }
+    // backward: U with the reciprocals of its diagonal, blocks from the bottom
+    for (int blk = (g2 - 1) / kNB; blk >= 0; --blk) {
+        const int k0 = blk * kNB, nb = min(kNB, g2 - k0);
+        if (warp < nc) {
+            double* x = xs + warp * g2;
+            double Ur[kNB];
+#pragma unroll
+            for (int c = 0; c < kNB; ++c)
+                Ur[c] = (c < nb && lane < nb) ? M[(long long)(k0 + c) * g2 + k0 + lane] : 0.0;
+            const double dl = lane < nb ? dinv[k0 + lane] : 0.0;
+            double val = lane < nb ? x[k0 + lane] : 0.0;
+#pragma unroll
+            for (int c = kNB - 1; c >= 0; --c) {
+                if (lane == c) val *= dl;
+                const double xc = __shfl_sync(0xffffffffu, val, c);
+                if (lane < c) val -= Ur[c] * xc;
+            }
+            if (lane < nb) x[k0 + lane] = val;
+        }
+        __syncthreads();
+        for (int i = tid; i < k0; i += NT) {
+            double Ui[kNB];
+#pragma unroll
+            for (int c = 0; c < kNB; ++c) Ui[c] = c < nb ? M[(long long)(k0 + c) * g2 + i] : 0.0;
+            for (int j = 0; j < nc; ++j) {
+                const double* x = xs + j * g2 + k0;
+                double acc = 0.0;
+#pragma unroll
+                for (int c = 0; c < kNB; ++c) acc += Ui[c] * (c < nb ? x[c] : 0.0);
+                xs[j * g2 + i] -= acc;
+            }
+        }
+        __syncthreads();
+    }
+    for (int idx = tid; idx < nc * g2; idx += NT) X[(long long)j0 * g2 + idx] = xs[idx];
+}
+
+// X = -W C with C = blockdiag(R^a_go, R^b_go): column j < o1 uses the first
+// g columns of W, the others the last g.  A CTA computes 64 rows x 16
+// columns; the gathered entries of C are staged in shared memory in chunks.
+constexpr int kXRows = 64, kXColsOut = 16, kXChunk = 64;
+__global__ void __launch_bounds__(256) merge_x_kernel(DevView v, int first) {
+    __shared__ double Cs[kXChunk][kXColsOut];
+    const MergeDesc D = v.merges[first + blockIdx.x];
+    const NodeRefs N = node_refs(v, D);
+    const int g = N.g, g2 = N.g2, m = N.m;
+    const int rt = (g2 + kXRows - 1) / kXRows;
+    const int r0 = (blockIdx.y % rt) * kXRows, j0 = (blockIdx.y / rt) * kXColsOut;
+    if (j0 >= m) return;                              // uniform per CTA
+    const double* W = v.W + D.LU_off;
+    double* X = v.X + D.X_off;
+    const int tid = threadIdx.x, rl = tid % kXRows, cg = tid / kXRows;   // 4 groups of 4 columns
+    const int r = r0 + rl;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    // columns of this CTA may straddle o1: treat the two halves separately
+    for (int half = 0; half < 2; ++half) {
+        const int jlo = half == 0 ? 0 : N.o1, jhi = half == 0 ? N.o1 : m;
+        if (j0 + kXColsOut <= jlo || j0 >= jhi) continue;  // uniform
+        for (int k0 = 0; k0 < g; k0 += kXChunk) {
+            const int kn = min(kXChunk, g - k0);
+            __syncthreads();
+            for (int idx = tid; idx < kXChunk * kXColsOut; idx += 256) {
+                const int kk = idx / kXColsOut, jj = idx % kXColsOut, j = j0 + jj;
+                double c = 0.0;
+                if (kk < kn && j >= jlo && j < jhi) {
+                    c = half == 0 ? N.R1[N.gpos1[k0 + kk] * N.m1 + N.opos1[j]]
+                                  : N.R2[N.gpos2[k0 + kk] * N.m2 + N.opos2[j - N.o1]];
+                }
+                Cs[kk][jj] = c;
+            }
+            __syncthreads();
+            if (r < g2) {
+                const double* wcol = W + (long long)(half * g + k0) * g2 + r;
+                for (int kk = 0; kk < kn; ++kk) {
+                    const double wv = wcol[(long long)kk * g2];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[q] += wv * Cs[kk][cg * 4 + q];
                 }
             }
         }
-        __syncthreads();
-        for (int k = k0; k < kend; ++k) {
-            const double* ck = M + (long long)k * g2;
-            const int rows = g2 - k - 1;
-            for (int idx = tid; idx < rows * nc; idx += 256) {
-                const int i = k + 1 + idx % rows, c = idx / rows;
-                xs[c * g2 + i] -= ck[i] * xs[c * g2 + k];
-            }
-            __syncthreads();
+    }
+    if (r < g2) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int j = j0 + cg * 4 + q;
+            if (j < m) X[(long long)j * g2 + r] = -acc[q];
         }
     }
-    // backward: U
-    for (int k = g2 - 1; k >= 0; --k) {
-        const double* ck = M + (long long)k * g2;
-        if (tid < nc) xs[tid * g2 + k] /= ck[k];
-        __syncthreads();
-        for (int idx = tid; idx < k * nc; idx += 256) {
-            const int i = idx % k, c = idx / k;
-            xs[c * g2 + i] -= ck[i] * xs[c * g2 + k];
-        }
-        __syncthreads();
-    }
-    for (int idx = tid; idx < nc * g2; idx += 256) X[(long long)j0 * g2 + idx] = xs[idx];
 }
 
 // R = blockdiag(R_oo) + blockdiag(R_og) X on kRTile^2 output tiles.
@@ -533,102 +664,42 @@ __global__ void __launch_bounds__(256) merge_rupdate_kernel(DevView v, int first
 }
 
 // ---------------------------------------------------------------------------
-// Solve phase, bottom-up: xbar = -M^-1 [rbar^a_gamma; rbar^b_gamma] and the
-// node's particular fluxes (Eqs. particular.1-2).  Blocked triangular
-// solves: warp 0 solves each 32 x 32 diagonal block with shuffles, the CTA
-// updates the remaining rows (a matrix-vector product per block).
-template <int NT>
-__global__ void __launch_bounds__(NT) merge_up_kernel(DevView v, int first) {
-    extern __shared__ __align__(16) double rhs[];
+// Solve phase, bottom-up: the node's particular fluxes
+// rbar = rbar_o + X^T rbar_gamma (Eqs. particular.1-2 with M symmetric); one
+// warp per output, lanes split the sum over gamma.
+constexpr int kUpOut = 32;
+__global__ void __launch_bounds__(256) merge_up_kernel(DevView v, int first) {
+    extern __shared__ __align__(16) double rg[];     // rbar_gamma (2g)
     const MergeDesc D = v.merges[first + blockIdx.x];
     const NodeRefs N = node_refs(v, D);
     const int g = N.g, g2 = N.g2, m = N.m, o1 = N.o1;
+    const int i0 = blockIdx.y * kUpOut;
+    if (i0 >= m) return;                              // uniform per CTA
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const double* M = v.LU + D.LU_off;
-    const int* piv = v.piv + D.piv_off;
-    const double* dinv = v.udinv + D.xb_off;
     const double* rb1 = v.rbar + D.r1_off;
     const double* rb2 = v.rbar + D.r2_off;
-    for (int r = tid; r < g2; r += NT) rhs[r] = -(r < g ? rb1[N.gpos1[r]] : rb2[N.gpos2[r - g]]);
+    for (int r = tid; r < g2; r += 256) rg[r] = r < g ? rb1[N.gpos1[r]] : rb2[N.gpos2[r - g]];
     __syncthreads();
-    if (D.pinned && tid == 0) {
-        const double a = rhs[0], b = rhs[g];
-        rhs[g] = a - b;
-        rhs[0] = 0.0;
-    }
-    __syncthreads();
-    // forward: per panel, its exchanges, the unit lower diagonal block, then
-    // the rows below
-    for (int k0 = 0; k0 < g2; k0 += kNB) {
-        const int nb = min(kNB, g2 - k0);
-        if (warp == 0) {
-            if (lane == 0) {
-                for (int k = k0; k < k0 + nb; ++k) {
-                    const int p = piv[k];
-                    if (p != k) { const double a = rhs[p]; rhs[p] = rhs[k]; rhs[k] = a; }
-                }
-            }
-            __syncwarp();
-            double val = lane < nb ? rhs[k0 + lane] : 0.0;
-            for (int c = 0; c < nb; ++c) {
-                const double xc = __shfl_sync(0xffffffffu, val, c);
-                if (lane > c && lane < nb) val -= M[(long long)(k0 + c) * g2 + k0 + lane] * xc;
-            }
-            if (lane < nb) rhs[k0 + lane] = val;
-        }
-        __syncthreads();
-        for (int i = k0 + nb + tid; i < g2; i += NT) {
-            double acc = 0.0;
-            for (int c = 0; c < nb; ++c) acc += M[(long long)(k0 + c) * g2 + i] * rhs[k0 + c];
-            rhs[i] -= acc;
-        }
-        __syncthreads();
-    }
-    // backward: U with the stored reciprocals of its diagonal, blocks from
-    // the bottom
-    for (int blk = (g2 - 1) / kNB; blk >= 0; --blk) {
-        const int k0 = blk * kNB, nb = min(kNB, g2 - k0);
-        if (warp == 0) {
-            double val = lane < nb ? rhs[k0 + lane] : 0.0;
-            for (int c = nb - 1; c >= 0; --c) {
-                if (lane == c) val *= dinv[k0 + c];
-                const double xc = __shfl_sync(0xffffffffu, val, c);
-                if (lane < c) val -= M[(long long)(k0 + c) * g2 + k0 + lane] * xc;
-            }
-            if (lane < nb) rhs[k0 + lane] = val;
-        }
-        __syncthreads();
-        for (int i = tid; i < k0; i += NT) {
-            double acc = 0.0;
-            for (int c = 0; c < nb; ++c) acc += M[(long long)(k0 + c) * g2 + i] * rhs[k0 + c];
-            rhs[i] -= acc;
-        }
-        __syncthreads();
-    }
-    double* xb = v.xbar + D.xb_off;
-    for (int r = tid; r < g2; r += NT) xb[r] = rhs[r];
-    // rbar of the node: one warp per output, lanes split the gamma sum
+    const double* X = v.X + D.X_off;
     double* rbp = v.rbar + D.r_off;
-    for (int i = warp; i < m; i += NT / 32) {
-        const bool first_child = i < o1;
-        const double* row = first_child ? N.R1 + N.opos1[i] * N.m1 : N.R2 + N.opos2[i - o1] * N.m2;
-        const int* gpos = first_child ? N.gpos1 : N.gpos2;
-        const double* x = first_child ? rhs : rhs + g;
+    for (int i = i0 + warp; i < min(i0 + kUpOut, m); i += 8) {
+        const double* xc = X + (long long)i * g2;
         double acc = 0.0;
-        for (int k = lane; k < g; k += 32) acc += row[gpos[k]] * x[k];
+        for (int k = lane; k < g2; k += 32) acc += xc[k] * rg[k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) acc += first_child ? rb1[N.opos1[i]] : rb2[N.opos2[i - o1]];
-        if (lane == 0) rbp[i] = acc;
+        if (lane == 0) rbp[i] = acc + (i < o1 ? rb1[N.opos1[i]] : rb2[N.opos2[i - o1]]);
     }
 }
 
-// Solve phase, top-down: lambda_gamma = X lambda_o + xbar, scattered into the
-// children's Robin data together with the node's own outer data.  A CTA
-// covers 64 rows of gamma; four thread groups split the sum over the outer
-// segments.
+// Solve phase, top-down: lambda_gamma = X lambda_o + W (-rbar_gamma) (with
+// the pinning rows of an all-Neumann root applied to the right-hand side),
+// scattered into the children's Robin data together with the node's own
+// outer data.  A CTA covers 64 rows of gamma; four thread groups split the
+// sums.
 constexpr int kDownRows = 64;
 __global__ void __launch_bounds__(256) merge_down_kernel(DevView v, int first) {
+    extern __shared__ __align__(16) double rhs[];    // -rbar_gamma (2g)
     __shared__ double part[4][kDownRows];
     const MergeDesc D = v.merges[first + blockIdx.x];
     const NodeRefs N = node_refs(v, D);
@@ -636,18 +707,31 @@ __global__ void __launch_bounds__(256) merge_down_kernel(DevView v, int first) {
     const int r0 = blockIdx.y * kDownRows;
     if (r0 >= g2) return;                                // uniform per CTA
     const int tid = threadIdx.x, rl = tid % kDownRows, grp = tid / kDownRows;
+    const double* rb1 = v.rbar + D.r1_off;
+    const double* rb2 = v.rbar + D.r2_off;
+    for (int r = tid; r < g2; r += 256) rhs[r] = -(r < g ? rb1[N.gpos1[r]] : rb2[N.gpos2[r - g]]);
+    __syncthreads();
+    if (D.pinned && tid == 0) {
+        const double a = rhs[0], b = rhs[g];
+        rhs[g] = a - b;
+        rhs[0] = 0.0;
+    }
+    __syncthreads();
     const double* lam_o = v.lam + D.r_off;
     const double* X = v.X + D.X_off;
+    const double* W = v.W + D.LU_off;
     double* l1 = v.lam + D.r1_off;
     double* l2 = v.lam + D.r2_off;
     const int r = r0 + rl;
     double acc = 0.0;
-    if (r < g2)
+    if (r < g2) {
         for (int j = grp; j < m; j += 4) acc += X[(long long)j * g2 + r] * lam_o[j];
+        for (int k = grp; k < g2; k += 4) acc += W[(long long)k * g2 + r] * rhs[k];
+    }
     part[grp][rl] = acc;
     __syncthreads();
     if (grp == 0 && r < g2) {
-        const double lg = v.xbar[D.xb_off + r] + ((part[0][rl] + part[1][rl]) + (part[2][rl] + part[3][rl]));
+        const double lg = (part[0][rl] + part[1][rl]) + (part[2][rl] + part[3][rl]);
         if (r < g) l1[N.gpos1[r]] = lg;
         else l2[N.gpos2[r - g]] = lg;
     }
@@ -713,11 +797,17 @@ cudaError_t launch_merge_build(const DevView& v, int first, int count, int max_g
         ++*launches;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    if (max_m > 0) {
+    {
         const size_t sm = (size_t)kXCols * max_g2 * sizeof(double);
-        e = cudaFuncSetAttribute(merge_xsolve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        e = cudaFuncSetAttribute(merge_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
-        merge_xsolve_kernel<<<dim3(count, (max_m + kXCols - 1) / kXCols), 256, sm, s>>>(v, first);
+        merge_inverse_kernel<<<dim3(count, (max_g2 + kXCols - 1) / kXCols), 32 * kXCols, sm, s>>>(v, first);
+        ++*launches;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (max_m > 0) {
+        const int rt = (max_g2 + kXRows - 1) / kXRows, ct = (max_m + kXColsOut - 1) / kXColsOut;
+        merge_x_kernel<<<dim3(count, rt * ct), 256, 0, s>>>(v, first);
         ++*launches;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         const int tiles = (max_m + kRTile - 1) / kRTile;
@@ -728,15 +818,17 @@ cudaError_t launch_merge_build(const DevView& v, int first, int count, int max_g
     return cudaSuccess;
 }
 
-cudaError_t launch_merge_up(const DevView& v, int first, int count, int max_g2, cudaStream_t s) {
-    if (count == 0) return cudaSuccess;
-    merge_up_kernel<kMergeThreads><<<count, kMergeThreads, (size_t)max_g2 * sizeof(double), s>>>(v, first);
+cudaError_t launch_merge_up(const DevView& v, int first, int count, int max_g2, int max_m, cudaStream_t s) {
+    if (count == 0 || max_m == 0) return cudaSuccess;
+    merge_up_kernel<<<dim3(count, (max_m + kUpOut - 1) / kUpOut), 256, (size_t)max_g2 * sizeof(double), s>>>(
+        v, first);
     return cudaGetLastError();
 }
 
-cudaError_t launch_merge_down(const DevView& v, int first, int count, int max_g2, cudaStream_t s) {
+cudaError_t launch_merge_down(const DevView& v, int first, int count, int max_g2, int, cudaStream_t s) {
     if (count == 0) return cudaSuccess;
-    merge_down_kernel<<<dim3(count, (max_g2 + kDownRows - 1) / kDownRows), 256, 0, s>>>(v, first);
+    merge_down_kernel<<<dim3(count, (max_g2 + kDownRows - 1) / kDownRows), 256, (size_t)max_g2 * sizeof(double),
+                        s>>>(v, first);
     return cudaGetLastError();
 }
 

@@ -514,7 +514,7 @@ static int setup_impl(mrcm_ctx* c, const mrcm_grid* g, const double* K_dev, cons
     TRY(dev_alloc(c, &v.LU, P.nLU));
     TRY(dev_alloc(c, &v.piv, P.npiv));
     TRY(dev_alloc(c, &v.X, P.nX));
-    TRY(dev_alloc(c, &v.xbar, P.nxb));
+    TRY(dev_alloc(c, &v.W, P.nLU));
     TRY(dev_alloc(c, &v.udinv, P.nxb));
     TRY(dev_alloc(c, &v.segP, P.nseg));
     TRY(dev_alloc(c, &v.segU, P.nseg));
@@ -619,11 +619,13 @@ static int solve_pass(mrcm_ctx* c, const double* q, const double* bc, bool with_
     {
         PhaseScope ps(c, MRCM_PHASE_TREE_SOLVE);
         for (int h = 1; h <= P.height; ++h) {
-            TRYC(launch_merge_up(v, P.level_first[h - 1], P.level_count[h - 1], P.level_max_g2[h - 1], s));
-            ++launches;
+            TRYC(launch_merge_up(v, P.level_first[h - 1], P.level_count[h - 1], P.level_max_g2[h - 1],
+                                 P.level_max_m[h - 1], s));
+            launches += P.level_max_m[h - 1] > 0;
         }
         for (int h = P.height; h >= 1; --h) {
-            TRYC(launch_merge_down(v, P.level_first[h - 1], P.level_count[h - 1], P.level_max_g2[h - 1], s));
+            TRYC(launch_merge_down(v, P.level_first[h - 1], P.level_count[h - 1], P.level_max_g2[h - 1],
+                                   P.level_max_m[h - 1], s));
             ++launches;
         }
     }

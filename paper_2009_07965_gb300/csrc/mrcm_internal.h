@@ -50,7 +50,7 @@ struct MergeDesc {
     long long LU_off;  // 2g x 2g LU factors (row-major, in place)
     long long piv_off; // 2g pivot rows (int)
     long long X_off;   // 2g x m coefficients X = -M^-1 C
-    long long xb_off;  // 2g particular coefficients
+    long long xb_off;  // per-merge vector of 2g values (U diagonal reciprocals)
 };
 
 // Device-side view of the plan and workspace.
@@ -91,7 +91,7 @@ struct DevView {
     double* LU;         // merge factors
     int* piv;
     double* X;
-    double* xbar;
+    double* W;          // explicit inverses of the interface matrices (LU_off layout)
     double* udinv;      // reciprocals of the U diagonal per merge (xb_off layout)
     double* segP;       // refined interface unknowns P_t, U_t (high parts)
     double* segU;
@@ -189,7 +189,7 @@ cudaError_t launch_mean_shift(const DevView& v, cudaStream_t s);
 cudaError_t launch_merge_build(const DevView& v, int first, int count, int max_g2, int max_m,
                                unsigned long long* amax_bits, cudaStream_t s, int* launches);
 bool merge_level_blocked(int count, int max_g2);
-cudaError_t launch_merge_up(const DevView& v, int first, int count, int max_g2, cudaStream_t s);
-cudaError_t launch_merge_down(const DevView& v, int first, int count, int max_g2, cudaStream_t s);
+cudaError_t launch_merge_up(const DevView& v, int first, int count, int max_g2, int max_m, cudaStream_t s);
+cudaError_t launch_merge_down(const DevView& v, int first, int count, int max_g2, int max_m, cudaStream_t s);
 
 }  // namespace mrcm
