@@ -49,8 +49,8 @@ namespace mrcm {
 namespace {
 
 constexpr int kNB = 32;         // panel width of the blocked LU
-constexpr int kGemmTile = 64;   // trailing-update tile (kGemmTile^2 outputs per CTA)
-constexpr int kXCols = 8;       // X columns per CTA in the blocked X solve
+constexpr int kGemmTile = 32;   // trailing-update tile (kGemmTile^2 outputs per CTA)
+constexpr int kXCols = 4;       // inverse columns per CTA
 constexpr int kRTile = 32;      // R update tile
 
 struct NodeRefs {
@@ -298,6 +298,7 @@ __global__ void __launch_bounds__(NT) lu_panel_kernel(DevView v, int first, int 
     __shared__ unsigned long long skey[NT / 32];
     __shared__ int si[NT / 32];
     __shared__ int s_p;
+    __shared__ double s_rcp;
     __shared__ double prow[kNB], krow[kNB];
     const MergeDesc D = v.merges[first + blockIdx.x];
     const int g2 = 2 * D.g;
@@ -308,12 +309,14 @@ __global__ void __launch_bounds__(NT) lu_panel_kernel(DevView v, int first, int 
     double* dinv = v.udinv + D.xb_off;
     const int tid = threadIdx.x;
     const bool staged = rows <= smem_rows;
-    double* P = staged ? Ps : Mg + (long long)k0 * g2 + k0;   // entry (i, c) at P[c * ld + i]
+    // shared memory: the multipliers of one step (rows), then the staged panel
+    double* lmul = Ps;
+    double* P = staged ? Ps + rows : Mg + (long long)k0 * g2 + k0;   // entry (i, c) at P[c * ld + i]
     const int ld = staged ? rows : g2;
     if (staged) {
         for (int idx = tid; idx < rows * nb; idx += NT) {
             const int i = idx % rows, c = idx / rows;
-            Ps[idx] = Mg[(long long)(k0 + c) * g2 + k0 + i];
+            P[idx] = Mg[(long long)(k0 + c) * g2 + k0 + i];
         }
         __syncthreads();
     }
@@ -352,39 +355,44 @@ __global__ void __launch_bounds__(NT) lu_panel_kernel(DevView v, int first, int 
                 krow[tid] = P[(long long)tid * ld + kk];
             }
             if (tid == 0) {
+                const double pivot = P[(long long)kk * ld + ki];
+                const double rcp = 1.0 / pivot;          // one warp: FP64 issue slots are scarce
+                if (!(fabs(pivot) > thresh)) singular = true;
+                s_rcp = rcp;
                 s_p = ki;
                 piv[k0 + kk] = k0 + ki;
+                dinv[k0 + kk] = rcp;
             }
         }
         __syncthreads();
         const int p = s_p;
-        const double pivot = prow[kk];
-        const double rcp = 1.0 / pivot;
-        if (tid == 0) {
-            if (!(fabs(pivot) > thresh)) singular = true;
-            dinv[k0 + kk] = rcp;
+        const double rcp = s_rcp;
+        const int nr = rows - kk - 1;
+        // multipliers, one lane per row (dense warps)
+        for (int r = tid; r < nr; r += NT) {
+            const int i = kk + 1 + r;
+            lmul[r] = (i == p ? krow[kk] : col[i]) * rcp;
         }
         if (tid < nb) P[(long long)tid * ld + kk] = prow[tid];       // row kk <- pivot row
-        // rows below: row p takes the old row kk (all panel columns), then
-        // every row gets its multiplier and the rank-1 update
-        for (int i = kk + 1 + tid; i < rows; i += NT) {
-            const bool is_p = (i == p);
-            if (is_p)
-                for (int c = 0; c < kk; ++c) P[(long long)c * ld + i] = krow[c];
-            const double l = (is_p ? krow[kk] : col[i]) * rcp;
-            P[(long long)kk * ld + i] = l;
-            for (int c = kk + 1; c < nb; ++c) {
-                const double a = is_p ? krow[c] : P[(long long)c * ld + i];
-                P[(long long)c * ld + i] = a - l * prow[c];
-            }
+        __syncthreads();
+        // rank-1 update of columns kk+1.., (row, column) pairs over all lanes;
+        // row p takes the old row kk's values, its multipliers included
+        const int ncu = nb - kk - 1;
+        for (int idx = tid; idx < nr * ncu; idx += NT) {
+            const int r = idx % nr, i = kk + 1 + r, c = kk + 1 + idx / nr;
+            const double a = (i == p) ? krow[c] : P[(long long)c * ld + i];
+            P[(long long)c * ld + i] = a - lmul[r] * prow[c];
         }
+        for (int r = tid; r < nr; r += NT) P[(long long)kk * ld + kk + 1 + r] = lmul[r];
+        if (p > kk)
+            for (int c = tid; c < kk; c += NT) P[(long long)c * ld + p] = krow[c];
         __syncthreads();
     }
     if (singular && tid == 0) atomicOr(v.status, kStatusSingular);
     if (staged) {
         for (int idx = tid; idx < rows * nb; idx += NT) {
             const int i = idx % rows, c = idx / rows;
-            Mg[(long long)(k0 + c) * g2 + k0 + i] = Ps[idx];
+            Mg[(long long)(k0 + c) * g2 + k0 + i] = P[idx];
         }
     }
 }
@@ -445,7 +453,7 @@ __global__ void __launch_bounds__(32 * kTrsmWarps) lu_trsm_kernel(DevView v, int
     if (lane < nb) col[k0 + lane] = u;
 }
 
-// Trailing update A22 -= L21 U12 on kGemmTile^2 tiles; 256 threads, 4x4 each.
+// Trailing update A22 -= L21 U12 on kGemmTile^2 tiles; 256 threads, 2x2 each.
 __global__ void __launch_bounds__(256) lu_gemm_kernel(DevView v, int first, int k0) {
     __shared__ double Ls[kNB][kGemmTile + 1];   // Ls[c][r]
     __shared__ double Us[kNB][kGemmTile + 1];   // Us[c][j]
@@ -469,29 +477,30 @@ __global__ void __launch_bounds__(256) lu_gemm_kernel(DevView v, int first, int 
         Us[c][jj] = (c < nb && j0 + jj < g2) ? M[(long long)(j0 + jj) * g2 + k0 + c] : 0.0;
     }
     __syncthreads();
-    const int tr = (tid % 16) * 4, tc = (tid / 16) * 4;
-    double acc[4][4];
+    constexpr int TS = kGemmTile / 16;                // outputs per thread per dimension
+    const int tr = (tid % 16) * TS, tc = (tid / 16) * TS;
+    double acc[TS][TS];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < TS; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
-#pragma unroll 4
+        for (int b = 0; b < TS; ++b) acc[a][b] = 0.0;
+#pragma unroll 8
     for (int c = 0; c < kNB; ++c) {
-        double lv[4], uv[4];
+        double lv[TS], uv[TS];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) { lv[a] = Ls[c][tr + a]; uv[a] = Us[c][tc + a]; }
+        for (int a = 0; a < TS; ++a) { lv[a] = Ls[c][tr + a]; uv[a] = Us[c][tc + a]; }
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+        for (int a = 0; a < TS; ++a)
 #pragma unroll
-            for (int b = 0; b < 4; ++b) acc[a][b] += lv[a] * uv[b];
+            for (int b = 0; b < TS; ++b) acc[a][b] += lv[a] * uv[b];
     }
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
+    for (int b = 0; b < TS; ++b) {
         const int j = j0 + tc + b;
         if (j >= g2) continue;
         double* col = M + (long long)j * g2;
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
+        for (int a = 0; a < TS; ++a) {
             const int r = r0 + tr + a;
             if (r < g2) col[r] -= acc[a][b];
         }
@@ -647,23 +656,72 @@ __global__ void __launch_bounds__(256) merge_x_kernel(DevView v, int first) {
     }
 }
 
-// R = blockdiag(R_oo) + blockdiag(R_og) X on kRTile^2 output tiles.
+// R = blockdiag(R_oo) + blockdiag(R_og) X on kRTile^2 output tiles: row i
+// of the tile uses the gathered row of R^a (i < o1) or R^b and the matching
+// half of X; both are staged in shared memory in chunks of kRTile.
 __global__ void __launch_bounds__(256) merge_rupdate_kernel(DevView v, int first) {
+    __shared__ double Cs[kRTile][kRTile + 1];        // Cs[row][k]
+    __shared__ double Xs[2][kRTile][kRTile + 1];     // Xs[half][k][col]
     const MergeDesc D = v.merges[first + blockIdx.x];
     const NodeRefs N = node_refs(v, D);
-    const int m = N.m;
+    const int m = N.m, g = N.g, g2 = N.g2, o1 = N.o1;
     const int tiles = (m + kRTile - 1) / kRTile;
     if ((int)blockIdx.y >= tiles * tiles) return;
     const int i0 = (blockIdx.y % tiles) * kRTile, jt = (blockIdx.y / tiles) * kRTile;
     const double* X = v.X + D.X_off;
     double* Rp = v.R + D.R_off;
-    for (int idx = threadIdx.x; idx < kRTile * kRTile; idx += 256) {
-        const int i = i0 + idx / kRTile, j = jt + idx % kRTile;
-        if (i < m && j < m) Rp[(long long)i * m + j] = r_entry(N, X, i, j);
+    const int tid = threadIdx.x;
+    constexpr int TS = kRTile / 16;
+    const int tr = (tid % 16) * TS, tc = (tid / 16) * TS;
+    double acc[TS][TS];
+#pragma unroll
+    for (int a = 0; a < TS; ++a)
+#pragma unroll
+        for (int b = 0; b < TS; ++b) acc[a][b] = 0.0;
+    for (int k0 = 0; k0 < g; k0 += kRTile) {
+        const int kn = min(kRTile, g - k0);
+        __syncthreads();
+        for (int idx = tid; idx < kRTile * kRTile; idx += 256) {
+            const int rr = idx / kRTile, kk = idx % kRTile, i = i0 + rr;
+            double c = 0.0;
+            if (kk < kn && i < m)
+                c = i < o1 ? N.R1[N.opos1[i] * N.m1 + N.gpos1[k0 + kk]]
+                           : N.R2[N.opos2[i - o1] * N.m2 + N.gpos2[k0 + kk]];
+            Cs[rr][kk] = c;
+        }
+        for (int idx = tid; idx < 2 * kRTile * kRTile; idx += 256) {
+            const int half = idx / (kRTile * kRTile), rem = idx % (kRTile * kRTile);
+            const int kk = rem % kRTile, jj = rem / kRTile, j = jt + jj;
+            Xs[half][kk][jj] = (kk < kn && j < m) ? X[(long long)j * g2 + half * g + k0 + kk] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int a = 0; a < TS; ++a) {
+            const int half = (i0 + tr + a) < o1 ? 0 : 1;
+            for (int kk = 0; kk < kRTile; ++kk) {
+                const double cv = Cs[tr + a][kk];
+#pragma unroll
+                for (int b = 0; b < TS; ++b) acc[a][b] += cv * Xs[half][kk][tc + b];
+            }
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < TS; ++a) {
+        const int i = i0 + tr + a;
+        if (i >= m) continue;
+        const double* row = i < o1 ? N.R1 + N.opos1[i] * N.m1 : N.R2 + N.opos2[i - o1] * N.m2;
+#pragma unroll
+        for (int b = 0; b < TS; ++b) {
+            const int j = jt + tc + b;
+            if (j >= m) continue;
+            double val = acc[a][b];
+            if (i < o1 && j < o1) val += row[N.opos1[j]];
+            if (i >= o1 && j >= o1) val += row[N.opos2[j - o1]];
+            Rp[(long long)i * m + j] = val;
+        }
     }
 }
 
-// ---------------------------------------------------------------------------
 // Solve phase, bottom-up: the node's particular fluxes
 // rbar = rbar_o + X^T rbar_gamma (Eqs. particular.1-2 with M symmetric); one
 // warp per output, lanes split the sum over gamma.
@@ -697,10 +755,10 @@ __global__ void __launch_bounds__(256) merge_up_kernel(DevView v, int first) {
 // scattered into the children's Robin data together with the node's own
 // outer data.  A CTA covers 64 rows of gamma; four thread groups split the
 // sums.
-constexpr int kDownRows = 64;
+constexpr int kDownRows = 32, kDownGroups = 8;
 __global__ void __launch_bounds__(256) merge_down_kernel(DevView v, int first) {
     extern __shared__ __align__(16) double rhs[];    // -rbar_gamma (2g)
-    __shared__ double part[4][kDownRows];
+    __shared__ double part[kDownGroups][kDownRows];
     const MergeDesc D = v.merges[first + blockIdx.x];
     const NodeRefs N = node_refs(v, D);
     const int g = N.g, g2 = N.g2, m = N.m, o1 = N.o1;
@@ -725,13 +783,15 @@ __global__ void __launch_bounds__(256) merge_down_kernel(DevView v, int first) {
     const int r = r0 + rl;
     double acc = 0.0;
     if (r < g2) {
-        for (int j = grp; j < m; j += 4) acc += X[(long long)j * g2 + r] * lam_o[j];
-        for (int k = grp; k < g2; k += 4) acc += W[(long long)k * g2 + r] * rhs[k];
+        for (int j = grp; j < m; j += kDownGroups) acc += X[(long long)j * g2 + r] * lam_o[j];
+        for (int k = grp; k < g2; k += kDownGroups) acc += W[(long long)k * g2 + r] * rhs[k];
     }
     part[grp][rl] = acc;
     __syncthreads();
     if (grp == 0 && r < g2) {
-        const double lg = (part[0][rl] + part[1][rl]) + (part[2][rl] + part[3][rl]);
+        double lg = 0.0;
+#pragma unroll
+        for (int q = 0; q < kDownGroups; ++q) lg += part[q][rl];
         if (r < g) l1[N.gpos1[r]] = lg;
         else l2[N.gpos2[r - g]] = lg;
     }
@@ -776,15 +836,16 @@ cudaError_t launch_merge_build(const DevView& v, int first, int count, int max_g
         ++*launches;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    const int smem_rows = kPanelSmemBytes / (kNB * (int)sizeof(double));
+    const int smem_rows = kPanelSmemBytes / ((kNB + 1) * (int)sizeof(double));
     e = cudaFuncSetAttribute(lu_panel_kernel<kPanelThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              kPanelSmemBytes);
     if (e != cudaSuccess) return e;
     for (int k0 = 0; k0 < max_g2; k0 += kNB) {
         const int rows = max_g2 - k0;
-        const size_t psm = rows <= smem_rows ? (size_t)rows * kNB * sizeof(double) : 0;
+        const bool staged = rows <= smem_rows;
+        const size_t psm = (size_t)rows * (staged ? kNB + 1 : 1) * sizeof(double);
         lu_panel_kernel<kPanelThreads><<<count, kPanelThreads, psm, s>>>(v, first, k0, amax_bits,
-                                                                          psm ? smem_rows : 0);
+                                                                          staged ? smem_rows : 0);
         ++*launches;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         const int rest = max_g2 - min(k0 + kNB, max_g2);
