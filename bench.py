@@ -270,16 +270,15 @@ def run_ours(args):
 
     launches = (mr.mrcm_query(solver.ctx, "KERNEL_LAUNCHES_BUILD")
                 + mr.mrcm_query(solver.ctx, "KERNEL_LAUNCHES_SOLVE"))
-    leaf_flops = mr.mrcm_query(solver.ctx, "LEAF_FLOPS")
     build_flops = mr.mrcm_query(solver.ctx, "BUILD_FLOPS")
-    solve_flops = mr.mrcm_query(solver.ctx, "SOLVE_FLOPS")
-    ph = {k: v / args.steps for k, v in phases.items()}
-    # dominant kernel: the leaf build (one launch per step) or the merge phase
-    if ph["leaf_build"] >= ph["merge_build"]:
-        dom, dom_flops, dom_ms = "leaf_build_kernel", leaf_flops, ph["leaf_build"]
-    else:
-        dom, dom_flops, dom_ms = "merge_build_kernel", build_flops - leaf_flops, ph["merge_build"]
-    achieved = dom_flops / (dom_ms / 1e3) / 1e12
+    ph = {k: v / args.steps for k, v in phases.items()}          # ms per step
+    pf = mr.mrcm_phase_flops(solver.ctx)                          # flops per step
+    table = {k: dict(ms=ph[k], gflop=pf[k] / 1e9,
+                     tflops=(pf[k] / (ph[k] / 1e3) / 1e12) if ph[k] > 0 else None)
+             for k in mr.PHASES}
+    # the dominant kernel family: the phase with the largest share of the step
+    dom = max(mr.PHASES, key=lambda k: ph[k])
+    achieved = pf[dom] / (ph[dom] / 1e3) / 1e12
     if rank != 0:
         return
     cpu = None
@@ -300,10 +299,11 @@ def run_ours(args):
                     l2="flushed between timed steps (256 MiB write outside the events)",
                     parallelism=f"replicas x{world}"),
         roofline=dict(bound="alu", achieved=achieved, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
-                      frac=achieved / FP64_PEAK_TFLOPS, traffic=None, kernel=dom,
+                      frac=achieved / FP64_PEAK_TFLOPS, traffic=None, kernel=mr.PHASE_KERNELS[dom],
+                      phase=dom, share=ph[dom] / (total_ms / args.steps),
                       peak_source="FP64 FMA pipe: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz"),
-        phases_ms=ph,
-        model_gflop=dict(build=build_flops / 1e9, leaf=leaf_flops / 1e9, solve=solve_flops / 1e9),
+        phases=table,
+        model_gflop_per_step=sum(pf.values()) / 1e9,
         e2e=dict(value=e2e_value, unit="cells/s", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
         gpu_launches=launches * args.steps,
         clocks=clocks,

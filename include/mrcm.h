@@ -180,17 +180,23 @@ int mrcm_query(const mrcm_ctx* ctx, int what, long long* value);
 int mrcm_plan_query(const mrcm_grid* g, const int sub_cells[3], const int seg_cells[3],
                     const int bc_type[6], int what, long long* value);
 
-/* Phases timed by mrcm_phase_times. */
+/* Phases timed by mrcm_phase_times: each groups the launches of one kernel
+ * family, so a phase time is the time of that family's kernels. */
 enum {
-    MRCM_PHASE_COEF = 0,        /* permeability check, Robin and face coefficients */
-    MRCM_PHASE_LEAF_BUILD = 1,  /* leaf factorisation and Robin-to-flux maps      */
-    MRCM_PHASE_MERGE_BUILD = 2, /* all interface merges of the build              */
-    MRCM_PHASE_LEAF_PART = 3,   /* leaf particular solutions (solve)              */
-    MRCM_PHASE_TREE_SOLVE = 4,  /* up-sweep, root, down-sweep (solve)             */
-    MRCM_PHASE_LEAF_FINAL = 5,  /* leaf pressures and interface unknowns (solve)  */
-    MRCM_PHASE_FINISH = 6,      /* mean shift and face fluxes (solve)             */
-    MRCM_PHASE_RESIDUAL = 7,    /* refinement residuals (solve)                   */
-    MRCM_PHASE_COUNT = 8
+    MRCM_PHASE_COEF = 0,           /* permeability check, Robin and face coefficients */
+    MRCM_PHASE_LEAF_BUILD = 1,     /* leaf factorisation and Robin-to-flux maps     */
+    MRCM_PHASE_MERGE_SMALL = 2,    /* fused merges of levels with many small nodes  */
+    MRCM_PHASE_LU_PANEL = 3,       /* blocked LU: panel factorisations              */
+    MRCM_PHASE_LU_UPDATE = 4,      /* blocked LU: U block rows and trailing updates */
+    MRCM_PHASE_MERGE_INVERSE = 5,  /* blocked merges: W = M^-1                      */
+    MRCM_PHASE_MERGE_PRODUCTS = 6, /* blocked merges: assembly, X = -W C, merged R  */
+    MRCM_PHASE_LEAF_PART = 7,      /* leaf particular solutions (solve)             */
+    MRCM_PHASE_TREE_UP = 8,        /* up-sweep of the particular fluxes (solve)     */
+    MRCM_PHASE_TREE_DOWN = 9,      /* down-sweep of the Robin data (solve)          */
+    MRCM_PHASE_LEAF_PRESSURE = 10, /* leaf pressures, interface unknowns (solve)    */
+    MRCM_PHASE_RESIDUAL = 11,      /* refinement residuals (solve)                  */
+    MRCM_PHASE_FINISH = 12,        /* mean shift and face fluxes (solve)            */
+    MRCM_PHASE_COUNT = 13
 };
 
 /*
@@ -216,14 +222,24 @@ int mrcm_set_refinement(mrcm_ctx* ctx, int steps, int check);
 int mrcm_residual_history(mrcm_ctx* ctx, double* out, int cap);
 
 /*
- * mrcm_enable_timing -- on != 0: record a CUDA event pair around every phase
- * of the following build / solve calls (on the context's stream).
- * mrcm_phase_times -- ms[MRCM_PHASE_COUNT] (host) receives the durations of
- * the phases of the most recent build and solve (0 where not run).  Only
- * valid after a call made with timing enabled.
+ * mrcm_enable_timing -- on != 0: record a CUDA event pair around every launch
+ * group of a phase in the following build / solve calls (on the context's
+ * stream).
+ * mrcm_phase_times -- ms[MRCM_PHASE_COUNT] (host) receives, per phase, the
+ * summed durations of its launch groups in the most recent build and solve
+ * (0 where not run).  Only valid after a call made with timing enabled.
  */
 int mrcm_enable_timing(mrcm_ctx* ctx, int on);
 int mrcm_phase_times(mrcm_ctx* ctx, double* ms);
+
+/*
+ * mrcm_phase_flops -- flops[MRCM_PHASE_COUNT] (host) receives the algorithmic
+ * FP64 flop count of each phase for one mrcm_build_basis (build phases) and
+ * one mrcm_solve with the current refinement setting (solve phases): the
+ * arithmetic the algorithm needs (a fused multiply-add counts 2), not the
+ * instructions a kernel issues.  Host only, no device call.
+ */
+int mrcm_phase_flops(const mrcm_ctx* ctx, double* flops);
 
 /*
  * Introspection for tests (host buffers, synchronous).

@@ -24,9 +24,17 @@ Q = dict(LEAVES=0, SEGMENTS=1, LEVELS=2, NODES=3, WORKSPACE_BYTES=4, MAX_GAMMA=5
 EXPORTS = ["mrcm_setup", "mrcm_plan_query", "mrcm_set_permeability", "mrcm_build_basis", "mrcm_solve", "mrcm_query",
            "mrcm_node_info", "mrcm_node_segments", "mrcm_segment_info", "mrcm_node_operator",
            "mrcm_destroy", "mrcm_error_string", "mrcm_enable_timing", "mrcm_phase_times",
-           "mrcm_merge_pair_noalloc", "mrcm_set_refinement", "mrcm_residual_history"]
-PHASES = ["coef", "leaf_build", "merge_build", "leaf_particular", "tree_solve", "leaf_final", "finish",
-          "residual"]
+           "mrcm_merge_pair_noalloc", "mrcm_set_refinement", "mrcm_residual_history", "mrcm_phase_flops"]
+PHASES = ["coef", "leaf_build", "merge_small", "lu_panel", "lu_update", "merge_inverse", "merge_products",
+          "leaf_particular", "tree_up", "tree_down", "leaf_pressure", "residual", "finish"]
+# kernel family behind each phase (for reports)
+PHASE_KERNELS = {"coef": "face_coef_kernel", "leaf_build": "leaf_build_kernel",
+                 "merge_small": "merge_small_kernel", "lu_panel": "lu_panel_kernel",
+                 "lu_update": "lu_trsm_kernel+lu_gemm_kernel", "merge_inverse": "merge_inverse_kernel",
+                 "merge_products": "merge_assemble/x/rupdate_kernel", "leaf_particular": "leaf_particular_kernel",
+                 "tree_up": "merge_up_kernel", "tree_down": "merge_down_kernel",
+                 "leaf_pressure": "leaf_pressure_kernel", "residual": "residual_cells/segments_kernel",
+                 "finish": "face_flux_kernel"}
 
 
 class MrcmError(RuntimeError):
@@ -77,6 +85,8 @@ def _lib():
         lib.mrcm_phase_times.restype = I
         lib.mrcm_merge_pair_noalloc.argtypes = [P, I, P, I, P, I, P, P, P, P]
         lib.mrcm_merge_pair_noalloc.restype = I
+        lib.mrcm_phase_flops.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
+        lib.mrcm_phase_flops.restype = I
         lib.mrcm_set_refinement.argtypes = [P, I, I]
         lib.mrcm_set_refinement.restype = I
         lib.mrcm_residual_history.argtypes = [P, ctypes.POINTER(ctypes.c_double), I]
@@ -199,6 +209,12 @@ def mrcm_residual_history(ctx, cap=17):
     if n < 0:
         raise MrcmError(n, "mrcm_residual_history")
     return list(buf)[:min(n, cap)]
+
+
+def mrcm_phase_flops(ctx):
+    f = (ctypes.c_double * len(PHASES))()
+    _check(_lib().mrcm_phase_flops(ctx, f), "mrcm_phase_flops")
+    return dict(zip(PHASES, list(f)))
 
 
 def mrcm_destroy(ctx):

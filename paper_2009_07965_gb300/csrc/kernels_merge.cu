@@ -813,11 +813,24 @@ constexpr int kBlockedBelow = 304;    // levels with fewer nodes take the blocke
 
 bool merge_level_blocked(int count, int max_g2) { return max_g2 > kSmemG2 || count < kBlockedBelow; }
 
+// phase ids (include/mrcm.h)
+enum { kPhMergeSmall = 2, kPhLuPanel = 3, kPhLuUpdate = 4, kPhMergeInverse = 5, kPhMergeProducts = 6 };
+
+struct HookScope {
+    const PhaseHook& h;
+    int phase;
+    HookScope(const PhaseHook& h_, int p) : h(h_), phase(p) { if (h.begin) h.begin(h.ctx, p); }
+    ~HookScope() { if (h.end) h.end(h.ctx, phase); }
+};
+
 cudaError_t launch_merge_build(const DevView& v, int first, int count, int max_g2, int max_m,
-                               unsigned long long* amax_bits, cudaStream_t s, int* launches) {
+                               unsigned long long* amax_bits, cudaStream_t s, int* launches,
+                               const PhaseHook& hook) {
+    static_assert(kNB == kMergePanel, "flop model panel width");
     if (count == 0) return cudaSuccess;
     cudaError_t e;
     if (!merge_level_blocked(count, max_g2)) {
+        HookScope hs(hook, kPhMergeSmall);
         const size_t sm = (size_t)max_g2 * max_g2 * sizeof(double);
         e = cudaFuncSetAttribute(merge_small_kernel<kMergeThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(kSmemG2 * kSmemG2 * sizeof(double)));
@@ -829,6 +842,7 @@ cudaError_t launch_merge_build(const DevView& v, int first, int count, int max_g
     e = cudaMemsetAsync(amax_bits, 0, sizeof(unsigned long long) * count, s);
     if (e != cudaSuccess) return e;
     {
+        HookScope hs(hook, kPhMergeProducts);
         const long long work = (long long)max_g2 * (max_g2 + max_m);
         int gy = (int)((work + 255) / 256);
         gy = gy < 1 ? 1 : (gy > 64 ? 64 : gy);
@@ -844,12 +858,16 @@ cudaError_t launch_merge_build(const DevView& v, int first, int count, int max_g
         const int rows = max_g2 - k0;
         const bool staged = rows <= smem_rows;
         const size_t psm = (size_t)rows * (staged ? kNB + 1 : 1) * sizeof(double);
-        lu_panel_kernel<kPanelThreads><<<count, kPanelThreads, psm, s>>>(v, first, k0, amax_bits,
-                                                                          staged ? smem_rows : 0);
-        ++*launches;
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        {
+            HookScope hs(hook, kPhLuPanel);
+            lu_panel_kernel<kPanelThreads><<<count, kPanelThreads, psm, s>>>(v, first, k0, amax_bits,
+                                                                              staged ? smem_rows : 0);
+            ++*launches;
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
         const int rest = max_g2 - min(k0 + kNB, max_g2);
         if (rest <= 0) break;
+        HookScope hs(hook, kPhLuUpdate);
         lu_trsm_kernel<<<dim3(count, (rest + kTrsmWarps - 1) / kTrsmWarps), 32 * kTrsmWarps, 0, s>>>(v, first, k0);
         ++*launches;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -859,6 +877,7 @@ cudaError_t launch_merge_build(const DevView& v, int first, int count, int max_g
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     {
+        HookScope hs(hook, kPhMergeInverse);
         const size_t sm = (size_t)kXCols * max_g2 * sizeof(double);
         e = cudaFuncSetAttribute(merge_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
@@ -867,6 +886,7 @@ cudaError_t launch_merge_build(const DevView& v, int first, int count, int max_g
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if (max_m > 0) {
+        HookScope hs(hook, kPhMergeProducts);
         const int rt = (max_g2 + kXRows - 1) / kXRows, ct = (max_m + kXColsOut - 1) / kXColsOut;
         merge_x_kernel<<<dim3(count, rt * ct), 256, 0, s>>>(v, first);
         ++*launches;

@@ -56,6 +56,9 @@ struct Plan {
     std::vector<long long> seg_lam_a, seg_lam_b;   // lam offsets of each segment in its two leaves
     // flop model
     long long leaf_flops = 0, merge_flops = 0, solve_flops = 0;
+    double phase_build[MRCM_PHASE_COUNT] = {};   // per build call
+    double phase_pass[MRCM_PHASE_COUNT] = {};    // per solve pass
+    double residual_flops = 0, finish_flops = 0;
 };
 
 inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
@@ -239,6 +242,8 @@ int make_plan(Plan& P) {
         P.leaf_flops += f;
         // solve phase per leaf: forward sweep, Z^T y, Z lambda, backward sweep
         P.solve_flops += 2 * n * L.w * 2 + 2 * n * L.m * 2 + 2 * n;
+        P.phase_pass[MRCM_PHASE_LEAF_PART] += 2.0 * n * L.w + 2.0 * n * L.m + n;
+        P.phase_pass[MRCM_PHASE_LEAF_PRESSURE] += 2.0 * n * L.m + 2.0 * n * L.w + 2.0 * n;
     }
     // offsets of each segment inside the Robin-data arrays of its two leaves
     P.seg_lam_a.assign(P.nseg, -1);
@@ -252,6 +257,7 @@ int make_plan(Plan& P) {
         }
     }
     // merges grouped by height
+    std::vector<double> node_lu_flops, node_inv_flops, node_prod_flops;
     std::vector<std::vector<int>> by_h(P.height + 1);
     for (int v = P.nleaf; v < nnode; ++v) by_h[P.nodes[v].height].push_back(v);
     P.level_first.assign(P.height, 0);
@@ -293,12 +299,47 @@ int make_plan(Plan& P) {
             P.level_max_g2[h - 1] = std::max(P.level_max_g2[h - 1], (int)g2);
             P.level_max_m[h - 1] = std::max(P.level_max_m[h - 1], (int)m);
             P.max_g2 = std::max(P.max_g2, (int)g2);
-            // flop model: LU (2/3 N^3), X solve (2 N^2 m), R update (2 g m^2)
-            const double N = (double)g2;
-            P.merge_flops += (long long)(2.0 / 3.0 * N * N * N) + 2LL * g2 * g2 * m + 2LL * D.g * m * m;
-            P.solve_flops += 2LL * g2 * g2 + 2LL * D.g * m + 2LL * g2 * m;
+            // flop model: LU with partial pivoting, W = M^-1 from the factors
+            // (2 N^3 on identity columns), X = -W C over C's blocks (2 N g m),
+            // R update (2 g m^2); solve passes: up 2 m N, down 2 N (m + N)
+            const double N = (double)g2, gd = (double)D.g, md = (double)m;
+            double lu = 0.0;
+            for (int k = 0; k < g2; ++k) lu += (double)(g2 - k - 1) + 2.0 * (g2 - k - 1) * (double)(g2 - k - 1);
+            const double inv = 2.0 * N * N * N, prod = 2.0 * N * gd * md + 2.0 * md * md * gd;
+            P.merge_flops += (long long)(lu + inv + prod);
+            P.solve_flops += 2LL * g2 * m + 2LL * g2 * (m + g2);
+            if (m > 0) P.phase_pass[MRCM_PHASE_TREE_UP] += 2.0 * md * N;
+            P.phase_pass[MRCM_PHASE_TREE_DOWN] += 2.0 * N * (md + N);
+            node_lu_flops.push_back(lu);
+            node_inv_flops.push_back(inv);
+            node_prod_flops.push_back(prod);
         }
     }
+    // build phases: leaves, then per level the fused or the blocked path
+    P.phase_build[MRCM_PHASE_LEAF_BUILD] = (double)P.leaf_flops;
+    for (int h = 1; h <= P.height; ++h) {
+        const int f0 = P.level_first[h - 1], cnt = P.level_count[h - 1];
+        const bool blocked = merge_level_blocked(cnt, P.level_max_g2[h - 1]);
+        for (int q = f0; q < f0 + cnt; ++q) {
+            if (!blocked) {
+                P.phase_build[MRCM_PHASE_MERGE_SMALL] += node_lu_flops[q] + node_inv_flops[q] + node_prod_flops[q];
+                continue;
+            }
+            const int N = 2 * P.merges[q].g;
+            for (int k0 = 0; k0 < N; k0 += kMergePanel) {
+                const int nb = std::min(kMergePanel, N - k0), rows = N - k0, rest = N - k0 - nb;
+                double pf = 0.0;
+                for (int kk = 0; kk < nb; ++kk) pf += (rows - kk - 1) + 2.0 * (rows - kk - 1) * (nb - kk - 1);
+                P.phase_build[MRCM_PHASE_LU_PANEL] += pf;
+                P.phase_build[MRCM_PHASE_LU_UPDATE] += (double)rest * nb * (nb - 1) + 2.0 * rest * rest * nb;
+            }
+            P.phase_build[MRCM_PHASE_MERGE_INVERSE] += node_inv_flops[q];
+            P.phase_build[MRCM_PHASE_MERGE_PRODUCTS] += node_prod_flops[q];
+        }
+    }
+    const double ncell = (double)P.nx * P.ny, nface = (double)(P.nx + 1) * P.ny + (double)P.nx * (P.ny + 1);
+    P.residual_flops = 8.0 * ncell + 8.0 * (double)P.nskel_faces;
+    P.finish_flops = 3.0 * nface + 2.0 * ncell;
     return MRCM_OK;
 }
 
@@ -316,9 +357,10 @@ struct mrcm_ctx {
     double* K = nullptr;
     int launches_build = 0, launches_solve = 0;
     bool timing = false;
-    cudaEvent_t ev[2 * MRCM_PHASE_COUNT * (kMaxRefine + 2)] = {};
+    std::vector<cudaEvent_t> ev;          // event pairs, handed out per launch group
+    std::vector<int> ev_phase;            // phase of each used pair
+    int ev_used = 0;
     unsigned long long* amax_bits = nullptr;
-    int ev_count[MRCM_PHASE_COUNT] = {};
     int refine_steps = 2;
     int refine_check = 0;
     int hist_count = 0;
@@ -370,21 +412,26 @@ int read_status(mrcm_ctx* c) {
     return MRCM_OK;
 }
 
-// Records a CUDA event pair around one occurrence of a phase; the phase time
-// of a call is the sum over its occurrences.
-constexpr int kMaxOcc = kMaxRefine + 2;
+// Records a CUDA event pair around one launch group of a phase; the phase
+// time of a call is the sum over its groups.
+constexpr int kEventPairs = 4096;
+void phase_begin(void* vc, int phase) {
+    mrcm_ctx* c = static_cast<mrcm_ctx*>(vc);
+    if (!c->timing || c->ev_used >= kEventPairs) return;
+    c->ev_phase[c->ev_used] = phase;
+    cudaEventRecord(c->ev[2 * c->ev_used], c->stream);
+}
+void phase_end(void* vc, int) {
+    mrcm_ctx* c = static_cast<mrcm_ctx*>(vc);
+    if (!c->timing || c->ev_used >= kEventPairs) return;
+    cudaEventRecord(c->ev[2 * c->ev_used + 1], c->stream);
+    ++c->ev_used;
+}
 struct PhaseScope {
     mrcm_ctx* c;
-    int slot = -1;
-    PhaseScope(mrcm_ctx* c_, int p) : c(c_) {
-        if (c->timing && c->ev_count[p] < kMaxOcc) {
-            slot = 2 * (p * kMaxOcc + c->ev_count[p]++);
-            cudaEventRecord(c->ev[slot], c->stream);
-        }
-    }
-    ~PhaseScope() {
-        if (slot >= 0) cudaEventRecord(c->ev[slot + 1], c->stream);
-    }
+    int phase;
+    PhaseScope(mrcm_ctx* c_, int p) : c(c_), phase(p) { phase_begin(c, p); }
+    ~PhaseScope() { phase_end(c, phase); }
 };
 
 }  // namespace
@@ -578,7 +625,7 @@ int mrcm_build_basis(mrcm_ctx* c) {
     c->built = false;
     c->solved = false;
     int launches = 0;
-    for (int p = 0; p < MRCM_PHASE_COUNT; ++p) c->ev_count[p] = 0;
+    c->ev_used = 0;
     TRYC(cudaMemsetAsync(v.status, 0, sizeof(int), s));
     {
         PhaseScope ps(c, MRCM_PHASE_COEF);
@@ -592,10 +639,10 @@ int mrcm_build_basis(mrcm_ctx* c) {
         TRYC(launch_leaf_build(v, P.max_m_leaf, s)); ++launches;
     }
     {
-        PhaseScope ps(c, MRCM_PHASE_MERGE_BUILD);
+        const PhaseHook hook{c, phase_begin, phase_end};
         for (int h = 1; h <= P.height; ++h) {
             TRYC(launch_merge_build(v, P.level_first[h - 1], P.level_count[h - 1], P.level_max_g2[h - 1],
-                                    P.level_max_m[h - 1], c->amax_bits, s, &launches));
+                                    P.level_max_m[h - 1], c->amax_bits, s, &launches, hook));
         }
     }
     c->launches_build = launches;
@@ -617,12 +664,15 @@ static int solve_pass(mrcm_ctx* c, const double* q, const double* bc, bool with_
         TRYC(launch_leaf_particular(v, q, bc, with_sadj, s)); ++launches;
     }
     {
-        PhaseScope ps(c, MRCM_PHASE_TREE_SOLVE);
+        PhaseScope ps(c, MRCM_PHASE_TREE_UP);
         for (int h = 1; h <= P.height; ++h) {
             TRYC(launch_merge_up(v, P.level_first[h - 1], P.level_count[h - 1], P.level_max_g2[h - 1],
                                  P.level_max_m[h - 1], s));
             launches += P.level_max_m[h - 1] > 0;
         }
+    }
+    {
+        PhaseScope ps(c, MRCM_PHASE_TREE_DOWN);
         for (int h = P.height; h >= 1; --h) {
             TRYC(launch_merge_down(v, P.level_first[h - 1], P.level_count[h - 1], P.level_max_g2[h - 1],
                                    P.level_max_m[h - 1], s));
@@ -630,7 +680,7 @@ static int solve_pass(mrcm_ctx* c, const double* q, const double* bc, bool with_
         }
     }
     {
-        PhaseScope ps(c, MRCM_PHASE_LEAF_FINAL);
+        PhaseScope ps(c, MRCM_PHASE_LEAF_PRESSURE);
         TRYC(launch_leaf_pressure(v, accumulate, s)); ++launches;
         TRYC(launch_lam_to_PU(v, accumulate, s)); launches += P.nseg > 0;
     }
@@ -646,7 +696,8 @@ int mrcm_solve(mrcm_ctx* c, const double* q_dev, const double* bc_val_dev, doubl
     const DevView& v = c->v;
     cudaStream_t s = c->stream;
     int launches = 0;
-    for (int p = MRCM_PHASE_LEAF_PART; p < MRCM_PHASE_COUNT; ++p) c->ev_count[p] = 0;
+    // keep the build's event pairs, reuse the solve's
+    while (c->ev_used > 0 && c->ev_phase[c->ev_used - 1] >= MRCM_PHASE_LEAF_PART) --c->ev_used;
     TRYC(cudaMemsetAsync(v.status, 0, sizeof(int), s));
     const int steps = c->refine_steps, nres = steps + (c->refine_check ? 1 : 0);
     if (nres > 0) TRYC(cudaMemsetAsync(v.res_max, 0, sizeof(unsigned long long) * nres, s));
@@ -761,8 +812,10 @@ int mrcm_node_operator(mrcm_ctx* c, int node, double* R_host, double* rbar_host)
 
 int mrcm_enable_timing(mrcm_ctx* c, int on) {
     if (!c) return MRCM_ERR_INVALID_ARG;
-    if (on && !c->ev[0]) {
-        for (int k = 0; k < 2 * MRCM_PHASE_COUNT * kMaxOcc; ++k) TRYC(cudaEventCreate(&c->ev[k]));
+    if (on && c->ev.empty()) {
+        c->ev.assign(2 * kEventPairs, nullptr);
+        c->ev_phase.assign(kEventPairs, 0);
+        for (auto& e : c->ev) TRYC(cudaEventCreate(&e));
     }
     c->timing = on != 0;
     return MRCM_OK;
@@ -771,24 +824,30 @@ int mrcm_enable_timing(mrcm_ctx* c, int on) {
 int mrcm_phase_times(mrcm_ctx* c, double* ms) {
     if (!c || !ms) return MRCM_ERR_INVALID_ARG;
     TRYC(cudaStreamSynchronize(c->stream));
-    for (int p = 0; p < MRCM_PHASE_COUNT; ++p) {
-        ms[p] = 0.0;
-        if (!c->ev[0]) continue;
-        for (int o = 0; o < c->ev_count[p]; ++o) {
-            float t = 0.f;
-            const int slot = 2 * (p * kMaxOcc + o);
-            TRYC(cudaEventElapsedTime(&t, c->ev[slot], c->ev[slot + 1]));
-            ms[p] += t;
-        }
+    for (int p = 0; p < MRCM_PHASE_COUNT; ++p) ms[p] = 0.0;
+    for (int k = 0; k < c->ev_used; ++k) {
+        float t = 0.f;
+        TRYC(cudaEventElapsedTime(&t, c->ev[2 * k], c->ev[2 * k + 1]));
+        ms[c->ev_phase[k]] += t;
     }
+    return MRCM_OK;
+}
+
+int mrcm_phase_flops(const mrcm_ctx* c, double* flops) {
+    if (!c || !flops) return MRCM_ERR_INVALID_ARG;
+    const Plan& P = c->P;
+    const double passes = 1.0 + c->refine_steps;
+    for (int p = 0; p < MRCM_PHASE_COUNT; ++p) flops[p] = P.phase_build[p] + passes * P.phase_pass[p];
+    flops[MRCM_PHASE_RESIDUAL] = (c->refine_steps + (c->refine_check ? 1 : 0)) * P.residual_flops;
+    flops[MRCM_PHASE_FINISH] = P.finish_flops;
     return MRCM_OK;
 }
 
 void mrcm_destroy(mrcm_ctx* c) {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
-    for (int k = 0; k < 2 * MRCM_PHASE_COUNT * kMaxOcc; ++k)
-        if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+    for (cudaEvent_t e : c->ev)
+        if (e) cudaEventDestroy(e);
     for (void* p : c->allocs) cudaFree(p);
     delete c;
 }

@@ -184,11 +184,19 @@ cudaError_t launch_face_fluxes(const DevView& v, const double* bc_val, double* p
                                double* Fy, double* iface, cudaStream_t s);
 // zero-mean shift of the state's p and P (all-Neumann problems)
 cudaError_t launch_mean_shift(const DevView& v, cudaStream_t s);
+// Brackets each launch group of a phase (the phase ids of include/mrcm.h).
+struct PhaseHook {
+    void* ctx;
+    void (*begin)(void* ctx, int phase);
+    void (*end)(void* ctx, int phase);
+};
 // one tree height of merges; amax_bits: scratch of `count` entries;
 // *launches is increased by the number of kernels launched
 cudaError_t launch_merge_build(const DevView& v, int first, int count, int max_g2, int max_m,
-                               unsigned long long* amax_bits, cudaStream_t s, int* launches);
+                               unsigned long long* amax_bits, cudaStream_t s, int* launches,
+                               const PhaseHook& hook);
 bool merge_level_blocked(int count, int max_g2);
+constexpr int kMergePanel = 32;      // panel width of the blocked LU (flop model)
 cudaError_t launch_merge_up(const DevView& v, int first, int count, int max_g2, int max_m, cudaStream_t s);
 cudaError_t launch_merge_down(const DevView& v, int first, int count, int max_g2, int max_m, cudaStream_t s);
 
