@@ -16,4 +16,7 @@ Modules (each function cites the passage of the paper it follows):
   recursive  the CPU Recursive MRCM (Algorithm 1, Eqs. particular.1-2)
   brute      monolithic dense solve of Eqs. 11.2-14.2 on tiny grids
   counts     number of MMBFs per decomposition (Table ntmmbfs)
+  refine     double-double residual of Eqs. 11.2-14.2 and iterative
+             refinement of the discrete solution
+  dd         double-double helpers (TwoSum, Dekker's TwoProd)
 """
