@@ -185,11 +185,13 @@ int mrcm_plan_query(const mrcm_grid* g, const int sub_cells[3], const int seg_ce
 enum {
     MRCM_PHASE_COEF = 0,           /* permeability check, Robin and face coefficients */
     MRCM_PHASE_LEAF_BUILD = 1,     /* leaf factorisation and Robin-to-flux maps     */
-    MRCM_PHASE_MERGE_SMALL = 2,    /* fused merges of levels with many small nodes  */
-    MRCM_PHASE_LU_PANEL = 3,       /* blocked LU: panel factorisations              */
-    MRCM_PHASE_LU_UPDATE = 4,      /* blocked LU: U block rows and trailing updates */
-    MRCM_PHASE_MERGE_INVERSE = 5,  /* blocked merges: W = M^-1                      */
-    MRCM_PHASE_MERGE_PRODUCTS = 6, /* blocked merges: assembly, X = -W C, merged R  */
+    MRCM_PHASE_MERGE_SMALL = 2,    /* whole merges of small interface systems       */
+    MRCM_PHASE_GJ_SWEEP = 3,       /* blocked merges: Gauss-Jordan inversion of the
+                                      quasi-definite form                           */
+    MRCM_PHASE_MERGE_FORM = 4,     /* blocked merges: the quasi-definite form of the
+                                      interface matrix and its back transform       */
+    MRCM_PHASE_MERGE_X = 5,        /* blocked merges: X = -W C                      */
+    MRCM_PHASE_MERGE_R = 6,        /* blocked merges: merged R = R_oo + C^T X       */
     MRCM_PHASE_LEAF_PART = 7,      /* leaf particular solutions (solve)             */
     MRCM_PHASE_TREE_UP = 8,        /* up-sweep of the particular fluxes (solve)     */
     MRCM_PHASE_TREE_DOWN = 9,      /* down-sweep of the Robin data (solve)          */

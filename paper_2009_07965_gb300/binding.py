@@ -25,13 +25,13 @@ EXPORTS = ["mrcm_setup", "mrcm_plan_query", "mrcm_set_permeability", "mrcm_build
            "mrcm_node_info", "mrcm_node_segments", "mrcm_segment_info", "mrcm_node_operator",
            "mrcm_destroy", "mrcm_error_string", "mrcm_enable_timing", "mrcm_phase_times",
            "mrcm_merge_pair_noalloc", "mrcm_set_refinement", "mrcm_residual_history", "mrcm_phase_flops"]
-PHASES = ["coef", "leaf_build", "merge_small", "lu_panel", "lu_update", "merge_inverse", "merge_products",
+PHASES = ["coef", "leaf_build", "merge_small", "gj_sweep", "merge_form", "merge_x", "merge_r",
           "leaf_particular", "tree_up", "tree_down", "leaf_pressure", "residual", "finish"]
 # kernel family behind each phase (for reports)
 PHASE_KERNELS = {"coef": "face_coef_kernel", "leaf_build": "leaf_build_kernel",
-                 "merge_small": "merge_small_kernel", "lu_panel": "lu_panel_kernel",
-                 "lu_update": "lu_trsm_kernel+lu_gemm_kernel", "merge_inverse": "merge_inverse_kernel",
-                 "merge_products": "merge_assemble/x/rupdate_kernel", "leaf_particular": "leaf_particular_kernel",
+                 "merge_small": "merge_small_kernel", "gj_sweep": "gj_sweep_kernel",
+                 "merge_form": "merge_form_kernel+merge_backform_kernel", "merge_x": "merge_x_kernel",
+                 "merge_r": "merge_rupdate_kernel", "leaf_particular": "leaf_particular_kernel",
                  "tree_up": "merge_up_kernel", "tree_down": "merge_down_kernel",
                  "leaf_pressure": "leaf_pressure_kernel", "residual": "residual_cells/segments_kernel",
                  "finish": "face_flux_kernel"}

@@ -18,40 +18,54 @@
 // fluxes gives the node's own map (Eqs. new_bfs.1-2 / particular.1-2):
 //     R = blockdiag(R^a_oo, R^b_oo) + blockdiag(R^a_og, R^b_og) X,
 //     rbar = rbar_o + blockdiag(R^a_og, R^b_og) xbar.
-// The root has no outer segments; for an all-Neumann problem its system has
-// the constant null vector and the continuity row of gamma[0] is replaced by
-// P_{gamma[0]} = 0 (lambda^a + lambda^b = 0), keeping the difference row.
 //
-// Storage: M is factored in place, column-major (entry (r, c) at c*2g + r),
-// with partial pivoting organised in panels of kNB columns: at step k rows k
-// and piv[k] are exchanged in the columns of k's panel and to its right, so
-// the multipliers of earlier panels stay where they were computed.  A forward
-// solve therefore takes the panels in order: apply the panel's exchanges,
-// then eliminate its columns.  X is column-major too (2g x m).
+// Quasi-definite form.  M is symmetric but indefinite.  With the scaled
+// maps Rh^c = D^-1/2 R^c_gg D^-1/2 and the sum / difference variables
+//     s = (xh + yh) / sqrt2,  d = (yh - xh) / sqrt2,   xh = D^1/2 lambda^a, yh = D^1/2 lambda^b,
+// the system becomes T [d; s] = (scaled right-hand side) with
+//     T = [[A_d, E], [E, -A_s]],  A_d = 2I + (Rh^a + Rh^b)/2,
+//     A_s = -(Rh^a + Rh^b)/2,     E = (Rh^b - Rh^a)/2.
+// A Robin-to-flux map with this beta satisfies -2D < R <= 0 (each leaf's map
+// is B^T A^-1 B - W with W < 2D, and a merged map inherits the bound as the
+// map of the union), so A_d is positive definite and A_s positive
+// semidefinite: T is symmetric quasi-definite.  Its inverse is therefore
+// computed by Gauss-Jordan elimination without pivoting, d block first
+// (positive pivots, then the negative pivots of the Schur complement
+// -(A_s + E A_d^-1 E)); no pivot search sits on the sequential chain.  The
+// inverse is mapped back to W = M^-1 = D^-1/2 Q T^-1 Q^T D^-1/2 (Q the
+// orthogonal sum / difference transform).
 //
-// The build also forms W = M^-1 explicitly; X = -W C then exploits the block
-// structure of C, and every solve pass is a pair of matrix-vector products
-// per node instead of two triangular solves: M is symmetric (R^a, R^b
-// symmetric, D diagonal), so blockdiag(R_og) xbar = -C^T M^-1 rbar_gamma
-// = X^T rbar_gamma, giving the up-sweep rbar = rbar_o + X^T rbar_gamma, and
-// the down-sweep lambda_gamma = X lambda_o + W (-rbar_gamma).  Iterative
-// refinement (kernels_refine.cu) absorbs the different rounding of an
-// inverse-based solve.
+// The root of an all-Neumann problem has the constant null vector (s along
+// D^1/2 1, d = 0).  Its s block is regularised by -v v^T, v = D^1/2 1 / |D^1/2 1|:
+// for the consistent right-hand sides of such a problem the regularised
+// inverse returns the solution with v^T s = 0, and the final zero-mean shift
+// fixes the constant.
 //
-// Two launch shapes.  Levels with many nodes: one CTA per node, M in shared
-// memory (merge_small_kernel).  Levels with few, large nodes: a blocked
-// right-looking LU across many CTAs -- a panel kernel (NB columns, one CTA
-// per node), a TRSM kernel for the block row of U and a tiled FP64 GEMM for
-// the trailing update -- then W by column blocks, X and R by output tiles.
+// Every solve pass then is a pair of matrix-vector products per node: M is
+// symmetric, so blockdiag(R_og) xbar = -C^T M^-1 rbar_gamma = X^T rbar_gamma,
+// giving the up-sweep rbar = rbar_o + X^T rbar_gamma, and the down-sweep
+// lambda_gamma = X lambda_o + W (-rbar_gamma).  Iterative refinement
+// (kernels_refine.cu) absorbs the rounding of an inverse-based solve.
+//
+// Storage: W column-major per node (entry (r, c) at c*2g + r); X column-major
+// (2g x m).  Two launch shapes.  Levels with 2g <= 32: one group of 2g (padded
+// to a power of two) lanes per node does the whole merge in registers
+// (merge_small_kernel).  Larger systems: the form T is written into W, then a
+// blocked Gauss-Jordan sweep (block kGJ) across many CTAs, the back
+// transform, and X and R by output tiles.
 #include "mrcm_internal.h"
+
+#include <algorithm>
 
 namespace mrcm {
 namespace {
 
-constexpr int kNB = 32;         // panel width of the blocked LU
-constexpr int kGemmTile = 32;   // trailing-update tile (kGemmTile^2 outputs per CTA)
-constexpr int kXCols = 4;       // inverse columns per CTA
-constexpr int kRTile = 32;      // R update tile
+constexpr int kGJ = kMergeBlock; // block size of the blocked Gauss-Jordan sweep
+constexpr int kGJTile = 32;       // output tile of the blocked update (kGJTile^2 per CTA)
+constexpr int kSmallMax = 32;     // largest 2g merged by the per-node register kernel
+constexpr int kSmallThreads = 128;
+constexpr int kRTile = 32;       // R update tile
+constexpr double kTinyPivot = 1e-14;   // pivots of the scaled form are O(1)
 
 struct NodeRefs {
     int g, g2, m, o1, m1, m2;
@@ -71,536 +85,467 @@ __device__ __forceinline__ NodeRefs node_refs(const DevView& v, const MergeDesc&
     return r;
 }
 
-// Entry (r, c) of the interface matrix M (before the pinning rows).
-__device__ __forceinline__ double m_entry(const DevView& v, const MergeDesc& D, const NodeRefs& N, int r, int c) {
+__device__ __forceinline__ double gamma_D(const DevView& v, const MergeDesc& D, int i) {
+    return v.seg_D[v.gamma_segs[D.gamma_off + i]];
+}
+
+// Entry of T at (row r, column c), r, c in [0, 2g): d block first.  sd* =
+// D^-1/2 and sq* = D^1/2 of the two gamma segments, inv_sum = 1 / sum D for
+// the regularised all-Neumann root (0 otherwise).
+__device__ __forceinline__ double t_entry(const NodeRefs& N, int r, int c, double sdi, double sdj, double sqi,
+                                          double sqj, double inv_sum) {
     const int g = N.g;
-    if (r < g && c < g) {
-        double val = N.R1[N.gpos1[r] * N.m1 + N.gpos1[c]];
-        if (r == c) val += v.seg_D[v.gamma_segs[D.gamma_off + r]];
-        return val;
-    }
-    if (r >= g && c >= g) {
-        double val = N.R2[N.gpos2[r - g] * N.m2 + N.gpos2[c - g]];
-        if (r == c) val += v.seg_D[v.gamma_segs[D.gamma_off + r - g]];
-        return val;
-    }
-    if (r < g && c - g == r) return -v.seg_D[v.gamma_segs[D.gamma_off + r]];
-    if (r >= g && r - g == c) return -v.seg_D[v.gamma_segs[D.gamma_off + c]];
-    return 0.0;
+    const bool dr = r < g, dc = c < g;
+    const int i = dr ? r : r - g, j = dc ? c : c - g;
+    const double ra = N.R1[N.gpos1[i] * N.m1 + N.gpos1[j]] * sdi * sdj;
+    const double rb = N.R2[N.gpos2[i] * N.m2 + N.gpos2[j]] * sdi * sdj;
+    if (dr && dc) return 0.5 * (ra + rb) + (i == j ? 2.0 : 0.0);
+    if (!dr && !dc) return 0.5 * (ra + rb) - sqi * sqj * inv_sum;
+    return 0.5 * (rb - ra);
 }
 
-// Entry (r, c) of M with the all-Neumann pinning of the root applied:
-// row 0 <- (lambda^a + lambda^b of gamma[0]), row g <- row 0 - row g.
-__device__ __forceinline__ double m_entry_pinned(const DevView& v, const MergeDesc& D, const NodeRefs& N, int r,
-                                                 int c) {
-    if (D.pinned) {
-        if (r == 0) return (c == 0 || c == N.g) ? 1.0 : 0.0;
-        if (r == N.g) return m_entry(v, D, N, 0, c) - m_entry(v, D, N, N.g, c);
-    }
-    return m_entry(v, D, N, r, c);
-}
-
-// Entry (r, j) of C = blockdiag(R^a_go, R^b_go).
-__device__ __forceinline__ double c_entry(const NodeRefs& N, int r, int j) {
-    if (r < N.g && j < N.o1) return N.R1[N.gpos1[r] * N.m1 + N.opos1[j]];
-    if (r >= N.g && j >= N.o1) return N.R2[N.gpos2[r - N.g] * N.m2 + N.opos2[j - N.o1]];
-    return 0.0;
-}
-
-// R(i, j) = blockdiag(R_oo) + blockdiag(R_og) X, X column-major (2g x m).
-__device__ __forceinline__ double r_entry(const NodeRefs& N, const double* X, int i, int j) {
-    double acc = 0.0;
-    const double* xc = X + (long long)j * N.g2;
-    if (i < N.o1) {
-        const double* row = N.R1 + N.opos1[i] * N.m1;
-        if (j < N.o1) acc = row[N.opos1[j]];
-        for (int k = 0; k < N.g; ++k) acc += row[N.gpos1[k]] * xc[k];
-    } else {
-        const double* row = N.R2 + N.opos2[i - N.o1] * N.m2;
-        if (j >= N.o1) acc = row[N.opos2[j - N.o1]];
-        for (int k = 0; k < N.g; ++k) acc += row[N.gpos2[k]] * xc[N.g + k];
-    }
-    return acc;
-}
-
-template <int NT>
-__device__ __forceinline__ double block_max(double val, double* sv) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) val = fmax(val, __shfl_xor_sync(0xffffffffu, val, o));
-    if ((threadIdx.x & 31) == 0) sv[threadIdx.x >> 5] = val;
-    __syncthreads();
-    double mx = 0.0;
-    for (int w = 0; w < NT / 32; ++w) mx = fmax(mx, sv[w]);
-    __syncthreads();
-    return mx;
-}
-
-// One elimination step k on a column-major matrix M (ld = n): pivot search
-// in column k, exchange of rows k and p in columns [cstart, cend) (cstart =
-// first column of k's panel), scaling of the multipliers, rank-1 update of
-// columns (k, cend).  The pivot's reciprocal is formed once (thread 0) and
-// shared through *s_rcp.
-template <int NT>
-__device__ __forceinline__ void lu_step(double* M, int n, int k, int cstart, int cend, double thresh, int* piv,
-                                        double* dinv, double* sv, int* si, double* s_rcp, bool& singular) {
-    const int tid = threadIdx.x;
-    double best = -1.0;
-    int bi = k;
-    const double* col = M + (long long)k * n;
-    for (int i = k + tid; i < n; i += NT) {
-        const double a = fabs(col[i]);
-        if (a > best) { best = a; bi = i; }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const double ov = __shfl_down_sync(0xffffffffu, best, o);
-        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-    }
-    if ((tid & 31) == 0) { sv[tid >> 5] = best; si[tid >> 5] = bi; }
-    __syncthreads();
-    if (tid == 0) {
-        double bv = sv[0];
-        int b = si[0];
-        for (int w = 1; w < NT / 32; ++w)
-            if (sv[w] > bv || (sv[w] == bv && si[w] < b)) { bv = sv[w]; b = si[w]; }
-        piv[k] = b;
-        si[0] = b;
-        const double pivot = col[b];
-        if (!(fabs(pivot) > thresh)) singular = true;
-        *s_rcp = 1.0 / pivot;
-        dinv[k] = *s_rcp;
-    }
-    __syncthreads();
-    const int p = si[0];
-    if (p != k) {
-        for (int c = cstart + tid; c < cend; c += NT) {
-            double* cc = M + (long long)c * n;
-            const double a = cc[k];
-            cc[k] = cc[p];
-            cc[p] = a;
-        }
-        __syncthreads();
-    }
-    const double rcp = *s_rcp;
-    double* ck = M + (long long)k * n;
-    for (int i = k + 1 + tid; i < n; i += NT) ck[i] *= rcp;
-    __syncthreads();
-    const int rows = n - k - 1, cols = cend - k - 1;
-    for (int idx = tid; idx < rows * cols; idx += NT) {
-        const int i = k + 1 + idx % rows, c = k + 1 + idx / rows;
-        double* cc = M + (long long)c * n;
-        cc[i] -= ck[i] * cc[k];
-    }
-    __syncthreads();
+// Expected pivot sign of step k: positive on the d block, negative on s.
+__device__ __forceinline__ bool pivot_ok(double p, bool d_row) {
+    return d_row ? (p > kTinyPivot) : (p < -kTinyPivot);
 }
 
 // ---------------------------------------------------------------------------
-// Fused path: one CTA per node, M in shared memory.
-template <int NT>
-__global__ void __launch_bounds__(NT) merge_small_kernel(DevView v, int first) {
-    extern __shared__ __align__(16) double M[];
-    __shared__ double sv[NT / 32];
-    __shared__ int si[NT / 32];
-    __shared__ double s_rcp;
-    const MergeDesc D = v.merges[first + blockIdx.x];
+// Per-node register path: NP lanes per node (NP = padded 2g, a power of two
+// <= 32; d rows at lanes [0, NP/2), s rows at [NP/2, NP), padding rows carry
+// the identity).  Lane r holds row r of T in registers; step k broadcasts
+// row k by shuffles and updates every row (Gauss-Jordan, no pivoting).  Then
+// the lanes exchange their d / s partner rows to form the rows of W, compute
+// their rows of X = -W C, stage X in shared memory and form the merged R.
+template <int NP>
+__global__ void __launch_bounds__(kSmallThreads) merge_small_kernel(DevView v, int first, int count, int mstride) {
+    extern __shared__ __align__(16) double xs_all[];   // per node slot: B (g x m) and X (2g x m)
+    constexpr int H = NP / 2;
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int r = lane % NP, base = lane - r;
+    const int slot = threadIdx.x / NP;
+    const int q = blockIdx.x * (blockDim.x / NP) + slot;
+    const bool active = q < count;                     // uniform over the NP lanes
+    const MergeDesc D = v.merges[first + (active ? q : 0)];
     const NodeRefs N = node_refs(v, D);
-    const int g2 = N.g2, m = N.m;
-    const int tid = threadIdx.x;
-    int* piv = v.piv + D.piv_off;
-    double* X = v.X + D.X_off;
-    double amax = 0.0;
-    for (int idx = tid; idx < g2 * g2; idx += NT) {
-        const int r = idx % g2, c = idx / g2;
-        const double val = m_entry_pinned(v, D, N, r, c);
-        M[idx] = val;
-        amax = fmax(amax, fabs(val));
+    const int g = N.g, g2 = N.g2, m = N.m, o1 = N.o1;
+    double* xs = xs_all + (long long)slot * (H + NP) * mstride;   // B then X of this node
+    const bool d_row = r < H;
+    const int li = d_row ? r : r - H;
+    const bool real_r = active && li < g;
+    double sqd = 1.0;
+    if (real_r) sqd = sqrt(gamma_D(v, D, li));
+    const double sdi = 1.0 / sqd;
+    // sum of D over gamma (d lanes), for the regularised root
+    double sum = (d_row && real_r) ? sqd * sqd : 0.0;
+#pragma unroll
+    for (int o = NP / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(FULL, sum, o);
+    const double inv_sum = (active && D.pinned && sum > 0.0) ? 1.0 / sum : 0.0;
+
+    double row[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+        const double sdj = __shfl_sync(FULL, sdi, base + j);
+        const double sqj = __shfl_sync(FULL, sqd, base + j);
+        const int lj = j < H ? j : j - H;
+        double t = (j == r) ? 1.0 : 0.0;
+        if (real_r && lj < g)
+            t = t_entry(N, d_row ? li : g + li, j < H ? lj : g + lj, sdi, sdj, sqd, sqj, inv_sum);
+        row[j] = t;
     }
-    const double thresh = 1e-14 * block_max<NT>(amax, sv);
-    bool singular = false;
-    for (int k = 0; k < g2; ++k)
-        lu_step<NT>(M, g2, k, (k / kNB) * kNB, g2, thresh, piv, v.udinv + D.xb_off, sv, si, &s_rcp, singular);
-    if (singular && tid == 0) atomicOr(v.status, kStatusSingular);
-    // W = M^-1, one column per thread (per panel: exchanges, unit lower
-    // columns; then the upper triangle)
-    double* Wg = v.W + D.LU_off;
-    for (int j = tid; j < g2; j += NT) {
-        double* x = Wg + (long long)j * g2;
-        for (int i = 0; i < g2; ++i) x[i] = (i == j) ? 1.0 : 0.0;
-        for (int k0 = 0; k0 < g2; k0 += kNB) {
-            const int kend = min(k0 + kNB, g2);
-            for (int k = k0; k < kend; ++k) {
-                const int p = piv[k];
-                if (p != k) { const double a = x[p]; x[p] = x[k]; x[k] = a; }
-            }
-            for (int k = k0; k < kend; ++k) {
-                const double xk = x[k];
-                const double* ck = M + k * g2;
-                for (int i = k + 1; i < g2; ++i) x[i] -= ck[i] * xk;
-            }
-        }
-        for (int k = g2 - 1; k >= 0; --k) {
-            const double* ck = M + k * g2;
-            const double xk = x[k] / ck[k];
-            x[k] = xk;
-            for (int i = 0; i < k; ++i) x[i] -= ck[i] * xk;
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        double prow[NP];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) prow[j] = __shfl_sync(FULL, row[j], base + k);
+        const double p = prow[k];
+        const int lk = k < H ? k : k - H;
+        if (active && lk < g && r == 0 && !pivot_ok(p, k < H)) bad = true;
+        const double rp = 1.0 / p;
+        const bool me = (r == k);
+        const double c = me ? -rp : row[k] * rp;
+#pragma unroll
+        for (int j = 0; j < NP; ++j) row[j] = fma(-c, prow[j], me ? 0.0 : row[j]);
+        row[k] = me ? rp : -c;
+    }
+    if (bad) atomicOr(v.status, kStatusSingular);
+    // rows of W: lane (d, i) -> row lambda^a_i, lane (s, i) -> row lambda^b_i
+    double oth[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) oth[j] = __shfl_xor_sync(FULL, row[j], H);
+    double Wr[NP];            // Wr[j] = W(row, a_j), Wr[H + j] = W(row, b_j)
+    double* Wg = v.W + D.W_off;
+    const int wrow = d_row ? li : g + li;
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+        const double sdj = __shfl_sync(FULL, sdi, base + j);
+        const double zdd = d_row ? row[j] : oth[j];
+        const double zds = d_row ? row[H + j] : oth[H + j];
+        const double zsd = d_row ? oth[j] : row[j];
+        const double zss = d_row ? oth[H + j] : row[H + j];
+        const double sc = 0.5 * sdi * sdj;
+        double wa, wb;
+        if (d_row) { wa = (zdd - zds - zsd + zss) * sc; wb = (zss + zsd - zds - zdd) * sc; }
+        else       { wa = (zss + zds - zsd - zdd) * sc; wb = (zdd + zds + zsd + zss) * sc; }
+        Wr[j] = wa;
+        Wr[H + j] = wb;
+        if (real_r && j < g) {
+            Wg[(long long)j * g2 + wrow] = wa;
+            Wg[(long long)(g + j) * g2 + wrow] = wb;
         }
     }
-    __syncthreads();
-    // X = -W C: C is block diagonal, so column j uses one half of W
-    for (int idx = tid; idx < g2 * m; idx += NT) {
-        const int r = idx % g2, j = idx / g2;
+    // B = C = blockdiag(R^a_go, R^b_go) compacted to g x m (row k: gamma
+    // segment k of the child that owns column j), staged in shared memory
+    double* Bs = xs;                       // B(k, j) at Bs[k * mstride + j]
+    double* Xs = xs + H * mstride;         // X(row, j) at Xs[row * mstride + j]
+    if (active) {
+        for (int k = 0; k < g; ++k) {
+            const double* ra = N.R1 + N.gpos1[k] * N.m1;
+            const double* rb = N.R2 + N.gpos2[k] * N.m2;
+            for (int j = r; j < m; j += NP) Bs[k * mstride + j] = j < o1 ? ra[N.opos1[j]] : rb[N.opos2[j - o1]];
+        }
+    }
+    __syncwarp();
+    // X = -W B: this lane's row (columns of side a use W's a columns)
+    double* Xg = v.X + D.X_off;
+    for (int j = 0; j < m; ++j) {
+        const bool ja = j < o1;
         double acc = 0.0;
-        if (j < N.o1) {
-            const double* crow = N.R1 + N.opos1[j];
-            for (int k = 0; k < N.g; ++k) acc += Wg[(long long)k * g2 + r] * crow[N.gpos1[k] * N.m1];
-        } else {
-            const double* crow = N.R2 + N.opos2[j - N.o1];
-            for (int k = 0; k < N.g; ++k)
-                acc += Wg[(long long)(N.g + k) * g2 + r] * crow[N.gpos2[k] * N.m2];
+#pragma unroll
+        for (int k = 0; k < H; ++k)
+            if (k < g) acc = fma(ja ? Wr[k] : Wr[H + k], Bs[k * mstride + j], acc);
+        if (real_r) {
+            Xg[(long long)j * g2 + wrow] = -acc;
+            Xs[wrow * mstride + j] = -acc;
         }
-        X[idx] = -acc;
     }
-    __syncthreads();
+    __syncwarp();
+    if (!active) return;
+    // merged R = R_oo + B^T X (row i of side a uses the a rows of X)
     double* Rp = v.R + D.R_off;
-    for (int idx = tid; idx < m * m; idx += NT) Rp[idx] = r_entry(N, X, idx / m, idx % m);
+    for (int i = 0; i < m; ++i) {
+        const bool ia = i < o1;
+        const double* Rrow = ia ? N.R1 + N.opos1[i] * N.m1 : N.R2 + N.opos2[i - o1] * N.m2;
+        const double* xh = Xs + (ia ? 0 : g) * mstride;
+        for (int j = r; j < m; j += NP) {
+            double acc = 0.0;
+            if (ia && j < o1) acc = Rrow[N.opos1[j]];
+            if (!ia && j >= o1) acc = Rrow[N.opos2[j - o1]];
+            for (int k = 0; k < g; ++k) acc = fma(Bs[k * mstride + i], xh[k * mstride + j], acc);
+            Rp[(long long)i * m + j] = acc;
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
-// Blocked path.
-// Assembly of M (column-major, pinned rows applied).
-__global__ void __launch_bounds__(256) merge_assemble_kernel(DevView v, int first, unsigned long long* amax_bits) {
-    const int node = first + blockIdx.x;
-    const MergeDesc D = v.merges[node];
+// Blocked path.  T into the W storage of each node (column-major).
+__global__ void __launch_bounds__(256) merge_form_kernel(DevView v, int first) {
+    const MergeDesc D = v.merges[first + blockIdx.x];
     const NodeRefs N = node_refs(v, D);
-    const int g2 = N.g2, m = N.m;
-    double* M = v.LU + D.LU_off;
-    const long long nM = (long long)g2 * g2;
-    double amax = 0.0;
-    for (long long idx = blockIdx.y * 256LL + threadIdx.x; idx < nM; idx += (long long)gridDim.y * 256) {
+    const int g = N.g, g2 = N.g2;
+    double inv_sum = 0.0;
+    if (D.pinned) {
+        double s = 0.0;
+        for (int i = 0; i < g; ++i) s += gamma_D(v, D, i);
+        inv_sum = s > 0.0 ? 1.0 / s : 0.0;
+    }
+    double* T = v.W + D.W_off;
+    const long long nT = (long long)g2 * g2;
+    for (long long idx = blockIdx.y * 256LL + threadIdx.x; idx < nT; idx += (long long)gridDim.y * 256) {
         const int r = (int)(idx % g2), c = (int)(idx / g2);
-        const double val = m_entry_pinned(v, D, N, r, c);
-        M[idx] = val;
-        amax = fmax(amax, fabs(val));
+        const double di = gamma_D(v, D, r < g ? r : r - g), dj = gamma_D(v, D, c < g ? c : c - g);
+        const double sqi = sqrt(di), sqj = sqrt(dj);
+        T[idx] = t_entry(N, r, c, 1.0 / sqi, 1.0 / sqj, sqi, sqj, inv_sum);
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-    if ((threadIdx.x & 31) == 0 && amax > 0.0)
-        atomicMax(amax_bits + (node - first), (unsigned long long)__double_as_longlong(amax));
 }
 
-// Panel factorisation of columns [k0, k0+NB) (rows k0..2g-1), one CTA per
-// node; the panel is staged in shared memory when it fits (smem_rows).
-template <int NT>
-__global__ void __launch_bounds__(NT) lu_panel_kernel(DevView v, int first, int k0,
-                                                      const unsigned long long* amax_bits, int smem_rows) {
-    extern __shared__ __align__(16) double Ps[];
-    __shared__ unsigned long long skey[NT / 32];
-    __shared__ int si[NT / 32];
-    __shared__ int s_p;
-    __shared__ double s_rcp;
-    __shared__ double prow[kNB], krow[kNB];
-    const MergeDesc D = v.merges[first + blockIdx.x];
-    const int g2 = 2 * D.g;
-    if (k0 >= g2) return;
-    const int nb = min(kNB, g2 - k0), rows = g2 - k0;
-    double* Mg = v.LU + D.LU_off;
-    int* piv = v.piv + D.piv_off;
-    double* dinv = v.udinv + D.xb_off;
+// Scratch of the blocked sweep, per node: two buffers for the inverse P of
+// a diagonal block (kGJ x kGJ, row-major; step k uses buffer k & 1), then
+// the previous column block (2g x kGJ, column-major).
+constexpr int kGJScratchHead = 2 * kGJ * kGJ;
+__device__ __forceinline__ double* gj_scratch(double* scratch, int slot, int nmax) {
+    return scratch + (long long)slot * (kGJScratchHead + (long long)nmax * kGJ);
+}
+
+struct GJSmem {
+    double Cs[kGJ][kGJTile + 1];    // old column block rows of a tile: Cs[c][i]
+    double Bs[kGJ][kGJTile + 1];    // block row of a tile (or P on the block columns)
+    double Ps[kGJ][kGJ + 1];        // a diagonal block being inverted
+    double rp;
+};
+
+// Inverse of a kGJ x kGJ block held in shared memory (Ps[r][c], identity
+// padding beyond nb), in place, by the whole CTA: Gauss-Jordan without
+// pivoting, one entry per thread and step; thread 0 forms each pivot's
+// reciprocal (one FP64 division per step for the CTA).  d_rows: rows of the
+// block that lie in the d part (positive pivots expected).  Returns false
+// (thread 0) on a pivot of the wrong sign or size.
+__device__ bool gj_invert_block(double (*Ps)[kGJ + 1], int nb, int d_rows, double* s_rp) {
+    const int tid = threadIdx.x, pr = tid / kGJ, pc = tid % kGJ;
+    bool ok = true;
+    for (int kk = 0; kk < kGJ; ++kk) {
+        if (tid == 0) {
+            const double p = Ps[kk][kk];
+            if (kk < nb && !pivot_ok(p, kk < d_rows)) ok = false;
+            *s_rp = 1.0 / p;
+        }
+        __syncthreads();
+        const double rp = *s_rp, a_rk = Ps[pr][kk], a_kc = Ps[kk][pc], a = Ps[pr][pc];
+        __syncthreads();
+        double nv;
+        if (pr == kk) nv = (pc == kk) ? rp : a_kc * rp;
+        else nv = (pc == kk) ? -a_rk * rp : fma(-a_rk * rp, a_kc, a);
+        Ps[pr][pc] = nv;
+        __syncthreads();
+    }
+    return ok;
+}
+
+// Block step at k0, part 1, for one (node, column tile of kGJRowTile): the
+// block row A_Kj <- P A_Kj on its columns, and a copy of its rows of the
+// column block A_iK before part 2 overwrites it.
+constexpr int kGJRowTile = 16;
+__device__ void gj_panel_item(const DevView& v, const MergeDesc& D, int slot, int c0, int k0, double* scratch,
+                              int nmax, GJSmem& S) {
+    const int N = 2 * D.g;
+    const int nb = min(kGJ, N - k0);
+    double* A = v.W + D.W_off;
+    double* sc = gj_scratch(scratch, slot, nmax);
+    const double* Pg = sc + ((k0 / kGJ) & 1) * kGJ * kGJ;
+    double* colblk = sc + kGJScratchHead;
     const int tid = threadIdx.x;
-    const bool staged = rows <= smem_rows;
-    // shared memory: the multipliers of one step (rows), then the staged panel
-    double* lmul = Ps;
-    double* P = staged ? Ps + rows : Mg + (long long)k0 * g2 + k0;   // entry (i, c) at P[c * ld + i]
-    const int ld = staged ? rows : g2;
-    if (staged) {
-        for (int idx = tid; idx < rows * nb; idx += NT) {
-            const int i = idx % rows, c = idx / rows;
-            P[idx] = Mg[(long long)(k0 + c) * g2 + k0 + i];
-        }
-        __syncthreads();
+    // rows [c0, c0 + kGJRowTile) of the column block, outside the block rows
+    for (int idx = tid; idx < kGJRowTile * kGJ; idx += 256) {
+        const int i = c0 + idx % kGJRowTile, cc = idx / kGJRowTile;
+        if (i < N && cc < nb && (i < k0 || i >= k0 + nb))
+            colblk[(long long)cc * N + i] = __ldcg(A + (long long)(k0 + cc) * N + i);
     }
-    const double thresh = 1e-14 * __longlong_as_double((long long)amax_bits[blockIdx.x]);
-    bool singular = false;
-    for (int kk = 0; kk < nb; ++kk) {
-        // pivot search on the bit patterns of |a| (ordered like the values)
-        unsigned long long best = 0ull;
-        int bi = kk;
-        const double* col = P + (long long)kk * ld;
-        for (int i = kk + tid; i < rows; i += NT) {
-            const unsigned long long a = (unsigned long long)__double_as_longlong(col[i]) & 0x7fffffffffffffffull;
-            if (a > best || (a == best && i < bi)) { best = a; bi = i; }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long ov = __shfl_down_sync(0xffffffffu, best, o);
-            const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-            if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-        }
-        if ((tid & 31) == 0) { skey[tid >> 5] = best; si[tid >> 5] = bi; }
-        __syncthreads();
-        if (tid < 32) {
-            unsigned long long kv = tid < NT / 32 ? skey[tid] : 0ull;
-            int ki = tid < NT / 32 ? si[tid] : 0x7fffffff;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const unsigned long long ov = __shfl_down_sync(0xffffffffu, kv, o);
-                const int oi = __shfl_down_sync(0xffffffffu, ki, o);
-                if (ov > kv || (ov == kv && oi < ki)) { kv = ov; ki = oi; }
-            }
-            ki = __shfl_sync(0xffffffffu, ki, 0);
-            // the pivot row (old row p) and the old row kk, all panel columns
-            if (tid < nb) {
-                prow[tid] = P[(long long)tid * ld + ki];
-                krow[tid] = P[(long long)tid * ld + kk];
-            }
-            if (tid == 0) {
-                const double pivot = P[(long long)kk * ld + ki];
-                const double rcp = 1.0 / pivot;          // one warp: FP64 issue slots are scarce
-                if (!(fabs(pivot) > thresh)) singular = true;
-                s_rcp = rcp;
-                s_p = ki;
-                piv[k0 + kk] = k0 + ki;
-                dinv[k0 + kk] = rcp;
-            }
-        }
-        __syncthreads();
-        const int p = s_p;
-        const double rcp = s_rcp;
-        const int nr = rows - kk - 1;
-        // multipliers, one lane per row (dense warps)
-        for (int r = tid; r < nr; r += NT) {
-            const int i = kk + 1 + r;
-            lmul[r] = (i == p ? krow[kk] : col[i]) * rcp;
-        }
-        if (tid < nb) P[(long long)tid * ld + kk] = prow[tid];       // row kk <- pivot row
-        __syncthreads();
-        // rank-1 update of columns kk+1.., (row, column) pairs over all lanes;
-        // row p takes the old row kk's values, its multipliers included
-        const int ncu = nb - kk - 1;
-        for (int idx = tid; idx < nr * ncu; idx += NT) {
-            const int r = idx % nr, i = kk + 1 + r, c = kk + 1 + idx / nr;
-            const double a = (i == p) ? krow[c] : P[(long long)c * ld + i];
-            P[(long long)c * ld + i] = a - lmul[r] * prow[c];
-        }
-        for (int r = tid; r < nr; r += NT) P[(long long)kk * ld + kk + 1 + r] = lmul[r];
-        if (p > kk)
-            for (int c = tid; c < kk; c += NT) P[(long long)c * ld + p] = krow[c];
-        __syncthreads();
-    }
-    if (singular && tid == 0) atomicOr(v.status, kStatusSingular);
-    if (staged) {
-        for (int idx = tid; idx < rows * nb; idx += NT) {
-            const int i = idx % rows, c = idx / rows;
-            Mg[(long long)(k0 + c) * g2 + k0 + i] = P[idx];
-        }
-    }
-}
-
-// Block row of U: the panel's exchanges applied to columns [kend, 2g) (as one
-// composed permutation of the touched rows), then U12 = L11^-1 A12 with one
-// warp per column (lane r holds row k0 + r).
-constexpr int kTrsmWarps = 8;
-__global__ void __launch_bounds__(32 * kTrsmWarps) lu_trsm_kernel(DevView v, int first, int k0) {
-    __shared__ double L11[kNB][kNB + 1];
-    __shared__ int rows_touched[2 * kNB];
-    __shared__ int src_row[2 * kNB];
-    __shared__ int n_touched;
-    const MergeDesc D = v.merges[first + blockIdx.x];
-    const int g2 = 2 * D.g;
-    const int kend = min(k0 + kNB, g2);
-    if (kend >= g2 || kend + (int)blockIdx.y * kTrsmWarps >= g2) return;   // uniform per CTA
-    double* M = v.LU + D.LU_off;
-    const int* piv = v.piv + D.piv_off;
-    const int nb = kend - k0;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int idx = tid; idx < kNB * kNB; idx += 32 * kTrsmWarps) {
-        const int r = idx % kNB, c = idx / kNB;
-        L11[r][c] = (r < nb && c < nb) ? M[(long long)(k0 + c) * g2 + k0 + r] : 0.0;
-    }
-    if (tid == 0) {
-        // rows touched by the exchanges and, after all of them, the original
-        // row whose value each touched row holds
-        int n = 0;
-        for (int c = 0; c < nb; ++c) { rows_touched[n] = k0 + c; src_row[n] = k0 + c; ++n; }
-        for (int c = 0; c < nb; ++c) {
-            const int p = piv[k0 + c];
-            int ip = -1;
-            for (int q = 0; q < n; ++q) if (rows_touched[q] == p) ip = q;
-            if (ip < 0) { rows_touched[n] = p; src_row[n] = p; ip = n; ++n; }
-            const int t = src_row[c];
-            src_row[c] = src_row[ip];
-            src_row[ip] = t;
-        }
-        n_touched = n;
+    // block row on columns [c0, c0 + kGJRowTile) outside the diagonal block;
+    // P staged in Cs (row-major kGJ x kGJ)
+    double* Ps = &S.Cs[0][0];
+    for (int idx = tid; idx < kGJ * kGJ; idx += 256) Ps[idx] = __ldcg(Pg + idx);
+    for (int idx = tid; idx < kGJ * kGJRowTile; idx += 256) {
+        const int cc = idx % kGJ, jj = idx / kGJ, j = c0 + jj;
+        S.Bs[cc][jj] = (cc < nb && j < N && (j < k0 || j >= k0 + nb)) ? __ldcg(A + (long long)j * N + k0 + cc) : 0.0;
     }
     __syncthreads();
-    const int j = kend + blockIdx.y * kTrsmWarps + warp;
-    if (j >= g2) return;
-    double* col = M + (long long)j * g2;
-    const int nt = n_touched;
-    double g0 = lane < nt ? col[src_row[lane]] : 0.0;
-    double g1 = lane + 32 < nt ? col[src_row[lane + 32]] : 0.0;
-    __syncwarp();
-    if (lane < nt) col[rows_touched[lane]] = g0;
-    if (lane + 32 < nt) col[rows_touched[lane + 32]] = g1;
-    __syncwarp();
-    double u = lane < nb ? col[k0 + lane] : 0.0;
-    for (int c = 0; c < nb; ++c) {
-        const double xc = __shfl_sync(0xffffffffu, u, c);
-        if (lane > c && lane < nb) u -= L11[lane][c] * xc;
+    for (int idx = tid; idx < kGJ * kGJRowTile; idx += 256) {
+        const int rr = idx % kGJ, jj = idx / kGJ, j = c0 + jj;
+        if (rr >= nb || j >= N || (j >= k0 && j < k0 + nb)) continue;
+        double acc0 = 0.0, acc1 = 0.0;
+#pragma unroll
+        for (int cc = 0; cc < kGJ; cc += 2) {
+            acc0 = fma(Ps[rr * kGJ + cc], S.Bs[cc][jj], acc0);
+            acc1 = fma(Ps[rr * kGJ + cc + 1], S.Bs[cc + 1][jj], acc1);
+        }
+        A[(long long)j * N + k0 + rr] = acc0 + acc1;
     }
-    if (lane < nb) col[k0 + lane] = u;
+    __syncthreads();
 }
 
-// Trailing update A22 -= L21 U12 on kGemmTile^2 tiles; 256 threads, 2x2 each.
-__global__ void __launch_bounds__(256) lu_gemm_kernel(DevView v, int first, int k0) {
-    __shared__ double Ls[kNB][kGemmTile + 1];   // Ls[c][r]
-    __shared__ double Us[kNB][kGemmTile + 1];   // Us[c][j]
-    const MergeDesc D = v.merges[first + blockIdx.x];
-    const int g2 = 2 * D.g;
-    const int kend = min(k0 + kNB, g2);
-    const int nb = kend - k0;
-    const int rest = g2 - kend;
-    const int tiles = (rest + kGemmTile - 1) / kGemmTile;
-    if (rest <= 0 || (int)blockIdx.y >= tiles * tiles) return;   // uniform per CTA
-    const int r0 = kend + (blockIdx.y % tiles) * kGemmTile;
-    const int j0 = kend + (blockIdx.y / tiles) * kGemmTile;
-    double* M = v.LU + D.LU_off;
+// Block step at k0, part 2, for one (node, kGJTile^2 output tile): rows
+// outside the block rows, A_ij <- A_ij - A_iK A_Kj (new block row) and
+// A_iK <- -A_iK P; the diagonal block <- P.  The next diagonal block is
+// left to gj_next_diag_item.
+__device__ void gj_update_item(const DevView& v, const MergeDesc& D, int slot, int r0, int c0, int k0,
+                               double* scratch, int nmax, GJSmem& S) {
+    const int N = 2 * D.g;
+    const int nb = min(kGJ, N - k0);
+    const int k1 = k0 + kGJ;                      // next diagonal block [k1, k1 + nb1)
+    double* A = v.W + D.W_off;
+    double* sc = gj_scratch(scratch, slot, nmax);
+    const double* Pg = sc + ((k0 / kGJ) & 1) * kGJ * kGJ;
+    const double* colblk = sc + kGJScratchHead;
     const int tid = threadIdx.x;
-    for (int idx = tid; idx < kNB * kGemmTile; idx += 256) {
-        const int r = idx % kGemmTile, c = idx / kGemmTile;
-        Ls[c][r] = (c < nb && r0 + r < g2) ? M[(long long)(k0 + c) * g2 + r0 + r] : 0.0;
-    }
-    for (int idx = tid; idx < kNB * kGemmTile; idx += 256) {
-        const int c = idx % kNB, jj = idx / kNB;
-        Us[c][jj] = (c < nb && j0 + jj < g2) ? M[(long long)(j0 + jj) * g2 + k0 + c] : 0.0;
+    for (int idx = tid; idx < kGJ * kGJTile; idx += 256) {
+        const int ii = idx % kGJTile, cc = idx / kGJTile, i = r0 + ii;
+        S.Cs[cc][ii] = (cc < nb && i < N && (i < k0 || i >= k0 + nb)) ? __ldcg(colblk + (long long)cc * N + i) : 0.0;
+        const int jj = idx % kGJTile, j = c0 + jj;
+        double b = 0.0;
+        if (cc < nb && j < N)
+            b = (j >= k0 && j < k0 + nb) ? __ldcg(Pg + cc * kGJ + (j - k0)) : __ldcg(A + (long long)j * N + k0 + cc);
+        S.Bs[cc][jj] = b;
     }
     __syncthreads();
-    constexpr int TS = kGemmTile / 16;                // outputs per thread per dimension
-    const int tr = (tid % 16) * TS, tc = (tid / 16) * TS;
-    double acc[TS][TS];
+    const int tr = (tid % 16) * 2, tc = (tid / 16) * 2;
+    double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
 #pragma unroll
-    for (int a = 0; a < TS; ++a)
-#pragma unroll
-        for (int b = 0; b < TS; ++b) acc[a][b] = 0.0;
-#pragma unroll 8
-    for (int c = 0; c < kNB; ++c) {
-        double lv[TS], uv[TS];
-#pragma unroll
-        for (int a = 0; a < TS; ++a) { lv[a] = Ls[c][tr + a]; uv[a] = Us[c][tc + a]; }
-#pragma unroll
-        for (int a = 0; a < TS; ++a)
-#pragma unroll
-            for (int b = 0; b < TS; ++b) acc[a][b] += lv[a] * uv[b];
+    for (int cc = 0; cc < kGJ; ++cc) {
+        const double l0 = S.Cs[cc][tr], l1 = S.Cs[cc][tr + 1];
+        const double u0 = S.Bs[cc][tc], u1 = S.Bs[cc][tc + 1];
+        acc[0][0] = fma(l0, u0, acc[0][0]);
+        acc[0][1] = fma(l0, u1, acc[0][1]);
+        acc[1][0] = fma(l1, u0, acc[1][0]);
+        acc[1][1] = fma(l1, u1, acc[1][1]);
     }
 #pragma unroll
-    for (int b = 0; b < TS; ++b) {
-        const int j = j0 + tc + b;
-        if (j >= g2) continue;
-        double* col = M + (long long)j * g2;
+    for (int b = 0; b < 2; ++b) {
+        const int j = c0 + tc + b;
+        if (j >= N) continue;
+        const bool jK = j >= k0 && j < k0 + nb;
+        const bool jK1 = j >= k1 && j < k1 + kGJ;
+        double* col = A + (long long)j * N;
 #pragma unroll
-        for (int a = 0; a < TS; ++a) {
-            const int r = r0 + tr + a;
-            if (r < g2) col[r] -= acc[a][b];
+        for (int a = 0; a < 2; ++a) {
+            const int i = r0 + tr + a;
+            if (i >= N) continue;
+            const bool iK = i >= k0 && i < k0 + nb;
+            if (iK) {
+                if (jK) col[i] = S.Bs[i - k0][tc + b];
+            } else if (!(jK1 && i >= k1 && i < k1 + kGJ)) {
+                col[i] = (jK ? 0.0 : __ldcg(col + i)) - acc[a][b];
+            }
         }
     }
+    __syncthreads();
 }
 
-// W = M^-1 for kXCols columns per CTA (identity columns staged in shared
-// memory).  Blocked like the factorisation: per 32-row block, warp j solves
-// the diagonal block for column j with shuffles (block rows preloaded into
-// registers), then every thread updates one remaining row for all columns.
-__global__ void __launch_bounds__(32 * kXCols) merge_inverse_kernel(DevView v, int first) {
-    extern __shared__ __align__(16) double xs[];   // kXCols x 2g
-    const MergeDesc D = v.merges[first + blockIdx.x];
-    const int g2 = 2 * D.g;
-    const int j0 = blockIdx.y * kXCols;
-    if (j0 >= g2) return;                             // uniform per CTA
-    const int nc = min(kXCols, g2 - j0);
-    const double* M = v.LU + D.LU_off;
-    const int* piv = v.piv + D.piv_off;
-    const double* dinv = v.udinv + D.xb_off;
-    double* X = v.W + D.LU_off;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    constexpr int NT = 32 * kXCols;
-    for (int idx = tid; idx < nc * g2; idx += NT) xs[idx] = (idx % g2 == j0 + idx / g2) ? 1.0 : 0.0;
+// Block step at k0, part 2, for the next diagonal block [k1, k1 + nb1) of a
+// node (k1 = k0 + kGJ < 2g): its update A -= A_iK A_Kj, then its inverse
+// into the other P buffer, so that part 1 of the next step finds P ready
+// (look-ahead; this item runs beside the tile updates).  Returns false on a
+// bad pivot.
+__device__ bool gj_next_diag_item(const DevView& v, const MergeDesc& D, int slot, int k0, double* scratch, int nmax,
+                                  GJSmem& S) {
+    const int N = 2 * D.g;
+    const int nb = min(kGJ, N - k0);
+    const int k1 = k0 + kGJ, nb1 = min(kGJ, N - k1);
+    double* A = v.W + D.W_off;
+    double* sc = gj_scratch(scratch, slot, nmax);
+    const double* colblk = sc + kGJScratchHead;
+    const int tid = threadIdx.x, pr = tid / kGJ, pc = tid % kGJ;
+    // Cs[c][r]: column block rows k1 + r; Bs[c][j]: new block row columns k1 + j
+    {
+        const int cc = tid / kGJ, rr = tid % kGJ;
+        S.Cs[cc][rr] = (cc < nb && rr < nb1) ? __ldcg(colblk + (long long)cc * N + k1 + rr) : 0.0;
+        S.Bs[cc][rr] = (cc < nb && rr < nb1) ? __ldcg(A + (long long)(k1 + rr) * N + k0 + cc) : 0.0;
+    }
     __syncthreads();
-    // forward: per panel, its exchanges, the unit lower diagonal block, then
-    // the rows below
-    for (int k0 = 0; k0 < g2; k0 += kNB) {
-        const int nb = min(kNB, g2 - k0);
-        if (warp < nc) {
-            double* x = xs + warp * g2;
-            double Lr[kNB];
+    double acc = 0.0;
 #pragma unroll
-            for (int c = 0; c < kNB; ++c)
-                Lr[c] = (c < nb && lane < nb) ? M[(long long)(k0 + c) * g2 + k0 + lane] : 0.0;
-            if (lane == 0) {
-                for (int k = k0; k < k0 + nb; ++k) {
-                    const int p = piv[k];
-                    if (p != k) { const double a = x[p]; x[p] = x[k]; x[k] = a; }
-                }
+    for (int cc = 0; cc < kGJ; ++cc) acc = fma(S.Cs[cc][pr], S.Bs[cc][pc], acc);
+    double val = (pr == pc) ? 1.0 : 0.0;
+    if (pr < nb1 && pc < nb1) {
+        double* at = A + (long long)(k1 + pc) * N + k1 + pr;
+        val = __ldcg(at) - acc;
+        *at = val;
+    }
+    S.Ps[pr][pc] = val;
+    __syncthreads();
+    const bool ok = gj_invert_block(S.Ps, nb1, D.g - k1, &S.rp);
+    double* Pn = sc + ((k1 / kGJ) & 1) * kGJ * kGJ;
+    Pn[pr * kGJ + pc] = S.Ps[pr][pc];
+    __syncthreads();
+    return ok;
+}
+
+// Grid-wide barrier of a cooperative launch: a monotonic arrival counter
+// (reset before the launch); round n ends when it reaches (n + 1) * grid.
+// Data written by other CTAs before a barrier is read after it with L2-only
+// loads (__ldcg).  Every wait is bounded (about a second); a CTA that gives
+// up sets kStatusTimeout and the caller returns.
+constexpr long long kBarrierSpins = 5000000;
+
+__device__ bool grid_barrier(unsigned int* counter, unsigned int& round, int* status) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned int target = (round + 1) * gridDim.x;
+        __threadfence();
+        atomicAdd(counter, 1u);
+        volatile unsigned int* vc = counter;
+        long long spins = 0;
+        while (*vc < target) {
+            if (++spins > kBarrierSpins) {
+                ok = 0;
+                atomicOr(status, kStatusTimeout);
+                break;
             }
-            __syncwarp();
-            double val = lane < nb ? x[k0 + lane] : 0.0;
-#pragma unroll
-            for (int c = 0; c < kNB; ++c) {
-                const double xc = __shfl_sync(0xffffffffu, val, c);
-                if (lane > c) val -= Lr[c] * xc;
-            }
-            if (lane < nb) x[k0 + lane] = val;
         }
+        __threadfence();
+        s_ok = ok;
+    }
+    ++round;
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// The whole blocked Gauss-Jordan sweep of one tree height in one cooperative
+// launch: the first diagonal block of every node, then per block step part
+// 1 over (node, column tile) items, a grid barrier, part 2 over the nodes'
+// next diagonal blocks and their (node, output tile) items, a grid barrier.
+__global__ void __launch_bounds__(256) gj_sweep_kernel(DevView v, int first, int count, int nmax, double* scratch,
+                                                       unsigned int* counter) {
+    __shared__ GJSmem S;
+    __shared__ int s_bad;
+    const int rtiles = (nmax + kGJRowTile - 1) / kGJRowTile;
+    const int tiles = (nmax + kGJTile - 1) / kGJTile;
+    const int tid = threadIdx.x, pr = tid / kGJ, pc = tid % kGJ;
+    unsigned int round = 0;
+    if (tid == 0) s_bad = 0;
+    __syncthreads();
+    for (int q = blockIdx.x; q < count; q += gridDim.x) {
+        const MergeDesc D = v.merges[first + q];
+        const int N = 2 * D.g, nb = min(kGJ, N);
+        const double* A = v.W + D.W_off;
+        S.Ps[pr][pc] = (pr < nb && pc < nb) ? __ldcg(A + (long long)pc * N + pr) : (pr == pc ? 1.0 : 0.0);
         __syncthreads();
-        for (int i = k0 + nb + tid; i < g2; i += NT) {
-            double Li[kNB];
-#pragma unroll
-            for (int c = 0; c < kNB; ++c) Li[c] = c < nb ? M[(long long)(k0 + c) * g2 + i] : 0.0;
-            for (int j = 0; j < nc; ++j) {
-                const double* x = xs + j * g2 + k0;
-                double acc = 0.0;
-#pragma unroll
-                for (int c = 0; c < kNB; ++c) acc += Li[c] * (c < nb ? x[c] : 0.0);
-                xs[j * g2 + i] -= acc;
-            }
-        }
+        if (!gj_invert_block(S.Ps, nb, D.g, &S.rp)) s_bad = 1;
+        gj_scratch(scratch, q, nmax)[pr * kGJ + pc] = S.Ps[pr][pc];
         __syncthreads();
     }
-    // backward: U with the reciprocals of its diagonal, blocks from the bottom
-    for (int blk = (g2 - 1) / kNB; blk >= 0; --blk) {
-        const int k0 = blk * kNB, nb = min(kNB, g2 - k0);
-        if (warp < nc) {
-            double* x = xs + warp * g2;
-            double Ur[kNB];
-#pragma unroll
-            for (int c = 0; c < kNB; ++c)
-                Ur[c] = (c < nb && lane < nb) ? M[(long long)(k0 + c) * g2 + k0 + lane] : 0.0;
-            const double dl = lane < nb ? dinv[k0 + lane] : 0.0;
-            double val = lane < nb ? x[k0 + lane] : 0.0;
-#pragma unroll
-            for (int c = kNB - 1; c >= 0; --c) {
-                if (lane == c) val *= dl;
-                const double xc = __shfl_sync(0xffffffffu, val, c);
-                if (lane < c) val -= Ur[c] * xc;
-            }
-            if (lane < nb) x[k0 + lane] = val;
+    if (!grid_barrier(counter, round, v.status)) return;
+    for (int k0 = 0; k0 < nmax; k0 += kGJ) {
+        for (int item = blockIdx.x; item < count * rtiles; item += gridDim.x) {
+            const int q = item / rtiles, c0 = (item % rtiles) * kGJRowTile;
+            const MergeDesc D = v.merges[first + q];
+            if (k0 >= 2 * D.g || c0 >= 2 * D.g) continue;     // uniform per CTA
+            gj_panel_item(v, D, q, c0, k0, scratch, nmax, S);
         }
-        __syncthreads();
-        for (int i = tid; i < k0; i += NT) {
-            double Ui[kNB];
-#pragma unroll
-            for (int c = 0; c < kNB; ++c) Ui[c] = c < nb ? M[(long long)(k0 + c) * g2 + i] : 0.0;
-            for (int j = 0; j < nc; ++j) {
-                const double* x = xs + j * g2 + k0;
-                double acc = 0.0;
-#pragma unroll
-                for (int c = 0; c < kNB; ++c) acc += Ui[c] * (c < nb ? x[c] : 0.0);
-                xs[j * g2 + i] -= acc;
+        if (!grid_barrier(counter, round, v.status)) return;
+        // items [0, count): next diagonal blocks; then the output tiles
+        for (int item = blockIdx.x; item < count * (1 + tiles * tiles); item += gridDim.x) {
+            if (item < count) {
+                const MergeDesc D = v.merges[first + item];
+                if (k0 + kGJ >= 2 * D.g) continue;
+                if (!gj_next_diag_item(v, D, item, k0, scratch, nmax, S)) s_bad = 1;
+                continue;
             }
+            const int it = item - count;
+            const int q = it / (tiles * tiles), t = it % (tiles * tiles);
+            const int r0 = (t % tiles) * kGJTile, c0 = (t / tiles) * kGJTile;
+            const MergeDesc D = v.merges[first + q];
+            if (k0 >= 2 * D.g || r0 >= 2 * D.g || c0 >= 2 * D.g) continue;
+            gj_update_item(v, D, q, r0, c0, k0, scratch, nmax, S);
         }
-        __syncthreads();
+        if (!grid_barrier(counter, round, v.status)) return;
     }
-    for (int idx = tid; idx < nc * g2; idx += NT) X[(long long)j0 * g2 + idx] = xs[idx];
+    __syncthreads();
+    if (tid == 0 && s_bad) atomicOr(v.status, kStatusSingular);
+}
+
+// T^-1 -> W = D^-1/2 Q T^-1 Q^T D^-1/2, in place (one thread per 2 x 2 block
+// pattern (i, j), i, j < g).
+__global__ void __launch_bounds__(256) merge_backform_kernel(DevView v, int first) {
+    const MergeDesc D = v.merges[first + blockIdx.x];
+    const int g = D.g, g2 = 2 * g;
+    double* A = v.W + D.W_off;
+    const long long n = (long long)g * g;
+    for (long long idx = blockIdx.y * 256LL + threadIdx.x; idx < n; idx += (long long)gridDim.y * 256) {
+        const int i = (int)(idx % g), j = (int)(idx / g);
+        const double sc = 0.5 / sqrt(gamma_D(v, D, i) * gamma_D(v, D, j));
+        double* dd = A + (long long)j * g2 + i;          // (d_i, d_j)
+        double* ds = A + (long long)(g + j) * g2 + i;    // (d_i, s_j)
+        double* sd = A + (long long)j * g2 + g + i;      // (s_i, d_j)
+        double* ss = A + (long long)(g + j) * g2 + g + i;
+        const double zdd = *dd, zds = *ds, zsd = *sd, zss = *ss;
+        *dd = (zdd - zds - zsd + zss) * sc;   // W(a_i, a_j)
+        *ds = (zss + zsd - zds - zdd) * sc;   // W(a_i, b_j)
+        *sd = (zss + zds - zsd - zdd) * sc;   // W(b_i, a_j)
+        *ss = (zdd + zds + zsd + zss) * sc;   // W(b_i, b_j)
+    }
 }
 
 // X = -W C with C = blockdiag(R^a_go, R^b_go): column j < o1 uses the first
@@ -615,7 +560,7 @@ __global__ void __launch_bounds__(256) merge_x_kernel(DevView v, int first) {
     const int rt = (g2 + kXRows - 1) / kXRows;
     const int r0 = (blockIdx.y % rt) * kXRows, j0 = (blockIdx.y / rt) * kXColsOut;
     if (j0 >= m) return;                              // uniform per CTA
-    const double* W = v.W + D.LU_off;
+    const double* W = v.W + D.W_off;
     double* X = v.X + D.X_off;
     const int tid = threadIdx.x, rl = tid % kXRows, cg = tid / kXRows;   // 4 groups of 4 columns
     const int r = r0 + rl;
@@ -750,8 +695,7 @@ __global__ void __launch_bounds__(256) merge_up_kernel(DevView v, int first) {
     }
 }
 
-// Solve phase, top-down: lambda_gamma = X lambda_o + W (-rbar_gamma) (with
-// the pinning rows of an all-Neumann root applied to the right-hand side),
+// Solve phase, top-down: lambda_gamma = X lambda_o + W (-rbar_gamma),
 // scattered into the children's Robin data together with the node's own
 // outer data.  A CTA covers 64 rows of gamma; four thread groups split the
 // sums.
@@ -769,15 +713,9 @@ __global__ void __launch_bounds__(256) merge_down_kernel(DevView v, int first) {
     const double* rb2 = v.rbar + D.r2_off;
     for (int r = tid; r < g2; r += 256) rhs[r] = -(r < g ? rb1[N.gpos1[r]] : rb2[N.gpos2[r - g]]);
     __syncthreads();
-    if (D.pinned && tid == 0) {
-        const double a = rhs[0], b = rhs[g];
-        rhs[g] = a - b;
-        rhs[0] = 0.0;
-    }
-    __syncthreads();
     const double* lam_o = v.lam + D.r_off;
     const double* X = v.X + D.X_off;
-    const double* W = v.W + D.LU_off;
+    const double* W = v.W + D.W_off;
     double* l1 = v.lam + D.r1_off;
     double* l2 = v.lam + D.r2_off;
     const int r = r0 + rl;
@@ -803,18 +741,31 @@ __global__ void __launch_bounds__(256) merge_down_kernel(DevView v, int first) {
     }
 }
 
-constexpr int kMergeThreads = 256;
-constexpr int kPanelThreads = 512;
-constexpr int kPanelSmemBytes = 200 * 1024;
-constexpr int kSmemG2 = 128;          // fused path: M in shared memory up to 128 x 128
-constexpr int kBlockedBelow = 304;    // levels with fewer nodes take the blocked path
 
 }  // namespace
 
-bool merge_level_blocked(int count, int max_g2) { return max_g2 > kSmemG2 || count < kBlockedBelow; }
+// 2g of the per-node register path, or 0 when the level takes the blocked path
+static int small_np(int max_g2) {
+    if (max_g2 <= 8) return 8;
+    if (max_g2 <= 16) return 16;
+    if (max_g2 <= kSmallMax) return 32;
+    return 0;
+}
+
+constexpr int kSmallSmemMax = 160 * 1024;
+
+bool merge_level_blocked(int, int max_g2, int max_m) {
+    // the register path stages B and X of one warp's nodes (48 rows x m) at least
+    return small_np(max_g2) == 0 || (size_t)48 * (max_m | 1) * sizeof(double) > (size_t)kSmallSmemMax;
+}
+
+size_t merge_scratch_doubles(int count, int max_g2, int max_m) {
+    if (!merge_level_blocked(count, max_g2, max_m)) return 0;
+    return (size_t)count * (kGJScratchHead + (size_t)max_g2 * kGJ);
+}
 
 // phase ids (include/mrcm.h)
-enum { kPhMergeSmall = 2, kPhLuPanel = 3, kPhLuUpdate = 4, kPhMergeInverse = 5, kPhMergeProducts = 6 };
+enum { kPhMergeSmall = 2, kPhGjSweep = 3, kPhMergeForm = 4, kPhMergeX = 5, kPhMergeR = 6 };
 
 struct HookScope {
     const PhaseHook& h;
@@ -823,76 +774,88 @@ struct HookScope {
     ~HookScope() { if (h.end) h.end(h.ctx, phase); }
 };
 
-cudaError_t launch_merge_build(const DevView& v, int first, int count, int max_g2, int max_m,
-                               unsigned long long* amax_bits, cudaStream_t s, int* launches,
-                               const PhaseHook& hook) {
-    static_assert(kNB == kMergePanel, "flop model panel width");
+template <int NP>
+static cudaError_t launch_small(const DevView& v, int first, int count, int max_m, cudaStream_t s) {
+    const int mstride = max_m | 1;          // odd: rows of B and X start in different banks
+    const size_t per_slot = (size_t)(NP / 2 + NP) * mstride * sizeof(double);
+    // whole warps per CTA; fewer when the staging would not fit
+    int threads = kSmallThreads;
+    while (threads > 32 && (size_t)(threads / NP) * per_slot > (size_t)kSmallSmemMax) threads -= 32;
+    const int per_cta = threads / NP;
+    const size_t sm = (size_t)per_cta * per_slot;
+    cudaError_t e = cudaFuncSetAttribute(merge_small_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kSmallSmemMax);
+    if (e != cudaSuccess) return e;
+    merge_small_kernel<NP><<<(count + per_cta - 1) / per_cta, threads, sm, s>>>(v, first, count, mstride);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_merge_build(const DevView& v, int first, int count, int max_g2, int max_m, double* scratch,
+                               void* barrier, cudaStream_t s, int* launches, const PhaseHook& hook) {
     if (count == 0) return cudaSuccess;
     cudaError_t e;
-    if (!merge_level_blocked(count, max_g2)) {
+    if (!merge_level_blocked(count, max_g2, max_m)) {
         HookScope hs(hook, kPhMergeSmall);
-        const size_t sm = (size_t)max_g2 * max_g2 * sizeof(double);
-        e = cudaFuncSetAttribute(merge_small_kernel<kMergeThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(kSmemG2 * kSmemG2 * sizeof(double)));
-        if (e != cudaSuccess) return e;
-        merge_small_kernel<kMergeThreads><<<count, kMergeThreads, sm, s>>>(v, first);
+        switch (small_np(max_g2)) {
+            case 8: e = launch_small<8>(v, first, count, max_m, s); break;
+            case 16: e = launch_small<16>(v, first, count, max_m, s); break;
+            default: e = launch_small<32>(v, first, count, max_m, s); break;
+        }
         ++*launches;
-        return cudaGetLastError();
+        return e;
     }
-    e = cudaMemsetAsync(amax_bits, 0, sizeof(unsigned long long) * count, s);
-    if (e != cudaSuccess) return e;
     {
-        HookScope hs(hook, kPhMergeProducts);
-        const long long work = (long long)max_g2 * (max_g2 + max_m);
+        HookScope hs(hook, kPhMergeForm);
+        const long long work = (long long)max_g2 * max_g2;
         int gy = (int)((work + 255) / 256);
         gy = gy < 1 ? 1 : (gy > 64 ? 64 : gy);
-        merge_assemble_kernel<<<dim3(count, gy), 256, 0, s>>>(v, first, amax_bits);
-        ++*launches;
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    const int smem_rows = kPanelSmemBytes / ((kNB + 1) * (int)sizeof(double));
-    e = cudaFuncSetAttribute(lu_panel_kernel<kPanelThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             kPanelSmemBytes);
-    if (e != cudaSuccess) return e;
-    for (int k0 = 0; k0 < max_g2; k0 += kNB) {
-        const int rows = max_g2 - k0;
-        const bool staged = rows <= smem_rows;
-        const size_t psm = (size_t)rows * (staged ? kNB + 1 : 1) * sizeof(double);
-        {
-            HookScope hs(hook, kPhLuPanel);
-            lu_panel_kernel<kPanelThreads><<<count, kPanelThreads, psm, s>>>(v, first, k0, amax_bits,
-                                                                              staged ? smem_rows : 0);
-            ++*launches;
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        }
-        const int rest = max_g2 - min(k0 + kNB, max_g2);
-        if (rest <= 0) break;
-        HookScope hs(hook, kPhLuUpdate);
-        lu_trsm_kernel<<<dim3(count, (rest + kTrsmWarps - 1) / kTrsmWarps), 32 * kTrsmWarps, 0, s>>>(v, first, k0);
-        ++*launches;
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        const int tiles = (rest + kGemmTile - 1) / kGemmTile;
-        lu_gemm_kernel<<<dim3(count, tiles * tiles), 256, 0, s>>>(v, first, k0);
+        merge_form_kernel<<<dim3(count, gy), 256, 0, s>>>(v, first);
         ++*launches;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     {
-        HookScope hs(hook, kPhMergeInverse);
-        const size_t sm = (size_t)kXCols * max_g2 * sizeof(double);
-        e = cudaFuncSetAttribute(merge_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        HookScope hs(hook, kPhGjSweep);
+        static int sms = 0, per_sm = 0;
+        if (sms == 0) {
+            int dev = 0;
+            if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+            if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gj_sweep_kernel, 256, 0)) != cudaSuccess)
+                return e;
+        }
+        const int tiles = (max_g2 + kGJTile - 1) / kGJTile;
+        const long long items = (long long)count * (1 + tiles * tiles);
+        int grid = (int)std::min<long long>(items, (long long)sms * per_sm);
+        grid = grid < 1 ? 1 : grid;
+        if ((e = cudaMemsetAsync(barrier, 0, sizeof(unsigned int), s)) != cudaSuccess) return e;
+        unsigned int* bar = reinterpret_cast<unsigned int*>(barrier);
+        DevView vv = v;
+        int f = first, c = count, n = max_g2;
+        void* args[] = {&vv, &f, &c, &n, &scratch, &bar};
+        e = cudaLaunchCooperativeKernel((const void*)gj_sweep_kernel, dim3(grid), dim3(256), args, 0, s);
+        ++*launches;
         if (e != cudaSuccess) return e;
-        merge_inverse_kernel<<<dim3(count, (max_g2 + kXCols - 1) / kXCols), 32 * kXCols, sm, s>>>(v, first);
+    }
+    {
+        HookScope hs(hook, kPhMergeForm);
+        const long long work = (long long)(max_g2 / 2) * (max_g2 / 2);
+        int gy = (int)((work + 255) / 256);
+        gy = gy < 1 ? 1 : (gy > 64 ? 64 : gy);
+        merge_backform_kernel<<<dim3(count, gy), 256, 0, s>>>(v, first);
         ++*launches;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if (max_m > 0) {
-        HookScope hs(hook, kPhMergeProducts);
-        const int rt = (max_g2 + kXRows - 1) / kXRows, ct = (max_m + kXColsOut - 1) / kXColsOut;
-        merge_x_kernel<<<dim3(count, rt * ct), 256, 0, s>>>(v, first);
-        ++*launches;
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        const int tiles = (max_m + kRTile - 1) / kRTile;
-        merge_rupdate_kernel<<<dim3(count, tiles * tiles), 256, 0, s>>>(v, first);
+        {
+            HookScope hs(hook, kPhMergeX);
+            const int rt = (max_g2 + kXRows - 1) / kXRows, ct = (max_m + kXColsOut - 1) / kXColsOut;
+            merge_x_kernel<<<dim3(count, rt * ct), 256, 0, s>>>(v, first);
+            ++*launches;
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+        HookScope hs(hook, kPhMergeR);
+        const int rtiles = (max_m + kRTile - 1) / kRTile;
+        merge_rupdate_kernel<<<dim3(count, rtiles * rtiles), 256, 0, s>>>(v, first);
         ++*launches;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }

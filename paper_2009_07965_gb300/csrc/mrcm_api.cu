@@ -51,7 +51,7 @@ struct Plan {
     std::vector<int> node_map, gamma_segs;
     int max_m_leaf = 0, max_g2 = 0;
     // storage sizes (doubles / ints)
-    long long nR = 0, nr = 0, nLU = 0, npiv = 0, nX = 0, nxb = 0, nL = 0, nZ = 0, nzb = 0;
+    long long nR = 0, nr = 0, nW = 0, nX = 0, nL = 0, nZ = 0, nzb = 0;
     std::vector<long long> node_R_off, node_r_off;
     std::vector<long long> seg_lam_a, seg_lam_b;   // lam offsets of each segment in its two leaves
     // flop model
@@ -291,21 +291,18 @@ int make_plan(Plan& P) {
             D.r1_off = P.node_r_off[nd.c1];
             D.r2_off = P.node_r_off[nd.c2];
             const long long g2 = 2LL * D.g, m = D.m;
-            D.LU_off = P.nLU;  P.nLU += g2 * g2;
-            D.piv_off = P.npiv; P.npiv += g2;
+            D.W_off = P.nW;    P.nW += g2 * g2;
             D.X_off = P.nX;    P.nX += g2 * m;
-            D.xb_off = P.nxb;  P.nxb += g2;
             P.merges.push_back(D);
             P.level_max_g2[h - 1] = std::max(P.level_max_g2[h - 1], (int)g2);
             P.level_max_m[h - 1] = std::max(P.level_max_m[h - 1], (int)m);
             P.max_g2 = std::max(P.max_g2, (int)g2);
-            // flop model: LU with partial pivoting, W = M^-1 from the factors
-            // (2 N^3 on identity columns), X = -W C over C's blocks (2 N g m),
-            // R update (2 g m^2); solve passes: up 2 m N, down 2 N (m + N)
+            // flop model: Gauss-Jordan inversion of the 2g x 2g form (2 N^3:
+            // N steps of an N x N rank-one update), X = -W C over C's blocks
+            // (2 N g m), R update (2 g m^2); solve passes: up 2 m N, down
+            // 2 N (m + N)
             const double N = (double)g2, gd = (double)D.g, md = (double)m;
-            double lu = 0.0;
-            for (int k = 0; k < g2; ++k) lu += (double)(g2 - k - 1) + 2.0 * (g2 - k - 1) * (double)(g2 - k - 1);
-            const double inv = 2.0 * N * N * N, prod = 2.0 * N * gd * md + 2.0 * md * md * gd;
+            const double lu = 0.0, inv = 2.0 * N * N * N, prod = 2.0 * N * gd * md + 2.0 * md * md * gd;
             P.merge_flops += (long long)(lu + inv + prod);
             P.solve_flops += 2LL * g2 * m + 2LL * g2 * (m + g2);
             if (m > 0) P.phase_pass[MRCM_PHASE_TREE_UP] += 2.0 * md * N;
@@ -315,26 +312,22 @@ int make_plan(Plan& P) {
             node_prod_flops.push_back(prod);
         }
     }
-    // build phases: leaves, then per level the fused or the blocked path
+    // build phases: leaves, then per level the per-node register path or the
+    // blocked Gauss-Jordan sweep
     P.phase_build[MRCM_PHASE_LEAF_BUILD] = (double)P.leaf_flops;
     for (int h = 1; h <= P.height; ++h) {
         const int f0 = P.level_first[h - 1], cnt = P.level_count[h - 1];
-        const bool blocked = merge_level_blocked(cnt, P.level_max_g2[h - 1]);
+        const bool blocked = merge_level_blocked(cnt, P.level_max_g2[h - 1], P.level_max_m[h - 1]);
         for (int q = f0; q < f0 + cnt; ++q) {
             if (!blocked) {
                 P.phase_build[MRCM_PHASE_MERGE_SMALL] += node_lu_flops[q] + node_inv_flops[q] + node_prod_flops[q];
                 continue;
             }
-            const int N = 2 * P.merges[q].g;
-            for (int k0 = 0; k0 < N; k0 += kMergePanel) {
-                const int nb = std::min(kMergePanel, N - k0), rows = N - k0, rest = N - k0 - nb;
-                double pf = 0.0;
-                for (int kk = 0; kk < nb; ++kk) pf += (rows - kk - 1) + 2.0 * (rows - kk - 1) * (nb - kk - 1);
-                P.phase_build[MRCM_PHASE_LU_PANEL] += pf;
-                P.phase_build[MRCM_PHASE_LU_UPDATE] += (double)rest * nb * (nb - 1) + 2.0 * rest * rest * nb;
-            }
-            P.phase_build[MRCM_PHASE_MERGE_INVERSE] += node_inv_flops[q];
-            P.phase_build[MRCM_PHASE_MERGE_PRODUCTS] += node_prod_flops[q];
+            const MergeDesc& D = P.merges[q];
+            const double N = 2.0 * D.g, gd = D.g, md = D.m;
+            P.phase_build[MRCM_PHASE_GJ_SWEEP] += node_inv_flops[q];
+            P.phase_build[MRCM_PHASE_MERGE_X] += 2.0 * N * gd * md;
+            P.phase_build[MRCM_PHASE_MERGE_R] += 2.0 * md * md * gd;
         }
     }
     const double ncell = (double)P.nx * P.ny, nface = (double)(P.nx + 1) * P.ny + (double)P.nx * (P.ny + 1);
@@ -360,7 +353,8 @@ struct mrcm_ctx {
     std::vector<cudaEvent_t> ev;          // event pairs, handed out per launch group
     std::vector<int> ev_phase;            // phase of each used pair
     int ev_used = 0;
-    unsigned long long* amax_bits = nullptr;
+    double* gj_scratch = nullptr;
+    unsigned long long* gj_barrier = nullptr;
     int refine_steps = 2;
     int refine_check = 0;
     int hist_count = 0;
@@ -558,11 +552,8 @@ static int setup_impl(mrcm_ctx* c, const mrcm_grid* g, const double* K_dev, cons
     TRY(dev_alloc(c, &v.R, P.nR));
     TRY(dev_alloc(c, &v.rbar, P.nr));
     TRY(dev_alloc(c, &v.lam, P.nr));
-    TRY(dev_alloc(c, &v.LU, P.nLU));
-    TRY(dev_alloc(c, &v.piv, P.npiv));
     TRY(dev_alloc(c, &v.X, P.nX));
-    TRY(dev_alloc(c, &v.W, P.nLU));
-    TRY(dev_alloc(c, &v.udinv, P.nxb));
+    TRY(dev_alloc(c, &v.W, P.nW));
     TRY(dev_alloc(c, &v.segP, P.nseg));
     TRY(dev_alloc(c, &v.segU, P.nseg));
     TRY(dev_alloc(c, &v.segP_lo, P.nseg));
@@ -574,9 +565,12 @@ static int setup_impl(mrcm_ctx* c, const mrcm_grid* g, const double* K_dev, cons
     TRY(dev_alloc(c, &v.res_max, kMaxRefine + 1));
     TRY(dev_alloc(c, &v.red, 1024));
     {
-        int maxc = 1;
-        for (int n : P.level_count) maxc = std::max(maxc, n);
-        TRY(dev_alloc(c, &c->amax_bits, maxc));
+        size_t nscr = 1;
+        for (int h = 1; h <= P.height; ++h)
+            nscr = std::max(nscr, merge_scratch_doubles(P.level_count[h - 1], P.level_max_g2[h - 1],
+                                                        P.level_max_m[h - 1]));
+        TRY(dev_alloc(c, &c->gj_scratch, (long long)nscr));
+        TRY(dev_alloc(c, &c->gj_barrier, (long long)(kMergeBarrierBytes / sizeof(unsigned long long))));
     }
     TRY(dev_alloc(c, &v.status, 4));
     TRYC(cudaMemcpyAsync(c->K, K_dev, sizeof(double) * ncell, cudaMemcpyDefault, c->stream));
@@ -642,7 +636,8 @@ int mrcm_build_basis(mrcm_ctx* c) {
         const PhaseHook hook{c, phase_begin, phase_end};
         for (int h = 1; h <= P.height; ++h) {
             TRYC(launch_merge_build(v, P.level_first[h - 1], P.level_count[h - 1], P.level_max_g2[h - 1],
-                                    P.level_max_m[h - 1], c->amax_bits, s, &launches, hook));
+                                    P.level_max_m[h - 1], c->gj_scratch, c->gj_barrier, s, &launches,
+                                    hook));
         }
     }
     c->launches_build = launches;

@@ -47,10 +47,8 @@ struct MergeDesc {
     int pinned;        // 1: root of an all-Neumann problem (P of gamma[0] = 0)
     long long R_off, R1_off, R2_off;   // node / children R
     long long r_off, r1_off, r2_off;   // node / children rbar (and lambda)
-    long long LU_off;  // 2g x 2g LU factors (row-major, in place)
-    long long piv_off; // 2g pivot rows (int)
-    long long X_off;   // 2g x m coefficients X = -M^-1 C
-    long long xb_off;  // per-merge vector of 2g values (U diagonal reciprocals)
+    long long W_off;   // 2g x 2g inverse W = M^-1 (column-major)
+    long long X_off;   // 2g x m coefficients X = -M^-1 C (column-major)
 };
 
 // Device-side view of the plan and workspace.
@@ -88,11 +86,8 @@ struct DevView {
     double* R;          // node maps (leaves and internal nodes)
     double* rbar;       // node particular fluxes
     double* lam;        // node Robin data (top-down)
-    double* LU;         // merge factors
-    int* piv;
     double* X;
-    double* W;          // explicit inverses of the interface matrices (LU_off layout)
-    double* udinv;      // reciprocals of the U diagonal per merge (xb_off layout)
+    double* W;          // explicit inverses of the interface matrices (W_off layout)
     double* segP;       // refined interface unknowns P_t, U_t (high parts)
     double* segU;
     double* segP_lo;    // ... and low parts of the double-double state
@@ -190,13 +185,15 @@ struct PhaseHook {
     void (*begin)(void* ctx, int phase);
     void (*end)(void* ctx, int phase);
 };
-// one tree height of merges; amax_bits: scratch of `count` entries;
-// *launches is increased by the number of kernels launched
-cudaError_t launch_merge_build(const DevView& v, int first, int count, int max_g2, int max_m,
-                               unsigned long long* amax_bits, cudaStream_t s, int* launches,
-                               const PhaseHook& hook);
-bool merge_level_blocked(int count, int max_g2);
-constexpr int kMergePanel = 32;      // panel width of the blocked LU (flop model)
+// one tree height of merges; scratch: merge_scratch_doubles(count, max_g2,
+// max_m) values; barrier: kMergeBarrierBytes of device memory (reset by the
+// call); *launches is increased by the number of kernels launched
+cudaError_t launch_merge_build(const DevView& v, int first, int count, int max_g2, int max_m, double* scratch,
+                               void* barrier, cudaStream_t s, int* launches, const PhaseHook& hook);
+constexpr size_t kMergeBarrierBytes = 64;
+bool merge_level_blocked(int count, int max_g2, int max_m);
+size_t merge_scratch_doubles(int count, int max_g2, int max_m);
+constexpr int kMergeBlock = 16;      // block size of the blocked Gauss-Jordan sweep (flop model)
 cudaError_t launch_merge_up(const DevView& v, int first, int count, int max_g2, int max_m, cudaStream_t s);
 cudaError_t launch_merge_down(const DevView& v, int first, int count, int max_g2, int max_m, cudaStream_t s);
 
