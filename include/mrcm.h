@@ -235,6 +235,15 @@ int mrcm_enable_timing(mrcm_ctx* ctx, int on);
 int mrcm_phase_times(mrcm_ctx* ctx, double* ms);
 
 /*
+ * mrcm_group_times -- the timed launch groups of the most recent build and
+ * solve in launch order: phase[k] (host) its phase id, ms[k] (host) its
+ * duration, for k < min(count, cap).  Returns the number of groups recorded
+ * (>= 0) or an error code.  A merge level contributes one group per phase
+ * it launches, so the groups of the build resolve the tree height by height.
+ */
+int mrcm_group_times(mrcm_ctx* ctx, int* phase, double* ms, int cap);
+
+/*
  * mrcm_phase_flops -- flops[MRCM_PHASE_COUNT] (host) receives the algorithmic
  * FP64 flop count of each phase for one mrcm_build_basis (build phases) and
  * one mrcm_solve with the current refinement setting (solve phases): the

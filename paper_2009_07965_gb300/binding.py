@@ -24,7 +24,8 @@ Q = dict(LEAVES=0, SEGMENTS=1, LEVELS=2, NODES=3, WORKSPACE_BYTES=4, MAX_GAMMA=5
 EXPORTS = ["mrcm_setup", "mrcm_plan_query", "mrcm_set_permeability", "mrcm_build_basis", "mrcm_solve", "mrcm_query",
            "mrcm_node_info", "mrcm_node_segments", "mrcm_segment_info", "mrcm_node_operator",
            "mrcm_destroy", "mrcm_error_string", "mrcm_enable_timing", "mrcm_phase_times",
-           "mrcm_merge_pair_noalloc", "mrcm_set_refinement", "mrcm_residual_history", "mrcm_phase_flops"]
+           "mrcm_merge_pair_noalloc", "mrcm_set_refinement", "mrcm_residual_history", "mrcm_phase_flops",
+           "mrcm_group_times"]
 PHASES = ["coef", "leaf_build", "merge_small", "gj_sweep", "merge_form", "merge_x", "merge_r",
           "leaf_particular", "tree_up", "tree_down", "leaf_pressure", "residual", "finish"]
 # kernel family behind each phase (for reports)
@@ -87,6 +88,8 @@ def _lib():
         lib.mrcm_merge_pair_noalloc.restype = I
         lib.mrcm_phase_flops.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
         lib.mrcm_phase_flops.restype = I
+        lib.mrcm_group_times.argtypes = [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), I]
+        lib.mrcm_group_times.restype = I
         lib.mrcm_set_refinement.argtypes = [P, I, I]
         lib.mrcm_set_refinement.restype = I
         lib.mrcm_residual_history.argtypes = [P, ctypes.POINTER(ctypes.c_double), I]
@@ -197,6 +200,15 @@ def mrcm_phase_times(ctx):
     ms = (ctypes.c_double * len(PHASES))()
     _check(_lib().mrcm_phase_times(ctx, ms), "mrcm_phase_times")
     return dict(zip(PHASES, list(ms)))
+
+
+def mrcm_group_times(ctx, cap=4096):
+    """[(phase name, ms)] of the timed launch groups of the last build and solve."""
+    ph = (ctypes.c_int * cap)()
+    ms = (ctypes.c_double * cap)()
+    n = _lib().mrcm_group_times(ctx, ph, ms, cap)
+    _check(min(n, 0), "mrcm_group_times")
+    return [(PHASES[ph[k]], ms[k]) for k in range(min(n, cap))]
 
 
 def mrcm_set_refinement(ctx, steps, check=False):

@@ -63,7 +63,6 @@ namespace {
 constexpr int kGJ = kMergeBlock; // block size of the blocked Gauss-Jordan sweep
 constexpr int kGJTile = 32;       // output tile of the blocked update (kGJTile^2 per CTA)
 constexpr int kSmallMax = 32;     // largest 2g merged by the per-node register kernel
-constexpr int kSmallThreads = 128;
 constexpr int kRTile = 32;       // R update tile
 constexpr double kTinyPivot = 1e-14;   // pivots of the scaled form are O(1)
 
@@ -110,131 +109,130 @@ __device__ __forceinline__ bool pivot_ok(double p, bool d_row) {
 }
 
 // ---------------------------------------------------------------------------
-// Per-node register path: NP lanes per node (NP = padded 2g, a power of two
-// <= 32; d rows at lanes [0, NP/2), s rows at [NP/2, NP), padding rows carry
-// the identity).  Lane r holds row r of T in registers; step k broadcasts
-// row k by shuffles and updates every row (Gauss-Jordan, no pivoting).  Then
-// the lanes exchange their d / s partner rows to form the rows of W, compute
-// their rows of X = -W C, stage X in shared memory and form the merged R.
-template <int NP>
-__global__ void __launch_bounds__(kSmallThreads) merge_small_kernel(DevView v, int first, int count, int mstride) {
-    extern __shared__ __align__(16) double xs_all[];   // per node slot: B (g x m) and X (2g x m)
-    constexpr int H = NP / 2;
-    constexpr unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    const int r = lane % NP, base = lane - r;
-    const int slot = threadIdx.x / NP;
-    const int q = blockIdx.x * (blockDim.x / NP) + slot;
-    const bool active = q < count;                     // uniform over the NP lanes
-    const MergeDesc D = v.merges[first + (active ? q : 0)];
+// Per-node path for small systems (2g <= kSmallMax): one CTA per node, all in
+// shared memory.  T (row-major), Gauss-Jordan without pivoting (one entry per
+// thread and step, thread 0 forms the pivot reciprocal), the back transform
+// into W (column-major), then X = -W B and R = R_oo + B^T X with B = C
+// compacted to g x m (row k: gamma segment k of the child owning column j).
+// Shared layout: T[g2*g2], Wc[g2*g2], Bs[g*mstride], Xs[g2*mstride].
+constexpr int kSmallThreads = 256;
+constexpr int kSmallPer = (kSmallMax * kSmallMax + kSmallThreads - 1) / kSmallThreads;   // T entries per thread
+__global__ void __launch_bounds__(kSmallThreads) merge_small_kernel(DevView v, int first, int mstride) {
+    extern __shared__ __align__(16) double sm[];
+    __shared__ double sd[kSmallMax / 2], sq[kSmallMax / 2];
+    __shared__ double s_rp, s_inv_sum;
+    __shared__ int s_bad;
+    const MergeDesc D = v.merges[first + blockIdx.x];
     const NodeRefs N = node_refs(v, D);
     const int g = N.g, g2 = N.g2, m = N.m, o1 = N.o1;
-    double* xs = xs_all + (long long)slot * (H + NP) * mstride;   // B then X of this node
-    const bool d_row = r < H;
-    const int li = d_row ? r : r - H;
-    const bool real_r = active && li < g;
-    double sqd = 1.0;
-    if (real_r) sqd = sqrt(gamma_D(v, D, li));
-    const double sdi = 1.0 / sqd;
-    // sum of D over gamma (d lanes), for the regularised root
-    double sum = (d_row && real_r) ? sqd * sqd : 0.0;
+    const int tid = threadIdx.x;
+    double* T = sm;
+    double* Wc = T + g2 * g2;
+    double* Bs = Wc + g2 * g2;
+    double* Xs = Bs + g * mstride;
+    if (tid < 32) {
+        double dsum = 0.0;
+        if (tid < g) {
+            const double d = gamma_D(v, D, tid);
+            sq[tid] = sqrt(d);
+            sd[tid] = 1.0 / sq[tid];
+            dsum = d;
+        }
 #pragma unroll
-    for (int o = NP / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(FULL, sum, o);
-    const double inv_sum = (active && D.pinned && sum > 0.0) ? 1.0 / sum : 0.0;
-
-    double row[NP];
-#pragma unroll
-    for (int j = 0; j < NP; ++j) {
-        const double sdj = __shfl_sync(FULL, sdi, base + j);
-        const double sqj = __shfl_sync(FULL, sqd, base + j);
-        const int lj = j < H ? j : j - H;
-        double t = (j == r) ? 1.0 : 0.0;
-        if (real_r && lj < g)
-            t = t_entry(N, d_row ? li : g + li, j < H ? lj : g + lj, sdi, sdj, sqd, sqj, inv_sum);
-        row[j] = t;
+        for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+        if (tid == 0) {
+            s_inv_sum = (D.pinned && dsum > 0.0) ? 1.0 / dsum : 0.0;
+            s_bad = 0;
+        }
     }
-    bool bad = false;
-#pragma unroll
-    for (int k = 0; k < NP; ++k) {
-        double prow[NP];
-#pragma unroll
-        for (int j = 0; j < NP; ++j) prow[j] = __shfl_sync(FULL, row[j], base + k);
-        const double p = prow[k];
-        const int lk = k < H ? k : k - H;
-        if (active && lk < g && r == 0 && !pivot_ok(p, k < H)) bad = true;
-        const double rp = 1.0 / p;
-        const bool me = (r == k);
-        const double c = me ? -rp : row[k] * rp;
-#pragma unroll
-        for (int j = 0; j < NP; ++j) row[j] = fma(-c, prow[j], me ? 0.0 : row[j]);
-        row[k] = me ? rp : -c;
+    __syncthreads();
+    for (int idx = tid; idx < g2 * g2; idx += kSmallThreads) {
+        const int r = idx / g2, c = idx % g2, i = r < g ? r : r - g, j = c < g ? c : c - g;
+        T[idx] = t_entry(N, r, c, sd[i], sd[j], sq[i], sq[j], s_inv_sum);
     }
-    if (bad) atomicOr(v.status, kStatusSingular);
-    // rows of W: lane (d, i) -> row lambda^a_i, lane (s, i) -> row lambda^b_i
-    double oth[NP];
+    for (int k = 0; k < g; ++k) {
+        const double* ra = N.R1 + N.gpos1[k] * N.m1;
+        const double* rb = N.R2 + N.gpos2[k] * N.m2;
+        for (int j = tid; j < m; j += kSmallThreads) Bs[k * mstride + j] = j < o1 ? ra[N.opos1[j]] : rb[N.opos2[j - o1]];
+    }
+    // Gauss-Jordan on T (d rows first: positive pivots, then negative)
+    for (int k = 0; k < g2; ++k) {
+        __syncthreads();
+        if (tid == 0) {
+            const double p = T[k * g2 + k];
+            if (!pivot_ok(p, k < g)) s_bad = 1;
+            s_rp = 1.0 / p;
+        }
+        __syncthreads();
+        const double rp = s_rp;
+        double nv[kSmallPer];
 #pragma unroll
-    for (int j = 0; j < NP; ++j) oth[j] = __shfl_xor_sync(FULL, row[j], H);
-    double Wr[NP];            // Wr[j] = W(row, a_j), Wr[H + j] = W(row, b_j)
+        for (int e = 0; e < kSmallPer; ++e) {
+            const int idx = tid + e * kSmallThreads;
+            if (idx >= g2 * g2) break;
+            const int r = idx / g2, c = idx % g2;
+            const double a_rk = T[r * g2 + k], a_kc = T[k * g2 + c];
+            if (r == k) nv[e] = (c == k) ? rp : a_kc * rp;
+            else nv[e] = (c == k) ? -a_rk * rp : fma(-a_rk * rp, a_kc, T[idx]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < kSmallPer; ++e) {
+            const int idx = tid + e * kSmallThreads;
+            if (idx >= g2 * g2) break;
+            T[idx] = nv[e];
+        }
+    }
+    __syncthreads();
+    if (tid == 0 && s_bad) atomicOr(v.status, kStatusSingular);
+    // W = D^-1/2 Q T^-1 Q^T D^-1/2 (column-major Wc), written out
+    for (int idx = tid; idx < g * g; idx += kSmallThreads) {
+        const int i = idx % g, j = idx / g;
+        const double zdd = T[i * g2 + j], zds = T[i * g2 + g + j];
+        const double zsd = T[(g + i) * g2 + j], zss = T[(g + i) * g2 + g + j];
+        const double sc = 0.5 * sd[i] * sd[j];
+        Wc[j * g2 + i] = (zdd - zds - zsd + zss) * sc;
+        Wc[(g + j) * g2 + i] = (zss + zsd - zds - zdd) * sc;
+        Wc[j * g2 + g + i] = (zss + zds - zsd - zdd) * sc;
+        Wc[(g + j) * g2 + g + i] = (zdd + zds + zsd + zss) * sc;
+    }
+    __syncthreads();
     double* Wg = v.W + D.W_off;
-    const int wrow = d_row ? li : g + li;
-#pragma unroll
-    for (int j = 0; j < H; ++j) {
-        const double sdj = __shfl_sync(FULL, sdi, base + j);
-        const double zdd = d_row ? row[j] : oth[j];
-        const double zds = d_row ? row[H + j] : oth[H + j];
-        const double zsd = d_row ? oth[j] : row[j];
-        const double zss = d_row ? oth[H + j] : row[H + j];
-        const double sc = 0.5 * sdi * sdj;
-        double wa, wb;
-        if (d_row) { wa = (zdd - zds - zsd + zss) * sc; wb = (zss + zsd - zds - zdd) * sc; }
-        else       { wa = (zss + zds - zsd - zdd) * sc; wb = (zdd + zds + zsd + zss) * sc; }
-        Wr[j] = wa;
-        Wr[H + j] = wb;
-        if (real_r && j < g) {
-            Wg[(long long)j * g2 + wrow] = wa;
-            Wg[(long long)(g + j) * g2 + wrow] = wb;
-        }
-    }
-    // B = C = blockdiag(R^a_go, R^b_go) compacted to g x m (row k: gamma
-    // segment k of the child that owns column j), staged in shared memory
-    double* Bs = xs;                       // B(k, j) at Bs[k * mstride + j]
-    double* Xs = xs + H * mstride;         // X(row, j) at Xs[row * mstride + j]
-    if (active) {
-        for (int k = 0; k < g; ++k) {
-            const double* ra = N.R1 + N.gpos1[k] * N.m1;
-            const double* rb = N.R2 + N.gpos2[k] * N.m2;
-            for (int j = r; j < m; j += NP) Bs[k * mstride + j] = j < o1 ? ra[N.opos1[j]] : rb[N.opos2[j - o1]];
-        }
-    }
-    __syncwarp();
-    // X = -W B: this lane's row (columns of side a use W's a columns)
+    for (int idx = tid; idx < g2 * g2; idx += kSmallThreads) Wg[idx] = Wc[idx];
+    // X = -W B (columns of side a use W's a columns)
     double* Xg = v.X + D.X_off;
-    for (int j = 0; j < m; ++j) {
-        const bool ja = j < o1;
-        double acc = 0.0;
-#pragma unroll
-        for (int k = 0; k < H; ++k)
-            if (k < g) acc = fma(ja ? Wr[k] : Wr[H + k], Bs[k * mstride + j], acc);
-        if (real_r) {
-            Xg[(long long)j * g2 + wrow] = -acc;
-            Xs[wrow * mstride + j] = -acc;
+    for (int idx = tid; idx < g2 * m; idx += kSmallThreads) {
+        const int r = idx % g2, j = idx / g2;
+        const double* wc = Wc + (j < o1 ? 0 : g) * g2 + r;
+        double acc0 = 0.0, acc1 = 0.0;
+        int k = 0;
+        for (; k + 1 < g; k += 2) {
+            acc0 = fma(wc[k * g2], Bs[k * mstride + j], acc0);
+            acc1 = fma(wc[(k + 1) * g2], Bs[(k + 1) * mstride + j], acc1);
         }
+        if (k < g) acc0 = fma(wc[k * g2], Bs[k * mstride + j], acc0);
+        const double x = -(acc0 + acc1);
+        Xg[idx] = x;
+        Xs[r * mstride + j] = x;
     }
-    __syncwarp();
-    if (!active) return;
+    __syncthreads();
     // merged R = R_oo + B^T X (row i of side a uses the a rows of X)
     double* Rp = v.R + D.R_off;
-    for (int i = 0; i < m; ++i) {
+    for (int idx = tid; idx < m * m; idx += kSmallThreads) {
+        const int i = idx / m, j = idx % m;
         const bool ia = i < o1;
-        const double* Rrow = ia ? N.R1 + N.opos1[i] * N.m1 : N.R2 + N.opos2[i - o1] * N.m2;
-        const double* xh = Xs + (ia ? 0 : g) * mstride;
-        for (int j = r; j < m; j += NP) {
-            double acc = 0.0;
-            if (ia && j < o1) acc = Rrow[N.opos1[j]];
-            if (!ia && j >= o1) acc = Rrow[N.opos2[j - o1]];
-            for (int k = 0; k < g; ++k) acc = fma(Bs[k * mstride + i], xh[k * mstride + j], acc);
-            Rp[(long long)i * m + j] = acc;
+        double roo = 0.0;       // loaded first, added last: its latency overlaps the sum
+        if (ia && j < o1) roo = N.R1[N.opos1[i] * N.m1 + N.opos1[j]];
+        if (!ia && j >= o1) roo = N.R2[N.opos2[i - o1] * N.m2 + N.opos2[j - o1]];
+        const double* xh = Xs + (ia ? 0 : g) * mstride + j;
+        double acc0 = 0.0, acc1 = 0.0;
+        int k = 0;
+        for (; k + 1 < g; k += 2) {
+            acc0 = fma(Bs[k * mstride + i], xh[k * mstride], acc0);
+            acc1 = fma(Bs[(k + 1) * mstride + i], xh[(k + 1) * mstride], acc1);
         }
+        if (k < g) acc0 = fma(Bs[k * mstride + i], xh[k * mstride], acc0);
+        Rp[idx] = roo + (acc0 + acc1);
     }
 }
 
@@ -744,19 +742,16 @@ __global__ void __launch_bounds__(256) merge_down_kernel(DevView v, int first) {
 
 }  // namespace
 
-// 2g of the per-node register path, or 0 when the level takes the blocked path
-static int small_np(int max_g2) {
-    if (max_g2 <= 8) return 8;
-    if (max_g2 <= 16) return 16;
-    if (max_g2 <= kSmallMax) return 32;
-    return 0;
+constexpr size_t kSmallSmemMax = 160 * 1024;
+
+// shared memory of the per-node path for a level
+static size_t small_smem(int max_g2, int max_m) {
+    const size_t mstride = (size_t)(max_m | 1);
+    return sizeof(double) * (2 * (size_t)max_g2 * max_g2 + (size_t)(max_g2 / 2) * mstride + (size_t)max_g2 * mstride);
 }
 
-constexpr int kSmallSmemMax = 160 * 1024;
-
 bool merge_level_blocked(int, int max_g2, int max_m) {
-    // the register path stages B and X of one warp's nodes (48 rows x m) at least
-    return small_np(max_g2) == 0 || (size_t)48 * (max_m | 1) * sizeof(double) > (size_t)kSmallSmemMax;
+    return max_g2 > kSmallMax || small_smem(max_g2, max_m) > kSmallSmemMax;
 }
 
 size_t merge_scratch_doubles(int count, int max_g2, int max_m) {
@@ -774,19 +769,13 @@ struct HookScope {
     ~HookScope() { if (h.end) h.end(h.ctx, phase); }
 };
 
-template <int NP>
-static cudaError_t launch_small(const DevView& v, int first, int count, int max_m, cudaStream_t s) {
+static cudaError_t launch_small(const DevView& v, int first, int count, int max_g2, int max_m, cudaStream_t s) {
     const int mstride = max_m | 1;          // odd: rows of B and X start in different banks
-    const size_t per_slot = (size_t)(NP / 2 + NP) * mstride * sizeof(double);
-    // whole warps per CTA; fewer when the staging would not fit
-    int threads = kSmallThreads;
-    while (threads > 32 && (size_t)(threads / NP) * per_slot > (size_t)kSmallSmemMax) threads -= 32;
-    const int per_cta = threads / NP;
-    const size_t sm = (size_t)per_cta * per_slot;
-    cudaError_t e = cudaFuncSetAttribute(merge_small_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kSmallSmemMax);
+    const size_t sm = small_smem(max_g2, max_m);
+    cudaError_t e = cudaFuncSetAttribute(merge_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kSmallSmemMax);
     if (e != cudaSuccess) return e;
-    merge_small_kernel<NP><<<(count + per_cta - 1) / per_cta, threads, sm, s>>>(v, first, count, mstride);
+    merge_small_kernel<<<count, kSmallThreads, sm, s>>>(v, first, mstride);
     return cudaGetLastError();
 }
 
@@ -796,11 +785,7 @@ cudaError_t launch_merge_build(const DevView& v, int first, int count, int max_g
     cudaError_t e;
     if (!merge_level_blocked(count, max_g2, max_m)) {
         HookScope hs(hook, kPhMergeSmall);
-        switch (small_np(max_g2)) {
-            case 8: e = launch_small<8>(v, first, count, max_m, s); break;
-            case 16: e = launch_small<16>(v, first, count, max_m, s); break;
-            default: e = launch_small<32>(v, first, count, max_m, s); break;
-        }
+        e = launch_small(v, first, count, max_g2, max_m, s);
         ++*launches;
         return e;
     }

@@ -828,6 +828,18 @@ int mrcm_phase_times(mrcm_ctx* c, double* ms) {
     return MRCM_OK;
 }
 
+int mrcm_group_times(mrcm_ctx* c, int* phase, double* ms, int cap) {
+    if (!c || cap < 0 || (cap > 0 && (!phase || !ms))) return MRCM_ERR_INVALID_ARG;
+    TRYC(cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < c->ev_used && k < cap; ++k) {
+        float t = 0.f;
+        TRYC(cudaEventElapsedTime(&t, c->ev[2 * k], c->ev[2 * k + 1]));
+        phase[k] = c->ev_phase[k];
+        ms[k] = t;
+    }
+    return c->ev_used;
+}
+
 int mrcm_phase_flops(const mrcm_ctx* c, double* flops) {
     if (!c || !flops) return MRCM_ERR_INVALID_ARG;
     const Plan& P = c->P;
