@@ -116,10 +116,10 @@ __device__ __forceinline__ bool pivot_ok(double p, bool d_row) {
 // compacted to g x m (row k: gamma segment k of the child owning column j).
 // Shared layout: T[g2*g2], Wc[g2*g2], Bs[g*mstride], Xs[g2*mstride].
 constexpr int kSmallThreads = 256;
-constexpr int kSmallPer = (kSmallMax * kSmallMax + kSmallThreads - 1) / kSmallThreads;   // T entries per thread
+constexpr int kSmallTri = (kSmallMax * (kSmallMax + 1) / 2 + kSmallThreads - 1) / kSmallThreads;   // kept T entries per thread
 __global__ void __launch_bounds__(kSmallThreads) merge_small_kernel(DevView v, int first, int mstride) {
     extern __shared__ __align__(16) double sm[];
-    __shared__ double sd[kSmallMax / 2], sq[kSmallMax / 2];
+    __shared__ double sd[kSmallMax / 2], sq[kSmallMax / 2], vrow[kSmallMax];
     __shared__ double s_rp, s_inv_sum;
     __shared__ int s_bad;
     const MergeDesc D = v.merges[first + blockIdx.x];
@@ -155,41 +155,69 @@ __global__ void __launch_bounds__(kSmallThreads) merge_small_kernel(DevView v, i
         const double* rb = N.R2 + N.gpos2[k] * N.m2;
         for (int j = tid; j < m; j += kSmallThreads) Bs[k * mstride + j] = j < o1 ? ra[N.opos1[j]] : rb[N.opos2[j - o1]];
     }
-    // Gauss-Jordan on T (d rows first: positive pivots, then negative)
+    // Gauss-Jordan on T (d rows first: positive pivots, then negative).  T
+    // is symmetric, and after step k the entries of an eliminated and a
+    // remaining index are antisymmetric, all others symmetric; so only the
+    // lower triangle r >= c is kept: a_rk = -T[k][r] for r < k, a_kc =
+    // T[c][k] for c > k.  Per step warp 0 forms the reciprocal and the scaled
+    // pivot row v_c = a_kc / p; every kept entry then takes one FMA.
+    int er[kSmallTri], ec[kSmallTri];
+#pragma unroll
+    for (int e = 0; e < kSmallTri; ++e) {
+        const int idx = tid + e * kSmallThreads;
+        int r = (int)((sqrtf(8.0f * idx + 1.0f) - 1.0f) * 0.5f);
+        while ((r + 1) * (r + 2) / 2 <= idx) ++r;
+        while (r * (r + 1) / 2 > idx) --r;
+        er[e] = r;
+        ec[e] = idx - r * (r + 1) / 2;
+    }
+    const int ntri = g2 * (g2 + 1) / 2;
     for (int k = 0; k < g2; ++k) {
         __syncthreads();
-        if (tid == 0) {
+        if (tid < 32) {
             const double p = T[k * g2 + k];
-            if (!pivot_ok(p, k < g)) s_bad = 1;
-            s_rp = 1.0 / p;
+            const double rp = 1.0 / p;
+            if (tid == 0) {
+                if (!pivot_ok(p, k < g)) s_bad = 1;
+                s_rp = rp;
+            }
+            if (tid < g2) {
+                const int c = tid;
+                const double a_kc = c <= k ? T[k * g2 + c] : T[c * g2 + k];
+                vrow[c] = a_kc * rp;
+            }
         }
         __syncthreads();
         const double rp = s_rp;
-        double nv[kSmallPer];
+        double nv[kSmallTri];
 #pragma unroll
-        for (int e = 0; e < kSmallPer; ++e) {
+        for (int e = 0; e < kSmallTri; ++e) {
             const int idx = tid + e * kSmallThreads;
-            if (idx >= g2 * g2) break;
-            const int r = idx / g2, c = idx % g2;
-            const double a_rk = T[r * g2 + k], a_kc = T[k * g2 + c];
-            if (r == k) nv[e] = (c == k) ? rp : a_kc * rp;
-            else nv[e] = (c == k) ? -a_rk * rp : fma(-a_rk * rp, a_kc, T[idx]);
+            if (idx >= ntri) break;
+            const int r = er[e], c = ec[e];
+            const double a_rk = r >= k ? T[r * g2 + k] : -T[k * g2 + r];
+            if (r == k) nv[e] = (c == k) ? rp : vrow[c];
+            else if (c == k) nv[e] = -a_rk * rp;
+            else nv[e] = fma(-a_rk, vrow[c], T[r * g2 + c]);
         }
         __syncthreads();
 #pragma unroll
-        for (int e = 0; e < kSmallPer; ++e) {
+        for (int e = 0; e < kSmallTri; ++e) {
             const int idx = tid + e * kSmallThreads;
-            if (idx >= g2 * g2) break;
-            T[idx] = nv[e];
+            if (idx >= ntri) break;
+            T[er[e] * g2 + ec[e]] = nv[e];
         }
     }
     __syncthreads();
     if (tid == 0 && s_bad) atomicOr(v.status, kStatusSingular);
-    // W = D^-1/2 Q T^-1 Q^T D^-1/2 (column-major Wc), written out
+    // W = D^-1/2 Q T^-1 Q^T D^-1/2 (column-major Wc); T^-1 symmetric, kept
+    // in the lower triangle
     for (int idx = tid; idx < g * g; idx += kSmallThreads) {
         const int i = idx % g, j = idx / g;
-        const double zdd = T[i * g2 + j], zds = T[i * g2 + g + j];
-        const double zsd = T[(g + i) * g2 + j], zss = T[(g + i) * g2 + g + j];
+        const double zdd = i >= j ? T[i * g2 + j] : T[j * g2 + i];
+        const double zds = T[(g + j) * g2 + i];           // (d_i, s_j) = (s_j, d_i)
+        const double zsd = T[(g + i) * g2 + j];
+        const double zss = i >= j ? T[(g + i) * g2 + g + j] : T[(g + j) * g2 + g + i];
         const double sc = 0.5 * sd[i] * sd[j];
         Wc[j * g2 + i] = (zdd - zds - zsd + zss) * sc;
         Wc[(g + j) * g2 + i] = (zss + zsd - zds - zdd) * sc;
@@ -216,10 +244,15 @@ __global__ void __launch_bounds__(kSmallThreads) merge_small_kernel(DevView v, i
         Xs[r * mstride + j] = x;
     }
     __syncthreads();
-    // merged R = R_oo + B^T X (row i of side a uses the a rows of X)
+    // merged R = R_oo + B^T X (row i of side a uses the a rows of X); R is
+    // symmetric (R_oo - B^T W B), so the lower triangle is formed and mirrored
     double* Rp = v.R + D.R_off;
-    for (int idx = tid; idx < m * m; idx += kSmallThreads) {
-        const int i = idx / m, j = idx % m;
+    const int mtri = m * (m + 1) / 2;
+    for (int idx = tid; idx < mtri; idx += kSmallThreads) {
+        int i = (int)((sqrtf(8.0f * idx + 1.0f) - 1.0f) * 0.5f);
+        while ((i + 1) * (i + 2) / 2 <= idx) ++i;
+        while (i * (i + 1) / 2 > idx) --i;
+        const int j = idx - i * (i + 1) / 2;
         const bool ia = i < o1;
         double roo = 0.0;       // loaded first, added last: its latency overlaps the sum
         if (ia && j < o1) roo = N.R1[N.opos1[i] * N.m1 + N.opos1[j]];
@@ -232,29 +265,54 @@ __global__ void __launch_bounds__(kSmallThreads) merge_small_kernel(DevView v, i
             acc1 = fma(Bs[(k + 1) * mstride + i], xh[(k + 1) * mstride], acc1);
         }
         if (k < g) acc0 = fma(Bs[k * mstride + i], xh[k * mstride], acc0);
-        Rp[idx] = roo + (acc0 + acc1);
+        const double val = roo + (acc0 + acc1);
+        Rp[(long long)i * m + j] = val;
+        Rp[(long long)j * m + i] = val;
     }
 }
 
 // ---------------------------------------------------------------------------
 // Blocked path.  T into the W storage of each node (column-major).
+__device__ __forceinline__ double block_sum256(double x, double* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;
+    __syncthreads();
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t += red[w];
+    __syncthreads();
+    return t;
+}
+
+// D^1/2 (scl[0, g)) and D^-1/2 (scl[g, 2g)) of a node's gamma segments in
+// shared memory; returns sum D (256 threads).
+__device__ double stage_gamma_scalings(const DevView& v, const MergeDesc& D, double* scl, double* red) {
+    const int g = D.g;
+    double part = 0.0;
+    for (int i = threadIdx.x; i < g; i += 256) {
+        const double d = gamma_D(v, D, i), sq = sqrt(d);
+        scl[i] = sq;
+        scl[g + i] = 1.0 / sq;
+        part += d;
+    }
+    return block_sum256(part, red);
+}
+
 __global__ void __launch_bounds__(256) merge_form_kernel(DevView v, int first) {
+    extern __shared__ __align__(16) double scl[];     // D^1/2, D^-1/2 of gamma
+    __shared__ double red[8];
     const MergeDesc D = v.merges[first + blockIdx.x];
     const NodeRefs N = node_refs(v, D);
     const int g = N.g, g2 = N.g2;
-    double inv_sum = 0.0;
-    if (D.pinned) {
-        double s = 0.0;
-        for (int i = 0; i < g; ++i) s += gamma_D(v, D, i);
-        inv_sum = s > 0.0 ? 1.0 / s : 0.0;
-    }
+    const double sum = stage_gamma_scalings(v, D, scl, red);
+    const double inv_sum = (D.pinned && sum > 0.0) ? 1.0 / sum : 0.0;
     double* T = v.W + D.W_off;
     const long long nT = (long long)g2 * g2;
     for (long long idx = blockIdx.y * 256LL + threadIdx.x; idx < nT; idx += (long long)gridDim.y * 256) {
         const int r = (int)(idx % g2), c = (int)(idx / g2);
-        const double di = gamma_D(v, D, r < g ? r : r - g), dj = gamma_D(v, D, c < g ? c : c - g);
-        const double sqi = sqrt(di), sqj = sqrt(dj);
-        T[idx] = t_entry(N, r, c, 1.0 / sqi, 1.0 / sqj, sqi, sqj, inv_sum);
+        const int i = r < g ? r : r - g, j = c < g ? c : c - g;
+        T[idx] = t_entry(N, r, c, scl[g + i], scl[g + j], scl[i], scl[j], inv_sum);
     }
 }
 
@@ -274,13 +332,16 @@ struct GJSmem {
 };
 
 // Inverse of a kGJ x kGJ block held in shared memory (Ps[r][c], identity
-// padding beyond nb), in place, by the whole CTA: Gauss-Jordan without
-// pivoting, one entry per thread and step; thread 0 forms each pivot's
-// reciprocal (one FP64 division per step for the CTA).  d_rows: rows of the
-// block that lie in the d part (positive pivots expected).  Returns false
-// (thread 0) on a pivot of the wrong sign or size.
+// padding beyond nb), in place, by the whole CTA (256 threads): Gauss-Jordan
+// without pivoting; thread t owns kGJEnt consecutive entries of row
+// t / (kGJ / kGJEnt), so the row multiplier is formed once per thread; thread
+// 0 forms each pivot's reciprocal.  d_rows: rows of the block that lie in the
+// d part (positive pivots expected).  Returns false (thread 0) on a pivot of
+// the wrong sign or size.
+constexpr int kGJEnt = (kGJ * kGJ) / 256;          // entries per thread (1 or 4)
+static_assert(kGJEnt >= 1 && kGJ * kGJ == 256 * kGJEnt, "block size and CTA size");
 __device__ bool gj_invert_block(double (*Ps)[kGJ + 1], int nb, int d_rows, double* s_rp) {
-    const int tid = threadIdx.x, pr = tid / kGJ, pc = tid % kGJ;
+    const int tid = threadIdx.x, pr = tid / (kGJ / kGJEnt), pc0 = (tid % (kGJ / kGJEnt)) * kGJEnt;
     bool ok = true;
     for (int kk = 0; kk < kGJ; ++kk) {
         if (tid == 0) {
@@ -289,12 +350,19 @@ __device__ bool gj_invert_block(double (*Ps)[kGJ + 1], int nb, int d_rows, doubl
             *s_rp = 1.0 / p;
         }
         __syncthreads();
-        const double rp = *s_rp, a_rk = Ps[pr][kk], a_kc = Ps[kk][pc], a = Ps[pr][pc];
+        const double rp = *s_rp;
+        const double mult = Ps[pr][kk] * rp;
+        double nv[kGJEnt];
+#pragma unroll
+        for (int e = 0; e < kGJEnt; ++e) {
+            const int pc = pc0 + e;
+            const double a_kc = Ps[kk][pc];
+            if (pr == kk) nv[e] = (pc == kk) ? rp : a_kc * rp;
+            else nv[e] = (pc == kk) ? -mult : fma(-mult, a_kc, Ps[pr][pc]);
+        }
         __syncthreads();
-        double nv;
-        if (pr == kk) nv = (pc == kk) ? rp : a_kc * rp;
-        else nv = (pc == kk) ? -a_rk * rp : fma(-a_rk * rp, a_kc, a);
-        Ps[pr][pc] = nv;
+#pragma unroll
+        for (int e = 0; e < kGJEnt; ++e) Ps[pr][pc0 + e] = nv[e];
         __syncthreads();
     }
     return ok;
@@ -412,28 +480,34 @@ __device__ bool gj_next_diag_item(const DevView& v, const MergeDesc& D, int slot
     double* A = v.W + D.W_off;
     double* sc = gj_scratch(scratch, slot, nmax);
     const double* colblk = sc + kGJScratchHead;
-    const int tid = threadIdx.x, pr = tid / kGJ, pc = tid % kGJ;
+    const int tid = threadIdx.x;
     // Cs[c][r]: column block rows k1 + r; Bs[c][j]: new block row columns k1 + j
-    {
-        const int cc = tid / kGJ, rr = tid % kGJ;
+    for (int idx = tid; idx < kGJ * kGJ; idx += 256) {
+        const int cc = idx / kGJ, rr = idx % kGJ;
         S.Cs[cc][rr] = (cc < nb && rr < nb1) ? __ldcg(colblk + (long long)cc * N + k1 + rr) : 0.0;
         S.Bs[cc][rr] = (cc < nb && rr < nb1) ? __ldcg(A + (long long)(k1 + rr) * N + k0 + cc) : 0.0;
     }
     __syncthreads();
-    double acc = 0.0;
+    for (int idx = tid; idx < kGJ * kGJ; idx += 256) {
+        const int pr = idx % kGJ, pc = idx / kGJ;
+        double acc0 = 0.0, acc1 = 0.0;
 #pragma unroll
-    for (int cc = 0; cc < kGJ; ++cc) acc = fma(S.Cs[cc][pr], S.Bs[cc][pc], acc);
-    double val = (pr == pc) ? 1.0 : 0.0;
-    if (pr < nb1 && pc < nb1) {
-        double* at = A + (long long)(k1 + pc) * N + k1 + pr;
-        val = __ldcg(at) - acc;
-        *at = val;
+        for (int cc = 0; cc < kGJ; cc += 2) {
+            acc0 = fma(S.Cs[cc][pr], S.Bs[cc][pc], acc0);
+            acc1 = fma(S.Cs[cc + 1][pr], S.Bs[cc + 1][pc], acc1);
+        }
+        double val = (pr == pc) ? 1.0 : 0.0;
+        if (pr < nb1 && pc < nb1) {
+            double* at = A + (long long)(k1 + pc) * N + k1 + pr;
+            val = __ldcg(at) - (acc0 + acc1);
+            *at = val;
+        }
+        S.Ps[pr][pc] = val;
     }
-    S.Ps[pr][pc] = val;
     __syncthreads();
     const bool ok = gj_invert_block(S.Ps, nb1, D.g - k1, &S.rp);
     double* Pn = sc + ((k1 / kGJ) & 1) * kGJ * kGJ;
-    Pn[pr * kGJ + pc] = S.Ps[pr][pc];
+    for (int idx = tid; idx < kGJ * kGJ; idx += 256) Pn[idx] = S.Ps[idx / kGJ][idx % kGJ];
     __syncthreads();
     return ok;
 }
@@ -480,7 +554,7 @@ __global__ void __launch_bounds__(256) gj_sweep_kernel(DevView v, int first, int
     __shared__ int s_bad;
     const int rtiles = (nmax + kGJRowTile - 1) / kGJRowTile;
     const int tiles = (nmax + kGJTile - 1) / kGJTile;
-    const int tid = threadIdx.x, pr = tid / kGJ, pc = tid % kGJ;
+    const int tid = threadIdx.x;
     unsigned int round = 0;
     if (tid == 0) s_bad = 0;
     __syncthreads();
@@ -488,10 +562,14 @@ __global__ void __launch_bounds__(256) gj_sweep_kernel(DevView v, int first, int
         const MergeDesc D = v.merges[first + q];
         const int N = 2 * D.g, nb = min(kGJ, N);
         const double* A = v.W + D.W_off;
-        S.Ps[pr][pc] = (pr < nb && pc < nb) ? __ldcg(A + (long long)pc * N + pr) : (pr == pc ? 1.0 : 0.0);
+        for (int idx = tid; idx < kGJ * kGJ; idx += 256) {
+            const int pr = idx % kGJ, pc = idx / kGJ;
+            S.Ps[pr][pc] = (pr < nb && pc < nb) ? __ldcg(A + (long long)pc * N + pr) : (pr == pc ? 1.0 : 0.0);
+        }
         __syncthreads();
         if (!gj_invert_block(S.Ps, nb, D.g, &S.rp)) s_bad = 1;
-        gj_scratch(scratch, q, nmax)[pr * kGJ + pc] = S.Ps[pr][pc];
+        double* P0 = gj_scratch(scratch, q, nmax);
+        for (int idx = tid; idx < kGJ * kGJ; idx += 256) P0[idx] = S.Ps[idx / kGJ][idx % kGJ];
         __syncthreads();
     }
     if (!grid_barrier(counter, round, v.status)) return;
@@ -527,21 +605,25 @@ __global__ void __launch_bounds__(256) gj_sweep_kernel(DevView v, int first, int
 // T^-1 -> W = D^-1/2 Q T^-1 Q^T D^-1/2, in place (one thread per 2 x 2 block
 // pattern (i, j), i, j < g).
 __global__ void __launch_bounds__(256) merge_backform_kernel(DevView v, int first) {
+    extern __shared__ __align__(16) double scl[];
+    __shared__ double red[8];
     const MergeDesc D = v.merges[first + blockIdx.x];
     const int g = D.g, g2 = 2 * g;
+    stage_gamma_scalings(v, D, scl, red);
+    const double* sd = scl + g;
     double* A = v.W + D.W_off;
     const long long n = (long long)g * g;
     for (long long idx = blockIdx.y * 256LL + threadIdx.x; idx < n; idx += (long long)gridDim.y * 256) {
         const int i = (int)(idx % g), j = (int)(idx / g);
-        const double sc = 0.5 / sqrt(gamma_D(v, D, i) * gamma_D(v, D, j));
+        const double sc = 0.5 * sd[i] * sd[j];
         double* dd = A + (long long)j * g2 + i;          // (d_i, d_j)
         double* ds = A + (long long)(g + j) * g2 + i;    // (d_i, s_j)
-        double* sd = A + (long long)j * g2 + g + i;      // (s_i, d_j)
+        double* sdp = A + (long long)j * g2 + g + i;     // (s_i, d_j)
         double* ss = A + (long long)(g + j) * g2 + g + i;
-        const double zdd = *dd, zds = *ds, zsd = *sd, zss = *ss;
+        const double zdd = *dd, zds = *ds, zsd = *sdp, zss = *ss;
         *dd = (zdd - zds - zsd + zss) * sc;   // W(a_i, a_j)
         *ds = (zss + zsd - zds - zdd) * sc;   // W(a_i, b_j)
-        *sd = (zss + zds - zsd - zdd) * sc;   // W(b_i, a_j)
+        *sdp = (zss + zds - zsd - zdd) * sc;  // W(b_i, a_j)
         *ss = (zdd + zds + zsd + zss) * sc;   // W(b_i, b_j)
     }
 }
@@ -599,7 +681,8 @@ __global__ void __launch_bounds__(256) merge_x_kernel(DevView v, int first) {
     }
 }
 
-// R = blockdiag(R_oo) + blockdiag(R_og) X on kRTile^2 output tiles: row i
+// R = blockdiag(R_oo) + blockdiag(R_og) X on kRTile^2 output tiles (the
+// lower triangle, mirrored: R is symmetric): row i
 // of the tile uses the gathered row of R^a (i < o1) or R^b and the matching
 // half of X; both are staged in shared memory in chunks of kRTile.
 __global__ void __launch_bounds__(256) merge_rupdate_kernel(DevView v, int first) {
@@ -609,8 +692,13 @@ __global__ void __launch_bounds__(256) merge_rupdate_kernel(DevView v, int first
     const NodeRefs N = node_refs(v, D);
     const int m = N.m, g = N.g, g2 = N.g2, o1 = N.o1;
     const int tiles = (m + kRTile - 1) / kRTile;
-    if ((int)blockIdx.y >= tiles * tiles) return;
-    const int i0 = (blockIdx.y % tiles) * kRTile, jt = (blockIdx.y / tiles) * kRTile;
+    if ((int)blockIdx.y >= tiles * (tiles + 1) / 2) return;
+    // R is symmetric: lower-triangle tiles (ti >= tj) only, mirrored on write
+    int ti = (int)((sqrtf(8.0f * blockIdx.y + 1.0f) - 1.0f) * 0.5f);
+    while ((ti + 1) * (ti + 2) / 2 <= (int)blockIdx.y) ++ti;
+    while (ti * (ti + 1) / 2 > (int)blockIdx.y) --ti;
+    const int tj = blockIdx.y - ti * (ti + 1) / 2;
+    const int i0 = ti * kRTile, jt = tj * kRTile;
     const double* X = v.X + D.X_off;
     double* Rp = v.R + D.R_off;
     const int tid = threadIdx.x;
@@ -656,11 +744,12 @@ __global__ void __launch_bounds__(256) merge_rupdate_kernel(DevView v, int first
 #pragma unroll
         for (int b = 0; b < TS; ++b) {
             const int j = jt + tc + b;
-            if (j >= m) continue;
+            if (j >= m || j > i) continue;
             double val = acc[a][b];
             if (i < o1 && j < o1) val += row[N.opos1[j]];
             if (i >= o1 && j >= o1) val += row[N.opos2[j - o1]];
             Rp[(long long)i * m + j] = val;
+            Rp[(long long)j * m + i] = val;
         }
     }
 }
@@ -794,7 +883,7 @@ cudaError_t launch_merge_build(const DevView& v, int first, int count, int max_g
         const long long work = (long long)max_g2 * max_g2;
         int gy = (int)((work + 255) / 256);
         gy = gy < 1 ? 1 : (gy > 64 ? 64 : gy);
-        merge_form_kernel<<<dim3(count, gy), 256, 0, s>>>(v, first);
+        merge_form_kernel<<<dim3(count, gy), 256, (size_t)max_g2 * sizeof(double), s>>>(v, first);
         ++*launches;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
@@ -826,7 +915,7 @@ cudaError_t launch_merge_build(const DevView& v, int first, int count, int max_g
         const long long work = (long long)(max_g2 / 2) * (max_g2 / 2);
         int gy = (int)((work + 255) / 256);
         gy = gy < 1 ? 1 : (gy > 64 ? 64 : gy);
-        merge_backform_kernel<<<dim3(count, gy), 256, 0, s>>>(v, first);
+        merge_backform_kernel<<<dim3(count, gy), 256, (size_t)max_g2 * sizeof(double), s>>>(v, first);
         ++*launches;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
@@ -840,7 +929,7 @@ cudaError_t launch_merge_build(const DevView& v, int first, int count, int max_g
         }
         HookScope hs(hook, kPhMergeR);
         const int rtiles = (max_m + kRTile - 1) / kRTile;
-        merge_rupdate_kernel<<<dim3(count, rtiles * rtiles), 256, 0, s>>>(v, first);
+        merge_rupdate_kernel<<<dim3(count, rtiles * (rtiles + 1) / 2), 256, 0, s>>>(v, first);
         ++*launches;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }

@@ -297,12 +297,15 @@ int make_plan(Plan& P) {
             P.level_max_g2[h - 1] = std::max(P.level_max_g2[h - 1], (int)g2);
             P.level_max_m[h - 1] = std::max(P.level_max_m[h - 1], (int)m);
             P.max_g2 = std::max(P.max_g2, (int)g2);
-            // flop model: Gauss-Jordan inversion of the 2g x 2g form (2 N^3:
-            // N steps of an N x N rank-one update), X = -W C over C's blocks
-            // (2 N g m), R update (2 g m^2); solve passes: up 2 m N, down
-            // 2 N (m + N)
+            // flop model: Gauss-Jordan inversion of the 2g x 2g form (N steps
+            // of a rank-one update: 2 N^3 on the full matrix of the blocked
+            // sweep, N^2 (N + 1) on the lower triangle kept by the per-node
+            // path), X = -W C over C's blocks (2 N g m), the lower triangle of
+            // the symmetric R update (g m (m + 1)); solve passes: up 2 m N,
+            // down 2 N (m + N).  The path of a level is known once all its
+            // nodes are listed, so inv is set in the phase pass below.
             const double N = (double)g2, gd = (double)D.g, md = (double)m;
-            const double lu = 0.0, inv = 2.0 * N * N * N, prod = 2.0 * N * gd * md + 2.0 * md * md * gd;
+            const double lu = 0.0, inv = 2.0 * N * N * N, prod = 2.0 * N * gd * md + md * (md + 1.0) * gd;
             P.merge_flops += (long long)(lu + inv + prod);
             P.solve_flops += 2LL * g2 * m + 2LL * g2 * (m + g2);
             if (m > 0) P.phase_pass[MRCM_PHASE_TREE_UP] += 2.0 * md * N;
@@ -319,15 +322,17 @@ int make_plan(Plan& P) {
         const int f0 = P.level_first[h - 1], cnt = P.level_count[h - 1];
         const bool blocked = merge_level_blocked(cnt, P.level_max_g2[h - 1], P.level_max_m[h - 1]);
         for (int q = f0; q < f0 + cnt; ++q) {
-            if (!blocked) {
-                P.phase_build[MRCM_PHASE_MERGE_SMALL] += node_lu_flops[q] + node_inv_flops[q] + node_prod_flops[q];
-                continue;
-            }
             const MergeDesc& D = P.merges[q];
             const double N = 2.0 * D.g, gd = D.g, md = D.m;
+            if (!blocked) {
+                const double sym = N * N * (N + 1.0);
+                P.merge_flops += (long long)(sym - node_inv_flops[q]);
+                P.phase_build[MRCM_PHASE_MERGE_SMALL] += sym + node_prod_flops[q];
+                continue;
+            }
             P.phase_build[MRCM_PHASE_GJ_SWEEP] += node_inv_flops[q];
             P.phase_build[MRCM_PHASE_MERGE_X] += 2.0 * N * gd * md;
-            P.phase_build[MRCM_PHASE_MERGE_R] += 2.0 * md * md * gd;
+            P.phase_build[MRCM_PHASE_MERGE_R] += md * (md + 1.0) * gd;
         }
     }
     const double ncell = (double)P.nx * P.ny, nface = (double)(P.nx + 1) * P.ny + (double)P.nx * (P.ny + 1);
