@@ -420,6 +420,12 @@ __global__ void mean_subtract_kernel(DevView v, long long n) {
         const DD x = dd_add(DD{v.segP[i], v.segP_lo[i]}, DD{-mean, 0.0});
         v.segP[i] = x.h;
         v.segP_lo[i] = x.l;
+        // the Robin data P -/+ beta U move with P
+        for (int side = 0; side < 2; ++side) {
+            const double2 l = v.seg_lam_dd[2 * i + side];
+            const DD y = dd_add(DD{l.x, l.y}, DD{-mean, 0.0});
+            v.seg_lam_dd[2 * i + side] = make_double2(y.h, y.l);
+        }
     }
 }
 

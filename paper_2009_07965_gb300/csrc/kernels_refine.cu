@@ -21,155 +21,162 @@
 namespace mrcm {
 namespace {
 
-// p_c - P + s * beta U  (s = +1: side a, s = -1: side b), as a double-double
-__device__ __forceinline__ DD robin_gap(DD pc, DD P, DD bu, double sgn) {
-    const DD x = dd_add(pc, dd_neg(P));
-    return dd_add(x, sgn > 0 ? bu : dd_neg(bu));
+// Unnormalised double-double pairs (hi + lo): the high parts are combined
+// with the error-free TwoSum / FMA TwoProd, the low parts are summed in FP64;
+// the represented value is exact to O(u^2) of the magnitudes involved, which
+// is all a residual needs, at a third of the operations of normalised
+// double-double arithmetic.
+__device__ __forceinline__ DD dd_sub_u(DD x, DD y) {
+    DD s = dd_two_sum(x.h, -y.h);
+    s.l += x.l - y.l;
+    return s;
+}
+__device__ __forceinline__ DD dd_scale_u(DD d, double c) {
+    const double p = c * d.h;
+    return {p, fma(c, d.l, fma(c, d.h, -p))};
+}
+__device__ __forceinline__ DD dd_acc_u(DD sum, DD x) {
+    DD s = dd_two_sum(sum.h, x.h);
+    s.l += sum.l + x.l;
+    return s;
 }
 
 __device__ __forceinline__ DD state_p(const DevView& v, long long c) { return {v.p_hi[c], v.p_lo[c]}; }
-__device__ __forceinline__ DD state_P(const DevView& v, int t) { return {v.segP[t], v.segP_lo[t]}; }
-__device__ __forceinline__ DD state_bu(const DevView& v, int t) {
-    return dd_mul_d(DD{v.segU[t], v.segU_lo[t]}, v.seg_beta[t]);
+__device__ __forceinline__ DD seg_lam(const DevView& v, int t, int side_b) {
+    const double2 x = v.seg_lam_dd[2 * t + side_b];
+    return {x.x, x.y};
 }
 
-__device__ __forceinline__ void record_max(unsigned long long* slot, double a) {
-    // |a| >= 0: the IEEE bit pattern orders like the value
-    atomicMax(slot, (unsigned long long)__double_as_longlong(fabs(a)));
+// Largest |x| over the CTA, one atomic per CTA (|x| >= 0: the IEEE bit
+// pattern orders like the value).
+__device__ __forceinline__ void block_record_max(unsigned long long* slot, double x) {
+    __shared__ double wmax[32];
+    double a = fabs(x);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = a;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double b = threadIdx.x < (blockDim.x >> 5) ? wmax[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+        if (threadIdx.x == 0 && b > 0.0) atomicMax(slot, (unsigned long long)__double_as_longlong(b));
+    }
 }
 
-// Outward flux of cell c through one face, double-double.
-// kind: 0 interior (coef T, neighbour cell n), 1 skeleton (coef rho, segment
-// t, sgn = +1 when the cell is side a), 2 Dirichlet (coef tau, value g),
-// 3 Neumann (|e| g).
-__device__ __forceinline__ DD face_out(const DevView& v, int kind, double coef, DD pc, long long n, int t,
-                                       double sgn, double g) {
-    if (kind == 0) return dd_mul_d(dd_add(pc, dd_neg(state_p(v, n))), coef);
-    if (kind == 1) return dd_mul_d(robin_gap(pc, state_P(v, t), state_bu(v, t), sgn), coef);
-    if (kind == 2) return dd_mul_d(dd_add(pc, DD{-g, 0.0}), coef);
-    return dd_two_prod(coef, g);
+// Outward flux of a cell through one face: coef (pc - pn) for an interior
+// face (pn the neighbour), coef (pc - lambda) for a skeleton face (lambda
+// the Robin datum of the cell's side), coef (pc - g) for a Dirichlet face.
+__device__ __forceinline__ DD face_out_u(DD pc, DD pn, double coef) { return dd_scale_u(dd_sub_u(pc, pn), coef); }
+
+// One face of cell c: its outward flux in the residual sum.  lower: the cell
+// lies below / left of the face (side a of a skeleton segment).
+__device__ __forceinline__ DD cell_face(const DevView& v, const double* bc_val, int bc_side, bool boundary,
+                                        int seg, bool lower, double coef, double area, DD pc, long long nb,
+                                        int bc_index) {
+    if (boundary) {
+        const double g = bc_val[bc_index];
+        if (v.bc[bc_side]) return face_out_u(pc, DD{g, 0.0}, coef);
+        return dd_two_prod(area, g);                 // Neumann: |e| g_N outward
+    }
+    if (seg >= 0) return face_out_u(pc, seg_lam(v, seg, lower ? 0 : 1), coef);
+    return face_out_u(pc, state_p(v, nb), coef);
 }
 
-__global__ void residual_cells_kernel(DevView v, const double* __restrict__ q, const double* __restrict__ bc_val,
-                                      int step) {
+__global__ void __launch_bounds__(256) residual_cells_kernel(DevView v, const double* __restrict__ q,
+                                                             const double* __restrict__ bc_val, int step) {
     const long long n = (long long)v.nx * v.ny;
     const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (c >= n) return;
-    const int i = (int)(c % v.nx), j = (int)(c / v.nx);
-    const DD pc = state_p(v, c);
-    const long long fx = i + (long long)(v.nx + 1) * j;
-    const long long fy = i + (long long)v.nx * j;
-    DD E = {0.0, 0.0};
-    // west
-    if (i == 0) {
-        E = dd_add(E, v.bc[0] ? face_out(v, 2, v.cxU[fx], pc, 0, 0, 0, bc_val[j])
-                              : face_out(v, 3, v.hy, pc, 0, 0, 0, bc_val[j]));
-    } else if (x_skeleton(v, i)) {
-        E = dd_add(E, face_out(v, 1, v.cxU[fx], pc, 0, skeleton_segment(v, 0, i, j), -1.0, 0));
-    } else {
-        E = dd_add(E, face_out(v, 0, v.cxU[fx], pc, c - 1, 0, 0, 0));
+    double e = 0.0;
+    if (c < n) {
+        const int i = (int)(c % v.nx), j = (int)(c / v.nx);
+        const DD pc = state_p(v, c);
+        const long long fx = i + (long long)(v.nx + 1) * j;
+        const long long fy = i + (long long)v.nx * j;
+        DD E = dd_two_sum(0.0, -q[c]);
+        E = dd_acc_u(E, cell_face(v, bc_val, 0, i == 0, i > 0 ? v.xface_seg[fx] : -1, false, v.cxU[fx], v.hy, pc,
+                                  c - 1, j));
+        E = dd_acc_u(E, cell_face(v, bc_val, 1, i == v.nx - 1, i < v.nx - 1 ? v.xface_seg[fx + 1] : -1, true,
+                                  v.cxL[fx + 1], v.hy, pc, c + 1, v.ny + j));
+        E = dd_acc_u(E, cell_face(v, bc_val, 2, j == 0, j > 0 ? v.yface_seg[fy] : -1, false, v.cyU[fy], v.hx, pc,
+                                  c - v.nx, 2 * v.ny + i));
+        E = dd_acc_u(E, cell_face(v, bc_val, 3, j == v.ny - 1, j < v.ny - 1 ? v.yface_seg[fy + v.nx] : -1, true,
+                                  v.cyL[fy + v.nx], v.hx, pc, c + v.nx, 2 * v.ny + v.nx + i));
+        e = E.h + E.l;
+        v.rcell[c] = -e;
     }
-    // east
-    if (i == v.nx - 1) {
-        const double g = bc_val[v.ny + j];
-        E = dd_add(E, v.bc[1] ? face_out(v, 2, v.cxL[fx + 1], pc, 0, 0, 0, g)
-                              : face_out(v, 3, v.hy, pc, 0, 0, 0, g));
-    } else if (x_skeleton(v, i + 1)) {
-        E = dd_add(E, face_out(v, 1, v.cxL[fx + 1], pc, 0, skeleton_segment(v, 0, i + 1, j), 1.0, 0));
-    } else {
-        E = dd_add(E, face_out(v, 0, v.cxL[fx + 1], pc, c + 1, 0, 0, 0));
-    }
-    // south
-    if (j == 0) {
-        const double g = bc_val[2 * v.ny + i];
-        E = dd_add(E, v.bc[2] ? face_out(v, 2, v.cyU[fy], pc, 0, 0, 0, g)
-                              : face_out(v, 3, v.hx, pc, 0, 0, 0, g));
-    } else if (y_skeleton(v, j)) {
-        E = dd_add(E, face_out(v, 1, v.cyU[fy], pc, 0, skeleton_segment(v, 1, j, i), -1.0, 0));
-    } else {
-        E = dd_add(E, face_out(v, 0, v.cyU[fy], pc, c - v.nx, 0, 0, 0));
-    }
-    // north
-    if (j == v.ny - 1) {
-        const double g = bc_val[2 * v.ny + v.nx + i];
-        E = dd_add(E, v.bc[3] ? face_out(v, 2, v.cyL[fy + v.nx], pc, 0, 0, 0, g)
-                              : face_out(v, 3, v.hx, pc, 0, 0, 0, g));
-    } else if (y_skeleton(v, j + 1)) {
-        E = dd_add(E, face_out(v, 1, v.cyL[fy + v.nx], pc, 0, skeleton_segment(v, 1, j + 1, i), 1.0, 0));
-    } else {
-        E = dd_add(E, face_out(v, 0, v.cyL[fy + v.nx], pc, c + v.nx, 0, 0, 0));
-    }
-    E = dd_add(E, DD{-q[c], 0.0});
-    const double e = dd_round(E);
-    v.rcell[c] = -e;
-    record_max(v.res_max + step, e);
+    block_record_max(v.res_max + step, e);
 }
 
-__global__ void residual_segments_kernel(DevView v, int step) {
+__global__ void __launch_bounds__(128) residual_segments_kernel(DevView v, int step) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= v.nseg) return;
-    const int axis = v.seg_axis[t], line = v.seg_line[t], lo = v.seg_lo[t], len = v.seg_len[t];
-    const DD P = state_P(v, t);
-    const DD bu = state_bu(v, t);
-    DD Fa = {0.0, 0.0}, Fb = {0.0, 0.0};
-    for (int e = 0; e < len; ++e) {
-        long long ca, cb, f;
-        double ra, rb;
-        if (axis == 0) {
-            const int j = lo + e;
-            ca = (long long)j * v.nx + line - 1;
-            cb = ca + 1;
-            f = line + (long long)(v.nx + 1) * j;
-            ra = v.cxL[f];
-            rb = v.cxU[f];
-        } else {
-            const int i = lo + e;
-            ca = (long long)(line - 1) * v.nx + i;
-            cb = ca + v.nx;
-            f = i + (long long)v.nx * line;
-            ra = v.cyL[f];
-            rb = v.cyU[f];
+    double E13 = 0.0, E14 = 0.0;
+    if (t < v.nseg) {
+        const int axis = v.seg_axis[t], line = v.seg_line[t], lo = v.seg_lo[t], len = v.seg_len[t];
+        const DD la = seg_lam(v, t, 0), lb = seg_lam(v, t, 1);
+        DD Fa = {0.0, 0.0}, Fb = {0.0, 0.0};
+        for (int e = 0; e < len; ++e) {
+            long long ca, cb, f;
+            double ra, rb;
+            if (axis == 0) {
+                const int j = lo + e;
+                ca = (long long)j * v.nx + line - 1;
+                cb = ca + 1;
+                f = line + (long long)(v.nx + 1) * j;
+                ra = v.cxL[f];
+                rb = v.cxU[f];
+            } else {
+                const int i = lo + e;
+                ca = (long long)(line - 1) * v.nx + i;
+                cb = ca + v.nx;
+                f = i + (long long)v.nx * line;
+                ra = v.cyL[f];
+                rb = v.cyU[f];
+            }
+            Fa = dd_acc_u(Fa, face_out_u(state_p(v, ca), la, ra));
+            Fb = dd_acc_u(Fb, face_out_u(state_p(v, cb), lb, rb));
         }
-        Fa = dd_add(Fa, dd_mul_d(robin_gap(state_p(v, ca), P, bu, 1.0), ra));
-        Fb = dd_add(Fb, dd_mul_d(robin_gap(state_p(v, cb), P, bu, -1.0), rb));
+        const double length = len * (axis == 0 ? v.hy : v.hx);
+        const DD two_u = dd_scale_u(DD{v.segU[t], v.segU_lo[t]}, 2.0 * length);
+        const DD e13 = dd_acc_u(Fa, Fb);
+        const DD e14 = dd_sub_u(dd_sub_u(Fa, Fb), two_u);
+        E13 = e13.h + e13.l;
+        E14 = e14.h + e14.l;
+        // lambda-form rows: row_a + row_b = Eq. 13.2, row_a - row_b = Eq. 14.2
+        v.sadj[v.seg_lam_a[t]] = -0.5 * (E13 + E14);
+        v.sadj[v.seg_lam_b[t]] = -0.5 * (E13 - E14);
     }
-    const double length = len * (axis == 0 ? v.hy : v.hx);
-    const DD e13 = dd_add(Fa, Fb);
-    DD e14 = dd_add(Fa, dd_neg(Fb));
-    e14 = dd_add(e14, dd_neg(dd_mul_d(DD{v.segU[t], v.segU_lo[t]}, 2.0 * length)));
-    const double E13 = dd_round(e13), E14 = dd_round(e14);
-    // lambda-form rows: row_a + row_b = Eq. 13.2, row_a - row_b = Eq. 14.2
-    v.sadj[v.seg_lam_a[t]] = -0.5 * (E13 + E14);
-    v.sadj[v.seg_lam_b[t]] = -0.5 * (E13 - E14);
-    record_max(v.res_max + step, E13);
-    record_max(v.res_max + step, E14);
+    block_record_max(v.res_max + step, fmax(fabs(E13), fabs(E14)));
 }
 
-// P = (lambda^a + lambda^b) / 2, U = (lambda^b - lambda^a) / (2 beta)
+// P = (lambda^a + lambda^b) / 2, U = (lambda^b - lambda^a) / (2 beta) into the
+// refined state (set, or added in double-double), then the state's Robin
+// data lambda^a = P - beta U, lambda^b = P + beta U in double-double.
 __global__ void lam_to_PU_kernel(DevView v, bool accumulate) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= v.nseg) return;
     const double la = v.lam[v.seg_lam_a[t]], lb = v.lam[v.seg_lam_b[t]];
+    const double beta = v.seg_beta[t];
     const double P = 0.5 * (la + lb);
-    const double U = (lb - la) / (2.0 * v.seg_beta[t]);
+    const double U = (lb - la) / (2.0 * beta);
+    DD xp = {P, 0.0}, xu = {U, 0.0};
     if (accumulate) {
-        const DD xp = dd_add(DD{v.segP[t], v.segP_lo[t]}, DD{P, 0.0});
-        const DD xu = dd_add(DD{v.segU[t], v.segU_lo[t]}, DD{U, 0.0});
-        v.segP[t] = xp.h;
-        v.segP_lo[t] = xp.l;
-        v.segU[t] = xu.h;
-        v.segU_lo[t] = xu.l;
-    } else {
-        v.segP[t] = P;
-        v.segP_lo[t] = 0.0;
-        v.segU[t] = U;
-        v.segU_lo[t] = 0.0;
+        xp = dd_add(DD{v.segP[t], v.segP_lo[t]}, xp);
+        xu = dd_add(DD{v.segU[t], v.segU_lo[t]}, xu);
     }
+    v.segP[t] = xp.h;
+    v.segP_lo[t] = xp.l;
+    v.segU[t] = xu.h;
+    v.segU_lo[t] = xu.l;
+    const DD bu = dd_mul_d(xu, beta);
+    const DD lam_a = dd_add(xp, dd_neg(bu)), lam_b = dd_add(xp, bu);
+    v.seg_lam_dd[2 * t] = make_double2(lam_a.h, lam_a.l);
+    v.seg_lam_dd[2 * t + 1] = make_double2(lam_b.h, lam_b.l);
 }
 
 // Cell pressures and face fluxes (+axis direction) from the double-double
 // state, each formed in double-double and rounded once.  Skeleton faces: the
-// one-sided F^a = rho^a (p_a - P + beta U), F^b = -(rho^b (p_b - P - beta U))
+// one-sided F^a = rho^a (p_a - lambda^a), F^b = -(rho^b (p_b - lambda^b))
 // and their mean.
 __global__ void face_flux_kernel(DevView v, const double* __restrict__ bc_val, double* __restrict__ p,
                                  double* __restrict__ Fx, double* __restrict__ Fy, double* __restrict__ iface) {
@@ -177,7 +184,7 @@ __global__ void face_flux_kernel(DevView v, const double* __restrict__ bc_val, d
     const long long nyf = (long long)v.nx * (v.ny + 1);
     const long long ncell = (long long)v.nx * v.ny;
     long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (f < ncell) p[f] = dd_round(state_p(v, f));
+    if (f < ncell) p[f] = v.p_hi[f] + v.p_lo[f];
     if (f >= nxf + nyf) return;
     const bool xface = f < nxf;
     const long long fl = xface ? f : f - nxf;
@@ -195,26 +202,26 @@ __global__ void face_flux_kernel(DevView v, const double* __restrict__ bc_val, d
     const double area = axis == 0 ? v.hy : v.hx;
     if (line == 0) {
         const double g = bc_val[axis == 0 ? k : 2 * v.ny + k];
-        const double out = v.bc[2 * axis] ? dd_round(dd_mul_d(dd_add(state_p(v, cb), DD{-g, 0.0}), cU[fl]))
-                                          : __dmul_rn(area, g);
-        F = -out;
+        DD out = v.bc[2 * axis] ? face_out_u(state_p(v, cb), DD{g, 0.0}, cU[fl]) : DD{__dmul_rn(area, g), 0.0};
+        F = -(out.h + out.l);
     } else if (line == nline) {
         const double g = bc_val[axis == 0 ? v.ny + k : 2 * v.ny + v.nx + k];
-        const double out = v.bc[2 * axis + 1]
-                               ? dd_round(dd_mul_d(dd_add(state_p(v, ca), DD{-g, 0.0}), cL[fl]))
-                               : __dmul_rn(area, g);
-        F = out;
-    } else if (axis == 0 ? x_skeleton(v, line) : y_skeleton(v, line)) {
-        const int t = skeleton_segment(v, axis, line, k);
-        const DD P = state_P(v, t), bu = state_bu(v, t);
-        const DD da = dd_mul_d(robin_gap(state_p(v, ca), P, bu, 1.0), cL[fl]);
-        const DD db = dd_mul_d(robin_gap(state_p(v, cb), P, bu, -1.0), cU[fl]);
-        fa = dd_round(da);
-        fb = -dd_round(db);
-        F = __dmul_rn(0.5, dd_round(dd_add(da, dd_neg(db))));
-        skel = true;
+        DD out = v.bc[2 * axis + 1] ? face_out_u(state_p(v, ca), DD{g, 0.0}, cL[fl]) : DD{__dmul_rn(area, g), 0.0};
+        F = out.h + out.l;
     } else {
-        F = dd_round(dd_mul_d(dd_add(state_p(v, ca), dd_neg(state_p(v, cb))), cL[fl]));
+        const int t = axis == 0 ? v.xface_seg[fl] : v.yface_seg[fl];
+        if (t >= 0) {
+            const DD da = face_out_u(state_p(v, ca), seg_lam(v, t, 0), cL[fl]);
+            const DD db = face_out_u(state_p(v, cb), seg_lam(v, t, 1), cU[fl]);
+            fa = da.h + da.l;
+            fb = -(db.h + db.l);
+            const DD dm = dd_sub_u(da, db);
+            F = 0.5 * (dm.h + dm.l);
+            skel = true;
+        } else {
+            const DD d = face_out_u(state_p(v, ca), state_p(v, cb), cL[fl]);
+            F = d.h + d.l;
+        }
     }
     if (xface) {
         Fx[fl] = F;

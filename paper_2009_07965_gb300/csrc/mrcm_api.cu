@@ -35,6 +35,7 @@ struct Plan {
     std::vector<int> seg_axis, seg_line, seg_lo, seg_len, seg_a, seg_b, seg_face_off;
     int nseg = 0;
     long long nskel_faces = 0;
+    std::vector<int> xface_seg, yface_seg;   // segment of each x- / y-face, -1 off the skeleton
     // tree (nodes 0..nleaf-1 are the leaves)
     struct Node {
         int box[4];
@@ -112,6 +113,15 @@ int make_plan(Plan& P) {
     P.seg_face_off[0] = 0;
     for (int t = 0; t < P.nseg; ++t) P.seg_face_off[t + 1] = P.seg_face_off[t] + P.seg_len[t];
     P.nskel_faces = P.seg_face_off[P.nseg];
+    P.xface_seg.assign((size_t)(P.nx + 1) * P.ny, -1);
+    P.yface_seg.assign((size_t)P.nx * (P.ny + 1), -1);
+    for (int t = 0; t < P.nseg; ++t) {
+        for (int e = 0; e < P.seg_len[t]; ++e) {
+            const int k = P.seg_lo[t] + e;
+            if (P.seg_axis[t] == 0) P.xface_seg[(size_t)P.seg_line[t] + (size_t)(P.nx + 1) * k] = t;
+            else P.yface_seg[(size_t)k + (size_t)P.nx * P.seg_line[t]] = t;
+        }
+    }
     // leaf segment lists: x-, x+, y-, y+ sides
     for (int id = 0; id < P.nleaf; ++id) {
         const int I = id % P.Nlx, J = id / P.Nlx;
@@ -544,6 +554,9 @@ static int setup_impl(mrcm_ctx* c, const mrcm_grid* g, const double* K_dev, cons
     TRY(upload(c, &v.seg_a, P.seg_a));
     TRY(upload(c, &v.seg_b, P.seg_b));
     TRY(upload(c, &v.seg_face_off, P.seg_face_off));
+    TRY(upload(c, &v.xface_seg, P.xface_seg));
+    TRY(upload(c, &v.yface_seg, P.yface_seg));
+    TRY(dev_alloc(c, &v.seg_lam_dd, 2LL * P.nseg));
     TRY(upload(c, &v.seg_lam_a, P.seg_lam_a));
     TRY(upload(c, &v.seg_lam_b, P.seg_lam_b));
     TRY(upload(c, &v.leaves, P.leaves));

@@ -73,6 +73,10 @@ struct DevView {
     const int* seg_a; const int* seg_b; const int* seg_face_off;
     const long long* seg_lam_a;   // offset in lam of segment t in the leaf on side a
     const long long* seg_lam_b;   //                                   ... side b
+    const int* xface_seg;         // (nx+1)*ny: segment of each x-face, -1 off the skeleton
+    const int* yface_seg;         // nx*(ny+1): segment of each y-face
+    double2* seg_lam_dd;          // per segment: Robin data of side a, of side b
+                                  // (P -/+ beta U of the refined state, double-double)
     // leaves and tree
     const LeafDesc* leaves;
     const int* leaf_segs;
