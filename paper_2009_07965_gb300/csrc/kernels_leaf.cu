@@ -136,7 +136,7 @@ leaf_build_kernel(DevView v) {
     const int w = L.w, n = L.w * L.h, m = L.m, W2 = L.w + 2;
     double* Lg = v.leafL + L.L_off;          // n x 16 multipliers
     double* Dg = Lg + (long long)n * kLeafThreads;   // n reciprocal pivots
-    double* Zg = v.leafZ + L.Z_off;          // n x m (local segment order)
+    double* Zg = v.leafZ + L.Z_off;          // n x m, column-major (local segment order)
 
     // Columns of B ordered by their first nonzero row: column q of Z stays
     // zero above start[q], so only the first c_k ordered columns take part
@@ -190,7 +190,7 @@ leaf_build_kernel(DevView v) {
         __syncwarp(mask);
         for (int s = t; s < m; s += kLeafThreads) {
             const int q = S.pos[s];
-            Zg[(long long)k * m + s] = q < ck ? S.zk[q] : 0.0;
+            Zg[(long long)s * n + k] = q < ck ? S.zk[q] : 0.0;
         }
         // ---- phase B: trailing band update, Z update, R update, new row -----
         const int ntri_w = wk * (wk + 1) / 2;
@@ -257,9 +257,12 @@ __device__ __forceinline__ double particular_rhs(const DevView& v, const LeafDes
 }
 
 struct LeafSolveSmem {
-    double buf[kWin];                                  // circular sweep rows
-    double y[kMaxLeafSide * kMaxLeafSide];             // D^-1 z (or the pressures)
+    double y[kMaxLeafSide * kMaxLeafSide];             // right-hand side, swept in place
 };
+
+// Depth of the register ring that prefetches the band multipliers of the
+// sweeps (rows streamed from HBM ahead of the sequential elimination chain).
+constexpr int kSweepAhead = 8;
 
 template <int LPB>
 __global__ void __launch_bounds__(kLeafThreads * LPB)
@@ -273,44 +276,48 @@ leaf_particular_kernel(DevView v, const double* __restrict__ q, const double* __
     const unsigned mask = 0xFFFFu << (threadIdx.x & 16);
     LeafSolveSmem& S = smem[slot_leaf];
     const LeafDesc L = v.leaves[leaf];
-    const int w = L.w, n = L.w * L.h, m = L.m, W2 = L.w + 2;
+    const int w = L.w, n = L.w * L.h, m = L.m;
     const double* Lg = v.leafL + L.L_off;
     const double* Dg = Lg + (long long)n * kLeafThreads;
     const double* Zg = v.leafZ + L.Z_off;
     double* zb = v.leafzb + L.zb_off;
 
     // forward sweep zbar = L^-1 bbar (unit lower band); the right-hand side
-    // is formed for all rows first, and each step's multiplier is loaded one
-    // step ahead so that no global load sits on the sequential chain
+    // is formed for all rows first, the multipliers stream through a
+    // register ring kSweepAhead steps ahead of their use
     for (int r = t; r < n; r += kLeafThreads) S.y[r] = particular_rhs(v, L, q, bc_val, r);
     __syncwarp(mask);
-    const int first = min(w, n - 1);
-    for (int r = t; r <= first; r += kLeafThreads) S.buf[r % W2] = S.y[r];
-    __syncwarp(mask);
-    double lnext = (t < min(w, n - 1)) ? Lg[t] : 0.0;
-    for (int k = 0; k < n; ++k) {
-        const double lk = lnext;
-        if (k + 1 < n && t < min(w, n - 2 - k)) lnext = Lg[(long long)(k + 1) * kLeafThreads + t];
-        const double zk = S.buf[k % W2];
-        const int wk = min(w, n - 1 - k);
-        if (t < wk) S.buf[(k + 1 + t) % W2] -= lk * zk;
-        if (t == 0) {
-            zb[k] = zk;
-            if (k + w + 1 < n) S.buf[(k + w + 1) % W2] = S.y[k + w + 1];
+    double ring[kSweepAhead];
+#pragma unroll
+    for (int d = 0; d < kSweepAhead; ++d) ring[d] = (d < n && t < min(w, n - 1 - d)) ? Lg[(long long)d * kLeafThreads + t] : 0.0;
+    for (int k0 = 0; k0 < n; k0 += kSweepAhead) {
+#pragma unroll
+        for (int d = 0; d < kSweepAhead; ++d) {
+            const int k = k0 + d;
+            if (k >= n) break;
+            const double lk = ring[d];
+            const int kn = k + kSweepAhead;
+            ring[d] = (kn < n && t < min(w, n - 1 - kn)) ? Lg[(long long)kn * kLeafThreads + t] : 0.0;
+            const double zk = S.y[k];
+            if (t < min(w, n - 1 - k)) S.y[k + 1 + t] = fma(-lk, zk, S.y[k + 1 + t]);
+            __syncwarp(mask);
         }
-        __syncwarp(mask);
     }
-    // y = D^-1 zbar ; rbar = Z^T y  (= B^T A^-1 bbar)
-    for (int k = t; k < n; k += kLeafThreads) S.y[k] = zb[k] * Dg[k];
+    for (int k = t; k < n; k += kLeafThreads) zb[k] = S.y[k];
+    // y = D^-1 zbar ; rbar = Z^T y  (= B^T A^-1 bbar): the 16 lanes share
+    // every column of Z (consecutive rows, coalesced) and reduce by shuffles
+    for (int k = t; k < n; k += kLeafThreads) S.y[k] *= Dg[k];
     __syncwarp(mask);
     double* rb = v.rbar + L.r_off;
-    for (int s = t; s < m; s += kLeafThreads) {
+    for (int s = 0; s < m; ++s) {
+        const double* zc = Zg + (long long)s * n;
         double acc = 0.0;
-        for (int k = 0; k < n; ++k) acc += Zg[(long long)k * m + s] * S.y[k];
+        for (int k = t; k < n; k += kLeafThreads) acc = fma(zc[k], S.y[k], acc);
+#pragma unroll
+        for (int o = kLeafThreads / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(mask, acc, o);
         // a right-hand side sigma on this segment's interface row,
         // F - D (lambda_other - lambda_own) = sigma, acts as rbar - sigma
-        if (with_sadj) acc -= v.sadj[L.r_off + s];
-        rb[s] = acc;
+        if (t == 0) rb[s] = with_sadj ? acc - v.sadj[L.r_off + s] : acc;
     }
 }
 
@@ -329,40 +336,45 @@ leaf_pressure_kernel(DevView v, bool accumulate) {
     LeafSolveSmem& S = smem[slot_leaf];
     double* lam = lam_s[slot_leaf];
     const LeafDesc L = v.leaves[leaf];
-    const int w = L.w, n = L.w * L.h, m = L.m, W2 = L.w + 2;
+    const int w = L.w, n = L.w * L.h, m = L.m;
     const double* Lg = v.leafL + L.L_off;
     const double* Dg = Lg + (long long)n * kLeafThreads;
     const double* Zg = v.leafZ + L.Z_off;
     const double* zb = v.leafzb + L.zb_off;
     for (int s = t; s < m; s += kLeafThreads) lam[s] = v.lam[L.r_off + s];
     __syncwarp(mask);
-    // y = D^-1 (zbar + Z lambda)
+    // y = D^-1 (zbar + Z lambda), Z column-major: consecutive rows per lane
     for (int k = t; k < n; k += kLeafThreads) {
-        double acc = zb[k];
-        for (int s = 0; s < m; ++s) acc += Zg[(long long)k * m + s] * lam[s];
-        S.y[k] = acc * Dg[k];
+        double acc0 = zb[k], acc1 = 0.0;
+        int s = 0;
+        for (; s + 1 < m; s += 2) {
+            acc0 = fma(Zg[(long long)s * n + k], lam[s], acc0);
+            acc1 = fma(Zg[(long long)(s + 1) * n + k], lam[s + 1], acc1);
+        }
+        if (s < m) acc0 = fma(Zg[(long long)s * n + k], lam[s], acc0);
+        S.y[k] = (acc0 + acc1) * Dg[k];
     }
     __syncwarp(mask);
-    // backward sweep L^T p = y, right-looking from the last row; the
-    // multiplier of each step is loaded one step ahead
-    const int first = min(w, n - 1);
-    for (int r = t; r <= first; r += kLeafThreads) S.buf[(n - 1 - r) % W2] = S.y[n - 1 - r];
-    __syncwarp(mask);
-    double lnext = (t < min(w, n - 1)) ? Lg[(long long)(n - 2 - t) * kLeafThreads + t] : 0.0;
-    for (int k = n - 1; k >= 0; --k) {
-        const double lk = lnext;
-        if (k >= 1 && t < min(w, k - 1)) lnext = Lg[(long long)(k - 2 - t) * kLeafThreads + t];
-        const double pk = S.buf[k % W2];
-        const int wk = min(w, k);
-        if (t < wk) {
-            const int i = k - 1 - t;   // row of L^T: entry L[k][i] = multiplier (i, k - i - 1)
-            S.buf[i % W2] -= lk * pk;
+    // backward sweep L^T p = y in place, right-looking from the last row;
+    // the multipliers stream through a register ring kSweepAhead steps ahead
+    double ring[kSweepAhead];
+#pragma unroll
+    for (int d = 0; d < kSweepAhead; ++d) {
+        const int k = n - 1 - d;
+        ring[d] = (k >= 1 && t < min(w, k)) ? Lg[(long long)(k - 1 - t) * kLeafThreads + t] : 0.0;
+    }
+    for (int k0 = n - 1; k0 >= 0; k0 -= kSweepAhead) {
+#pragma unroll
+        for (int d = 0; d < kSweepAhead; ++d) {
+            const int k = k0 - d;
+            if (k < 0) break;
+            const double lk = ring[d];
+            const int kn = k - kSweepAhead;
+            ring[d] = (kn >= 1 && t < min(w, kn)) ? Lg[(long long)(kn - 1 - t) * kLeafThreads + t] : 0.0;
+            const double pk = S.y[k];
+            if (t < min(w, k)) S.y[k - 1 - t] = fma(-lk, pk, S.y[k - 1 - t]);   // entry L[k][k-1-t]
+            __syncwarp(mask);
         }
-        if (t == 0) {
-            S.y[k] = pk;   // y[k] is no longer needed: keep p in its place
-            if (k - w - 1 >= 0) S.buf[(k - w - 1) % W2] = S.y[k - w - 1];
-        }
-        __syncwarp(mask);
     }
     for (int k = t; k < n; k += kLeafThreads) {
         const int i = k % w, j = k / w;

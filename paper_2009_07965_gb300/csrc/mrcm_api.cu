@@ -370,7 +370,7 @@ struct mrcm_ctx {
     int ev_used = 0;
     double* gj_scratch = nullptr;
     unsigned long long* gj_barrier = nullptr;
-    int refine_steps = 2;
+    int refine_steps = 1;
     int refine_check = 0;
     int hist_count = 0;
 };

@@ -200,6 +200,28 @@ def test_refinement_converges(mrcm_lib):
     _compare(g, solve_mrcm(prob), keys=("p", "Fx", "Fy"))
 
 
+def test_unrefined_solve_is_close_to_the_refined_one(mrcm_lib):
+    # the quasi-definite interface inverses keep the plain FP64 solve of a
+    # high-contrast field close to the discrete solution; one refinement
+    # step (the default) then reaches the rounding level
+    import paper_2009_07965_gb300 as mr
+    import torch
+    prob = inputs.darcy_problem(256, 256, sigma2=4.0, corr=0.05, seed=2001, bc="quarter_five_spot")
+    s = mr.Solver(torch.from_numpy(prob.K).cuda(), sub=prob.sub, seg=prob.seg, alpha=prob.alpha,
+                  bc_type=prob.bc_type)
+    s.build_basis()
+    q, bc = torch.from_numpy(prob.q).cuda(), torch.from_numpy(prob.bc_val).cuda()
+    out = {}
+    for k in (0, 1, 3):
+        mr.mrcm_set_refinement(s.ctx, k)
+        s.solve(q, bc)
+        out[k] = [t.cpu().numpy().copy() for t in (s.p, s.Fx, s.Fy)]
+    for a, b in zip(out[0], out[3]):
+        assert rel(a, b) < 1e-9
+    for a, b in zip(out[1], out[3]):
+        assert rel(a, b) < 1e-14
+
+
 def test_square512_same_recipe_as_benchmark(mrcm_lib):
     # the benchmark recipe (sigma^2 = 4, corr 0.05, quarter-five-spot) at
     # 512^2: 1024 leaves, 10 levels, interface systems up to 2g = 256
