@@ -236,6 +236,17 @@ int mrcm_enable_timing(mrcm_ctx* ctx, int on);
 int mrcm_phase_times(mrcm_ctx* ctx, double* ms);
 
 /*
+ * mrcm_check_reciprocal -- self-check of the reciprocal the interface and
+ * leaf kernels use on their sequential pivot chains (Newton-Raphson from a
+ * single-precision seed, within an ulp of 1/x); the paper has no
+ * counterpart.  r_dev[i] = 1/x_dev[i] for i < n, both device arrays of n
+ * doubles owned by the caller, on cuda_stream (NULL: legacy default
+ * stream); synchronises the stream.  Returns MRCM_OK, MRCM_ERR_INVALID_ARG
+ * (null pointer, n < 0) or MRCM_ERR_CUDA.
+ */
+int mrcm_check_reciprocal(const double* x_dev, double* r_dev, long long n, void* cuda_stream);
+
+/*
  * mrcm_group_times -- the timed launch groups of the most recent build and
  * solve in launch order: phase[k] (host) its phase id, ms[k] (host) its
  * duration, for k < min(count, cap).  Returns the number of groups recorded

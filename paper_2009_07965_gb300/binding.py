@@ -25,7 +25,7 @@ EXPORTS = ["mrcm_setup", "mrcm_plan_query", "mrcm_set_permeability", "mrcm_build
            "mrcm_node_info", "mrcm_node_segments", "mrcm_segment_info", "mrcm_node_operator",
            "mrcm_destroy", "mrcm_error_string", "mrcm_enable_timing", "mrcm_phase_times",
            "mrcm_merge_pair_noalloc", "mrcm_set_refinement", "mrcm_residual_history", "mrcm_phase_flops",
-           "mrcm_group_times"]
+           "mrcm_group_times", "mrcm_check_reciprocal"]
 PHASES = ["coef", "leaf_build", "merge_small", "gj_sweep", "merge_form", "merge_x", "merge_r",
           "leaf_particular", "tree_up", "tree_down", "leaf_pressure", "residual", "finish"]
 # kernel family behind each phase (for reports)
@@ -90,6 +90,8 @@ def _lib():
         lib.mrcm_phase_flops.restype = I
         lib.mrcm_group_times.argtypes = [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), I]
         lib.mrcm_group_times.restype = I
+        lib.mrcm_check_reciprocal.argtypes = [P, P, ctypes.c_longlong, P]
+        lib.mrcm_check_reciprocal.restype = I
         lib.mrcm_set_refinement.argtypes = [P, I, I]
         lib.mrcm_set_refinement.restype = I
         lib.mrcm_residual_history.argtypes = [P, ctypes.POINTER(ctypes.c_double), I]
@@ -209,6 +211,17 @@ def mrcm_group_times(ctx, cap=4096):
     n = _lib().mrcm_group_times(ctx, ph, ms, cap)
     _check(min(n, 0), "mrcm_group_times")
     return [(PHASES[ph[k]], ms[k]) for k in range(min(n, cap))]
+
+
+def mrcm_check_reciprocal(x, out=None):
+    """The kernels' reciprocal of every entry of a float64 CUDA tensor."""
+    import torch
+    x = x.contiguous()
+    out = torch.empty_like(x) if out is None else out
+    stream = torch.cuda.current_stream(x.device).cuda_stream
+    _check(_lib().mrcm_check_reciprocal(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                        x.numel(), ctypes.c_void_p(stream)), "mrcm_check_reciprocal")
+    return out
 
 
 def mrcm_set_refinement(ctx, steps, check=False):

@@ -317,112 +317,173 @@ __global__ void __launch_bounds__(256) merge_form_kernel(DevView v, int first) {
 }
 
 // Scratch of the blocked sweep, per node: two buffers for the inverse P of
-// a diagonal block (kGJ x kGJ, row-major; step k uses buffer k & 1), then
-// the previous column block (2g x kGJ, column-major).
+// a diagonal block (kGJ x kGJ, row-major; block step k uses buffer k & 1),
+// two buffers for the previous column block (2g x kGJ, column-major, same
+// parity rule), and a flag word (the number of the last block whose P has
+// been published).
 constexpr int kGJScratchHead = 2 * kGJ * kGJ;
+__device__ __forceinline__ long long gj_scratch_stride(int nmax) {
+    return kGJScratchHead + 2LL * nmax * kGJ + 2;
+}
 __device__ __forceinline__ double* gj_scratch(double* scratch, int slot, int nmax) {
-    return scratch + (long long)slot * (kGJScratchHead + (long long)nmax * kGJ);
+    return scratch + (long long)slot * gj_scratch_stride(nmax);
+}
+__device__ __forceinline__ double* gj_P(double* sc, int step) { return sc + (step & 1) * kGJ * kGJ; }
+__device__ __forceinline__ double* gj_colblk(double* sc, int step, int nmax) {
+    return sc + kGJScratchHead + (long long)(step & 1) * nmax * kGJ;
+}
+__device__ __forceinline__ unsigned int* gj_flag(double* sc, int nmax) {
+    return reinterpret_cast<unsigned int*>(sc + kGJScratchHead + 2LL * nmax * kGJ);
 }
 
 struct GJSmem {
     double Cs[kGJ][kGJTile + 1];    // old column block rows of a tile: Cs[c][i]
     double Bs[kGJ][kGJTile + 1];    // block row of a tile (or P on the block columns)
-    double Ps[kGJ][kGJ + 1];        // a diagonal block being inverted
+    double Ps[kGJ][kGJ + 1];        // a diagonal block being inverted, or a P
+    double Pt[kGJ][kGJ + 1];        // second buffer of the inversion
+    double vrow[kGJ];
     double rp;
 };
 
-// Inverse of a kGJ x kGJ block held in shared memory (Ps[r][c], identity
-// padding beyond nb), in place, by the whole CTA (256 threads): Gauss-Jordan
-// without pivoting; thread t owns kGJEnt consecutive entries of row
-// t / (kGJ / kGJEnt), so the row multiplier is formed once per thread; thread
-// 0 forms each pivot's reciprocal.  d_rows: rows of the block that lie in the
-// d part (positive pivots expected).  Returns false (thread 0) on a pivot of
-// the wrong sign or size.
-constexpr int kGJEnt = (kGJ * kGJ) / 256;          // entries per thread (1 or 4)
-static_assert(kGJEnt >= 1 && kGJ * kGJ == 256 * kGJEnt, "block size and CTA size");
-__device__ bool gj_invert_block(double (*Ps)[kGJ + 1], int nb, int d_rows, double* s_rp) {
-    const int tid = threadIdx.x, pr = tid / (kGJ / kGJEnt), pc0 = (tid % (kGJ / kGJEnt)) * kGJEnt;
+// Inverse of a symmetric kGJ x kGJ block held in shared memory (lower
+// triangle of Ps used; identity padding beyond nb), by the whole CTA (256
+// threads): Gauss-Jordan without pivot search on the lower triangle (after a
+// step, entries of an eliminated and a remaining index are antisymmetric,
+// all others symmetric), one entry per thread, ping-ponging between Ps and
+// Pt.  Each warp-wide FP64 instruction holds its SMSP for many cycles, so the
+// sequential part per pivot is kept to a few of them: warp 0 forms the
+// pivot's reciprocal (rcp_nr) and the scaled pivot row, warp 1 checks the
+// pivot, every kept entry takes one FMA.  On return Ps holds the full
+// inverse.  d_rows: rows of the block in the d part (positive pivots
+// expected).  Returns false (lane 0 of warp 1) on a pivot of the wrong sign
+// or size.
+__device__ bool gj_invert_block(double (*Ps)[kGJ + 1], double (*Pt)[kGJ + 1], double* vrow, int nb, int d_rows,
+                                double* s_rp) {
+    constexpr int kTri = kGJ * (kGJ + 1) / 2;
+    static_assert(kTri <= 256 && (kGJ % 2) == 0, "one entry per thread; even number of steps");
+    const int tid = threadIdx.x;
+    int r = 0, c = 0;
+    if (tid < kTri) {
+        r = (int)((sqrtf(8.0f * tid + 1.0f) - 1.0f) * 0.5f);
+        while ((r + 1) * (r + 2) / 2 <= tid) ++r;
+        while (r * (r + 1) / 2 > tid) --r;
+        c = tid - r * (r + 1) / 2;
+    }
+    double (*cur)[kGJ + 1] = Ps;
+    double (*nxt)[kGJ + 1] = Pt;
     bool ok = true;
     for (int kk = 0; kk < kGJ; ++kk) {
-        if (tid == 0) {
-            const double p = Ps[kk][kk];
-            if (kk < nb && !pivot_ok(p, kk < d_rows)) ok = false;
-            *s_rp = 1.0 / p;
+        if (tid < kGJ) {
+            const double rp = rcp_nr(cur[kk][kk]);
+            if (tid == 0) *s_rp = rp;
+            vrow[tid] = (tid <= kk ? cur[kk][tid] : cur[tid][kk]) * rp;
+        } else if (tid == 32) {
+            if (kk < nb && !pivot_ok(cur[kk][kk], kk < d_rows)) ok = false;
         }
         __syncthreads();
-        const double rp = *s_rp;
-        const double mult = Ps[pr][kk] * rp;
-        double nv[kGJEnt];
-#pragma unroll
-        for (int e = 0; e < kGJEnt; ++e) {
-            const int pc = pc0 + e;
-            const double a_kc = Ps[kk][pc];
-            if (pr == kk) nv[e] = (pc == kk) ? rp : a_kc * rp;
-            else nv[e] = (pc == kk) ? -mult : fma(-mult, a_kc, Ps[pr][pc]);
+        if (tid < kTri) {
+            const double rp = *s_rp;
+            const double a_rk = r >= kk ? cur[r][kk] : -cur[kk][r];
+            double nv;
+            if (r == kk) nv = (c == kk) ? rp : vrow[c];
+            else if (c == kk) nv = -a_rk * rp;
+            else nv = fma(-a_rk, vrow[c], cur[r][c]);
+            nxt[r][c] = nv;
         }
         __syncthreads();
-#pragma unroll
-        for (int e = 0; e < kGJEnt; ++e) Ps[pr][pc0 + e] = nv[e];
-        __syncthreads();
+        double (*t)[kGJ + 1] = cur;
+        cur = nxt;
+        nxt = t;
     }
+    // kGJ (even) swaps: the result is back in Ps; mirror the upper triangle
+    {
+        const int i = tid / kGJ, j = tid % kGJ;
+        if (i < j) Ps[i][j] = Ps[j][i];
+    }
+    __syncthreads();
     return ok;
 }
 
-// Block step at k0, part 1, for one (node, column tile of kGJRowTile): the
-// block row A_Kj <- P A_Kj on its columns, and a copy of its rows of the
-// column block A_iK before part 2 overwrites it.
+// Block row of step 0 for one (node, column tile of kGJRowTile): A_0j <-
+// P_0 A_0j on its columns, and its rows of the column block 0 into the
+// step-0 copy.  (Later block rows are formed inside the fused step.)
 constexpr int kGJRowTile = 16;
-__device__ void gj_panel_item(const DevView& v, const MergeDesc& D, int slot, int c0, int k0, double* scratch,
-                              int nmax, GJSmem& S) {
+__device__ void gj_first_row_item(const DevView& v, const MergeDesc& D, int slot, int c0, double* scratch, int nmax,
+                                  GJSmem& S) {
     const int N = 2 * D.g;
-    const int nb = min(kGJ, N - k0);
+    const int nb = min(kGJ, N);
     double* A = v.W + D.W_off;
     double* sc = gj_scratch(scratch, slot, nmax);
-    const double* Pg = sc + ((k0 / kGJ) & 1) * kGJ * kGJ;
-    double* colblk = sc + kGJScratchHead;
+    const double* Pg = gj_P(sc, 0);
+    double* colblk = gj_colblk(sc, 0, nmax);
     const int tid = threadIdx.x;
-    // rows [c0, c0 + kGJRowTile) of the column block, outside the block rows
     for (int idx = tid; idx < kGJRowTile * kGJ; idx += 256) {
         const int i = c0 + idx % kGJRowTile, cc = idx / kGJRowTile;
-        if (i < N && cc < nb && (i < k0 || i >= k0 + nb))
-            colblk[(long long)cc * N + i] = __ldcg(A + (long long)(k0 + cc) * N + i);
+        if (i < N && cc < nb && i >= nb) colblk[(long long)cc * N + i] = __ldcg(A + (long long)cc * N + i);
     }
-    // block row on columns [c0, c0 + kGJRowTile) outside the diagonal block;
-    // P staged in Cs (row-major kGJ x kGJ)
-    double* Ps = &S.Cs[0][0];
-    for (int idx = tid; idx < kGJ * kGJ; idx += 256) Ps[idx] = __ldcg(Pg + idx);
+    for (int idx = tid; idx < kGJ * kGJ; idx += 256) S.Ps[idx / kGJ][idx % kGJ] = __ldcg(Pg + idx);
     for (int idx = tid; idx < kGJ * kGJRowTile; idx += 256) {
         const int cc = idx % kGJ, jj = idx / kGJ, j = c0 + jj;
-        S.Bs[cc][jj] = (cc < nb && j < N && (j < k0 || j >= k0 + nb)) ? __ldcg(A + (long long)j * N + k0 + cc) : 0.0;
+        S.Bs[cc][jj] = (cc < nb && j < N && j >= nb) ? __ldcg(A + (long long)j * N + cc) : 0.0;
     }
     __syncthreads();
     for (int idx = tid; idx < kGJ * kGJRowTile; idx += 256) {
         const int rr = idx % kGJ, jj = idx / kGJ, j = c0 + jj;
-        if (rr >= nb || j >= N || (j >= k0 && j < k0 + nb)) continue;
+        if (rr >= nb || j >= N || j < nb) continue;
         double acc0 = 0.0, acc1 = 0.0;
 #pragma unroll
         for (int cc = 0; cc < kGJ; cc += 2) {
-            acc0 = fma(Ps[rr * kGJ + cc], S.Bs[cc][jj], acc0);
-            acc1 = fma(Ps[rr * kGJ + cc + 1], S.Bs[cc + 1][jj], acc1);
+            acc0 = fma(S.Ps[rr][cc], S.Bs[cc][jj], acc0);
+            acc1 = fma(S.Ps[rr][cc + 1], S.Bs[cc + 1][jj], acc1);
         }
-        A[(long long)j * N + k0 + rr] = acc0 + acc1;
+        A[(long long)j * N + rr] = acc0 + acc1;
     }
     __syncthreads();
 }
 
-// Block step at k0, part 2, for one (node, kGJTile^2 output tile): rows
-// outside the block rows, A_ij <- A_ij - A_iK A_Kj (new block row) and
-// A_iK <- -A_iK P; the diagonal block <- P.  The next diagonal block is
-// left to gj_next_diag_item.
-__device__ void gj_update_item(const DevView& v, const MergeDesc& D, int slot, int r0, int c0, int k0,
-                               double* scratch, int nmax, GJSmem& S) {
+// Bounded wait of one CTA for a flag that another CTA of the same
+// cooperative launch raises (about a second); false on timeout
+// (kStatusTimeout set).
+constexpr long long kFlagSpins = 5000000;
+__device__ bool wait_flag(const unsigned int* flag, unsigned int value, int* status) {
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const volatile unsigned int* vf = flag;
+        long long spins = 0;
+        while (*vf < value) {
+            if (++spins > kFlagSpins) {
+                ok = 0;
+                atomicOr(status, kStatusTimeout);
+                break;
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Block step k (block K = [k0, k0 + nb)), for one (node, kGJTile^2 output
+// tile), fused with the preparation of step k + 1 (block K1):
+//   rows outside K: A_ij <- A_ij - A_iK A_Kj (block row already formed) and
+//   A_iK <- -A_iK P_k; the diagonal block <- P_k; the block K1 x K1 is left
+//   to gj_next_diag_item;
+//   then, if the tile holds columns of K1, its rows of the new column block
+//   (all rows outside K1) go to the step-(k+1) copy; and if it holds the rows
+//   of K1, it waits for P_{k+1} and forms its part of the block row of step
+//   k + 1, A_{K1 j} <- P_{k+1} A_{K1 j}.
+// Returns false when a wait timed out.
+__device__ bool gj_step_item(const DevView& v, const MergeDesc& D, int slot, int r0, int c0, int step,
+                             double* scratch, int nmax, GJSmem& S) {
     const int N = 2 * D.g;
-    const int nb = min(kGJ, N - k0);
-    const int k1 = k0 + kGJ;                      // next diagonal block [k1, k1 + nb1)
+    const int k0 = step * kGJ, nb = min(kGJ, N - k0);
+    const int k1 = k0 + kGJ, nb1 = k1 < N ? min(kGJ, N - k1) : 0;
     double* A = v.W + D.W_off;
     double* sc = gj_scratch(scratch, slot, nmax);
-    const double* Pg = sc + ((k0 / kGJ) & 1) * kGJ * kGJ;
-    const double* colblk = sc + kGJScratchHead;
+    const double* Pg = gj_P(sc, step);
+    const double* colblk = gj_colblk(sc, step, nmax);
     const int tid = threadIdx.x;
     for (int idx = tid; idx < kGJ * kGJTile; idx += 256) {
         const int ii = idx % kGJTile, cc = idx / kGJTile, i = r0 + ii;
@@ -445,43 +506,79 @@ __device__ void gj_update_item(const DevView& v, const MergeDesc& D, int slot, i
         acc[1][0] = fma(l1, u0, acc[1][0]);
         acc[1][1] = fma(l1, u1, acc[1][1]);
     }
+    double* colnext = gj_colblk(sc, step + 1, nmax);
 #pragma unroll
     for (int b = 0; b < 2; ++b) {
         const int j = c0 + tc + b;
         if (j >= N) continue;
         const bool jK = j >= k0 && j < k0 + nb;
-        const bool jK1 = j >= k1 && j < k1 + kGJ;
+        const bool jK1 = j >= k1 && j < k1 + nb1;
         double* col = A + (long long)j * N;
 #pragma unroll
         for (int a = 0; a < 2; ++a) {
             const int i = r0 + tr + a;
             if (i >= N) continue;
             const bool iK = i >= k0 && i < k0 + nb;
+            const bool iK1 = i >= k1 && i < k1 + nb1;
+            double val;
             if (iK) {
                 if (jK) col[i] = S.Bs[i - k0][tc + b];
-            } else if (!(jK1 && i >= k1 && i < k1 + kGJ)) {
-                col[i] = (jK ? 0.0 : __ldcg(col + i)) - acc[a][b];
+                val = S.Bs[i - k0][tc + b];          // block row K: final for this step
+            } else if (jK1 && iK1) {
+                continue;                             // the next diagonal block
+            } else {
+                val = (jK ? 0.0 : __ldcg(col + i)) - acc[a][b];
+                col[i] = val;
+            }
+            if (jK1 && !iK1) colnext[(long long)(j - k1) * N + i] = val;
+        }
+    }
+    bool ok = true;
+    if (nb1 > 0 && k1 >= r0 && k1 < r0 + kGJTile) {
+        // block row of step k + 1 on this tile's columns (outside K1)
+        __syncthreads();
+        ok = wait_flag(gj_flag(sc, nmax), (unsigned int)(step + 1), v.status);
+        if (ok) {
+            const double* Pn = gj_P(sc, step + 1);
+            for (int idx = tid; idx < kGJ * kGJ; idx += 256) S.Ps[idx / kGJ][idx % kGJ] = __ldcg(Pn + idx);
+            for (int idx = tid; idx < kGJ * kGJTile; idx += 256) {
+                const int cc = idx % kGJ, jj = idx / kGJ, j = c0 + jj;
+                S.Bs[cc][jj] = (cc < nb1 && j < N && (j < k1 || j >= k1 + nb1)) ? __ldcg(A + (long long)j * N + k1 + cc)
+                                                                                 : 0.0;
+            }
+            __syncthreads();
+            for (int idx = tid; idx < kGJ * kGJTile; idx += 256) {
+                const int rr = idx % kGJ, jj = idx / kGJ, j = c0 + jj;
+                if (rr >= nb1 || j >= N || (j >= k1 && j < k1 + nb1)) continue;
+                double acc0 = 0.0, acc1 = 0.0;
+#pragma unroll
+                for (int cc = 0; cc < kGJ; cc += 2) {
+                    acc0 = fma(S.Ps[rr][cc], S.Bs[cc][jj], acc0);
+                    acc1 = fma(S.Ps[rr][cc + 1], S.Bs[cc + 1][jj], acc1);
+                }
+                A[(long long)j * N + k1 + rr] = acc0 + acc1;
             }
         }
     }
     __syncthreads();
+    return ok;
 }
 
-// Block step at k0, part 2, for the next diagonal block [k1, k1 + nb1) of a
-// node (k1 = k0 + kGJ < 2g): its update A -= A_iK A_Kj, then its inverse
-// into the other P buffer, so that part 1 of the next step finds P ready
-// (look-ahead; this item runs beside the tile updates).  Returns false on a
-// bad pivot.
-__device__ bool gj_next_diag_item(const DevView& v, const MergeDesc& D, int slot, int k0, double* scratch, int nmax,
-                                  GJSmem& S) {
+// Block step k, for the next diagonal block K1 = [k1, k1 + nb1) of a node
+// (k1 = k0 + kGJ < 2g): its update A -= A_iK A_Kj, then its inverse into the
+// P buffer of step k + 1, then the node's flag is raised to k + 1 (the tiles
+// of the next block row wait for it).  Runs before any tile item of its
+// CTA.  Returns false on a bad pivot.
+__device__ bool gj_next_diag_item(const DevView& v, const MergeDesc& D, int slot, int step, double* scratch,
+                                  int nmax, GJSmem& S) {
     const int N = 2 * D.g;
-    const int nb = min(kGJ, N - k0);
+    const int k0 = step * kGJ, nb = min(kGJ, N - k0);
     const int k1 = k0 + kGJ, nb1 = min(kGJ, N - k1);
     double* A = v.W + D.W_off;
     double* sc = gj_scratch(scratch, slot, nmax);
-    const double* colblk = sc + kGJScratchHead;
+    const double* colblk = gj_colblk(sc, step, nmax);
     const int tid = threadIdx.x;
-    // Cs[c][r]: column block rows k1 + r; Bs[c][j]: new block row columns k1 + j
+    // Cs[c][r]: column block rows k1 + r; Bs[c][j]: block row columns k1 + j
     for (int idx = tid; idx < kGJ * kGJ; idx += 256) {
         const int cc = idx / kGJ, rr = idx % kGJ;
         S.Cs[cc][rr] = (cc < nb && rr < nb1) ? __ldcg(colblk + (long long)cc * N + k1 + rr) : 0.0;
@@ -497,18 +594,16 @@ __device__ bool gj_next_diag_item(const DevView& v, const MergeDesc& D, int slot
             acc1 = fma(S.Cs[cc + 1][pr], S.Bs[cc + 1][pc], acc1);
         }
         double val = (pr == pc) ? 1.0 : 0.0;
-        if (pr < nb1 && pc < nb1) {
-            double* at = A + (long long)(k1 + pc) * N + k1 + pr;
-            val = __ldcg(at) - (acc0 + acc1);
-            *at = val;
-        }
+        if (pr < nb1 && pc < nb1) val = __ldcg(A + (long long)(k1 + pc) * N + k1 + pr) - (acc0 + acc1);
         S.Ps[pr][pc] = val;
     }
     __syncthreads();
-    const bool ok = gj_invert_block(S.Ps, nb1, D.g - k1, &S.rp);
-    double* Pn = sc + ((k1 / kGJ) & 1) * kGJ * kGJ;
+    const bool ok = gj_invert_block(S.Ps, S.Pt, S.vrow, nb1, D.g - k1, &S.rp);
+    double* Pn = gj_P(sc, step + 1);
     for (int idx = tid; idx < kGJ * kGJ; idx += 256) Pn[idx] = S.Ps[idx / kGJ][idx % kGJ];
+    __threadfence();
     __syncthreads();
+    if (tid == 0) atomicExch(gj_flag(sc, nmax), (unsigned int)(step + 1));
     return ok;
 }
 
@@ -545,15 +640,17 @@ __device__ bool grid_barrier(unsigned int* counter, unsigned int& round, int* st
 }
 
 // The whole blocked Gauss-Jordan sweep of one tree height in one cooperative
-// launch: the first diagonal block of every node, then per block step part
-// 1 over (node, column tile) items, a grid barrier, part 2 over the nodes'
-// next diagonal blocks and their (node, output tile) items, a grid barrier.
+// launch: P_0 of every node, a grid barrier, the block row and column-block
+// copy of step 0, a grid barrier, then per block step one fused phase (the
+// nodes' next diagonal blocks first, then their output tiles) and a grid
+// barrier.
 __global__ void __launch_bounds__(256) gj_sweep_kernel(DevView v, int first, int count, int nmax, double* scratch,
                                                        unsigned int* counter) {
     __shared__ GJSmem S;
     __shared__ int s_bad;
     const int rtiles = (nmax + kGJRowTile - 1) / kGJRowTile;
     const int tiles = (nmax + kGJTile - 1) / kGJTile;
+    const int nsteps = (nmax + kGJ - 1) / kGJ;
     const int tid = threadIdx.x;
     unsigned int round = 0;
     if (tid == 0) s_bad = 0;
@@ -567,34 +664,55 @@ __global__ void __launch_bounds__(256) gj_sweep_kernel(DevView v, int first, int
             S.Ps[pr][pc] = (pr < nb && pc < nb) ? __ldcg(A + (long long)pc * N + pr) : (pr == pc ? 1.0 : 0.0);
         }
         __syncthreads();
-        if (!gj_invert_block(S.Ps, nb, D.g, &S.rp)) s_bad = 1;
-        double* P0 = gj_scratch(scratch, q, nmax);
+        if (!gj_invert_block(S.Ps, S.Pt, S.vrow, nb, D.g, &S.rp)) s_bad = 1;
+        double* sc = gj_scratch(scratch, q, nmax);
+        double* P0 = gj_P(sc, 0);
         for (int idx = tid; idx < kGJ * kGJ; idx += 256) P0[idx] = S.Ps[idx / kGJ][idx % kGJ];
+        if (tid == 0) *gj_flag(sc, nmax) = 0u;
         __syncthreads();
     }
     if (!grid_barrier(counter, round, v.status)) return;
-    for (int k0 = 0; k0 < nmax; k0 += kGJ) {
-        for (int item = blockIdx.x; item < count * rtiles; item += gridDim.x) {
-            const int q = item / rtiles, c0 = (item % rtiles) * kGJRowTile;
-            const MergeDesc D = v.merges[first + q];
-            if (k0 >= 2 * D.g || c0 >= 2 * D.g) continue;     // uniform per CTA
-            gj_panel_item(v, D, q, c0, k0, scratch, nmax, S);
-        }
-        if (!grid_barrier(counter, round, v.status)) return;
+    for (int item = blockIdx.x; item < count * rtiles; item += gridDim.x) {
+        const int q = item / rtiles, c0 = (item % rtiles) * kGJRowTile;
+        const MergeDesc D = v.merges[first + q];
+        if (c0 >= 2 * D.g) continue;                         // uniform per CTA
+        gj_first_row_item(v, D, q, c0, scratch, nmax, S);
+    }
+    if (!grid_barrier(counter, round, v.status)) return;
+    for (int step = 0; step < nsteps; ++step) {
+        const int k0 = step * kGJ;
         // items [0, count): next diagonal blocks; then the output tiles
         for (int item = blockIdx.x; item < count * (1 + tiles * tiles); item += gridDim.x) {
             if (item < count) {
                 const MergeDesc D = v.merges[first + item];
                 if (k0 + kGJ >= 2 * D.g) continue;
-                if (!gj_next_diag_item(v, D, item, k0, scratch, nmax, S)) s_bad = 1;
+                if (!gj_next_diag_item(v, D, item, step, scratch, nmax, S)) s_bad = 1;
                 continue;
             }
+            // the tiles of the next block row (they wait for its P) come last
             const int it = item - count;
-            const int q = it / (tiles * tiles), t = it % (tiles * tiles);
-            const int r0 = (t % tiles) * kGJTile, c0 = (t / tiles) * kGJTile;
+            const int tk = (k0 + kGJ) / kGJTile;
+            const int head = count * (tiles - 1) * tiles;
+            int q, ti, tj;
+            if (tk < tiles && it < head) {
+                q = it / ((tiles - 1) * tiles);
+                const int t = it % ((tiles - 1) * tiles);
+                ti = t % (tiles - 1);
+                ti += ti >= tk ? 1 : 0;
+                tj = t / (tiles - 1);
+            } else if (tk < tiles) {
+                q = (it - head) / tiles;
+                ti = tk;
+                tj = (it - head) % tiles;
+            } else {
+                q = it / (tiles * tiles);
+                ti = (it % (tiles * tiles)) % tiles;
+                tj = (it % (tiles * tiles)) / tiles;
+            }
+            const int r0 = ti * kGJTile, c0 = tj * kGJTile;
             const MergeDesc D = v.merges[first + q];
             if (k0 >= 2 * D.g || r0 >= 2 * D.g || c0 >= 2 * D.g) continue;
-            gj_update_item(v, D, q, r0, c0, k0, scratch, nmax, S);
+            if (!gj_step_item(v, D, q, r0, c0, step, scratch, nmax, S)) return;
         }
         if (!grid_barrier(counter, round, v.status)) return;
     }
@@ -832,6 +950,7 @@ __global__ void __launch_bounds__(256) merge_down_kernel(DevView v, int first) {
 }  // namespace
 
 constexpr size_t kSmallSmemMax = 160 * 1024;
+constexpr int kSweepSmemPad = 120 * 1024;   // > half an SM's shared memory
 
 // shared memory of the per-node path for a level
 static size_t small_smem(int max_g2, int max_m) {
@@ -845,7 +964,7 @@ bool merge_level_blocked(int, int max_g2, int max_m) {
 
 size_t merge_scratch_doubles(int count, int max_g2, int max_m) {
     if (!merge_level_blocked(count, max_g2, max_m)) return 0;
-    return (size_t)count * (kGJScratchHead + (size_t)max_g2 * kGJ);
+    return (size_t)count * (2 * kGJ * kGJ + 2 * (size_t)max_g2 * kGJ + 2);
 }
 
 // phase ids (include/mrcm.h)
@@ -889,24 +1008,29 @@ cudaError_t launch_merge_build(const DevView& v, int first, int count, int max_g
     }
     {
         HookScope hs(hook, kPhGjSweep);
-        static int sms = 0, per_sm = 0;
+        // One CTA per SM (the unused dynamic shared memory keeps a second one
+        // off): the CTAs that invert the next diagonal blocks, which lie on
+        // the sequential chain of the sweep, then own their SM's FP64 pipe
+        // instead of queueing behind another CTA's tile updates.
+        static int sms = 0;
         if (sms == 0) {
             int dev = 0;
             if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
             if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gj_sweep_kernel, 256, 0)) != cudaSuccess)
+            if ((e = cudaFuncSetAttribute(gj_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          kSweepSmemPad)) != cudaSuccess)
                 return e;
         }
         const int tiles = (max_g2 + kGJTile - 1) / kGJTile;
         const long long items = (long long)count * (1 + tiles * tiles);
-        int grid = (int)std::min<long long>(items, (long long)sms * per_sm);
+        int grid = (int)std::min<long long>(items, (long long)sms);
         grid = grid < 1 ? 1 : grid;
         if ((e = cudaMemsetAsync(barrier, 0, sizeof(unsigned int), s)) != cudaSuccess) return e;
         unsigned int* bar = reinterpret_cast<unsigned int*>(barrier);
         DevView vv = v;
         int f = first, c = count, n = max_g2;
         void* args[] = {&vv, &f, &c, &n, &scratch, &bar};
-        e = cudaLaunchCooperativeKernel((const void*)gj_sweep_kernel, dim3(grid), dim3(256), args, 0, s);
+        e = cudaLaunchCooperativeKernel((const void*)gj_sweep_kernel, dim3(grid), dim3(256), args, kSweepSmemPad, s);
         ++*launches;
         if (e != cudaSuccess) return e;
     }

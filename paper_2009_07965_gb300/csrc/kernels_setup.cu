@@ -116,7 +116,20 @@ __global__ void face_coef_kernel(DevView v) {
     }
 }
 
+__global__ void reciprocal_kernel(const double* __restrict__ x, double* __restrict__ r, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        r[i] = rcp_nr(x[i]);
+}
+
 }  // namespace
+
+cudaError_t launch_reciprocal(const double* x, double* r, long long n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    reciprocal_kernel<<<(unsigned)blocks, 256, 0, s>>>(x, r, n);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_check_K(const DevView& v, cudaStream_t s) {
     const long long n = (long long)v.nx * v.ny;

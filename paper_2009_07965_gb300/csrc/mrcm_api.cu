@@ -846,6 +846,14 @@ int mrcm_phase_times(mrcm_ctx* c, double* ms) {
     return MRCM_OK;
 }
 
+int mrcm_check_reciprocal(const double* x_dev, double* r_dev, long long n, void* cuda_stream) {
+    if (!x_dev || !r_dev || n < 0) return MRCM_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = launch_reciprocal(x_dev, r_dev, n, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? MRCM_OK : MRCM_ERR_CUDA;
+}
+
 int mrcm_group_times(mrcm_ctx* c, int* phase, double* ms, int cap) {
     if (!c || cap < 0 || (cap > 0 && (!phase || !ms))) return MRCM_ERR_INVALID_ARG;
     TRYC(cudaStreamSynchronize(c->stream));

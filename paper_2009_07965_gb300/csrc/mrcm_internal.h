@@ -149,6 +149,32 @@ __device__ __forceinline__ DD dd_mul_d(DD x, double b) {
     return dd_two_sum(p.h, __fma_rn(x.l, b, p.l));
 }
 __device__ __forceinline__ DD dd_neg(DD x) { return {-x.h, -x.l}; }
+
+// Reciprocal by Newton-Raphson iteration from a single-precision seed
+// (Markstein; Muller et al., Handbook of Floating-Point Arithmetic, Sec. 5.3):
+// the seed is the FP32 reciprocal of p's sign, exponent and leading 23
+// mantissa bits, moved between formats with integer operations; two steps
+// x <- x + x (1 - p x) take its 2^-23 relative error to below 2^-90, so the
+// result is within an ulp of 1/p.  Four FP64 instructions on the dependent
+// chain instead of the longer IEEE division sequence, which matters where a
+// reciprocal sits on a sequential chain (pivots).  Outside the exponent
+// range of FP32 it falls back to the division.
+__device__ __forceinline__ double rcp_nr(double p) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(p);
+    const int e = (int)((bits >> 52) & 0x7ff) - 1023;
+    if (e < -120 || e > 120) return 1.0 / p;
+    const unsigned int fb = (unsigned int)(bits >> 32 & 0x80000000u) | ((unsigned int)(e + 127) << 23) |
+                            (unsigned int)(bits >> 29 & 0x7fffffu);
+    const unsigned int rb = __float_as_uint(__frcp_rn(__uint_as_float(fb)));
+    const int er = (int)((rb >> 23) & 0xff) - 127;
+    const unsigned long long xb = ((unsigned long long)(rb & 0x80000000u) << 32) |
+                                  ((unsigned long long)(er + 1023) << 52) | ((unsigned long long)(rb & 0x7fffffu) << 29);
+    double x = __longlong_as_double((long long)xb);
+    double t = fma(-p, x, 1.0);
+    x = fma(x, t, x);
+    t = fma(-p, x, 1.0);
+    return fma(x, t, x);
+}
 __device__ __forceinline__ double dd_round(DD x) { return __dadd_rn(x.h, x.l); }
 
 // x-face (i, j) / y-face (i, j) lies on the skeleton
@@ -162,6 +188,8 @@ __device__ __forceinline__ bool y_skeleton(const DevView& v, int j) {
 
 // ---- launchers (return cudaGetLastError() of the launch) -----------------
 cudaError_t launch_check_K(const DevView& v, cudaStream_t s);
+// r[i] = rcp_nr(x[i]) (self-check of the kernels' reciprocal)
+cudaError_t launch_reciprocal(const double* x, double* r, long long n, cudaStream_t s);
 cudaError_t launch_cell_resist(const DevView& v, cudaStream_t s);
 cudaError_t launch_seg_beta(const DevView& v, cudaStream_t s);
 cudaError_t launch_face_coef(const DevView& v, cudaStream_t s);

@@ -236,3 +236,22 @@ def test_square1024_quarter_five_spot_full_size(mrcm_lib):
     g = gpu_solve(prob, want_iface=True)
     errs = _compare(g, solve_mrcm(prob))
     print("1024^2 rel errors", errs)
+
+
+def test_kernel_reciprocal_within_an_ulp(mrcm_lib):
+    # the Newton-Raphson reciprocal of the pivot chains against CUDA's
+    # division (torch on the same device): within one ulp over a wide range
+    # of magnitudes, both signs, powers of two, and the fallback range
+    import paper_2009_07965_gb300 as mr
+    import torch
+    rng = np.random.default_rng(11)
+    x = np.concatenate([
+        np.exp(rng.uniform(-80.0, 80.0, 200000)) * rng.choice([-1.0, 1.0], 200000),
+        2.0 ** np.arange(-125, 126, dtype=np.float64),
+        np.array([1.0, -1.0, 3.0, 1e-40, -1e-40, 1e40, 7.5e37, 1.5e-37, 0.9999999999999999, 1.0000000000000002]),
+    ])
+    xd = torch.from_numpy(x).cuda()
+    r = mr.mrcm_check_reciprocal(xd).cpu().numpy()
+    ref = (1.0 / xd).cpu().numpy()
+    err = np.abs(r - ref) / np.spacing(np.abs(ref))
+    assert err.max() <= 1.0, (err.max(), x[np.argmax(err)])
