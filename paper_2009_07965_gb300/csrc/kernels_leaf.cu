@@ -85,7 +85,7 @@ __device__ __forceinline__ void cell_robin_segments(const DevView& v, const Leaf
 
 template <int MMAX>
 __device__ __forceinline__ void init_row(const DevView& v, const LeafDesc& L, LeafBuildSmem<MMAX>& S,
-                                         int row, int t, double* Wacc) {
+                                         int row, int t) {
     const int w = L.w, m = L.m;
     const int i = row % w, j = row / w;
     const int slot = row % (w + 2);
@@ -99,8 +99,7 @@ __device__ __forceinline__ void init_row(const DevView& v, const LeafDesc& L, Le
     }
     int sw, se, ss, sn;
     cell_robin_segments(v, L, i, j, sw, se, ss, sn);
-    int qq = 0;
-    for (int q = t; q < m; q += kLeafThreads, ++qq) {
+    for (int q = t; q < m; q += kLeafThreads) {
         const int s = S.order[q];
         double b = 0.0;
         if (s == sw) b = f.w_;
@@ -108,8 +107,25 @@ __device__ __forceinline__ void init_row(const DevView& v, const LeafDesc& L, Le
         if (s == ss) b = f.s_;
         if (s == sn) b = f.n_;
         S.zw[slot][q] = b;
-        Wacc[qq] += b;
     }
+}
+
+// Sum of the Robin coefficients rho_e over the faces of local segment s,
+// seen from the leaf's own cells (the diagonal W_s of B^T A^-1 B - W).
+__device__ __forceinline__ double segment_rho_sum(const DevView& v, const LeafDesc& L, int s) {
+    int side = 0;
+    for (int d = 1; d < 4; ++d)
+        if (L.side_off[d] >= 0 && s >= L.side_off[d]) side = d;
+    const int p = s - L.side_off[side];
+    const int len = side < 2 ? L.h : L.w, g = side < 2 ? v.gy : v.gx;
+    double sum = 0.0;
+    for (int e = p * g; e < min((p + 1) * g, len); ++e) {
+        if (side == 0) sum += v.cxU[(long long)L.i0 + (long long)(v.nx + 1) * (L.j0 + e)];
+        else if (side == 1) sum += v.cxL[(long long)(L.i0 + L.w) + (long long)(v.nx + 1) * (L.j0 + e)];
+        else if (side == 2) sum += v.cyU[(long long)(L.i0 + e) + (long long)v.nx * L.j0];
+        else sum += v.cyL[(long long)(L.i0 + e) + (long long)v.nx * (L.j0 + L.h)];
+    }
+    return sum;
 }
 
 // First row of the leaf whose cell touches local segment s (the first
@@ -157,13 +173,9 @@ leaf_build_kernel(DevView v) {
     }
     __syncwarp(mask);
 
-    constexpr int NQ = (MMAX + kLeafThreads - 1) / kLeafThreads;
-    double Wacc[NQ];
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) Wacc[q] = 0.0;
     for (int idx = t; idx < m * (MMAX + 1); idx += kLeafThreads) S.R[idx / (MMAX + 1)][idx % (MMAX + 1)] = 0.0;
     const int first = min(w, n - 1);
-    for (int r = 0; r <= first; ++r) init_row(v, L, S, r, t, Wacc);
+    for (int r = 0; r <= first; ++r) init_row(v, L, S, r, t);
     __syncwarp(mask);
 
     bool bad_pivot = false;
@@ -173,8 +185,12 @@ leaf_build_kernel(DevView v) {
         // ---- phase A: pivot, multipliers, row k of Z -------------------------
         const int sk = k % W2;
         const double dk = S.win[sk][0];
-        bad_pivot |= !(dk > 0.0);
-        const double rcp = 1.0 / dk;
+        {
+            // dk > 0 and finite, tested on the bit pattern (no FP64 compare)
+            const long long bits = __double_as_longlong(dk);
+            bad_pivot |= !(bits > 0 && bits < 0x7ff0000000000000LL);
+        }
+        const double rcp = rcp_nr(dk);
         const int wk = min(w, n - 1 - k);
         if (t < wk) {
             const double l = S.win[(k + 1 + t) % W2][1 + t] * rcp;
@@ -197,27 +213,27 @@ leaf_build_kernel(DevView v) {
         for (int idx = t; idx < ntri_w; idx += kLeafThreads) {
             int a, b;
             tri_index(idx, a, b);
-            S.win[(k + 1 + a) % W2][a - b] -= S.lcol[a] * S.win[(k + 1 + b) % W2][1 + b];
+            double& x = S.win[(k + 1 + a) % W2][a - b];
+            x = fma(-S.lcol[a], S.win[(k + 1 + b) % W2][1 + b], x);
         }
         const int nz = wk * ck;
         for (int idx = t; idx < nz; idx += kLeafThreads) {
             const int a = idx / ck, q = idx - a * ck;
-            S.zw[(k + 1 + a) % W2][q] -= S.lcol[a] * S.zk[q];
+            double& x = S.zw[(k + 1 + a) % W2][q];
+            x = fma(-S.lcol[a], S.zk[q], x);
         }
         const int ntri_m = ck * (ck + 1) / 2;
         for (int idx = t; idx < ntri_m; idx += kLeafThreads) {
             int r, c;
             tri_index(idx, r, c);
-            S.R[r][c] += S.zk[r] * S.uk[c];
+            S.R[r][c] = fma(S.zk[r], S.uk[c], S.R[r][c]);
         }
-        if (k + w + 1 < n) init_row(v, L, S, k + w + 1, t, Wacc);
+        if (k + w + 1 < n) init_row(v, L, S, k + w + 1, t);
         __syncwarp(mask);
     }
     if (bad_pivot) atomicOr(v.status, kStatusSingular);
-    {
-        int qq = 0;
-        for (int q = t; q < m; q += kLeafThreads, ++qq) S.W[q] = Wacc[qq];
-    }
+    // W_s = sum of rho over the faces of segment s (seen from this leaf)
+    for (int q = t; q < m; q += kLeafThreads) S.W[q] = segment_rho_sum(v, L, S.order[q]);
     __syncwarp(mask);
     double* Rg = v.R + L.R_off;
     for (int idx = t; idx < m * m; idx += kLeafThreads) {
