@@ -924,12 +924,28 @@ __global__ void __launch_bounds__(256) merge_down_kernel(DevView v, int first) {
     double* l1 = v.lam + D.r1_off;
     double* l2 = v.lam + D.r2_off;
     const int r = r0 + rl;
-    double acc = 0.0;
+    // four independent partial sums per thread: four loads in flight
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
     if (r < g2) {
-        for (int j = grp; j < m; j += kDownGroups) acc += X[(long long)j * g2 + r] * lam_o[j];
-        for (int k = grp; k < g2; k += kDownGroups) acc += W[(long long)k * g2 + r] * rhs[k];
+        constexpr int G = kDownGroups;
+        int j = grp;
+        for (; j + 3 * G < m; j += 4 * G) {
+            a0 = fma(X[(long long)j * g2 + r], lam_o[j], a0);
+            a1 = fma(X[(long long)(j + G) * g2 + r], lam_o[j + G], a1);
+            a2 = fma(X[(long long)(j + 2 * G) * g2 + r], lam_o[j + 2 * G], a2);
+            a3 = fma(X[(long long)(j + 3 * G) * g2 + r], lam_o[j + 3 * G], a3);
+        }
+        for (; j < m; j += G) a0 = fma(X[(long long)j * g2 + r], lam_o[j], a0);
+        int k = grp;
+        for (; k + 3 * G < g2; k += 4 * G) {
+            a0 = fma(W[(long long)k * g2 + r], rhs[k], a0);
+            a1 = fma(W[(long long)(k + G) * g2 + r], rhs[k + G], a1);
+            a2 = fma(W[(long long)(k + 2 * G) * g2 + r], rhs[k + 2 * G], a2);
+            a3 = fma(W[(long long)(k + 3 * G) * g2 + r], rhs[k + 3 * G], a3);
+        }
+        for (; k < g2; k += G) a0 = fma(W[(long long)k * g2 + r], rhs[k], a0);
     }
-    part[grp][rl] = acc;
+    part[grp][rl] = (a0 + a1) + (a2 + a3);
     __syncthreads();
     if (grp == 0 && r < g2) {
         double lg = 0.0;
