@@ -178,12 +178,28 @@ leaf_build_kernel(DevView v) {
     for (int r = 0; r <= first; ++r) init_row(v, L, S, r, t);
     __syncwarp(mask);
 
+    // per-thread index patterns of the two triangles (band update: rows a >=
+    // b of the w x w trailing block; R update: r >= c of the active columns),
+    // fixed for the whole elimination: entry idx = t + 16 e
+    constexpr int kBandEnt = (kMaxLeafSide * (kMaxLeafSide + 1) / 2 + kLeafThreads - 1) / kLeafThreads;
+    constexpr int kREnt = (MMAX * (MMAX + 1) / 2 + kLeafThreads - 1) / kLeafThreads;
+    constexpr bool kRPre = kREnt <= 12;       // keep the R pattern in registers when it is small
+    constexpr int kRReg = kRPre ? kREnt : 1;
+    int band_a[kBandEnt], band_b[kBandEnt], tri_r[kRReg], tri_c[kRReg];
+#pragma unroll
+    for (int e = 0; e < kBandEnt; ++e) tri_index(t + e * kLeafThreads, band_a[e], band_b[e]);
+    if constexpr (kRPre) {
+#pragma unroll
+        for (int e = 0; e < kREnt; ++e) tri_index(t + e * kLeafThreads, tri_r[e], tri_c[e]);
+    }
+
     bool bad_pivot = false;
     int ck = 0;                      // active ordered columns
+    int sk = 0;                      // window slot of row k (k mod W2)
     for (int k = 0; k < n; ++k) {
         while (ck < m && S.start[ck] <= k) ++ck;
+        const int s1 = sk + 1 == W2 ? 0 : sk + 1;        // slot of row k + 1
         // ---- phase A: pivot, multipliers, row k of Z -------------------------
-        const int sk = k % W2;
         const double dk = S.win[sk][0];
         {
             // dk > 0 and finite, tested on the bit pattern (no FP64 compare)
@@ -193,7 +209,9 @@ leaf_build_kernel(DevView v) {
         const double rcp = rcp_nr(dk);
         const int wk = min(w, n - 1 - k);
         if (t < wk) {
-            const double l = S.win[(k + 1 + t) % W2][1 + t] * rcp;
+            int sl = s1 + t;
+            sl -= sl >= W2 ? W2 : 0;
+            const double l = S.win[sl][1 + t] * rcp;
             S.lcol[t] = l;
             Lg[(long long)k * kLeafThreads + t] = l;
         }
@@ -210,26 +228,51 @@ leaf_build_kernel(DevView v) {
         }
         // ---- phase B: trailing band update, Z update, R update, new row -----
         const int ntri_w = wk * (wk + 1) / 2;
-        for (int idx = t; idx < ntri_w; idx += kLeafThreads) {
-            int a, b;
-            tri_index(idx, a, b);
-            double& x = S.win[(k + 1 + a) % W2][a - b];
-            x = fma(-S.lcol[a], S.win[(k + 1 + b) % W2][1 + b], x);
+#pragma unroll
+        for (int e = 0; e < kBandEnt; ++e) {
+            if (t + e * kLeafThreads >= ntri_w) break;
+            const int a = band_a[e], b = band_b[e];
+            int ra = s1 + a, rb = s1 + b;
+            ra -= ra >= W2 ? W2 : 0;
+            rb -= rb >= W2 ? W2 : 0;
+            double& x = S.win[ra][a - b];
+            x = fma(-S.lcol[a], S.win[rb][1 + b], x);
         }
-        const int nz = wk * ck;
-        for (int idx = t; idx < nz; idx += kLeafThreads) {
-            const int a = idx / ck, q = idx - a * ck;
-            double& x = S.zw[(k + 1 + a) % W2][q];
-            x = fma(-S.lcol[a], S.zk[q], x);
+        if (ck > 0) {
+            // (row a, column q) of entry idx = a ck + q, stepped by 16 entries
+            const int nz = wk * ck, da = kLeafThreads / ck, dq = kLeafThreads - da * ck;
+            int a = t / ck, q = t - a * ck;
+            for (int idx = t; idx < nz; idx += kLeafThreads) {
+                int ra = s1 + a;
+                ra -= ra >= W2 ? W2 : 0;
+                double& x = S.zw[ra][q];
+                x = fma(-S.lcol[a], S.zk[q], x);
+                a += da;
+                q += dq;
+                if (q >= ck) {
+                    q -= ck;
+                    ++a;
+                }
+            }
         }
         const int ntri_m = ck * (ck + 1) / 2;
-        for (int idx = t; idx < ntri_m; idx += kLeafThreads) {
-            int r, c;
-            tri_index(idx, r, c);
-            S.R[r][c] = fma(S.zk[r], S.uk[c], S.R[r][c]);
+        if constexpr (kRPre) {
+#pragma unroll
+            for (int e = 0; e < kREnt; ++e) {
+                if (t + e * kLeafThreads >= ntri_m) break;
+                const int r = tri_r[e], c = tri_c[e];
+                S.R[r][c] = fma(S.zk[r], S.uk[c], S.R[r][c]);
+            }
+        } else {
+            for (int idx = t; idx < ntri_m; idx += kLeafThreads) {
+                int r, c;
+                tri_index(idx, r, c);
+                S.R[r][c] = fma(S.zk[r], S.uk[c], S.R[r][c]);
+            }
         }
         if (k + w + 1 < n) init_row(v, L, S, k + w + 1, t);
         __syncwarp(mask);
+        sk = s1;
     }
     if (bad_pivot) atomicOr(v.status, kStatusSingular);
     // W_s = sum of rho over the faces of segment s (seen from this leaf)
