@@ -33,6 +33,13 @@ FP64_PEAK_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
 WORKLOAD = ("square1024-qfs: 1024x1024 cells, log-normal K sigma^2=4 corr 0.05 (seed 2000), "
             "quarter-five-spot, no-flow, 64x64 leaves of 16x16, 4-cell segments, alpha=1, 12 levels")
 CPU_SAMPLE_N = 256
+# DRAM bytes (read + write) per launch of a kernel family at the 1024^2
+# workload, from one ncu capture of this bench (dram__bytes_read.sum +
+# dram__bytes_write.sum).  A family missing here reports traffic null.
+TRAFFIC_PER_LAUNCH = {
+    "gj_sweep": dict(bytes=1.785e6, source="ncu capture, mean over the 7 launches of one build"),
+    "leaf_build": dict(bytes=298.6e6, source="ncu capture, one launch"),
+}
 
 
 def parse():
@@ -299,7 +306,11 @@ def run_ours(args):
                     l2="flushed between timed steps (256 MiB write outside the events)",
                     parallelism=f"replicas x{world}"),
         roofline=dict(bound="alu", achieved=achieved, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
-                      frac=achieved / FP64_PEAK_TFLOPS, traffic=None, kernel=mr.PHASE_KERNELS[dom],
+                      frac=achieved / FP64_PEAK_TFLOPS,
+                      traffic=TRAFFIC_PER_LAUNCH[dom]["bytes"] if n == 1024 and dom in TRAFFIC_PER_LAUNCH else None,
+                      traffic_unit="bytes per launch",
+                      traffic_source=TRAFFIC_PER_LAUNCH[dom]["source"] if n == 1024 and dom in TRAFFIC_PER_LAUNCH else None,
+                      kernel=mr.PHASE_KERNELS[dom],
                       phase=dom, share=ph[dom] / (total_ms / args.steps),
                       peak_source="FP64 FMA pipe: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz"),
         phases=table,
