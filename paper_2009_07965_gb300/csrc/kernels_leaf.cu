@@ -152,6 +152,7 @@ leaf_build_kernel(DevView v) {
     const int w = L.w, n = L.w * L.h, m = L.m, W2 = L.w + 2;
     double* Lg = v.leafL + L.L_off;          // n x 16 multipliers
     double* Dg = Lg + (long long)n * kLeafThreads;   // n reciprocal pivots
+    double* LTg = Dg + n;                    // n x 16 multipliers by row
     double* Zg = v.leafZ + L.Z_off;          // n x m, column-major (local segment order)
 
     // Columns of B ordered by their first nonzero row: column q of Z stays
@@ -214,6 +215,7 @@ leaf_build_kernel(DevView v) {
             const double l = S.win[sl][1 + t] * rcp;
             S.lcol[t] = l;
             Lg[(long long)k * kLeafThreads + t] = l;
+            LTg[(long long)(k + 1 + t) * kLeafThreads + t] = l;
         }
         if (t == 0) Dg[k] = rcp;
         for (int q = t; q < ck; q += kLeafThreads) {
@@ -370,8 +372,16 @@ leaf_particular_kernel(DevView v, const double* __restrict__ q, const double* __
     double* rb = v.rbar + L.r_off;
     for (int s = 0; s < m; ++s) {
         const double* zc = Zg + (long long)s * n;
-        double acc = 0.0;
-        for (int k = t; k < n; k += kLeafThreads) acc = fma(zc[k], S.y[k], acc);
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        int k = t;
+        for (; k + 3 * kLeafThreads < n; k += 4 * kLeafThreads) {
+            a0 = fma(zc[k], S.y[k], a0);
+            a1 = fma(zc[k + kLeafThreads], S.y[k + kLeafThreads], a1);
+            a2 = fma(zc[k + 2 * kLeafThreads], S.y[k + 2 * kLeafThreads], a2);
+            a3 = fma(zc[k + 3 * kLeafThreads], S.y[k + 3 * kLeafThreads], a3);
+        }
+        for (; k < n; k += kLeafThreads) a0 = fma(zc[k], S.y[k], a0);
+        double acc = (a0 + a1) + (a2 + a3);
 #pragma unroll
         for (int o = kLeafThreads / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(mask, acc, o);
         // a right-hand side sigma on this segment's interface row,
@@ -402,25 +412,40 @@ leaf_pressure_kernel(DevView v, bool accumulate) {
     const double* zb = v.leafzb + L.zb_off;
     for (int s = t; s < m; s += kLeafThreads) lam[s] = v.lam[L.r_off + s];
     __syncwarp(mask);
-    // y = D^-1 (zbar + Z lambda), Z column-major: consecutive rows per lane
-    for (int k = t; k < n; k += kLeafThreads) {
-        double acc0 = zb[k], acc1 = 0.0;
-        int s = 0;
-        for (; s + 1 < m; s += 2) {
-            acc0 = fma(Zg[(long long)s * n + k], lam[s], acc0);
-            acc1 = fma(Zg[(long long)(s + 1) * n + k], lam[s + 1], acc1);
+    // y = D^-1 (zbar + Z lambda), Z column-major: the lane's rows
+    // k = t + 16 r accumulate together, one column at a time, so that
+    // kRows independent loads are in flight per lane
+    constexpr int kRows = kMaxLeafSide * kMaxLeafSide / kLeafThreads;
+    double acc[kRows];
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+        const int k = t + r * kLeafThreads;
+        acc[r] = k < n ? zb[k] : 0.0;
+    }
+    for (int s = 0; s < m; ++s) {
+        const double ls = lam[s];
+        const double* zc = Zg + (long long)s * n;
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) {
+            const int k = t + r * kLeafThreads;
+            if (k < n) acc[r] = fma(zc[k], ls, acc[r]);
         }
-        if (s < m) acc0 = fma(Zg[(long long)s * n + k], lam[s], acc0);
-        S.y[k] = (acc0 + acc1) * Dg[k];
+    }
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+        const int k = t + r * kLeafThreads;
+        if (k < n) S.y[k] = acc[r] * Dg[k];
     }
     __syncwarp(mask);
-    // backward sweep L^T p = y in place, right-looking from the last row;
+    // backward sweep L^T p = y in place, right-looking from the last row,
+    // on the row layout of L (row k: L[k][k-1-t] at LTg[16 k + t], contiguous);
     // the multipliers stream through a register ring kSweepAhead steps ahead
+    const double* LTg = Dg + n;
     double ring[kSweepAhead];
 #pragma unroll
     for (int d = 0; d < kSweepAhead; ++d) {
         const int k = n - 1 - d;
-        ring[d] = (k >= 1 && t < min(w, k)) ? Lg[(long long)(k - 1 - t) * kLeafThreads + t] : 0.0;
+        ring[d] = (k >= 1 && t < min(w, k)) ? LTg[(long long)k * kLeafThreads + t] : 0.0;
     }
     for (int k0 = n - 1; k0 >= 0; k0 -= kSweepAhead) {
 #pragma unroll
@@ -429,7 +454,7 @@ leaf_pressure_kernel(DevView v, bool accumulate) {
             if (k < 0) break;
             const double lk = ring[d];
             const int kn = k - kSweepAhead;
-            ring[d] = (kn >= 1 && t < min(w, kn)) ? Lg[(long long)(kn - 1 - t) * kLeafThreads + t] : 0.0;
+            ring[d] = (kn >= 1 && t < min(w, kn)) ? LTg[(long long)kn * kLeafThreads + t] : 0.0;
             const double pk = S.y[k];
             if (t < min(w, k)) S.y[k - 1 - t] = fma(-lk, pk, S.y[k - 1 - t]);   // entry L[k][k-1-t]
             __syncwarp(mask);
