@@ -318,27 +318,32 @@ __global__ void __launch_bounds__(256) merge_form_kernel(DevView v, int first) {
 
 // Scratch of the blocked sweep, per node: two buffers for the inverse P of
 // a diagonal block (kGJ x kGJ, row-major; block step k uses buffer k & 1),
-// two buffers for the previous column block (2g x kGJ, column-major, same
-// parity rule), and a flag word (the number of the last block whose P has
-// been published).
+// two buffers of the column vectors c_x = A(x, K) of the current block for
+// every index x outside it (2g x kGJ, row x at x * kGJ), two buffers of
+// u_x = P c_x^T (same layout), and a flag word (the number of the last block
+// whose P has been published).
 constexpr int kGJScratchHead = 2 * kGJ * kGJ;
 __device__ __forceinline__ long long gj_scratch_stride(int nmax) {
-    return kGJScratchHead + 2LL * nmax * kGJ + 2;
+    return kGJScratchHead + 4LL * nmax * kGJ + 2;
 }
 __device__ __forceinline__ double* gj_scratch(double* scratch, int slot, int nmax) {
     return scratch + (long long)slot * gj_scratch_stride(nmax);
 }
 __device__ __forceinline__ double* gj_P(double* sc, int step) { return sc + (step & 1) * kGJ * kGJ; }
-__device__ __forceinline__ double* gj_colblk(double* sc, int step, int nmax) {
+__device__ __forceinline__ double* gj_cvec(double* sc, int step, int nmax) {
     return sc + kGJScratchHead + (long long)(step & 1) * nmax * kGJ;
 }
+__device__ __forceinline__ double* gj_uvec(double* sc, int step, int nmax) {
+    return sc + kGJScratchHead + 2LL * nmax * kGJ + (long long)(step & 1) * nmax * kGJ;
+}
 __device__ __forceinline__ unsigned int* gj_flag(double* sc, int nmax) {
-    return reinterpret_cast<unsigned int*>(sc + kGJScratchHead + 2LL * nmax * kGJ);
+    return reinterpret_cast<unsigned int*>(sc + kGJScratchHead + 4LL * nmax * kGJ);
 }
 
 struct GJSmem {
-    double Cs[kGJ][kGJTile + 1];    // old column block rows of a tile: Cs[c][i]
-    double Bs[kGJ][kGJTile + 1];    // block row of a tile (or P on the block columns)
+    double Cr[kGJTile][kGJ + 1];    // c of the tile's rows
+    double Ur[kGJTile][kGJ + 1];    // u of the tile's rows
+    double Uc[kGJTile][kGJ + 1];    // u of the tile's columns
     double Ps[kGJ][kGJ + 1];        // a diagonal block being inverted, or a P
     double Pt[kGJ][kGJ + 1];        // second buffer of the inversion
     double vrow[kGJ];
@@ -404,39 +409,46 @@ __device__ bool gj_invert_block(double (*Ps)[kGJ + 1], double (*Pt)[kGJ + 1], do
     return ok;
 }
 
-// Block row of step 0 for one (node, column tile of kGJRowTile): A_0j <-
-// P_0 A_0j on its columns, and its rows of the column block 0 into the
-// step-0 copy.  (Later block rows are formed inside the fused step.)
-constexpr int kGJRowTile = 16;
-__device__ void gj_first_row_item(const DevView& v, const MergeDesc& D, int slot, int c0, double* scratch, int nmax,
-                                  GJSmem& S) {
+// The sweep keeps only the lower triangle of the symmetric T: after step k
+// an entry of an eliminated and a remaining index is antisymmetric, all
+// others symmetric.  With K the current block, P = A_KK^-1, and for every
+// index x outside K the column vector c_x = A(x, K) (read from the lower
+// triangle: A(x, K) for x > K, -A(K, x) for x < K) and u_x = P c_x^T, one
+// block step is
+//     A_ij <- A_ij - s_j c_i . u_j   (i >= j outside K; s_j = -1 for j < K, +1 for j > K)
+//     A(i, K) <- -u_i^T (i > K),  A(K, j) <- -u_j (j < K),  A_KK <- P.
+// The tiles that hold the next block K1 as rows or as columns write the
+// step's c for their indices and, once P of K1 is published, its u.
+
+// c and u of block 0 for one (node, chunk of kGJTile indices x >= nb0).
+__device__ void gj_first_cu_item(const DevView& v, const MergeDesc& D, int slot, int x0, double* scratch, int nmax,
+                                 GJSmem& S) {
     const int N = 2 * D.g;
     const int nb = min(kGJ, N);
-    double* A = v.W + D.W_off;
+    const double* A = v.W + D.W_off;
     double* sc = gj_scratch(scratch, slot, nmax);
-    const double* Pg = gj_P(sc, 0);
-    double* colblk = gj_colblk(sc, 0, nmax);
+    const double* P0 = gj_P(sc, 0);
+    double* cv = gj_cvec(sc, 0, nmax);
+    double* uv = gj_uvec(sc, 0, nmax);
     const int tid = threadIdx.x;
-    for (int idx = tid; idx < kGJRowTile * kGJ; idx += 256) {
-        const int i = c0 + idx % kGJRowTile, cc = idx / kGJRowTile;
-        if (i < N && cc < nb && i >= nb) colblk[(long long)cc * N + i] = __ldcg(A + (long long)cc * N + i);
-    }
-    for (int idx = tid; idx < kGJ * kGJ; idx += 256) S.Ps[idx / kGJ][idx % kGJ] = __ldcg(Pg + idx);
-    for (int idx = tid; idx < kGJ * kGJRowTile; idx += 256) {
-        const int cc = idx % kGJ, jj = idx / kGJ, j = c0 + jj;
-        S.Bs[cc][jj] = (cc < nb && j < N && j >= nb) ? __ldcg(A + (long long)j * N + cc) : 0.0;
+    for (int idx = tid; idx < kGJ * kGJ; idx += 256) S.Ps[idx / kGJ][idx % kGJ] = __ldcg(P0 + idx);
+    for (int idx = tid; idx < kGJTile * kGJ; idx += 256) {
+        const int xl = idx % kGJTile, cc = idx / kGJTile, x = x0 + xl;
+        const double c = (x < N && x >= nb && cc < nb) ? __ldcg(A + (long long)cc * N + x) : 0.0;
+        S.Cr[xl][cc] = c;
+        if (x < N && x >= nb) cv[(long long)x * kGJ + cc] = c;
     }
     __syncthreads();
-    for (int idx = tid; idx < kGJ * kGJRowTile; idx += 256) {
-        const int rr = idx % kGJ, jj = idx / kGJ, j = c0 + jj;
-        if (rr >= nb || j >= N || j < nb) continue;
-        double acc0 = 0.0, acc1 = 0.0;
+    for (int idx = tid; idx < kGJTile * kGJ; idx += 256) {
+        const int xl = idx / kGJ, rr = idx % kGJ, x = x0 + xl;
+        if (x >= N || x < nb) continue;
+        double a0 = 0.0, a1 = 0.0;
 #pragma unroll
         for (int cc = 0; cc < kGJ; cc += 2) {
-            acc0 = fma(S.Ps[rr][cc], S.Bs[cc][jj], acc0);
-            acc1 = fma(S.Ps[rr][cc + 1], S.Bs[cc + 1][jj], acc1);
+            a0 = fma(S.Ps[rr][cc], S.Cr[xl][cc], a0);
+            a1 = fma(S.Ps[rr][cc + 1], S.Cr[xl][cc + 1], a1);
         }
-        A[(long long)j * N + rr] = acc0 + acc1;
+        uv[(long long)x * kGJ + rr] = a0 + a1;
     }
     __syncthreads();
 }
@@ -465,48 +477,46 @@ __device__ bool wait_flag(const unsigned int* flag, unsigned int value, int* sta
     return s_ok != 0;
 }
 
-// Block step k (block K = [k0, k0 + nb)), for one (node, kGJTile^2 output
-// tile), fused with the preparation of step k + 1 (block K1):
-//   rows outside K: A_ij <- A_ij - A_iK A_Kj (block row already formed) and
-//   A_iK <- -A_iK P_k; the diagonal block <- P_k; the block K1 x K1 is left
-//   to gj_next_diag_item;
-//   then, if the tile holds columns of K1, its rows of the new column block
-//   (all rows outside K1) go to the step-(k+1) copy; and if it holds the rows
-//   of K1, it waits for P_{k+1} and forms its part of the block row of step
-//   k + 1, A_{K1 j} <- P_{k+1} A_{K1 j}.
-// Returns false when a wait timed out.
-__device__ bool gj_step_item(const DevView& v, const MergeDesc& D, int slot, int r0, int c0, int step,
+// Block step k for one (node, lower output tile (ti >= tj)), fused with the
+// preparation of step k + 1: the tile's part of the update above (entries
+// r >= c; the block K1 x K1 is left to gj_next_diag_item); its indices'
+// c of step k + 1 when it holds K1 as rows or columns, and then, once P of
+// K1 is published, their u.  Returns false when the wait timed out.
+__device__ bool gj_step_item(const DevView& v, const MergeDesc& D, int slot, int ti, int tj, int step,
                              double* scratch, int nmax, GJSmem& S) {
     const int N = 2 * D.g;
     const int k0 = step * kGJ, nb = min(kGJ, N - k0);
     const int k1 = k0 + kGJ, nb1 = k1 < N ? min(kGJ, N - k1) : 0;
+    const int r0 = ti * kGJTile, c0 = tj * kGJTile;
     double* A = v.W + D.W_off;
     double* sc = gj_scratch(scratch, slot, nmax);
     const double* Pg = gj_P(sc, step);
-    const double* colblk = gj_colblk(sc, step, nmax);
+    const double* cv = gj_cvec(sc, step, nmax);
+    const double* uv = gj_uvec(sc, step, nmax);
+    double* cn = gj_cvec(sc, step + 1, nmax);
     const int tid = threadIdx.x;
-    for (int idx = tid; idx < kGJ * kGJTile; idx += 256) {
-        const int ii = idx % kGJTile, cc = idx / kGJTile, i = r0 + ii;
-        S.Cs[cc][ii] = (cc < nb && i < N && (i < k0 || i >= k0 + nb)) ? __ldcg(colblk + (long long)cc * N + i) : 0.0;
-        const int jj = idx % kGJTile, j = c0 + jj;
-        double b = 0.0;
-        if (cc < nb && j < N)
-            b = (j >= k0 && j < k0 + nb) ? __ldcg(Pg + cc * kGJ + (j - k0)) : __ldcg(A + (long long)j * N + k0 + cc);
-        S.Bs[cc][jj] = b;
+    for (int idx = tid; idx < kGJTile * kGJ; idx += 256) {
+        const int xl = idx / kGJ, cc = idx % kGJ;
+        const int xi = r0 + xl, xj = c0 + xl;
+        const bool okc = cc < nb;
+        S.Cr[xl][cc] = (okc && xi < N && (xi < k0 || xi >= k0 + nb)) ? __ldcg(cv + (long long)xi * kGJ + cc) : 0.0;
+        S.Ur[xl][cc] = (okc && xi < N && (xi < k0 || xi >= k0 + nb)) ? __ldcg(uv + (long long)xi * kGJ + cc) : 0.0;
+        S.Uc[xl][cc] = (okc && xj < N && (xj < k0 || xj >= k0 + nb)) ? __ldcg(uv + (long long)xj * kGJ + cc) : 0.0;
     }
     __syncthreads();
     const int tr = (tid % 16) * 2, tc = (tid / 16) * 2;
     double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
 #pragma unroll
     for (int cc = 0; cc < kGJ; ++cc) {
-        const double l0 = S.Cs[cc][tr], l1 = S.Cs[cc][tr + 1];
-        const double u0 = S.Bs[cc][tc], u1 = S.Bs[cc][tc + 1];
+        const double l0 = S.Cr[tr][cc], l1 = S.Cr[tr + 1][cc];
+        const double u0 = S.Uc[tc][cc], u1 = S.Uc[tc + 1][cc];
         acc[0][0] = fma(l0, u0, acc[0][0]);
         acc[0][1] = fma(l0, u1, acc[0][1]);
         acc[1][0] = fma(l1, u0, acc[1][0]);
         acc[1][1] = fma(l1, u1, acc[1][1]);
     }
-    double* colnext = gj_colblk(sc, step + 1, nmax);
+    const bool k1rows = nb1 > 0 && k1 >= r0 && k1 < r0 + kGJTile;
+    const bool k1cols = nb1 > 0 && k1 >= c0 && k1 < c0 + kGJTile;
 #pragma unroll
     for (int b = 0; b < 2; ++b) {
         const int j = c0 + tc + b;
@@ -517,46 +527,72 @@ __device__ bool gj_step_item(const DevView& v, const MergeDesc& D, int slot, int
 #pragma unroll
         for (int a = 0; a < 2; ++a) {
             const int i = r0 + tr + a;
-            if (i >= N) continue;
+            if (i >= N || i < j) continue;
             const bool iK = i >= k0 && i < k0 + nb;
             const bool iK1 = i >= k1 && i < k1 + nb1;
             double val;
-            if (iK) {
-                if (jK) col[i] = S.Bs[i - k0][tc + b];
-                val = S.Bs[i - k0][tc + b];          // block row K: final for this step
-            } else if (jK1 && iK1) {
-                continue;                             // the next diagonal block
+            if (iK && jK) {
+                val = __ldcg(Pg + (i - k0) * kGJ + (j - k0));
+            } else if (jK) {
+                val = -S.Ur[tr + a][j - k0];             // block column, i > K
+            } else if (iK) {
+                val = -S.Uc[tc + b][i - k0];             // block row, j < K
+            } else if (iK1 && jK1) {
+                continue;                                 // the next diagonal block
             } else {
-                val = (jK ? 0.0 : __ldcg(col + i)) - acc[a][b];
-                col[i] = val;
+                const double sj = j < k0 ? -1.0 : 1.0;
+                val = fma(-sj, acc[a][b], __ldcg(col + i));
             }
-            if (jK1 && !iK1) colnext[(long long)(j - k1) * N + i] = val;
+            col[i] = val;
+            if (jK1 && !iK1) cn[(long long)i * kGJ + (j - k1)] = val;       // c_i = A(i, K1), i > K1
+            if (iK1 && !jK1) cn[(long long)j * kGJ + (i - k1)] = -val;      // c_j = -A(K1, j), j < K1
         }
     }
     bool ok = true;
-    if (nb1 > 0 && k1 >= r0 && k1 < r0 + kGJTile) {
-        // block row of step k + 1 on this tile's columns (outside K1)
+    if (k1rows || k1cols) {
+        // u of step k + 1 for this tile's indices: columns j < K1 (rows K1 held
+        // here), rows i > K1 (columns K1 held here)
+        __threadfence_block();
         __syncthreads();
         ok = wait_flag(gj_flag(sc, nmax), (unsigned int)(step + 1), v.status);
         if (ok) {
             const double* Pn = gj_P(sc, step + 1);
+            double* un = gj_uvec(sc, step + 1, nmax);
             for (int idx = tid; idx < kGJ * kGJ; idx += 256) S.Ps[idx / kGJ][idx % kGJ] = __ldcg(Pn + idx);
-            for (int idx = tid; idx < kGJ * kGJTile; idx += 256) {
-                const int cc = idx % kGJ, jj = idx / kGJ, j = c0 + jj;
-                S.Bs[cc][jj] = (cc < nb1 && j < N && (j < k1 || j >= k1 + nb1)) ? __ldcg(A + (long long)j * N + k1 + cc)
-                                                                                 : 0.0;
+            // which index range this tile produced c for
+            for (int idx = tid; idx < kGJTile * kGJ; idx += 256) {
+                const int xl = idx / kGJ, cc = idx % kGJ;
+                int x = -1;
+                if (k1rows) {
+                    const int j = c0 + xl;
+                    if (j < N && j < k1) x = j;
+                }
+                if (k1cols && x < 0) {
+                    const int i = r0 + xl;
+                    if (i < N && i >= k1 + nb1) x = i;
+                }
+                S.Cr[xl][cc] = (x >= 0 && cc < nb1) ? __ldcg(cn + (long long)x * kGJ + cc) : 0.0;
             }
             __syncthreads();
-            for (int idx = tid; idx < kGJ * kGJTile; idx += 256) {
-                const int rr = idx % kGJ, jj = idx / kGJ, j = c0 + jj;
-                if (rr >= nb1 || j >= N || (j >= k1 && j < k1 + nb1)) continue;
-                double acc0 = 0.0, acc1 = 0.0;
+            for (int idx = tid; idx < kGJTile * kGJ; idx += 256) {
+                const int xl = idx / kGJ, rr = idx % kGJ;
+                int x = -1;
+                if (k1rows) {
+                    const int j = c0 + xl;
+                    if (j < N && j < k1) x = j;
+                }
+                if (k1cols && x < 0) {
+                    const int i = r0 + xl;
+                    if (i < N && i >= k1 + nb1) x = i;
+                }
+                if (x < 0 || rr >= nb1) continue;
+                double a0 = 0.0, a1 = 0.0;
 #pragma unroll
                 for (int cc = 0; cc < kGJ; cc += 2) {
-                    acc0 = fma(S.Ps[rr][cc], S.Bs[cc][jj], acc0);
-                    acc1 = fma(S.Ps[rr][cc + 1], S.Bs[cc + 1][jj], acc1);
+                    a0 = fma(S.Ps[rr][cc], S.Cr[xl][cc], a0);
+                    a1 = fma(S.Ps[rr][cc + 1], S.Cr[xl][cc + 1], a1);
                 }
-                A[(long long)j * N + k1 + rr] = acc0 + acc1;
+                un[(long long)x * kGJ + rr] = a0 + a1;
             }
         }
     }
@@ -564,38 +600,41 @@ __device__ bool gj_step_item(const DevView& v, const MergeDesc& D, int slot, int
     return ok;
 }
 
-// Block step k, for the next diagonal block K1 = [k1, k1 + nb1) of a node
-// (k1 = k0 + kGJ < 2g): its update A -= A_iK A_Kj, then its inverse into the
-// P buffer of step k + 1, then the node's flag is raised to k + 1 (the tiles
-// of the next block row wait for it).  Runs before any tile item of its
-// CTA.  Returns false on a bad pivot.
+// Block step k, for the next diagonal block K1 = [k1, k1 + nb1) of a node:
+// its update A_ij - c_i . u_j (lower triangle; both indices above K), its
+// inverse into the P buffer of step k + 1, then the node's flag is raised to
+// k + 1.  Runs before any tile item of its CTA.  Returns false on a bad
+// pivot.
 __device__ bool gj_next_diag_item(const DevView& v, const MergeDesc& D, int slot, int step, double* scratch,
                                   int nmax, GJSmem& S) {
     const int N = 2 * D.g;
     const int k0 = step * kGJ, nb = min(kGJ, N - k0);
     const int k1 = k0 + kGJ, nb1 = min(kGJ, N - k1);
-    double* A = v.W + D.W_off;
+    const double* A = v.W + D.W_off;
     double* sc = gj_scratch(scratch, slot, nmax);
-    const double* colblk = gj_colblk(sc, step, nmax);
+    const double* cv = gj_cvec(sc, step, nmax);
+    const double* uv = gj_uvec(sc, step, nmax);
     const int tid = threadIdx.x;
-    // Cs[c][r]: column block rows k1 + r; Bs[c][j]: block row columns k1 + j
     for (int idx = tid; idx < kGJ * kGJ; idx += 256) {
-        const int cc = idx / kGJ, rr = idx % kGJ;
-        S.Cs[cc][rr] = (cc < nb && rr < nb1) ? __ldcg(colblk + (long long)cc * N + k1 + rr) : 0.0;
-        S.Bs[cc][rr] = (cc < nb && rr < nb1) ? __ldcg(A + (long long)(k1 + rr) * N + k0 + cc) : 0.0;
+        const int xl = idx / kGJ, cc = idx % kGJ;
+        const bool ok = xl < nb1 && cc < nb;
+        S.Cr[xl][cc] = ok ? __ldcg(cv + (long long)(k1 + xl) * kGJ + cc) : 0.0;
+        S.Uc[xl][cc] = ok ? __ldcg(uv + (long long)(k1 + xl) * kGJ + cc) : 0.0;
     }
     __syncthreads();
     for (int idx = tid; idx < kGJ * kGJ; idx += 256) {
-        const int pr = idx % kGJ, pc = idx / kGJ;
-        double acc0 = 0.0, acc1 = 0.0;
-#pragma unroll
-        for (int cc = 0; cc < kGJ; cc += 2) {
-            acc0 = fma(S.Cs[cc][pr], S.Bs[cc][pc], acc0);
-            acc1 = fma(S.Cs[cc + 1][pr], S.Bs[cc + 1][pc], acc1);
-        }
+        const int pr = idx / kGJ, pc = idx % kGJ;
         double val = (pr == pc) ? 1.0 : 0.0;
-        if (pr < nb1 && pc < nb1) val = __ldcg(A + (long long)(k1 + pc) * N + k1 + pr) - (acc0 + acc1);
-        S.Ps[pr][pc] = val;
+        if (pr < nb1 && pc < nb1 && pr >= pc) {
+            double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+            for (int cc = 0; cc < kGJ; cc += 2) {
+                a0 = fma(S.Cr[pr][cc], S.Uc[pc][cc], a0);
+                a1 = fma(S.Cr[pr][cc + 1], S.Uc[pc][cc + 1], a1);
+            }
+            val = __ldcg(A + (long long)(k1 + pc) * N + k1 + pr) - (a0 + a1);
+        }
+        if (pr >= pc) S.Ps[pr][pc] = val;
     }
     __syncthreads();
     const bool ok = gj_invert_block(S.Ps, S.Pt, S.vrow, nb1, D.g - k1, &S.rp);
@@ -639,17 +678,49 @@ __device__ bool grid_barrier(unsigned int* counter, unsigned int& round, int* st
     return s_ok != 0;
 }
 
+// Lower tile of rank r among the tiles of one node at a block step: the
+// tiles outside block row / column tk (the one holding K1) first, in row
+// order, then the tk ones (they wait for the look-ahead inverse).
+__device__ __forceinline__ void gj_lower_tile(int r, int tiles, int tk, int& ti, int& tj) {
+    if (tk >= tiles) {
+        ti = (int)((sqrtf(8.0f * r + 1.0f) - 1.0f) * 0.5f);
+        while ((ti + 1) * (ti + 2) / 2 <= r) ++ti;
+        while (ti * (ti + 1) / 2 > r) --ti;
+        tj = r - ti * (ti + 1) / 2;
+        return;
+    }
+    const int head = tiles * (tiles + 1) / 2 - tiles;
+    if (r >= head) {
+        const int q = r - head;                 // row tk (tj <= tk), then column tk (ti > tk)
+        if (q <= tk) { ti = tk; tj = q; }
+        else { ti = q; tj = tk; }
+        return;
+    }
+    int cnt = 0;
+    for (ti = 0; ti < tiles; ++ti) {
+        if (ti == tk) continue;
+        const int nrow = ti < tk ? ti + 1 : ti;  // tiles (ti, tj <= ti) with tj != tk
+        if (r < cnt + nrow) {
+            tj = r - cnt;
+            if (ti > tk && tj >= tk) ++tj;
+            return;
+        }
+        cnt += nrow;
+    }
+    tj = 0;
+}
+
 // The whole blocked Gauss-Jordan sweep of one tree height in one cooperative
-// launch: P_0 of every node, a grid barrier, the block row and column-block
-// copy of step 0, a grid barrier, then per block step one fused phase (the
-// nodes' next diagonal blocks first, then their output tiles) and a grid
-// barrier.
+// launch, on the lower triangle: P_0 of every node; c and u of block 0; per
+// block step one fused phase (the nodes' next diagonal blocks first, then
+// their lower output tiles) with a grid barrier after each; finally the
+// lower triangle is mirrored so that W is stored in full.
 __global__ void __launch_bounds__(256) gj_sweep_kernel(DevView v, int first, int count, int nmax, double* scratch,
                                                        unsigned int* counter) {
     __shared__ GJSmem S;
     __shared__ int s_bad;
-    const int rtiles = (nmax + kGJRowTile - 1) / kGJRowTile;
     const int tiles = (nmax + kGJTile - 1) / kGJTile;
+    const int nlower = tiles * (tiles + 1) / 2;
     const int nsteps = (nmax + kGJ - 1) / kGJ;
     const int tid = threadIdx.x;
     unsigned int round = 0;
@@ -672,49 +743,51 @@ __global__ void __launch_bounds__(256) gj_sweep_kernel(DevView v, int first, int
         __syncthreads();
     }
     if (!grid_barrier(counter, round, v.status)) return;
-    for (int item = blockIdx.x; item < count * rtiles; item += gridDim.x) {
-        const int q = item / rtiles, c0 = (item % rtiles) * kGJRowTile;
+    for (int item = blockIdx.x; item < count * tiles; item += gridDim.x) {
+        const int q = item / tiles, x0 = (item % tiles) * kGJTile;
         const MergeDesc D = v.merges[first + q];
-        if (c0 >= 2 * D.g) continue;                         // uniform per CTA
-        gj_first_row_item(v, D, q, c0, scratch, nmax, S);
+        if (x0 >= 2 * D.g) continue;                         // uniform per CTA
+        gj_first_cu_item(v, D, q, x0, scratch, nmax, S);
     }
     if (!grid_barrier(counter, round, v.status)) return;
     for (int step = 0; step < nsteps; ++step) {
         const int k0 = step * kGJ;
-        // items [0, count): next diagonal blocks; then the output tiles
-        for (int item = blockIdx.x; item < count * (1 + tiles * tiles); item += gridDim.x) {
+        const int tk = (k0 + kGJ) / kGJTile;                  // tile index of the next block
+        for (int item = blockIdx.x; item < count * (1 + nlower); item += gridDim.x) {
             if (item < count) {
                 const MergeDesc D = v.merges[first + item];
                 if (k0 + kGJ >= 2 * D.g) continue;
                 if (!gj_next_diag_item(v, D, item, step, scratch, nmax, S)) s_bad = 1;
                 continue;
             }
-            // the tiles of the next block row (they wait for its P) come last
+            // all nodes' tiles outside row / column tk first, then those
             const int it = item - count;
-            const int tk = (k0 + kGJ) / kGJTile;
-            const int head = count * (tiles - 1) * tiles;
-            int q, ti, tj;
-            if (tk < tiles && it < head) {
-                q = it / ((tiles - 1) * tiles);
-                const int t = it % ((tiles - 1) * tiles);
-                ti = t % (tiles - 1);
-                ti += ti >= tk ? 1 : 0;
-                tj = t / (tiles - 1);
-            } else if (tk < tiles) {
-                q = (it - head) / tiles;
-                ti = tk;
-                tj = (it - head) % tiles;
-            } else {
-                q = it / (tiles * tiles);
-                ti = (it % (tiles * tiles)) % tiles;
-                tj = (it % (tiles * tiles)) / tiles;
-            }
-            const int r0 = ti * kGJTile, c0 = tj * kGJTile;
+            const int tkc = tk < tiles ? tiles : 0;           // tiles per node in the tail group
+            const int head = nlower - tkc;
+            int q, r;
+            if (it < count * head) { q = it / head; r = it % head; }
+            else { q = (it - count * head) / tkc; r = head + (it - count * head) % tkc; }
+            int ti, tj;
+            gj_lower_tile(r, tiles, tk, ti, tj);
             const MergeDesc D = v.merges[first + q];
-            if (k0 >= 2 * D.g || r0 >= 2 * D.g || c0 >= 2 * D.g) continue;
-            if (!gj_step_item(v, D, q, r0, c0, step, scratch, nmax, S)) return;
+            if (k0 >= 2 * D.g || ti * kGJTile >= 2 * D.g) continue;
+            if (!gj_step_item(v, D, q, ti, tj, step, scratch, nmax, S)) return;
         }
         if (!grid_barrier(counter, round, v.status)) return;
+    }
+    // mirror the lower triangle (strictly lower entries of the lower tiles)
+    for (int item = blockIdx.x; item < count * nlower; item += gridDim.x) {
+        const int q = item / nlower, r = item % nlower;
+        int ti, tj;
+        gj_lower_tile(r, tiles, tiles, ti, tj);
+        const MergeDesc D = v.merges[first + q];
+        const int N = 2 * D.g;
+        if (ti * kGJTile >= N) continue;
+        double* A = v.W + D.W_off;
+        for (int idx = tid; idx < kGJTile * kGJTile; idx += 256) {
+            const int i = ti * kGJTile + idx % kGJTile, j = tj * kGJTile + idx / kGJTile;
+            if (i < N && j < N && i > j) A[(long long)i * N + j] = __ldcg(A + (long long)j * N + i);
+        }
     }
     __syncthreads();
     if (tid == 0 && s_bad) atomicOr(v.status, kStatusSingular);
@@ -980,7 +1053,7 @@ bool merge_level_blocked(int, int max_g2, int max_m) {
 
 size_t merge_scratch_doubles(int count, int max_g2, int max_m) {
     if (!merge_level_blocked(count, max_g2, max_m)) return 0;
-    return (size_t)count * (2 * kGJ * kGJ + 2 * (size_t)max_g2 * kGJ + 2);
+    return (size_t)count * (2 * kGJ * kGJ + 4 * (size_t)max_g2 * kGJ + 2);
 }
 
 // phase ids (include/mrcm.h)
@@ -1038,7 +1111,7 @@ cudaError_t launch_merge_build(const DevView& v, int first, int count, int max_g
                 return e;
         }
         const int tiles = (max_g2 + kGJTile - 1) / kGJTile;
-        const long long items = (long long)count * (1 + tiles * tiles);
+        const long long items = (long long)count * (1 + tiles * (tiles + 1) / 2);
         int grid = (int)std::min<long long>(items, (long long)sms);
         grid = grid < 1 ? 1 : grid;
         if ((e = cudaMemsetAsync(barrier, 0, sizeof(unsigned int), s)) != cudaSuccess) return e;

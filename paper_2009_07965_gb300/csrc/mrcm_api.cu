@@ -308,9 +308,8 @@ int make_plan(Plan& P) {
             P.level_max_m[h - 1] = std::max(P.level_max_m[h - 1], (int)m);
             P.max_g2 = std::max(P.max_g2, (int)g2);
             // flop model: Gauss-Jordan inversion of the 2g x 2g form (N steps
-            // of a rank-one update: 2 N^3 on the full matrix of the blocked
-            // sweep, N^2 (N + 1) on the lower triangle kept by the per-node
-            // path), X = -W C over C's blocks (2 N g m), the lower triangle of
+            // of a rank-one update of the lower triangle: N^2 (N + 1)), X =
+            // -W C over C's blocks (2 N g m), the lower triangle of
             // the symmetric R update (g m (m + 1)); solve passes: up 2 m N,
             // down 2 N (m + N).  The path of a level is known once all its
             // nodes are listed, so inv is set in the phase pass below.
@@ -340,7 +339,9 @@ int make_plan(Plan& P) {
                 P.phase_build[MRCM_PHASE_MERGE_SMALL] += sym + node_prod_flops[q];
                 continue;
             }
-            P.phase_build[MRCM_PHASE_GJ_SWEEP] += node_inv_flops[q];
+            const double sym = N * N * (N + 1.0);      // lower-triangle sweep
+            P.merge_flops += (long long)(sym - node_inv_flops[q]);
+            P.phase_build[MRCM_PHASE_GJ_SWEEP] += sym;
             P.phase_build[MRCM_PHASE_MERGE_X] += 2.0 * N * gd * md;
             P.phase_build[MRCM_PHASE_MERGE_R] += md * (md + 1.0) * gd;
         }
