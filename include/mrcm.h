@@ -165,7 +165,9 @@ enum {
     MRCM_Q_SOLVE_FLOPS = 7,   /* algorithmic FP64 flops of mrcm_solve        */
     MRCM_Q_LEAF_FLOPS = 8,    /* part of BUILD_FLOPS in the leaf kernel      */
     MRCM_Q_KERNEL_LAUNCHES_BUILD = 9, /* kernels launched by one build call  */
-    MRCM_Q_KERNEL_LAUNCHES_SOLVE = 10 /* kernels launched by one solve call  */
+    MRCM_Q_KERNEL_LAUNCHES_SOLVE = 10, /* kernels launched by one solve call */
+    MRCM_Q_GRAPH_REPLAYS = 11 /* build and solve calls so far that replayed a
+                                 captured CUDA graph (see mrcm_use_graphs)   */
 };
 
 /* mrcm_query -- integer facts about a context.  value: host out pointer. */
@@ -234,6 +236,20 @@ int mrcm_residual_history(mrcm_ctx* ctx, double* out, int cap);
  */
 int mrcm_enable_timing(mrcm_ctx* ctx, int on);
 int mrcm_phase_times(mrcm_ctx* ctx, double* ms);
+
+/*
+ * mrcm_use_graphs -- on != 0 (the default): mrcm_build_basis and mrcm_solve
+ * capture their launch sequence into a CUDA graph on the first call and
+ * replay it on later calls; the solve graph is captured again when its
+ * buffer pointers, the refinement settings or timing change.  The results
+ * are those of the direct launches, bit for bit.  A context created on the
+ * legacy default stream (stream NULL), or whose stream refuses capture,
+ * launches directly.  on == 0 launches directly and frees the graphs (after
+ * synchronising the context's stream).  The graph replays the buffers given
+ * at capture, so their contents may change between calls but they must
+ * stay allocated while the graph may run again.
+ */
+int mrcm_use_graphs(mrcm_ctx* ctx, int on);
 
 /*
  * mrcm_check_reciprocal -- self-check of the reciprocal the interface and
@@ -339,6 +355,13 @@ void mrcm_destroy(mrcm_ctx* ctx);
 
 /* mrcm_error_string -- static text for an MRCM_* code. */
 const char* mrcm_error_string(int code);
+
+/*
+ * mrcm_last_cuda_error -- the cudaError_t behind the last MRCM_ERR_CUDA or
+ * MRCM_ERR_OOM returned on the calling thread (0 if none); its name is
+ * copied into name[cap] (host, NUL-terminated, may be NULL).
+ */
+int mrcm_last_cuda_error(char* name, int cap);
 
 #ifdef __cplusplus
 }

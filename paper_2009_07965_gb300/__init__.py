@@ -5,7 +5,8 @@ of include/mrcm.h); this package only builds it and marshals arguments.
 """
 from .binding import (mrcm_setup, mrcm_plan_query, mrcm_set_permeability, mrcm_build_basis, mrcm_solve,
                       mrcm_query, mrcm_node_info, mrcm_node_segments, mrcm_segment_info,
-                      mrcm_node_operator, mrcm_destroy, mrcm_error_string, mrcm_enable_timing,
+                      mrcm_node_operator, mrcm_destroy, mrcm_error_string, mrcm_enable_timing, mrcm_use_graphs,
+                      mrcm_last_cuda_error,
                       mrcm_phase_times, mrcm_merge_pair_noalloc, mrcm_set_refinement,
                       mrcm_residual_history, mrcm_phase_flops, mrcm_group_times, mrcm_check_reciprocal, MrcmError, PHASES, PHASE_KERNELS,
                       EXPORTS, LIB_PATH)
@@ -13,6 +14,7 @@ from .solver import Solver
 
 __all__ = ["mrcm_setup", "mrcm_plan_query", "mrcm_set_permeability", "mrcm_build_basis", "mrcm_solve", "mrcm_query",
            "mrcm_node_info", "mrcm_node_segments", "mrcm_segment_info", "mrcm_node_operator",
-           "mrcm_destroy", "mrcm_error_string", "mrcm_enable_timing", "mrcm_phase_times",
+           "mrcm_destroy", "mrcm_error_string", "mrcm_enable_timing", "mrcm_phase_times", "mrcm_use_graphs",
+           "mrcm_last_cuda_error",
            "mrcm_merge_pair_noalloc", "mrcm_set_refinement", "mrcm_residual_history", "mrcm_phase_flops",
            "mrcm_group_times", "mrcm_check_reciprocal", "MrcmError", "PHASE_KERNELS", "PHASES", "EXPORTS", "LIB_PATH", "Solver"]

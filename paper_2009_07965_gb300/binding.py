@@ -18,12 +18,13 @@ ERRORS = {0: "MRCM_OK", -1: "MRCM_ERR_INVALID_ARG", -2: "MRCM_ERR_SHAPE", -3: "M
           -7: "MRCM_ERR_OOM", -8: "MRCM_ERR_TIMEOUT", -9: "MRCM_ERR_UNSUPPORTED"}
 Q = dict(LEAVES=0, SEGMENTS=1, LEVELS=2, NODES=3, WORKSPACE_BYTES=4, MAX_GAMMA=5,
          BUILD_FLOPS=6, SOLVE_FLOPS=7, LEAF_FLOPS=8, KERNEL_LAUNCHES_BUILD=9,
-         KERNEL_LAUNCHES_SOLVE=10)
+         KERNEL_LAUNCHES_SOLVE=10, GRAPH_REPLAYS=11)
 
 # every symbol include/mrcm.h declares
 EXPORTS = ["mrcm_setup", "mrcm_plan_query", "mrcm_set_permeability", "mrcm_build_basis", "mrcm_solve", "mrcm_query",
            "mrcm_node_info", "mrcm_node_segments", "mrcm_segment_info", "mrcm_node_operator",
-           "mrcm_destroy", "mrcm_error_string", "mrcm_enable_timing", "mrcm_phase_times",
+           "mrcm_destroy", "mrcm_error_string", "mrcm_enable_timing", "mrcm_phase_times", "mrcm_use_graphs",
+           "mrcm_last_cuda_error",
            "mrcm_merge_pair_noalloc", "mrcm_set_refinement", "mrcm_residual_history", "mrcm_phase_flops",
            "mrcm_group_times", "mrcm_check_reciprocal"]
 PHASES = ["coef", "leaf_build", "merge_small", "gj_sweep", "merge_form", "merge_x", "merge_r",
@@ -41,7 +42,12 @@ PHASE_KERNELS = {"coef": "face_coef_kernel", "leaf_build": "leaf_build_kernel",
 class MrcmError(RuntimeError):
     def __init__(self, code, call):
         self.code = code
-        super().__init__(f"{call} failed: {ERRORS.get(code, code)} ({_lib().mrcm_error_string(code).decode()})")
+        msg = f"{call} failed: {ERRORS.get(code, code)} ({_lib().mrcm_error_string(code).decode()})"
+        self.cuda_error = None
+        if code in (-6, -7):                 # MRCM_ERR_CUDA, MRCM_ERR_OOM
+            self.cuda_error = mrcm_last_cuda_error()
+            msg += f" [{self.cuda_error[1]}]"
+        super().__init__(msg)
 
 
 class mrcm_grid(ctypes.Structure):
@@ -82,6 +88,8 @@ def _lib():
         lib.mrcm_node_operator.restype = I
         lib.mrcm_enable_timing.argtypes = [P, I]
         lib.mrcm_enable_timing.restype = I
+        lib.mrcm_use_graphs.argtypes = [P, I]
+        lib.mrcm_use_graphs.restype = I
         lib.mrcm_phase_times.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
         lib.mrcm_phase_times.restype = I
         lib.mrcm_merge_pair_noalloc.argtypes = [P, I, P, I, P, I, P, P, P, P]
@@ -100,6 +108,8 @@ def _lib():
         lib.mrcm_destroy.restype = None
         lib.mrcm_error_string.argtypes = [I]
         lib.mrcm_error_string.restype = ctypes.c_char_p
+        lib.mrcm_last_cuda_error.argtypes = [ctypes.c_char_p, I]
+        lib.mrcm_last_cuda_error.restype = I
         _LIB = lib
     return _LIB
 
@@ -196,6 +206,17 @@ def mrcm_node_operator(ctx, node, with_rbar=False):
 
 def mrcm_enable_timing(ctx, on=True):
     _check(_lib().mrcm_enable_timing(ctx, 1 if on else 0), "mrcm_enable_timing")
+
+
+def mrcm_last_cuda_error():
+    """(cudaError_t code, name) behind the last CUDA failure on this thread."""
+    buf = ctypes.create_string_buffer(64)
+    code = _lib().mrcm_last_cuda_error(buf, 64)
+    return code, buf.value.decode()
+
+
+def mrcm_use_graphs(ctx, on=True):
+    _check(_lib().mrcm_use_graphs(ctx, 1 if on else 0), "mrcm_use_graphs")
 
 
 def mrcm_phase_times(ctx):

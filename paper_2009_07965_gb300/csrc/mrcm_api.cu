@@ -374,12 +374,28 @@ struct mrcm_ctx {
     int refine_steps = 1;
     int refine_check = 0;
     int hist_count = 0;
+    // CUDA graphs of the build and solve launch sequences (captured on first
+    // use, replayed after; the solve graph is keyed by its arguments)
+    bool use_graphs = true;      // mrcm_use_graphs
+    bool graphs_ok = true;       // false once a capture failed on this stream
+    bool capturing = false;
+    long long graph_replays = 0;
+    cudaGraphExec_t build_exec = nullptr;
+    bool build_timing = false;
+    int build_ev_used = 0;
+    cudaGraphExec_t solve_exec = nullptr;
+    const void* solve_key[8] = {};
+    int solve_ev_begin = 0, solve_ev_used = 0, solve_launches = 0;
 };
 
 namespace {
 
+// The CUDA error behind the last MRCM_ERR_CUDA / MRCM_ERR_OOM of this thread.
+thread_local cudaError_t g_last_cuda_error = cudaSuccess;
+
 int cuda_err(cudaError_t e) {
     if (e == cudaSuccess) return MRCM_OK;
+    g_last_cuda_error = e;
     if (e == cudaErrorMemoryAllocation) return MRCM_ERR_OOM;
     return MRCM_ERR_CUDA;
 }
@@ -423,18 +439,25 @@ int read_status(mrcm_ctx* c) {
 }
 
 // Records a CUDA event pair around one launch group of a phase; the phase
-// time of a call is the sum over its groups.
+// time of a call is the sum over its groups.  The external-record flag makes
+// the records event-record nodes when the sequence is captured into a graph.
 constexpr int kEventPairs = 4096;
+void record_event(mrcm_ctx* c, cudaEvent_t e) {
+    if (c->capturing)
+        cudaEventRecordWithFlags(e, c->stream, cudaEventRecordExternal);
+    else
+        cudaEventRecord(e, c->stream);
+}
 void phase_begin(void* vc, int phase) {
     mrcm_ctx* c = static_cast<mrcm_ctx*>(vc);
     if (!c->timing || c->ev_used >= kEventPairs) return;
     c->ev_phase[c->ev_used] = phase;
-    cudaEventRecord(c->ev[2 * c->ev_used], c->stream);
+    record_event(c, c->ev[2 * c->ev_used]);
 }
 void phase_end(void* vc, int) {
     mrcm_ctx* c = static_cast<mrcm_ctx*>(vc);
     if (!c->timing || c->ev_used >= kEventPairs) return;
-    cudaEventRecord(c->ev[2 * c->ev_used + 1], c->stream);
+    record_event(c, c->ev[2 * c->ev_used + 1]);
     ++c->ev_used;
 }
 struct PhaseScope {
@@ -449,7 +472,61 @@ struct PhaseScope {
 #define TRY(x) do { int rc_ = (x); if (rc_ != MRCM_OK) return rc_; } while (0)
 #define TRYC(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) return cuda_err(e_); } while (0)
 
+// Captures the launches of fn into a graph executable on the context's
+// stream (updating *exec in place when only launch arguments differ); false
+// (nothing left captured) when the stream cannot be captured (the legacy
+// default stream) or capture fails.
+template <class F>
+static bool capture_graph(mrcm_ctx* c, cudaGraphExec_t* exec, F&& fn) {
+    if (!c->use_graphs || !c->graphs_ok || c->stream == nullptr) return false;
+    if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        c->graphs_ok = false;
+        return false;
+    }
+    c->capturing = true;
+    const int rc = fn();
+    c->capturing = false;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+    if (rc != MRCM_OK || e != cudaSuccess || graph == nullptr) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        c->graphs_ok = false;
+        return false;
+    }
+    if (*exec) {
+        // same launch sequence with other arguments: update in place
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(*exec, graph, &info) == cudaSuccess) {
+            cudaGraphDestroy(graph);
+            return true;
+        }
+        cudaGetLastError();
+    }
+    cudaGraphExec_t ge = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&ge, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+        cudaGetLastError();
+        c->graphs_ok = false;
+        return false;
+    }
+    if (*exec) cudaGraphExecDestroy(*exec);
+    *exec = ge;
+    return true;
+}
+
 extern "C" {
+
+int mrcm_last_cuda_error(char* name, int cap) {
+    const cudaError_t e = g_last_cuda_error;
+    if (name && cap > 0) {
+        std::strncpy(name, cudaGetErrorName(e), (size_t)cap - 1);
+        name[cap - 1] = 0;
+    }
+    return (int)e;
+}
 
 const char* mrcm_error_string(int code) {
     switch (code) {
@@ -630,15 +707,12 @@ int mrcm_set_permeability(mrcm_ctx* c, const double* K_dev) {
     return MRCM_OK;
 }
 
-int mrcm_build_basis(mrcm_ctx* c) {
-    if (!c) return MRCM_ERR_INVALID_ARG;
+// The launch sequence of mrcm_build_basis (no synchronisation).
+static int enqueue_build(mrcm_ctx* c, int& launches) {
     const Plan& P = c->P;
     const DevView& v = c->v;
     cudaStream_t s = c->stream;
-    c->built = false;
-    c->solved = false;
-    int launches = 0;
-    c->ev_used = 0;
+    launches = 0;
     TRYC(cudaMemsetAsync(v.status, 0, sizeof(int), s));
     {
         PhaseScope ps(c, MRCM_PHASE_COEF);
@@ -659,7 +733,32 @@ int mrcm_build_basis(mrcm_ctx* c) {
                                     hook));
         }
     }
-    c->launches_build = launches;
+    return MRCM_OK;
+}
+
+int mrcm_build_basis(mrcm_ctx* c) {
+    if (!c) return MRCM_ERR_INVALID_ARG;
+    c->built = false;
+    c->solved = false;
+    int launches = 0;
+    if (c->build_exec == nullptr || c->build_timing != c->timing) {
+        c->ev_used = 0;
+        if (capture_graph(c, &c->build_exec, [&] { return enqueue_build(c, launches); })) {
+            c->build_timing = c->timing;
+            c->build_ev_used = c->ev_used;
+            c->launches_build = launches;
+            c->solve_key[0] = nullptr;          // the solve graph's event pairs follow these
+        }
+    }
+    if (c->use_graphs && c->build_exec != nullptr && c->build_timing == c->timing) {
+        c->ev_used = c->build_ev_used;
+        TRYC(cudaGraphLaunch(c->build_exec, c->stream));
+        ++c->graph_replays;
+    } else {
+        c->ev_used = 0;
+        TRY(enqueue_build(c, launches));
+        c->launches_build = launches;
+    }
     TRY(read_status(c));
     c->built = true;
     return MRCM_OK;
@@ -701,17 +800,13 @@ static int solve_pass(mrcm_ctx* c, const double* q, const double* bc, bool with_
     return MRCM_OK;
 }
 
-int mrcm_solve(mrcm_ctx* c, const double* q_dev, const double* bc_val_dev, double* p_dev, double* Fx_dev,
-               double* Fy_dev, double* Fz_dev, double* iface_dev) {
-    if (!c) return MRCM_ERR_INVALID_ARG;
-    if (!c->built) return MRCM_ERR_NOT_BUILT;
-    if (!q_dev || !bc_val_dev || !p_dev || !Fx_dev || !Fy_dev || Fz_dev) return MRCM_ERR_INVALID_ARG;
+// The launch sequence of mrcm_solve (no synchronisation).
+static int enqueue_solve(mrcm_ctx* c, const double* q_dev, const double* bc_val_dev, double* p_dev, double* Fx_dev,
+                         double* Fy_dev, double* iface_dev, int& launches) {
     const Plan& P = c->P;
     const DevView& v = c->v;
     cudaStream_t s = c->stream;
-    int launches = 0;
-    // keep the build's event pairs, reuse the solve's
-    while (c->ev_used > 0 && c->ev_phase[c->ev_used - 1] >= MRCM_PHASE_LEAF_PART) --c->ev_used;
+    launches = 0;
     TRYC(cudaMemsetAsync(v.status, 0, sizeof(int), s));
     const int steps = c->refine_steps, nres = steps + (c->refine_check ? 1 : 0);
     if (nres > 0) TRYC(cudaMemsetAsync(v.res_max, 0, sizeof(unsigned long long) * nres, s));
@@ -728,7 +823,6 @@ int mrcm_solve(mrcm_ctx* c, const double* q_dev, const double* bc_val_dev, doubl
         TRYC(launch_residual(v, q_dev, bc_val_dev, steps, s));
         launches += 1 + (P.nseg > 0);
     }
-    c->hist_count = nres;
     {
         PhaseScope ps(c, MRCM_PHASE_FINISH);
         if (P.pure_neumann) {
@@ -738,7 +832,44 @@ int mrcm_solve(mrcm_ctx* c, const double* q_dev, const double* bc_val_dev, doubl
         TRYC(launch_face_fluxes(v, bc_val_dev, p_dev, Fx_dev, Fy_dev, iface_dev, s));
         ++launches;
     }
-    c->launches_solve = launches;
+    return MRCM_OK;
+}
+
+int mrcm_solve(mrcm_ctx* c, const double* q_dev, const double* bc_val_dev, double* p_dev, double* Fx_dev,
+               double* Fy_dev, double* Fz_dev, double* iface_dev) {
+    if (!c) return MRCM_ERR_INVALID_ARG;
+    if (!c->built) return MRCM_ERR_NOT_BUILT;
+    if (!q_dev || !bc_val_dev || !p_dev || !Fx_dev || !Fy_dev || Fz_dev) return MRCM_ERR_INVALID_ARG;
+    // keep the build's event pairs, reuse the solve's
+    while (c->ev_used > 0 && c->ev_phase[c->ev_used - 1] >= MRCM_PHASE_LEAF_PART) --c->ev_used;
+    const int ev_begin = c->ev_used;
+    const void* key[8] = {q_dev, bc_val_dev, p_dev, Fx_dev, Fy_dev, iface_dev,
+                          reinterpret_cast<const void*>((long long)(c->refine_steps * 2 + c->refine_check) + 1),
+                          reinterpret_cast<const void*>((long long)(c->timing ? 2 : 1) + 4 * (long long)ev_begin)};
+    int launches = 0;
+    if (c->solve_exec == nullptr || std::memcmp(key, c->solve_key, sizeof(key)) != 0) {
+        if (capture_graph(c, &c->solve_exec, [&] {
+                return enqueue_solve(c, q_dev, bc_val_dev, p_dev, Fx_dev, Fy_dev, iface_dev, launches);
+            })) {
+            std::memcpy(c->solve_key, key, sizeof(key));
+            c->solve_ev_begin = ev_begin;
+            c->solve_ev_used = c->ev_used;
+            c->solve_launches = launches;
+        } else {
+            c->solve_key[0] = nullptr;
+        }
+    }
+    if (c->use_graphs && c->solve_exec != nullptr && std::memcmp(key, c->solve_key, sizeof(key)) == 0) {
+        c->ev_used = c->solve_ev_used;
+        c->launches_solve = c->solve_launches;
+        TRYC(cudaGraphLaunch(c->solve_exec, c->stream));
+        ++c->graph_replays;
+    } else {
+        c->ev_used = ev_begin;
+        TRY(enqueue_solve(c, q_dev, bc_val_dev, p_dev, Fx_dev, Fy_dev, iface_dev, launches));
+        c->launches_solve = launches;
+    }
+    c->hist_count = c->refine_steps + (c->refine_check ? 1 : 0);
     TRY(read_status(c));
     c->solved = true;
     return MRCM_OK;
@@ -771,6 +902,7 @@ int mrcm_query(const mrcm_ctx* c, int what, long long* value) {
         case MRCM_Q_WORKSPACE_BYTES: *value = (long long)c->bytes; return MRCM_OK;
         case MRCM_Q_KERNEL_LAUNCHES_BUILD: *value = c->launches_build; return MRCM_OK;
         case MRCM_Q_KERNEL_LAUNCHES_SOLVE: *value = c->launches_solve; return MRCM_OK;
+        case MRCM_Q_GRAPH_REPLAYS: *value = c->graph_replays; return MRCM_OK;
         default: return plan_value(c->P, what, value);
     }
 }
@@ -835,6 +967,19 @@ int mrcm_enable_timing(mrcm_ctx* c, int on) {
     return MRCM_OK;
 }
 
+int mrcm_use_graphs(mrcm_ctx* c, int on) {
+    if (!c) return MRCM_ERR_INVALID_ARG;
+    c->use_graphs = on != 0;
+    if (!c->use_graphs) {
+        TRYC(cudaStreamSynchronize(c->stream));
+        if (c->build_exec) cudaGraphExecDestroy(c->build_exec);
+        if (c->solve_exec) cudaGraphExecDestroy(c->solve_exec);
+        c->build_exec = c->solve_exec = nullptr;
+        c->solve_key[0] = nullptr;
+    }
+    return MRCM_OK;
+}
+
 int mrcm_phase_times(mrcm_ctx* c, double* ms) {
     if (!c || !ms) return MRCM_ERR_INVALID_ARG;
     TRYC(cudaStreamSynchronize(c->stream));
@@ -880,6 +1025,8 @@ int mrcm_phase_flops(const mrcm_ctx* c, double* flops) {
 void mrcm_destroy(mrcm_ctx* c) {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
+    if (c->build_exec) cudaGraphExecDestroy(c->build_exec);
+    if (c->solve_exec) cudaGraphExecDestroy(c->solve_exec);
     for (cudaEvent_t e : c->ev)
         if (e) cudaEventDestroy(e);
     for (void* p : c->allocs) cudaFree(p);

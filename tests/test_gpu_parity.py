@@ -155,6 +155,47 @@ def test_repeat_solves_bitwise_identical(mrcm_lib):
     assert np.array_equal(p2, g["p"]) and np.array_equal(fx2, g["Fx"]) and np.array_equal(fy2, g["Fy"])
 
 
+def test_graph_replay_matches_direct_launches(mrcm_lib):
+    # on a side stream mrcm_build_basis / mrcm_solve replay CUDA graphs; the
+    # replay (also with new input buffers and with phase timing) must give
+    # the direct launches' results bit for bit
+    import paper_2009_07965_gb300 as mr
+    import torch
+    prob = inputs.darcy_problem(128, 128, sigma2=3.0, corr=0.1, seed=31, bc="quarter_five_spot")
+    st = torch.cuda.Stream()
+    res = {}
+    for graphs in (False, True):
+        with torch.cuda.stream(st):
+            s = mr.Solver(torch.from_numpy(prob.K).cuda(), sub=prob.sub, seg=prob.seg, alpha=prob.alpha,
+                          bc_type=prob.bc_type, stream=st)
+            mr.mrcm_use_graphs(s.ctx, graphs)
+            out = []
+            for it in range(3):
+                if it == 2:
+                    mr.mrcm_enable_timing(s.ctx, True)
+                s.build_basis()
+                for scale in (1.0, 2.5, 1.0):
+                    q = torch.from_numpy(scale * prob.q).cuda()          # a new buffer every call
+                    bc = torch.from_numpy(scale * prob.bc_val).cuda()
+                    s.solve(q, bc)
+                    out.append([t.cpu().numpy().copy() for t in (s.p, s.Fx, s.Fy)])
+            assert mr.mrcm_query(s.ctx, "GRAPH_REPLAYS") == (12 if graphs else 0)
+            if graphs:
+                ms = mr.mrcm_phase_times(s.ctx)
+                assert ms["leaf_build"] > 0 and ms["finish"] > 0
+            st.synchronize()
+            s.close()
+        res[graphs] = out
+    assert len(res[False]) == len(res[True]) == 9
+    for a, b in zip(res[False], res[True]):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+    for k in (3, 6):
+        for x, y in zip(res[True][0], res[True][k]):
+            assert np.array_equal(x, y)
+    assert not np.array_equal(res[True][0][0], res[True][1][0])
+
+
 def test_errors_are_reported(mrcm_lib):
     import torch
     from paper_2009_07965_gb300 import Solver, MrcmError
