@@ -107,6 +107,15 @@ __device__ __forceinline__ double t_entry(const NodeRefs& N, int r, int c, doubl
 __device__ __forceinline__ bool pivot_ok(double p, bool d_row) {
     return d_row ? (p > kTinyPivot) : (p < -kTinyPivot);
 }
+// The same test on the bit pattern (integer instructions only; an FP64
+// compare takes a full FP64 instruction): sign as expected, magnitude above
+// kTinyPivot and finite.
+__device__ __forceinline__ bool pivot_ok_bits(double p, bool d_row) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(p);
+    const unsigned long long mag = b & 0x7fffffffffffffffull;
+    const unsigned long long tiny = (unsigned long long)__double_as_longlong(kTinyPivot);
+    return ((b >> 63) == (d_row ? 0ull : 1ull)) && mag > tiny && mag < 0x7ff0000000000000ull;
+}
 
 // ---------------------------------------------------------------------------
 // Per-node path for small systems (2g <= kSmallMax): one CTA per node, all in
@@ -346,64 +355,89 @@ struct GJSmem {
     double Uc[kGJTile][kGJ + 1];    // u of the tile's columns
     double Ps[kGJ][kGJ + 1];        // a diagonal block being inverted, or a P
     double Pt[kGJ][kGJ + 1];        // second buffer of the inversion
-    double vrow[kGJ];
-    double rp;
+    double rp[2];                   // pivot reciprocals (by step parity)
+    double tt[2];                   // squared subdiagonal entry of the next pivot
 };
 
 // Inverse of a symmetric kGJ x kGJ block held in shared memory (lower
-// triangle of Ps used; identity padding beyond nb), by the whole CTA (256
-// threads): Gauss-Jordan without pivot search on the lower triangle (after a
-// step, entries of an eliminated and a remaining index are antisymmetric,
-// all others symmetric), one entry per thread, ping-ponging between Ps and
-// Pt.  Each warp-wide FP64 instruction holds its SMSP for many cycles, so the
-// sequential part per pivot is kept to a few of them: warp 0 forms the
-// pivot's reciprocal (rcp_nr) and the scaled pivot row, warp 1 checks the
-// pivot, every kept entry takes one FMA.  On return Ps holds the full
-// inverse.  d_rows: rows of the block in the d part (positive pivots
-// expected).  Returns false (lane 0 of warp 1) on a pivot of the wrong sign
-// or size.
-__device__ bool gj_invert_block(double (*Ps)[kGJ + 1], double (*Pt)[kGJ + 1], double* vrow, int nb, int d_rows,
-                                double* s_rp) {
+// triangle of Ps used; identity padding beyond nb), by the whole CTA (at
+// least 224 threads): Gauss-Jordan without pivot search on the lower triangle
+// (after a step, entries of an eliminated and a remaining index are
+// antisymmetric, all others symmetric), ping-ponging between Ps and Pt.
+//
+// A warp-wide FP64 instruction holds its scheduler for about 64 cycles, so
+// the pivots are a sequential chain of FP64 latencies.  Warp 0 runs that
+// chain one step ahead of the rest: while warps 1-3, 5 and 6 apply step k - 1
+// to the 136 entries (two FP64 instructions per entry, no divergent branches,
+// sign flips on the bit pattern), warp 0 forms pivot k itself,
+//     p_k = b_k - t_k r_(k-1),   b_k, t_k from the entries after step k - 2,
+// where t_k, the square of entry (k, k - 1) after step k - 2 (both indices
+// still remaining, so the row and column entries agree), is left in s_tt by
+// the thread that produced it, and then its reciprocal r_k (rcp_nr) and the
+// integer pivot test.  One CTA barrier per pivot hands r_k to the update and
+// the fresh entries to warp 0.  On return Ps holds the full inverse.
+// d_rows: rows of the block in the d part (positive pivots expected).
+// Returns false (lane 0 of warp 0) on a pivot of the wrong sign or size.
+__device__ bool gj_invert_block(double (*Ps)[kGJ + 1], double (*Pt)[kGJ + 1], double* s_rp, double* s_tt,
+                                int nb, int d_rows) {
     constexpr int kTri = kGJ * (kGJ + 1) / 2;
-    static_assert(kTri <= 256 && (kGJ % 2) == 0, "one entry per thread; even number of steps");
-    const int tid = threadIdx.x;
+    static_assert(kTri <= 5 * 32 && (kGJ % 2) == 0, "five update warps; even number of steps");
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int rank = (warp >= 1 && warp <= 3) ? (warp - 1) * 32 + lane
+                   : (warp == 5 || warp == 6) ? (warp - 2) * 32 + lane : kTri;
     int r = 0, c = 0;
-    if (tid < kTri) {
-        r = (int)((sqrtf(8.0f * tid + 1.0f) - 1.0f) * 0.5f);
-        while ((r + 1) * (r + 2) / 2 <= tid) ++r;
-        while (r * (r + 1) / 2 > tid) --r;
-        c = tid - r * (r + 1) / 2;
+    if (rank < kTri) {
+        r = (int)((sqrtf(8.0f * rank + 1.0f) - 1.0f) * 0.5f);
+        while ((r + 1) * (r + 2) / 2 <= rank) ++r;
+        while (r * (r + 1) / 2 > rank) --r;
+        c = rank - r * (r + 1) / 2;
     }
-    double (*cur)[kGJ + 1] = Ps;
+    double (*cur)[kGJ + 1] = Ps;      // entries after step kk - 2 (the input for kk <= 1)
     double (*nxt)[kGJ + 1] = Pt;
+    double rp_prev = 0.0;
     bool ok = true;
-    for (int kk = 0; kk < kGJ; ++kk) {
-        if (tid < kGJ) {
-            const double rp = rcp_nr(cur[kk][kk]);
-            if (tid == 0) *s_rp = rp;
-            vrow[tid] = (tid <= kk ? cur[kk][tid] : cur[tid][kk]) * rp;
-        } else if (tid == 32) {
-            if (kk < nb && !pivot_ok(cur[kk][kk], kk < d_rows)) ok = false;
-        }
-        __syncthreads();
-        if (tid < kTri) {
-            const double rp = *s_rp;
-            const double a_rk = r >= kk ? cur[r][kk] : -cur[kk][r];
-            double nv;
-            if (r == kk) nv = (c == kk) ? rp : vrow[c];
-            else if (c == kk) nv = -a_rk * rp;
-            else nv = fma(-a_rk, vrow[c], cur[r][c]);
+    for (int kk = 0; kk <= kGJ; ++kk) {
+        if (warp == 0) {
+            if (kk < kGJ) {
+                double p;
+                if (kk == 0) {
+                    p = cur[0][0];
+                } else if (kk == 1) {
+                    const double a = cur[1][0];
+                    p = fma(-(a * a), rp_prev, cur[1][1]);
+                } else {
+                    p = fma(-s_tt[kk & 1], rp_prev, cur[kk][kk]);
+                }
+                const double rp = rcp_nr(p);
+                if (lane == 0) {
+                    s_rp[kk & 1] = rp;
+                    if (kk < nb && !pivot_ok_bits(p, kk < d_rows)) ok = false;
+                }
+                rp_prev = rp;
+            }
+        } else if (rank < kTri && kk >= 1) {
+            // step s = kk - 1: B'(r, c) = B(r, c) - B(r, s) B(s, c) r_s, with
+            // the pivot row scaled by r_s, the pivot column by -r_s
+            const int s = kk - 1;
+            const double rp = s_rp[s & 1];
+            const double xa = (r == s) ? 1.0 : (r > s ? neg_bits(cur[r][s]) : cur[s][r]);   // -B(r, s)
+            const double xb = (c == s) ? 1.0 : (c < s ? cur[s][c] : cur[c][s]);             //  B(s, c)
+            const double y = (r == s || c == s) ? 0.0 : cur[r][c];
+            const double nv = fma(xa * xb, rp, y);
             nxt[r][c] = nv;
+            if (r == kk + 1 && c == kk) s_tt[(kk + 1) & 1] = nv * nv;
         }
         __syncthreads();
-        double (*t)[kGJ + 1] = cur;
-        cur = nxt;
-        nxt = t;
+        if (kk >= 1) {
+            double (*t)[kGJ + 1] = cur;
+            cur = nxt;
+            nxt = t;
+        }
     }
     // kGJ (even) swaps: the result is back in Ps; mirror the upper triangle
     {
         const int i = tid / kGJ, j = tid % kGJ;
-        if (i < j) Ps[i][j] = Ps[j][i];
+        if (tid < kGJ * kGJ && i < j) Ps[i][j] = Ps[j][i];
     }
     __syncthreads();
     return ok;
@@ -637,7 +671,7 @@ __device__ bool gj_next_diag_item(const DevView& v, const MergeDesc& D, int slot
         if (pr >= pc) S.Ps[pr][pc] = val;
     }
     __syncthreads();
-    const bool ok = gj_invert_block(S.Ps, S.Pt, S.vrow, nb1, D.g - k1, &S.rp);
+    const bool ok = gj_invert_block(S.Ps, S.Pt, S.rp, S.tt, nb1, D.g - k1);
     double* Pn = gj_P(sc, step + 1);
     for (int idx = tid; idx < kGJ * kGJ; idx += 256) Pn[idx] = S.Ps[idx / kGJ][idx % kGJ];
     __threadfence();
@@ -735,7 +769,7 @@ __global__ void __launch_bounds__(256) gj_sweep_kernel(DevView v, int first, int
             S.Ps[pr][pc] = (pr < nb && pc < nb) ? __ldcg(A + (long long)pc * N + pr) : (pr == pc ? 1.0 : 0.0);
         }
         __syncthreads();
-        if (!gj_invert_block(S.Ps, S.Pt, S.vrow, nb, D.g, &S.rp)) s_bad = 1;
+        if (!gj_invert_block(S.Ps, S.Pt, S.rp, S.tt, nb, D.g)) s_bad = 1;
         double* sc = gj_scratch(scratch, q, nmax);
         double* P0 = gj_P(sc, 0);
         for (int idx = tid; idx < kGJ * kGJ; idx += 256) P0[idx] = S.Ps[idx / kGJ][idx % kGJ];

@@ -152,30 +152,39 @@ __device__ __forceinline__ DD dd_mul_d(DD x, double b) {
 }
 __device__ __forceinline__ DD dd_neg(DD x) { return {-x.h, -x.l}; }
 
-// Reciprocal by Newton-Raphson iteration from a single-precision seed
-// (Markstein; Muller et al., Handbook of Floating-Point Arithmetic, Sec. 5.3):
-// the seed is the FP32 reciprocal of p's sign, exponent and leading 23
-// mantissa bits, moved between formats with integer operations; two steps
-// x <- x + x (1 - p x) take its 2^-23 relative error to below 2^-90, so the
-// result is within an ulp of 1/p.  Four FP64 instructions on the dependent
-// chain instead of the longer IEEE division sequence, which matters where a
-// reciprocal sits on a sequential chain (pivots).  Outside the exponent
-// range of FP32 it falls back to the division.
+// Reciprocal from a single-precision seed refined by one third-order step of
+// the Newton-Raphson family (Muller et al., Handbook of Floating-Point
+// Arithmetic, Sec. 5.3): with x the seed and e = 1 - p x, 1/p = x / (1 - e) =
+// x (1 + e + e^2 + ...), and the series is cut after e^2.  The seed is the
+// approximate FP32 reciprocal (at most 1 ulp off) of p's sign, exponent and
+// leading 23 mantissa bits, moved between formats with integer operations
+// (conversion instructions run on the slower FP64 path), so |e| < 2^-21.9 and
+// the dropped terms are below 2^-65 relative: the result is within an ulp of
+// 1/p.  Three dependent FP64 instructions (e, e + e^2, x + x (e + e^2))
+// instead of the longer IEEE division sequence, which matters where a
+// reciprocal sits on a sequential chain (pivots).  Outside the exponent range
+// of FP32 it falls back to the division.
 __device__ __forceinline__ double rcp_nr(double p) {
     const unsigned long long bits = (unsigned long long)__double_as_longlong(p);
     const int e = (int)((bits >> 52) & 0x7ff) - 1023;
     if (e < -120 || e > 120) return 1.0 / p;
     const unsigned int fb = (unsigned int)(bits >> 32 & 0x80000000u) | ((unsigned int)(e + 127) << 23) |
                             (unsigned int)(bits >> 29 & 0x7fffffu);
-    const unsigned int rb = __float_as_uint(__frcp_rn(__uint_as_float(fb)));
+    float rf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(__uint_as_float(fb)));
+    const unsigned int rb = __float_as_uint(rf);
     const int er = (int)((rb >> 23) & 0xff) - 127;
     const unsigned long long xb = ((unsigned long long)(rb & 0x80000000u) << 32) |
                                   ((unsigned long long)(er + 1023) << 52) | ((unsigned long long)(rb & 0x7fffffu) << 29);
-    double x = __longlong_as_double((long long)xb);
-    double t = fma(-p, x, 1.0);
-    x = fma(x, t, x);
-    t = fma(-p, x, 1.0);
-    return fma(x, t, x);
+    const double x = __longlong_as_double((long long)xb);
+    const double e0 = fma(-p, x, 1.0);
+    const double s = fma(e0, e0, e0);
+    return fma(x, s, x);
+}
+// -x by flipping the sign bit: an FP64 negation that is not an FMA operand
+// modifier (inside a select, say) costs a full FP64 instruction.
+__device__ __forceinline__ double neg_bits(double x) {
+    return __hiloint2double(__double2hiint(x) ^ (int)0x80000000u, __double2loint(x));
 }
 __device__ __forceinline__ double dd_round(DD x) { return __dadd_rn(x.h, x.l); }
 
