@@ -329,8 +329,9 @@ __global__ void __launch_bounds__(256) merge_form_kernel(DevView v, int first) {
 // a diagonal block (kGJ x kGJ, row-major; block step k uses buffer k & 1),
 // two buffers of the column vectors c_x = A(x, K) of the current block for
 // every index x outside it (2g x kGJ, row x at x * kGJ), two buffers of
-// u_x = P c_x^T (same layout), and a flag word (the number of the last block
-// whose P has been published).
+// u_x = P c_x^T (same layout), a flag word (the number of the last block
+// whose P has been published) and a counter of the tile items that have
+// written c of a next block.
 constexpr int kGJScratchHead = 2 * kGJ * kGJ;
 __device__ __forceinline__ long long gj_scratch_stride(int nmax) {
     return kGJScratchHead + 4LL * nmax * kGJ + 2;
@@ -348,6 +349,9 @@ __device__ __forceinline__ double* gj_uvec(double* sc, int step, int nmax) {
 __device__ __forceinline__ unsigned int* gj_flag(double* sc, int nmax) {
     return reinterpret_cast<unsigned int*>(sc + kGJScratchHead + 4LL * nmax * kGJ);
 }
+// number of tile items so far that wrote c of a next block (monotonic over
+// the steps: each step has one per tile row of the node)
+__device__ __forceinline__ unsigned int* gj_cready(double* sc, int nmax) { return gj_flag(sc, nmax) + 1; }
 
 struct GJSmem {
     double Cr[kGJTile][kGJ + 1];    // c of the tile's rows
@@ -511,12 +515,11 @@ __device__ bool wait_flag(const unsigned int* flag, unsigned int value, int* sta
     return s_ok != 0;
 }
 
-// Block step k for one (node, lower output tile (ti >= tj)), fused with the
-// preparation of step k + 1: the tile's part of the update above (entries
-// r >= c; the block K1 x K1 is left to gj_next_diag_item); its indices'
-// c of step k + 1 when it holds K1 as rows or columns, and then, once P of
-// K1 is published, their u.  Returns false when the wait timed out.
-__device__ bool gj_step_item(const DevView& v, const MergeDesc& D, int slot, int ti, int tj, int step,
+// Block step k for one (node, lower output tile (ti >= tj)): the tile's part
+// of the update above (entries r >= c; the block K1 x K1 is left to
+// gj_next_diag_item), and c of step k + 1 for its indices when it holds K1
+// as rows or columns (then the node's c counter is raised).
+__device__ void gj_step_item(const DevView& v, const MergeDesc& D, int slot, int ti, int tj, int step,
                              double* scratch, int nmax, GJSmem& S) {
     const int N = 2 * D.g;
     const int k0 = step * kGJ, nb = min(kGJ, N - k0);
@@ -529,6 +532,18 @@ __device__ bool gj_step_item(const DevView& v, const MergeDesc& D, int slot, int
     const double* uv = gj_uvec(sc, step, nmax);
     double* cn = gj_cvec(sc, step + 1, nmax);
     const int tid = threadIdx.x;
+    const int tr = (tid % 16) * 2, tc = (tid / 16) * 2;
+    // the tile's current entries, in flight while c and u are staged
+    double old[2][2];
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+        const int j = c0 + tc + b;
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            const int i = r0 + tr + a;
+            old[a][b] = (j < N && i < N && i >= j) ? __ldcg(A + (long long)j * N + i) : 0.0;
+        }
+    }
     for (int idx = tid; idx < kGJTile * kGJ; idx += 256) {
         const int xl = idx / kGJ, cc = idx % kGJ;
         const int xi = r0 + xl, xj = c0 + xl;
@@ -538,7 +553,6 @@ __device__ bool gj_step_item(const DevView& v, const MergeDesc& D, int slot, int
         S.Uc[xl][cc] = (okc && xj < N && (xj < k0 || xj >= k0 + nb)) ? __ldcg(uv + (long long)xj * kGJ + cc) : 0.0;
     }
     __syncthreads();
-    const int tr = (tid % 16) * 2, tc = (tid / 16) * 2;
     double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
 #pragma unroll
     for (int cc = 0; cc < kGJ; ++cc) {
@@ -568,70 +582,70 @@ __device__ bool gj_step_item(const DevView& v, const MergeDesc& D, int slot, int
             if (iK && jK) {
                 val = __ldcg(Pg + (i - k0) * kGJ + (j - k0));
             } else if (jK) {
-                val = -S.Ur[tr + a][j - k0];             // block column, i > K
+                val = neg_bits(S.Ur[tr + a][j - k0]);     // block column, i > K
             } else if (iK) {
-                val = -S.Uc[tc + b][i - k0];             // block row, j < K
+                val = neg_bits(S.Uc[tc + b][i - k0]);     // block row, j < K
             } else if (iK1 && jK1) {
                 continue;                                 // the next diagonal block
             } else {
-                const double sj = j < k0 ? -1.0 : 1.0;
-                val = fma(-sj, acc[a][b], __ldcg(col + i));
+                // A_ij - s_j c_i . u_j with s_j = -1 below K
+                val = j < k0 ? old[a][b] + acc[a][b] : old[a][b] - acc[a][b];
             }
             col[i] = val;
-            if (jK1 && !iK1) cn[(long long)i * kGJ + (j - k1)] = val;       // c_i = A(i, K1), i > K1
-            if (iK1 && !jK1) cn[(long long)j * kGJ + (i - k1)] = -val;      // c_j = -A(K1, j), j < K1
+            if (jK1 && !iK1) cn[(long long)i * kGJ + (j - k1)] = val;                 // c_i = A(i, K1), i > K1
+            if (iK1 && !jK1) cn[(long long)j * kGJ + (i - k1)] = neg_bits(val);       // c_j = -A(K1, j), j < K1
         }
     }
-    bool ok = true;
     if (k1rows || k1cols) {
-        // u of step k + 1 for this tile's indices: columns j < K1 (rows K1 held
-        // here), rows i > K1 (columns K1 held here)
-        __threadfence_block();
+        __threadfence();
         __syncthreads();
-        ok = wait_flag(gj_flag(sc, nmax), (unsigned int)(step + 1), v.status);
-        if (ok) {
-            const double* Pn = gj_P(sc, step + 1);
-            double* un = gj_uvec(sc, step + 1, nmax);
-            for (int idx = tid; idx < kGJ * kGJ; idx += 256) S.Ps[idx / kGJ][idx % kGJ] = __ldcg(Pn + idx);
-            // which index range this tile produced c for
-            for (int idx = tid; idx < kGJTile * kGJ; idx += 256) {
-                const int xl = idx / kGJ, cc = idx % kGJ;
-                int x = -1;
-                if (k1rows) {
-                    const int j = c0 + xl;
-                    if (j < N && j < k1) x = j;
-                }
-                if (k1cols && x < 0) {
-                    const int i = r0 + xl;
-                    if (i < N && i >= k1 + nb1) x = i;
-                }
-                S.Cr[xl][cc] = (x >= 0 && cc < nb1) ? __ldcg(cn + (long long)x * kGJ + cc) : 0.0;
-            }
-            __syncthreads();
-            for (int idx = tid; idx < kGJTile * kGJ; idx += 256) {
-                const int xl = idx / kGJ, rr = idx % kGJ;
-                int x = -1;
-                if (k1rows) {
-                    const int j = c0 + xl;
-                    if (j < N && j < k1) x = j;
-                }
-                if (k1cols && x < 0) {
-                    const int i = r0 + xl;
-                    if (i < N && i >= k1 + nb1) x = i;
-                }
-                if (x < 0 || rr >= nb1) continue;
-                double a0 = 0.0, a1 = 0.0;
-#pragma unroll
-                for (int cc = 0; cc < kGJ; cc += 2) {
-                    a0 = fma(S.Ps[rr][cc], S.Cr[xl][cc], a0);
-                    a1 = fma(S.Ps[rr][cc + 1], S.Cr[xl][cc + 1], a1);
-                }
-                un[(long long)x * kGJ + rr] = a0 + a1;
-            }
-        }
+        if (tid == 0) atomicAdd(gj_cready(sc, nmax), 1u);
     }
     __syncthreads();
-    return ok;
+}
+
+// u of step k + 1 for one (node, run of indices [x0, x0 + len) outside K1):
+// u_x = P_(k+1) c_x^T, once P_(k+1) is published and every tile row of the
+// node has written its c (counter = (k + 1) tiles).  Sub-chunks of kUChunk
+// indices, two threads per output entry, each summing half of the kGJ
+// products.  Returns false when a wait timed out.
+constexpr int kUChunk = 8;
+__device__ bool gj_u_item(const DevView& v, const MergeDesc& D, int slot, int x0, int len, int step,
+                          double* scratch, int nmax, GJSmem& S) {
+    const int N = 2 * D.g;
+    const int k1 = (step + 1) * kGJ, nb1 = min(kGJ, N - k1);
+    const int tiles = (N + kGJTile - 1) / kGJTile;
+    double* sc = gj_scratch(scratch, slot, nmax);
+    if (!wait_flag(gj_flag(sc, nmax), (unsigned int)(step + 1), v.status)) return false;
+    if (!wait_flag(gj_cready(sc, nmax), (unsigned int)((step + 1) * tiles), v.status)) return false;
+    const double* Pn = gj_P(sc, step + 1);
+    const double* cn = gj_cvec(sc, step + 1, nmax);
+    double* un = gj_uvec(sc, step + 1, nmax);
+    const int tid = threadIdx.x;
+    for (int idx = tid; idx < kGJ * kGJ; idx += 256) S.Ps[idx / kGJ][idx % kGJ] = __ldcg(Pn + idx);
+    static_assert(kUChunk * kGJ * 2 == 256 && kUChunk <= kGJTile, "two threads per output");
+    const int o = tid >> 1, half = tid & 1;
+    const int xl = o / kGJ, rr = o % kGJ;
+    for (int xs = x0; xs < x0 + len; xs += kUChunk) {
+        for (int idx = tid; idx < kUChunk * kGJ; idx += 256) {
+            const int yl = idx / kGJ, cc = idx % kGJ, y = xs + yl;
+            const bool ok = y < N && (y < k1 || y >= k1 + nb1) && cc < nb1;
+            S.Cr[yl][cc] = ok ? __ldcg(cn + (long long)y * kGJ + cc) : 0.0;
+        }
+        __syncthreads();
+        const int x = xs + xl;
+        double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+        for (int cc = half * (kGJ / 2); cc < (half + 1) * (kGJ / 2); cc += 2) {
+            a0 = fma(S.Ps[rr][cc], S.Cr[xl][cc], a0);
+            a1 = fma(S.Ps[rr][cc + 1], S.Cr[xl][cc + 1], a1);
+        }
+        double sum = a0 + a1;
+        sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+        if (half == 0 && x < N && (x < k1 || x >= k1 + nb1) && rr < nb1) un[(long long)x * kGJ + rr] = sum;
+        __syncthreads();
+    }
+    return true;
 }
 
 // Block step k, for the next diagonal block K1 = [k1, k1 + nb1) of a node:
@@ -713,8 +727,8 @@ __device__ bool grid_barrier(unsigned int* counter, unsigned int& round, int* st
 }
 
 // Lower tile of rank r among the tiles of one node at a block step: the
-// tiles outside block row / column tk (the one holding K1) first, in row
-// order, then the tk ones (they wait for the look-ahead inverse).
+// tiles outside block row / column tk (the one holding K1), in row order,
+// then the tk ones.
 __device__ __forceinline__ void gj_lower_tile(int r, int tiles, int tk, int& ti, int& tj) {
     if (tk >= tiles) {
         ti = (int)((sqrtf(8.0f * r + 1.0f) - 1.0f) * 0.5f);
@@ -747,8 +761,9 @@ __device__ __forceinline__ void gj_lower_tile(int r, int tiles, int tk, int& ti,
 // The whole blocked Gauss-Jordan sweep of one tree height in one cooperative
 // launch, on the lower triangle: P_0 of every node; c and u of block 0; per
 // block step one fused phase (the nodes' next diagonal blocks first, then
-// their lower output tiles) with a grid barrier after each; finally the
-// lower triangle is mirrored so that W is stored in full.
+// their lower output tiles, the row / column tk ones leading, then the u
+// of the next step in chunks over all CTAs) with a grid barrier after each;
+// finally the lower triangle is mirrored so that W is stored in full.
 __global__ void __launch_bounds__(256) gj_sweep_kernel(DevView v, int first, int count, int nmax, double* scratch,
                                                        unsigned int* counter) {
     __shared__ GJSmem S;
@@ -773,7 +788,10 @@ __global__ void __launch_bounds__(256) gj_sweep_kernel(DevView v, int first, int
         double* sc = gj_scratch(scratch, q, nmax);
         double* P0 = gj_P(sc, 0);
         for (int idx = tid; idx < kGJ * kGJ; idx += 256) P0[idx] = S.Ps[idx / kGJ][idx % kGJ];
-        if (tid == 0) *gj_flag(sc, nmax) = 0u;
+        if (tid == 0) {
+            *gj_flag(sc, nmax) = 0u;
+            *gj_cready(sc, nmax) = 0u;
+        }
         __syncthreads();
     }
     if (!grid_barrier(counter, round, v.status)) return;
@@ -794,18 +812,31 @@ __global__ void __launch_bounds__(256) gj_sweep_kernel(DevView v, int first, int
                 if (!gj_next_diag_item(v, D, item, step, scratch, nmax, S)) s_bad = 1;
                 continue;
             }
-            // all nodes' tiles outside row / column tk first, then those
+            // all nodes' tiles in row / column tk first (their c feeds the u
+            // items), then the others
             const int it = item - count;
-            const int tkc = tk < tiles ? tiles : 0;           // tiles per node in the tail group
+            const int tkc = tk < tiles ? tiles : 0;           // tiles per node in row / column tk
             const int head = nlower - tkc;
             int q, r;
-            if (it < count * head) { q = it / head; r = it % head; }
-            else { q = (it - count * head) / tkc; r = head + (it - count * head) % tkc; }
+            if (it < count * tkc) { q = it / tkc; r = head + it % tkc; }
+            else { q = (it - count * tkc) / head; r = (it - count * tkc) % head; }
             int ti, tj;
             gj_lower_tile(r, tiles, tk, ti, tj);
             const MergeDesc D = v.merges[first + q];
             if (k0 >= 2 * D.g || ti * kGJTile >= 2 * D.g) continue;
-            if (!gj_step_item(v, D, q, ti, tj, step, scratch, nmax, S)) return;
+            gj_step_item(v, D, q, ti, tj, step, scratch, nmax, S);
+        }
+        // u of step + 1 for every index outside the next block, spread over
+        // all CTAs once their tiles are done
+        // (runs sized so that one round of items covers the level)
+        const int per = (count * nmax + (int)gridDim.x - 1) / (int)gridDim.x;
+        const int ulen = max(kUChunk, (per + kUChunk - 1) / kUChunk * kUChunk);
+        const int uchunks = (nmax + ulen - 1) / ulen;
+        for (int item = blockIdx.x; item < count * uchunks; item += gridDim.x) {
+            const int q = item / uchunks, x0 = (item % uchunks) * ulen;
+            const MergeDesc D = v.merges[first + q];
+            if (k0 + kGJ >= 2 * D.g || x0 >= 2 * D.g) continue;       // no next block, or past the end
+            if (!gj_u_item(v, D, q, x0, min(ulen, 2 * D.g - x0), step, scratch, nmax, S)) return;
         }
         if (!grid_barrier(counter, round, v.status)) return;
     }
