@@ -493,22 +493,27 @@ __device__ void gj_first_cu_item(const DevView& v, const MergeDesc& D, int slot,
 
 // Bounded wait of one CTA for a flag that another CTA of the same
 // cooperative launch raises (about a second); false on timeout
-// (kStatusTimeout set).
+// (kStatusTimeout set).  Thread 0 polls with acquire loads, so what the
+// raising CTA wrote before its release (fence + atomic) is visible to the
+// whole CTA after the barrier that ends the wait.
 constexpr long long kFlagSpins = 5000000;
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
 __device__ bool wait_flag(const unsigned int* flag, unsigned int value, int* status) {
     __shared__ int s_ok;
     if (threadIdx.x == 0) {
         int ok = 1;
-        const volatile unsigned int* vf = flag;
         long long spins = 0;
-        while (*vf < value) {
+        while (ld_acquire_gpu(flag) < value) {
             if (++spins > kFlagSpins) {
                 ok = 0;
                 atomicOr(status, kStatusTimeout);
                 break;
             }
         }
-        __threadfence();
         s_ok = ok;
     }
     __syncthreads();
@@ -616,22 +621,28 @@ __device__ bool gj_u_item(const DevView& v, const MergeDesc& D, int slot, int x0
     const int k1 = (step + 1) * kGJ, nb1 = min(kGJ, N - k1);
     const int tiles = (N + kGJTile - 1) / kGJTile;
     double* sc = gj_scratch(scratch, slot, nmax);
-    if (!wait_flag(gj_flag(sc, nmax), (unsigned int)(step + 1), v.status)) return false;
-    if (!wait_flag(gj_cready(sc, nmax), (unsigned int)((step + 1) * tiles), v.status)) return false;
     const double* Pn = gj_P(sc, step + 1);
     const double* cn = gj_cvec(sc, step + 1, nmax);
     double* un = gj_uvec(sc, step + 1, nmax);
     const int tid = threadIdx.x;
-    for (int idx = tid; idx < kGJ * kGJ; idx += 256) S.Ps[idx / kGJ][idx % kGJ] = __ldcg(Pn + idx);
     static_assert(kUChunk * kGJ * 2 == 256 && kUChunk <= kGJTile, "two threads per output");
     const int o = tid >> 1, half = tid & 1;
     const int xl = o / kGJ, rr = o % kGJ;
-    for (int xs = x0; xs < x0 + len; xs += kUChunk) {
+    // the c are usually in before P: wait for them first and stage the
+    // first run while P is awaited
+    if (!wait_flag(gj_cready(sc, nmax), (unsigned int)((step + 1) * tiles), v.status)) return false;
+    auto stage_c = [&](int xs) {
         for (int idx = tid; idx < kUChunk * kGJ; idx += 256) {
             const int yl = idx / kGJ, cc = idx % kGJ, y = xs + yl;
             const bool ok = y < N && (y < k1 || y >= k1 + nb1) && cc < nb1;
             S.Cr[yl][cc] = ok ? __ldcg(cn + (long long)y * kGJ + cc) : 0.0;
         }
+    };
+    stage_c(x0);
+    if (!wait_flag(gj_flag(sc, nmax), (unsigned int)(step + 1), v.status)) return false;
+    for (int idx = tid; idx < kGJ * kGJ; idx += 256) S.Ps[idx / kGJ][idx % kGJ] = __ldcg(Pn + idx);
+    for (int xs = x0; xs < x0 + len; xs += kUChunk) {
+        if (xs != x0) stage_c(xs);
         __syncthreads();
         const int x = xs + xl;
         double a0 = 0.0, a1 = 0.0;
@@ -709,16 +720,14 @@ __device__ bool grid_barrier(unsigned int* counter, unsigned int& round, int* st
         const unsigned int target = (round + 1) * gridDim.x;
         __threadfence();
         atomicAdd(counter, 1u);
-        volatile unsigned int* vc = counter;
         long long spins = 0;
-        while (*vc < target) {
+        while (ld_acquire_gpu(counter) < target) {
             if (++spins > kBarrierSpins) {
                 ok = 0;
                 atomicOr(status, kStatusTimeout);
                 break;
             }
         }
-        __threadfence();
         s_ok = ok;
     }
     ++round;
