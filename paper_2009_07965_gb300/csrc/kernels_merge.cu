@@ -1022,90 +1022,205 @@ __global__ void __launch_bounds__(256) merge_rupdate_kernel(DevView v, int first
 // Solve phase, bottom-up: the node's particular fluxes
 // rbar = rbar_o + X^T rbar_gamma (Eqs. particular.1-2 with M symmetric); one
 // warp per output, lanes split the sum over gamma.
-constexpr int kUpOut = 32;
-__global__ void __launch_bounds__(256) merge_up_kernel(DevView v, int first) {
-    extern __shared__ __align__(16) double rg[];     // rbar_gamma (2g)
-    const MergeDesc D = v.merges[first + blockIdx.x];
-    const NodeRefs N = node_refs(v, D);
-    const int g = N.g, g2 = N.g2, m = N.m, o1 = N.o1;
-    const int i0 = blockIdx.y * kUpOut;
-    if (i0 >= m) return;                              // uniform per CTA
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const double* rb1 = v.rbar + D.r1_off;
-    const double* rb2 = v.rbar + D.r2_off;
-    for (int r = tid; r < g2; r += 256) rg[r] = r < g ? rb1[N.gpos1[r]] : rb2[N.gpos2[r - g]];
-    __syncthreads();
-    const double* X = v.X + D.X_off;
-    double* rbp = v.rbar + D.r_off;
-    for (int i = i0 + warp; i < min(i0 + kUpOut, m); i += 8) {
-        const double* xc = X + (long long)i * g2;
-        double acc = 0.0;
-        for (int k = lane; k < g2; k += 32) acc += xc[k] * rg[k];
+// ---------------------------------------------------------------------------
+// Solve-phase tree sweeps (Algorithm 1's upward pass of the particular
+// fluxes and its downward pass of the interface unknowns), every tree height
+// in one cooperative launch with a grid barrier between heights.  Each
+// height's dot products are spread over the whole grid, so that the top of
+// the tree (few nodes, long rows of W and X) keeps enough loads in flight.
+
+// Lanes per output of the up sweep: a power of two, up to 32, so that each
+// lane has about kUpTerms terms (FP64 products are costly per warp
+// instruction: they are spread thin, and padded ones are avoided).
+constexpr int kUpTerms = 4;
+__device__ __forceinline__ int tree_up_lanes(int g2) {
+    int l = 1;
+    while (l < 32 && l * kUpTerms < g2) l <<= 1;
+    return l;
+}
+
+// Hint one 128-byte line of global memory into L2.
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+// Every line of [p, p + bytes) into L2, spread over the grid's threads.
+__device__ __forceinline__ void prefetch_range_l2(const void* p, long long bytes, long long t0, long long stride) {
+    const char* c = static_cast<const char*>(p);
+    for (long long off = t0 * 128; off < bytes; off += stride * 128) prefetch_l2(c + off);
+}
+
+// rbar_node(i) = sum_k X(k, i) rbar_gamma(k) + rbar of outer segment i
+// (i < m, k < 2g).  Per height: rbar_gamma of every node gathered from the
+// children into rgam, a grid barrier, then the dot products on contiguous
+// rgam (no dependent gathers inside them).
+__global__ void __launch_bounds__(256) tree_up_kernel(DevView v, TreeLevels L, unsigned int* counter) {
+    const int tid = threadIdx.x, lane = tid & 31;
+    const long long stride = (long long)gridDim.x * 256;
+    const long long t0 = (long long)blockIdx.x * 256 + tid;
+    unsigned int round = 0;
+    // The static data of both sweeps (descriptors, index maps, X, W: tens of
+    // MB at most) into L2 first, in the order of use: each height is a short
+    // chain of dependent loads, and cold misses would set its pace.
+    prefetch_range_l2(v.merges, L.n_merges * (long long)sizeof(MergeDesc), t0, stride);
+    prefetch_range_l2(v.node_map, L.map_len * (long long)sizeof(int), t0, stride);
+    prefetch_range_l2(v.X, L.x_len * (long long)sizeof(double), t0, stride);
+    prefetch_range_l2(v.W, L.w_len * (long long)sizeof(double), t0, stride);
+    for (int h = 0; h < L.height; ++h) {
+        const int first = L.first[h], count = L.count[h], g2max = L.g2[h], mmax = L.m[h];
+        if (count == 0) continue;                           // uniform over the grid
+        for (long long t = t0; t < (long long)count * g2max; t += stride) {
+            const int q = (int)(t / g2max), k = (int)(t % g2max);
+            const MergeDesc D = v.merges[first + q];
+            if (k >= 2 * D.g) continue;
+            const NodeRefs N = node_refs(v, D);
+            v.rgam[2LL * D.gamma_off + k] = k < N.g ? __ldcg(v.rbar + D.r1_off + N.gpos1[k])
+                                                    : __ldcg(v.rbar + D.r2_off + N.gpos2[k - N.g]);
+        }
+        if (!grid_barrier(counter, round, v.status)) return;
+        if (mmax == 0) continue;                            // (the root) uniform
+        const int lanes = tree_up_lanes(g2max);
+        const unsigned int gmask = (lanes == 32 ? 0xffffffffu : ((1u << lanes) - 1u) << (lane & ~(lanes - 1)));
+        const long long total = (long long)count * mmax * lanes;
+        for (long long t = t0; t < total; t += stride) {
+            const long long o = t / lanes;
+            const int sub = (int)(t % lanes);
+            const int q = (int)(o / mmax), i = (int)(o % mmax);
+            const MergeDesc D = v.merges[first + q];
+            const int g2 = 2 * D.g;
+            const double* rg = v.rgam + 2LL * D.gamma_off;
+            double acc = 0.0;
+            if (i < D.m) {
+                // blocks of kUpTerms terms per lane (one block up to
+                // 2g = 32 kUpTerms), all loads issued before the products
+                const double* xc = v.X + D.X_off + (long long)i * g2;
+                double a0 = 0.0, a1 = 0.0;
+                int kb = sub;
+                for (; kb + (kUpTerms - 1) * lanes < g2; kb += kUpTerms * lanes) {
+                    double xv[kUpTerms], rv[kUpTerms];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) rbp[i] = acc + (i < o1 ? rb1[N.opos1[i]] : rb2[N.opos2[i - o1]]);
+                    for (int u = 0; u < kUpTerms; ++u) {
+                        xv[u] = xc[kb + u * lanes];
+                        rv[u] = __ldcg(rg + kb + u * lanes);
+                    }
+#pragma unroll
+                    for (int u = 0; u < kUpTerms; u += 2) {
+                        a0 = fma(xv[u], rv[u], a0);
+                        a1 = fma(xv[u + 1], rv[u + 1], a1);
+                    }
+                }
+                for (; kb < g2; kb += lanes) a0 = fma(xc[kb], __ldcg(rg + kb), a0);
+                acc = a0 + a1;
+            }
+            for (int w = lanes >> 1; w > 0; w >>= 1) acc += __shfl_xor_sync(gmask, acc, w, lanes);
+            if (sub == 0 && i < D.m) {
+                const NodeRefs N = node_refs(v, D);
+                const double ro = i < N.o1 ? __ldcg(v.rbar + D.r1_off + N.opos1[i])
+                                           : __ldcg(v.rbar + D.r2_off + N.opos2[i - N.o1]);
+                v.rbar[D.r_off + i] = acc + ro;
+            }
+        }
+        if (h + 1 < L.height && !grid_barrier(counter, round, v.status)) return;
     }
 }
 
-// Solve phase, top-down: lambda_gamma = X lambda_o + W (-rbar_gamma),
-// scattered into the children's Robin data together with the node's own
-// outer data.  A CTA covers 64 rows of gamma; four thread groups split the
-// sums.
-constexpr int kDownRows = 32, kDownGroups = 8;
-__global__ void __launch_bounds__(256) merge_down_kernel(DevView v, int first) {
-    extern __shared__ __align__(16) double rhs[];    // -rbar_gamma (2g)
-    __shared__ double part[kDownGroups][kDownRows];
-    const MergeDesc D = v.merges[first + blockIdx.x];
-    const NodeRefs N = node_refs(v, D);
-    const int g = N.g, g2 = N.g2, m = N.m, o1 = N.o1;
-    const int r0 = blockIdx.y * kDownRows;
-    if (r0 >= g2) return;                                // uniform per CTA
-    const int tid = threadIdx.x, rl = tid % kDownRows, grp = tid / kDownRows;
-    const double* rb1 = v.rbar + D.r1_off;
-    const double* rb2 = v.rbar + D.r2_off;
-    for (int r = tid; r < g2; r += 256) rhs[r] = -(r < g ? rb1[N.gpos1[r]] : rb2[N.gpos2[r - g]]);
-    __syncthreads();
-    const double* lam_o = v.lam + D.r_off;
-    const double* X = v.X + D.X_off;
-    const double* W = v.W + D.W_off;
-    double* l1 = v.lam + D.r1_off;
-    double* l2 = v.lam + D.r2_off;
-    const int r = r0 + rl;
-    // four independent partial sums per thread: four loads in flight
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-    if (r < g2) {
-        constexpr int G = kDownGroups;
-        int j = grp;
-        for (; j + 3 * G < m; j += 4 * G) {
-            a0 = fma(X[(long long)j * g2 + r], lam_o[j], a0);
-            a1 = fma(X[(long long)(j + G) * g2 + r], lam_o[j + G], a1);
-            a2 = fma(X[(long long)(j + 2 * G) * g2 + r], lam_o[j + 2 * G], a2);
-            a3 = fma(X[(long long)(j + 3 * G) * g2 + r], lam_o[j + 3 * G], a3);
-        }
-        for (; j < m; j += G) a0 = fma(X[(long long)j * g2 + r], lam_o[j], a0);
-        int k = grp;
-        for (; k + 3 * G < g2; k += 4 * G) {
-            a0 = fma(W[(long long)k * g2 + r], rhs[k], a0);
-            a1 = fma(W[(long long)(k + G) * g2 + r], rhs[k + G], a1);
-            a2 = fma(W[(long long)(k + 2 * G) * g2 + r], rhs[k + 2 * G], a2);
-            a3 = fma(W[(long long)(k + 3 * G) * g2 + r], rhs[k + 3 * G], a3);
-        }
-        for (; k < g2; k += G) a0 = fma(W[(long long)k * g2 + r], rhs[k], a0);
-    }
-    part[grp][rl] = (a0 + a1) + (a2 + a3);
-    __syncthreads();
-    if (grp == 0 && r < g2) {
-        double lg = 0.0;
+// lambda_gamma(r) = sum_j X(r, j) lambda_o(j) - sum_k W(r, k) rbar_gamma(k),
+// scattered to the children, whose outer lambda are copied from the node;
+// rbar_gamma is read from rgam, which the up sweep of the same pass wrote.
+// Data written by other CTAs of the launch (lambda, partial sums) is read
+// with L2-only loads: a line left in L1 from an earlier height may be stale.
+// Thread per (node, row r, term chunk), the chunk taken in blocks of
+// kDownTerms terms whose loads are all in flight together; with several
+// chunks the partial sums go to scratch and a second phase adds them in
+// chunk order.
+constexpr int kDownTerms = 8;
+__global__ void __launch_bounds__(256) tree_down_kernel(DevView v, TreeLevels L, double* scratch,
+                                                        unsigned int* counter) {
+    const int tid = threadIdx.x;
+    const long long stride = (long long)gridDim.x * 256;
+    const long long t0 = (long long)blockIdx.x * 256 + tid;
+    unsigned int round = 0;
+    for (int h = L.height - 1; h >= 0; --h) {
+        const int first = L.first[h], count = L.count[h], g2max = L.g2[h], mmax = L.m[h], nkc = L.nkc[h];
+        if (count == 0) continue;                           // uniform over the grid
+        const int kc_len = L.kcl[h];
+        const long long rows = (long long)count * nkc * g2max;
+        // the rows, then the children's outer lambda (copied from the node),
+        // in one index space so that their load chains overlap
+        for (long long t = t0; t < rows + (long long)count * mmax; t += stride) {
+            if (t >= rows) {
+                const int q = (int)((t - rows) / mmax), j = (int)((t - rows) % mmax);
+                const MergeDesc D = v.merges[first + q];
+                if (j >= D.m) continue;
+                const NodeRefs N = node_refs(v, D);
+                const double lo = __ldcg(v.lam + D.r_off + j);
+                if (j < N.o1) v.lam[D.r1_off + N.opos1[j]] = lo;
+                else v.lam[D.r2_off + N.opos2[j - N.o1]] = lo;
+                continue;
+            }
+            const int r = (int)(t % g2max);
+            const long long qk = t / g2max;
+            const int q = (int)(qk / nkc), kc = (int)(qk % nkc);
+            const MergeDesc D = v.merges[first + q];
+            const NodeRefs N = node_refs(v, D);
+            if (r >= N.g2) continue;
+            const double* lam_o = v.lam + D.r_off;
+            const double* X = v.X + D.X_off;
+            const double* W = v.W + D.W_off;
+            const int lo = kc * kc_len, hi = min(lo + kc_len, N.m + N.g2);
+            const double* rg = v.rgam + 2LL * D.gamma_off;
+            double a[4] = {0.0, 0.0, 0.0, 0.0};
+            int jb = lo;
+            for (; jb + kDownTerms <= hi; jb += kDownTerms) {
+                // one block of terms: every load issued before the products
+                double mv[kDownTerms], cv[kDownTerms];
 #pragma unroll
-        for (int q = 0; q < kDownGroups; ++q) lg += part[q][rl];
-        if (r < g) l1[N.gpos1[r]] = lg;
-        else l2[N.gpos2[r - g]] = lg;
-    }
-    if (blockIdx.y == 0) {
-        for (int j = tid; j < m; j += 256) {
-            if (j < o1) l1[N.opos1[j]] = lam_o[j];
-            else l2[N.opos2[j - o1]] = lam_o[j];
+                for (int u = 0; u < kDownTerms; ++u) {
+                    const int j = jb + u;
+                    const bool xpart = j < N.m;
+                    mv[u] = xpart ? X[(long long)j * N.g2 + r] : W[(long long)(j - N.m) * N.g2 + r];
+                    cv[u] = xpart ? __ldcg(lam_o + j) : neg_bits(__ldcg(rg + (j - N.m)));
+                }
+#pragma unroll
+                for (int u = 0; u < kDownTerms; ++u) a[u & 3] = fma(mv[u], cv[u], a[u & 3]);
+            }
+            for (; jb < hi; ++jb) {
+                const bool xpart = jb < N.m;
+                const double mvv = xpart ? X[(long long)jb * N.g2 + r] : W[(long long)(jb - N.m) * N.g2 + r];
+                const double cvv = xpart ? __ldcg(lam_o + jb) : neg_bits(__ldcg(rg + (jb - N.m)));
+                a[jb & 3] = fma(mvv, cvv, a[jb & 3]);
+            }
+            const double part = (a[0] + a[1]) + (a[2] + a[3]);
+            if (nkc == 1) {
+                if (r < N.g) v.lam[D.r1_off + N.gpos1[r]] = part;
+                else v.lam[D.r2_off + N.gpos2[r - N.g]] = part;
+            } else {
+                scratch[t] = part;
+            }
         }
+        if (nkc > 1) {
+            if (!grid_barrier(counter, round, v.status)) return;
+            // G lanes per row add the chunk partials, then a shuffle tree
+            const int G = nkc < 32 ? nkc : 32;
+            const int lane = tid & 31;
+            const unsigned int gmask = (G == 32 ? 0xffffffffu : ((1u << G) - 1u) << (lane & ~(G - 1)));
+            for (long long t = t0; t < (long long)count * g2max * G; t += stride) {
+                const int sub = (int)(t % G);
+                const long long o = t / G;
+                const int q = (int)(o / g2max), r = (int)(o % g2max);
+                const MergeDesc D = v.merges[first + q];
+                const double* ps = scratch + (long long)q * nkc * g2max + r;
+                double lg = 0.0;
+                if (r < 2 * D.g)
+                    for (int kc = sub; kc < nkc; kc += G) lg += __ldcg(ps + (long long)kc * g2max);
+                for (int w = G >> 1; w > 0; w >>= 1) lg += __shfl_xor_sync(gmask, lg, w, G);
+                if (sub == 0 && r < 2 * D.g) {
+                    const NodeRefs N = node_refs(v, D);
+                    if (r < N.g) v.lam[D.r1_off + N.gpos1[r]] = lg;
+                    else v.lam[D.r2_off + N.gpos2[r - N.g]] = lg;
+                }
+            }
+        }
+        if (h > 0 && !grid_barrier(counter, round, v.status)) return;
     }
 }
 
@@ -1223,18 +1338,59 @@ cudaError_t launch_merge_build(const DevView& v, int first, int count, int max_g
     return cudaSuccess;
 }
 
-cudaError_t launch_merge_up(const DevView& v, int first, int count, int max_g2, int max_m, cudaStream_t s) {
-    if (count == 0 || max_m == 0) return cudaSuccess;
-    merge_up_kernel<<<dim3(count, (max_m + kUpOut - 1) / kUpOut), 256, (size_t)max_g2 * sizeof(double), s>>>(
-        v, first);
-    return cudaGetLastError();
+cudaError_t tree_grid(int* grid) {
+    int dev = 0, sms = 0, per = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tree_down_kernel, 256, 0)) != cudaSuccess) return e;
+    int per_up = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_up, tree_up_kernel, 256, 0)) != cudaSuccess) return e;
+    per = std::min(std::min(per, per_up), 2);
+    *grid = std::max(1, sms * std::max(per, 1));
+    return cudaSuccess;
 }
 
-cudaError_t launch_merge_down(const DevView& v, int first, int count, int max_g2, int, cudaStream_t s) {
-    if (count == 0) return cudaSuccess;
-    merge_down_kernel<<<dim3(count, (max_g2 + kDownRows - 1) / kDownRows), 256, (size_t)max_g2 * sizeof(double),
-                        s>>>(v, first);
-    return cudaGetLastError();
+long long tree_plan_chunks(TreeLevels& L, int grid) {
+    // A warp-wide FP64 instruction holds its scheduler for many cycles, so a
+    // height's products have to be spread over the whole grid: the terms of
+    // a row are split into chunks (a power of two of them) until rows x
+    // chunks fills the grid's threads, keeping at least 8 terms per chunk.
+    const long long threads = (long long)grid * 256;
+    long long need = 0;
+    for (int h = 0; h < L.height; ++h) {
+        const long long rows = (long long)L.count[h] * L.g2[h];
+        const int T = L.m[h] + L.g2[h];
+        int nkc = 1;
+        while (rows * nkc * 2 <= threads && (T + 2 * nkc - 1) / (2 * nkc) >= 8) nkc *= 2;
+        L.nkc[h] = nkc;
+        L.kcl[h] = ((T + nkc - 1) / nkc + 7) / 8 * 8;
+        if (nkc > 1) need = std::max(need, rows * nkc);
+    }
+    return need;
+}
+
+cudaError_t launch_tree_up(const DevView& v, const TreeLevels& L, int grid, void* barrier, cudaStream_t s) {
+    if (L.height == 0) return cudaSuccess;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(barrier, 0, sizeof(unsigned int), s)) != cudaSuccess) return e;
+    DevView vv = v;
+    TreeLevels ll = L;
+    unsigned int* bar = reinterpret_cast<unsigned int*>(barrier);
+    void* args[] = {&vv, &ll, &bar};
+    return cudaLaunchCooperativeKernel((const void*)tree_up_kernel, dim3(grid), dim3(256), args, 0, s);
+}
+
+cudaError_t launch_tree_down(const DevView& v, const TreeLevels& L, int grid, double* scratch, void* barrier,
+                             cudaStream_t s) {
+    if (L.height == 0) return cudaSuccess;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(barrier, 0, sizeof(unsigned int), s)) != cudaSuccess) return e;
+    DevView vv = v;
+    TreeLevels ll = L;
+    unsigned int* bar = reinterpret_cast<unsigned int*>(barrier);
+    void* args[] = {&vv, &ll, &scratch, &bar};
+    return cudaLaunchCooperativeKernel((const void*)tree_down_kernel, dim3(grid), dim3(256), args, 0, s);
 }
 
 }  // namespace mrcm

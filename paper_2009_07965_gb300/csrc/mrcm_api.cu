@@ -371,6 +371,9 @@ struct mrcm_ctx {
     int ev_used = 0;
     double* gj_scratch = nullptr;
     unsigned long long* gj_barrier = nullptr;
+    TreeLevels tree{};                    // merge levels for the fused solve sweeps
+    int tree_grid = 1;
+    double* tree_scratch = nullptr;
     int refine_steps = 1;
     int refine_check = 0;
     int hist_count = 0;
@@ -668,6 +671,25 @@ static int setup_impl(mrcm_ctx* c, const mrcm_grid* g, const double* K_dev, cons
         TRY(dev_alloc(c, &c->gj_scratch, (long long)nscr));
         TRY(dev_alloc(c, &c->gj_barrier, (long long)(kMergeBarrierBytes / sizeof(unsigned long long))));
     }
+    {
+        if (P.height > kMaxTreeLevels) return MRCM_ERR_UNSUPPORTED;
+        TreeLevels& T = c->tree;
+        T.height = P.height;
+        T.x_len = P.nX;
+        T.w_len = P.nW;
+        T.n_merges = (long long)P.merges.size();
+        T.map_len = (long long)P.node_map.size();
+        for (int h = 1; h <= P.height; ++h) {
+            T.first[h - 1] = P.level_first[h - 1];
+            T.count[h - 1] = P.level_count[h - 1];
+            T.g2[h - 1] = P.level_max_g2[h - 1];
+            T.m[h - 1] = P.level_max_m[h - 1];
+        }
+        TRY(dev_alloc(c, &v.rgam, std::max<long long>(2 * (long long)P.gamma_segs.size(), 1)));
+        TRYC(tree_grid(&c->tree_grid));
+        const long long need = tree_plan_chunks(T, c->tree_grid);
+        TRY(dev_alloc(c, &c->tree_scratch, std::max(need, 1LL)));
+    }
     TRY(dev_alloc(c, &v.status, 4));
     TRYC(cudaMemcpyAsync(c->K, K_dev, sizeof(double) * ncell, cudaMemcpyDefault, c->stream));
     // the root's lambda has no entries; lambda of every other node is written
@@ -776,21 +798,15 @@ static int solve_pass(mrcm_ctx* c, const double* q, const double* bc, bool with_
         PhaseScope ps(c, MRCM_PHASE_LEAF_PART);
         TRYC(launch_leaf_particular(v, q, bc, with_sadj, s)); ++launches;
     }
-    {
-        PhaseScope ps(c, MRCM_PHASE_TREE_UP);
-        for (int h = 1; h <= P.height; ++h) {
-            TRYC(launch_merge_up(v, P.level_first[h - 1], P.level_count[h - 1], P.level_max_g2[h - 1],
-                                 P.level_max_m[h - 1], s));
-            launches += P.level_max_m[h - 1] > 0;
-        }
-    }
-    {
-        PhaseScope ps(c, MRCM_PHASE_TREE_DOWN);
-        for (int h = P.height; h >= 1; --h) {
-            TRYC(launch_merge_down(v, P.level_first[h - 1], P.level_count[h - 1], P.level_max_g2[h - 1],
-                                   P.level_max_m[h - 1], s));
+    if (P.height > 0) {
+        {
+            PhaseScope ps(c, MRCM_PHASE_TREE_UP);
+            TRYC(launch_tree_up(v, c->tree, c->tree_grid, c->gj_barrier, s));
             ++launches;
         }
+        PhaseScope ps(c, MRCM_PHASE_TREE_DOWN);
+        TRYC(launch_tree_down(v, c->tree, c->tree_grid, c->tree_scratch, c->gj_barrier, s));
+        ++launches;
     }
     {
         PhaseScope ps(c, MRCM_PHASE_LEAF_PRESSURE);

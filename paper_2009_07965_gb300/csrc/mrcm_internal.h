@@ -91,6 +91,8 @@ struct DevView {
     double* leafzb;     // particular forward solves
     double* R;          // node maps (leaves and internal nodes)
     double* rbar;       // node particular fluxes
+    double* rgam;       // per merge, rbar of its 2g gamma unknowns gathered from
+                        // the children (at 2 * gamma_off), written by the up sweep
     double* lam;        // node Robin data (top-down)
     double* X;
     double* W;          // explicit inverses of the interface matrices (W_off layout)
@@ -237,7 +239,30 @@ constexpr size_t kMergeBarrierBytes = 64;
 bool merge_level_blocked(int count, int max_g2, int max_m);
 size_t merge_scratch_doubles(int count, int max_g2, int max_m);
 constexpr int kMergeBlock = 16;      // block size of the blocked Gauss-Jordan sweep (flop model)
-cudaError_t launch_merge_up(const DevView& v, int first, int count, int max_g2, int max_m, cudaStream_t s);
-cudaError_t launch_merge_down(const DevView& v, int first, int count, int max_g2, int max_m, cudaStream_t s);
+
+// The merge levels of the tree for the fused up / down sweeps of the solve
+// (passed by value as a kernel argument; index h - 1 for height h).
+constexpr int kMaxTreeLevels = 48;
+struct TreeLevels {
+    int height;
+    int first[kMaxTreeLevels], count[kMaxTreeLevels], g2[kMaxTreeLevels], m[kMaxTreeLevels];
+    int nkc[kMaxTreeLevels];   // down sweep: term chunks per row, a power of two (1: no partial sums)
+    int kcl[kMaxTreeLevels];   // down sweep: terms per chunk (a multiple of 8)
+    // extents of the static data the sweeps read (prefetched into L2)
+    long long x_len, w_len;    // doubles of X and W
+    long long n_merges, map_len;
+};
+// Grid of the fused tree sweeps on the current device (CTAs of 256 threads).
+cudaError_t tree_grid(int* grid);
+// Fills nkc for a grid of `grid` CTAs; returns the scratch doubles the down
+// sweep needs (partial sums of the levels with nkc > 1).
+long long tree_plan_chunks(TreeLevels& L, int grid);
+// rbar of every merge, leaves' parents to the root, in one cooperative
+// launch (grid barrier on `barrier` between heights).
+cudaError_t launch_tree_up(const DevView& v, const TreeLevels& L, int grid, void* barrier, cudaStream_t s);
+// lambda of every merge's gamma, root to the leaves' parents, in one
+// cooperative launch; scratch: tree_plan_chunks doubles.
+cudaError_t launch_tree_down(const DevView& v, const TreeLevels& L, int grid, double* scratch, void* barrier,
+                             cudaStream_t s);
 
 }  // namespace mrcm
