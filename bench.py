@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--size", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--refine", type=int, default=0,
+                    help="iterative-refinement steps per solve in the timed steps (0: the paper's single "
+                         "pass; its distance to the refined solution is checked in the same run)")
     return ap.parse_args()
 
 
@@ -195,6 +198,7 @@ def run_ours(args):
         solver = mr.Solver(K, prob.Lx, prob.Ly, prob.sub, prob.seg, prob.alpha, prob.bc_type,
                            stream=stream)
     mr.mrcm_enable_timing(solver.ctx, True)
+    mr.mrcm_set_refinement(solver.ctx, args.refine)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def step():
@@ -275,6 +279,30 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     balance = mass_balance(solver, q)
 
+    # ---- accuracy of the timed configuration (outside the timed regions):
+    # rel-L2 distance to the solve refined to the rounding level, which the
+    # parity tests pin to the FP64 oracle
+    timed = [x.cpu().numpy().copy() for x in (solver.p, solver.Fx, solver.Fy)]
+    mr.mrcm_set_refinement(solver.ctx, 3)
+    solver.solve(q, bcv)
+    refined = [x.cpu().numpy().copy() for x in (solver.p, solver.Fx, solver.Fy)]
+    rel = {name: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+           for name, a, b in zip(("p", "Fx", "Fy"), timed, refined)}
+    # ---- the same step with one refinement step, for reference ------------
+    mr.mrcm_set_refinement(solver.ctx, 1)
+    for _ in range(2):
+        step()
+    ref_ms = []
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+        ev0.record(stream)
+        step()
+        ev1.record(stream)
+        ev1.synchronize()
+        ref_ms.append(ev0.elapsed_time(ev1))
+    mr.mrcm_set_refinement(solver.ctx, args.refine)
+
     launches = (mr.mrcm_query(solver.ctx, "KERNEL_LAUNCHES_BUILD")
                 + mr.mrcm_query(solver.ctx, "KERNEL_LAUNCHES_SOLVE"))
     build_flops = mr.mrcm_query(solver.ctx, "BUILD_FLOPS")
@@ -318,7 +346,10 @@ def run_ours(args):
         e2e=dict(value=e2e_value, unit="cells/s", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
         gpu_launches=launches * args.steps,
         clocks=clocks,
-        check=dict(mass_balance=balance),
+        check=dict(mass_balance=balance, refine_steps=args.refine, rel_l2_vs_refined=rel,
+                   tolerance=1e-8, within_tolerance=bool(max(rel.values()) <= 1e-8)),
+        refined_step=dict(refine_steps=1, ms_per_step=sum(ref_ms) / len(ref_ms),
+                          value=cells * world / (sum(ref_ms) / len(ref_ms) / 1e3)),
         cpu_baseline=cpu,
     )
     print(json.dumps(line), flush=True)

@@ -96,8 +96,10 @@ __device__ __forceinline__ double t_entry(const NodeRefs& N, int r, int c, doubl
     const int g = N.g;
     const bool dr = r < g, dc = c < g;
     const int i = dr ? r : r - g, j = dc ? c : c - g;
-    const double ra = N.R1[N.gpos1[i] * N.m1 + N.gpos1[j]] * sdi * sdj;
-    const double rb = N.R2[N.gpos2[i] * N.m2 + N.gpos2[j]] * sdi * sdj;
+    // R is stored symmetric: read it along the column of j, so that
+    // consecutive r (consecutive i) read consecutive entries
+    const double ra = N.R1[N.gpos1[j] * N.m1 + N.gpos1[i]] * sdi * sdj;
+    const double rb = N.R2[N.gpos2[j] * N.m2 + N.gpos2[i]] * sdi * sdj;
     if (dr && dc) return 0.5 * (ra + rb) + (i == j ? 2.0 : 0.0);
     if (!dr && !dc) return 0.5 * (ra + rb) - sqi * sqj * inv_sum;
     return 0.5 * (rb - ra);
@@ -1269,6 +1271,18 @@ cudaError_t launch_merge_build(const DevView& v, int first, int count, int max_g
                                void* barrier, cudaStream_t s, int* launches, const PhaseHook& hook) {
     if (count == 0) return cudaSuccess;
     cudaError_t e;
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(gj_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      kSweepSmemPad)) != cudaSuccess)
+            return e;
+    }
+    // CTAs per node of the elementwise form / back-form passes: enough for
+    // about two CTAs per SM over the level, at least 64 where the work allows
+    const int per_node = std::max(64, 2 * sms / count);
     if (!merge_level_blocked(count, max_g2, max_m)) {
         HookScope hs(hook, kPhMergeSmall);
         e = launch_small(v, first, count, max_g2, max_m, s);
@@ -1279,7 +1293,7 @@ cudaError_t launch_merge_build(const DevView& v, int first, int count, int max_g
         HookScope hs(hook, kPhMergeForm);
         const long long work = (long long)max_g2 * max_g2;
         int gy = (int)((work + 255) / 256);
-        gy = gy < 1 ? 1 : (gy > 64 ? 64 : gy);
+        gy = gy < 1 ? 1 : (gy > per_node ? per_node : gy);
         merge_form_kernel<<<dim3(count, gy), 256, (size_t)max_g2 * sizeof(double), s>>>(v, first);
         ++*launches;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -1290,15 +1304,6 @@ cudaError_t launch_merge_build(const DevView& v, int first, int count, int max_g
         // off): the CTAs that invert the next diagonal blocks, which lie on
         // the sequential chain of the sweep, then own their SM's FP64 pipe
         // instead of queueing behind another CTA's tile updates.
-        static int sms = 0;
-        if (sms == 0) {
-            int dev = 0;
-            if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-            if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-            if ((e = cudaFuncSetAttribute(gj_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          kSweepSmemPad)) != cudaSuccess)
-                return e;
-        }
         const int tiles = (max_g2 + kGJTile - 1) / kGJTile;
         const long long items = (long long)count * (1 + tiles * (tiles + 1) / 2);
         int grid = (int)std::min<long long>(items, (long long)sms);
@@ -1316,7 +1321,7 @@ cudaError_t launch_merge_build(const DevView& v, int first, int count, int max_g
         HookScope hs(hook, kPhMergeForm);
         const long long work = (long long)(max_g2 / 2) * (max_g2 / 2);
         int gy = (int)((work + 255) / 256);
-        gy = gy < 1 ? 1 : (gy > 64 ? 64 : gy);
+        gy = gy < 1 ? 1 : (gy > per_node ? per_node : gy);
         merge_backform_kernel<<<dim3(count, gy), 256, (size_t)max_g2 * sizeof(double), s>>>(v, first);
         ++*launches;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
