@@ -131,7 +131,7 @@ constexpr int kSmallTri = (kSmallMax * (kSmallMax + 1) / 2 + kSmallThreads - 1) 
 __global__ void __launch_bounds__(kSmallThreads) merge_small_kernel(DevView v, int first, int mstride) {
     extern __shared__ __align__(16) double sm[];
     __shared__ double sd[kSmallMax / 2], sq[kSmallMax / 2], vrow[kSmallMax];
-    __shared__ double s_rp, s_inv_sum;
+    __shared__ double s_inv_sum;
     __shared__ int s_bad;
     const MergeDesc D = v.merges[first + blockIdx.x];
     const NodeRefs N = node_refs(v, D);
@@ -170,8 +170,11 @@ __global__ void __launch_bounds__(kSmallThreads) merge_small_kernel(DevView v, i
     // is symmetric, and after step k the entries of an eliminated and a
     // remaining index are antisymmetric, all others symmetric; so only the
     // lower triangle r >= c is kept: a_rk = -T[k][r] for r < k, a_kc =
-    // T[c][k] for c > k.  Per step warp 0 forms the reciprocal and the scaled
-    // pivot row v_c = a_kc / p; every kept entry then takes one FMA.
+    // T[c][k] for c > k.  Per step warp 0 forms the reciprocal (rcp_nr) and
+    // the scaled pivot row v_c = a_kc / p (v_k = 1 / p); every kept entry then
+    // takes one FMA, the same for all of them (no divergent branches):
+    //     T'_rc = x_r v_c + y_rc,  x_r = -a_rk (1 on the pivot row),
+    //     y_rc = T_rc off the pivot row and column, 0 on them.
     int er[kSmallTri], ec[kSmallTri];
 #pragma unroll
     for (int e = 0; e < kSmallTri; ++e) {
@@ -187,29 +190,24 @@ __global__ void __launch_bounds__(kSmallThreads) merge_small_kernel(DevView v, i
         __syncthreads();
         if (tid < 32) {
             const double p = T[k * g2 + k];
-            const double rp = 1.0 / p;
-            if (tid == 0) {
-                if (!pivot_ok(p, k < g)) s_bad = 1;
-                s_rp = rp;
-            }
+            const double rp = rcp_nr(p);
             if (tid < g2) {
                 const int c = tid;
-                const double a_kc = c <= k ? T[k * g2 + c] : T[c * g2 + k];
+                const double a_kc = c == k ? 1.0 : (c < k ? T[k * g2 + c] : T[c * g2 + k]);
                 vrow[c] = a_kc * rp;
             }
+            if (tid == 0 && !pivot_ok_bits(p, k < g)) s_bad = 1;
         }
         __syncthreads();
-        const double rp = s_rp;
         double nv[kSmallTri];
 #pragma unroll
         for (int e = 0; e < kSmallTri; ++e) {
             const int idx = tid + e * kSmallThreads;
             if (idx >= ntri) break;
             const int r = er[e], c = ec[e];
-            const double a_rk = r >= k ? T[r * g2 + k] : -T[k * g2 + r];
-            if (r == k) nv[e] = (c == k) ? rp : vrow[c];
-            else if (c == k) nv[e] = -a_rk * rp;
-            else nv[e] = fma(-a_rk, vrow[c], T[r * g2 + c]);
+            const double xr = r == k ? 1.0 : (r > k ? neg_bits(T[r * g2 + k]) : T[k * g2 + r]);
+            const double y = (r == k || c == k) ? 0.0 : T[r * g2 + c];
+            nv[e] = fma(xr, vrow[c], y);
         }
         __syncthreads();
 #pragma unroll
