@@ -215,7 +215,9 @@ enum {
  * the conditioning is below 1/u.  (With the quasi-definite interface
  * inverses the unrefined solve of a sigma^2 = 4 log-normal field at 1024^2
  * is already within 1e-11 of it; one step reaches the rounding level.)
- *   steps  0..16 refinement steps per mrcm_solve
+ *   steps  0..16 refinement steps per mrcm_solve; with 0 (the paper's single
+ *          pass) the outputs are formed in plain FP64, otherwise from the
+ *          double-double state, rounded once
  *   check  != 0: evaluate the residual once more after the last step (for
  *          mrcm_residual_history)
  *

@@ -494,6 +494,7 @@ __global__ void mean_partial_kernel(const double* __restrict__ ph, const double*
 
 // Subtracts the mean of the rounded cell pressures from p and P, in
 // double-double (the shift is exact up to its own rounding).
+template <bool kPlain>
 __global__ void mean_subtract_kernel(DevView v, long long n) {
     __shared__ double mean;
     if (threadIdx.x < 32) {
@@ -507,6 +508,16 @@ __global__ void mean_subtract_kernel(DevView v, long long n) {
     }
     __syncthreads();
     const long long stride = (long long)gridDim.x * blockDim.x;
+    if (kPlain) {
+        // no low parts: shift the high parts
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) v.p_hi[i] -= mean;
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < v.nseg; i += stride) {
+            v.segP[i] -= mean;
+            v.seg_lam_dd[2 * i].x -= mean;
+            v.seg_lam_dd[2 * i + 1].x -= mean;
+        }
+        return;
+    }
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) {
         const DD x = dd_add(DD{v.p_hi[i], v.p_lo[i]}, DD{-mean, 0.0});
         v.p_hi[i] = x.h;
@@ -556,12 +567,15 @@ cudaError_t launch_leaf_pressure(const DevView& v, bool accumulate, cudaStream_t
     return cudaGetLastError();
 }
 
-cudaError_t launch_mean_shift(const DevView& v, cudaStream_t s) {
+cudaError_t launch_mean_shift(const DevView& v, bool plain, cudaStream_t s) {
     const long long n = (long long)v.nx * v.ny;
     mean_partial_kernel<<<kRedBlocks, 256, 0, s>>>(v.p_hi, v.p_lo, n, v.red);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    mean_subtract_kernel<<<kRedBlocks, 256, 0, s>>>(v, n);
+    if (plain)
+        mean_subtract_kernel<true><<<kRedBlocks, 256, 0, s>>>(v, n);
+    else
+        mean_subtract_kernel<false><<<kRedBlocks, 256, 0, s>>>(v, n);
     return cudaGetLastError();
 }
 

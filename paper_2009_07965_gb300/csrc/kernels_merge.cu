@@ -319,7 +319,8 @@ __global__ void __launch_bounds__(256) merge_form_kernel(DevView v, int first) {
     double* T = v.W + D.W_off;
     const long long nT = (long long)g2 * g2;
     for (long long idx = blockIdx.y * 256LL + threadIdx.x; idx < nT; idx += (long long)gridDim.y * 256) {
-        const int r = (int)(idx % g2), c = (int)(idx / g2);
+        int r, c;
+        udivmod(idx, g2, c, r);
         const int i = r < g ? r : r - g, j = c < g ? c : c - g;
         T[idx] = t_entry(N, r, c, scl[g + i], scl[g + j], scl[i], scl[j], inv_sum);
     }
@@ -879,7 +880,8 @@ __global__ void __launch_bounds__(256) merge_backform_kernel(DevView v, int firs
     double* A = v.W + D.W_off;
     const long long n = (long long)g * g;
     for (long long idx = blockIdx.y * 256LL + threadIdx.x; idx < n; idx += (long long)gridDim.y * 256) {
-        const int i = (int)(idx % g), j = (int)(idx / g);
+        int i, j;
+        udivmod(idx, g, j, i);
         const double sc = 0.5 * sd[i] * sd[j];
         double* dd = A + (long long)j * g2 + i;          // (d_i, d_j)
         double* ds = A + (long long)(g + j) * g2 + i;    // (d_i, s_j)
@@ -1069,7 +1071,8 @@ __global__ void __launch_bounds__(256) tree_up_kernel(DevView v, TreeLevels L, u
         const int first = L.first[h], count = L.count[h], g2max = L.g2[h], mmax = L.m[h];
         if (count == 0) continue;                           // uniform over the grid
         for (long long t = t0; t < (long long)count * g2max; t += stride) {
-            const int q = (int)(t / g2max), k = (int)(t % g2max);
+            int q, k;
+            udivmod(t, g2max, q, k);
             const MergeDesc D = v.merges[first + q];
             if (k >= 2 * D.g) continue;
             const NodeRefs N = node_refs(v, D);
@@ -1082,9 +1085,9 @@ __global__ void __launch_bounds__(256) tree_up_kernel(DevView v, TreeLevels L, u
         const unsigned int gmask = (lanes == 32 ? 0xffffffffu : ((1u << lanes) - 1u) << (lane & ~(lanes - 1)));
         const long long total = (long long)count * mmax * lanes;
         for (long long t = t0; t < total; t += stride) {
-            const long long o = t / lanes;
-            const int sub = (int)(t % lanes);
-            const int q = (int)(o / mmax), i = (int)(o % mmax);
+            int o, sub, q, i;
+            udivmod(t, lanes, o, sub);
+            udivmod(o, mmax, q, i);
             const MergeDesc D = v.merges[first + q];
             const int g2 = 2 * D.g;
             const double* rg = v.rgam + 2LL * D.gamma_off;
@@ -1148,7 +1151,8 @@ __global__ void __launch_bounds__(256) tree_down_kernel(DevView v, TreeLevels L,
         // in one index space so that their load chains overlap
         for (long long t = t0; t < rows + (long long)count * mmax; t += stride) {
             if (t >= rows) {
-                const int q = (int)((t - rows) / mmax), j = (int)((t - rows) % mmax);
+                int q, j;
+                udivmod(t - rows, mmax, q, j);
                 const MergeDesc D = v.merges[first + q];
                 if (j >= D.m) continue;
                 const NodeRefs N = node_refs(v, D);
@@ -1157,9 +1161,9 @@ __global__ void __launch_bounds__(256) tree_down_kernel(DevView v, TreeLevels L,
                 else v.lam[D.r2_off + N.opos2[j - N.o1]] = lo;
                 continue;
             }
-            const int r = (int)(t % g2max);
-            const long long qk = t / g2max;
-            const int q = (int)(qk / nkc), kc = (int)(qk % nkc);
+            int r, qk, q, kc;
+            udivmod(t, g2max, qk, r);
+            udivmod(qk, nkc, q, kc);
             const MergeDesc D = v.merges[first + q];
             const NodeRefs N = node_refs(v, D);
             if (r >= N.g2) continue;
@@ -1204,9 +1208,9 @@ __global__ void __launch_bounds__(256) tree_down_kernel(DevView v, TreeLevels L,
             const int lane = tid & 31;
             const unsigned int gmask = (G == 32 ? 0xffffffffu : ((1u << G) - 1u) << (lane & ~(G - 1)));
             for (long long t = t0; t < (long long)count * g2max * G; t += stride) {
-                const int sub = (int)(t % G);
-                const long long o = t / G;
-                const int q = (int)(o / g2max), r = (int)(o % g2max);
+                int o, sub, q, r;
+                udivmod(t, G, o, sub);
+                udivmod(o, g2max, q, r);
                 const MergeDesc D = v.merges[first + q];
                 const double* ps = scratch + (long long)q * nkc * g2max + r;
                 double lg = 0.0;

@@ -89,7 +89,8 @@ __global__ void __launch_bounds__(256) residual_cells_kernel(DevView v, const do
     const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     double e = 0.0;
     if (c < n) {
-        const int i = (int)(c % v.nx), j = (int)(c / v.nx);
+        int i, j;
+        udivmod(c, v.nx, j, i);
         const DD pc = state_p(v, c);
         const long long fx = i + (long long)(v.nx + 1) * j;
         const long long fy = i + (long long)v.nx * j;
@@ -178,6 +179,7 @@ __global__ void lam_to_PU_kernel(DevView v, bool accumulate) {
 // state, each formed in double-double and rounded once.  Skeleton faces: the
 // one-sided F^a = rho^a (p_a - lambda^a), F^b = -(rho^b (p_b - lambda^b))
 // and their mean.
+template <bool kPlain>
 __global__ void face_flux_kernel(DevView v, const double* __restrict__ bc_val, double* __restrict__ p,
                                  double* __restrict__ Fx, double* __restrict__ Fy, double* __restrict__ iface) {
     const long long nxf = (long long)(v.nx + 1) * v.ny;
@@ -191,8 +193,8 @@ __global__ void face_flux_kernel(DevView v, const double* __restrict__ bc_val, d
     double F, fa = 0.0, fb = 0.0;
     bool skel = false;
     int axis, line, k;
-    if (xface) { axis = 0; line = (int)(fl % (v.nx + 1)); k = (int)(fl / (v.nx + 1)); }
-    else { axis = 1; k = (int)(fl % v.nx); line = (int)(fl / v.nx); }
+    if (xface) { axis = 0; udivmod(fl, v.nx + 1, k, line); }
+    else { axis = 1; udivmod(fl, v.nx, line, k); }
     const int nline = axis == 0 ? v.nx : v.ny;
     const double* cL = axis == 0 ? v.cxL : v.cyL;
     const double* cU = axis == 0 ? v.cxU : v.cyU;
@@ -200,7 +202,29 @@ __global__ void face_flux_kernel(DevView v, const double* __restrict__ bc_val, d
     const long long cb = axis == 0 ? (long long)k * v.nx + line : (long long)line * v.nx + k;
     const long long ca = axis == 0 ? cb - 1 : cb - v.nx;
     const double area = axis == 0 ? v.hy : v.hx;
-    if (line == 0) {
+    if (kPlain) {
+        // state without low parts (no refinement step): plain FP64
+        if (line == 0) {
+            const double g = bc_val[axis == 0 ? k : 2 * v.ny + k];
+            F = v.bc[2 * axis] ? -(cU[fl] * (v.p_hi[cb] - g)) : -(area * g);
+        } else if (line == nline) {
+            const double g = bc_val[axis == 0 ? v.ny + k : 2 * v.ny + v.nx + k];
+            F = v.bc[2 * axis + 1] ? cL[fl] * (v.p_hi[ca] - g) : area * g;
+        } else {
+            const int t = axis == 0 ? v.xface_seg[fl] : v.yface_seg[fl];
+            if (t >= 0) {
+                const double2 la = v.seg_lam_dd[2 * t], lb = v.seg_lam_dd[2 * t + 1];
+                const double da = cL[fl] * (v.p_hi[ca] - (la.x + la.y));
+                const double db = cU[fl] * (v.p_hi[cb] - (lb.x + lb.y));
+                fa = da;
+                fb = -db;
+                F = 0.5 * (da - db);
+                skel = true;
+            } else {
+                F = cL[fl] * (v.p_hi[ca] - v.p_hi[cb]);
+            }
+        }
+    } else if (line == 0) {
         const double g = bc_val[axis == 0 ? k : 2 * v.ny + k];
         DD out = v.bc[2 * axis] ? face_out_u(state_p(v, cb), DD{g, 0.0}, cU[fl]) : DD{__dmul_rn(area, g), 0.0};
         F = -(out.h + out.l);
@@ -257,9 +281,12 @@ cudaError_t launch_lam_to_PU(const DevView& v, bool accumulate, cudaStream_t s) 
 }
 
 cudaError_t launch_face_fluxes(const DevView& v, const double* bc_val, double* p, double* Fx,
-                               double* Fy, double* iface, cudaStream_t s) {
+                               double* Fy, double* iface, bool plain, cudaStream_t s) {
     const long long nf = (long long)(v.nx + 1) * v.ny + (long long)v.nx * (v.ny + 1);
-    face_flux_kernel<<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(v, bc_val, p, Fx, Fy, iface);
+    if (plain)
+        face_flux_kernel<true><<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(v, bc_val, p, Fx, Fy, iface);
+    else
+        face_flux_kernel<false><<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(v, bc_val, p, Fx, Fy, iface);
     return cudaGetLastError();
 }
 

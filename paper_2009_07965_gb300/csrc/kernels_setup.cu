@@ -70,7 +70,8 @@ __global__ void face_coef_kernel(DevView v) {
     const long long nyf = (long long)v.nx * (v.ny + 1);
     long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (f < nxf) {
-        const int i = (int)(f % (v.nx + 1)), j = (int)(f / (v.nx + 1));
+        int i, j;
+        udivmod(f, v.nx + 1, j, i);
         const double area = v.hy, hn = v.hx;
         const long long row = (long long)j * v.nx;
         double cl = 0.0, cu = 0.0;
@@ -94,7 +95,8 @@ __global__ void face_coef_kernel(DevView v) {
     }
     f -= nxf;
     if (f < nyf) {
-        const int i = (int)(f % v.nx), j = (int)(f / v.nx);
+        int i, j;
+        udivmod(f, v.nx, j, i);
         const double area = v.hx, hn = v.hy;
         double cl = 0.0, cu = 0.0;
         if (j == 0) {

@@ -842,10 +842,10 @@ static int enqueue_solve(mrcm_ctx* c, const double* q_dev, const double* bc_val_
     {
         PhaseScope ps(c, MRCM_PHASE_FINISH);
         if (P.pure_neumann) {
-            TRYC(launch_mean_shift(v, s));
+            TRYC(launch_mean_shift(v, steps == 0, s));
             launches += 2;
         }
-        TRYC(launch_face_fluxes(v, bc_val_dev, p_dev, Fx_dev, Fy_dev, iface_dev, s));
+        TRYC(launch_face_fluxes(v, bc_val_dev, p_dev, Fx_dev, Fy_dev, iface_dev, steps == 0, s));
         ++launches;
     }
     return MRCM_OK;

@@ -183,6 +183,15 @@ __device__ __forceinline__ double rcp_nr(double p) {
     const double s = fma(e0, e0, e0);
     return fma(x, s, x);
 }
+// Quotient and remainder of a non-negative index by a positive divisor in
+// 32-bit unsigned arithmetic (every index of the workspace is below 2^32;
+// a 64-bit division is a long emulated sequence).
+__device__ __forceinline__ void udivmod(long long x, int d, int& q, int& r) {
+    const unsigned ux = (unsigned)x, ud = (unsigned)d;
+    const unsigned uq = ux / ud;
+    q = (int)uq;
+    r = (int)(ux - uq * ud);
+}
 // -x by flipping the sign bit: an FP64 negation that is not an FMA operand
 // modifier (inside a select, say) costs a full FP64 instruction.
 __device__ __forceinline__ double neg_bits(double x) {
@@ -219,11 +228,14 @@ cudaError_t launch_lam_to_PU(const DevView& v, bool accumulate, cudaStream_t s);
 // residual of the discrete equations in double-double; fills rcell, sadj
 cudaError_t launch_residual(const DevView& v, const double* q, const double* bc_val, int step,
                             cudaStream_t s);
-// cell pressures and face fluxes from the double-double state; iface optional
+// cell pressures and face fluxes from the double-double state; iface
+// optional; plain: the state has no low parts (no refinement step ran), the
+// fluxes are formed in plain FP64
 cudaError_t launch_face_fluxes(const DevView& v, const double* bc_val, double* p, double* Fx,
-                               double* Fy, double* iface, cudaStream_t s);
-// zero-mean shift of the state's p and P (all-Neumann problems)
-cudaError_t launch_mean_shift(const DevView& v, cudaStream_t s);
+                               double* Fy, double* iface, bool plain, cudaStream_t s);
+// zero-mean shift of the state's p and P (all-Neumann problems); plain as
+// above (the shift is applied to the high parts only)
+cudaError_t launch_mean_shift(const DevView& v, bool plain, cudaStream_t s);
 // Brackets each launch group of a phase (the phase ids of include/mrcm.h).
 struct PhaseHook {
     void* ctx;

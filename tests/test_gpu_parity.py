@@ -263,6 +263,25 @@ def test_unrefined_solve_is_close_to_the_refined_one(mrcm_lib):
         assert rel(a, b) < 1e-14
 
 
+@pytest.mark.parametrize("bc", ["left_right", "quarter_five_spot"])
+def test_single_pass_matches_oracle(mrcm_lib, bc):
+    # the paper's single pass (no refinement step; outputs formed in plain
+    # FP64, the all-Neumann mean shift on the high parts) against the oracle
+    # at the 1e-8 rel-L2 the benchmark claims, one-sided fluxes included
+    import paper_2009_07965_gb300 as mr
+    import torch
+    prob = inputs.darcy_problem(160, 144, sigma2=4.0, corr=0.05, seed=77, bc=bc)
+    s = mr.Solver(torch.from_numpy(prob.K).cuda(), prob.Lx, prob.Ly, prob.sub, prob.seg, prob.alpha,
+                  prob.bc_type)
+    mr.mrcm_set_refinement(s.ctx, 0)
+    s.build_basis()
+    s.solve(torch.from_numpy(prob.q).cuda(), torch.from_numpy(prob.bc_val).cuda(), want_iface=True)
+    fa_x, fb_x, fa_y, fb_y = s.iface_parts()
+    g = dict(p=s.p, Fx=s.Fx, Fy=s.Fy, Fa_x=fa_x, Fb_x=fb_x, Fa_y=fa_y, Fb_y=fb_y)
+    g = {k: v.cpu().numpy() for k, v in g.items()}
+    _compare(g, solve_mrcm(prob), tol=1e-8)
+
+
 def test_square512_same_recipe_as_benchmark(mrcm_lib):
     # the benchmark recipe (sigma^2 = 4, corr 0.05, quarter-five-spot) at
     # 512^2: 1024 leaves, 10 levels, interface systems up to 2g = 256
