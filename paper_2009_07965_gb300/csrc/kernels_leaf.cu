@@ -138,18 +138,13 @@ __device__ __forceinline__ int segment_start_row(const DevView& v, const LeafDes
     return (s - L.side_off[0]) * v.gy * w;
 }
 
-template <int MMAX, int LPB>
-__global__ void __launch_bounds__(kLeafThreads * LPB)
-leaf_build_kernel(DevView v) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int t = threadIdx.x & (kLeafThreads - 1);
-    const int slot_leaf = threadIdx.x / kLeafThreads;
-    const int leaf = blockIdx.x * LPB + slot_leaf;
-    if (leaf >= v.nleaf) return;     // uniform over the 16 threads of the leaf
-    const unsigned mask = 0xFFFFu << (threadIdx.x & 16);
-    LeafBuildSmem<MMAX>& S = reinterpret_cast<LeafBuildSmem<MMAX>*>(smem_raw)[slot_leaf];
-    const LeafDesc L = v.leaves[leaf];
-    const int w = L.w, n = L.w * L.h, m = L.m, W2 = L.w + 2;
+// Body of the leaf build for one leaf; WF > 0 fixes the leaf to WF x WF
+// cells at compile time (the full leaf), 0 reads the size from the
+// descriptor (truncated leaves).
+template <int MMAX, int WF>
+__device__ __forceinline__ void leaf_build_body(const DevView& v, LeafBuildSmem<MMAX>& S, const LeafDesc& L, int t,
+                                                unsigned mask) {
+    const int w = WF ? WF : L.w, n = WF ? WF * WF : L.w * L.h, m = L.m, W2 = w + 2;
     double* Lg = v.leafL + L.L_off;          // n x 16 multipliers
     double* Dg = Lg + (long long)n * kLeafThreads;   // n reciprocal pivots
     double* LTg = Dg + n;                    // n x 16 multipliers by row
@@ -286,7 +281,23 @@ leaf_build_kernel(DevView v) {
         double val = (r >= c) ? S.R[r][c] : S.R[c][r];
         if (r == c) val -= S.W[r];
         Rg[idx] = val;
-    }
+    }}
+
+template <int MMAX, int LPB>
+__global__ void __launch_bounds__(kLeafThreads * LPB)
+leaf_build_kernel(DevView v) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int t = threadIdx.x & (kLeafThreads - 1);
+    const int slot_leaf = threadIdx.x / kLeafThreads;
+    const int leaf = blockIdx.x * LPB + slot_leaf;
+    if (leaf >= v.nleaf) return;     // uniform over the 16 threads of the leaf
+    const unsigned mask = 0xFFFFu << (threadIdx.x & 16);
+    LeafBuildSmem<MMAX>& S = reinterpret_cast<LeafBuildSmem<MMAX>*>(smem_raw)[slot_leaf];
+    const LeafDesc L = v.leaves[leaf];
+    if (L.w == kMaxLeafSide && L.h == kMaxLeafSide)
+        leaf_build_body<MMAX, kMaxLeafSide>(v, S, L, t, mask);
+    else
+        leaf_build_body<MMAX, 0>(v, S, L, t, mask);
 }
 
 // ---------------------------------------------------------------------------
