@@ -128,14 +128,14 @@ __device__ __forceinline__ bool pivot_ok_bits(double p, bool d_row) {
 // Shared layout: T[g2*g2], Wc[g2*g2], Bs[g*mstride], Xs[g2*mstride].
 constexpr int kSmallThreads = 256;
 constexpr int kSmallTri = (kSmallMax * (kSmallMax + 1) / 2 + kSmallThreads - 1) / kSmallThreads;   // kept T entries per thread
-__global__ void __launch_bounds__(kSmallThreads) merge_small_kernel(DevView v, int first, int mstride) {
-    extern __shared__ __align__(16) double sm[];
-    __shared__ double sd[kSmallMax / 2], sq[kSmallMax / 2], vrow[kSmallMax];
-    __shared__ double s_inv_sum;
-    __shared__ int s_bad;
-    const MergeDesc D = v.merges[first + blockIdx.x];
-    const NodeRefs N = node_refs(v, D);
-    const int g = N.g, g2 = N.g2, m = N.m, o1 = N.o1;
+// Body of the per-node merge; G2F > 0 fixes 2g at compile time (the sizes of
+// a uniform tree's lower levels: its loops and the T index arithmetic then
+// fold), 0 reads it from the descriptor.
+template <int G2F>
+__device__ __forceinline__ void merge_small_body(const DevView& v, const MergeDesc& D, const NodeRefs& N, int mstride,
+                                                 double* sm, double* sd, double* sq, double* vrow,
+                                                 double& s_inv_sum, int& s_bad) {
+    const int g2 = G2F ? G2F : N.g2, g = g2 / 2, m = N.m, o1 = N.o1;
     const int tid = threadIdx.x;
     double* T = sm;
     double* Wc = T + g2 * g2;
@@ -277,6 +277,20 @@ __global__ void __launch_bounds__(kSmallThreads) merge_small_kernel(DevView v, i
         const double val = roo + (acc0 + acc1);
         Rp[(long long)i * m + j] = val;
         Rp[(long long)j * m + i] = val;
+    }}
+
+__global__ void __launch_bounds__(kSmallThreads) merge_small_kernel(DevView v, int first, int mstride) {
+    extern __shared__ __align__(16) double sm[];
+    __shared__ double sd[kSmallMax / 2], sq[kSmallMax / 2], vrow[kSmallMax];
+    __shared__ double s_inv_sum;
+    __shared__ int s_bad;
+    const MergeDesc D = v.merges[first + blockIdx.x];
+    const NodeRefs N = node_refs(v, D);
+    switch (N.g2) {                                       // uniform per CTA
+        case 8: merge_small_body<8>(v, D, N, mstride, sm, sd, sq, vrow, s_inv_sum, s_bad); break;
+        case 16: merge_small_body<16>(v, D, N, mstride, sm, sd, sq, vrow, s_inv_sum, s_bad); break;
+        case 32: merge_small_body<32>(v, D, N, mstride, sm, sd, sq, vrow, s_inv_sum, s_bad); break;
+        default: merge_small_body<0>(v, D, N, mstride, sm, sd, sq, vrow, s_inv_sum, s_bad); break;
     }
 }
 
