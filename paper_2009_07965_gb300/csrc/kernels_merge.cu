@@ -912,8 +912,13 @@ __global__ void __launch_bounds__(256) merge_backform_kernel(DevView v, int firs
 // X = -W C with C = blockdiag(R^a_go, R^b_go): column j < o1 uses the first
 // g columns of W, the others the last g.  A CTA computes 64 rows x 16
 // columns; the gathered entries of C are staged in shared memory in chunks.
-constexpr int kXRows = 64, kXColsOut = 16, kXChunk = 64;
+constexpr int kXColsOut = 16, kXChunk = 64;
+// XROWS rows x kXColsOut columns of X per CTA: 32 unless the level has
+// CTAs in great excess (then 64, fewer staged loads per product); with few
+// long rows per node the smaller CTAs keep more SMs busy.
+template <int XROWS>
 __global__ void __launch_bounds__(256) merge_x_kernel(DevView v, int first) {
+    constexpr int kXRows = XROWS, kQ = kXRows * kXColsOut / 256;   // outputs per thread
     __shared__ double Cs[kXChunk][kXColsOut];
     const MergeDesc D = v.merges[first + blockIdx.x];
     const NodeRefs N = node_refs(v, D);
@@ -923,9 +928,11 @@ __global__ void __launch_bounds__(256) merge_x_kernel(DevView v, int first) {
     if (j0 >= m) return;                              // uniform per CTA
     const double* W = v.W + D.W_off;
     double* X = v.X + D.X_off;
-    const int tid = threadIdx.x, rl = tid % kXRows, cg = tid / kXRows;   // 4 groups of 4 columns
+    const int tid = threadIdx.x, rl = tid % kXRows, cg = tid / kXRows;   // column groups of kQ
     const int r = r0 + rl;
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    double acc[kQ];
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) acc[q] = 0.0;
     // columns of this CTA may straddle o1: treat the two halves separately
     for (int half = 0; half < 2; ++half) {
         const int jlo = half == 0 ? 0 : N.o1, jhi = half == 0 ? N.o1 : m;
@@ -948,42 +955,47 @@ __global__ void __launch_bounds__(256) merge_x_kernel(DevView v, int first) {
                 for (int kk = 0; kk < kn; ++kk) {
                     const double wv = wcol[(long long)kk * g2];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) acc[q] += wv * Cs[kk][cg * 4 + q];
+                    for (int q = 0; q < kQ; ++q) acc[q] += wv * Cs[kk][cg * kQ + q];
                 }
             }
         }
     }
     if (r < g2) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int j = j0 + cg * 4 + q;
+        for (int q = 0; q < kQ; ++q) {
+            const int j = j0 + cg * kQ + q;
             if (j < m) X[(long long)j * g2 + r] = -acc[q];
         }
     }
 }
 
-// R = blockdiag(R_oo) + blockdiag(R_og) X on kRTile^2 output tiles (the
+// R = blockdiag(R_oo) + blockdiag(R_og) X on (16 TS)^2 output tiles (the
 // lower triangle, mirrored: R is symmetric): row i
 // of the tile uses the gathered row of R^a (i < o1) or R^b and the matching
 // half of X; both are staged in shared memory in chunks of kRTile.
+// staged in shared memory in chunks of kRTile.  TS = 1 (16 x 16 tiles, one
+// entry per thread) unless the level has tiles in great excess (then TS = 2,
+// 32 x 32 tiles, 2 x 2 per thread): with few nodes per height the small
+// tiles keep more SMs busy behind the long k loops.
+template <int TS>
 __global__ void __launch_bounds__(256) merge_rupdate_kernel(DevView v, int first) {
-    __shared__ double Cs[kRTile][kRTile + 1];        // Cs[row][k]
-    __shared__ double Xs[2][kRTile][kRTile + 1];     // Xs[half][k][col]
+    constexpr int kTile = 16 * TS;
+    __shared__ double Cs[kTile][kRTile + 1];         // Cs[row][k]
+    __shared__ double Xs[2][kRTile][kTile + 1];      // Xs[half][k][col]
     const MergeDesc D = v.merges[first + blockIdx.x];
     const NodeRefs N = node_refs(v, D);
     const int m = N.m, g = N.g, g2 = N.g2, o1 = N.o1;
-    const int tiles = (m + kRTile - 1) / kRTile;
+    const int tiles = (m + kTile - 1) / kTile;
     if ((int)blockIdx.y >= tiles * (tiles + 1) / 2) return;
     // R is symmetric: lower-triangle tiles (ti >= tj) only, mirrored on write
     int ti = (int)((sqrtf(8.0f * blockIdx.y + 1.0f) - 1.0f) * 0.5f);
     while ((ti + 1) * (ti + 2) / 2 <= (int)blockIdx.y) ++ti;
     while (ti * (ti + 1) / 2 > (int)blockIdx.y) --ti;
     const int tj = blockIdx.y - ti * (ti + 1) / 2;
-    const int i0 = ti * kRTile, jt = tj * kRTile;
+    const int i0 = ti * kTile, jt = tj * kTile;
     const double* X = v.X + D.X_off;
     double* Rp = v.R + D.R_off;
     const int tid = threadIdx.x;
-    constexpr int TS = kRTile / 16;
     const int tr = (tid % 16) * TS, tc = (tid / 16) * TS;
     double acc[TS][TS];
 #pragma unroll
@@ -993,7 +1005,7 @@ __global__ void __launch_bounds__(256) merge_rupdate_kernel(DevView v, int first
     for (int k0 = 0; k0 < g; k0 += kRTile) {
         const int kn = min(kRTile, g - k0);
         __syncthreads();
-        for (int idx = tid; idx < kRTile * kRTile; idx += 256) {
+        for (int idx = tid; idx < kTile * kRTile; idx += 256) {
             const int rr = idx / kRTile, kk = idx % kRTile, i = i0 + rr;
             double c = 0.0;
             if (kk < kn && i < m)
@@ -1001,8 +1013,8 @@ __global__ void __launch_bounds__(256) merge_rupdate_kernel(DevView v, int first
                            : N.R2[N.opos2[i - o1] * N.m2 + N.gpos2[k0 + kk]];
             Cs[rr][kk] = c;
         }
-        for (int idx = tid; idx < 2 * kRTile * kRTile; idx += 256) {
-            const int half = idx / (kRTile * kRTile), rem = idx % (kRTile * kRTile);
+        for (int idx = tid; idx < 2 * kRTile * kTile; idx += 256) {
+            const int half = idx / (kRTile * kTile), rem = idx % (kRTile * kTile);
             const int kk = rem % kRTile, jj = rem / kRTile, j = jt + jj;
             Xs[half][kk][jj] = (kk < kn && j < m) ? X[(long long)j * g2 + half * g + k0 + kk] : 0.0;
         }
@@ -1345,14 +1357,25 @@ cudaError_t launch_merge_build(const DevView& v, int first, int count, int max_g
     if (max_m > 0) {
         {
             HookScope hs(hook, kPhMergeX);
-            const int rt = (max_g2 + kXRows - 1) / kXRows, ct = (max_m + kXColsOut - 1) / kXColsOut;
-            merge_x_kernel<<<dim3(count, rt * ct), 256, 0, s>>>(v, first);
+            const int ct = (max_m + kXColsOut - 1) / kXColsOut;
+            const int rt64 = (max_g2 + 63) / 64;
+            if ((long long)count * rt64 * ct >= 64LL * sms) {
+                merge_x_kernel<64><<<dim3(count, rt64 * ct), 256, 0, s>>>(v, first);
+            } else {
+                const int rt32 = (max_g2 + 31) / 32;
+                merge_x_kernel<32><<<dim3(count, rt32 * ct), 256, 0, s>>>(v, first);
+            }
             ++*launches;
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
         HookScope hs(hook, kPhMergeR);
-        const int rtiles = (max_m + kRTile - 1) / kRTile;
-        merge_rupdate_kernel<<<dim3(count, rtiles * (rtiles + 1) / 2), 256, 0, s>>>(v, first);
+        const int rt32 = (max_m + 31) / 32;
+        if ((long long)count * rt32 * (rt32 + 1) / 2 >= 64LL * sms) {
+            merge_rupdate_kernel<2><<<dim3(count, rt32 * (rt32 + 1) / 2), 256, 0, s>>>(v, first);
+        } else {
+            const int rt16 = (max_m + 15) / 16;
+            merge_rupdate_kernel<1><<<dim3(count, rt16 * (rt16 + 1) / 2), 256, 0, s>>>(v, first);
+        }
         ++*launches;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
