@@ -191,7 +191,9 @@ enum {
     MRCM_PHASE_GJ_SWEEP = 3,       /* blocked merges: Gauss-Jordan inversion of the
                                       quasi-definite form                           */
     MRCM_PHASE_MERGE_FORM = 4,     /* blocked merges: the quasi-definite form of the
-                                      interface matrix and its back transform       */
+                                      interface matrix and its back transform; now
+                                      done inside the sweep's launch (timed as
+                                      MRCM_PHASE_GJ_SWEEP, this phase reports 0)   */
     MRCM_PHASE_MERGE_X = 5,        /* blocked merges: X = -W C                      */
     MRCM_PHASE_MERGE_R = 6,        /* blocked merges: merged R = R_oo + C^T X       */
     MRCM_PHASE_LEAF_PART = 7,      /* leaf particular solutions (solve)             */

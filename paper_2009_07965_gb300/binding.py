@@ -32,7 +32,7 @@ PHASES = ["coef", "leaf_build", "merge_small", "gj_sweep", "merge_form", "merge_
 # kernel family behind each phase (for reports)
 PHASE_KERNELS = {"coef": "face_coef_kernel", "leaf_build": "leaf_build_kernel",
                  "merge_small": "merge_small_kernel", "gj_sweep": "gj_sweep_kernel",
-                 "merge_form": "merge_form_kernel+merge_backform_kernel", "merge_x": "merge_x_kernel",
+                 "merge_form": "gj_sweep_kernel (form and back-form folded in)", "merge_x": "merge_x_kernel",
                  "merge_r": "merge_rupdate_kernel", "leaf_particular": "leaf_particular_kernel",
                  "tree_up": "tree_up_kernel", "tree_down": "tree_down_kernel",
                  "leaf_pressure": "leaf_pressure_kernel", "residual": "residual_cells/segments_kernel",

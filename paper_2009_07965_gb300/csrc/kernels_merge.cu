@@ -322,23 +322,6 @@ __device__ double stage_gamma_scalings(const DevView& v, const MergeDesc& D, dou
     return block_sum256(part, red);
 }
 
-__global__ void __launch_bounds__(256) merge_form_kernel(DevView v, int first) {
-    extern __shared__ __align__(16) double scl[];     // D^1/2, D^-1/2 of gamma
-    __shared__ double red[8];
-    const MergeDesc D = v.merges[first + blockIdx.x];
-    const NodeRefs N = node_refs(v, D);
-    const int g = N.g, g2 = N.g2;
-    const double sum = stage_gamma_scalings(v, D, scl, red);
-    const double inv_sum = (D.pinned && sum > 0.0) ? 1.0 / sum : 0.0;
-    double* T = v.W + D.W_off;
-    const long long nT = (long long)g2 * g2;
-    for (long long idx = blockIdx.y * 256LL + threadIdx.x; idx < nT; idx += (long long)gridDim.y * 256) {
-        int r, c;
-        udivmod(idx, g2, c, r);
-        const int i = r < g ? r : r - g, j = c < g ? c : c - g;
-        T[idx] = t_entry(N, r, c, scl[g + i], scl[g + j], scl[i], scl[j], inv_sum);
-    }
-}
 
 // Scratch of the blocked sweep, per node: two buffers for the inverse P of
 // a diagonal block (kGJ x kGJ, row-major; block step k uses buffer k & 1),
@@ -782,6 +765,56 @@ __device__ __forceinline__ void gj_lower_tile(int r, int tiles, int tk, int& ti,
     tj = 0;
 }
 
+// T (the quasi-definite form) of one node for entries [e0, e1) of its
+// column-major 2g x 2g storage, by one CTA (scalings staged in scl: 2g
+// doubles).
+__device__ void form_item(const DevView& v, const MergeDesc& D, long long e0, long long e1, double* scl,
+                          double* red) {
+    const NodeRefs N = node_refs(v, D);
+    const int g = N.g, g2 = N.g2;
+    const double sum = stage_gamma_scalings(v, D, scl, red);
+    const double inv_sum = (D.pinned && sum > 0.0) ? 1.0 / sum : 0.0;
+    double* T = v.W + D.W_off;
+    for (long long idx = e0 + threadIdx.x; idx < e1; idx += 256) {
+        int r, c;
+        udivmod(idx, g2, c, r);
+        const int i = r < g ? r : r - g, j = c < g ? c : c - g;
+        T[idx] = t_entry(N, r, c, scl[g + i], scl[g + j], scl[i], scl[j], inv_sum);
+    }
+}
+// T^-1 -> W = D^-1/2 Q T^-1 Q^T D^-1/2 in place for the 2 x 2 block patterns
+// (i, j), i, j < g, with pattern index in [e0, e1), by one CTA.
+__device__ void backform_item(const DevView& v, const MergeDesc& D, long long e0, long long e1, double* scl,
+                              double* red) {
+    const int g = D.g, g2 = 2 * g;
+    stage_gamma_scalings(v, D, scl, red);
+    const double* sd = scl + g;
+    double* A = v.W + D.W_off;
+    for (long long idx = e0 + threadIdx.x; idx < e1; idx += 256) {
+        int i, j;
+        udivmod(idx, g, j, i);
+        const double sc = 0.5 * sd[i] * sd[j];
+        double* dd = A + (long long)j * g2 + i;          // (d_i, d_j)
+        double* ds = A + (long long)(g + j) * g2 + i;    // (d_i, s_j)
+        double* sdp = A + (long long)j * g2 + g + i;     // (s_i, d_j)
+        double* ss = A + (long long)(g + j) * g2 + g + i;
+        const double zdd = __ldcg(dd), zds = __ldcg(ds), zsd = __ldcg(sdp), zss = __ldcg(ss);
+        *dd = (zdd - zds - zsd + zss) * sc;   // W(a_i, a_j)
+        *ds = (zss + zsd - zds - zdd) * sc;   // W(a_i, b_j)
+        *sdp = (zss + zds - zsd - zdd) * sc;  // W(b_i, a_j)
+        *ss = (zdd + zds + zsd + zss) * sc;   // W(b_i, b_j)
+    }
+}
+// Items of an elementwise pass over every node of a level: each node's
+// `per_node` entries split into runs of a multiple of 256, about one item
+// per CTA over the level.
+__device__ __forceinline__ long long level_run(long long per_node, int count) {
+    const long long want = (gridDim.x + count - 1) / count;          // items per node
+    long long run = (per_node + want - 1) / want;
+    run = (run + 255) / 256 * 256;
+    return run < 256 ? 256 : run;
+}
+
 // The whole blocked Gauss-Jordan sweep of one tree height in one cooperative
 // launch, on the lower triangle: P_0 of every node; c and u of block 0; per
 // block step one fused phase (the nodes' next diagonal blocks first, then
@@ -792,6 +825,8 @@ __global__ void __launch_bounds__(256) gj_sweep_kernel(DevView v, int first, int
                                                        unsigned int* counter) {
     __shared__ GJSmem S;
     __shared__ int s_bad;
+    __shared__ double red[8];
+    extern __shared__ __align__(16) double scl[];           // 2g scalings (form / back-form)
     const int tiles = (nmax + kGJTile - 1) / kGJTile;
     const int nlower = tiles * (tiles + 1) / 2;
     const int nsteps = (nmax + kGJ - 1) / kGJ;
@@ -799,6 +834,20 @@ __global__ void __launch_bounds__(256) gj_sweep_kernel(DevView v, int first, int
     unsigned int round = 0;
     if (tid == 0) s_bad = 0;
     __syncthreads();
+    // T of every node of the level into its W storage
+    {
+        const long long per = (long long)nmax * nmax, run = level_run(per, count);
+        const long long runs = (per + run - 1) / run;
+        for (long long item = blockIdx.x; item < count * runs; item += gridDim.x) {
+            const int q = (int)(item / runs);
+            const long long e0 = (item % runs) * run;
+            const MergeDesc D = v.merges[first + q];
+            const long long nT = 4LL * D.g * D.g;
+            if (e0 >= nT) continue;                                  // uniform per CTA
+            form_item(v, D, e0, min(e0 + run, nT), scl, red);
+        }
+    }
+    if (!grid_barrier(counter, round, v.status)) return;
     for (int q = blockIdx.x; q < count; q += gridDim.x) {
         const MergeDesc D = v.merges[first + q];
         const int N = 2 * D.g, nb = min(kGJ, N);
@@ -878,36 +927,24 @@ __global__ void __launch_bounds__(256) gj_sweep_kernel(DevView v, int first, int
             if (i < N && j < N && i > j) A[(long long)i * N + j] = __ldcg(A + (long long)j * N + i);
         }
     }
+    // T^-1 -> W of every node
+    if (!grid_barrier(counter, round, v.status)) return;
+    {
+        const long long per = (long long)(nmax / 2) * (nmax / 2), run = level_run(per, count);
+        const long long runs = (per + run - 1) / run;
+        for (long long item = blockIdx.x; item < count * runs; item += gridDim.x) {
+            const int q = (int)(item / runs);
+            const long long e0 = (item % runs) * run;
+            const MergeDesc D = v.merges[first + q];
+            const long long np = (long long)D.g * D.g;
+            if (e0 >= np) continue;                                  // uniform per CTA
+            backform_item(v, D, e0, min(e0 + run, np), scl, red);
+        }
+    }
     __syncthreads();
     if (tid == 0 && s_bad) atomicOr(v.status, kStatusSingular);
 }
 
-// T^-1 -> W = D^-1/2 Q T^-1 Q^T D^-1/2, in place (one thread per 2 x 2 block
-// pattern (i, j), i, j < g).
-__global__ void __launch_bounds__(256) merge_backform_kernel(DevView v, int first) {
-    extern __shared__ __align__(16) double scl[];
-    __shared__ double red[8];
-    const MergeDesc D = v.merges[first + blockIdx.x];
-    const int g = D.g, g2 = 2 * g;
-    stage_gamma_scalings(v, D, scl, red);
-    const double* sd = scl + g;
-    double* A = v.W + D.W_off;
-    const long long n = (long long)g * g;
-    for (long long idx = blockIdx.y * 256LL + threadIdx.x; idx < n; idx += (long long)gridDim.y * 256) {
-        int i, j;
-        udivmod(idx, g, j, i);
-        const double sc = 0.5 * sd[i] * sd[j];
-        double* dd = A + (long long)j * g2 + i;          // (d_i, d_j)
-        double* ds = A + (long long)(g + j) * g2 + i;    // (d_i, s_j)
-        double* sdp = A + (long long)j * g2 + g + i;     // (s_i, d_j)
-        double* ss = A + (long long)(g + j) * g2 + g + i;
-        const double zdd = *dd, zds = *ds, zsd = *sdp, zss = *ss;
-        *dd = (zdd - zds - zsd + zss) * sc;   // W(a_i, a_j)
-        *ds = (zss + zsd - zds - zdd) * sc;   // W(a_i, b_j)
-        *sdp = (zss + zds - zsd - zdd) * sc;  // W(b_i, a_j)
-        *ss = (zdd + zds + zsd + zss) * sc;   // W(b_i, b_j)
-    }
-}
 
 // X = -W C with C = blockdiag(R^a_go, R^b_go): column j < o1 uses the first
 // g columns of W, the others the last g.  A CTA computes 64 rows x 16
@@ -1308,23 +1345,11 @@ cudaError_t launch_merge_build(const DevView& v, int first, int count, int max_g
                                       kSweepSmemPad)) != cudaSuccess)
             return e;
     }
-    // CTAs per node of the elementwise form / back-form passes: enough for
-    // about two CTAs per SM over the level, at least 64 where the work allows
-    const int per_node = std::max(64, 2 * sms / count);
     if (!merge_level_blocked(count, max_g2, max_m)) {
         HookScope hs(hook, kPhMergeSmall);
         e = launch_small(v, first, count, max_g2, max_m, s);
         ++*launches;
         return e;
-    }
-    {
-        HookScope hs(hook, kPhMergeForm);
-        const long long work = (long long)max_g2 * max_g2;
-        int gy = (int)((work + 255) / 256);
-        gy = gy < 1 ? 1 : (gy > per_node ? per_node : gy);
-        merge_form_kernel<<<dim3(count, gy), 256, (size_t)max_g2 * sizeof(double), s>>>(v, first);
-        ++*launches;
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     {
         HookScope hs(hook, kPhGjSweep);
@@ -1344,15 +1369,6 @@ cudaError_t launch_merge_build(const DevView& v, int first, int count, int max_g
         e = cudaLaunchCooperativeKernel((const void*)gj_sweep_kernel, dim3(grid), dim3(256), args, kSweepSmemPad, s);
         ++*launches;
         if (e != cudaSuccess) return e;
-    }
-    {
-        HookScope hs(hook, kPhMergeForm);
-        const long long work = (long long)(max_g2 / 2) * (max_g2 / 2);
-        int gy = (int)((work + 255) / 256);
-        gy = gy < 1 ? 1 : (gy > per_node ? per_node : gy);
-        merge_backform_kernel<<<dim3(count, gy), 256, (size_t)max_g2 * sizeof(double), s>>>(v, first);
-        ++*launches;
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if (max_m > 0) {
         {
