@@ -1336,15 +1336,15 @@ cudaError_t launch_merge_build(const DevView& v, int first, int count, int max_g
                                void* barrier, cudaStream_t s, int* launches, const PhaseHook& hook) {
     if (count == 0) return cudaSuccess;
     cudaError_t e;
-    static int sms = 0;
-    if (sms == 0) {
-        int dev = 0;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        if ((e = cudaFuncSetAttribute(gj_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      kSweepSmemPad)) != cudaSuccess)
-            return e;
-    }
+    // per call, so that every device the library runs on gets its own SM
+    // count and the sweep's shared-memory attribute (cheap host calls; a
+    // captured build makes them once)
+    int sms = 0, dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(gj_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSweepSmemPad)) !=
+        cudaSuccess)
+        return e;
     if (!merge_level_blocked(count, max_g2, max_m)) {
         HookScope hs(hook, kPhMergeSmall);
         e = launch_small(v, first, count, max_g2, max_m, s);
