@@ -60,6 +60,19 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def job_throughput(local_ms, cells_per_rank, steps, world, device="cpu"):
+    """Whole-job cells/s of a weakly scaled run: every rank's summed step
+    time is reduced to the maximum over ranks (the job ends with its slowest
+    rank) and all ranks' cells are counted.  Returns (value, max_ms)."""
+    import torch
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    max_ms = float(t.item())
+    return cells_per_rank * world * steps / (max_ms / 1e3), max_ms
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle timing (the cpu_baseline leg and the reference arm)
 ORACLE_SNIPPET = r"""
@@ -232,13 +245,8 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
-    total_ms = sum(step_ms)
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
     cells = n * n
-    value = cells * world * args.steps / (total_ms / 1e3)
+    value, total_ms = job_throughput(sum(step_ms), cells, args.steps, world, dev)
 
     # ---- end to end from pinned host buffers ------------------------------
     K_h = torch.from_numpy(prob.K).pin_memory()
@@ -268,10 +276,7 @@ def run_ours(args):
         ev1.synchronize()
         if it >= args.warmup:
             e2e_ms.append(ev0.elapsed_time(ev1))
-    t = torch.tensor([sum(e2e_ms)], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_value = cells * world * args.steps / (float(t.item()) / 1e3)
+    e2e_value, _ = job_throughput(sum(e2e_ms), cells, args.steps, world, dev)
     h2d = (K_h.numel() + q_h.numel() + bc_h.numel()) * 8
     d2h = (p_h.numel() + fx_h.numel() + fy_h.numel()) * 8
     solver.solve(q, bcv, want_iface=True)
