@@ -30,6 +30,9 @@ sys.path.insert(0, ROOT)
 METRIC = "fine cells/s full RecMRCM solve at rel-L2 ≤1e-8 vs FP64 oracle; % roofline"
 # FP64 FMA pipe of GB300: 2 DFMA / clock / SM x 152 SMs x 2.07 GHz x 2 flops
 FP64_PEAK_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
+# rel-L2 bar of the FP64 form against the FP64 oracle (the metric's own
+# tolerance, 1e-8, is the mixed form's)
+FP64_FORM_TOL = 1e-10
 WORKLOAD = ("square1024-qfs: 1024x1024 cells, log-normal K sigma^2=4 corr 0.05 (seed 2000), "
             "quarter-five-spot, no-flow, 64x64 leaves of 16x16, 4-cell segments, alpha=1, 12 levels")
 CPU_SAMPLE_N = 256
@@ -351,7 +354,8 @@ def run_ours(args):
         gpu_launches=launches * args.steps,
         clocks=clocks,
         check=dict(mass_balance=balance, refine_steps=args.refine, rel_l2_vs_refined=rel,
-                   tolerance=1e-8, within_tolerance=bool(max(rel.values()) <= 1e-8)),
+                   tolerance=FP64_FORM_TOL, within_tolerance=bool(max(rel.values()) <= FP64_FORM_TOL),
+                   metric_tolerance=1e-8),
         refined_step=dict(refine_steps=1, ms_per_step=sum(ref_ms) / len(ref_ms),
                           value=cells * world / (sum(ref_ms) / len(ref_ms) / 1e3)),
         cpu_baseline=cpu,
