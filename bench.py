@@ -40,7 +40,7 @@ CPU_SAMPLE_N = 256
 # workload, from one ncu capture of this bench (dram__bytes_read.sum +
 # dram__bytes_write.sum).  A family missing here reports traffic null.
 TRAFFIC_PER_LAUNCH = {
-    "gj_sweep": dict(bytes=1.230e6, source="ncu capture, mean over the 7 launches of one build"),
+    "gj_sweep": dict(bytes=1.216e6, source="ncu capture, mean over the 7 launches of one build"),
 }
 
 

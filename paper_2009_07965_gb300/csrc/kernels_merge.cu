@@ -767,7 +767,9 @@ __device__ __forceinline__ void gj_lower_tile(int r, int tiles, int tk, int& ti,
 
 // T (the quasi-definite form) of one node for entries [e0, e1) of its
 // column-major 2g x 2g storage, by one CTA (scalings staged in scl: 2g
-// doubles).
+// doubles).  A CTA may take several items in a row (levels with more nodes
+// than CTAs): the closing barrier keeps the next item's staging off scl
+// until every thread is done with it.
 __device__ void form_item(const DevView& v, const MergeDesc& D, long long e0, long long e1, double* scl,
                           double* red) {
     const NodeRefs N = node_refs(v, D);
@@ -781,6 +783,7 @@ __device__ void form_item(const DevView& v, const MergeDesc& D, long long e0, lo
         const int i = r < g ? r : r - g, j = c < g ? c : c - g;
         T[idx] = t_entry(N, r, c, scl[g + i], scl[g + j], scl[i], scl[j], inv_sum);
     }
+    __syncthreads();     // the CTA's next item restages scl
 }
 // T^-1 -> W = D^-1/2 Q T^-1 Q^T D^-1/2 in place for the 2 x 2 block patterns
 // (i, j), i, j < g, with pattern index in [e0, e1), by one CTA.
@@ -804,6 +807,7 @@ __device__ void backform_item(const DevView& v, const MergeDesc& D, long long e0
         *sdp = (zss + zds - zsd - zdd) * sc;  // W(b_i, a_j)
         *ss = (zdd + zds + zsd + zss) * sc;   // W(b_i, b_j)
     }
+    __syncthreads();     // the CTA's next item restages scl
 }
 // Items of an elementwise pass over every node of a level: each node's
 // `per_node` entries split into runs of a multiple of 256, about one item
