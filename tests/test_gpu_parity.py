@@ -282,6 +282,34 @@ def test_single_pass_matches_oracle(mrcm_lib, bc):
     _compare(g, solve_mrcm(prob), tol=1e-10)
 
 
+def test_heights_with_more_nodes_than_ctas(mrcm_lib):
+    # one-cell segments: at 512^2 the first blocked height (2g = 64) has 256
+    # nodes, more than the sweep's CTAs, so CTAs take several form, look-ahead
+    # and back-form items in a row; MRCM with one-face segments equals the fine
+    # solution, and a repeated build gives the same bits
+    import paper_2009_07965_gb300 as mr
+    import torch
+    prob = inputs.darcy_problem(512, 512, sigma2=2.0, corr=0.1, seed=41, bc="quarter_five_spot", seg=(1, 1),
+                                alpha=5.0)
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        s = mr.Solver(torch.from_numpy(prob.K).cuda(), prob.Lx, prob.Ly, prob.sub, prob.seg, prob.alpha,
+                      prob.bc_type, stream=st)
+        q, bc = torch.from_numpy(prob.q).cuda(), torch.from_numpy(prob.bc_val).cuda()
+        outs = []
+        for _ in range(2):
+            s.build_basis()
+            s.solve(q, bc)
+            outs.append([t.cpu().numpy().copy() for t in (s.p, s.Fx, s.Fy)])
+        st.synchronize()
+        s.close()
+    for a, b in zip(outs[0], outs[1]):
+        assert np.array_equal(a, b)
+    f = solve_fine(prob)
+    for k, g in zip(("p", "Fx", "Fy"), outs[0]):
+        assert rel(g, f[k]) < 1e-10, (k, rel(g, f[k]))
+
+
 def test_square512_same_recipe_as_benchmark(mrcm_lib):
     # the benchmark recipe (sigma^2 = 4, corr 0.05, quarter-five-spot) at
     # 512^2: 1024 leaves, 10 levels, interface systems up to 2g = 256
