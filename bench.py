@@ -248,6 +248,10 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
+    # kernels one timed step launched (read before the accuracy check and
+    # the refined step below change the solve's launch sequence)
+    launches = (mr.mrcm_query(solver.ctx, "KERNEL_LAUNCHES_BUILD")
+                + mr.mrcm_query(solver.ctx, "KERNEL_LAUNCHES_SOLVE"))
     cells = n * n
     value, total_ms = job_throughput(sum(step_ms), cells, args.steps, world, dev)
 
@@ -310,8 +314,6 @@ def run_ours(args):
         ref_ms.append(ev0.elapsed_time(ev1))
     mr.mrcm_set_refinement(solver.ctx, args.refine)
 
-    launches = (mr.mrcm_query(solver.ctx, "KERNEL_LAUNCHES_BUILD")
-                + mr.mrcm_query(solver.ctx, "KERNEL_LAUNCHES_SOLVE"))
     build_flops = mr.mrcm_query(solver.ctx, "BUILD_FLOPS")
     ph = {k: v / args.steps for k, v in phases.items()}          # ms per step
     pf = mr.mrcm_phase_flops(solver.ctx)                          # flops per step
