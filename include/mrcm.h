@@ -58,8 +58,9 @@ enum {
                                   leaf larger than 16x16 cells              */
     MRCM_ERR_BAD_K = -3,       /* a permeability is <= 0 or not finite      */
     MRCM_ERR_NOT_BUILT = -4,   /* mrcm_solve before mrcm_build_basis         */
-    MRCM_ERR_SINGULAR = -5,    /* zero / tiny pivot in a local or interface
-                                  factorisation                             */
+    MRCM_ERR_SINGULAR = -5,    /* zero / tiny pivot, or a pivot of the wrong
+                                  sign for the quasi-definite interface form,
+                                  in a local or interface factorisation     */
     MRCM_ERR_CUDA = -6,        /* a CUDA runtime call failed                 */
     MRCM_ERR_OOM = -7,         /* device allocation failed                   */
     MRCM_ERR_TIMEOUT = -8,     /* a bounded device wait gave up              */
@@ -257,9 +258,9 @@ int mrcm_use_graphs(mrcm_ctx* ctx, int on);
 
 /*
  * mrcm_check_reciprocal -- self-check of the reciprocal the interface and
- * leaf kernels use on their sequential pivot chains (Newton-Raphson from a
- * single-precision seed, within an ulp of 1/x); the paper has no
- * counterpart.  r_dev[i] = 1/x_dev[i] for i < n, both device arrays of n
+ * leaf kernels use on their sequential pivot chains (a single-precision seed
+ * refined by one third-order step of the Newton-Raphson family, within an
+ * ulp of 1/x); the paper has no counterpart.  r_dev[i] = 1/x_dev[i] for i < n, both device arrays of n
  * doubles owned by the caller, on cuda_stream (NULL: legacy default
  * stream); synchronises the stream.  Returns MRCM_OK, MRCM_ERR_INVALID_ARG
  * (null pointer, n < 0) or MRCM_ERR_CUDA.
