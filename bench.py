@@ -1,46 +1,71 @@
 #!/usr/bin/env python3
 """Benchmark: fine cells/s of a full Recursive MRCM solve (build + solve).
 
-Workload (default): the 1024 x 1024 quarter-five-spot problem -- unit square,
-log-normal K with sigma^2 = 4 and correlation length 0.05 (seeded FFT
-circulant embedding), no-flow boundary with zero-mean pressure, +1 / -1
-sources in opposite corner cells, 64 x 64 leaves of 16 x 16 cells, 4-cell
-interface segments, alpha = 1, 12 merge levels, FP64 throughout.
+Workloads (--workload):
+  square4096 (default): 4096 x 4096 cells on the unit square, log-normal K
+      with sigma^2 = 3 and correlation length 0.02 (seeded FFT circulant
+      embedding, seed 5000), no-flow boundary with zero-mean pressure,
+      +1 / -1 sources in opposite corner cells (quarter five-spot), 256 x 256
+      leaves of 16 x 16 cells, 4-cell interface segments, alpha = 1, 16
+      merge levels, FP64 throughout.
+  square1024: the 1024 x 1024 problem of the same kind with sigma^2 = 4,
+      correlation length 0.05, seed 2000 (64 x 64 leaves, 12 levels).
 
-One step = mrcm_build_basis + mrcm_solve on inputs resident in HBM; L2 is
-flushed (a 256 MiB write) between timed steps, outside the timed events.
-`e2e` repeats the step through the same C-ABI calls from pinned host
-buffers, host->device copies of K, q and the boundary values and the
-device->host copies of p, Fx, Fy inside the timed region.
+One step = mrcm_build_basis + mrcm_solve on inputs resident in HBM (larger
+than L2 at 4096^2; L2 is also flushed by a 256 MiB write between timed
+steps, outside the timed events).  `e2e` repeats the step through the same
+C-ABI calls from pinned host buffers, with the host->device copies of K, q
+and the boundary values and the device->host copies of p, Fx, Fy inside
+the timed region.
+
+The roofline denominators are measured in the same run by the library's
+pipe probes (mrcm_probe_peak: FP64 FMA, FP64 MMA, FP32 FMA).
 
 N > 1 (torchrun): every rank solves its own realisation (independent
 replicas, no collective on the data path); value = all ranks' cells / max
-time.  --impl reference times the FP64 CPU oracle on a bounded sample.
+time.  --impl reference times the FP64 CPU oracle on a bounded sample of
+the same workload on every host core.
 """
 import argparse
 import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "fine cells/s full RecMRCM solve at rel-L2 ≤1e-8 vs FP64 oracle; % roofline"
-# FP64 FMA pipe of GB300: 2 DFMA / clock / SM x 152 SMs x 2.07 GHz x 2 flops
-FP64_PEAK_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
+# nominal FP64 FMA pipe of GB300: 2 DFMA lane-ops / clock / SM x 152 SMs x
+# 2.07 GHz x 2 flops (context beside the measured probe)
+FP64_NOMINAL_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
 # rel-L2 bar of the FP64 form against the FP64 oracle (the metric's own
 # tolerance, 1e-8, is the mixed form's)
 FP64_FORM_TOL = 1e-10
-WORKLOAD = ("square1024-qfs: 1024x1024 cells, log-normal K sigma^2=4 corr 0.05 (seed 2000), "
-            "quarter-five-spot, no-flow, 64x64 leaves of 16x16, 4-cell segments, alpha=1, 12 levels")
-CPU_SAMPLE_N = 256
-# DRAM bytes (read + write) per launch of a kernel family at the 1024^2
-# workload, from one ncu capture of this bench (dram__bytes_read.sum +
+
+WORKLOADS = {
+    "square4096": dict(
+        n=4096, sigma2=3.0, corr=0.02, seed=5000,
+        desc=("square4096-qfs: 4096x4096 cells, log-normal K sigma^2=3 corr 0.02 (seed 5000), "
+              "quarter-five-spot, no-flow, 256x256 leaves of 16x16, 4-cell segments, alpha=1, 16 levels"),
+        golden="square4096_qfs_oracle.npz"),
+    "square1024": dict(
+        n=1024, sigma2=4.0, corr=0.05, seed=2000,
+        desc=("square1024-qfs: 1024x1024 cells, log-normal K sigma^2=4 corr 0.05 (seed 2000), "
+              "quarter-five-spot, no-flow, 64x64 leaves of 16x16, 4-cell segments, alpha=1, 12 levels"),
+        golden=None),
+}
+# The CPU sample: one window of CPU_WINDOW^2 cells per host core, with the
+# workload's cell size, field statistics and leaves (the oracle's global
+# sparse factorisation does not fit a whole 4096^2 field in a bench run).
+CPU_WINDOW = 256
+# DRAM bytes (read + write) per launch of a kernel family, per workload,
+# from one ncu capture of this bench (dram__bytes_read.sum +
 # dram__bytes_write.sum).  A family missing here reports traffic null.
 TRAFFIC_PER_LAUNCH = {
-    "gj_sweep": dict(bytes=1.216e6, source="ncu capture, mean over the 7 launches of one build"),
+    ("square1024", "gj_sweep"): dict(bytes=1.216e6, source="ncu capture, mean over the 7 launches of one build"),
 }
 
 
@@ -50,11 +75,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--size", type=int, default=1024)
+    ap.add_argument("--workload", default="square4096", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--refine", type=int, default=0,
                     help="iterative-refinement steps per solve in the timed steps (0: the paper's single "
                          "pass; its distance to the refined solution is checked in the same run)")
+    ap.add_argument("--probe-peaks", action="store_true",
+                    help="only measure the arithmetic pipes (FP64 FMA/MMA, FP32 FMA, TF32, BF16) and print them")
     return ap.parse_args()
 
 
@@ -77,69 +104,108 @@ def job_throughput(local_ms, cells_per_rank, steps, world, device="cpu"):
 
 
 # ---------------------------------------------------------------------------
-# CPU oracle timing (the cpu_baseline leg and the reference arm)
+# CPU oracle timing (the cpu_baseline leg and the reference arm): one fresh
+# interpreter per host core, each solving its own window of the workload
+# with the oracle O2 (global MRCM, plain FP64, one BLAS thread).
 ORACLE_SNIPPET = r"""
 import json, sys, time
 sys.path.insert(0, {root!r})
 import inputs
 from oracle.mrcm import solve_mrcm
-prob = inputs.darcy_problem({n}, {n}, sigma2=4.0, corr=0.05, seed=2000, bc="quarter_five_spot")
+n, N = {n}, {N}
 times = []
-for _ in range({reps}):
+for r in range({reps}):
+    prob = inputs.darcy_problem(n, n, Lx=n / N, sigma2={sigma2}, corr={corr}, seed={seed} + 100 * r,
+                                bc="quarter_five_spot")
     t = time.perf_counter()
     solve_mrcm(prob)
     times.append(time.perf_counter() - t)
-print(json.dumps(dict(times=times, cells={n} * {n})))
+print(json.dumps(dict(times=times, cells=n * n)))
 """
 
 
-def time_oracle(n, reps):
+def host_cores():
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except AttributeError:
+        return max(1, os.cpu_count() or 1)
+
+
+def time_oracle_parallel(wl, reps, procs):
+    """Runs `procs` oracle processes at once, each solving `reps` windows of
+    CPU_WINDOW^2 cells (seeds differ per process).  Returns (cells/s of all
+    processes together, per-process single-core cells/s, the slowest
+    process's solve seconds)."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = ORACLE_SNIPPET.format(root=ROOT, n=n, reps=reps)
-    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
-                         timeout=1800)
-    if out.returncode:
-        raise RuntimeError(out.stderr[-2000:])
-    return json.loads(out.stdout.strip().splitlines()[-1])
+    ps = []
+    t0 = time.perf_counter()
+    for k in range(procs):
+        code = ORACLE_SNIPPET.format(root=ROOT, n=CPU_WINDOW, N=wl["n"], reps=reps, sigma2=wl["sigma2"],
+                                     corr=wl["corr"], seed=wl["seed"] + 1 + k)
+        ps.append(subprocess.Popen([sys.executable, "-c", code], env=env, stdout=subprocess.PIPE,
+                                   stderr=subprocess.PIPE, text=True))
+    results = []
+    for p in ps:
+        out, err = p.communicate(timeout=1800)
+        if p.returncode:
+            raise RuntimeError(err[-2000:])
+        results.append(json.loads(out.strip().splitlines()[-1]))
+    wall = time.perf_counter() - t0
+    cells = sum(r["cells"] * len(r["times"]) for r in results)
+    single = [r["cells"] * len(r["times"]) / sum(r["times"]) for r in results]
+    # the processes run concurrently: the slowest one's solve time (field
+    # generation and interpreter start-up excluded) is the sample's time
+    slowest = max(sum(r["times"]) for r in results)
+    return cells / slowest, single, slowest
 
 
-def oracle_sample_desc(n):
-    return (f"oracle O2 (global MRCM, numpy/scipy FP64, single thread) on the {n}x{n} problem of "
-            f"the same recipe (sigma^2=4, corr 0.05, seed 2000, quarter-five-spot, 16x16 leaves)")
+def oracle_sample_desc(wl, procs, reps):
+    return (f"oracle O2 (global MRCM: leaf solves, sparse LU of the interface system, final solves; "
+            f"numpy/scipy FP64, one BLAS thread per process) on {procs} concurrent processes, one per host "
+            f"core, each solving {reps} {CPU_WINDOW}x{CPU_WINDOW}-cell window(s) of the workload "
+            f"(cell size 1/{wl['n']}, sigma^2={wl['sigma2']}, corr {wl['corr']}, quarter-five-spot, "
+            f"16x16 leaves, 4-cell segments); value = all cells / the slowest process's solve time")
 
 
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    n = CPU_SAMPLE_N
-    res = time_oracle(n, args.warmup + args.steps)
-    times = res["times"][args.warmup:]
-    value = res["cells"] * len(times) / sum(times)
+    wl = WORKLOADS[args.workload]
+    procs = host_cores()
+    times = []
+    value_steps = []
+    for it in range(args.warmup + args.steps):
+        v, _, wall = time_oracle_parallel(wl, 1, procs)
+        if it >= args.warmup:
+            times.append(wall)
+            value_steps.append(v)
+    cells = CPU_WINDOW * CPU_WINDOW * procs
+    value = cells * len(times) / sum(times)
     line = dict(metric=METRIC, value=value, unit="cells/s", n_gpus=args.gpus, steps=args.steps,
                 warmup=args.warmup, ms_per_step=1e3 * sum(times) / len(times),
                 higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
                 data="synthetic", impl="reference",
-                config=dict(workload=WORKLOAD, sample=f"{n}x{n}"),
-                cpu_baseline=dict(value=value, unit="cells/s", cores=1, kind="oracle",
-                                  sample=oracle_sample_desc(n)),
+                config=dict(workload=wl["desc"], sample=f"{procs} x {CPU_WINDOW}x{CPU_WINDOW} windows per step"),
+                cpu_baseline=dict(value=value, unit="cells/s", cores=procs, kind="oracle",
+                                  sample=oracle_sample_desc(wl, procs, 1)),
                 e2e=dict(value=value, unit="cells/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
 
 
 # ---------------------------------------------------------------------------
 class ClockSampler:
-    """nvidia-smi clock / throttle samples during the timed region."""
+    """nvidia-smi clock / throttle samples during the timed region (written
+    to a temporary file, removed after reading)."""
 
     def __init__(self, uuid):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
         q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.f = open(self.path, "w")
+            fd, self.path = tempfile.mkstemp(prefix="mrcm_clocks_", suffix=".csv")
+            self.f = os.fdopen(fd, "w")
             cmd = ["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "100"]
             if uuid:
                 cmd.insert(1, f"--id={uuid}")
@@ -156,7 +222,10 @@ class ClockSampler:
         self.f.close()
         sms, maxs, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for row in open(self.path):
+        with open(self.path) as fh:
+            rows = fh.readlines()
+        os.unlink(self.path)
+        for row in rows:
             parts = [x.strip() for x in row.split(",")]
             if len(parts) < 8:
                 continue
@@ -185,6 +254,42 @@ def mass_balance(solver, q):
     return float((div - q).abs().max()) / scale
 
 
+def golden_check(wl, outs):
+    """rel-L2 over the oracle's stored samples of the workload (written by
+    tests/golden/make_square4096.py from the oracle alone), or None."""
+    import numpy as np
+    if not wl.get("golden"):
+        return None
+    path = os.path.join(ROOT, "tests", "golden", wl["golden"])
+    if not os.path.exists(path):
+        return None
+    g = np.load(path)
+    res = {}
+    for key, arr in outs.items():
+        idx = g[f"{key}_idx"]
+        ref = g[f"{key}_val"]
+        val = arr.reshape(-1)[idx]
+        res[key] = float(np.linalg.norm(val - ref) / np.linalg.norm(ref))
+    return dict(rel_l2=res, samples=int(sum(len(g[f"{k}_idx"]) for k in outs)),
+                source=f"tests/golden/{wl['golden']}")
+
+
+def probe_peaks(seconds=0.3):
+    import paper_2009_07965_gb300 as mr
+    return {k: mr.mrcm_probe_peak(k, seconds) for k in ("DFMA", "DMMA", "FFMA", "TF32", "BF16")}
+
+
+def run_probe_only():
+    import torch
+    from paper_2009_07965_gb300 import build as build_mod
+    build_mod.build()
+    torch.cuda.init()
+    peaks = probe_peaks(1.0)
+    props = torch.cuda.get_device_properties(0)
+    print(json.dumps(dict(device=props.name, sms=props.multi_processor_count, tflops=peaks,
+                          fp64_nominal_tflops=FP64_NOMINAL_TFLOPS)), flush=True)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -202,9 +307,11 @@ def run_ours(args):
         build_mod.build()
     if world > 1:
         dist.barrier()
-    n = args.size
-    prob = inputs.darcy_problem(n, n, sigma2=4.0, corr=0.05, seed=2000 + rank,
+    wl = WORKLOADS[args.workload]
+    n = wl["n"]
+    prob = inputs.darcy_problem(n, n, sigma2=wl["sigma2"], corr=wl["corr"], seed=wl["seed"] + rank,
                                 bc="quarter_five_spot", alpha=1.0)
+    peaks = probe_peaks()
     stream = torch.cuda.Stream(dev)
     K = torch.from_numpy(prob.K).to(dev)
     q = torch.from_numpy(prob.q).to(dev)
@@ -252,6 +359,7 @@ def run_ours(args):
     # the refined step below change the solve's launch sequence)
     launches = (mr.mrcm_query(solver.ctx, "KERNEL_LAUNCHES_BUILD")
                 + mr.mrcm_query(solver.ctx, "KERNEL_LAUNCHES_SOLVE"))
+    groups = mr.mrcm_group_times(solver.ctx)
     cells = n * n
     value, total_ms = job_throughput(sum(step_ms), cells, args.steps, world, dev)
 
@@ -291,9 +399,10 @@ def run_ours(args):
     balance = mass_balance(solver, q)
 
     # ---- accuracy of the timed configuration (outside the timed regions):
-    # rel-L2 distance to the solve refined to the rounding level, which the
-    # parity tests pin to the FP64 oracle
+    # rel-L2 distance to the solve refined to the rounding level, and to the
+    # oracle's stored samples of this workload (rank 0's realisation)
     timed = [x.cpu().numpy().copy() for x in (solver.p, solver.Fx, solver.Fy)]
+    vs_oracle = golden_check(wl, dict(zip(("p", "Fx", "Fy"), timed))) if rank == 0 else None
     mr.mrcm_set_refinement(solver.ctx, 3)
     solver.solve(q, bcv)
     refined = [x.cpu().numpy().copy() for x in (solver.p, solver.Fx, solver.Fy)]
@@ -314,7 +423,6 @@ def run_ours(args):
         ref_ms.append(ev0.elapsed_time(ev1))
     mr.mrcm_set_refinement(solver.ctx, args.refine)
 
-    build_flops = mr.mrcm_query(solver.ctx, "BUILD_FLOPS")
     ph = {k: v / args.steps for k, v in phases.items()}          # ms per step
     pf = mr.mrcm_phase_flops(solver.ctx)                          # flops per step
     table = {k: dict(ms=ph[k], gflop=pf[k] / 1e9,
@@ -323,39 +431,70 @@ def run_ours(args):
     # the dominant kernel family: the phase with the largest share of the step
     dom = max(mr.PHASES, key=lambda k: ph[k])
     achieved = pf[dom] / (ph[dom] / 1e3) / 1e12
+    peak = peaks["DFMA"]
+    model = {}
+    if dom == "gj_sweep":
+        mflops = mr.mrcm_query(solver.ctx, "MODEL_SWEEP_FLOPS")
+        model = dict(achieved_model=mflops / (ph[dom] / 1e3) / 1e12,
+                     model="(2/3) N^3 per blocked interface system (LU count)")
+        model["frac_model"] = model["achieved_model"] / peak
+    build_ms = sum(ph[k] for k in ("coef", "leaf_build", "merge_small", "gj_sweep", "merge_form", "merge_x",
+                                   "merge_r"))
+    model_build = mr.mrcm_query(solver.ctx, "MODEL_BUILD_FLOPS")
+    basis = dict(ms=build_ms, model_gflop=model_build / 1e9,
+                 model_tflops=model_build / (build_ms / 1e3) / 1e12,
+                 frac_model=model_build / (build_ms / 1e3) / 1e12 / peak,
+                 model="banded-Cholesky leaves + LU merges (MRCM_Q_MODEL_BUILD_FLOPS)")
+    # per tree height of the build: the launch groups in order
+    heights = []
+    for name, ms in groups:
+        if name in ("merge_small", "gj_sweep"):
+            heights.append(ms)                  # a new tree height starts
+        elif name in ("merge_x", "merge_r") and heights:
+            heights[-1] += ms
+    heights = [round(h, 4) for h in heights]
     if rank != 0:
         return
+    traffic = TRAFFIC_PER_LAUNCH.get((args.workload, dom))
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
+        procs = host_cores()
         try:
-            res = time_oracle(CPU_SAMPLE_N, 2)
-            cpu = dict(value=res["cells"] * 2 / sum(res["times"]), unit="cells/s", cores=1, kind="oracle",
-                       sample=oracle_sample_desc(CPU_SAMPLE_N))
+            v, single, wall = time_oracle_parallel(wl, 1, procs)
+            cpu = dict(value=v, unit="cells/s", cores=procs, kind="oracle",
+                       single_core_value=sum(single) / len(single), wall_s=wall,
+                       sample=oracle_sample_desc(wl, procs, 1))
         except Exception as e:  # report, do not hide
-            cpu = dict(value=None, unit="cells/s", cores=1, kind="oracle", error=str(e)[-300:])
+            cpu = dict(value=None, unit="cells/s", cores=procs, kind="oracle", error=str(e)[-300:])
     line = dict(
         metric=METRIC, value=value, unit="cells/s", n_gpus=world, steps=args.steps,
         warmup=args.warmup, ms_per_step=total_ms / args.steps, higher_is_better=True,
         scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
-        config=dict(workload=WORKLOAD if n == 1024 else f"square{n}-qfs", cells=cells,
+        config=dict(workload=wl["desc"], cells=cells,
                     leaves=mr.mrcm_query(solver.ctx, "LEAVES"),
                     levels=mr.mrcm_query(solver.ctx, "LEVELS"),
-                    l2="flushed between timed steps (256 MiB write outside the events)",
+                    l2="inputs larger than L2; L2 also flushed between timed steps (256 MiB write outside the events)",
                     parallelism=f"replicas x{world}"),
-        roofline=dict(bound="alu", achieved=achieved, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
-                      frac=achieved / FP64_PEAK_TFLOPS,
-                      traffic=TRAFFIC_PER_LAUNCH[dom]["bytes"] if n == 1024 and dom in TRAFFIC_PER_LAUNCH else None,
+        roofline=dict(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s",
+                      frac=achieved / peak,
+                      traffic=traffic["bytes"] if traffic else None,
                       traffic_unit="bytes per launch",
-                      traffic_source=TRAFFIC_PER_LAUNCH[dom]["source"] if n == 1024 and dom in TRAFFIC_PER_LAUNCH else None,
-                      kernel=mr.PHASE_KERNELS[dom],
-                      phase=dom, share=ph[dom] / (total_ms / args.steps),
-                      peak_source="FP64 FMA pipe: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz"),
+                      traffic_source=traffic["source"] if traffic else None,
+                      kernel=mr.PHASE_KERNELS[dom], phase=dom, share=ph[dom] / (total_ms / args.steps),
+                      flop_count="algorithmic flops of the implemented algorithm (mrcm_phase_flops)",
+                      peak_source=("measured in this run: FP64 FMA probe (mrcm_probe_peak DFMA), "
+                                   "of measured"),
+                      peak_nominal=FP64_NOMINAL_TFLOPS, **model),
+        peaks_measured_tflops=peaks,
+        basis_build=basis,
+        merge_ms_per_height=heights,
         phases=table,
-        model_gflop_per_step=sum(pf.values()) / 1e9,
+        gflop_per_step=sum(pf.values()) / 1e9,
         e2e=dict(value=e2e_value, unit="cells/s", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
         gpu_launches=launches * args.steps,
         clocks=clocks,
         check=dict(mass_balance=balance, refine_steps=args.refine, rel_l2_vs_refined=rel,
+                   vs_oracle_samples=vs_oracle,
                    tolerance=FP64_FORM_TOL, within_tolerance=bool(max(rel.values()) <= FP64_FORM_TOL),
                    metric_tolerance=1e-8),
         refined_step=dict(refine_steps=1, ms_per_step=sum(ref_ms) / len(ref_ms),
@@ -370,7 +509,9 @@ def run_ours(args):
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.probe_peaks:
+        run_probe_only()
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -135,8 +135,10 @@ int mrcm_build_basis(mrcm_ctx* ctx);
  *      of all-Neumann problems and the face fluxes from the cell pressures
  *      and the interface unknowns.
  *
- *   q_dev      n[0]*n[1] integrated sources (all-Neumann problems need
- *              sum(q) + boundary inflow = 0 up to rounding)
+ *   q_dev      n[0]*n[1] integrated sources.  All-Neumann problems need
+ *              compatible data: |sum q - sum |e| g_N| <= 1e-14 (sum |q| +
+ *              sum |e| |g_N|), both sums evaluated in double-double on the
+ *              device; otherwise the call returns MRCM_ERR_INVALID_ARG
  *   bc_val_dev 2*(n[0]+n[1]) boundary values (layout in the header comment)
  *   p_dev      out: n[0]*n[1] cell pressures
  *   Fx_dev     out: (n[0]+1)*n[1] x-face fluxes; skeleton faces hold the
@@ -148,7 +150,8 @@ int mrcm_build_basis(mrcm_ctx* ctx);
  *              each face-shaped like Fx / Fy; side a is the lower-coordinate
  *              leaf, side b the upper one, both in the +axis direction; off
  *              the skeleton both equal the face flux.
- * Errors: MRCM_ERR_NOT_BUILT, MRCM_ERR_INVALID_ARG, MRCM_ERR_CUDA.
+ * Errors: MRCM_ERR_NOT_BUILT, MRCM_ERR_INVALID_ARG, MRCM_ERR_TIMEOUT,
+ * MRCM_ERR_CUDA.
  */
 int mrcm_solve(mrcm_ctx* ctx, const double* q_dev, const double* bc_val_dev,
                double* p_dev, double* Fx_dev, double* Fy_dev, double* Fz_dev,
@@ -167,8 +170,15 @@ enum {
     MRCM_Q_LEAF_FLOPS = 8,    /* part of BUILD_FLOPS in the leaf kernel      */
     MRCM_Q_KERNEL_LAUNCHES_BUILD = 9, /* kernels launched by one build call  */
     MRCM_Q_KERNEL_LAUNCHES_SOLVE = 10, /* kernels launched by one solve call */
-    MRCM_Q_GRAPH_REPLAYS = 11 /* build and solve calls so far that replayed a
+    MRCM_Q_GRAPH_REPLAYS = 11, /* build and solve calls so far that replayed a
                                  captured CUDA graph (see mrcm_use_graphs)   */
+    /* reference flop model of a direct method, independent of this
+       library's algorithms: banded Cholesky leaves n b^2 + 2 n b m +
+       m (m + 1) n + 4 n b (n cells, bandwidth b, m segments), LU-based
+       merges (2/3) N^3 + 2 N^2 (m + 1) + 2 m g (m + 1) (N = 2g) */
+    MRCM_Q_MODEL_BUILD_FLOPS = 12, /* the whole build under that model        */
+    MRCM_Q_MODEL_SWEEP_FLOPS = 13  /* (2/3) N^3 of the merges that run in the
+                                     blocked sweep (MRCM_PHASE_GJ_SWEEP)     */
 };
 
 /* mrcm_query -- integer facts about a context.  value: host out pointer. */
@@ -176,7 +186,8 @@ int mrcm_query(const mrcm_ctx* ctx, int what, long long* value);
 
 /*
  * mrcm_plan_query -- the same integer facts as mrcm_query (keys
- * MRCM_Q_LEAVES .. MRCM_Q_LEAF_FLOPS except WORKSPACE_BYTES, which is 0),
+ * MRCM_Q_LEAVES .. MRCM_Q_LEAF_FLOPS and the two MODEL keys; WORKSPACE_BYTES
+ * is 0),
  * computed from the decomposition alone on the host: no device, no CUDA
  * call.  Arguments as in mrcm_setup; value: host out pointer.
  */
@@ -229,6 +240,20 @@ enum {
  * unscaled); returns the number of evaluations (>= 0) or an error code.
  */
 int mrcm_set_refinement(mrcm_ctx* ctx, int steps, int check);
+
+/*
+ * mrcm_set_wait_limit -- polls after which a bounded wait between the CTAs
+ * of one cooperative launch (the blocked interface sweeps and the solve's
+ * tree sweeps) gives up; the paper has no counterpart.  polls <= 0 restores
+ * the default (about a second of polling).  A wait that gives up makes the
+ * call return MRCM_ERR_TIMEOUT; every CTA then leaves the launch at its
+ * next wait, nothing is left running, and the context stays usable (a later
+ * call with a sufficient limit recomputes everything it needs).  A very
+ * small limit is how failure handling is exercised without a fault.
+ * Synchronises the context's stream and drops its captured graphs when the
+ * limit changes.
+ */
+int mrcm_set_wait_limit(mrcm_ctx* ctx, long long polls);
 int mrcm_residual_history(mrcm_ctx* ctx, double* out, int cap);
 
 /*
@@ -341,19 +366,41 @@ int mrcm_node_operator(mrcm_ctx* ctx, int node, double* R_host, double* rbar_hos
  * Workspace: the LU factors, pivots and a status word live in one
  * file-scope device array sized for 2g = MRCM_NOALLOC_MAX_G2 (about 513 KB),
  * which every GPU that loads the library holds until the process exits.
- * The first call on a device looks up that array's device address (once
- * per device, with that device current); make that first call before any
- * stream capture.  Every call reuses the same array and clears the status
- * word itself, so calls that overlap on the GPU (different streams or
- * devices sharing a context) race: serialise them.  The call synchronises
- * its stream once to read the status.  Larger systems return
- * MRCM_ERR_INVALID_ARG.  Errors: MRCM_ERR_INVALID_ARG, MRCM_ERR_SINGULAR,
- * MRCM_ERR_CUDA.
+ * Every call looks up that array's device address for the current device
+ * and context (a host-side query that allocates nothing).  Every call
+ * reuses the same array and clears the status word itself, so calls that
+ * overlap on the GPU (different streams or devices sharing a context) race:
+ * serialise them.  The call synchronises its stream once to read the
+ * status.  Larger systems return MRCM_ERR_INVALID_ARG.  The interface
+ * matrix is factored by LU with partial pivoting (not by the build's
+ * quasi-definite inversion, which gives the same maps); MRCM_ERR_SINGULAR
+ * here means a pivot of magnitude <= 1e-14 max|M| (no sign test).
+ * Errors: MRCM_ERR_INVALID_ARG, MRCM_ERR_SINGULAR, MRCM_ERR_CUDA.
  */
 #define MRCM_NOALLOC_MAX_G2 256
 int mrcm_merge_pair_noalloc(const double* R1_dev, int m1, const double* R2_dev, int m2,
                             const int* map_dev, int g, const double* D_dev,
                             double* R_dev, double* X_dev, void* cuda_stream);
+
+/*
+ * mrcm_probe_peak -- measured throughput ceiling of one arithmetic pipe of
+ * the current device, the denominator of the kernels' roofline figures; the
+ * paper has no counterpart.  Every scheduler of every SM runs independent
+ * chains of one instruction kind for about `seconds` (0 < seconds <= 10) in
+ * three timed runs on cuda_stream (NULL: legacy default stream); *tflops
+ * (host) receives the fastest run's rate in TFLOP/s (an FMA counts 2
+ * flops, an m x n x k MMA 2mnk).  Synchronises the stream.  Errors:
+ * MRCM_ERR_INVALID_ARG (unknown kind, bad seconds, NULL tflops),
+ * MRCM_ERR_CUDA.
+ */
+enum {
+    MRCM_PROBE_DFMA = 0,   /* FP64 fused multiply-add                        */
+    MRCM_PROBE_DMMA = 1,   /* FP64 mma.sync m8n8k4                           */
+    MRCM_PROBE_FFMA = 2,   /* FP32 fused multiply-add                        */
+    MRCM_PROBE_TF32 = 3,   /* mma.sync m16n8k8, TF32 inputs, FP32 accumulate */
+    MRCM_PROBE_BF16 = 4    /* mma.sync m16n8k16, BF16 inputs, FP32 accumulate */
+};
+int mrcm_probe_peak(int kind, double seconds, double* tflops, void* cuda_stream);
 
 /* mrcm_destroy -- free all device and host resources (NULL is a no-op). */
 void mrcm_destroy(mrcm_ctx* ctx);

@@ -18,7 +18,7 @@ ERRORS = {0: "MRCM_OK", -1: "MRCM_ERR_INVALID_ARG", -2: "MRCM_ERR_SHAPE", -3: "M
           -7: "MRCM_ERR_OOM", -8: "MRCM_ERR_TIMEOUT", -9: "MRCM_ERR_UNSUPPORTED"}
 Q = dict(LEAVES=0, SEGMENTS=1, LEVELS=2, NODES=3, WORKSPACE_BYTES=4, MAX_GAMMA=5,
          BUILD_FLOPS=6, SOLVE_FLOPS=7, LEAF_FLOPS=8, KERNEL_LAUNCHES_BUILD=9,
-         KERNEL_LAUNCHES_SOLVE=10, GRAPH_REPLAYS=11)
+         KERNEL_LAUNCHES_SOLVE=10, GRAPH_REPLAYS=11, MODEL_BUILD_FLOPS=12, MODEL_SWEEP_FLOPS=13)
 
 # every symbol include/mrcm.h declares
 EXPORTS = ["mrcm_setup", "mrcm_plan_query", "mrcm_set_permeability", "mrcm_build_basis", "mrcm_solve", "mrcm_query",
@@ -26,7 +26,8 @@ EXPORTS = ["mrcm_setup", "mrcm_plan_query", "mrcm_set_permeability", "mrcm_build
            "mrcm_destroy", "mrcm_error_string", "mrcm_enable_timing", "mrcm_phase_times", "mrcm_use_graphs",
            "mrcm_last_cuda_error",
            "mrcm_merge_pair_noalloc", "mrcm_set_refinement", "mrcm_residual_history", "mrcm_phase_flops",
-           "mrcm_group_times", "mrcm_check_reciprocal"]
+           "mrcm_group_times", "mrcm_check_reciprocal", "mrcm_set_wait_limit",
+           "mrcm_probe_peak"]
 PHASES = ["coef", "leaf_build", "merge_small", "gj_sweep", "merge_form", "merge_x", "merge_r",
           "leaf_particular", "tree_up", "tree_down", "leaf_pressure", "residual", "finish"]
 # kernel family behind each phase (for reports)
@@ -102,6 +103,10 @@ def _lib():
         lib.mrcm_check_reciprocal.restype = I
         lib.mrcm_set_refinement.argtypes = [P, I, I]
         lib.mrcm_set_refinement.restype = I
+        lib.mrcm_probe_peak.argtypes = [I, D, ctypes.POINTER(ctypes.c_double), P]
+        lib.mrcm_probe_peak.restype = I
+        lib.mrcm_set_wait_limit.argtypes = [P, ctypes.c_longlong]
+        lib.mrcm_set_wait_limit.restype = I
         lib.mrcm_residual_history.argtypes = [P, ctypes.POINTER(ctypes.c_double), I]
         lib.mrcm_residual_history.restype = I
         lib.mrcm_destroy.argtypes = [P]
@@ -247,6 +252,21 @@ def mrcm_check_reciprocal(x, out=None):
 
 def mrcm_set_refinement(ctx, steps, check=False):
     _check(_lib().mrcm_set_refinement(ctx, int(steps), 1 if check else 0), "mrcm_set_refinement")
+
+
+PROBES = dict(DFMA=0, DMMA=1, FFMA=2, TF32=3, BF16=4)
+
+
+def mrcm_probe_peak(kind, seconds=0.3, stream=None):
+    """Measured TFLOP/s of one arithmetic pipe (kind: a PROBES key)."""
+    out = ctypes.c_double()
+    _check(_lib().mrcm_probe_peak(PROBES[kind] if isinstance(kind, str) else int(kind), float(seconds),
+                                  ctypes.byref(out), stream), "mrcm_probe_peak")
+    return out.value
+
+
+def mrcm_set_wait_limit(ctx, polls):
+    _check(_lib().mrcm_set_wait_limit(ctx, int(polls)), "mrcm_set_wait_limit")
 
 
 def mrcm_residual_history(ctx, cap=17):

@@ -490,23 +490,22 @@ __device__ void gj_first_cu_item(const DevView& v, const MergeDesc& D, int slot,
 }
 
 // Bounded wait of one CTA for a flag that another CTA of the same
-// cooperative launch raises (about a second); false on timeout
-// (kStatusTimeout set).  Thread 0 polls with acquire loads, so what the
+// cooperative launch raises (at most `limit` polls, about a second by
+// default: DevView::spin_limit); false on timeout (kStatusTimeout set).  Thread 0 polls with acquire loads, so what the
 // raising CTA wrote before its release (fence + atomic) is visible to the
 // whole CTA after the barrier that ends the wait.
-constexpr long long kFlagSpins = 5000000;
 __device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
     unsigned int v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ bool wait_flag(const unsigned int* flag, unsigned int value, int* status) {
+__device__ bool wait_flag(const unsigned int* flag, unsigned int value, int* status, long long limit) {
     __shared__ int s_ok;
     if (threadIdx.x == 0) {
         int ok = 1;
         long long spins = 0;
         while (ld_acquire_gpu(flag) < value) {
-            if (++spins > kFlagSpins) {
+            if (++spins > limit) {
                 ok = 0;
                 atomicOr(status, kStatusTimeout);
                 break;
@@ -628,7 +627,7 @@ __device__ bool gj_u_item(const DevView& v, const MergeDesc& D, int slot, int x0
     const int xl = o / kGJ, rr = o % kGJ;
     // the c are usually in before P: wait for them first and stage the
     // first run while P is awaited
-    if (!wait_flag(gj_cready(sc, nmax), (unsigned int)((step + 1) * tiles), v.status)) return false;
+    if (!wait_flag(gj_cready(sc, nmax), (unsigned int)((step + 1) * tiles), v.status, v.spin_limit)) return false;
     auto stage_c = [&](int xs) {
         for (int idx = tid; idx < kUChunk * kGJ; idx += 256) {
             const int yl = idx / kGJ, cc = idx % kGJ, y = xs + yl;
@@ -637,7 +636,7 @@ __device__ bool gj_u_item(const DevView& v, const MergeDesc& D, int slot, int x0
         }
     };
     stage_c(x0);
-    if (!wait_flag(gj_flag(sc, nmax), (unsigned int)(step + 1), v.status)) return false;
+    if (!wait_flag(gj_flag(sc, nmax), (unsigned int)(step + 1), v.status, v.spin_limit)) return false;
     for (int idx = tid; idx < kGJ * kGJ; idx += 256) S.Ps[idx / kGJ][idx % kGJ] = __ldcg(Pn + idx);
     for (int xs = x0; xs < x0 + len; xs += kUChunk) {
         if (xs != x0) stage_c(xs);
@@ -706,11 +705,10 @@ __device__ bool gj_next_diag_item(const DevView& v, const MergeDesc& D, int slot
 // Grid-wide barrier of a cooperative launch: a monotonic arrival counter
 // (reset before the launch); round n ends when it reaches (n + 1) * grid.
 // Data written by other CTAs before a barrier is read after it with L2-only
-// loads (__ldcg).  Every wait is bounded (about a second); a CTA that gives
-// up sets kStatusTimeout and the caller returns.
-constexpr long long kBarrierSpins = 5000000;
+// loads (__ldcg).  Every wait is bounded (`limit` polls, about a second by
+// default); a CTA that gives up sets kStatusTimeout and the caller returns.
 
-__device__ bool grid_barrier(unsigned int* counter, unsigned int& round, int* status) {
+__device__ bool grid_barrier(unsigned int* counter, unsigned int& round, int* status, long long limit) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -720,7 +718,7 @@ __device__ bool grid_barrier(unsigned int* counter, unsigned int& round, int* st
         atomicAdd(counter, 1u);
         long long spins = 0;
         while (ld_acquire_gpu(counter) < target) {
-            if (++spins > kBarrierSpins) {
+            if (++spins > limit) {
                 ok = 0;
                 atomicOr(status, kStatusTimeout);
                 break;
@@ -851,7 +849,7 @@ __global__ void __launch_bounds__(256) gj_sweep_kernel(DevView v, int first, int
             form_item(v, D, e0, min(e0 + run, nT), scl, red);
         }
     }
-    if (!grid_barrier(counter, round, v.status)) return;
+    if (!grid_barrier(counter, round, v.status, v.spin_limit)) return;
     for (int q = blockIdx.x; q < count; q += gridDim.x) {
         const MergeDesc D = v.merges[first + q];
         const int N = 2 * D.g, nb = min(kGJ, N);
@@ -871,14 +869,14 @@ __global__ void __launch_bounds__(256) gj_sweep_kernel(DevView v, int first, int
         }
         __syncthreads();
     }
-    if (!grid_barrier(counter, round, v.status)) return;
+    if (!grid_barrier(counter, round, v.status, v.spin_limit)) return;
     for (int item = blockIdx.x; item < count * tiles; item += gridDim.x) {
         const int q = item / tiles, x0 = (item % tiles) * kGJTile;
         const MergeDesc D = v.merges[first + q];
         if (x0 >= 2 * D.g) continue;                         // uniform per CTA
         gj_first_cu_item(v, D, q, x0, scratch, nmax, S);
     }
-    if (!grid_barrier(counter, round, v.status)) return;
+    if (!grid_barrier(counter, round, v.status, v.spin_limit)) return;
     for (int step = 0; step < nsteps; ++step) {
         const int k0 = step * kGJ;
         const int tk = (k0 + kGJ) / kGJTile;                  // tile index of the next block
@@ -915,7 +913,7 @@ __global__ void __launch_bounds__(256) gj_sweep_kernel(DevView v, int first, int
             if (k0 + kGJ >= 2 * D.g || x0 >= 2 * D.g) continue;       // no next block, or past the end
             if (!gj_u_item(v, D, q, x0, min(ulen, 2 * D.g - x0), step, scratch, nmax, S)) return;
         }
-        if (!grid_barrier(counter, round, v.status)) return;
+        if (!grid_barrier(counter, round, v.status, v.spin_limit)) return;
     }
     // mirror the lower triangle (strictly lower entries of the lower tiles)
     for (int item = blockIdx.x; item < count * nlower; item += gridDim.x) {
@@ -932,7 +930,7 @@ __global__ void __launch_bounds__(256) gj_sweep_kernel(DevView v, int first, int
         }
     }
     // T^-1 -> W of every node
-    if (!grid_barrier(counter, round, v.status)) return;
+    if (!grid_barrier(counter, round, v.status, v.spin_limit)) return;
     {
         const long long per = (long long)(nmax / 2) * (nmax / 2), run = level_run(per, count);
         const long long runs = (per + run - 1) / run;
@@ -1146,7 +1144,7 @@ __global__ void __launch_bounds__(256) tree_up_kernel(DevView v, TreeLevels L, u
             v.rgam[2LL * D.gamma_off + k] = k < N.g ? __ldcg(v.rbar + D.r1_off + N.gpos1[k])
                                                     : __ldcg(v.rbar + D.r2_off + N.gpos2[k - N.g]);
         }
-        if (!grid_barrier(counter, round, v.status)) return;
+        if (!grid_barrier(counter, round, v.status, v.spin_limit)) return;
         if (mmax == 0) continue;                            // (the root) uniform
         const int lanes = tree_up_lanes(g2max);
         const unsigned int gmask = (lanes == 32 ? 0xffffffffu : ((1u << lanes) - 1u) << (lane & ~(lanes - 1)));
@@ -1189,7 +1187,7 @@ __global__ void __launch_bounds__(256) tree_up_kernel(DevView v, TreeLevels L, u
                 v.rbar[D.r_off + i] = acc + ro;
             }
         }
-        if (h + 1 < L.height && !grid_barrier(counter, round, v.status)) return;
+        if (h + 1 < L.height && !grid_barrier(counter, round, v.status, v.spin_limit)) return;
     }
 }
 
@@ -1269,7 +1267,7 @@ __global__ void __launch_bounds__(256) tree_down_kernel(DevView v, TreeLevels L,
             }
         }
         if (nkc > 1) {
-            if (!grid_barrier(counter, round, v.status)) return;
+            if (!grid_barrier(counter, round, v.status, v.spin_limit)) return;
             // G lanes per row add the chunk partials, then a shuffle tree
             const int G = nkc < 32 ? nkc : 32;
             const int lane = tid & 31;
@@ -1291,7 +1289,7 @@ __global__ void __launch_bounds__(256) tree_down_kernel(DevView v, TreeLevels L,
                 }
             }
         }
-        if (h > 0 && !grid_barrier(counter, round, v.status)) return;
+        if (h > 0 && !grid_barrier(counter, round, v.status, v.spin_limit)) return;
     }
 }
 

@@ -10,11 +10,14 @@
 // file-scope device array of fixed size, which each GPU that loads the
 // library holds until the process exits.
 //
-// The arithmetic is that of the merge step of the build (one CTA, partial
-// pivoting): M = [[R1_gg + D, -D], [-D, R2_gg + D]], X = -M^-1 C,
-// R = blockdiag(R1_oo, R2_oo) + blockdiag(R1_og, R2_og) X.
-#include <mutex>
-
+// It gives the merged map of one merge step of the build, but by its own
+// route: one CTA factors the interface matrix by LU with partial pivoting
+// (the build inverts the quasi-definite form instead), then
+//     M = [[R1_gg + D, -D], [-D, R2_gg + D]],  X = -M^-1 C,
+//     R = blockdiag(R1_oo, R2_oo) + blockdiag(R1_og, R2_og) X.
+// Its singularity test looks at pivot magnitudes only (|pivot| <= 1e-14
+// max |M|); the build's pivot-sign test of the quasi-definite form has no
+// counterpart in a partial-pivot LU.
 #include "mrcm_internal.h"
 #include "../../include/mrcm.h"
 
@@ -23,7 +26,6 @@ namespace {
 
 constexpr int kNoAllocMaxG2 = MRCM_NOALLOC_MAX_G2;
 constexpr int kNoAllocThreads = 256;
-constexpr int kMaxDevices = 64;
 
 // LU factors (row-major), pivot rows and one status word.
 struct NoAllocScratch {
@@ -174,9 +176,6 @@ merge_pair_noalloc_kernel(NoAllocScratch* S, const double* __restrict__ R1, int 
     }
 }
 
-std::mutex g_addr_mutex;
-NoAllocScratch* g_addr[kMaxDevices] = {};
-
 }  // namespace
 }  // namespace mrcm
 
@@ -188,29 +187,27 @@ extern "C" int mrcm_merge_pair_noalloc(const double* R1_dev, int m1, const doubl
     if (!R1_dev || !R2_dev || !map_dev || !D_dev || !R_dev || !X_dev) return MRCM_ERR_INVALID_ARG;
     if (g < 1 || 2 * g > kNoAllocMaxG2) return MRCM_ERR_INVALID_ARG;
     if (m1 < g || m2 < g) return MRCM_ERR_INVALID_ARG;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return MRCM_ERR_CUDA;
-    if (dev < 0 || dev >= kMaxDevices) return MRCM_ERR_UNSUPPORTED;
-    NoAllocScratch* scratch = nullptr;
-    {
-        // first call on this device: the symbol's device address (the host
-        // name of the array is only a host-side stand-in)
-        std::lock_guard<std::mutex> lock(g_addr_mutex);
-        if (!g_addr[dev]) {
-            void* p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) return MRCM_ERR_CUDA;
-            g_addr[dev] = static_cast<NoAllocScratch*>(p);
-        }
-        scratch = g_addr[dev];
-    }
+    // The array's device address, looked up on every call with the
+    // caller's device and context current (the host name of the array is
+    // only a host-side stand-in).  The lookup is a host-side query: it
+    // allocates nothing and does not synchronise, and a fresh lookup stays
+    // right when the module is loaded again (after cudaDeviceReset, or in
+    // another context of the same device).
+    void* addr = nullptr;
+    int rc = cuda_status(cudaGetSymbolAddress(&addr, g_noalloc_scratch));
+    if (rc != MRCM_OK) return rc;
+    NoAllocScratch* scratch = static_cast<NoAllocScratch*>(addr);
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    // an error left pending by earlier work is not this call's failure
+    cudaGetLastError();
     merge_pair_noalloc_kernel<<<1, kNoAllocThreads, 0, s>>>(scratch, R1_dev, m1, R2_dev, m2, map_dev, g,
                                                             D_dev, R_dev, X_dev);
-    if (cudaGetLastError() != cudaSuccess) return MRCM_ERR_CUDA;
+    if ((rc = cuda_status(cudaGetLastError())) != MRCM_OK) return rc;
     int status = 0;
-    if (cudaMemcpyAsync(&status, &scratch->status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
-        return MRCM_ERR_CUDA;
-    if (cudaStreamSynchronize(s) != cudaSuccess) return MRCM_ERR_CUDA;
+    if ((rc = cuda_status(cudaMemcpyAsync(&status, &scratch->status, sizeof(int), cudaMemcpyDeviceToHost, s))) !=
+        MRCM_OK)
+        return rc;
+    if ((rc = cuda_status(cudaStreamSynchronize(s))) != MRCM_OK) return rc;
     if (status & kStatusBadIndex) return MRCM_ERR_INVALID_ARG;
     return (status & kStatusSingular) ? MRCM_ERR_SINGULAR : MRCM_OK;
 }

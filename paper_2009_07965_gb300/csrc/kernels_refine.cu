@@ -262,7 +262,72 @@ __global__ void face_flux_kernel(DevView v, const double* __restrict__ bc_val, d
     }
 }
 
+// Compatibility of all-Neumann data: the sources must balance the boundary
+// outflow, sum_c q_c = sum_e |e| g_N (otherwise the problem has no
+// solution).  Each of kCompatBlocks CTAs sums its share of
+// q_c - (outflow of the boundary faces) in double-double (error-free
+// TwoSum / TwoProd) and of the magnitudes in FP64; one CTA then adds the
+// partials in a fixed order and sets kStatusInconsistent when
+// |sum| > kCompatTol * (sum of magnitudes).  Partials in v.red[256, 1024).
+constexpr int kCompatBlocks = 256;
+__global__ void __launch_bounds__(256) compat_partial_kernel(DevView v, const double* __restrict__ q,
+                                                             const double* __restrict__ bc_val) {
+    __shared__ double sh_h[256], sh_l[256], sh_a[256];
+    const long long n = (long long)v.nx * v.ny, nb = 2LL * (v.nx + v.ny);
+    DD acc = {0.0, 0.0};
+    double mag = 0.0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n + nb; i += stride) {
+        DD x;
+        if (i < n) {
+            x = {q[i], 0.0};
+        } else {
+            const long long b = i - n;
+            const double area = b < 2LL * v.ny ? v.hy : v.hx;
+            x = dd_neg(dd_two_prod(area, bc_val[b]));
+        }
+        acc = dd_add(acc, x);
+        mag += fabs(x.h);
+    }
+    sh_h[threadIdx.x] = acc.h;
+    sh_l[threadIdx.x] = acc.l;
+    sh_a[threadIdx.x] = mag;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            const DD y = dd_add(DD{sh_h[threadIdx.x], sh_l[threadIdx.x]},
+                                DD{sh_h[threadIdx.x + w], sh_l[threadIdx.x + w]});
+            sh_h[threadIdx.x] = y.h;
+            sh_l[threadIdx.x] = y.l;
+            sh_a[threadIdx.x] += sh_a[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        v.red[256 + 2 * blockIdx.x] = sh_h[0];
+        v.red[256 + 2 * blockIdx.x + 1] = sh_l[0];
+        v.red[768 + blockIdx.x] = sh_a[0];
+    }
+}
+__global__ void compat_final_kernel(DevView v) {
+    DD acc = {0.0, 0.0};
+    double mag = 0.0;
+    for (int b = 0; b < kCompatBlocks; ++b) {
+        acc = dd_add(acc, DD{v.red[256 + 2 * b], v.red[256 + 2 * b + 1]});
+        mag += v.red[768 + b];
+    }
+    if (!(fabs(acc.h + acc.l) <= kCompatTol * mag)) atomicOr(v.status, kStatusInconsistent);
+}
+
 }  // namespace
+
+cudaError_t launch_compat_check(const DevView& v, const double* q, const double* bc_val, cudaStream_t s) {
+    compat_partial_kernel<<<kCompatBlocks, 256, 0, s>>>(v, q, bc_val);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    compat_final_kernel<<<1, 1, 0, s>>>(v);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_residual(const DevView& v, const double* q, const double* bc_val, int step,
                             cudaStream_t s) {

@@ -57,6 +57,10 @@ struct Plan {
     std::vector<long long> seg_lam_a, seg_lam_b;   // lam offsets of each segment in its two leaves
     // flop model
     long long leaf_flops = 0, merge_flops = 0, solve_flops = 0;
+    // reference flop model of a direct method (LU-based merges, banded
+    // Cholesky leaves): the roofline numerator independent of this
+    // implementation's choices
+    double model_build = 0, model_sweep = 0;
     double phase_build[MRCM_PHASE_COUNT] = {};   // per build call
     double phase_pass[MRCM_PHASE_COUNT] = {};    // per solve pass
     double residual_flops = 0, finish_flops = 0;
@@ -250,6 +254,10 @@ int make_plan(Plan& P) {
             f += ck + (long long)ck * (ck + 1);       // scaling + R update
         }
         P.leaf_flops += f;
+        {
+            const double nn = (double)n, b = (double)L.w, mm = (double)L.m;
+            P.model_build += nn * b * b + 2.0 * nn * b * mm + mm * (mm + 1.0) * nn + 4.0 * nn * b;
+        }
         // solve phase per leaf: forward sweep, Z^T y, Z lambda, backward sweep
         P.solve_flops += 2 * n * L.w * 2 + 2 * n * L.m * 2 + 2 * n;
         P.phase_pass[MRCM_PHASE_LEAF_PART] += 2.0 * n * L.w + 2.0 * n * L.m + n;
@@ -316,6 +324,7 @@ int make_plan(Plan& P) {
             const double N = (double)g2, gd = (double)D.g, md = (double)m;
             const double lu = 0.0, inv = 2.0 * N * N * N, prod = 2.0 * N * gd * md + md * (md + 1.0) * gd;
             P.merge_flops += (long long)(lu + inv + prod);
+            P.model_build += 2.0 / 3.0 * N * N * N + 2.0 * N * N * (md + 1.0) + 2.0 * md * gd * (md + 1.0);
             P.solve_flops += 2LL * g2 * m + 2LL * g2 * (m + g2);
             if (m > 0) P.phase_pass[MRCM_PHASE_TREE_UP] += 2.0 * md * N;
             P.phase_pass[MRCM_PHASE_TREE_DOWN] += 2.0 * N * (md + N);
@@ -341,6 +350,7 @@ int make_plan(Plan& P) {
             }
             const double sym = N * N * (N + 1.0);      // lower-triangle sweep
             P.merge_flops += (long long)(sym - node_inv_flops[q]);
+            P.model_sweep += 2.0 / 3.0 * N * N * N;
             P.phase_build[MRCM_PHASE_GJ_SWEEP] += sym;
             P.phase_build[MRCM_PHASE_MERGE_X] += 2.0 * N * gd * md;
             P.phase_build[MRCM_PHASE_MERGE_R] += md * (md + 1.0) * gd;
@@ -353,6 +363,16 @@ int make_plan(Plan& P) {
 }
 
 }  // namespace
+
+// The CUDA error behind the last MRCM_ERR_CUDA / MRCM_ERR_OOM of this thread.
+static thread_local cudaError_t g_last_cuda_error = cudaSuccess;
+
+int mrcm::cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return MRCM_OK;
+    g_last_cuda_error = e;
+    if (e == cudaErrorMemoryAllocation) return MRCM_ERR_OOM;
+    return MRCM_ERR_CUDA;
+}
 
 struct mrcm_ctx {
     Plan P;
@@ -393,15 +413,7 @@ struct mrcm_ctx {
 
 namespace {
 
-// The CUDA error behind the last MRCM_ERR_CUDA / MRCM_ERR_OOM of this thread.
-thread_local cudaError_t g_last_cuda_error = cudaSuccess;
-
-int cuda_err(cudaError_t e) {
-    if (e == cudaSuccess) return MRCM_OK;
-    g_last_cuda_error = e;
-    if (e == cudaErrorMemoryAllocation) return MRCM_ERR_OOM;
-    return MRCM_ERR_CUDA;
-}
+int cuda_err(cudaError_t e) { return mrcm::cuda_status(e); }
 
 template <class T>
 int dev_alloc(mrcm_ctx* c, T** p, long long count) {
@@ -437,7 +449,7 @@ int read_status(mrcm_ctx* c) {
     if (st & kStatusBadK) return MRCM_ERR_BAD_K;
     if (st & kStatusSingular) return MRCM_ERR_SINGULAR;
     if (st & kStatusTimeout) return MRCM_ERR_TIMEOUT;
-    if (st & kStatusBadIndex) return MRCM_ERR_INVALID_ARG;
+    if (st & (kStatusBadIndex | kStatusInconsistent)) return MRCM_ERR_INVALID_ARG;
     return MRCM_OK;
 }
 
@@ -587,6 +599,8 @@ static int plan_value(const Plan& P, int what, long long* value) {
         case MRCM_Q_BUILD_FLOPS: *value = P.leaf_flops + P.merge_flops; break;
         case MRCM_Q_SOLVE_FLOPS: *value = P.solve_flops; break;  // one solve pass
         case MRCM_Q_LEAF_FLOPS: *value = P.leaf_flops; break;
+        case MRCM_Q_MODEL_BUILD_FLOPS: *value = (long long)P.model_build; break;
+        case MRCM_Q_MODEL_SWEEP_FLOPS: *value = (long long)P.model_sweep; break;
         default: return MRCM_ERR_INVALID_ARG;
     }
     return MRCM_OK;
@@ -691,6 +705,7 @@ static int setup_impl(mrcm_ctx* c, const mrcm_grid* g, const double* K_dev, cons
         TRY(dev_alloc(c, &c->tree_scratch, std::max(need, 1LL)));
     }
     TRY(dev_alloc(c, &v.status, 4));
+    v.spin_limit = kDefaultSpinLimit;
     TRYC(cudaMemcpyAsync(c->K, K_dev, sizeof(double) * ncell, cudaMemcpyDefault, c->stream));
     // the root's lambda has no entries; lambda of every other node is written
     // top-down before it is read
@@ -706,6 +721,8 @@ int mrcm_setup(mrcm_ctx** out, const mrcm_grid* g, const double* K_dev, const in
     *out = nullptr;
     if (!K_dev) return MRCM_ERR_INVALID_ARG;
     TRY(validate(g, sub_cells, seg_cells, bc_type));
+    if (precision != MRCM_FP64 && precision != MRCM_MIXED && precision != MRCM_SURROGATE)
+        return MRCM_ERR_INVALID_ARG;
     if (precision != MRCM_FP64) return MRCM_ERR_UNSUPPORTED;
     if (!(alpha > 0) || !std::isfinite(alpha)) return MRCM_ERR_INVALID_ARG;
     mrcm_ctx* c = new (std::nothrow) mrcm_ctx();
@@ -826,6 +843,12 @@ static int enqueue_solve(mrcm_ctx* c, const double* q_dev, const double* bc_val_
     TRYC(cudaMemsetAsync(v.status, 0, sizeof(int), s));
     const int steps = c->refine_steps, nres = steps + (c->refine_check ? 1 : 0);
     if (nres > 0) TRYC(cudaMemsetAsync(v.res_max, 0, sizeof(unsigned long long) * nres, s));
+    if (P.pure_neumann) {
+        // all-Neumann data must balance (Section 2: no solution otherwise)
+        PhaseScope ps(c, MRCM_PHASE_FINISH);
+        TRYC(launch_compat_check(v, q_dev, bc_val_dev, s));
+        launches += 2;
+    }
     TRY(solve_pass(c, q_dev, bc_val_dev, false, false, launches));
     for (int it = 0; it < steps; ++it) {
         {
@@ -888,6 +911,20 @@ int mrcm_solve(mrcm_ctx* c, const double* q_dev, const double* bc_val_dev, doubl
     c->hist_count = c->refine_steps + (c->refine_check ? 1 : 0);
     TRY(read_status(c));
     c->solved = true;
+    return MRCM_OK;
+}
+
+int mrcm_set_wait_limit(mrcm_ctx* c, long long polls) {
+    if (!c) return MRCM_ERR_INVALID_ARG;
+    const long long lim = polls > 0 ? polls : kDefaultSpinLimit;
+    if (lim == c->v.spin_limit) return MRCM_OK;
+    c->v.spin_limit = lim;
+    // the captured graphs hold the old limit in their launch arguments
+    TRYC(cudaStreamSynchronize(c->stream));
+    if (c->build_exec) cudaGraphExecDestroy(c->build_exec);
+    if (c->solve_exec) cudaGraphExecDestroy(c->solve_exec);
+    c->build_exec = c->solve_exec = nullptr;
+    c->solve_key[0] = nullptr;
     return MRCM_OK;
 }
 

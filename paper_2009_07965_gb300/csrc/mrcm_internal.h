@@ -17,7 +17,13 @@ enum : int {
     kStatusSingular = 2,
     kStatusTimeout = 4,
     kStatusBadIndex = 8,
+    kStatusInconsistent = 16,   // all-Neumann data violate the compatibility condition
 };
+// Polls of a bounded inter-CTA wait before it gives up (about a second).
+constexpr long long kDefaultSpinLimit = 5000000;
+// Relative tolerance of the all-Neumann compatibility condition
+// |sum q - sum |e| g_N| <= kCompatTol (sum |q| + sum |e| |g_N|).
+constexpr double kCompatTol = 1e-14;
 
 // Geometry of one leaf, uploaded once by mrcm_setup.
 struct LeafDesc {
@@ -107,6 +113,7 @@ struct DevView {
     double* red;        // reduction scratch (mean pressure)
     unsigned long long* res_max;  // max |residual| per refinement step (double bits)
     int* status;        // device status word
+    long long spin_limit;         // polls of a bounded inter-CTA wait (mrcm_set_wait_limit)
 };
 
 #ifdef __CUDACC__
@@ -208,6 +215,11 @@ __device__ __forceinline__ bool y_skeleton(const DevView& v, int j) {
 }
 #endif
 
+// MRCM_OK for cudaSuccess; otherwise records e as the calling thread's last
+// CUDA error (mrcm_last_cuda_error) and returns MRCM_ERR_OOM or
+// MRCM_ERR_CUDA.
+int cuda_status(cudaError_t e);
+
 // ---- launchers (return cudaGetLastError() of the launch) -----------------
 cudaError_t launch_check_K(const DevView& v, cudaStream_t s);
 // r[i] = rcp_nr(x[i]) (self-check of the kernels' reciprocal)
@@ -233,6 +245,9 @@ cudaError_t launch_residual(const DevView& v, const double* q, const double* bc_
 // fluxes are formed in plain FP64
 cudaError_t launch_face_fluxes(const DevView& v, const double* bc_val, double* p, double* Fx,
                                double* Fy, double* iface, bool plain, cudaStream_t s);
+// all-Neumann data: sets kStatusInconsistent unless the sources balance the
+// boundary outflow to kCompatTol (double-double sums; scratch in v.red)
+cudaError_t launch_compat_check(const DevView& v, const double* q, const double* bc_val, cudaStream_t s);
 // zero-mean shift of the state's p and P (all-Neumann problems); plain as
 // above (the shift is applied to the high parts only)
 cudaError_t launch_mean_shift(const DevView& v, bool plain, cudaStream_t s);

@@ -31,14 +31,17 @@ def mrcm_lib():
     return pkg
 
 
-def gpu_solve(prob, want_iface=True):
-    """Run the CUDA path on one Problem through the C ABI; numpy results."""
+def gpu_solve(prob, want_iface=True, refine=None):
+    """Run the CUDA path on one Problem through the C ABI; numpy results.
+    refine: refinement steps of the solve (None: the library default)."""
     import numpy as np
     import torch
-    from paper_2009_07965_gb300 import Solver
+    from paper_2009_07965_gb300 import Solver, mrcm_set_refinement
     dev = torch.device("cuda:0")
     K = torch.from_numpy(prob.K).to(dev)
     s = Solver(K, prob.Lx, prob.Ly, prob.sub, prob.seg, prob.alpha, prob.bc_type)
+    if refine is not None:
+        mrcm_set_refinement(s.ctx, refine)
     s.build_basis()
     q = torch.from_numpy(prob.q).to(dev)
     g = torch.from_numpy(prob.bc_val).to(dev)

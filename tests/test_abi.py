@@ -79,3 +79,24 @@ def test_setup_rejects_bad_shapes_without_a_device(mrcm_lib):
     with pytest.raises(MrcmError) as e:
         mrcm_lib.mrcm_plan_query((64, 64), (1, 1), (16, 16), (4, 4), (1, 2, 0, 0), "LEAVES")
     assert e.value.code == -1
+
+
+def test_unsupported_requests_are_refused_before_any_device_work(mrcm_lib):
+    # 3D grids and the surrogate precision are reserved by the ABI; the call
+    # returns MRCM_ERR_UNSUPPORTED after validating its host arguments and
+    # before touching the device (the permeability pointer is never read)
+    import ctypes
+    from paper_2009_07965_gb300 import binding as B
+    lib = B._lib()
+    ctx = ctypes.c_void_p()
+    fake_K = ctypes.c_void_p(16)
+    sub, seg, bc = B._ints((16, 16, 16), 3), B._ints((4, 4, 4), 3), B._ints((1, 1, 0, 0, 0, 0), 6)
+    g3 = B.mrcm_grid(3, (ctypes.c_int * 3)(64, 64, 64), (ctypes.c_double * 3)(1.0, 1.0, 1.0))
+    assert lib.mrcm_setup(ctypes.byref(ctx), ctypes.byref(g3), fake_K, sub, seg, 1.0, bc, B.MRCM_FP64,
+                          None) == -9
+    assert not ctx.value
+    g2 = B.mrcm_grid(2, (ctypes.c_int * 3)(64, 64, 1), (ctypes.c_double * 3)(1.0, 1.0, 1.0))
+    assert lib.mrcm_setup(ctypes.byref(ctx), ctypes.byref(g2), fake_K, sub, seg, 1.0, bc, B.MRCM_SURROGATE,
+                          None) == -9
+    assert lib.mrcm_setup(ctypes.byref(ctx), ctypes.byref(g2), fake_K, sub, seg, 1.0, bc, 7, None) == -1
+    assert not ctx.value

@@ -69,7 +69,7 @@ def test_rectangular_leaves_and_segments(mrcm_lib):
 def test_alpha_range(mrcm_lib, alpha):
     prob = inputs.darcy_problem(64, 48, sigma2=1.0, corr=0.1, seed=7, bc="quarter_five_spot",
                                 alpha=alpha)
-    _compare(gpu_solve(prob), solve_mrcm(prob), tol=1e-9 if alpha > 1 else TOL)
+    _compare(gpu_solve(prob, refine=REFINE), solve_mrcm(prob))
 
 
 def test_tiny_leaves(mrcm_lib):

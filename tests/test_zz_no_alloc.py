@@ -77,7 +77,46 @@ def test_noalloc_merge_matches_build(mrcm_lib):
         torch.cuda.synchronize()
         R_ref = mr.mrcm_node_operator(ctx, node)
         assert rel(R_out.cpu().numpy(), R_ref) < 1e-12, (node, rel(R_out.cpu().numpy(), R_ref))
+        # X (2g x m, row-major) against -M^-1 C formed on the host from the
+        # same children maps, index map and D
+        X_ref = _host_X(R1.cpu().numpy(), R2.cpu().numpy(), index_map.cpu().numpy(), g, Dt.cpu().numpy())
+        assert rel(X_out.cpu().numpy(), X_ref) < 1e-12, (node, rel(X_out.cpu().numpy(), X_ref))
     s.close()
+
+
+def _host_X(R1, R2, index_map, g, D):
+    m1, m2 = R1.shape[0], R2.shape[0]
+    o1 = m1 - g
+    gpos1, gpos2 = index_map[:g], index_map[g:2 * g]
+    opos1, opos2 = index_map[2 * g:2 * g + o1], index_map[2 * g + o1:]
+    M = np.block([[R1[np.ix_(gpos1, gpos1)] + np.diag(D), -np.diag(D)],
+                  [-np.diag(D), R2[np.ix_(gpos2, gpos2)] + np.diag(D)]])
+    C = np.zeros((2 * g, len(opos1) + len(opos2)))
+    C[:g, :o1] = R1[np.ix_(gpos1, opos1)]
+    C[g:, o1:] = R2[np.ix_(gpos2, opos2)]
+    return -np.linalg.solve(M, C)
+
+
+def test_noalloc_reports_a_singular_interface_system(mrcm_lib):
+    # zero children maps on gamma and D = 0 make the interface matrix zero:
+    # the call must report MRCM_ERR_SINGULAR (on a host-made input; the
+    # kernel only divides by the zero pivots, which faults nothing)
+    import torch
+    import paper_2009_07965_gb300 as mr
+    from paper_2009_07965_gb300 import MrcmError
+    dev = torch.device("cuda:0")
+    g = 2
+    R = torch.zeros(4, 4, dtype=torch.float64, device=dev)
+    idx = torch.tensor([0, 1, 0, 1, 2, 3, 2, 3], dtype=torch.int32, device=dev)
+    D = torch.zeros(g, dtype=torch.float64, device=dev)
+    Ro = torch.zeros(4, 4, dtype=torch.float64, device=dev)
+    Xo = torch.zeros(4, 4, dtype=torch.float64, device=dev)
+    with pytest.raises(MrcmError) as e:
+        mr.mrcm_merge_pair_noalloc(R, 4, R, 4, idx, g, D, Ro, Xo)
+    assert e.value.code == -5
+    # the shared array keeps no state that spoils the next call
+    R1 = -torch.eye(4, dtype=torch.float64, device=dev)
+    mr.mrcm_merge_pair_noalloc(R1, 4, R1, 4, idx, g, torch.ones(g, dtype=torch.float64, device=dev), Ro, Xo)
 
 
 def test_noalloc_rejects_oversized_and_bad_maps(mrcm_lib):
