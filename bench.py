@@ -77,9 +77,13 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="square4096", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision measurement")
     ap.add_argument("--refine", type=int, default=0,
                     help="iterative-refinement steps per solve in the timed steps (0: the paper's single "
                          "pass; its distance to the refined solution is checked in the same run)")
+    ap.add_argument("--profile-step", choices=["fp64", "mixed"], default=None,
+                    help="for profilers: --warmup steps, then one build + solve inside the NVTX range "
+                         "'mrcm_step', nothing else")
     ap.add_argument("--probe-peaks", action="store_true",
                     help="only measure the arithmetic pipes (FP64 FMA/MMA, FP32 FMA, TF32, BF16) and print them")
     return ap.parse_args()
@@ -290,6 +294,61 @@ def run_probe_only():
                           fp64_nominal_tflops=FP64_NOMINAL_TFLOPS)), flush=True)
 
 
+def time_mixed(mr, prob, q, bcv, stream, flush, args, split, ref_fp64, wl, rank):
+    """The mixed form (FP32 leaves and lower merges, FP64 top merges, refined
+    with double-double residuals): ms per build + solve, its accuracy
+    against the refined FP64 result and the oracle's samples, and its phase
+    times."""
+    import numpy as np
+    import torch
+    dev = q.device
+    K = torch.from_numpy(prob.K).to(dev)
+    with torch.cuda.stream(stream):
+        s = mr.Solver(K, prob.Lx, prob.Ly, prob.sub, prob.seg, prob.alpha, prob.bc_type, stream=stream,
+                      precision=mr.binding.MRCM_MIXED)
+    if split is not None:
+        mr.mrcm_set_mixed_split(s.ctx, split)
+    mr.mrcm_set_refinement(s.ctx, 3)
+    mr.mrcm_enable_timing(s.ctx, True)
+
+    def step():
+        s.build_basis()
+        s.solve(q, bcv)
+
+    for _ in range(args.warmup):
+        step()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ms = []
+    phases = {k: 0.0 for k in mr.PHASES}
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+        ev0.record(stream)
+        step()
+        ev1.record(stream)
+        ev1.synchronize()
+        ms.append(ev0.elapsed_time(ev1))
+        for k, v in mr.mrcm_phase_times(s.ctx).items():
+            phases[k] += v
+    out = [x.cpu().numpy().copy() for x in (s.p, s.Fx, s.Fy)]
+    mr.mrcm_set_refinement(s.ctx, 3, check=True)
+    s.solve(q, bcv)
+    hist = mr.mrcm_residual_history(s.ctx)
+    rel = {name: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+           for name, a, b in zip(("p", "Fx", "Fy"), out, ref_fp64)}
+    vs_oracle = golden_check(wl, dict(zip(("p", "Fx", "Fy"), out))) if rank == 0 else None
+    s.close()
+    del K
+    torch.cuda.empty_cache()
+    step_ms = sum(ms) / len(ms)
+    return dict(ms_per_step=step_ms, value=prob.nx * prob.ny / (step_ms / 1e3), refine_steps=3,
+                fp32_merges_up_to_2g=(split if split is not None else 512),
+                rel_l2_vs_fp64_refined=rel, vs_oracle_samples=vs_oracle, residual_history=hist,
+                within_tolerance=bool(max(rel.values()) <= 1e-8), tolerance=1e-8,
+                phases_ms={k: v / args.steps for k, v in phases.items() if v > 0})
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -422,6 +481,12 @@ def run_ours(args):
         ev1.synchronize()
         ref_ms.append(ev0.elapsed_time(ev1))
     mr.mrcm_set_refinement(solver.ctx, args.refine)
+    mixed = {}
+    if not args.no_mixed:
+        # free the FP64 form's workspace first (two 4096^2 contexts fit, but
+        # the timing should not share L2 with a resident second workspace)
+        for split, name in ((None, "mixed"), (1 << 30, "mixed_all_fp32")):
+            mixed[name] = time_mixed(mr, prob, q, bcv, stream, flush, args, split, refined, wl, rank)
 
     ph = {k: v / args.steps for k, v in phases.items()}          # ms per step
     pf = mr.mrcm_phase_flops(solver.ctx)                          # flops per step
@@ -499,6 +564,7 @@ def run_ours(args):
                    metric_tolerance=1e-8),
         refined_step=dict(refine_steps=1, ms_per_step=sum(ref_ms) / len(ref_ms),
                           value=cells * world / (sum(ref_ms) / len(ref_ms) / 1e3)),
+        mixed=mixed or None,
         cpu_baseline=cpu,
     )
     print(json.dumps(line), flush=True)
@@ -507,10 +573,50 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_profile_step(args):
+    """--warmup steps, then exactly one step inside the NVTX range
+    'mrcm_step' (for ncu --nvtx --nvtx-include mrcm_step/)."""
+    import torch
+    import inputs
+    import paper_2009_07965_gb300 as mr
+    from paper_2009_07965_gb300 import build as build_mod
+    build_mod.build()
+    wl = WORKLOADS[args.workload]
+    n = wl["n"]
+    prob = inputs.darcy_problem(n, n, sigma2=wl["sigma2"], corr=wl["corr"], seed=wl["seed"],
+                                bc="quarter_five_spot", alpha=1.0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    K = torch.from_numpy(prob.K).to(dev)
+    q = torch.from_numpy(prob.q).to(dev)
+    bcv = torch.from_numpy(prob.bc_val).to(dev)
+    prec = mr.binding.MRCM_MIXED if args.profile_step == "mixed" else mr.binding.MRCM_FP64
+    with torch.cuda.stream(stream):
+        solver = mr.Solver(K, prob.Lx, prob.Ly, prob.sub, prob.seg, prob.alpha, prob.bc_type, stream=stream,
+                           precision=prec)
+    if args.profile_step == "fp64":
+        mr.mrcm_set_refinement(solver.ctx, args.refine)
+    for _ in range(args.warmup):
+        solver.build_basis()
+        solver.solve(q, bcv)
+    torch.cuda.synchronize(dev)
+    torch.cuda.nvtx.range_push("mrcm_step")
+    solver.build_basis()
+    solver.solve(q, bcv)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize(dev)
+    launches = (mr.mrcm_query(solver.ctx, "KERNEL_LAUNCHES_BUILD")
+                + mr.mrcm_query(solver.ctx, "KERNEL_LAUNCHES_SOLVE"))
+    print(json.dumps(dict(profile_step=args.profile_step, workload=args.workload, launches=launches)), flush=True)
+    solver.close()
+
+
 def main():
     args = parse()
     if args.probe_peaks:
         run_probe_only()
+    elif args.profile_step:
+        run_profile_step(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -91,7 +91,16 @@ enum {
  *   bc_type    per side (x-, x+, y-, y+, z-, z+): MRCM_BC_NEUMANN or
  *              MRCM_BC_DIRICHLET (z entries ignored in 2D).  All-Neumann
  *              problems are solved with zero-mean pressure.
- *   precision  MRCM_FP64 (others return MRCM_ERR_UNSUPPORTED)
+ *   precision  MRCM_FP64: every step in FP64.  MRCM_MIXED: the leaf
+ *              factorisations, the multi-right-hand-side basis solves and
+ *              the merges of interface systems up to 2g = 512
+ *              (mrcm_set_mixed_split) in FP32; the coefficients, the top
+ *              merges, the solve passes, the residuals (double-double) and
+ *              the fluxes in FP64; mrcm_solve then refines 3 times by
+ *              default (mrcm_set_refinement), which brings the result to
+ *              the FP64 form's accuracy when the FP32 factors contract the
+ *              error (Wilkinson's iterative refinement).  MRCM_SURROGATE
+ *              returns MRCM_ERR_UNSUPPORTED.
  *   cuda_stream  cudaStream_t to run on (NULL = legacy default stream)
  * The context allocates and owns all device workspace.
  */
@@ -254,6 +263,17 @@ int mrcm_set_refinement(mrcm_ctx* ctx, int steps, int check);
  * limit changes.
  */
 int mrcm_set_wait_limit(mrcm_ctx* ctx, long long polls);
+
+/*
+ * mrcm_set_mixed_split -- mixed form only: merges whose interface system
+ * has 2g <= max_g2_fp32 run in FP32, larger ones in FP64 (default 512; 0:
+ * every merge in FP64; a value at least the largest 2g: every merge in
+ * FP32).  The paper has no counterpart (its arithmetic is FP64 throughout).
+ * Invalidates the basis (call mrcm_build_basis again).  Errors:
+ * MRCM_ERR_INVALID_ARG (negative), MRCM_ERR_UNSUPPORTED (not a mixed
+ * context), MRCM_ERR_CUDA.
+ */
+int mrcm_set_mixed_split(mrcm_ctx* ctx, int max_g2_fp32);
 int mrcm_residual_history(mrcm_ctx* ctx, double* out, int cap);
 
 /*

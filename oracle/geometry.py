@@ -62,9 +62,14 @@ class Decomposition:
                 self.xface_seg[t["lo"]:t["hi"], t["line"]] = t["id"]
             else:
                 self.yface_seg[t["line"], t["lo"]:t["hi"]] = t["id"]
+        # segments of each leaf (those with the leaf on side a or b), by id
         for lf in self.leaves:
-            lf["segs"] = sorted(t["id"] for t in self.segments
-                                if t["a"] == lf["id"] or t["b"] == lf["id"])
+            lf["segs"] = []
+        for t in self.segments:
+            self.leaves[t["a"]]["segs"].append(t["id"])
+            self.leaves[t["b"]]["segs"].append(t["id"])
+        for lf in self.leaves:
+            lf["segs"].sort()
         self._robin_coefficients()
 
     def leaf_id(self, I, J):

@@ -25,6 +25,15 @@ The homogeneous part (R, X) is built once; solve_rhs() runs the particular
 up-sweep and the top-down pass for any data (source, external boundary data
 on or off, right-hand sides of the Eq. 13.2 / 14.2 rows), which also serves
 iterative refinement (oracle.refine).
+
+Large problems (leaf_map): the per-leaf work -- each leaf's map R, its
+particular fluxes for given data, its final pressures for given Robin data
+-- is independent from leaf to leaf (the local problems of Eqs. 11.2-12.2).
+With leaf_map (a map function, e.g. a process pool's, whose workers ran
+leaf_worker_init(prob)) that work is handed to it leaf by leaf and the leaf
+problems are rebuilt for every use instead of being kept: the same
+arithmetic per leaf, without the memory of 256 x 256 dense factors for tens
+of thousands of leaves.
 """
 import numpy as np
 
@@ -76,19 +85,60 @@ def outer_segments(dec, box):
     return out
 
 
+# per-process state of the leaf workers (leaf_map mode)
+_WORKER = {}
+
+
+def leaf_worker_init(prob):
+    """Initialiser of a leaf worker: the decomposition of the problem."""
+    _WORKER["dec"] = Decomposition(prob)
+
+
+def leaf_R_task(leaf):
+    """Robin-to-flux map of one leaf (as in RecursiveMRCM._build)."""
+    R, _ = LeafProblem(_WORKER["dec"], leaf).robin_to_flux()
+    return R
+
+
+def leaf_rbar_task(args):
+    """Particular segment fluxes of one leaf for the data (lambda = 0)."""
+    leaf, with_bc, src = args
+    lp = LeafProblem(_WORKER["dec"], leaf)
+    _, rbar, _ = lp.solve(np.zeros(len(lp.segs)), with_data=with_bc, source=src, want_faces=False)
+    return rbar
+
+
+def leaf_p_task(args):
+    """Final pressures of one leaf for its Robin data lam and the data."""
+    leaf, lam, with_bc, src = args
+    lp = LeafProblem(_WORKER["dec"], leaf)
+    pl, _, _ = lp.solve(lam, with_data=with_bc, source=src, want_faces=False)
+    return pl
+
+
 class RecursiveMRCM:
-    def __init__(self, prob, tie="x"):
+    def __init__(self, prob, tie="x", leaf_map=None):
         self.prob = prob
         self.dec = Decomposition(prob)
         self.root = build_tree(self.dec, tie)
         self.leaf_problems = {}
+        self.leaf_map = leaf_map
+        if leaf_map is not None:
+            ids = [lf["id"] for lf in self.dec.leaves]
+            self._leaf_R = dict(zip(ids, leaf_map(leaf_R_task, ids)))
         self._build(self.root)
+        self._leaf_R = None
 
     # ---- homogeneous part: leaves via MFEM, merges -------------------------
     def _build(self, node):
         dec = self.dec
-        node.segs = outer_segments(dec, node.box)
         if node.leaf is not None:
+            # the segments touching the leaf: those with exactly one side
+            # in its box
+            node.segs = dec.leaves[node.leaf]["segs"]
+            if self.leaf_map is not None:
+                node.R = self._leaf_R[node.leaf]
+                return
             lp = LeafProblem(dec, node.leaf)
             self.leaf_problems[node.leaf] = lp
             assert lp.segs == node.segs
@@ -97,13 +147,18 @@ class RecursiveMRCM:
         c1, c2 = node.children
         self._build(c1)
         self._build(c2)
-        gamma = [t for t in c1.segs if t in set(c2.segs)]
+        # gamma: segments with one side in each child; the node's outer
+        # segments (exactly one side in its box) are the children's others
+        s2 = set(c2.segs)
+        gamma = [t for t in c1.segs if t in s2]
         node.gamma = gamma
+        gset = set(gamma)
+        node.segs = sorted([t for t in c1.segs if t not in gset] + [t for t in c2.segs if t not in gset])
         g = len(gamma)
         p1 = {t: k for k, t in enumerate(c1.segs)}
         p2 = {t: k for k, t in enumerate(c2.segs)}
-        o1 = [t for t in c1.segs if t not in set(gamma)]
-        o2 = [t for t in c2.segs if t not in set(gamma)]
+        o1 = [t for t in c1.segs if t not in gset]
+        o2 = [t for t in c2.segs if t not in gset]
         assert sorted(o1 + o2) == node.segs
         node.o1, node.o2 = o1, o2
         beta = np.array([dec.segments[t]["beta"] for t in gamma])
@@ -157,6 +212,9 @@ class RecursiveMRCM:
     # ---- particular part for given data -----------------------------------
     def _up(self, node, data):
         if node.leaf is not None:
+            if self.leaf_map is not None:
+                node.rbar = data["leaf_rbar"][node.leaf]
+                return
             lp = self.leaf_problems[node.leaf]
             src = data["source"]
             src = None if src is None else src[lp.j0:lp.j1, lp.i0:lp.i1]
@@ -226,14 +284,32 @@ class RecursiveMRCM:
         data = dict(with_bc=with_bc, source=source, rhs13=rhs13, rhs14=rhs14)
         nseg = len(self.dec.segments)
         UP = (np.zeros(nseg), np.zeros(nseg))
+        leaves = self.dec.leaves
+
+        def block(lf):
+            return None if source is None else source[lf["j0"]:lf["j1"], lf["i0"]:lf["i1"]]
+
+        if self.leaf_map is not None:
+            ids = [lf["id"] for lf in leaves]
+            data["leaf_rbar"] = dict(zip(ids, self.leaf_map(
+                leaf_rbar_task, [(i, with_bc, block(leaves[i])) for i in ids])))
         self._up(self.root, data)
         self._down(self.root, np.zeros(0), UP)
         p = np.zeros((prob.ny, prob.nx))
-        for node in self._leaves():
-            lp = self.leaf_problems[node.leaf]
-            src = None if source is None else source[lp.j0:lp.j1, lp.i0:lp.i1]
-            pl, _, _ = lp.solve(node.lam, with_data=with_bc, source=src, want_faces=False)
-            p[lp.j0:lp.j1, lp.i0:lp.i1] = pl.reshape(lp.h, lp.w)
+        nodes = list(self._leaves())
+        if self.leaf_map is not None:
+            pls = self.leaf_map(leaf_p_task, [(nd.leaf, nd.lam, with_bc, block(leaves[nd.leaf])) for nd in nodes])
+        else:
+            pls = []
+            for node in nodes:
+                lp = self.leaf_problems[node.leaf]
+                pl, _, _ = lp.solve(node.lam, with_data=with_bc, source=block(leaves[node.leaf]),
+                                    want_faces=False)
+                pls.append(pl)
+        for node, pl in zip(nodes, pls):
+            lf = leaves[node.leaf]
+            p[lf["j0"]:lf["j1"], lf["i0"]:lf["i1"]] = np.asarray(pl).reshape(lf["j1"] - lf["j0"],
+                                                                               lf["i1"] - lf["i0"])
         return p, UP[0], UP[1]
 
     def solve(self, refine=0):
@@ -255,7 +331,7 @@ class RecursiveMRCM:
         Fa_x = np.zeros((ny, nx + 1)); Fb_x = np.zeros((ny, nx + 1))
         Fa_y = np.zeros((ny + 1, nx)); Fb_y = np.zeros((ny + 1, nx))
         for node in self._leaves():
-            lp = self.leaf_problems[node.leaf]
+            lp = self.leaf_problems.get(node.leaf) or LeafProblem(self.dec, node.leaf)
             pl, _, faces = lp.solve(node.lam, with_data=True)
             p[lp.j0:lp.j1, lp.i0:lp.i1] = pl.reshape(lp.h, lp.w)
             for key, val in faces.items():
@@ -273,5 +349,5 @@ class RecursiveMRCM:
                     Fa_x=Fa_x, Fb_x=Fb_x, Fa_y=Fa_y, Fb_y=Fb_y)
 
 
-def solve_recursive(prob, tie="x", refine=0):
-    return RecursiveMRCM(prob, tie).solve(refine=refine)
+def solve_recursive(prob, tie="x", refine=0, leaf_map=None):
+    return RecursiveMRCM(prob, tie, leaf_map=leaf_map).solve(refine=refine)

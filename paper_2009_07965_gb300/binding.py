@@ -27,7 +27,7 @@ EXPORTS = ["mrcm_setup", "mrcm_plan_query", "mrcm_set_permeability", "mrcm_build
            "mrcm_last_cuda_error",
            "mrcm_merge_pair_noalloc", "mrcm_set_refinement", "mrcm_residual_history", "mrcm_phase_flops",
            "mrcm_group_times", "mrcm_check_reciprocal", "mrcm_set_wait_limit",
-           "mrcm_probe_peak"]
+           "mrcm_probe_peak", "mrcm_set_mixed_split"]
 PHASES = ["coef", "leaf_build", "merge_small", "gj_sweep", "merge_form", "merge_x", "merge_r",
           "leaf_particular", "tree_up", "tree_down", "leaf_pressure", "residual", "finish"]
 # kernel family behind each phase (for reports)
@@ -103,6 +103,8 @@ def _lib():
         lib.mrcm_check_reciprocal.restype = I
         lib.mrcm_set_refinement.argtypes = [P, I, I]
         lib.mrcm_set_refinement.restype = I
+        lib.mrcm_set_mixed_split.argtypes = [P, I]
+        lib.mrcm_set_mixed_split.restype = I
         lib.mrcm_probe_peak.argtypes = [I, D, ctypes.POINTER(ctypes.c_double), P]
         lib.mrcm_probe_peak.restype = I
         lib.mrcm_set_wait_limit.argtypes = [P, ctypes.c_longlong]
@@ -263,6 +265,10 @@ def mrcm_probe_peak(kind, seconds=0.3, stream=None):
     _check(_lib().mrcm_probe_peak(PROBES[kind] if isinstance(kind, str) else int(kind), float(seconds),
                                   ctypes.byref(out), stream), "mrcm_probe_peak")
     return out.value
+
+
+def mrcm_set_mixed_split(ctx, max_g2_fp32):
+    _check(_lib().mrcm_set_mixed_split(ctx, int(max_g2_fp32)), "mrcm_set_mixed_split")
 
 
 def mrcm_set_wait_limit(ctx, polls):

@@ -31,15 +31,16 @@ namespace {
 
 constexpr int kWin = kMaxLeafSide + 2;   // circular window rows
 
-template <int MMAX>
+// T: the arithmetic of the factorisation (double; float in the mixed form).
+template <int MMAX, class T>
 struct LeafBuildSmem {
-    double win[kWin][kMaxLeafSide + 1];  // win[row % (w+2)][o] = A[row][row - o]
-    double zw[kWin][MMAX + 1];           // rows of Z being updated (ordered columns)
-    double R[MMAX][MMAX + 1];            // lower triangle of B^T A^-1 B (ordered)
+    T win[kWin][kMaxLeafSide + 1];       // win[row % (w+2)][o] = A[row][row - o]
+    T zw[kWin][MMAX + 1];                // rows of Z being updated (ordered columns)
+    T R[MMAX][MMAX + 1];                 // lower triangle of B^T A^-1 B (ordered)
     double W[MMAX];                      // sum of rho per segment (ordered)
-    double lcol[kMaxLeafSide];           // column k of L below the diagonal
-    double zk[MMAX];                     // row k of Z (ordered)
-    double uk[MMAX];                     // row k of Z / d_k (ordered)
+    T lcol[kMaxLeafSide];                // column k of L below the diagonal
+    T zk[MMAX];                          // row k of Z (ordered)
+    T uk[MMAX];                          // row k of Z / d_k (ordered)
     int order[MMAX];                     // ordered column q -> local segment
     int pos[MMAX];                       // local segment -> ordered column
     int start[MMAX];                     // first row with a nonzero, per ordered column
@@ -83,8 +84,8 @@ __device__ __forceinline__ void cell_robin_segments(const DevView& v, const Leaf
     sn = (j == L.h - 1 && L.side_off[3] >= 0) ? L.side_off[3] + i / v.gx : -1;
 }
 
-template <int MMAX>
-__device__ __forceinline__ void init_row(const DevView& v, const LeafDesc& L, LeafBuildSmem<MMAX>& S,
+template <int MMAX, class T>
+__device__ __forceinline__ void init_row(const DevView& v, const LeafDesc& L, LeafBuildSmem<MMAX, T>& S,
                                          int row, int t) {
     const int w = L.w, m = L.m;
     const int i = row % w, j = row / w;
@@ -95,7 +96,7 @@ __device__ __forceinline__ void init_row(const DevView& v, const LeafDesc& L, Le
         if (o == 0) a = (f.w_ + f.e_) + (f.s_ + f.n_);
         if (o == 1 && i > 0) a = -f.tx;
         if (o == w && j > 0) a = -f.ty;   // w == 1: the y neighbour sits at offset 1
-        S.win[slot][o] = a;
+        S.win[slot][o] = (T)a;
     }
     int sw, se, ss, sn;
     cell_robin_segments(v, L, i, j, sw, se, ss, sn);
@@ -106,7 +107,7 @@ __device__ __forceinline__ void init_row(const DevView& v, const LeafDesc& L, Le
         if (s == se) b = f.e_;
         if (s == ss) b = f.s_;
         if (s == sn) b = f.n_;
-        S.zw[slot][q] = b;
+        S.zw[slot][q] = (T)b;
     }
 }
 
@@ -140,15 +141,16 @@ __device__ __forceinline__ int segment_start_row(const DevView& v, const LeafDes
 
 // Body of the leaf build for one leaf; WF > 0 fixes the leaf to WF x WF
 // cells at compile time (the full leaf), 0 reads the size from the
-// descriptor (truncated leaves).
-template <int MMAX, int WF>
-__device__ __forceinline__ void leaf_build_body(const DevView& v, LeafBuildSmem<MMAX>& S, const LeafDesc& L, int t,
-                                                unsigned mask) {
+// descriptor (truncated leaves).  T: arithmetic and storage of the factors
+// (double, or float in the mixed form; the map R is stored in double).
+template <int MMAX, int WF, class T>
+__device__ __forceinline__ void leaf_build_body(const DevView& v, LeafBuildSmem<MMAX, T>& S, const LeafDesc& L,
+                                                int t, unsigned mask) {
     const int w = WF ? WF : L.w, n = WF ? WF * WF : L.w * L.h, m = L.m, W2 = w + 2;
-    double* Lg = v.leafL + L.L_off;          // n x 16 multipliers
-    double* Dg = Lg + (long long)n * kLeafThreads;   // n reciprocal pivots
-    double* LTg = Dg + n;                    // n x 16 multipliers by row
-    double* Zg = v.leafZ + L.Z_off;          // n x m, column-major (local segment order)
+    T* Lg = leaf_L<T>(v) + L.L_off;          // n x 16 multipliers
+    T* Dg = Lg + (long long)n * kLeafThreads;   // n reciprocal pivots
+    T* LTg = Dg + n;                         // n x 16 multipliers by row
+    T* Zg = leaf_Z<T>(v) + L.Z_off;          // n x m, column-major (local segment order)
 
     // Columns of B ordered by their first nonzero row: column q of Z stays
     // zero above start[q], so only the first c_k ordered columns take part
@@ -169,7 +171,7 @@ __device__ __forceinline__ void leaf_build_body(const DevView& v, LeafBuildSmem<
     }
     __syncwarp(mask);
 
-    for (int idx = t; idx < m * (MMAX + 1); idx += kLeafThreads) S.R[idx / (MMAX + 1)][idx % (MMAX + 1)] = 0.0;
+    for (int idx = t; idx < m * (MMAX + 1); idx += kLeafThreads) S.R[idx / (MMAX + 1)][idx % (MMAX + 1)] = (T)0;
     const int first = min(w, n - 1);
     for (int r = 0; r <= first; ++r) init_row(v, L, S, r, t);
     __syncwarp(mask);
@@ -196,32 +198,29 @@ __device__ __forceinline__ void leaf_build_body(const DevView& v, LeafBuildSmem<
         while (ck < m && S.start[ck] <= k) ++ck;
         const int s1 = sk + 1 == W2 ? 0 : sk + 1;        // slot of row k + 1
         // ---- phase A: pivot, multipliers, row k of Z -------------------------
-        const double dk = S.win[sk][0];
-        {
-            // dk > 0 and finite, tested on the bit pattern (no FP64 compare)
-            const long long bits = __double_as_longlong(dk);
-            bad_pivot |= !(bits > 0 && bits < 0x7ff0000000000000LL);
-        }
-        const double rcp = rcp_nr(dk);
+        const T dk = S.win[sk][0];
+        // dk > 0 and finite, tested on the bit pattern (no FP64 compare)
+        bad_pivot |= !positive_finite_bits(dk);
+        const T rcp = rcp_nr(dk);
         const int wk = min(w, n - 1 - k);
         if (t < wk) {
             int sl = s1 + t;
             sl -= sl >= W2 ? W2 : 0;
-            const double l = S.win[sl][1 + t] * rcp;
+            const T l = S.win[sl][1 + t] * rcp;
             S.lcol[t] = l;
             Lg[(long long)k * kLeafThreads + t] = l;
             LTg[(long long)(k + 1 + t) * kLeafThreads + t] = l;
         }
         if (t == 0) Dg[k] = rcp;
         for (int q = t; q < ck; q += kLeafThreads) {
-            const double z = S.zw[sk][q];
+            const T z = S.zw[sk][q];
             S.zk[q] = z;
             S.uk[q] = z * rcp;
         }
         __syncwarp(mask);
         for (int s = t; s < m; s += kLeafThreads) {
             const int q = S.pos[s];
-            Zg[(long long)s * n + k] = q < ck ? S.zk[q] : 0.0;
+            Zg[(long long)s * n + k] = q < ck ? S.zk[q] : (T)0;
         }
         // ---- phase B: trailing band update, Z update, R update, new row -----
         const int ntri_w = wk * (wk + 1) / 2;
@@ -232,7 +231,7 @@ __device__ __forceinline__ void leaf_build_body(const DevView& v, LeafBuildSmem<
             int ra = s1 + a, rb = s1 + b;
             ra -= ra >= W2 ? W2 : 0;
             rb -= rb >= W2 ? W2 : 0;
-            double& x = S.win[ra][a - b];
+            T& x = S.win[ra][a - b];
             x = fma(-S.lcol[a], S.win[rb][1 + b], x);
         }
         if (ck > 0) {
@@ -242,7 +241,7 @@ __device__ __forceinline__ void leaf_build_body(const DevView& v, LeafBuildSmem<
             for (int idx = t; idx < nz; idx += kLeafThreads) {
                 int ra = s1 + a;
                 ra -= ra >= W2 ? W2 : 0;
-                double& x = S.zw[ra][q];
+                T& x = S.zw[ra][q];
                 x = fma(-S.lcol[a], S.zk[q], x);
                 a += da;
                 q += dq;
@@ -278,12 +277,12 @@ __device__ __forceinline__ void leaf_build_body(const DevView& v, LeafBuildSmem<
     double* Rg = v.R + L.R_off;
     for (int idx = t; idx < m * m; idx += kLeafThreads) {
         const int r = S.pos[idx / m], c = S.pos[idx % m];
-        double val = (r >= c) ? S.R[r][c] : S.R[c][r];
+        double val = (r >= c) ? (double)S.R[r][c] : (double)S.R[c][r];
         if (r == c) val -= S.W[r];
         Rg[idx] = val;
     }}
 
-template <int MMAX, int LPB>
+template <int MMAX, int LPB, class T>
 __global__ void __launch_bounds__(kLeafThreads * LPB)
 leaf_build_kernel(DevView v) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -292,12 +291,12 @@ leaf_build_kernel(DevView v) {
     const int leaf = blockIdx.x * LPB + slot_leaf;
     if (leaf >= v.nleaf) return;     // uniform over the 16 threads of the leaf
     const unsigned mask = 0xFFFFu << (threadIdx.x & 16);
-    LeafBuildSmem<MMAX>& S = reinterpret_cast<LeafBuildSmem<MMAX>*>(smem_raw)[slot_leaf];
+    LeafBuildSmem<MMAX, T>& S = reinterpret_cast<LeafBuildSmem<MMAX, T>*>(smem_raw)[slot_leaf];
     const LeafDesc L = v.leaves[leaf];
     if (L.w == kMaxLeafSide && L.h == kMaxLeafSide)
-        leaf_build_body<MMAX, kMaxLeafSide>(v, S, L, t, mask);
+        leaf_build_body<MMAX, kMaxLeafSide, T>(v, S, L, t, mask);
     else
-        leaf_build_body<MMAX, 0>(v, S, L, t, mask);
+        leaf_build_body<MMAX, 0, T>(v, S, L, t, mask);
 }
 
 // ---------------------------------------------------------------------------
@@ -339,15 +338,16 @@ constexpr int kSweepAhead = 8;
 // Body of the particular solve for one leaf; NF, WF > 0 fix the row count
 // and the band width at compile time (the full kMaxLeafSide^2 leaf: the
 // sweep's bounds and end tests then fold away, which makes it ~3x faster),
-// 0 reads them from the descriptor (truncated leaves).
-template <int NF, int WF>
+// 0 reads them from the descriptor (truncated leaves).  TS: storage type of
+// the factors (float in the mixed form); the sweep itself runs in FP64.
+template <int NF, int WF, class TS>
 __device__ __forceinline__ void leaf_particular_body(const DevView& v, const double* __restrict__ q,
                                                      const double* __restrict__ bc_val, bool with_sadj,
                                                      LeafSolveSmem& S, const LeafDesc& L, int t, unsigned mask) {
     const int w = WF ? WF : L.w, n = NF ? NF : L.w * L.h, m = L.m;
-    const double* Lg = v.leafL + L.L_off;
-    const double* Dg = Lg + (long long)n * kLeafThreads;
-    const double* Zg = v.leafZ + L.Z_off;
+    const TS* Lg = leaf_L<TS>(v) + L.L_off;
+    const TS* Dg = Lg + (long long)n * kLeafThreads;
+    const TS* Zg = leaf_Z<TS>(v) + L.Z_off;
     double* zb = v.leafzb + L.zb_off;
 
     // forward sweep zbar = L^-1 bbar (unit lower band); the right-hand side
@@ -374,20 +374,20 @@ __device__ __forceinline__ void leaf_particular_body(const DevView& v, const dou
     for (int k = t; k < n; k += kLeafThreads) zb[k] = S.y[k];
     // y = D^-1 zbar ; rbar = Z^T y  (= B^T A^-1 bbar): the 16 lanes share
     // every column of Z (consecutive rows, coalesced) and reduce by shuffles
-    for (int k = t; k < n; k += kLeafThreads) S.y[k] *= Dg[k];
+    for (int k = t; k < n; k += kLeafThreads) S.y[k] *= (double)Dg[k];
     __syncwarp(mask);
     double* rb = v.rbar + L.r_off;
     for (int s = 0; s < m; ++s) {
-        const double* zc = Zg + (long long)s * n;
+        const TS* zc = Zg + (long long)s * n;
         double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
         int k = t;
         for (; k + 3 * kLeafThreads < n; k += 4 * kLeafThreads) {
-            a0 = fma(zc[k], S.y[k], a0);
-            a1 = fma(zc[k + kLeafThreads], S.y[k + kLeafThreads], a1);
-            a2 = fma(zc[k + 2 * kLeafThreads], S.y[k + 2 * kLeafThreads], a2);
-            a3 = fma(zc[k + 3 * kLeafThreads], S.y[k + 3 * kLeafThreads], a3);
+            a0 = fma((double)zc[k], S.y[k], a0);
+            a1 = fma((double)zc[k + kLeafThreads], S.y[k + kLeafThreads], a1);
+            a2 = fma((double)zc[k + 2 * kLeafThreads], S.y[k + 2 * kLeafThreads], a2);
+            a3 = fma((double)zc[k + 3 * kLeafThreads], S.y[k + 3 * kLeafThreads], a3);
         }
-        for (; k < n; k += kLeafThreads) a0 = fma(zc[k], S.y[k], a0);
+        for (; k < n; k += kLeafThreads) a0 = fma((double)zc[k], S.y[k], a0);
         double acc = (a0 + a1) + (a2 + a3);
 #pragma unroll
         for (int o = kLeafThreads / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(mask, acc, o);
@@ -396,7 +396,7 @@ __device__ __forceinline__ void leaf_particular_body(const DevView& v, const dou
         if (t == 0) rb[s] = with_sadj ? acc - v.sadj[L.r_off + s] : acc;
     }}
 
-template <int LPB>
+template <int LPB, class TS>
 __global__ void __launch_bounds__(kLeafThreads * LPB)
 leaf_particular_kernel(DevView v, const double* __restrict__ q, const double* __restrict__ bc_val,
                        bool with_sadj) {
@@ -409,21 +409,22 @@ leaf_particular_kernel(DevView v, const double* __restrict__ q, const double* __
     LeafSolveSmem& S = smem[slot_leaf];
     const LeafDesc L = v.leaves[leaf];
     if (L.w == kMaxLeafSide && L.h == kMaxLeafSide)
-        leaf_particular_body<kMaxLeafSide * kMaxLeafSide, kMaxLeafSide>(v, q, bc_val, with_sadj, S, L, t, mask);
+        leaf_particular_body<kMaxLeafSide * kMaxLeafSide, kMaxLeafSide, TS>(v, q, bc_val, with_sadj, S, L, t,
+                                                                            mask);
     else
-        leaf_particular_body<0, 0>(v, q, bc_val, with_sadj, S, L, t, mask);
+        leaf_particular_body<0, 0, TS>(v, q, bc_val, with_sadj, S, L, t, mask);
 }
 
 // p = A^-1 (bbar + B lambda) = L^-T D^-1 (zbar + Z lambda), written into the
 // state (p_hi, p_lo) or added to it in double-double (refinement corrections).
 // Body of the final solve for one leaf; NF, WF as for the particular solve.
-template <int NF, int WF>
+template <int NF, int WF, class TS>
 __device__ __forceinline__ void leaf_pressure_body(const DevView& v, bool accumulate, LeafSolveSmem& S,
                                                    double* lam, const LeafDesc& L, int t, unsigned mask) {
     const int w = WF ? WF : L.w, n = NF ? NF : L.w * L.h, m = L.m;
-    const double* Lg = v.leafL + L.L_off;
-    const double* Dg = Lg + (long long)n * kLeafThreads;
-    const double* Zg = v.leafZ + L.Z_off;
+    const TS* Lg = leaf_L<TS>(v) + L.L_off;
+    const TS* Dg = Lg + (long long)n * kLeafThreads;
+    const TS* Zg = leaf_Z<TS>(v) + L.Z_off;
     const double* zb = v.leafzb + L.zb_off;
     for (int s = t; s < m; s += kLeafThreads) lam[s] = v.lam[L.r_off + s];
     __syncwarp(mask);
@@ -439,23 +440,23 @@ __device__ __forceinline__ void leaf_pressure_body(const DevView& v, bool accumu
     }
     for (int s = 0; s < m; ++s) {
         const double ls = lam[s];
-        const double* zc = Zg + (long long)s * n;
+        const TS* zc = Zg + (long long)s * n;
 #pragma unroll
         for (int r = 0; r < kRows; ++r) {
             const int k = t + r * kLeafThreads;
-            if (k < n) acc[r] = fma(zc[k], ls, acc[r]);
+            if (k < n) acc[r] = fma((double)zc[k], ls, acc[r]);
         }
     }
 #pragma unroll
     for (int r = 0; r < kRows; ++r) {
         const int k = t + r * kLeafThreads;
-        if (k < n) S.y[k] = acc[r] * Dg[k];
+        if (k < n) S.y[k] = acc[r] * (double)Dg[k];
     }
     __syncwarp(mask);
     // backward sweep L^T p = y in place, right-looking from the last row,
     // on the row layout of L (row k: L[k][k-1-t] at LTg[16 k + t], contiguous);
     // the multipliers stream through a register ring kSweepAhead steps ahead
-    const double* LTg = Dg + n;
+    const TS* LTg = Dg + n;
     double ring[kSweepAhead];
 #pragma unroll
     for (int d = 0; d < kSweepAhead; ++d) {
@@ -488,7 +489,7 @@ __device__ __forceinline__ void leaf_pressure_body(const DevView& v, bool accumu
         }
     }}
 
-template <int LPB>
+template <int LPB, class TS>
 __global__ void __launch_bounds__(kLeafThreads * LPB)
 leaf_pressure_kernel(DevView v, bool accumulate) {
     __shared__ LeafSolveSmem smem[LPB];
@@ -502,9 +503,9 @@ leaf_pressure_kernel(DevView v, bool accumulate) {
     double* lam = lam_s[slot_leaf];
     const LeafDesc L = v.leaves[leaf];
     if (L.w == kMaxLeafSide && L.h == kMaxLeafSide)
-        leaf_pressure_body<kMaxLeafSide * kMaxLeafSide, kMaxLeafSide>(v, accumulate, S, lam, L, t, mask);
+        leaf_pressure_body<kMaxLeafSide * kMaxLeafSide, kMaxLeafSide, TS>(v, accumulate, S, lam, L, t, mask);
     else
-        leaf_pressure_body<0, 0>(v, accumulate, S, lam, L, t, mask);
+        leaf_pressure_body<0, 0, TS>(v, accumulate, S, lam, L, t, mask);
 }
 
 constexpr int kRedBlocks = 256;
@@ -571,32 +572,44 @@ __global__ void mean_subtract_kernel(DevView v, long long n) {
 
 }  // namespace
 
-cudaError_t launch_leaf_build(const DevView& v, int max_m, cudaStream_t s) {
+template <class T>
+static cudaError_t launch_leaf_build_t(const DevView& v, int max_m, cudaStream_t s) {
     if (max_m <= 16) {
         constexpr int LPB = 4;
-        const size_t sm = sizeof(LeafBuildSmem<16>) * LPB;
-        cudaFuncSetAttribute(leaf_build_kernel<16, LPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        leaf_build_kernel<16, LPB><<<(v.nleaf + LPB - 1) / LPB, kLeafThreads * LPB, sm, s>>>(v);
+        const size_t sm = sizeof(LeafBuildSmem<16, T>) * LPB;
+        cudaFuncSetAttribute(leaf_build_kernel<16, LPB, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        leaf_build_kernel<16, LPB, T><<<(v.nleaf + LPB - 1) / LPB, kLeafThreads * LPB, sm, s>>>(v);
     } else {
         constexpr int LPB = 2;
-        const size_t sm = sizeof(LeafBuildSmem<64>) * LPB;
-        cudaFuncSetAttribute(leaf_build_kernel<64, LPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        leaf_build_kernel<64, LPB><<<(v.nleaf + LPB - 1) / LPB, kLeafThreads * LPB, sm, s>>>(v);
+        const size_t sm = sizeof(LeafBuildSmem<64, T>) * LPB;
+        cudaFuncSetAttribute(leaf_build_kernel<64, LPB, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        leaf_build_kernel<64, LPB, T><<<(v.nleaf + LPB - 1) / LPB, kLeafThreads * LPB, sm, s>>>(v);
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_leaf_build(const DevView& v, int max_m, cudaStream_t s) {
+    return v.mixed ? launch_leaf_build_t<float>(v, max_m, s) : launch_leaf_build_t<double>(v, max_m, s);
 }
 
 cudaError_t launch_leaf_particular(const DevView& v, const double* q, const double* bc_val,
                                    bool with_sadj, cudaStream_t s) {
     constexpr int LPB = 8;
-    leaf_particular_kernel<LPB><<<(v.nleaf + LPB - 1) / LPB, kLeafThreads * LPB, 0, s>>>(v, q, bc_val,
-                                                                                          with_sadj);
+    const int grid = (v.nleaf + LPB - 1) / LPB;
+    if (v.mixed)
+        leaf_particular_kernel<LPB, float><<<grid, kLeafThreads * LPB, 0, s>>>(v, q, bc_val, with_sadj);
+    else
+        leaf_particular_kernel<LPB, double><<<grid, kLeafThreads * LPB, 0, s>>>(v, q, bc_val, with_sadj);
     return cudaGetLastError();
 }
 
 cudaError_t launch_leaf_pressure(const DevView& v, bool accumulate, cudaStream_t s) {
     constexpr int LPB = 8;
-    leaf_pressure_kernel<LPB><<<(v.nleaf + LPB - 1) / LPB, kLeafThreads * LPB, 0, s>>>(v, accumulate);
+    const int grid = (v.nleaf + LPB - 1) / LPB;
+    if (v.mixed)
+        leaf_pressure_kernel<LPB, float><<<grid, kLeafThreads * LPB, 0, s>>>(v, accumulate);
+    else
+        leaf_pressure_kernel<LPB, double><<<grid, kLeafThreads * LPB, 0, s>>>(v, accumulate);
     return cudaGetLastError();
 }
 

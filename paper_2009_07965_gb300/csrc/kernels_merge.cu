@@ -118,6 +118,17 @@ __device__ __forceinline__ bool pivot_ok_bits(double p, bool d_row) {
     const unsigned long long tiny = (unsigned long long)__double_as_longlong(kTinyPivot);
     return ((b >> 63) == (d_row ? 0ull : 1ull)) && mag > tiny && mag < 0x7ff0000000000000ull;
 }
+__device__ __forceinline__ bool pivot_ok_bits(float p, bool d_row) {
+    const unsigned int b = __float_as_uint(p);
+    const unsigned int mag = b & 0x7fffffffu;
+    const unsigned int tiny = __float_as_uint((float)kTinyPivot);
+    return ((b >> 31) == (d_row ? 0u : 1u)) && mag > tiny && mag < 0x7f800000u;
+}
+// The interface matrix being inverted in place: the W storage itself in
+// FP64, or the FP32 work array of the mixed form (same offsets).
+template <class T> __device__ __forceinline__ T* gj_work(const DevView& v);
+template <> __device__ __forceinline__ double* gj_work<double>(const DevView& v) { return v.W; }
+template <> __device__ __forceinline__ float* gj_work<float>(const DevView& v) { return v.W32; }
 
 // ---------------------------------------------------------------------------
 // Per-node path for small systems (2g <= kSmallMax): one CTA per node, all in
@@ -131,16 +142,18 @@ constexpr int kSmallTri = (kSmallMax * (kSmallMax + 1) / 2 + kSmallThreads - 1) 
 // Body of the per-node merge; G2F > 0 fixes 2g at compile time (the sizes of
 // a uniform tree's lower levels: its loops and the T index arithmetic then
 // fold), 0 reads it from the descriptor.
-template <int G2F>
+// F: the arithmetic of the merge (double; float for the FP32 levels of the
+// mixed form); the scalings, W, X and R are stored in double.
+template <int G2F, class F>
 __device__ __forceinline__ void merge_small_body(const DevView& v, const MergeDesc& D, const NodeRefs& N, int mstride,
-                                                 double* sm, double* sd, double* sq, double* vrow,
+                                                 F* sm, double* sd, double* sq, F* vrow,
                                                  double& s_inv_sum, int& s_bad) {
     const int g2 = G2F ? G2F : N.g2, g = g2 / 2, m = N.m, o1 = N.o1;
     const int tid = threadIdx.x;
-    double* T = sm;
-    double* Wc = T + g2 * g2;
-    double* Bs = Wc + g2 * g2;
-    double* Xs = Bs + g * mstride;
+    F* T = sm;
+    F* Wc = T + g2 * g2;
+    F* Bs = Wc + g2 * g2;
+    F* Xs = Bs + g * mstride;
     if (tid < 32) {
         double dsum = 0.0;
         if (tid < g) {
@@ -159,12 +172,13 @@ __device__ __forceinline__ void merge_small_body(const DevView& v, const MergeDe
     __syncthreads();
     for (int idx = tid; idx < g2 * g2; idx += kSmallThreads) {
         const int r = idx / g2, c = idx % g2, i = r < g ? r : r - g, j = c < g ? c : c - g;
-        T[idx] = t_entry(N, r, c, sd[i], sd[j], sq[i], sq[j], s_inv_sum);
+        T[idx] = (F)t_entry(N, r, c, sd[i], sd[j], sq[i], sq[j], s_inv_sum);
     }
     for (int k = 0; k < g; ++k) {
         const double* ra = N.R1 + N.gpos1[k] * N.m1;
         const double* rb = N.R2 + N.gpos2[k] * N.m2;
-        for (int j = tid; j < m; j += kSmallThreads) Bs[k * mstride + j] = j < o1 ? ra[N.opos1[j]] : rb[N.opos2[j - o1]];
+        for (int j = tid; j < m; j += kSmallThreads)
+            Bs[k * mstride + j] = (F)(j < o1 ? ra[N.opos1[j]] : rb[N.opos2[j - o1]]);
     }
     // Gauss-Jordan on T (d rows first: positive pivots, then negative).  T
     // is symmetric, and after step k the entries of an eliminated and a
@@ -189,24 +203,24 @@ __device__ __forceinline__ void merge_small_body(const DevView& v, const MergeDe
     for (int k = 0; k < g2; ++k) {
         __syncthreads();
         if (tid < 32) {
-            const double p = T[k * g2 + k];
-            const double rp = rcp_nr(p);
+            const F p = T[k * g2 + k];
+            const F rp = rcp_nr(p);
             if (tid < g2) {
                 const int c = tid;
-                const double a_kc = c == k ? 1.0 : (c < k ? T[k * g2 + c] : T[c * g2 + k]);
+                const F a_kc = c == k ? (F)1 : (c < k ? T[k * g2 + c] : T[c * g2 + k]);
                 vrow[c] = a_kc * rp;
             }
             if (tid == 0 && !pivot_ok_bits(p, k < g)) s_bad = 1;
         }
         __syncthreads();
-        double nv[kSmallTri];
+        F nv[kSmallTri];
 #pragma unroll
         for (int e = 0; e < kSmallTri; ++e) {
             const int idx = tid + e * kSmallThreads;
             if (idx >= ntri) break;
             const int r = er[e], c = ec[e];
-            const double xr = r == k ? 1.0 : (r > k ? neg_bits(T[r * g2 + k]) : T[k * g2 + r]);
-            const double y = (r == k || c == k) ? 0.0 : T[r * g2 + c];
+            const F xr = r == k ? (F)1 : (r > k ? neg_bits(T[r * g2 + k]) : T[k * g2 + r]);
+            const F y = (r == k || c == k) ? (F)0 : T[r * g2 + c];
             nv[e] = fma(xr, vrow[c], y);
         }
         __syncthreads();
@@ -223,11 +237,11 @@ __device__ __forceinline__ void merge_small_body(const DevView& v, const MergeDe
     // in the lower triangle
     for (int idx = tid; idx < g * g; idx += kSmallThreads) {
         const int i = idx % g, j = idx / g;
-        const double zdd = i >= j ? T[i * g2 + j] : T[j * g2 + i];
-        const double zds = T[(g + j) * g2 + i];           // (d_i, s_j) = (s_j, d_i)
-        const double zsd = T[(g + i) * g2 + j];
-        const double zss = i >= j ? T[(g + i) * g2 + g + j] : T[(g + j) * g2 + g + i];
-        const double sc = 0.5 * sd[i] * sd[j];
+        const F zdd = i >= j ? T[i * g2 + j] : T[j * g2 + i];
+        const F zds = T[(g + j) * g2 + i];           // (d_i, s_j) = (s_j, d_i)
+        const F zsd = T[(g + i) * g2 + j];
+        const F zss = i >= j ? T[(g + i) * g2 + g + j] : T[(g + j) * g2 + g + i];
+        const F sc = (F)(0.5 * sd[i] * sd[j]);
         Wc[j * g2 + i] = (zdd - zds - zsd + zss) * sc;
         Wc[(g + j) * g2 + i] = (zss + zsd - zds - zdd) * sc;
         Wc[j * g2 + g + i] = (zss + zds - zsd - zdd) * sc;
@@ -235,21 +249,21 @@ __device__ __forceinline__ void merge_small_body(const DevView& v, const MergeDe
     }
     __syncthreads();
     double* Wg = v.W + D.W_off;
-    for (int idx = tid; idx < g2 * g2; idx += kSmallThreads) Wg[idx] = Wc[idx];
+    for (int idx = tid; idx < g2 * g2; idx += kSmallThreads) Wg[idx] = (double)Wc[idx];
     // X = -W B (columns of side a use W's a columns)
     double* Xg = v.X + D.X_off;
     for (int idx = tid; idx < g2 * m; idx += kSmallThreads) {
         const int r = idx % g2, j = idx / g2;
-        const double* wc = Wc + (j < o1 ? 0 : g) * g2 + r;
-        double acc0 = 0.0, acc1 = 0.0;
+        const F* wc = Wc + (j < o1 ? 0 : g) * g2 + r;
+        F acc0 = 0, acc1 = 0;
         int k = 0;
         for (; k + 1 < g; k += 2) {
             acc0 = fma(wc[k * g2], Bs[k * mstride + j], acc0);
             acc1 = fma(wc[(k + 1) * g2], Bs[(k + 1) * mstride + j], acc1);
         }
         if (k < g) acc0 = fma(wc[k * g2], Bs[k * mstride + j], acc0);
-        const double x = -(acc0 + acc1);
-        Xg[idx] = x;
+        const F x = -(acc0 + acc1);
+        Xg[idx] = (double)x;
         Xs[r * mstride + j] = x;
     }
     __syncthreads();
@@ -266,31 +280,34 @@ __device__ __forceinline__ void merge_small_body(const DevView& v, const MergeDe
         double roo = 0.0;       // loaded first, added last: its latency overlaps the sum
         if (ia && j < o1) roo = N.R1[N.opos1[i] * N.m1 + N.opos1[j]];
         if (!ia && j >= o1) roo = N.R2[N.opos2[i - o1] * N.m2 + N.opos2[j - o1]];
-        const double* xh = Xs + (ia ? 0 : g) * mstride + j;
-        double acc0 = 0.0, acc1 = 0.0;
+        const F* xh = Xs + (ia ? 0 : g) * mstride + j;
+        F acc0 = 0, acc1 = 0;
         int k = 0;
         for (; k + 1 < g; k += 2) {
             acc0 = fma(Bs[k * mstride + i], xh[k * mstride], acc0);
             acc1 = fma(Bs[(k + 1) * mstride + i], xh[(k + 1) * mstride], acc1);
         }
         if (k < g) acc0 = fma(Bs[k * mstride + i], xh[k * mstride], acc0);
-        const double val = roo + (acc0 + acc1);
+        const double val = roo + (double)(acc0 + acc1);
         Rp[(long long)i * m + j] = val;
         Rp[(long long)j * m + i] = val;
     }}
 
+template <class F>
 __global__ void __launch_bounds__(kSmallThreads) merge_small_kernel(DevView v, int first, int mstride) {
-    extern __shared__ __align__(16) double sm[];
-    __shared__ double sd[kSmallMax / 2], sq[kSmallMax / 2], vrow[kSmallMax];
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    F* sm = reinterpret_cast<F*>(sm_raw);
+    __shared__ double sd[kSmallMax / 2], sq[kSmallMax / 2];
+    __shared__ F vrow[kSmallMax];
     __shared__ double s_inv_sum;
     __shared__ int s_bad;
     const MergeDesc D = v.merges[first + blockIdx.x];
     const NodeRefs N = node_refs(v, D);
     switch (N.g2) {                                       // uniform per CTA
-        case 8: merge_small_body<8>(v, D, N, mstride, sm, sd, sq, vrow, s_inv_sum, s_bad); break;
-        case 16: merge_small_body<16>(v, D, N, mstride, sm, sd, sq, vrow, s_inv_sum, s_bad); break;
-        case 32: merge_small_body<32>(v, D, N, mstride, sm, sd, sq, vrow, s_inv_sum, s_bad); break;
-        default: merge_small_body<0>(v, D, N, mstride, sm, sd, sq, vrow, s_inv_sum, s_bad); break;
+        case 8: merge_small_body<8, F>(v, D, N, mstride, sm, sd, sq, vrow, s_inv_sum, s_bad); break;
+        case 16: merge_small_body<16, F>(v, D, N, mstride, sm, sd, sq, vrow, s_inv_sum, s_bad); break;
+        case 32: merge_small_body<32, F>(v, D, N, mstride, sm, sd, sq, vrow, s_inv_sum, s_bad); break;
+        default: merge_small_body<0, F>(v, D, N, mstride, sm, sd, sq, vrow, s_inv_sum, s_bad); break;
     }
 }
 
@@ -330,35 +347,44 @@ __device__ double stage_gamma_scalings(const DevView& v, const MergeDesc& D, dou
 // u_x = P c_x^T (same layout), a flag word (the number of the last block
 // whose P has been published) and a counter of the tile items that have
 // written c of a next block.
+// (In the mixed form's FP32 levels every value below is a float; the
+// scratch buffer is the same, read through a float pointer.)
 constexpr int kGJScratchHead = 2 * kGJ * kGJ;
 __device__ __forceinline__ long long gj_scratch_stride(int nmax) {
     return kGJScratchHead + 4LL * nmax * kGJ + 2;
 }
-__device__ __forceinline__ double* gj_scratch(double* scratch, int slot, int nmax) {
+template <class T>
+__device__ __forceinline__ T* gj_scratch(T* scratch, int slot, int nmax) {
     return scratch + (long long)slot * gj_scratch_stride(nmax);
 }
-__device__ __forceinline__ double* gj_P(double* sc, int step) { return sc + (step & 1) * kGJ * kGJ; }
-__device__ __forceinline__ double* gj_cvec(double* sc, int step, int nmax) {
+template <class T>
+__device__ __forceinline__ T* gj_P(T* sc, int step) { return sc + (step & 1) * kGJ * kGJ; }
+template <class T>
+__device__ __forceinline__ T* gj_cvec(T* sc, int step, int nmax) {
     return sc + kGJScratchHead + (long long)(step & 1) * nmax * kGJ;
 }
-__device__ __forceinline__ double* gj_uvec(double* sc, int step, int nmax) {
+template <class T>
+__device__ __forceinline__ T* gj_uvec(T* sc, int step, int nmax) {
     return sc + kGJScratchHead + 2LL * nmax * kGJ + (long long)(step & 1) * nmax * kGJ;
 }
-__device__ __forceinline__ unsigned int* gj_flag(double* sc, int nmax) {
+template <class T>
+__device__ __forceinline__ unsigned int* gj_flag(T* sc, int nmax) {
     return reinterpret_cast<unsigned int*>(sc + kGJScratchHead + 4LL * nmax * kGJ);
 }
 // number of tile items so far that wrote c of a next block (monotonic over
 // the steps: each step has one per tile row of the node)
-__device__ __forceinline__ unsigned int* gj_cready(double* sc, int nmax) { return gj_flag(sc, nmax) + 1; }
+template <class T>
+__device__ __forceinline__ unsigned int* gj_cready(T* sc, int nmax) { return gj_flag(sc, nmax) + 1; }
 
+template <class T>
 struct GJSmem {
-    double Cr[kGJTile][kGJ + 1];    // c of the tile's rows
-    double Ur[kGJTile][kGJ + 1];    // u of the tile's rows
-    double Uc[kGJTile][kGJ + 1];    // u of the tile's columns
-    double Ps[kGJ][kGJ + 1];        // a diagonal block being inverted, or a P
-    double Pt[kGJ][kGJ + 1];        // second buffer of the inversion
-    double rp[2];                   // pivot reciprocals (by step parity)
-    double tt[2];                   // squared subdiagonal entry of the next pivot
+    T Cr[kGJTile][kGJ + 1];    // c of the tile's rows
+    T Ur[kGJTile][kGJ + 1];    // u of the tile's rows
+    T Uc[kGJTile][kGJ + 1];    // u of the tile's columns
+    T Ps[kGJ][kGJ + 1];        // a diagonal block being inverted, or a P
+    T Pt[kGJ][kGJ + 1];        // second buffer of the inversion
+    T rp[2];                   // pivot reciprocals (by step parity)
+    T tt[2];                   // squared subdiagonal entry of the next pivot
 };
 
 // Inverse of a symmetric kGJ x kGJ block held in shared memory (lower
@@ -380,8 +406,8 @@ struct GJSmem {
 // the fresh entries to warp 0.  On return Ps holds the full inverse.
 // d_rows: rows of the block in the d part (positive pivots expected).
 // Returns false (lane 0 of warp 0) on a pivot of the wrong sign or size.
-__device__ bool gj_invert_block(double (*Ps)[kGJ + 1], double (*Pt)[kGJ + 1], double* s_rp, double* s_tt,
-                                int nb, int d_rows) {
+template <class T>
+__device__ bool gj_invert_block(T (*Ps)[kGJ + 1], T (*Pt)[kGJ + 1], T* s_rp, T* s_tt, int nb, int d_rows) {
     constexpr int kTri = kGJ * (kGJ + 1) / 2;
     static_assert(kTri <= 5 * 32 && (kGJ % 2) == 0, "five update warps; even number of steps");
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -394,23 +420,23 @@ __device__ bool gj_invert_block(double (*Ps)[kGJ + 1], double (*Pt)[kGJ + 1], do
         while (r * (r + 1) / 2 > rank) --r;
         c = rank - r * (r + 1) / 2;
     }
-    double (*cur)[kGJ + 1] = Ps;      // entries after step kk - 2 (the input for kk <= 1)
-    double (*nxt)[kGJ + 1] = Pt;
-    double rp_prev = 0.0;
+    T (*cur)[kGJ + 1] = Ps;      // entries after step kk - 2 (the input for kk <= 1)
+    T (*nxt)[kGJ + 1] = Pt;
+    T rp_prev = 0;
     bool ok = true;
     for (int kk = 0; kk <= kGJ; ++kk) {
         if (warp == 0) {
             if (kk < kGJ) {
-                double p;
+                T p;
                 if (kk == 0) {
                     p = cur[0][0];
                 } else if (kk == 1) {
-                    const double a = cur[1][0];
+                    const T a = cur[1][0];
                     p = fma(-(a * a), rp_prev, cur[1][1]);
                 } else {
                     p = fma(-s_tt[kk & 1], rp_prev, cur[kk][kk]);
                 }
-                const double rp = rcp_nr(p);
+                const T rp = rcp_nr(p);
                 if (lane == 0) {
                     s_rp[kk & 1] = rp;
                     if (kk < nb && !pivot_ok_bits(p, kk < d_rows)) ok = false;
@@ -421,17 +447,17 @@ __device__ bool gj_invert_block(double (*Ps)[kGJ + 1], double (*Pt)[kGJ + 1], do
             // step s = kk - 1: B'(r, c) = B(r, c) - B(r, s) B(s, c) r_s, with
             // the pivot row scaled by r_s, the pivot column by -r_s
             const int s = kk - 1;
-            const double rp = s_rp[s & 1];
-            const double xa = (r == s) ? 1.0 : (r > s ? neg_bits(cur[r][s]) : cur[s][r]);   // -B(r, s)
-            const double xb = (c == s) ? 1.0 : (c < s ? cur[s][c] : cur[c][s]);             //  B(s, c)
-            const double y = (r == s || c == s) ? 0.0 : cur[r][c];
-            const double nv = fma(xa * xb, rp, y);
+            const T rp = s_rp[s & 1];
+            const T xa = (r == s) ? (T)1 : (r > s ? neg_bits(cur[r][s]) : cur[s][r]);   // -B(r, s)
+            const T xb = (c == s) ? (T)1 : (c < s ? cur[s][c] : cur[c][s]);             //  B(s, c)
+            const T y = (r == s || c == s) ? (T)0 : cur[r][c];
+            const T nv = fma(xa * xb, rp, y);
             nxt[r][c] = nv;
             if (r == kk + 1 && c == kk) s_tt[(kk + 1) & 1] = nv * nv;
         }
         __syncthreads();
         if (kk >= 1) {
-            double (*t)[kGJ + 1] = cur;
+            T (*t)[kGJ + 1] = cur;
             cur = nxt;
             nxt = t;
         }
@@ -457,20 +483,21 @@ __device__ bool gj_invert_block(double (*Ps)[kGJ + 1], double (*Pt)[kGJ + 1], do
 // step's c for their indices and, once P of K1 is published, its u.
 
 // c and u of block 0 for one (node, chunk of kGJTile indices x >= nb0).
-__device__ void gj_first_cu_item(const DevView& v, const MergeDesc& D, int slot, int x0, double* scratch, int nmax,
-                                 GJSmem& S) {
+template <class T>
+__device__ void gj_first_cu_item(const DevView& v, const MergeDesc& D, int slot, int x0, T* scratch, int nmax,
+                                 GJSmem<T>& S) {
     const int N = 2 * D.g;
     const int nb = min(kGJ, N);
-    const double* A = v.W + D.W_off;
-    double* sc = gj_scratch(scratch, slot, nmax);
-    const double* P0 = gj_P(sc, 0);
-    double* cv = gj_cvec(sc, 0, nmax);
-    double* uv = gj_uvec(sc, 0, nmax);
+    const T* A = gj_work<T>(v) + D.W_off;
+    T* sc = gj_scratch(scratch, slot, nmax);
+    const T* P0 = gj_P(sc, 0);
+    T* cv = gj_cvec(sc, 0, nmax);
+    T* uv = gj_uvec(sc, 0, nmax);
     const int tid = threadIdx.x;
-    for (int idx = tid; idx < kGJ * kGJ; idx += 256) S.Ps[idx / kGJ][idx % kGJ] = __ldcg(P0 + idx);
+    for (int idx = tid; idx < kGJ * kGJ; idx += 256) S.Ps[idx / kGJ][idx % kGJ] = ldcg(P0 + idx);
     for (int idx = tid; idx < kGJTile * kGJ; idx += 256) {
         const int xl = idx % kGJTile, cc = idx / kGJTile, x = x0 + xl;
-        const double c = (x < N && x >= nb && cc < nb) ? __ldcg(A + (long long)cc * N + x) : 0.0;
+        const T c = (x < N && x >= nb && cc < nb) ? ldcg(A + (long long)cc * N + x) : (T)0;
         S.Cr[xl][cc] = c;
         if (x < N && x >= nb) cv[(long long)x * kGJ + cc] = c;
     }
@@ -478,7 +505,7 @@ __device__ void gj_first_cu_item(const DevView& v, const MergeDesc& D, int slot,
     for (int idx = tid; idx < kGJTile * kGJ; idx += 256) {
         const int xl = idx / kGJ, rr = idx % kGJ, x = x0 + xl;
         if (x >= N || x < nb) continue;
-        double a0 = 0.0, a1 = 0.0;
+        T a0 = 0, a1 = 0;
 #pragma unroll
         for (int cc = 0; cc < kGJ; cc += 2) {
             a0 = fma(S.Ps[rr][cc], S.Cr[xl][cc], a0);
@@ -521,45 +548,46 @@ __device__ bool wait_flag(const unsigned int* flag, unsigned int value, int* sta
 // of the update above (entries r >= c; the block K1 x K1 is left to
 // gj_next_diag_item), and c of step k + 1 for its indices when it holds K1
 // as rows or columns (then the node's c counter is raised).
+template <class T>
 __device__ void gj_step_item(const DevView& v, const MergeDesc& D, int slot, int ti, int tj, int step,
-                             double* scratch, int nmax, GJSmem& S) {
+                             T* scratch, int nmax, GJSmem<T>& S) {
     const int N = 2 * D.g;
     const int k0 = step * kGJ, nb = min(kGJ, N - k0);
     const int k1 = k0 + kGJ, nb1 = k1 < N ? min(kGJ, N - k1) : 0;
     const int r0 = ti * kGJTile, c0 = tj * kGJTile;
-    double* A = v.W + D.W_off;
-    double* sc = gj_scratch(scratch, slot, nmax);
-    const double* Pg = gj_P(sc, step);
-    const double* cv = gj_cvec(sc, step, nmax);
-    const double* uv = gj_uvec(sc, step, nmax);
-    double* cn = gj_cvec(sc, step + 1, nmax);
+    T* A = gj_work<T>(v) + D.W_off;
+    T* sc = gj_scratch(scratch, slot, nmax);
+    const T* Pg = gj_P(sc, step);
+    const T* cv = gj_cvec(sc, step, nmax);
+    const T* uv = gj_uvec(sc, step, nmax);
+    T* cn = gj_cvec(sc, step + 1, nmax);
     const int tid = threadIdx.x;
     const int tr = (tid % 16) * 2, tc = (tid / 16) * 2;
     // the tile's current entries, in flight while c and u are staged
-    double old[2][2];
+    T old[2][2];
 #pragma unroll
     for (int b = 0; b < 2; ++b) {
         const int j = c0 + tc + b;
 #pragma unroll
         for (int a = 0; a < 2; ++a) {
             const int i = r0 + tr + a;
-            old[a][b] = (j < N && i < N && i >= j) ? __ldcg(A + (long long)j * N + i) : 0.0;
+            old[a][b] = (j < N && i < N && i >= j) ? ldcg(A + (long long)j * N + i) : (T)0;
         }
     }
     for (int idx = tid; idx < kGJTile * kGJ; idx += 256) {
         const int xl = idx / kGJ, cc = idx % kGJ;
         const int xi = r0 + xl, xj = c0 + xl;
         const bool okc = cc < nb;
-        S.Cr[xl][cc] = (okc && xi < N && (xi < k0 || xi >= k0 + nb)) ? __ldcg(cv + (long long)xi * kGJ + cc) : 0.0;
-        S.Ur[xl][cc] = (okc && xi < N && (xi < k0 || xi >= k0 + nb)) ? __ldcg(uv + (long long)xi * kGJ + cc) : 0.0;
-        S.Uc[xl][cc] = (okc && xj < N && (xj < k0 || xj >= k0 + nb)) ? __ldcg(uv + (long long)xj * kGJ + cc) : 0.0;
+        S.Cr[xl][cc] = (okc && xi < N && (xi < k0 || xi >= k0 + nb)) ? ldcg(cv + (long long)xi * kGJ + cc) : (T)0;
+        S.Ur[xl][cc] = (okc && xi < N && (xi < k0 || xi >= k0 + nb)) ? ldcg(uv + (long long)xi * kGJ + cc) : (T)0;
+        S.Uc[xl][cc] = (okc && xj < N && (xj < k0 || xj >= k0 + nb)) ? ldcg(uv + (long long)xj * kGJ + cc) : (T)0;
     }
     __syncthreads();
-    double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+    T acc[2][2] = {{0, 0}, {0, 0}};
 #pragma unroll
     for (int cc = 0; cc < kGJ; ++cc) {
-        const double l0 = S.Cr[tr][cc], l1 = S.Cr[tr + 1][cc];
-        const double u0 = S.Uc[tc][cc], u1 = S.Uc[tc + 1][cc];
+        const T l0 = S.Cr[tr][cc], l1 = S.Cr[tr + 1][cc];
+        const T u0 = S.Uc[tc][cc], u1 = S.Uc[tc + 1][cc];
         acc[0][0] = fma(l0, u0, acc[0][0]);
         acc[0][1] = fma(l0, u1, acc[0][1]);
         acc[1][0] = fma(l1, u0, acc[1][0]);
@@ -573,16 +601,16 @@ __device__ void gj_step_item(const DevView& v, const MergeDesc& D, int slot, int
         if (j >= N) continue;
         const bool jK = j >= k0 && j < k0 + nb;
         const bool jK1 = j >= k1 && j < k1 + nb1;
-        double* col = A + (long long)j * N;
+        T* col = A + (long long)j * N;
 #pragma unroll
         for (int a = 0; a < 2; ++a) {
             const int i = r0 + tr + a;
             if (i >= N || i < j) continue;
             const bool iK = i >= k0 && i < k0 + nb;
             const bool iK1 = i >= k1 && i < k1 + nb1;
-            double val;
+            T val;
             if (iK && jK) {
-                val = __ldcg(Pg + (i - k0) * kGJ + (j - k0));
+                val = ldcg(Pg + (i - k0) * kGJ + (j - k0));
             } else if (jK) {
                 val = neg_bits(S.Ur[tr + a][j - k0]);     // block column, i > K
             } else if (iK) {
@@ -612,15 +640,16 @@ __device__ void gj_step_item(const DevView& v, const MergeDesc& D, int slot, int
 // indices, two threads per output entry, each summing half of the kGJ
 // products.  Returns false when a wait timed out.
 constexpr int kUChunk = 8;
+template <class T>
 __device__ bool gj_u_item(const DevView& v, const MergeDesc& D, int slot, int x0, int len, int step,
-                          double* scratch, int nmax, GJSmem& S) {
+                          T* scratch, int nmax, GJSmem<T>& S) {
     const int N = 2 * D.g;
     const int k1 = (step + 1) * kGJ, nb1 = min(kGJ, N - k1);
     const int tiles = (N + kGJTile - 1) / kGJTile;
-    double* sc = gj_scratch(scratch, slot, nmax);
-    const double* Pn = gj_P(sc, step + 1);
-    const double* cn = gj_cvec(sc, step + 1, nmax);
-    double* un = gj_uvec(sc, step + 1, nmax);
+    T* sc = gj_scratch(scratch, slot, nmax);
+    const T* Pn = gj_P(sc, step + 1);
+    const T* cn = gj_cvec(sc, step + 1, nmax);
+    T* un = gj_uvec(sc, step + 1, nmax);
     const int tid = threadIdx.x;
     static_assert(kUChunk * kGJ * 2 == 256 && kUChunk <= kGJTile, "two threads per output");
     const int o = tid >> 1, half = tid & 1;
@@ -632,23 +661,23 @@ __device__ bool gj_u_item(const DevView& v, const MergeDesc& D, int slot, int x0
         for (int idx = tid; idx < kUChunk * kGJ; idx += 256) {
             const int yl = idx / kGJ, cc = idx % kGJ, y = xs + yl;
             const bool ok = y < N && (y < k1 || y >= k1 + nb1) && cc < nb1;
-            S.Cr[yl][cc] = ok ? __ldcg(cn + (long long)y * kGJ + cc) : 0.0;
+            S.Cr[yl][cc] = ok ? ldcg(cn + (long long)y * kGJ + cc) : (T)0;
         }
     };
     stage_c(x0);
     if (!wait_flag(gj_flag(sc, nmax), (unsigned int)(step + 1), v.status, v.spin_limit)) return false;
-    for (int idx = tid; idx < kGJ * kGJ; idx += 256) S.Ps[idx / kGJ][idx % kGJ] = __ldcg(Pn + idx);
+    for (int idx = tid; idx < kGJ * kGJ; idx += 256) S.Ps[idx / kGJ][idx % kGJ] = ldcg(Pn + idx);
     for (int xs = x0; xs < x0 + len; xs += kUChunk) {
         if (xs != x0) stage_c(xs);
         __syncthreads();
         const int x = xs + xl;
-        double a0 = 0.0, a1 = 0.0;
+        T a0 = 0, a1 = 0;
 #pragma unroll
         for (int cc = half * (kGJ / 2); cc < (half + 1) * (kGJ / 2); cc += 2) {
             a0 = fma(S.Ps[rr][cc], S.Cr[xl][cc], a0);
             a1 = fma(S.Ps[rr][cc + 1], S.Cr[xl][cc + 1], a1);
         }
-        double sum = a0 + a1;
+        T sum = a0 + a1;
         sum += __shfl_xor_sync(0xffffffffu, sum, 1);
         if (half == 0 && x < N && (x < k1 || x >= k1 + nb1) && rr < nb1) un[(long long)x * kGJ + rr] = sum;
         __syncthreads();
@@ -661,40 +690,41 @@ __device__ bool gj_u_item(const DevView& v, const MergeDesc& D, int slot, int x0
 // inverse into the P buffer of step k + 1, then the node's flag is raised to
 // k + 1.  Runs before any tile item of its CTA.  Returns false on a bad
 // pivot.
-__device__ bool gj_next_diag_item(const DevView& v, const MergeDesc& D, int slot, int step, double* scratch,
-                                  int nmax, GJSmem& S) {
+template <class T>
+__device__ bool gj_next_diag_item(const DevView& v, const MergeDesc& D, int slot, int step, T* scratch,
+                                  int nmax, GJSmem<T>& S) {
     const int N = 2 * D.g;
     const int k0 = step * kGJ, nb = min(kGJ, N - k0);
     const int k1 = k0 + kGJ, nb1 = min(kGJ, N - k1);
-    const double* A = v.W + D.W_off;
-    double* sc = gj_scratch(scratch, slot, nmax);
-    const double* cv = gj_cvec(sc, step, nmax);
-    const double* uv = gj_uvec(sc, step, nmax);
+    const T* A = gj_work<T>(v) + D.W_off;
+    T* sc = gj_scratch(scratch, slot, nmax);
+    const T* cv = gj_cvec(sc, step, nmax);
+    const T* uv = gj_uvec(sc, step, nmax);
     const int tid = threadIdx.x;
     for (int idx = tid; idx < kGJ * kGJ; idx += 256) {
         const int xl = idx / kGJ, cc = idx % kGJ;
         const bool ok = xl < nb1 && cc < nb;
-        S.Cr[xl][cc] = ok ? __ldcg(cv + (long long)(k1 + xl) * kGJ + cc) : 0.0;
-        S.Uc[xl][cc] = ok ? __ldcg(uv + (long long)(k1 + xl) * kGJ + cc) : 0.0;
+        S.Cr[xl][cc] = ok ? ldcg(cv + (long long)(k1 + xl) * kGJ + cc) : (T)0;
+        S.Uc[xl][cc] = ok ? ldcg(uv + (long long)(k1 + xl) * kGJ + cc) : (T)0;
     }
     __syncthreads();
     for (int idx = tid; idx < kGJ * kGJ; idx += 256) {
         const int pr = idx / kGJ, pc = idx % kGJ;
-        double val = (pr == pc) ? 1.0 : 0.0;
+        T val = (pr == pc) ? (T)1 : (T)0;
         if (pr < nb1 && pc < nb1 && pr >= pc) {
-            double a0 = 0.0, a1 = 0.0;
+            T a0 = 0, a1 = 0;
 #pragma unroll
             for (int cc = 0; cc < kGJ; cc += 2) {
                 a0 = fma(S.Cr[pr][cc], S.Uc[pc][cc], a0);
                 a1 = fma(S.Cr[pr][cc + 1], S.Uc[pc][cc + 1], a1);
             }
-            val = __ldcg(A + (long long)(k1 + pc) * N + k1 + pr) - (a0 + a1);
+            val = ldcg(A + (long long)(k1 + pc) * N + k1 + pr) - (a0 + a1);
         }
         if (pr >= pc) S.Ps[pr][pc] = val;
     }
     __syncthreads();
     const bool ok = gj_invert_block(S.Ps, S.Pt, S.rp, S.tt, nb1, D.g - k1);
-    double* Pn = gj_P(sc, step + 1);
+    T* Pn = gj_P(sc, step + 1);
     for (int idx = tid; idx < kGJ * kGJ; idx += 256) Pn[idx] = S.Ps[idx / kGJ][idx % kGJ];
     __threadfence();
     __syncthreads();
@@ -768,42 +798,47 @@ __device__ __forceinline__ void gj_lower_tile(int r, int tiles, int tk, int& ti,
 // doubles).  A CTA may take several items in a row (levels with more nodes
 // than CTAs): the closing barrier keeps the next item's staging off scl
 // until every thread is done with it.
+template <class T>
 __device__ void form_item(const DevView& v, const MergeDesc& D, long long e0, long long e1, double* scl,
                           double* red) {
     const NodeRefs N = node_refs(v, D);
     const int g = N.g, g2 = N.g2;
     const double sum = stage_gamma_scalings(v, D, scl, red);
     const double inv_sum = (D.pinned && sum > 0.0) ? 1.0 / sum : 0.0;
-    double* T = v.W + D.W_off;
+    T* Tm = gj_work<T>(v) + D.W_off;
     for (long long idx = e0 + threadIdx.x; idx < e1; idx += 256) {
         int r, c;
         udivmod(idx, g2, c, r);
         const int i = r < g ? r : r - g, j = c < g ? c : c - g;
-        T[idx] = t_entry(N, r, c, scl[g + i], scl[g + j], scl[i], scl[j], inv_sum);
+        Tm[idx] = (T)t_entry(N, r, c, scl[g + i], scl[g + j], scl[i], scl[j], inv_sum);
     }
     __syncthreads();     // the CTA's next item restages scl
 }
 // T^-1 -> W = D^-1/2 Q T^-1 Q^T D^-1/2 in place for the 2 x 2 block patterns
 // (i, j), i, j < g, with pattern index in [e0, e1), by one CTA.
+// (The mixed form's FP32 levels read T^-1 from the FP32 work array and write
+// W in double; in FP64 the four entries are read and written in place.)
+template <class T>
 __device__ void backform_item(const DevView& v, const MergeDesc& D, long long e0, long long e1, double* scl,
                               double* red) {
     const int g = D.g, g2 = 2 * g;
     stage_gamma_scalings(v, D, scl, red);
     const double* sd = scl + g;
-    double* A = v.W + D.W_off;
+    const T* A = gj_work<T>(v) + D.W_off;
+    double* Wd = v.W + D.W_off;
     for (long long idx = e0 + threadIdx.x; idx < e1; idx += 256) {
         int i, j;
         udivmod(idx, g, j, i);
-        const double sc = 0.5 * sd[i] * sd[j];
-        double* dd = A + (long long)j * g2 + i;          // (d_i, d_j)
-        double* ds = A + (long long)(g + j) * g2 + i;    // (d_i, s_j)
-        double* sdp = A + (long long)j * g2 + g + i;     // (s_i, d_j)
-        double* ss = A + (long long)(g + j) * g2 + g + i;
-        const double zdd = __ldcg(dd), zds = __ldcg(ds), zsd = __ldcg(sdp), zss = __ldcg(ss);
-        *dd = (zdd - zds - zsd + zss) * sc;   // W(a_i, a_j)
-        *ds = (zss + zsd - zds - zdd) * sc;   // W(a_i, b_j)
-        *sdp = (zss + zds - zsd - zdd) * sc;  // W(b_i, a_j)
-        *ss = (zdd + zds + zsd + zss) * sc;   // W(b_i, b_j)
+        const long long odd = (long long)j * g2 + i;          // (d_i, d_j)
+        const long long ods = (long long)(g + j) * g2 + i;    // (d_i, s_j)
+        const long long osd = (long long)j * g2 + g + i;      // (s_i, d_j)
+        const long long oss = (long long)(g + j) * g2 + g + i;
+        const T zdd = ldcg(A + odd), zds = ldcg(A + ods), zsd = ldcg(A + osd), zss = ldcg(A + oss);
+        const T sc = (T)(0.5 * sd[i] * sd[j]);
+        Wd[odd] = (double)((zdd - zds - zsd + zss) * sc);   // W(a_i, a_j)
+        Wd[ods] = (double)((zss + zsd - zds - zdd) * sc);   // W(a_i, b_j)
+        Wd[osd] = (double)((zss + zds - zsd - zdd) * sc);   // W(b_i, a_j)
+        Wd[oss] = (double)((zdd + zds + zsd + zss) * sc);   // W(b_i, b_j)
     }
     __syncthreads();     // the CTA's next item restages scl
 }
@@ -823,9 +858,12 @@ __device__ __forceinline__ long long level_run(long long per_node, int count) {
 // their lower output tiles, the row / column tk ones leading, then the u
 // of the next step in chunks over all CTAs) with a grid barrier after each;
 // finally the lower triangle is mirrored so that W is stored in full.
-__global__ void __launch_bounds__(256) gj_sweep_kernel(DevView v, int first, int count, int nmax, double* scratch,
+// T: the arithmetic of the level (double; float for the FP32 levels of the
+// mixed form, which sweep the FP32 work array and write W in double).
+template <class T>
+__global__ void __launch_bounds__(256) gj_sweep_kernel(DevView v, int first, int count, int nmax, T* scratch,
                                                        unsigned int* counter) {
-    __shared__ GJSmem S;
+    __shared__ GJSmem<T> S;
     __shared__ int s_bad;
     __shared__ double red[8];
     extern __shared__ __align__(16) double scl[];           // 2g scalings (form / back-form)
@@ -846,22 +884,22 @@ __global__ void __launch_bounds__(256) gj_sweep_kernel(DevView v, int first, int
             const MergeDesc D = v.merges[first + q];
             const long long nT = 4LL * D.g * D.g;
             if (e0 >= nT) continue;                                  // uniform per CTA
-            form_item(v, D, e0, min(e0 + run, nT), scl, red);
+            form_item<T>(v, D, e0, min(e0 + run, nT), scl, red);
         }
     }
     if (!grid_barrier(counter, round, v.status, v.spin_limit)) return;
     for (int q = blockIdx.x; q < count; q += gridDim.x) {
         const MergeDesc D = v.merges[first + q];
         const int N = 2 * D.g, nb = min(kGJ, N);
-        const double* A = v.W + D.W_off;
+        const T* A = gj_work<T>(v) + D.W_off;
         for (int idx = tid; idx < kGJ * kGJ; idx += 256) {
             const int pr = idx % kGJ, pc = idx / kGJ;
-            S.Ps[pr][pc] = (pr < nb && pc < nb) ? __ldcg(A + (long long)pc * N + pr) : (pr == pc ? 1.0 : 0.0);
+            S.Ps[pr][pc] = (pr < nb && pc < nb) ? ldcg(A + (long long)pc * N + pr) : (pr == pc ? (T)1 : (T)0);
         }
         __syncthreads();
         if (!gj_invert_block(S.Ps, S.Pt, S.rp, S.tt, nb, D.g)) s_bad = 1;
-        double* sc = gj_scratch(scratch, q, nmax);
-        double* P0 = gj_P(sc, 0);
+        T* sc = gj_scratch(scratch, q, nmax);
+        T* P0 = gj_P(sc, 0);
         for (int idx = tid; idx < kGJ * kGJ; idx += 256) P0[idx] = S.Ps[idx / kGJ][idx % kGJ];
         if (tid == 0) {
             *gj_flag(sc, nmax) = 0u;
@@ -923,10 +961,10 @@ __global__ void __launch_bounds__(256) gj_sweep_kernel(DevView v, int first, int
         const MergeDesc D = v.merges[first + q];
         const int N = 2 * D.g;
         if (ti * kGJTile >= N) continue;
-        double* A = v.W + D.W_off;
+        T* A = gj_work<T>(v) + D.W_off;
         for (int idx = tid; idx < kGJTile * kGJTile; idx += 256) {
             const int i = ti * kGJTile + idx % kGJTile, j = tj * kGJTile + idx / kGJTile;
-            if (i < N && j < N && i > j) A[(long long)i * N + j] = __ldcg(A + (long long)j * N + i);
+            if (i < N && j < N && i > j) A[(long long)i * N + j] = ldcg(A + (long long)j * N + i);
         }
     }
     // T^-1 -> W of every node
@@ -940,7 +978,7 @@ __global__ void __launch_bounds__(256) gj_sweep_kernel(DevView v, int first, int
             const MergeDesc D = v.merges[first + q];
             const long long np = (long long)D.g * D.g;
             if (e0 >= np) continue;                                  // uniform per CTA
-            backform_item(v, D, e0, min(e0 + run, np), scl, red);
+            backform_item<T>(v, D, e0, min(e0 + run, np), scl, red);
         }
     }
     __syncthreads();
@@ -955,10 +993,12 @@ constexpr int kXColsOut = 16, kXChunk = 64;
 // XROWS rows x kXColsOut columns of X per CTA: 32 unless the level has
 // CTAs in great excess (then 64, fewer staged loads per product); with few
 // long rows per node the smaller CTAs keep more SMs busy.
-template <int XROWS>
+// F: the arithmetic (double; float for the FP32 levels of the mixed form,
+// which read W and the children's maps in double and write X in double).
+template <int XROWS, class F>
 __global__ void __launch_bounds__(256) merge_x_kernel(DevView v, int first) {
     constexpr int kXRows = XROWS, kQ = kXRows * kXColsOut / 256;   // outputs per thread
-    __shared__ double Cs[kXChunk][kXColsOut];
+    __shared__ F Cs[kXChunk][kXColsOut];
     const MergeDesc D = v.merges[first + blockIdx.x];
     const NodeRefs N = node_refs(v, D);
     const int g = N.g, g2 = N.g2, m = N.m;
@@ -969,9 +1009,9 @@ __global__ void __launch_bounds__(256) merge_x_kernel(DevView v, int first) {
     double* X = v.X + D.X_off;
     const int tid = threadIdx.x, rl = tid % kXRows, cg = tid / kXRows;   // column groups of kQ
     const int r = r0 + rl;
-    double acc[kQ];
+    F acc[kQ];
 #pragma unroll
-    for (int q = 0; q < kQ; ++q) acc[q] = 0.0;
+    for (int q = 0; q < kQ; ++q) acc[q] = 0;
     // columns of this CTA may straddle o1: treat the two halves separately
     for (int half = 0; half < 2; ++half) {
         const int jlo = half == 0 ? 0 : N.o1, jhi = half == 0 ? N.o1 : m;
@@ -986,13 +1026,13 @@ __global__ void __launch_bounds__(256) merge_x_kernel(DevView v, int first) {
                     c = half == 0 ? N.R1[N.gpos1[k0 + kk] * N.m1 + N.opos1[j]]
                                   : N.R2[N.gpos2[k0 + kk] * N.m2 + N.opos2[j - N.o1]];
                 }
-                Cs[kk][jj] = c;
+                Cs[kk][jj] = (F)c;
             }
             __syncthreads();
             if (r < g2) {
                 const double* wcol = W + (long long)(half * g + k0) * g2 + r;
                 for (int kk = 0; kk < kn; ++kk) {
-                    const double wv = wcol[(long long)kk * g2];
+                    const F wv = (F)wcol[(long long)kk * g2];
 #pragma unroll
                     for (int q = 0; q < kQ; ++q) acc[q] += wv * Cs[kk][cg * kQ + q];
                 }
@@ -1003,7 +1043,7 @@ __global__ void __launch_bounds__(256) merge_x_kernel(DevView v, int first) {
 #pragma unroll
         for (int q = 0; q < kQ; ++q) {
             const int j = j0 + cg * kQ + q;
-            if (j < m) X[(long long)j * g2 + r] = -acc[q];
+            if (j < m) X[(long long)j * g2 + r] = (double)(-acc[q]);
         }
     }
 }
@@ -1016,11 +1056,11 @@ __global__ void __launch_bounds__(256) merge_x_kernel(DevView v, int first) {
 // entry per thread) unless the level has tiles in great excess (then TS = 2,
 // 32 x 32 tiles, 2 x 2 per thread): with few nodes per height the small
 // tiles keep more SMs busy behind the long k loops.
-template <int TS>
+template <int TS, class F>
 __global__ void __launch_bounds__(256) merge_rupdate_kernel(DevView v, int first) {
     constexpr int kTile = 16 * TS;
-    __shared__ double Cs[kTile][kRTile + 1];         // Cs[row][k]
-    __shared__ double Xs[2][kRTile][kTile + 1];      // Xs[half][k][col]
+    __shared__ F Cs[kTile][kRTile + 1];         // Cs[row][k]
+    __shared__ F Xs[2][kRTile][kTile + 1];      // Xs[half][k][col]
     const MergeDesc D = v.merges[first + blockIdx.x];
     const NodeRefs N = node_refs(v, D);
     const int m = N.m, g = N.g, g2 = N.g2, o1 = N.o1;
@@ -1036,11 +1076,11 @@ __global__ void __launch_bounds__(256) merge_rupdate_kernel(DevView v, int first
     double* Rp = v.R + D.R_off;
     const int tid = threadIdx.x;
     const int tr = (tid % 16) * TS, tc = (tid / 16) * TS;
-    double acc[TS][TS];
+    F acc[TS][TS];
 #pragma unroll
     for (int a = 0; a < TS; ++a)
 #pragma unroll
-        for (int b = 0; b < TS; ++b) acc[a][b] = 0.0;
+        for (int b = 0; b < TS; ++b) acc[a][b] = 0;
     for (int k0 = 0; k0 < g; k0 += kRTile) {
         const int kn = min(kRTile, g - k0);
         __syncthreads();
@@ -1050,19 +1090,19 @@ __global__ void __launch_bounds__(256) merge_rupdate_kernel(DevView v, int first
             if (kk < kn && i < m)
                 c = i < o1 ? N.R1[N.opos1[i] * N.m1 + N.gpos1[k0 + kk]]
                            : N.R2[N.opos2[i - o1] * N.m2 + N.gpos2[k0 + kk]];
-            Cs[rr][kk] = c;
+            Cs[rr][kk] = (F)c;
         }
         for (int idx = tid; idx < 2 * kRTile * kTile; idx += 256) {
             const int half = idx / (kRTile * kTile), rem = idx % (kRTile * kTile);
             const int kk = rem % kRTile, jj = rem / kRTile, j = jt + jj;
-            Xs[half][kk][jj] = (kk < kn && j < m) ? X[(long long)j * g2 + half * g + k0 + kk] : 0.0;
+            Xs[half][kk][jj] = (kk < kn && j < m) ? (F)X[(long long)j * g2 + half * g + k0 + kk] : (F)0;
         }
         __syncthreads();
 #pragma unroll
         for (int a = 0; a < TS; ++a) {
             const int half = (i0 + tr + a) < o1 ? 0 : 1;
             for (int kk = 0; kk < kRTile; ++kk) {
-                const double cv = Cs[tr + a][kk];
+                const F cv = Cs[tr + a][kk];
 #pragma unroll
                 for (int b = 0; b < TS; ++b) acc[a][b] += cv * Xs[half][kk][tc + b];
             }
@@ -1077,7 +1117,7 @@ __global__ void __launch_bounds__(256) merge_rupdate_kernel(DevView v, int first
         for (int b = 0; b < TS; ++b) {
             const int j = jt + tc + b;
             if (j >= m || j > i) continue;
-            double val = acc[a][b];
+            double val = (double)acc[a][b];
             if (i < o1 && j < o1) val += row[N.opos1[j]];
             if (i >= o1 && j >= o1) val += row[N.opos2[j - o1]];
             Rp[(long long)i * m + j] = val;
@@ -1324,18 +1364,21 @@ struct HookScope {
     ~HookScope() { if (h.end) h.end(h.ctx, phase); }
 };
 
+template <class F>
 static cudaError_t launch_small(const DevView& v, int first, int count, int max_g2, int max_m, cudaStream_t s) {
     const int mstride = max_m | 1;          // odd: rows of B and X start in different banks
     const size_t sm = small_smem(max_g2, max_m);
-    cudaError_t e = cudaFuncSetAttribute(merge_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(merge_small_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kSmallSmemMax);
     if (e != cudaSuccess) return e;
-    merge_small_kernel<<<count, kSmallThreads, sm, s>>>(v, first, mstride);
+    merge_small_kernel<F><<<count, kSmallThreads, sm, s>>>(v, first, mstride);
     return cudaGetLastError();
 }
 
-cudaError_t launch_merge_build(const DevView& v, int first, int count, int max_g2, int max_m, double* scratch,
-                               void* barrier, cudaStream_t s, int* launches, const PhaseHook& hook) {
+template <class F>
+static cudaError_t launch_merge_build_t(const DevView& v, int first, int count, int max_g2, int max_m,
+                                        double* scratch, void* barrier, cudaStream_t s, int* launches,
+                                        const PhaseHook& hook) {
     if (count == 0) return cudaSuccess;
     cudaError_t e;
     // per call, so that every device the library runs on gets its own SM
@@ -1344,12 +1387,12 @@ cudaError_t launch_merge_build(const DevView& v, int first, int count, int max_g
     int sms = 0, dev = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(gj_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSweepSmemPad)) !=
-        cudaSuccess)
+    if ((e = cudaFuncSetAttribute(gj_sweep_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  kSweepSmemPad)) != cudaSuccess)
         return e;
     if (!merge_level_blocked(count, max_g2, max_m)) {
         HookScope hs(hook, kPhMergeSmall);
-        e = launch_small(v, first, count, max_g2, max_m, s);
+        e = launch_small<F>(v, first, count, max_g2, max_m, s);
         ++*launches;
         return e;
     }
@@ -1367,8 +1410,10 @@ cudaError_t launch_merge_build(const DevView& v, int first, int count, int max_g
         unsigned int* bar = reinterpret_cast<unsigned int*>(barrier);
         DevView vv = v;
         int f = first, c = count, n = max_g2;
-        void* args[] = {&vv, &f, &c, &n, &scratch, &bar};
-        e = cudaLaunchCooperativeKernel((const void*)gj_sweep_kernel, dim3(grid), dim3(256), args, kSweepSmemPad, s);
+        F* scr = reinterpret_cast<F*>(scratch);
+        void* args[] = {&vv, &f, &c, &n, &scr, &bar};
+        e = cudaLaunchCooperativeKernel((const void*)gj_sweep_kernel<F>, dim3(grid), dim3(256), args, kSweepSmemPad,
+                                        s);
         ++*launches;
         if (e != cudaSuccess) return e;
     }
@@ -1378,10 +1423,10 @@ cudaError_t launch_merge_build(const DevView& v, int first, int count, int max_g
             const int ct = (max_m + kXColsOut - 1) / kXColsOut;
             const int rt64 = (max_g2 + 63) / 64;
             if ((long long)count * rt64 * ct >= 64LL * sms) {
-                merge_x_kernel<64><<<dim3(count, rt64 * ct), 256, 0, s>>>(v, first);
+                merge_x_kernel<64, F><<<dim3(count, rt64 * ct), 256, 0, s>>>(v, first);
             } else {
                 const int rt32 = (max_g2 + 31) / 32;
-                merge_x_kernel<32><<<dim3(count, rt32 * ct), 256, 0, s>>>(v, first);
+                merge_x_kernel<32, F><<<dim3(count, rt32 * ct), 256, 0, s>>>(v, first);
             }
             ++*launches;
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -1389,15 +1434,22 @@ cudaError_t launch_merge_build(const DevView& v, int first, int count, int max_g
         HookScope hs(hook, kPhMergeR);
         const int rt32 = (max_m + 31) / 32;
         if ((long long)count * rt32 * (rt32 + 1) / 2 >= 64LL * sms) {
-            merge_rupdate_kernel<2><<<dim3(count, rt32 * (rt32 + 1) / 2), 256, 0, s>>>(v, first);
+            merge_rupdate_kernel<2, F><<<dim3(count, rt32 * (rt32 + 1) / 2), 256, 0, s>>>(v, first);
         } else {
             const int rt16 = (max_m + 15) / 16;
-            merge_rupdate_kernel<1><<<dim3(count, rt16 * (rt16 + 1) / 2), 256, 0, s>>>(v, first);
+            merge_rupdate_kernel<1, F><<<dim3(count, rt16 * (rt16 + 1) / 2), 256, 0, s>>>(v, first);
         }
         ++*launches;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+cudaError_t launch_merge_build(const DevView& v, int first, int count, int max_g2, int max_m, bool fp32,
+                               double* scratch, void* barrier, cudaStream_t s, int* launches, const PhaseHook& hook) {
+    if (fp32)
+        return launch_merge_build_t<float>(v, first, count, max_g2, max_m, scratch, barrier, s, launches, hook);
+    return launch_merge_build_t<double>(v, first, count, max_g2, max_m, scratch, barrier, s, launches, hook);
 }
 
 cudaError_t tree_grid(int* grid) {

@@ -374,8 +374,19 @@ int mrcm::cuda_status(cudaError_t e) {
     return MRCM_ERR_CUDA;
 }
 
+// Refinement steps of the mixed form by default: each step contracts the
+// error by about the condition of the FP32 leaf factors times the FP32
+// rounding unit, so three reach the FP64 rounding level on the workloads.
+constexpr int kMixedRefineDefault = 3;
+
+// Largest interface system 2g merged in FP32 by default in the mixed form:
+// the levels above stay FP64 (their conditioning grows with the contrast).
+constexpr int kMixedSplitDefault = 512;
+
 struct mrcm_ctx {
     Plan P;
+    int precision = MRCM_FP64;
+    int mixed_split = kMixedSplitDefault;
     cudaStream_t stream = nullptr;
     int device = 0;
     bool built = false;
@@ -618,7 +629,7 @@ int mrcm_plan_query(const mrcm_grid* g, const int sub_cells[3], const int seg_ce
 }
 
 static int setup_impl(mrcm_ctx* c, const mrcm_grid* g, const double* K_dev, const int sub[3],
-                      const int seg[3], double alpha, const int bc_type[6], void* stream) {
+                      const int seg[3], double alpha, const int bc_type[6], int precision, void* stream) {
     Plan& P = c->P;
     fill_plan_inputs(P, g, sub, seg, alpha, bc_type);
     c->stream = static_cast<cudaStream_t>(stream);
@@ -626,6 +637,9 @@ static int setup_impl(mrcm_ctx* c, const mrcm_grid* g, const double* K_dev, cons
     TRY(make_plan(P));
     if (P.pure_neumann && P.nleaf == 1) return MRCM_ERR_UNSUPPORTED;
     DevView& v = c->v;
+    v.mixed = precision == MRCM_MIXED ? 1 : 0;
+    c->precision = precision;
+    if (v.mixed) c->refine_steps = kMixedRefineDefault;
     v.nx = P.nx; v.ny = P.ny; v.hx = P.hx; v.hy = P.hy; v.alpha = P.alpha;
     for (int s = 0; s < 4; ++s) v.bc[s] = P.bc[s];
     v.nleaf = P.nleaf; v.nseg = P.nseg;
@@ -659,14 +673,18 @@ static int setup_impl(mrcm_ctx* c, const mrcm_grid* g, const double* K_dev, cons
     TRY(upload(c, &v.merges, P.merges));
     TRY(upload(c, &v.node_map, P.node_map));
     TRY(upload(c, &v.gamma_segs, P.gamma_segs));
-    TRY(dev_alloc(c, &v.leafL, P.nL));
-    TRY(dev_alloc(c, &v.leafZ, P.nZ));
+    // leaf factors in the precision of the form (FP32 in the mixed form)
+    TRY(dev_alloc(c, &v.leafL, v.mixed ? 1 : P.nL));
+    TRY(dev_alloc(c, &v.leafZ, v.mixed ? 1 : P.nZ));
+    TRY(dev_alloc(c, &v.leafL32, v.mixed ? P.nL : 1));
+    TRY(dev_alloc(c, &v.leafZ32, v.mixed ? P.nZ : 1));
     TRY(dev_alloc(c, &v.leafzb, P.nzb));
     TRY(dev_alloc(c, &v.R, P.nR));
     TRY(dev_alloc(c, &v.rbar, P.nr));
     TRY(dev_alloc(c, &v.lam, P.nr));
     TRY(dev_alloc(c, &v.X, P.nX));
     TRY(dev_alloc(c, &v.W, P.nW));
+    TRY(dev_alloc(c, &v.W32, v.mixed ? P.nW : 1));
     TRY(dev_alloc(c, &v.segP, P.nseg));
     TRY(dev_alloc(c, &v.segU, P.nseg));
     TRY(dev_alloc(c, &v.segP_lo, P.nseg));
@@ -723,11 +741,11 @@ int mrcm_setup(mrcm_ctx** out, const mrcm_grid* g, const double* K_dev, const in
     TRY(validate(g, sub_cells, seg_cells, bc_type));
     if (precision != MRCM_FP64 && precision != MRCM_MIXED && precision != MRCM_SURROGATE)
         return MRCM_ERR_INVALID_ARG;
-    if (precision != MRCM_FP64) return MRCM_ERR_UNSUPPORTED;
+    if (precision == MRCM_SURROGATE) return MRCM_ERR_UNSUPPORTED;
     if (!(alpha > 0) || !std::isfinite(alpha)) return MRCM_ERR_INVALID_ARG;
     mrcm_ctx* c = new (std::nothrow) mrcm_ctx();
     if (!c) return MRCM_ERR_OOM;
-    int rc = setup_impl(c, g, K_dev, sub_cells, seg_cells, alpha, bc_type, cuda_stream);
+    int rc = setup_impl(c, g, K_dev, sub_cells, seg_cells, alpha, bc_type, precision, cuda_stream);
     if (rc != MRCM_OK) {
         mrcm_destroy(c);
         return rc;
@@ -767,8 +785,9 @@ static int enqueue_build(mrcm_ctx* c, int& launches) {
     {
         const PhaseHook hook{c, phase_begin, phase_end};
         for (int h = 1; h <= P.height; ++h) {
+            const bool fp32 = v.mixed && P.level_max_g2[h - 1] <= c->mixed_split;
             TRYC(launch_merge_build(v, P.level_first[h - 1], P.level_count[h - 1], P.level_max_g2[h - 1],
-                                    P.level_max_m[h - 1], c->gj_scratch, c->gj_barrier, s, &launches,
+                                    P.level_max_m[h - 1], fp32, c->gj_scratch, c->gj_barrier, s, &launches,
                                     hook));
         }
     }
@@ -911,6 +930,20 @@ int mrcm_solve(mrcm_ctx* c, const double* q_dev, const double* bc_val_dev, doubl
     c->hist_count = c->refine_steps + (c->refine_check ? 1 : 0);
     TRY(read_status(c));
     c->solved = true;
+    return MRCM_OK;
+}
+
+int mrcm_set_mixed_split(mrcm_ctx* c, int max_g2_fp32) {
+    if (!c || max_g2_fp32 < 0) return MRCM_ERR_INVALID_ARG;
+    if (!c->v.mixed) return MRCM_ERR_UNSUPPORTED;
+    if (max_g2_fp32 == c->mixed_split) return MRCM_OK;
+    c->mixed_split = max_g2_fp32;
+    c->built = false;
+    c->solved = false;
+    // the captured build graph holds the old per-level choice
+    TRYC(cudaStreamSynchronize(c->stream));
+    if (c->build_exec) cudaGraphExecDestroy(c->build_exec);
+    c->build_exec = nullptr;
     return MRCM_OK;
 }
 

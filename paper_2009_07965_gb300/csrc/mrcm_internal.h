@@ -94,6 +94,9 @@ struct DevView {
     // workspace
     double* leafL;      // band factors
     double* leafZ;      // Z per leaf
+    float* leafL32;     // the same in FP32 (mixed precision: leaf work in FP32)
+    float* leafZ32;
+    int mixed;          // 1: leaf factors and the merges of FP32 levels in FP32
     double* leafzb;     // particular forward solves
     double* R;          // node maps (leaves and internal nodes)
     double* rbar;       // node particular fluxes
@@ -102,6 +105,7 @@ struct DevView {
     double* lam;        // node Robin data (top-down)
     double* X;
     double* W;          // explicit inverses of the interface matrices (W_off layout)
+    float* W32;         // FP32 work array of the mixed form's blocked levels (W_off layout)
     double* segP;       // refined interface unknowns P_t, U_t (high parts)
     double* segU;
     double* segP_lo;    // ... and low parts of the double-double state
@@ -205,6 +209,30 @@ __device__ __forceinline__ double neg_bits(double x) {
     return __hiloint2double(__double2hiint(x) ^ (int)0x80000000u, __double2loint(x));
 }
 __device__ __forceinline__ double dd_round(DD x) { return __dadd_rn(x.h, x.l); }
+// FP32 counterparts used by the mixed-precision instantiations of the leaf
+// and merge kernels: the IEEE reciprocal (a single instruction in FP32) and
+// the sign flip on the bit pattern.
+__device__ __forceinline__ float rcp_nr(float p) { return __frcp_rn(p); }
+__device__ __forceinline__ float neg_bits(float x) { return __int_as_float(__float_as_int(x) ^ (int)0x80000000u); }
+// positive and finite, tested on the bit pattern
+__device__ __forceinline__ bool positive_finite_bits(double x) {
+    const long long b = __double_as_longlong(x);
+    return b > 0 && b < 0x7ff0000000000000LL;
+}
+__device__ __forceinline__ bool positive_finite_bits(float x) {
+    const int b = __float_as_int(x);
+    return b > 0 && b < 0x7f800000;
+}
+// L2-only loads for either precision
+__device__ __forceinline__ float ldcg(const float* p) { return __ldcg(p); }
+__device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
+// the leaf factor arrays of either precision
+template <class T> __device__ __forceinline__ T* leaf_L(const DevView& v);
+template <> __device__ __forceinline__ double* leaf_L<double>(const DevView& v) { return v.leafL; }
+template <> __device__ __forceinline__ float* leaf_L<float>(const DevView& v) { return v.leafL32; }
+template <class T> __device__ __forceinline__ T* leaf_Z(const DevView& v);
+template <> __device__ __forceinline__ double* leaf_Z<double>(const DevView& v) { return v.leafZ; }
+template <> __device__ __forceinline__ float* leaf_Z<float>(const DevView& v) { return v.leafZ32; }
 
 // x-face (i, j) / y-face (i, j) lies on the skeleton
 __device__ __forceinline__ bool x_skeleton(const DevView& v, int i) {
@@ -260,8 +288,10 @@ struct PhaseHook {
 // one tree height of merges; scratch: merge_scratch_doubles(count, max_g2,
 // max_m) values; barrier: kMergeBarrierBytes of device memory (reset by the
 // call); *launches is increased by the number of kernels launched
-cudaError_t launch_merge_build(const DevView& v, int first, int count, int max_g2, int max_m, double* scratch,
-                               void* barrier, cudaStream_t s, int* launches, const PhaseHook& hook);
+// fp32: the mixed form's FP32 arithmetic for this level (T of the blocked
+// sweep in v.W32; W, X and R stored in double either way)
+cudaError_t launch_merge_build(const DevView& v, int first, int count, int max_g2, int max_m, bool fp32,
+                               double* scratch, void* barrier, cudaStream_t s, int* launches, const PhaseHook& hook);
 constexpr size_t kMergeBarrierBytes = 64;
 bool merge_level_blocked(int count, int max_g2, int max_m);
 size_t merge_scratch_doubles(int count, int max_g2, int max_m);

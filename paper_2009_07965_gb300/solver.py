@@ -8,17 +8,18 @@ class Solver:
     """Recursive MRCM solver for one grid / decomposition / alpha / BC types.
 
     K: (ny, nx) float64 CUDA tensor.  bc_type: (x-, x+, y-, y+).
+    precision: binding.MRCM_FP64 or binding.MRCM_MIXED.
     """
 
     def __init__(self, K, Lx=1.0, Ly=1.0, sub=(16, 16), seg=(4, 4), alpha=1.0,
-                 bc_type=(1, 1, 0, 0), stream=None):
+                 bc_type=(1, 1, 0, 0), stream=None, precision=B.MRCM_FP64):
         if not (K.is_cuda and K.dtype == torch.float64):
             raise TypeError("K must be a float64 CUDA tensor")
         self.ny, self.nx = K.shape
         self.stream = stream if stream is not None else torch.cuda.current_stream(K.device)
         self.device = K.device
         self.ctx = B.mrcm_setup((self.nx, self.ny), (Lx, Ly), K.contiguous(), sub, seg, alpha,
-                                bc_type, B.MRCM_FP64, self.stream.cuda_stream)
+                                bc_type, precision, self.stream.cuda_stream)
         dev = self.device
         self.p = torch.empty(self.ny, self.nx, dtype=torch.float64, device=dev)
         self.Fx = torch.empty(self.ny, self.nx + 1, dtype=torch.float64, device=dev)

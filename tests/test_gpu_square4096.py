@@ -1,0 +1,60 @@
+"""Parity at the full 4096^2 workload (the benchmark's field) against the
+oracle's stored solution.
+
+tests/golden/square4096_qfs_oracle.npz holds a seeded sample of the
+oracle's solution of inputs.config_4096() (CPU Recursive MRCM, refined with
+double-double residuals; written by tests/golden/make_square4096.py, which
+calls only the oracle): p, Fx, Fy at 20 000 entries each (uniform, plus the
+source corners), the one-sided skeleton fluxes at 10 000 faces per axis, and
+each full array's L2 norm.  The CUDA path runs in the benchmark's launch
+configuration (side stream, captured graphs) once refined and once as the
+paper's single pass; both must match the oracle to 1e-10 relative L2 over
+the samples, and the full arrays' norms to 1e-10.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import inputs
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+GOLDEN = os.path.join(HERE, "golden", "square4096_qfs_oracle.npz")
+TOL = 1e-10
+KEYS = ("p", "Fx", "Fy", "Fa_x", "Fb_x", "Fa_y", "Fb_y")
+
+
+def test_square4096_matches_the_oracle_samples(mrcm_lib):
+    import torch
+    import paper_2009_07965_gb300 as mr
+    g = np.load(GOLDEN)
+    prob = inputs.config_4096()
+    K = prob.K
+    # the same field as the oracle's, up to the rounding of the generator's
+    # FFT and exp on this machine
+    fp = np.array([K.sum(), (K * K).sum(), np.log(K).sum(), K.min(), K.max()])
+    assert np.allclose(fp, g["K_fingerprint"], rtol=1e-12, atol=0.0), (fp, g["K_fingerprint"])
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        s = mr.Solver(torch.from_numpy(K).cuda(), prob.Lx, prob.Ly, prob.sub, prob.seg, prob.alpha,
+                      prob.bc_type, stream=st)
+        q, bc = torch.from_numpy(prob.q).cuda(), torch.from_numpy(prob.bc_val).cuda()
+        s.build_basis()
+        errs = {}
+        for steps in (3, 0):
+            mr.mrcm_set_refinement(s.ctx, steps)
+            s.solve(q, bc, want_iface=True)
+            fa_x, fb_x, fa_y, fb_y = s.iface_parts()
+            out = dict(p=s.p, Fx=s.Fx, Fy=s.Fy, Fa_x=fa_x, Fb_x=fb_x, Fa_y=fa_y, Fb_y=fb_y)
+            out = {k: v.cpu().numpy() for k, v in out.items()}
+            for k in KEYS:
+                idx, ref = g[f"{k}_idx"], g[f"{k}_val"]
+                errs[(steps, k)] = float(np.linalg.norm(out[k].reshape(-1)[idx] - ref) / np.linalg.norm(ref))
+                norm_err = abs(np.linalg.norm(out[k]) - float(g[f"{k}_norm"])) / float(g[f"{k}_norm"])
+                errs[(steps, k, "norm")] = float(norm_err)
+        st.synchronize()
+        s.close()
+    bad = {k: e for k, e in errs.items() if not e <= TOL}
+    print("4096^2 rel errors vs oracle samples", errs)
+    assert not bad, bad

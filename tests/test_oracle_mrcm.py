@@ -221,3 +221,31 @@ def test_refined_one_face_segments_equal_fine():
     f, m = solve_fine(prob), solve_mrcm(prob, refine=2)
     for key in ("p", "Fx", "Fy"):
         assert rel(m[key], f[key]) < 1e-11
+
+
+def test_node_segments_from_children_match_the_box_definition():
+    # the recursion takes a node's outer segments from its children (their
+    # segments minus gamma); they must be the segments with exactly one side
+    # in the node's box, on a ragged grid with both split axes
+    from oracle.recursive import outer_segments
+    prob = inputs.darcy_problem(72, 52, sigma2=1.0, corr=0.2, seed=8, bc="left_right")
+    rm = RecursiveMRCM(prob)
+    stack, n = [rm.root], 0
+    while stack:
+        nd = stack.pop()
+        stack += nd.children
+        assert nd.segs == outer_segments(rm.dec, nd.box)
+        n += 1
+    assert n == 2 * len(rm.dec.leaves) - 1
+
+
+def test_leaf_map_mode_gives_the_same_solution():
+    # handing the per-leaf work to a map function (a process pool's at large
+    # sizes) changes no arithmetic: the same refined solution
+    from oracle.recursive import leaf_worker_init
+    prob = inputs.darcy_problem(48, 40, sigma2=2.0, corr=0.1, seed=12, bc="quarter_five_spot")
+    a = solve_recursive(prob, refine=2)
+    leaf_worker_init(prob)
+    b = solve_recursive(prob, refine=2, leaf_map=map)
+    for k in ("p", "Fx", "Fy", "Fa_x", "Fb_y"):
+        assert rel(b[k], a[k]) < 1e-13, k
