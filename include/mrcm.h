@@ -274,6 +274,25 @@ int mrcm_set_wait_limit(mrcm_ctx* ctx, long long polls);
  * context), MRCM_ERR_CUDA.
  */
 int mrcm_set_mixed_split(mrcm_ctx* ctx, int max_g2_fp32);
+
+/*
+ * mrcm_autotune -- picks the launch shapes of every blocked merge level by
+ * timing them on this device: CTAs per SM of the cooperative Gauss-Jordan
+ * sweep (1 or 2), rows of X per CTA (32 or 64), side of an R tile (16 or
+ * 32); each candidate is run `reps` times (1..100) on the context's stream
+ * and the fastest kept per launch and tree height.  Every shape computes the
+ * same numbers, so the basis stays valid; later builds use the choices (the
+ * captured build graph is dropped).  The paper has no counterpart.  Needs a
+ * built basis (MRCM_ERR_NOT_BUILT otherwise).  Errors: MRCM_ERR_INVALID_ARG,
+ * MRCM_ERR_NOT_BUILT, MRCM_ERR_TIMEOUT, MRCM_ERR_CUDA.
+ *
+ * mrcm_tune_info -- the choices for tree height `height` (1 = the leaves'
+ * parents): out[0] CTAs per SM of the sweep, out[1] X rows, out[2] R tile;
+ * 0 where the built-in heuristic applies (before mrcm_autotune, and on
+ * heights merged by the small-system kernel).
+ */
+int mrcm_autotune(mrcm_ctx* ctx, int reps);
+int mrcm_tune_info(const mrcm_ctx* ctx, int height, int out[3]);
 int mrcm_residual_history(mrcm_ctx* ctx, double* out, int cap);
 
 /*
@@ -418,7 +437,8 @@ enum {
     MRCM_PROBE_DMMA = 1,   /* FP64 mma.sync m8n8k4                           */
     MRCM_PROBE_FFMA = 2,   /* FP32 fused multiply-add                        */
     MRCM_PROBE_TF32 = 3,   /* mma.sync m16n8k8, TF32 inputs, FP32 accumulate */
-    MRCM_PROBE_BF16 = 4    /* mma.sync m16n8k16, BF16 inputs, FP32 accumulate */
+    MRCM_PROBE_BF16 = 4,   /* mma.sync m16n8k16, BF16 inputs, FP32 accumulate */
+    MRCM_PROBE_DFMA_DMMA = 5  /* half the warps FP64 FMA, half FP64 MMA      */
 };
 int mrcm_probe_peak(int kind, double seconds, double* tflops, void* cuda_stream);
 

@@ -27,7 +27,7 @@ EXPORTS = ["mrcm_setup", "mrcm_plan_query", "mrcm_set_permeability", "mrcm_build
            "mrcm_last_cuda_error",
            "mrcm_merge_pair_noalloc", "mrcm_set_refinement", "mrcm_residual_history", "mrcm_phase_flops",
            "mrcm_group_times", "mrcm_check_reciprocal", "mrcm_set_wait_limit",
-           "mrcm_probe_peak", "mrcm_set_mixed_split"]
+           "mrcm_probe_peak", "mrcm_set_mixed_split", "mrcm_autotune", "mrcm_tune_info"]
 PHASES = ["coef", "leaf_build", "merge_small", "gj_sweep", "merge_form", "merge_x", "merge_r",
           "leaf_particular", "tree_up", "tree_down", "leaf_pressure", "residual", "finish"]
 # kernel family behind each phase (for reports)
@@ -103,6 +103,10 @@ def _lib():
         lib.mrcm_check_reciprocal.restype = I
         lib.mrcm_set_refinement.argtypes = [P, I, I]
         lib.mrcm_set_refinement.restype = I
+        lib.mrcm_autotune.argtypes = [P, I]
+        lib.mrcm_autotune.restype = I
+        lib.mrcm_tune_info.argtypes = [P, I, IP]
+        lib.mrcm_tune_info.restype = I
         lib.mrcm_set_mixed_split.argtypes = [P, I]
         lib.mrcm_set_mixed_split.restype = I
         lib.mrcm_probe_peak.argtypes = [I, D, ctypes.POINTER(ctypes.c_double), P]
@@ -256,7 +260,7 @@ def mrcm_set_refinement(ctx, steps, check=False):
     _check(_lib().mrcm_set_refinement(ctx, int(steps), 1 if check else 0), "mrcm_set_refinement")
 
 
-PROBES = dict(DFMA=0, DMMA=1, FFMA=2, TF32=3, BF16=4)
+PROBES = dict(DFMA=0, DMMA=1, FFMA=2, TF32=3, BF16=4, DFMA_DMMA=5)
 
 
 def mrcm_probe_peak(kind, seconds=0.3, stream=None):
@@ -265,6 +269,16 @@ def mrcm_probe_peak(kind, seconds=0.3, stream=None):
     _check(_lib().mrcm_probe_peak(PROBES[kind] if isinstance(kind, str) else int(kind), float(seconds),
                                   ctypes.byref(out), stream), "mrcm_probe_peak")
     return out.value
+
+
+def mrcm_autotune(ctx, reps=3):
+    _check(_lib().mrcm_autotune(ctx, int(reps)), "mrcm_autotune")
+
+
+def mrcm_tune_info(ctx, height):
+    out = (ctypes.c_int * 3)()
+    _check(_lib().mrcm_tune_info(ctx, int(height), out), "mrcm_tune_info")
+    return dict(sweep_per_sm=out[0], x_rows=out[1], r_tile=out[2])
 
 
 def mrcm_set_mixed_split(ctx, max_g2_fp32):

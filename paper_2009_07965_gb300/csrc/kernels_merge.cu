@@ -1375,18 +1375,88 @@ static cudaError_t launch_small(const DevView& v, int first, int count, int max_
     return cudaGetLastError();
 }
 
+// The three launches of a blocked level, each with its tuning choice (0:
+// the heuristic below).  Every choice computes the same numbers: a tile,
+// an X block or an R tile is formed by the same thread arithmetic whichever
+// CTA shape runs it, so the tuner may pick any of them.
+template <class F>
+static cudaError_t sweep_launch(const DevView& v, int first, int count, int max_g2, double* scratch, void* barrier,
+                                int sms, int per_sm, cudaStream_t s) {
+    cudaError_t e;
+    // Default one CTA per SM (the padded dynamic shared memory keeps a
+    // second one off): the CTAs that invert the next diagonal blocks, which
+    // lie on the sequential chain of the sweep, then own their SM's FP64
+    // pipe.  Two per SM let one CTA's staging loads overlap the other's
+    // tile updates, which pays where the tiles of a step outnumber the CTAs
+    // many times over (the largest systems).
+    size_t dyn = kSweepSmemPad;
+    if (per_sm >= 2) {
+        dyn = std::max<size_t>((size_t)max_g2 * sizeof(double), 16);
+        int fit = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, gj_sweep_kernel<F>, 256, dyn)) != cudaSuccess)
+            return e;
+        if (fit < 2) {
+            per_sm = 1;
+            dyn = kSweepSmemPad;
+        }
+    }
+    const int tiles = (max_g2 + kGJTile - 1) / kGJTile;
+    const long long items = (long long)count * (1 + tiles * (tiles + 1) / 2);
+    int grid = (int)std::min<long long>(items, (long long)sms * per_sm);
+    grid = grid < 1 ? 1 : grid;
+    if ((e = cudaMemsetAsync(barrier, 0, sizeof(unsigned int), s)) != cudaSuccess) return e;
+    unsigned int* bar = reinterpret_cast<unsigned int*>(barrier);
+    DevView vv = v;
+    int f = first, c = count, n = max_g2;
+    F* scr = reinterpret_cast<F*>(scratch);
+    void* args[] = {&vv, &f, &c, &n, &scr, &bar};
+    return cudaLaunchCooperativeKernel((const void*)gj_sweep_kernel<F>, dim3(grid), dim3(256), args, dyn, s);
+}
+template <class F>
+static cudaError_t x_launch(const DevView& v, int first, int count, int max_g2, int max_m, int sms, int rows,
+                            cudaStream_t s) {
+    const int ct = (max_m + kXColsOut - 1) / kXColsOut;
+    const int rt64 = (max_g2 + 63) / 64;
+    if (rows == 0) rows = (long long)count * rt64 * ct >= 64LL * sms ? 64 : 32;
+    if (rows == 64) {
+        merge_x_kernel<64, F><<<dim3(count, rt64 * ct), 256, 0, s>>>(v, first);
+    } else {
+        const int rt32 = (max_g2 + 31) / 32;
+        merge_x_kernel<32, F><<<dim3(count, rt32 * ct), 256, 0, s>>>(v, first);
+    }
+    return cudaGetLastError();
+}
+template <class F>
+static cudaError_t r_launch(const DevView& v, int first, int count, int max_m, int sms, int tile, cudaStream_t s) {
+    const int rt32 = (max_m + 31) / 32;
+    if (tile == 0) tile = (long long)count * rt32 * (rt32 + 1) / 2 >= 64LL * sms ? 32 : 16;
+    if (tile == 32) {
+        merge_rupdate_kernel<2, F><<<dim3(count, rt32 * (rt32 + 1) / 2), 256, 0, s>>>(v, first);
+    } else {
+        const int rt16 = (max_m + 15) / 16;
+        merge_rupdate_kernel<1, F><<<dim3(count, rt16 * (rt16 + 1) / 2), 256, 0, s>>>(v, first);
+    }
+    return cudaGetLastError();
+}
+
+static cudaError_t device_sms(int* sms) {
+    int dev = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    return cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev);
+}
+
 template <class F>
 static cudaError_t launch_merge_build_t(const DevView& v, int first, int count, int max_g2, int max_m,
-                                        double* scratch, void* barrier, cudaStream_t s, int* launches,
-                                        const PhaseHook& hook) {
+                                        const MergeTune& tune, double* scratch, void* barrier, cudaStream_t s,
+                                        int* launches, const PhaseHook& hook) {
     if (count == 0) return cudaSuccess;
     cudaError_t e;
     // per call, so that every device the library runs on gets its own SM
     // count and the sweep's shared-memory attribute (cheap host calls; a
     // captured build makes them once)
-    int sms = 0, dev = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    int sms = 0;
+    if ((e = device_sms(&sms)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(gj_sweep_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   kSweepSmemPad)) != cudaSuccess)
         return e;
@@ -1398,58 +1468,106 @@ static cudaError_t launch_merge_build_t(const DevView& v, int first, int count, 
     }
     {
         HookScope hs(hook, kPhGjSweep);
-        // One CTA per SM (the unused dynamic shared memory keeps a second one
-        // off): the CTAs that invert the next diagonal blocks, which lie on
-        // the sequential chain of the sweep, then own their SM's FP64 pipe
-        // instead of queueing behind another CTA's tile updates.
-        const int tiles = (max_g2 + kGJTile - 1) / kGJTile;
-        const long long items = (long long)count * (1 + tiles * (tiles + 1) / 2);
-        int grid = (int)std::min<long long>(items, (long long)sms);
-        grid = grid < 1 ? 1 : grid;
-        if ((e = cudaMemsetAsync(barrier, 0, sizeof(unsigned int), s)) != cudaSuccess) return e;
-        unsigned int* bar = reinterpret_cast<unsigned int*>(barrier);
-        DevView vv = v;
-        int f = first, c = count, n = max_g2;
-        F* scr = reinterpret_cast<F*>(scratch);
-        void* args[] = {&vv, &f, &c, &n, &scr, &bar};
-        e = cudaLaunchCooperativeKernel((const void*)gj_sweep_kernel<F>, dim3(grid), dim3(256), args, kSweepSmemPad,
-                                        s);
+        e = sweep_launch<F>(v, first, count, max_g2, scratch, barrier, sms, tune.sweep_per_sm, s);
         ++*launches;
         if (e != cudaSuccess) return e;
     }
     if (max_m > 0) {
         {
             HookScope hs(hook, kPhMergeX);
-            const int ct = (max_m + kXColsOut - 1) / kXColsOut;
-            const int rt64 = (max_g2 + 63) / 64;
-            if ((long long)count * rt64 * ct >= 64LL * sms) {
-                merge_x_kernel<64, F><<<dim3(count, rt64 * ct), 256, 0, s>>>(v, first);
-            } else {
-                const int rt32 = (max_g2 + 31) / 32;
-                merge_x_kernel<32, F><<<dim3(count, rt32 * ct), 256, 0, s>>>(v, first);
-            }
+            e = x_launch<F>(v, first, count, max_g2, max_m, sms, tune.x_rows, s);
             ++*launches;
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            if (e != cudaSuccess) return e;
         }
         HookScope hs(hook, kPhMergeR);
-        const int rt32 = (max_m + 31) / 32;
-        if ((long long)count * rt32 * (rt32 + 1) / 2 >= 64LL * sms) {
-            merge_rupdate_kernel<2, F><<<dim3(count, rt32 * (rt32 + 1) / 2), 256, 0, s>>>(v, first);
-        } else {
-            const int rt16 = (max_m + 15) / 16;
-            merge_rupdate_kernel<1, F><<<dim3(count, rt16 * (rt16 + 1) / 2), 256, 0, s>>>(v, first);
-        }
+        e = r_launch<F>(v, first, count, max_m, sms, tune.r_tile, s);
         ++*launches;
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
 
 cudaError_t launch_merge_build(const DevView& v, int first, int count, int max_g2, int max_m, bool fp32,
-                               double* scratch, void* barrier, cudaStream_t s, int* launches, const PhaseHook& hook) {
+                               const MergeTune& tune, double* scratch, void* barrier, cudaStream_t s, int* launches,
+                               const PhaseHook& hook) {
     if (fp32)
-        return launch_merge_build_t<float>(v, first, count, max_g2, max_m, scratch, barrier, s, launches, hook);
-    return launch_merge_build_t<double>(v, first, count, max_g2, max_m, scratch, barrier, s, launches, hook);
+        return launch_merge_build_t<float>(v, first, count, max_g2, max_m, tune, scratch, barrier, s, launches,
+                                           hook);
+    return launch_merge_build_t<double>(v, first, count, max_g2, max_m, tune, scratch, barrier, s, launches, hook);
+}
+
+// Times fn (one launch, already valid to repeat) `reps` times on s with
+// events; the best run in ms.
+template <class Fn>
+static cudaError_t best_time(cudaStream_t s, int reps, cudaEvent_t e0, cudaEvent_t e1, Fn&& fn, float* best) {
+    *best = 1e30f;
+    for (int r = 0; r < reps; ++r) {
+        cudaError_t e;
+        if ((e = cudaEventRecord(e0, s)) != cudaSuccess) return e;
+        if ((e = fn()) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(e1, s)) != cudaSuccess) return e;
+        if ((e = cudaEventSynchronize(e1)) != cudaSuccess) return e;
+        float ms = 0.f;
+        if ((e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) return e;
+        *best = std::min(*best, ms);
+    }
+    return cudaSuccess;
+}
+
+template <class F>
+static cudaError_t tune_level_t(const DevView& v, int first, int count, int max_g2, int max_m, double* scratch,
+                                void* barrier, cudaStream_t s, int reps, MergeTune* out) {
+    *out = MergeTune{};
+    if (count == 0 || !merge_level_blocked(count, max_g2, max_m)) return cudaSuccess;
+    int sms = 0;
+    cudaError_t e;
+    if ((e = device_sms(&sms)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(gj_sweep_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  kSweepSmemPad)) != cudaSuccess)
+        return e;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if ((e = cudaEventCreate(&e0)) != cudaSuccess) return e;
+    if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return e;
+    }
+    float best = 1e30f;
+    for (int per_sm : {1, 2}) {
+        float t = 0.f;
+        e = best_time(s, reps, e0, e1, [&] {
+            return sweep_launch<F>(v, first, count, max_g2, scratch, barrier, sms, per_sm, s);
+        }, &t);
+        if (e != cudaSuccess) break;
+        if (t < best) { best = t; out->sweep_per_sm = per_sm; }
+    }
+    if (e == cudaSuccess && max_m > 0) {
+        best = 1e30f;
+        for (int rows : {32, 64}) {
+            float t = 0.f;
+            e = best_time(s, reps, e0, e1, [&] { return x_launch<F>(v, first, count, max_g2, max_m, sms, rows, s); },
+                          &t);
+            if (e != cudaSuccess) break;
+            if (t < best) { best = t; out->x_rows = rows; }
+        }
+    }
+    if (e == cudaSuccess && max_m > 0) {
+        best = 1e30f;
+        for (int tile : {16, 32}) {
+            float t = 0.f;
+            e = best_time(s, reps, e0, e1, [&] { return r_launch<F>(v, first, count, max_m, sms, tile, s); }, &t);
+            if (e != cudaSuccess) break;
+            if (t < best) { best = t; out->r_tile = tile; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return e;
+}
+
+cudaError_t tune_merge_level(const DevView& v, int first, int count, int max_g2, int max_m, bool fp32,
+                             double* scratch, void* barrier, cudaStream_t s, int reps, MergeTune* out) {
+    if (fp32) return tune_level_t<float>(v, first, count, max_g2, max_m, scratch, barrier, s, reps, out);
+    return tune_level_t<double>(v, first, count, max_g2, max_m, scratch, barrier, s, reps, out);
 }
 
 cudaError_t tree_grid(int* grid) {

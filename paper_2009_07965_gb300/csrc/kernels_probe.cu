@@ -9,6 +9,7 @@
 //   FFMA  FP32 fused multiply-add, 8 chains per thread (2 flops)
 //   TF32  mma.sync m16n8k8 tf32 -> f32, 4 accumulators per warp (2048)
 //   BF16  mma.sync m16n8k16 bf16 -> f32, 4 accumulators per warp (4096)
+//   DFMA_DMMA  half the warps DFMA, half DMMA (do the two FP64 paths add up?)
 // The results never leave the registers except through a store guarded by a
 // comparison with a runtime NaN (never true), which keeps the compiler from
 // dropping the chains.
@@ -25,17 +26,59 @@ __device__ double g_probe_sink;
 constexpr int kProbeThreads = 256;
 constexpr int kProbeBlocksPerSM = 4;
 
+__device__ __forceinline__ void dfma_chains(double (&a)[8], double b, double c) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = fma(a[k], b, c);
+}
 __global__ void __launch_bounds__(kProbeThreads) probe_dfma(int iters, double b, double never) {
     double a[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) a[k] = threadIdx.x * 1e-3 + k;
-    for (int it = 0; it < iters; ++it) {
-#pragma unroll
-        for (int k = 0; k < 8; ++k) a[k] = fma(a[k], b, 1e-9);
+    const double c = b * 1e-9;
+    // four iterations per loop trip: the loop's own instructions stay far
+    // below the FP64 issue rate
+    int it = 0;
+    for (; it + 3 < iters; it += 4) {
+        dfma_chains(a, b, c);
+        dfma_chains(a, b, c);
+        dfma_chains(a, b, c);
+        dfma_chains(a, b, c);
     }
+    for (; it < iters; ++it) dfma_chains(a, b, c);
     double s = 0.0;
 #pragma unroll
     for (int k = 0; k < 8; ++k) s += a[k];
+    if (s == never) g_probe_sink = s;
+}
+
+// Half of the warps of each CTA run FP64 FMA chains and half FP64 MMA
+// chains (the same per-warp flops per iteration as the two probes above
+// divided evenly): shows whether the two FP64 paths share one unit.
+__global__ void __launch_bounds__(kProbeThreads) probe_dfma_dmma(int iters, double b, double never) {
+    double s = 0.0;
+    if ((threadIdx.x >> 5) & 1) {
+        double a[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) a[k] = threadIdx.x * 1e-3 + k;
+        const double c = b * 1e-9;
+        for (int it = 0; it < iters; ++it) dfma_chains(a, b, c);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) s += a[k];
+    } else {
+        const double av = threadIdx.x * 1e-3;
+        double c[4][2];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) c[k][0] = c[k][1] = 0.0;
+        for (int it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};"
+                             : "+d"(c[k][0]), "+d"(c[k][1])
+                             : "d"(av), "d"(b));
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) s += c[k][0] + c[k][1];
+    }
     if (s == never) g_probe_sink = s;
 }
 
@@ -125,6 +168,7 @@ double probe_flops_per_thread_iter(int kind) {
         case MRCM_PROBE_FFMA: return 16.0;
         case MRCM_PROBE_TF32: return 4.0 * 2048.0 / 32.0;
         case MRCM_PROBE_BF16: return 4.0 * 4096.0 / 32.0;
+        case MRCM_PROBE_DFMA_DMMA: return 0.5 * 16.0 + 0.5 * (4.0 * 512.0 / 32.0);
         default: return 0.0;
     }
 }
@@ -137,6 +181,7 @@ cudaError_t probe_launch(int kind, int grid, int iters, cudaStream_t s) {
         case MRCM_PROBE_FFMA: probe_ffma<<<grid, kProbeThreads, 0, s>>>(iters, 0.999999f, never); break;
         case MRCM_PROBE_TF32: probe_tf32<<<grid, kProbeThreads, 0, s>>>(iters, 0.999999f, never); break;
         case MRCM_PROBE_BF16: probe_bf16<<<grid, kProbeThreads, 0, s>>>(iters, 0.999999f, never); break;
+        case MRCM_PROBE_DFMA_DMMA: probe_dfma_dmma<<<grid, kProbeThreads, 0, s>>>(iters, 0.999999, never); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

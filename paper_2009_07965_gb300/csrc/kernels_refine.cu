@@ -278,13 +278,16 @@ __global__ void __launch_bounds__(256) compat_partial_kernel(DevView v, const do
     double mag = 0.0;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n + nb; i += stride) {
+        const double val = i < n ? q[i] : bc_val[i - n];
+        // zeros (most cells of a point-source problem) are skipped on the
+        // bit pattern: an FP64 compare would cost a full FP64 instruction
+        if (((unsigned long long)__double_as_longlong(val) << 1) == 0ull) continue;
         DD x;
         if (i < n) {
-            x = {q[i], 0.0};
+            x = {val, 0.0};
         } else {
-            const long long b = i - n;
-            const double area = b < 2LL * v.ny ? v.hy : v.hx;
-            x = dd_neg(dd_two_prod(area, bc_val[b]));
+            const double area = i - n < 2LL * v.ny ? v.hy : v.hx;
+            x = dd_neg(dd_two_prod(area, val));
         }
         acc = dd_add(acc, x);
         mag += fabs(x.h);
@@ -309,14 +312,23 @@ __global__ void __launch_bounds__(256) compat_partial_kernel(DevView v, const do
         v.red[768 + blockIdx.x] = sh_a[0];
     }
 }
-__global__ void compat_final_kernel(DevView v) {
-    DD acc = {0.0, 0.0};
-    double mag = 0.0;
-    for (int b = 0; b < kCompatBlocks; ++b) {
-        acc = dd_add(acc, DD{v.red[256 + 2 * b], v.red[256 + 2 * b + 1]});
-        mag += v.red[768 + b];
+__global__ void __launch_bounds__(kCompatBlocks) compat_final_kernel(DevView v) {
+    __shared__ double sh_h[kCompatBlocks], sh_l[kCompatBlocks], sh_a[kCompatBlocks];
+    const int b = threadIdx.x;
+    sh_h[b] = v.red[256 + 2 * b];
+    sh_l[b] = v.red[256 + 2 * b + 1];
+    sh_a[b] = v.red[768 + b];
+    __syncthreads();
+    for (int w = kCompatBlocks / 2; w > 0; w >>= 1) {
+        if (b < w) {
+            const DD y = dd_add(DD{sh_h[b], sh_l[b]}, DD{sh_h[b + w], sh_l[b + w]});
+            sh_h[b] = y.h;
+            sh_l[b] = y.l;
+            sh_a[b] += sh_a[b + w];
+        }
+        __syncthreads();
     }
-    if (!(fabs(acc.h + acc.l) <= kCompatTol * mag)) atomicOr(v.status, kStatusInconsistent);
+    if (b == 0 && !(fabs(sh_h[0] + sh_l[0]) <= kCompatTol * sh_a[0])) atomicOr(v.status, kStatusInconsistent);
 }
 
 }  // namespace
@@ -325,7 +337,7 @@ cudaError_t launch_compat_check(const DevView& v, const double* q, const double*
     compat_partial_kernel<<<kCompatBlocks, 256, 0, s>>>(v, q, bc_val);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    compat_final_kernel<<<1, 1, 0, s>>>(v);
+    compat_final_kernel<<<1, kCompatBlocks, 0, s>>>(v);
     return cudaGetLastError();
 }
 

@@ -387,6 +387,7 @@ struct mrcm_ctx {
     Plan P;
     int precision = MRCM_FP64;
     int mixed_split = kMixedSplitDefault;
+    std::vector<MergeTune> tune;          // per tree height (mrcm_autotune); empty: heuristics
     cudaStream_t stream = nullptr;
     int device = 0;
     bool built = false;
@@ -786,8 +787,9 @@ static int enqueue_build(mrcm_ctx* c, int& launches) {
         const PhaseHook hook{c, phase_begin, phase_end};
         for (int h = 1; h <= P.height; ++h) {
             const bool fp32 = v.mixed && P.level_max_g2[h - 1] <= c->mixed_split;
+            const MergeTune tune = c->tune.empty() ? MergeTune{} : c->tune[h - 1];
             TRYC(launch_merge_build(v, P.level_first[h - 1], P.level_count[h - 1], P.level_max_g2[h - 1],
-                                    P.level_max_m[h - 1], fp32, c->gj_scratch, c->gj_barrier, s, &launches,
+                                    P.level_max_m[h - 1], fp32, tune, c->gj_scratch, c->gj_barrier, s, &launches,
                                     hook));
         }
     }
@@ -930,6 +932,34 @@ int mrcm_solve(mrcm_ctx* c, const double* q_dev, const double* bc_val_dev, doubl
     c->hist_count = c->refine_steps + (c->refine_check ? 1 : 0);
     TRY(read_status(c));
     c->solved = true;
+    return MRCM_OK;
+}
+
+int mrcm_autotune(mrcm_ctx* c, int reps) {
+    if (!c || reps < 1 || reps > 100) return MRCM_ERR_INVALID_ARG;
+    if (!c->built) return MRCM_ERR_NOT_BUILT;
+    const Plan& P = c->P;
+    std::vector<MergeTune> tune(P.height);
+    for (int h = 1; h <= P.height; ++h) {
+        const bool fp32 = c->v.mixed && P.level_max_g2[h - 1] <= c->mixed_split;
+        TRYC(tune_merge_level(c->v, P.level_first[h - 1], P.level_count[h - 1], P.level_max_g2[h - 1],
+                              P.level_max_m[h - 1], fp32, c->gj_scratch, c->gj_barrier, c->stream, reps,
+                              &tune[h - 1]));
+    }
+    TRY(read_status(c));
+    c->tune = tune;
+    // the captured build graph holds the previous launch shapes
+    if (c->build_exec) cudaGraphExecDestroy(c->build_exec);
+    c->build_exec = nullptr;
+    return MRCM_OK;
+}
+
+int mrcm_tune_info(const mrcm_ctx* c, int height, int out[3]) {
+    if (!c || !out || height < 1 || height > c->P.height) return MRCM_ERR_INVALID_ARG;
+    const MergeTune t = c->tune.empty() ? MergeTune{} : c->tune[height - 1];
+    out[0] = t.sweep_per_sm;
+    out[1] = t.x_rows;
+    out[2] = t.r_tile;
     return MRCM_OK;
 }
 

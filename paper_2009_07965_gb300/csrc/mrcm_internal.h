@@ -288,10 +288,22 @@ struct PhaseHook {
 // one tree height of merges; scratch: merge_scratch_doubles(count, max_g2,
 // max_m) values; barrier: kMergeBarrierBytes of device memory (reset by the
 // call); *launches is increased by the number of kernels launched
+// Launch shapes of one blocked merge level (0 everywhere: the built-in
+// heuristic).  sweep_per_sm: CTAs per SM of the cooperative sweep (1, 2);
+// x_rows: rows of X per CTA (32, 64); r_tile: side of an R tile (16, 32).
+struct MergeTune {
+    int sweep_per_sm = 0, x_rows = 0, r_tile = 0;
+};
 // fp32: the mixed form's FP32 arithmetic for this level (T of the blocked
 // sweep in v.W32; W, X and R stored in double either way)
 cudaError_t launch_merge_build(const DevView& v, int first, int count, int max_g2, int max_m, bool fp32,
-                               double* scratch, void* barrier, cudaStream_t s, int* launches, const PhaseHook& hook);
+                               const MergeTune& tune, double* scratch, void* barrier, cudaStream_t s, int* launches,
+                               const PhaseHook& hook);
+// Times every launch shape of one blocked level (its children's maps must
+// be built: the launches are repeated and recompute the same numbers) and
+// returns the fastest per launch; `reps` timed runs each.
+cudaError_t tune_merge_level(const DevView& v, int first, int count, int max_g2, int max_m, bool fp32,
+                             double* scratch, void* barrier, cudaStream_t s, int reps, MergeTune* out);
 constexpr size_t kMergeBarrierBytes = 64;
 bool merge_level_blocked(int count, int max_g2, int max_m);
 size_t merge_scratch_doubles(int count, int max_g2, int max_m);

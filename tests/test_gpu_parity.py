@@ -343,3 +343,37 @@ def test_kernel_reciprocal_within_an_ulp(mrcm_lib):
     ref = (1.0 / xd).cpu().numpy()
     err = np.abs(r - ref) / np.spacing(np.abs(ref))
     assert err.max() <= 1.0, (err.max(), x[np.argmax(err)])
+
+
+def test_autotuned_launch_shapes_give_the_same_bits(mrcm_lib):
+    # the tuner times every launch shape of the blocked levels and keeps the
+    # fastest; all shapes compute the same numbers, so the solution after
+    # tuning (graph replay included) is bit-identical to the untuned one
+    import paper_2009_07965_gb300 as mr
+    import torch
+    prob = inputs.darcy_problem(512, 512, sigma2=3.0, corr=0.05, seed=47, bc="quarter_five_spot")
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        s = mr.Solver(torch.from_numpy(prob.K).cuda(), prob.Lx, prob.Ly, prob.sub, prob.seg, prob.alpha,
+                      prob.bc_type, stream=st)
+        q, bc = torch.from_numpy(prob.q).cuda(), torch.from_numpy(prob.bc_val).cuda()
+        s.build_basis()
+        s.solve(q, bc)
+        before = [t.cpu().numpy().copy() for t in (s.p, s.Fx, s.Fy)]
+        levels = mr.mrcm_query(s.ctx, "LEVELS")
+        assert all(v == 0 for h in range(1, levels + 1) for v in mr.mrcm_tune_info(s.ctx, h).values())
+        mr.mrcm_autotune(s.ctx, 2)
+        chosen = [mr.mrcm_tune_info(s.ctx, h) for h in range(1, levels + 1)]
+        assert any(c["sweep_per_sm"] in (1, 2) for c in chosen), chosen
+        for _ in range(2):
+            s.build_basis()
+            s.solve(q, bc)
+            after = [t.cpu().numpy() for t in (s.p, s.Fx, s.Fy)]
+            for a, b in zip(before, after):
+                assert np.array_equal(a, b)
+        st.synchronize()
+        s.close()
+    with pytest.raises(mr.MrcmError) as e:
+        s2 = mr.Solver(torch.from_numpy(prob.K).cuda())
+        mr.mrcm_autotune(s2.ctx, 1)                   # not built
+    assert e.value.code == -4

@@ -34,7 +34,7 @@ def test_square4096_matches_the_oracle_samples(mrcm_lib):
     # the same field as the oracle's, up to the rounding of the generator's
     # FFT and exp on this machine
     fp = np.array([K.sum(), (K * K).sum(), np.log(K).sum(), K.min(), K.max()])
-    assert np.allclose(fp, g["K_fingerprint"], rtol=1e-12, atol=0.0), (fp, g["K_fingerprint"])
+    assert np.allclose(fp, g["K_fingerprint"], rtol=1e-10, atol=0.0), (fp, g["K_fingerprint"])
     st = torch.cuda.Stream()
     with torch.cuda.stream(st):
         s = mr.Solver(torch.from_numpy(K).cuda(), prob.Lx, prob.Ly, prob.sub, prob.seg, prob.alpha,

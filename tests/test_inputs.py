@@ -60,3 +60,19 @@ def test_problem_sources_and_boundary_data(bc):
     else:
         assert np.all(p.q == 0.0)
         assert np.all(p.bc_val[:24] == 1.0) and np.all(p.bc_val[24:48] == 0.0)
+
+
+def test_golden_4096_matches_this_generator():
+    # the oracle's stored 4096^2 solution was computed for the field this
+    # generator makes (fingerprint equal up to the rounding of the FFT and
+    # exp of the machine), and its refinement reached the rounding level
+    import os
+    g = np.load(os.path.join(os.path.dirname(__file__), "golden", "square4096_qfs_oracle.npz"))
+    K = inputs.config_4096().K
+    fp = np.array([K.sum(), (K * K).sum(), np.log(K).sum(), K.min(), K.max()])
+    assert np.allclose(fp, g["K_fingerprint"], rtol=1e-10, atol=0.0)
+    assert int(g["n"]) == 4096 and int(g["refine"]) == 3
+    assert g["history"][-1] < 1e-20 * max(1.0, g["history"][0])
+    for k in ("p", "Fx", "Fy", "Fa_x", "Fb_x", "Fa_y", "Fb_y"):
+        assert len(g[f"{k}_idx"]) == len(g[f"{k}_val"]) >= 9000
+        assert np.all(np.isfinite(g[f"{k}_val"])) and float(g[f"{k}_norm"]) > 0
