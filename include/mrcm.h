@@ -253,8 +253,9 @@ int mrcm_set_refinement(mrcm_ctx* ctx, int steps, int check);
 /*
  * mrcm_set_wait_limit -- polls after which a bounded wait between the CTAs
  * of one cooperative launch (the blocked interface sweeps and the solve's
- * tree sweeps) gives up; the paper has no counterpart.  polls <= 0 restores
- * the default (about a second of polling).  A wait that gives up makes the
+ * tree sweeps) gives up; the paper has no counterpart.  polls < 0 restores
+ * the default (about a second of polling); 0 gives up at the first check
+ * that finds the awaited condition unmet.  A wait that gives up makes the
  * call return MRCM_ERR_TIMEOUT; every CTA then leaves the launch at its
  * next wait, nothing is left running, and the context stays usable (a later
  * call with a sufficient limit recomputes everything it needs).  A very

@@ -979,7 +979,7 @@ int mrcm_set_mixed_split(mrcm_ctx* c, int max_g2_fp32) {
 
 int mrcm_set_wait_limit(mrcm_ctx* c, long long polls) {
     if (!c) return MRCM_ERR_INVALID_ARG;
-    const long long lim = polls > 0 ? polls : kDefaultSpinLimit;
+    const long long lim = polls >= 0 ? polls : kDefaultSpinLimit;
     if (lim == c->v.spin_limit) return MRCM_OK;
     c->v.spin_limit = lim;
     // the captured graphs hold the old limit in their launch arguments

@@ -1,7 +1,7 @@
 """Failure handling of the CUDA path, made without faulting the GPU.
 
 - MRCM_ERR_TIMEOUT: the bounded inter-CTA waits of the cooperative launches
-  (blocked interface sweep, solve tree sweeps) are given a limit of a few
+  (blocked interface sweep, solve tree sweeps) are given a limit of zero
   polls, so that they run out; the call must return MRCM_ERR_TIMEOUT and the
   context must give the normal results once the default limit is back.
 - MRCM_ERR_INVALID_ARG for all-Neumann data whose sources do not balance
@@ -40,17 +40,19 @@ def test_bounded_waits_time_out_and_the_context_recovers(mrcm_lib, graphs):
         s.build_basis()
         s.solve(q, bc)
         ref = [t.cpu().numpy().copy() for t in (s.p, s.Fx, s.Fy)]
-        mr.mrcm_set_wait_limit(s.ctx, 1)
+        # limit 0: a wait gives up at its first unmet check, so every CTA
+        # of a launch but the last to arrive at a grid barrier gives up
+        mr.mrcm_set_wait_limit(s.ctx, 0)
         with pytest.raises(MrcmError) as e:
             s.build_basis()
         assert e.value.code == -8                    # MRCM_ERR_TIMEOUT
-        mr.mrcm_set_wait_limit(s.ctx, 0)             # default limit
+        mr.mrcm_set_wait_limit(s.ctx, -1)            # default limit
         s.build_basis()                              # everything recomputed
-        mr.mrcm_set_wait_limit(s.ctx, 1)
+        mr.mrcm_set_wait_limit(s.ctx, 0)
         with pytest.raises(MrcmError) as e:
             s.solve(q, bc)
         assert e.value.code == -8
-        mr.mrcm_set_wait_limit(s.ctx, 0)
+        mr.mrcm_set_wait_limit(s.ctx, -1)
         s.solve(q, bc)
         out = [t.cpu().numpy() for t in (s.p, s.Fx, s.Fy)]
         st.synchronize()
