@@ -1389,6 +1389,7 @@ static cudaError_t sweep_launch(const DevView& v, int first, int count, int max_
     // pipe.  Two per SM let one CTA's staging loads overlap the other's
     // tile updates, which pays where the tiles of a step outnumber the CTAs
     // many times over (the largest systems).
+    if (per_sm < 1) per_sm = 1;              // the heuristic: one CTA per SM
     size_t dyn = kSweepSmemPad;
     if (per_sm >= 2) {
         dyn = std::max<size_t>((size_t)max_g2 * sizeof(double), 16);
