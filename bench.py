@@ -51,6 +51,11 @@ WORKLOADS = {
         desc=("square4096-qfs: 4096x4096 cells, log-normal K sigma^2=3 corr 0.02 (seed 5000), "
               "quarter-five-spot, no-flow, 256x256 leaves of 16x16, 4-cell segments, alpha=1, 16 levels"),
         golden="square4096_qfs_oracle.npz"),
+    "square2048": dict(
+        n=2048, sigma2=3.0, corr=0.02, seed=5000,
+        desc=("square2048-qfs: 2048x2048 cells, log-normal K sigma^2=3 corr 0.02 (seed 5000), "
+              "quarter-five-spot, no-flow, 128x128 leaves of 16x16, 4-cell segments, alpha=1, 14 levels"),
+        golden=None),
     "square1024": dict(
         n=1024, sigma2=4.0, corr=0.05, seed=2000,
         desc=("square1024-qfs: 1024x1024 cells, log-normal K sigma^2=4 corr 0.05 (seed 2000), "

@@ -1386,9 +1386,9 @@ static cudaError_t sweep_launch(const DevView& v, int first, int count, int max_
     // Default one CTA per SM (the padded dynamic shared memory keeps a
     // second one off): the CTAs that invert the next diagonal blocks, which
     // lie on the sequential chain of the sweep, then own their SM's FP64
-    // pipe.  Two per SM let one CTA's staging loads overlap the other's
-    // tile updates, which pays where the tiles of a step outnumber the CTAs
-    // many times over (the largest systems).
+    // pipe.  Two or three per SM let one CTA's staging loads overlap the
+    // others' tile updates, which pays where the tiles of a step outnumber
+    // the CTAs many times over (the largest systems).
     if (per_sm < 1) per_sm = 1;              // the heuristic: one CTA per SM
     size_t dyn = kSweepSmemPad;
     if (per_sm >= 2) {
@@ -1396,9 +1396,9 @@ static cudaError_t sweep_launch(const DevView& v, int first, int count, int max_
         int fit = 0;
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, gj_sweep_kernel<F>, 256, dyn)) != cudaSuccess)
             return e;
-        if (fit < 2) {
-            per_sm = 1;
-            dyn = kSweepSmemPad;
+        if (fit < per_sm) {
+            per_sm = fit >= 2 ? fit : 1;
+            if (per_sm == 1) dyn = kSweepSmemPad;
         }
     }
     const int tiles = (max_g2 + kGJTile - 1) / kGJTile;
@@ -1533,7 +1533,7 @@ static cudaError_t tune_level_t(const DevView& v, int first, int count, int max_
         return e;
     }
     float best = 1e30f;
-    for (int per_sm : {1, 2}) {
+    for (int per_sm : {1, 2, 3}) {
         float t = 0.f;
         e = best_time(s, reps, e0, e1, [&] {
             return sweep_launch<F>(v, first, count, max_g2, scratch, barrier, sms, per_sm, s);

@@ -364,7 +364,7 @@ def test_autotuned_launch_shapes_give_the_same_bits(mrcm_lib):
         assert all(v == 0 for h in range(1, levels + 1) for v in mr.mrcm_tune_info(s.ctx, h).values())
         mr.mrcm_autotune(s.ctx, 2)
         chosen = [mr.mrcm_tune_info(s.ctx, h) for h in range(1, levels + 1)]
-        assert any(c["sweep_per_sm"] in (1, 2) for c in chosen), chosen
+        assert any(c["sweep_per_sm"] in (1, 2, 3) for c in chosen), chosen
         for _ in range(2):
             s.build_basis()
             s.solve(q, bc)
