@@ -56,6 +56,13 @@ WORKLOADS = {
         desc=("square2048-qfs: 2048x2048 cells, log-normal K sigma^2=3 corr 0.02 (seed 5000), "
               "quarter-five-spot, no-flow, 128x128 leaves of 16x16, 4-cell segments, alpha=1, 14 levels"),
         golden=None),
+    "ensemble512": dict(
+        kind="ensemble", count=512, nmin=250, nmax=1000, seed=4000,
+        desc=("ensemble512: 512 independent realisations on the unit square, nx and ny each uniform in "
+              "250..1000 cells, log-normal K with sigma^2 uniform in [1, 4], corr 0.05 (seed 4000 + r), p=1 "
+              "left / p=0 right, no-flow top and bottom, 16x16 leaves truncated at each grid's edges, 4-cell "
+              "segments, alpha=1; one batched context (mrcm_setup_batch), FP64"),
+        golden=None),
     "square1024": dict(
         n=1024, sigma2=4.0, corr=0.05, seed=2000,
         desc=("square1024-qfs: 1024x1024 cells, log-normal K sigma^2=4 corr 0.05 (seed 2000), "
@@ -185,20 +192,32 @@ def run_reference(args):
     procs = host_cores()
     times = []
     value_steps = []
+    ensemble = wl.get("kind") == "ensemble"
+    if ensemble:
+        probs = ensemble_inputs(wl, count=wl["count"])
+        order = sorted(range(len(probs)), key=lambda k: probs[k].nx * probs[k].ny)[:procs]
+        cells = sum(probs[k].nx * probs[k].ny for k in order)
+        sample = "the smallest members of the ensemble, one per host core"
+    else:
+        cells = CPU_WINDOW * CPU_WINDOW * procs
+        sample = f"{procs} x {CPU_WINDOW}x{CPU_WINDOW} windows per step"
     for it in range(args.warmup + args.steps):
-        v, _, wall = time_oracle_parallel(wl, 1, procs)
+        if ensemble:
+            v = time_ensemble_oracle(wl, probs)["value"]
+            wall = cells / v
+        else:
+            v, _, wall = time_oracle_parallel(wl, 1, procs)
         if it >= args.warmup:
             times.append(wall)
             value_steps.append(v)
-    cells = CPU_WINDOW * CPU_WINDOW * procs
     value = cells * len(times) / sum(times)
     line = dict(metric=METRIC, value=value, unit="cells/s", n_gpus=args.gpus, steps=args.steps,
                 warmup=args.warmup, ms_per_step=1e3 * sum(times) / len(times),
                 higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
                 data="synthetic", impl="reference",
-                config=dict(workload=wl["desc"], sample=f"{procs} x {CPU_WINDOW}x{CPU_WINDOW} windows per step"),
+                config=dict(workload=wl["desc"], sample=sample),
                 cpu_baseline=dict(value=value, unit="cells/s", cores=procs, kind="oracle",
-                                  sample=oracle_sample_desc(wl, procs, 1)),
+                                  sample=sample if ensemble else oracle_sample_desc(wl, procs, 1)),
                 e2e=dict(value=value, unit="cells/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
 
@@ -630,6 +649,200 @@ def run_profile_step(args):
     solver.close()
 
 
+def _member(args):
+    import inputs
+    r, nmin, nmax, seed = args
+    return inputs.ensemble_member(r, nmin=nmin, nmax=nmax, seed0=seed)
+
+
+def ensemble_inputs(wl, count=None):
+    """The ensemble's problems, generated on every host core (a spawn pool,
+    started before this process touches the GPU)."""
+    import multiprocessing as mp
+    count = wl["count"] if count is None else count
+    jobs = [(r, wl["nmin"], wl["nmax"], wl["seed"]) for r in range(count)]
+    with mp.get_context("spawn").Pool(host_cores()) as pool:
+        return pool.map(_member, jobs, chunksize=4)
+
+
+def run_ensemble(args):
+    """The batched-ensemble workload: every realisation in one context."""
+    import numpy as np
+    import torch
+    wl = WORKLOADS[args.workload]
+    probs = ensemble_inputs(wl)                      # before any CUDA call
+    import paper_2009_07965_gb300 as mr
+    from paper_2009_07965_gb300 import build as build_mod
+    rank, world, local = dist_env()
+    if world > 1:
+        raise SystemExit("the ensemble workload runs on one GPU")
+    build_mod.build()
+    dev = torch.device("cuda", 0)
+    peaks = probe_peaks()
+    stream = torch.cuda.Stream(dev)
+    Ks = [torch.from_numpy(p.K).to(dev) for p in probs]
+    with torch.cuda.stream(stream):
+        b = mr.BatchSolver(Ks, [(p.Lx, p.Ly) for p in probs], [p.bc_type for p in probs], stream=stream)
+    del Ks
+    mr.mrcm_enable_timing(b.ctx, True)
+    mr.mrcm_set_refinement(b.ctx, args.refine)
+    q = b.pack([torch.from_numpy(p.q).to(dev) for p in probs])
+    bcv = b.pack([torch.from_numpy(p.bc_val).to(dev) for p in probs])
+    cells = b.ncell
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        b.build_basis()
+        b.solve_packed(q, bcv)
+
+    for _ in range(args.warmup):
+        step()
+    tuned = None
+    if not args.no_autotune:
+        mr.mrcm_autotune(b.ctx, 3)
+        tuned = {h: mr.mrcm_tune_info(b.ctx, h) for h in range(1, mr.mrcm_query(b.ctx, "LEVELS") + 1)}
+        tuned = {h: t for h, t in tuned.items() if any(t.values())}
+        step()
+    torch.cuda.synchronize(dev)
+    props = torch.cuda.get_device_properties(dev)
+    uuid = getattr(props, "uuid", None)
+    uuid = f"GPU-{uuid}" if uuid is not None and not str(uuid).startswith("GPU-") else uuid
+    sampler = ClockSampler(uuid)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    step_ms = []
+    phases = {k: 0.0 for k in mr.PHASES}
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+        ev0.record(stream)
+        step()
+        ev1.record(stream)
+        ev1.synchronize()
+        step_ms.append(ev0.elapsed_time(ev1))
+        for k, v in mr.mrcm_phase_times(b.ctx).items():
+            phases[k] += v
+    clocks = sampler.stop()
+    launches = mr.mrcm_query(b.ctx, "KERNEL_LAUNCHES_BUILD") + mr.mrcm_query(b.ctx, "KERNEL_LAUNCHES_SOLVE")
+    value, total_ms = job_throughput(sum(step_ms), cells, args.steps, 1, dev)
+    # end to end from pinned host buffers
+    K_h = b.K.cpu().pin_memory()
+    q_h, bc_h = q.cpu().pin_memory(), bcv.cpu().pin_memory()
+    p_h = torch.empty_like(b.p, device="cpu").pin_memory()
+    fx_h = torch.empty_like(b.Fx, device="cpu").pin_memory()
+    fy_h = torch.empty_like(b.Fy, device="cpu").pin_memory()
+    K_d, q_d, bc_d = torch.empty_like(b.K), torch.empty_like(q), torch.empty_like(bcv)
+    e2e_ms = []
+    for it in range(args.warmup + args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+        ev0.record(stream)
+        with torch.cuda.stream(stream):
+            K_d.copy_(K_h, non_blocking=True)
+            q_d.copy_(q_h, non_blocking=True)
+            bc_d.copy_(bc_h, non_blocking=True)
+        mr.mrcm_set_permeability(b.ctx, K_d)
+        b.build_basis()
+        pd, fxd, fyd = b.solve_packed(q_d, bc_d)
+        with torch.cuda.stream(stream):
+            p_h.copy_(pd, non_blocking=True)
+            fx_h.copy_(fxd, non_blocking=True)
+            fy_h.copy_(fyd, non_blocking=True)
+        ev1.record(stream)
+        ev1.synchronize()
+        if it >= args.warmup:
+            e2e_ms.append(ev0.elapsed_time(ev1))
+    e2e_value, _ = job_throughput(sum(e2e_ms), cells, args.steps, 1, dev)
+    h2d = (K_h.numel() + q_h.numel() + bc_h.numel()) * 8
+    d2h = (p_h.numel() + fx_h.numel() + fy_h.numel()) * 8
+    # accuracy: the single pass against the refined solution, and the two
+    # smallest members against the oracle
+    b.solve_packed(q, bcv)
+    timed = [t.cpu().numpy().copy() for t in (b.p, b.Fx, b.Fy)]
+    mr.mrcm_set_refinement(b.ctx, 3)
+    b.solve_packed(q, bcv)
+    refined = [t.cpu().numpy().copy() for t in (b.p, b.Fx, b.Fy)]
+    rel = {k: float(np.linalg.norm(a - c) / np.linalg.norm(c)) for k, a, c in zip(("p", "Fx", "Fy"), timed, refined)}
+    split = b.split()
+    order = sorted(range(len(probs)), key=lambda k: probs[k].nx * probs[k].ny)[:2]
+    vs_oracle = {}
+    if not args.no_cpu_baseline:
+        from oracle.mrcm import solve_mrcm
+        for k in order:
+            o = solve_mrcm(probs[k], refine=3)
+            vs_oracle[probs[k].name] = {n: float(np.linalg.norm(t.cpu().numpy() - o[n]) / np.linalg.norm(o[n]))
+                                        for n, t in zip(("p", "Fx", "Fy"), split[k])}
+    ph = {k: v / args.steps for k, v in phases.items()}
+    pf = mr.mrcm_phase_flops(b.ctx)
+    dom = max(mr.PHASES, key=lambda k: ph[k])
+    achieved = pf[dom] / (ph[dom] / 1e3) / 1e12
+    peak = peaks["DFMA"]
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = time_ensemble_oracle(wl, probs)
+    line = dict(
+        metric=METRIC, value=value, unit="cells/s", n_gpus=1, steps=args.steps, warmup=args.warmup,
+        ms_per_step=total_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
+        data="synthetic",
+        config=dict(workload=wl["desc"], realisations=len(probs), cells=cells,
+                    leaves=mr.mrcm_query(b.ctx, "LEAVES"), levels=mr.mrcm_query(b.ctx, "LEVELS"),
+                    l2="inputs larger than L2; L2 also flushed between timed steps", parallelism="one context"),
+        roofline=dict(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
+                      traffic=None, kernel=mr.PHASE_KERNELS[dom], phase=dom,
+                      share=ph[dom] / (total_ms / args.steps),
+                      peak_source="measured in this run: FP64 FMA probe (mrcm_probe_peak DFMA), of measured",
+                      peak_nominal=FP64_NOMINAL_TFLOPS),
+        peaks_measured_tflops=peaks,
+        autotuned_shapes=tuned,
+        phases={k: dict(ms=ph[k], gflop=pf[k] / 1e9, tflops=(pf[k] / (ph[k] / 1e3) / 1e12) if ph[k] > 0 else None)
+                for k in mr.PHASES},
+        e2e=dict(value=e2e_value, unit="cells/s", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
+        gpu_launches=launches * args.steps,
+        clocks=clocks,
+        check=dict(refine_steps=args.refine, rel_l2_vs_refined=rel, vs_oracle_smallest_members=vs_oracle,
+                   tolerance=FP64_FORM_TOL, within_tolerance=bool(max(rel.values()) <= FP64_FORM_TOL)),
+        cpu_baseline=cpu,
+    )
+    print(json.dumps(line), flush=True)
+    b.close()
+
+
+ENSEMBLE_ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import inputs
+from oracle.mrcm import solve_mrcm
+prob = inputs.ensemble_member({r}, nmin={nmin}, nmax={nmax}, seed0={seed})
+t = time.perf_counter()
+solve_mrcm(prob)
+print(json.dumps(dict(times=[time.perf_counter() - t], cells=prob.nx * prob.ny)))
+"""
+
+
+def time_ensemble_oracle(wl, probs):
+    """The oracle on the host cores: one process per core, each solving one
+    member of the ensemble (the smallest ones, so that the sample stays
+    bounded)."""
+    procs = host_cores()
+    order = sorted(range(len(probs)), key=lambda k: probs[k].nx * probs[k].ny)[:procs]
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    ps = [subprocess.Popen([sys.executable, "-c", ENSEMBLE_ORACLE_SNIPPET.format(
+        root=ROOT, r=k, nmin=wl["nmin"], nmax=wl["nmax"], seed=wl["seed"])], env=env, stdout=subprocess.PIPE,
+        stderr=subprocess.PIPE, text=True) for k in order]
+    res = []
+    for p in ps:
+        out, err = p.communicate(timeout=1800)
+        if p.returncode:
+            return dict(value=None, unit="cells/s", cores=procs, kind="oracle", error=err[-300:])
+        res.append(json.loads(out.strip().splitlines()[-1]))
+    slowest = max(r["times"][0] for r in res)
+    cells = sum(r["cells"] for r in res)
+    return dict(value=cells / slowest, unit="cells/s", cores=procs, kind="oracle",
+                single_core_value=sum(r["cells"] / r["times"][0] for r in res) / len(res),
+                sample=(f"oracle O2 on {procs} concurrent processes (one per host core), each solving one of the "
+                        f"{procs} smallest members of the ensemble; value = their cells / the slowest solve time"))
+
+
 def main():
     args = parse()
     if args.probe_peaks:
@@ -638,6 +851,8 @@ def main():
         run_profile_step(args)
     elif args.impl == "reference":
         run_reference(args)
+    elif WORKLOADS[args.workload].get("kind") == "ensemble":
+        run_ensemble(args)
     else:
         run_ours(args)
 

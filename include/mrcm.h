@@ -109,6 +109,31 @@ int mrcm_setup(mrcm_ctx** out, const mrcm_grid* g, const double* K_dev,
                const int bc_type[6], int precision, void* cuda_stream);
 
 /*
+ * mrcm_setup_batch -- one context for `count` independent problems (an
+ * ensemble of realisations, Section 5's permeability studies run many at
+ * once), each on its own grid: grids[k] and bc_types[6 k .. 6 k + 5] as in
+ * mrcm_setup; sub_cells, seg_cells, alpha and precision shared.  Every grid
+ * gets its own leaves (truncated at its own edges), segments and merge
+ * tree; the build and solve then run all of them together, one launch per
+ * tree height over every tree (the Recursive MRCM of Algorithm 1 applied to
+ * each problem), so small problems fill the GPU as one large one would.
+ * The paper solves one problem at a time; batching is this library's.
+ *
+ * Arrays of a batched context are the problems' arrays concatenated in
+ * grid order: K_dev, q, p (sum of n[0] n[1]), Fx (sum of (n[0]+1) n[1]),
+ * Fy (sum of n[0] (n[1]+1)), bc_val (sum of 2 (n[0] + n[1])), and the
+ * one-sided fluxes [Fa_x | Fb_x | Fa_y | Fb_y], each part concatenated in
+ * grid order.  mrcm_setup is mrcm_setup_batch with count 1.
+ *
+ * Errors as mrcm_setup; MRCM_ERR_UNSUPPORTED when count > 1 and a problem
+ * has no Dirichlet side (the zero-mean all-Neumann form is single-problem
+ * only); MRCM_ERR_INVALID_ARG beyond 2^31 cells or faces in total.
+ */
+int mrcm_setup_batch(mrcm_ctx** out, int count, const mrcm_grid* grids, const int* bc_types,
+                     const double* K_dev, const int sub_cells[3], const int seg_cells[3], double alpha,
+                     int precision, void* cuda_stream);
+
+/*
  * mrcm_set_permeability -- replace K (same grid), invalidating the basis.
  * K_dev: device array of n[0]*n[1] values > 0, copied.
  */
@@ -186,8 +211,10 @@ enum {
        m (m + 1) n + 4 n b (n cells, bandwidth b, m segments), LU-based
        merges (2/3) N^3 + 2 N^2 (m + 1) + 2 m g (m + 1) (N = 2g) */
     MRCM_Q_MODEL_BUILD_FLOPS = 12, /* the whole build under that model        */
-    MRCM_Q_MODEL_SWEEP_FLOPS = 13  /* (2/3) N^3 of the merges that run in the
+    MRCM_Q_MODEL_SWEEP_FLOPS = 13, /* (2/3) N^3 of the merges that run in the
                                      blocked sweep (MRCM_PHASE_GJ_SWEEP)     */
+    MRCM_Q_GRIDS = 14,        /* problems in the context (mrcm_setup_batch)   */
+    MRCM_Q_CELLS = 15         /* cells over all of them                       */
 };
 
 /* mrcm_query -- integer facts about a context.  value: host out pointer. */
@@ -356,8 +383,9 @@ int mrcm_phase_flops(const mrcm_ctx* ctx, double* flops);
  * mrcm_node_info: info[0] = height (0 for leaves), info[1] = m (outer
  * segments), info[2] = g (segments on the node's internal interface gamma,
  * 0 for leaves), info[3], info[4] = children (-1 for leaves), info[5] =
- * parent (-1 for the root), info[6] = leaf index or -1, info[7..10] = leaf
- * box I0, I1, J0, J1 (half-open).  Nodes 0..leaves-1 are the leaves.
+ * parent (-1 for a root), info[6] = leaf index or -1, info[7..10] = leaf
+ * box I0, I1, J0, J1 (half-open, in the leaf grid of the node's own
+ * problem).  Nodes 0..leaves-1 are the leaves (problem after problem).
  *
  * mrcm_node_segments: seg_ids[m] = the node's outer segments in the order
  * its R uses.

@@ -7,8 +7,8 @@ part of the computation.
 """
 from .fields import gaussian_random_field, lognormal_permeability
 from .problems import (Problem, darcy_problem, config_64, config_1024,
-                       config_4096, NEUMANN, DIRICHLET)
+                       config_4096, ensemble_member, NEUMANN, DIRICHLET)
 
 __all__ = ["gaussian_random_field", "lognormal_permeability", "Problem",
-           "darcy_problem", "config_64", "config_1024", "config_4096",
+           "darcy_problem", "config_64", "config_1024", "config_4096", "ensemble_member",
            "NEUMANN", "DIRICHLET"]

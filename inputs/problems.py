@@ -122,3 +122,17 @@ def config_4096(n=4096):
     return darcy_problem(n, n, sigma2=3.0, corr=0.02, seed=5000,
                          bc="quarter_five_spot", alpha=1.0,
                          name=f"square{n}-qfs")
+
+
+def ensemble_member(r, nmin=250, nmax=1000, seed0=4000):
+    """Realisation r of the batched ensemble workload: a unit square with nx,
+    ny drawn uniformly from nmin..nmax cells and a log-normal K with sigma^2
+    drawn uniformly from [1, 4], correlation length 0.05 (seed seed0 + r for
+    both draws); p = 1 on x = 0, p = 0 on x = 1, no-flow on y = 0 and y = 1;
+    16 x 16 leaves (truncated at the right and top edges), 4-cell segments,
+    alpha = 1."""
+    rng = np.random.default_rng(seed0 + r)
+    nx, ny = (int(x) for x in rng.integers(nmin, nmax + 1, 2))
+    sigma2 = float(rng.uniform(1.0, 4.0))
+    return darcy_problem(nx, ny, sigma2=sigma2, corr=0.05, seed=seed0 + r, bc="left_right", alpha=1.0,
+                         Lx=1.0, Ly=1.0, name=f"ensemble{r}-{nx}x{ny}")

@@ -3,18 +3,18 @@
 The compute path is libmrcm.so (hand-written sm_103a CUDA behind the C ABI
 of include/mrcm.h); this package only builds it and marshals arguments.
 """
-from .binding import (mrcm_setup, mrcm_plan_query, mrcm_set_permeability, mrcm_build_basis, mrcm_solve,
+from .binding import (mrcm_setup, mrcm_setup_batch, mrcm_plan_query, mrcm_set_permeability, mrcm_build_basis, mrcm_solve,
                       mrcm_query, mrcm_node_info, mrcm_node_segments, mrcm_segment_info,
                       mrcm_node_operator, mrcm_destroy, mrcm_error_string, mrcm_enable_timing, mrcm_use_graphs,
                       mrcm_last_cuda_error,
                       mrcm_phase_times, mrcm_merge_pair_noalloc, mrcm_set_refinement,
                       mrcm_residual_history, mrcm_phase_flops, mrcm_group_times, mrcm_check_reciprocal, mrcm_set_wait_limit, mrcm_probe_peak, mrcm_set_mixed_split, mrcm_autotune, mrcm_tune_info, PROBES, MrcmError, PHASES, PHASE_KERNELS,
                       EXPORTS, LIB_PATH)
-from .solver import Solver
+from .solver import Solver, BatchSolver
 
-__all__ = ["mrcm_setup", "mrcm_plan_query", "mrcm_set_permeability", "mrcm_build_basis", "mrcm_solve", "mrcm_query",
+__all__ = ["mrcm_setup", "mrcm_setup_batch", "mrcm_plan_query", "mrcm_set_permeability", "mrcm_build_basis", "mrcm_solve", "mrcm_query",
            "mrcm_node_info", "mrcm_node_segments", "mrcm_segment_info", "mrcm_node_operator",
            "mrcm_destroy", "mrcm_error_string", "mrcm_enable_timing", "mrcm_phase_times", "mrcm_use_graphs",
            "mrcm_last_cuda_error",
            "mrcm_merge_pair_noalloc", "mrcm_set_refinement", "mrcm_residual_history", "mrcm_phase_flops",
-           "mrcm_group_times", "mrcm_check_reciprocal", "mrcm_set_wait_limit", "mrcm_probe_peak", "mrcm_set_mixed_split", "mrcm_autotune", "mrcm_tune_info", "PROBES", "MrcmError", "PHASE_KERNELS", "PHASES", "EXPORTS", "LIB_PATH", "Solver"]
+           "mrcm_group_times", "mrcm_check_reciprocal", "mrcm_set_wait_limit", "mrcm_probe_peak", "mrcm_set_mixed_split", "mrcm_autotune", "mrcm_tune_info", "PROBES", "MrcmError", "PHASE_KERNELS", "PHASES", "EXPORTS", "LIB_PATH", "Solver", "BatchSolver"]

@@ -18,10 +18,11 @@ ERRORS = {0: "MRCM_OK", -1: "MRCM_ERR_INVALID_ARG", -2: "MRCM_ERR_SHAPE", -3: "M
           -7: "MRCM_ERR_OOM", -8: "MRCM_ERR_TIMEOUT", -9: "MRCM_ERR_UNSUPPORTED"}
 Q = dict(LEAVES=0, SEGMENTS=1, LEVELS=2, NODES=3, WORKSPACE_BYTES=4, MAX_GAMMA=5,
          BUILD_FLOPS=6, SOLVE_FLOPS=7, LEAF_FLOPS=8, KERNEL_LAUNCHES_BUILD=9,
-         KERNEL_LAUNCHES_SOLVE=10, GRAPH_REPLAYS=11, MODEL_BUILD_FLOPS=12, MODEL_SWEEP_FLOPS=13)
+         KERNEL_LAUNCHES_SOLVE=10, GRAPH_REPLAYS=11, MODEL_BUILD_FLOPS=12, MODEL_SWEEP_FLOPS=13,
+         GRIDS=14, CELLS=15)
 
 # every symbol include/mrcm.h declares
-EXPORTS = ["mrcm_setup", "mrcm_plan_query", "mrcm_set_permeability", "mrcm_build_basis", "mrcm_solve", "mrcm_query",
+EXPORTS = ["mrcm_setup", "mrcm_setup_batch", "mrcm_plan_query", "mrcm_set_permeability", "mrcm_build_basis", "mrcm_solve", "mrcm_query",
            "mrcm_node_info", "mrcm_node_segments", "mrcm_segment_info", "mrcm_node_operator",
            "mrcm_destroy", "mrcm_error_string", "mrcm_enable_timing", "mrcm_phase_times", "mrcm_use_graphs",
            "mrcm_last_cuda_error",
@@ -68,6 +69,8 @@ def _lib():
         IP = ctypes.POINTER(ctypes.c_int)
         lib.mrcm_setup.argtypes = [ctypes.POINTER(P), ctypes.POINTER(mrcm_grid), P, IP, IP, D, IP, I, P]
         lib.mrcm_setup.restype = I
+        lib.mrcm_setup_batch.argtypes = [ctypes.POINTER(P), I, ctypes.POINTER(mrcm_grid), IP, P, IP, IP, D, I, P]
+        lib.mrcm_setup_batch.restype = I
         lib.mrcm_plan_query.argtypes = [ctypes.POINTER(mrcm_grid), IP, IP, IP, I,
                                         ctypes.POINTER(ctypes.c_longlong)]
         lib.mrcm_plan_query.restype = I
@@ -153,6 +156,25 @@ def mrcm_setup(n, L, K, sub_cells=(16, 16), seg_cells=(4, 4), alpha=1.0,
     _check(_lib().mrcm_setup(ctypes.byref(ctx), ctypes.byref(g), _ptr(K), _ints(sub_cells, 3),
                              _ints(seg_cells, 3), float(alpha), _ints(bc_type, 6), int(precision),
                              stream), "mrcm_setup")
+    return ctx
+
+
+def mrcm_setup_batch(ns, Ls, bc_types, K, sub_cells=(16, 16), seg_cells=(4, 4), alpha=1.0,
+                     precision=MRCM_FP64, stream=0):
+    """One context for several problems: ns[k] = (nx, ny), Ls[k] = (Lx, Ly),
+    bc_types[k] = (x-, x+, y-, y+); K holds their permeabilities
+    concatenated in problem order."""
+    count = len(ns)
+    grids = (mrcm_grid * count)()
+    for k, (n, L) in enumerate(zip(ns, Ls)):
+        grids[k] = mrcm_grid(2, (ctypes.c_int * 3)(n[0], n[1], 1), (ctypes.c_double * 3)(L[0], L[1], 1.0))
+    bcs = []
+    for b in bc_types:
+        bcs += list(b) + [0] * (6 - len(b))
+    ctx = ctypes.c_void_p()
+    _check(_lib().mrcm_setup_batch(ctypes.byref(ctx), count, grids, _ints(bcs, 6 * count), _ptr(K),
+                                   _ints(sub_cells, 3), _ints(seg_cells, 3), float(alpha), int(precision),
+                                   stream), "mrcm_setup_batch")
     return ctx
 
 

@@ -61,14 +61,15 @@ struct CellFaces {
 };
 
 __device__ __forceinline__ CellFaces cell_faces(const DevView& v, const LeafDesc& L, int i, int j) {
+    const GridDesc& G = v.grids[L.grid];
     const int gi = L.i0 + i, gj = L.j0 + j;
-    const long long fx = gi + (long long)(v.nx + 1) * gj;
-    const long long fy = gi + (long long)v.nx * gj;
+    const long long fx = G.fx0 + gi + (long long)(G.nx + 1) * gj;
+    const long long fy = G.fy0 + gi + (long long)G.nx * gj;
     CellFaces c;
     c.w_ = v.cxU[fx];
     c.e_ = v.cxL[fx + 1];
     c.s_ = v.cyU[fy];
-    c.n_ = v.cyL[fy + v.nx];
+    c.n_ = v.cyL[fy + G.nx];
     c.tx = (i > 0) ? v.cxL[fx] : 0.0;
     c.ty = (j > 0) ? v.cyL[fy] : 0.0;
     return c;
@@ -119,12 +120,17 @@ __device__ __forceinline__ double segment_rho_sum(const DevView& v, const LeafDe
         if (L.side_off[d] >= 0 && s >= L.side_off[d]) side = d;
     const int p = s - L.side_off[side];
     const int len = side < 2 ? L.h : L.w, g = side < 2 ? v.gy : v.gx;
+    const GridDesc& G = v.grids[L.grid];
+    const double* cxL = v.cxL + G.fx0;
+    const double* cxU = v.cxU + G.fx0;
+    const double* cyL = v.cyL + G.fy0;
+    const double* cyU = v.cyU + G.fy0;
     double sum = 0.0;
     for (int e = p * g; e < min((p + 1) * g, len); ++e) {
-        if (side == 0) sum += v.cxU[(long long)L.i0 + (long long)(v.nx + 1) * (L.j0 + e)];
-        else if (side == 1) sum += v.cxL[(long long)(L.i0 + L.w) + (long long)(v.nx + 1) * (L.j0 + e)];
-        else if (side == 2) sum += v.cyU[(long long)(L.i0 + e) + (long long)v.nx * L.j0];
-        else sum += v.cyL[(long long)(L.i0 + e) + (long long)v.nx * (L.j0 + L.h)];
+        if (side == 0) sum += cxU[(long long)L.i0 + (long long)(G.nx + 1) * (L.j0 + e)];
+        else if (side == 1) sum += cxL[(long long)(L.i0 + L.w) + (long long)(G.nx + 1) * (L.j0 + e)];
+        else if (side == 2) sum += cyU[(long long)(L.i0 + e) + (long long)G.nx * L.j0];
+        else sum += cyL[(long long)(L.i0 + e) + (long long)G.nx * (L.j0 + L.h)];
     }
     return sum;
 }
@@ -304,25 +310,27 @@ leaf_build_kernel(DevView v) {
 // source plus Dirichlet and Neumann data of the leaf's domain-boundary faces.
 __device__ __forceinline__ double particular_rhs(const DevView& v, const LeafDesc& L, const double* q,
                                                  const double* bc_val, int row) {
+    const GridDesc& G = v.grids[L.grid];
     const int i = row % L.w, j = row / L.w;
     const int gi = L.i0 + i, gj = L.j0 + j;
-    double b = q[(long long)gj * v.nx + gi];
+    double b = q[G.c0 + (long long)gj * G.nx + gi];
     if (!bc_val) return b;
+    const double* bv = bc_val + G.b0;
     if (gi == 0) {
-        const double g = bc_val[gj];
-        b += v.bc[0] ? v.cxU[(long long)(v.nx + 1) * gj] * g : -v.hy * g;
+        const double g = bv[gj];
+        b += G.bc[0] ? v.cxU[G.fx0 + (long long)(G.nx + 1) * gj] * g : -G.hy * g;
     }
-    if (gi == v.nx - 1) {
-        const double g = bc_val[v.ny + gj];
-        b += v.bc[1] ? v.cxL[v.nx + (long long)(v.nx + 1) * gj] * g : -v.hy * g;
+    if (gi == G.nx - 1) {
+        const double g = bv[G.ny + gj];
+        b += G.bc[1] ? v.cxL[G.fx0 + G.nx + (long long)(G.nx + 1) * gj] * g : -G.hy * g;
     }
     if (gj == 0) {
-        const double g = bc_val[2 * v.ny + gi];
-        b += v.bc[2] ? v.cyU[gi] * g : -v.hx * g;
+        const double g = bv[2 * G.ny + gi];
+        b += G.bc[2] ? v.cyU[G.fy0 + gi] * g : -G.hx * g;
     }
-    if (gj == v.ny - 1) {
-        const double g = bc_val[2 * v.ny + v.nx + gi];
-        b += v.bc[3] ? v.cyL[gi + (long long)v.nx * v.ny] * g : -v.hx * g;
+    if (gj == G.ny - 1) {
+        const double g = bv[2 * G.ny + G.nx + gi];
+        b += G.bc[3] ? v.cyL[G.fy0 + gi + (long long)G.nx * G.ny] * g : -G.hx * g;
     }
     return b;
 }
@@ -476,9 +484,10 @@ __device__ __forceinline__ void leaf_pressure_body(const DevView& v, bool accumu
             __syncwarp(mask);
         }
     }
+    const GridDesc& G = v.grids[L.grid];
     for (int k = t; k < n; k += kLeafThreads) {
         const int i = k % w, j = k / w;
-        const long long c = (long long)(L.j0 + j) * v.nx + L.i0 + i;
+        const long long c = G.c0 + (long long)(L.j0 + j) * G.nx + L.i0 + i;
         if (accumulate) {
             const DD x = dd_add(DD{v.p_hi[c], v.p_lo[c]}, DD{S.y[k], 0.0});
             v.p_hi[c] = x.h;
@@ -614,7 +623,7 @@ cudaError_t launch_leaf_pressure(const DevView& v, bool accumulate, cudaStream_t
 }
 
 cudaError_t launch_mean_shift(const DevView& v, bool plain, cudaStream_t s) {
-    const long long n = (long long)v.nx * v.ny;
+    const long long n = v.ncell;      // all-Neumann problems: single-grid contexts only
     mean_partial_kernel<<<kRedBlocks, 256, 0, s>>>(v.p_hi, v.p_lo, n, v.red);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

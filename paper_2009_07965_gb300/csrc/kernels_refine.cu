@@ -71,12 +71,12 @@ __device__ __forceinline__ DD face_out_u(DD pc, DD pn, double coef) { return dd_
 
 // One face of cell c: its outward flux in the residual sum.  lower: the cell
 // lies below / left of the face (side a of a skeleton segment).
-__device__ __forceinline__ DD cell_face(const DevView& v, const double* bc_val, int bc_side, bool boundary,
+__device__ __forceinline__ DD cell_face(const DevView& v, const double* bc_val, int dirichlet, bool boundary,
                                         int seg, bool lower, double coef, double area, DD pc, long long nb,
-                                        int bc_index) {
+                                        long long bc_index) {
     if (boundary) {
         const double g = bc_val[bc_index];
-        if (v.bc[bc_side]) return face_out_u(pc, DD{g, 0.0}, coef);
+        if (dirichlet) return face_out_u(pc, DD{g, 0.0}, coef);
         return dd_two_prod(area, g);                 // Neumann: |e| g_N outward
     }
     if (seg >= 0) return face_out_u(pc, seg_lam(v, seg, lower ? 0 : 1), coef);
@@ -85,24 +85,25 @@ __device__ __forceinline__ DD cell_face(const DevView& v, const double* bc_val, 
 
 __global__ void __launch_bounds__(256) residual_cells_kernel(DevView v, const double* __restrict__ q,
                                                              const double* __restrict__ bc_val, int step) {
-    const long long n = (long long)v.nx * v.ny;
     const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     double e = 0.0;
-    if (c < n) {
+    if (c < v.ncell) {
+        const GridDesc& G = v.grids[grid_of<0>(v, c)];
         int i, j;
-        udivmod(c, v.nx, j, i);
+        udivmod(c - G.c0, G.nx, j, i);
         const DD pc = state_p(v, c);
-        const long long fx = i + (long long)(v.nx + 1) * j;
-        const long long fy = i + (long long)v.nx * j;
+        const long long fx = G.fx0 + i + (long long)(G.nx + 1) * j;
+        const long long fy = G.fy0 + i + (long long)G.nx * j;
+        const long long b0 = G.b0;
         DD E = dd_two_sum(0.0, -q[c]);
-        E = dd_acc_u(E, cell_face(v, bc_val, 0, i == 0, i > 0 ? v.xface_seg[fx] : -1, false, v.cxU[fx], v.hy, pc,
-                                  c - 1, j));
-        E = dd_acc_u(E, cell_face(v, bc_val, 1, i == v.nx - 1, i < v.nx - 1 ? v.xface_seg[fx + 1] : -1, true,
-                                  v.cxL[fx + 1], v.hy, pc, c + 1, v.ny + j));
-        E = dd_acc_u(E, cell_face(v, bc_val, 2, j == 0, j > 0 ? v.yface_seg[fy] : -1, false, v.cyU[fy], v.hx, pc,
-                                  c - v.nx, 2 * v.ny + i));
-        E = dd_acc_u(E, cell_face(v, bc_val, 3, j == v.ny - 1, j < v.ny - 1 ? v.yface_seg[fy + v.nx] : -1, true,
-                                  v.cyL[fy + v.nx], v.hx, pc, c + v.nx, 2 * v.ny + v.nx + i));
+        E = dd_acc_u(E, cell_face(v, bc_val, G.bc[0], i == 0, i > 0 ? v.xface_seg[fx] : -1, false, v.cxU[fx], G.hy,
+                                  pc, c - 1, b0 + j));
+        E = dd_acc_u(E, cell_face(v, bc_val, G.bc[1], i == G.nx - 1, i < G.nx - 1 ? v.xface_seg[fx + 1] : -1, true,
+                                  v.cxL[fx + 1], G.hy, pc, c + 1, b0 + G.ny + j));
+        E = dd_acc_u(E, cell_face(v, bc_val, G.bc[2], j == 0, j > 0 ? v.yface_seg[fy] : -1, false, v.cyU[fy], G.hx,
+                                  pc, c - G.nx, b0 + 2 * G.ny + i));
+        E = dd_acc_u(E, cell_face(v, bc_val, G.bc[3], j == G.ny - 1, j < G.ny - 1 ? v.yface_seg[fy + G.nx] : -1,
+                                  true, v.cyL[fy + G.nx], G.hx, pc, c + G.nx, b0 + 2 * G.ny + G.nx + i));
         e = E.h + E.l;
         v.rcell[c] = -e;
     }
@@ -114,6 +115,7 @@ __global__ void __launch_bounds__(128) residual_segments_kernel(DevView v, int s
     double E13 = 0.0, E14 = 0.0;
     if (t < v.nseg) {
         const int axis = v.seg_axis[t], line = v.seg_line[t], lo = v.seg_lo[t], len = v.seg_len[t];
+        const GridDesc& G = v.grids[v.seg_grid[t]];
         const DD la = seg_lam(v, t, 0), lb = seg_lam(v, t, 1);
         DD Fa = {0.0, 0.0}, Fb = {0.0, 0.0};
         for (int e = 0; e < len; ++e) {
@@ -121,23 +123,23 @@ __global__ void __launch_bounds__(128) residual_segments_kernel(DevView v, int s
             double ra, rb;
             if (axis == 0) {
                 const int j = lo + e;
-                ca = (long long)j * v.nx + line - 1;
+                ca = G.c0 + (long long)j * G.nx + line - 1;
                 cb = ca + 1;
-                f = line + (long long)(v.nx + 1) * j;
+                f = G.fx0 + line + (long long)(G.nx + 1) * j;
                 ra = v.cxL[f];
                 rb = v.cxU[f];
             } else {
                 const int i = lo + e;
-                ca = (long long)(line - 1) * v.nx + i;
-                cb = ca + v.nx;
-                f = i + (long long)v.nx * line;
+                ca = G.c0 + (long long)(line - 1) * G.nx + i;
+                cb = ca + G.nx;
+                f = G.fy0 + i + (long long)G.nx * line;
                 ra = v.cyL[f];
                 rb = v.cyU[f];
             }
             Fa = dd_acc_u(Fa, face_out_u(state_p(v, ca), la, ra));
             Fb = dd_acc_u(Fb, face_out_u(state_p(v, cb), lb, rb));
         }
-        const double length = len * (axis == 0 ? v.hy : v.hx);
+        const double length = len * (axis == 0 ? G.hy : G.hx);
         const DD two_u = dd_scale_u(DD{v.segU[t], v.segU_lo[t]}, 2.0 * length);
         const DD e13 = dd_acc_u(Fa, Fb);
         const DD e14 = dd_sub_u(dd_sub_u(Fa, Fb), two_u);
@@ -182,34 +184,34 @@ __global__ void lam_to_PU_kernel(DevView v, bool accumulate) {
 template <bool kPlain>
 __global__ void face_flux_kernel(DevView v, const double* __restrict__ bc_val, double* __restrict__ p,
                                  double* __restrict__ Fx, double* __restrict__ Fy, double* __restrict__ iface) {
-    const long long nxf = (long long)(v.nx + 1) * v.ny;
-    const long long nyf = (long long)v.nx * (v.ny + 1);
-    const long long ncell = (long long)v.nx * v.ny;
+    const long long nxf = v.nxface, nyf = v.nyface;
     long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (f < ncell) p[f] = v.p_hi[f] + v.p_lo[f];
+    if (f < v.ncell) p[f] = v.p_hi[f] + v.p_lo[f];
     if (f >= nxf + nyf) return;
     const bool xface = f < nxf;
-    const long long fl = xface ? f : f - nxf;
+    const long long fl = xface ? f : f - nxf;        // index in Fx or Fy (all grids)
+    const GridDesc& G = v.grids[xface ? grid_of<1>(v, fl) : grid_of<2>(v, fl)];
     double F, fa = 0.0, fb = 0.0;
     bool skel = false;
     int axis, line, k;
-    if (xface) { axis = 0; udivmod(fl, v.nx + 1, k, line); }
-    else { axis = 1; udivmod(fl, v.nx, line, k); }
-    const int nline = axis == 0 ? v.nx : v.ny;
+    if (xface) { axis = 0; udivmod(fl - G.fx0, G.nx + 1, k, line); }
+    else { axis = 1; udivmod(fl - G.fy0, G.nx, line, k); }
+    const int nline = axis == 0 ? G.nx : G.ny;
     const double* cL = axis == 0 ? v.cxL : v.cyL;
     const double* cU = axis == 0 ? v.cxU : v.cyU;
     // cells below / above the face
-    const long long cb = axis == 0 ? (long long)k * v.nx + line : (long long)line * v.nx + k;
-    const long long ca = axis == 0 ? cb - 1 : cb - v.nx;
-    const double area = axis == 0 ? v.hy : v.hx;
+    const long long cb = G.c0 + (axis == 0 ? (long long)k * G.nx + line : (long long)line * G.nx + k);
+    const long long ca = axis == 0 ? cb - 1 : cb - G.nx;
+    const double area = axis == 0 ? G.hy : G.hx;
+    const double* bv = bc_val + G.b0;
     if (kPlain) {
         // state without low parts (no refinement step): plain FP64
         if (line == 0) {
-            const double g = bc_val[axis == 0 ? k : 2 * v.ny + k];
-            F = v.bc[2 * axis] ? -(cU[fl] * (v.p_hi[cb] - g)) : -(area * g);
+            const double g = bv[axis == 0 ? k : 2 * G.ny + k];
+            F = G.bc[2 * axis] ? -(cU[fl] * (v.p_hi[cb] - g)) : -(area * g);
         } else if (line == nline) {
-            const double g = bc_val[axis == 0 ? v.ny + k : 2 * v.ny + v.nx + k];
-            F = v.bc[2 * axis + 1] ? cL[fl] * (v.p_hi[ca] - g) : area * g;
+            const double g = bv[axis == 0 ? G.ny + k : 2 * G.ny + G.nx + k];
+            F = G.bc[2 * axis + 1] ? cL[fl] * (v.p_hi[ca] - g) : area * g;
         } else {
             const int t = axis == 0 ? v.xface_seg[fl] : v.yface_seg[fl];
             if (t >= 0) {
@@ -225,12 +227,12 @@ __global__ void face_flux_kernel(DevView v, const double* __restrict__ bc_val, d
             }
         }
     } else if (line == 0) {
-        const double g = bc_val[axis == 0 ? k : 2 * v.ny + k];
-        DD out = v.bc[2 * axis] ? face_out_u(state_p(v, cb), DD{g, 0.0}, cU[fl]) : DD{__dmul_rn(area, g), 0.0};
+        const double g = bv[axis == 0 ? k : 2 * G.ny + k];
+        DD out = G.bc[2 * axis] ? face_out_u(state_p(v, cb), DD{g, 0.0}, cU[fl]) : DD{__dmul_rn(area, g), 0.0};
         F = -(out.h + out.l);
     } else if (line == nline) {
-        const double g = bc_val[axis == 0 ? v.ny + k : 2 * v.ny + v.nx + k];
-        DD out = v.bc[2 * axis + 1] ? face_out_u(state_p(v, ca), DD{g, 0.0}, cL[fl]) : DD{__dmul_rn(area, g), 0.0};
+        const double g = bv[axis == 0 ? G.ny + k : 2 * G.ny + G.nx + k];
+        DD out = G.bc[2 * axis + 1] ? face_out_u(state_p(v, ca), DD{g, 0.0}, cL[fl]) : DD{__dmul_rn(area, g), 0.0};
         F = out.h + out.l;
     } else {
         const int t = axis == 0 ? v.xface_seg[fl] : v.yface_seg[fl];
@@ -273,7 +275,9 @@ constexpr int kCompatBlocks = 256;
 __global__ void __launch_bounds__(256) compat_partial_kernel(DevView v, const double* __restrict__ q,
                                                              const double* __restrict__ bc_val) {
     __shared__ double sh_h[256], sh_l[256], sh_a[256];
-    const long long n = (long long)v.nx * v.ny, nb = 2LL * (v.nx + v.ny);
+    // all-Neumann problems: single-grid contexts only
+    const GridDesc& G = v.grids[0];
+    const long long n = v.ncell, nb = v.nbc;
     DD acc = {0.0, 0.0};
     double mag = 0.0;
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -286,7 +290,7 @@ __global__ void __launch_bounds__(256) compat_partial_kernel(DevView v, const do
         if (i < n) {
             x = {val, 0.0};
         } else {
-            const double area = i - n < 2LL * v.ny ? v.hy : v.hx;
+            const double area = i - n < 2LL * G.ny ? G.hy : G.hx;
             x = dd_neg(dd_two_prod(area, val));
         }
         acc = dd_add(acc, x);
@@ -343,7 +347,7 @@ cudaError_t launch_compat_check(const DevView& v, const double* q, const double*
 
 cudaError_t launch_residual(const DevView& v, const double* q, const double* bc_val, int step,
                             cudaStream_t s) {
-    const long long n = (long long)v.nx * v.ny;
+    const long long n = v.ncell;
     residual_cells_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(v, q, bc_val, step);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || v.nseg == 0) return e;
@@ -359,7 +363,7 @@ cudaError_t launch_lam_to_PU(const DevView& v, bool accumulate, cudaStream_t s) 
 
 cudaError_t launch_face_fluxes(const DevView& v, const double* bc_val, double* p, double* Fx,
                                double* Fy, double* iface, bool plain, cudaStream_t s) {
-    const long long nf = (long long)(v.nx + 1) * v.ny + (long long)v.nx * (v.ny + 1);
+    const long long nf = v.nxface + v.nyface;
     if (plain)
         face_flux_kernel<true><<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(v, bc_val, p, Fx, Fy, iface);
     else

@@ -33,56 +33,58 @@ __global__ void check_K_kernel(const double* __restrict__ K, long long n, int* s
 // Half-cell resistances r = h_d / (2 K_c), the building block of every face
 // coefficient below (evaluated once per cell, in this order).
 __global__ void cell_resist_kernel(DevView v) {
-    const long long n = (long long)v.nx * v.ny;
     const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (c >= n) return;
+    if (c >= v.ncell) return;
+    const GridDesc& G = v.grids[grid_of<0>(v, c)];
     const double k2 = 2.0 * v.K[c];
-    v.rx[c] = v.hx / k2;
-    v.ry[c] = v.hy / k2;
+    v.rx[c] = G.hx / k2;
+    v.ry[c] = G.hy / k2;
 }
 
 __global__ void seg_beta_kernel(DevView v) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= v.nseg) return;
     const int axis = v.seg_axis[t], line = v.seg_line[t], lo = v.seg_lo[t], len = v.seg_len[t];
+    const GridDesc& G = v.grids[v.seg_grid[t]];
+    const double* K = v.K + G.c0;
     double sum = 0.0;
     for (int e = 0; e < len; ++e) {
         double ka, kb;
         if (axis == 0) {
-            const long long row = (long long)(lo + e) * v.nx;
-            ka = v.K[row + line - 1];
-            kb = v.K[row + line];
+            const long long row = (long long)(lo + e) * G.nx;
+            ka = K[row + line - 1];
+            kb = K[row + line];
         } else {
-            ka = v.K[(long long)(line - 1) * v.nx + lo + e];
-            kb = v.K[(long long)line * v.nx + lo + e];
+            ka = K[(long long)(line - 1) * G.nx + lo + e];
+            kb = K[(long long)line * G.nx + lo + e];
         }
         sum += 2.0 * ka * kb / (ka + kb);
     }
     const double keff = sum / len;
-    const double length = len * (axis == 0 ? v.hy : v.hx);
+    const double length = len * (axis == 0 ? G.hy : G.hx);
     v.seg_beta[t] = v.alpha * length / keff;
     // D = |t| / (2 beta) = Keff / (2 alpha)
     v.seg_D[t] = keff / (2.0 * v.alpha);
 }
 
 __global__ void face_coef_kernel(DevView v) {
-    const long long nxf = (long long)(v.nx + 1) * v.ny;
-    const long long nyf = (long long)v.nx * (v.ny + 1);
     long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (f < nxf) {
+    if (f < v.nxface) {
+        const GridDesc& G = v.grids[grid_of<1>(v, f)];
         int i, j;
-        udivmod(f, v.nx + 1, j, i);
-        const double area = v.hy, hn = v.hx;
-        const long long row = (long long)j * v.nx;
+        udivmod(f - G.fx0, G.nx + 1, j, i);
+        const double area = G.hy, hn = G.hx;
+        const long long row = G.c0 + (long long)j * G.nx;
         double cl = 0.0, cu = 0.0;
         if (i == 0) {
-            if (v.bc[0]) cu = 2.0 * v.K[row] * area / hn;
-        } else if (i == v.nx) {
-            if (v.bc[1]) cl = 2.0 * v.K[row + v.nx - 1] * area / hn;
+            if (G.bc[0]) cu = 2.0 * v.K[row] * area / hn;
+        } else if (i == G.nx) {
+            if (G.bc[1]) cl = 2.0 * v.K[row + G.nx - 1] * area / hn;
         } else {
             const double ra = v.rx[row + i - 1], rb = v.rx[row + i];
-            if (i % v.sx == 0) {
-                const double beta = v.seg_beta[skeleton_segment(v, 0, i, j)];
+            const int t = v.xface_seg[f];
+            if (t >= 0) {
+                const double beta = v.seg_beta[t];
                 cl = area / (ra + beta);
                 cu = area / (rb + beta);
             } else {
@@ -93,20 +95,23 @@ __global__ void face_coef_kernel(DevView v) {
         v.cxU[f] = cu;
         return;
     }
-    f -= nxf;
-    if (f < nyf) {
+    f -= v.nxface;
+    if (f < v.nyface) {
+        const GridDesc& G = v.grids[grid_of<2>(v, f)];
         int i, j;
-        udivmod(f, v.nx, j, i);
-        const double area = v.hx, hn = v.hy;
+        udivmod(f - G.fy0, G.nx, j, i);
+        const double area = G.hx, hn = G.hy;
+        const double* K = v.K + G.c0;
         double cl = 0.0, cu = 0.0;
         if (j == 0) {
-            if (v.bc[2]) cu = 2.0 * v.K[i] * area / hn;
-        } else if (j == v.ny) {
-            if (v.bc[3]) cl = 2.0 * v.K[(long long)(v.ny - 1) * v.nx + i] * area / hn;
+            if (G.bc[2]) cu = 2.0 * K[i] * area / hn;
+        } else if (j == G.ny) {
+            if (G.bc[3]) cl = 2.0 * K[(long long)(G.ny - 1) * G.nx + i] * area / hn;
         } else {
-            const double ra = v.ry[(long long)(j - 1) * v.nx + i], rb = v.ry[(long long)j * v.nx + i];
-            if (j % v.sy == 0) {
-                const double beta = v.seg_beta[skeleton_segment(v, 1, j, i)];
+            const double ra = v.ry[G.c0 + (long long)(j - 1) * G.nx + i], rb = v.ry[G.c0 + (long long)j * G.nx + i];
+            const int t = v.yface_seg[f];
+            if (t >= 0) {
+                const double beta = v.seg_beta[t];
                 cl = area / (ra + beta);
                 cu = area / (rb + beta);
             } else {
@@ -134,7 +139,7 @@ cudaError_t launch_reciprocal(const double* x, double* r, long long n, cudaStrea
 }
 
 cudaError_t launch_check_K(const DevView& v, cudaStream_t s) {
-    const long long n = (long long)v.nx * v.ny;
+    const long long n = v.ncell;
     int blocks = (int)((n + 255) / 256);
     if (blocks > 152 * 8) blocks = 152 * 8;
     check_K_kernel<<<blocks, 256, 0, s>>>(v.K, n, v.status);
@@ -142,7 +147,7 @@ cudaError_t launch_check_K(const DevView& v, cudaStream_t s) {
 }
 
 cudaError_t launch_cell_resist(const DevView& v, cudaStream_t s) {
-    const long long n = (long long)v.nx * v.ny;
+    const long long n = v.ncell;
     cell_resist_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(v);
     return cudaGetLastError();
 }
@@ -154,7 +159,7 @@ cudaError_t launch_seg_beta(const DevView& v, cudaStream_t s) {
 }
 
 cudaError_t launch_face_coef(const DevView& v, cudaStream_t s) {
-    const long long nf = (long long)(v.nx + 1) * v.ny + (long long)v.nx * (v.ny + 1);
+    const long long nf = v.nxface + v.nyface;
     face_coef_kernel<<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(v);
     return cudaGetLastError();
 }

@@ -23,16 +23,18 @@ namespace {
 constexpr int kMaxRefine = 16;
 
 struct Plan {
-    int nx = 0, ny = 0;
-    double hx = 0, hy = 0, alpha = 0;
+    double alpha = 0;
     int sx = 0, sy = 0, gx = 0, gy = 0;
-    int bc[4] = {0, 0, 0, 0};
-    bool pure_neumann = false;
-    int Nlx = 0, Nly = 0, nleaf = 0;
+    // the grids (one problem, or a batch of independent realisations)
+    std::vector<GridDesc> grids;
+    std::vector<int> grid_Nlx, grid_Nly, grid_leaf0;   // leaf grid and first leaf of each grid
+    long long ncell = 0, nxface = 0, nyface = 0, nbc = 0;
+    bool pure_neumann = false;           // a single grid with no Dirichlet side
+    int nleaf = 0;
     std::vector<LeafDesc> leaves;
     std::vector<int> leaf_segs;
     // segments
-    std::vector<int> seg_axis, seg_line, seg_lo, seg_len, seg_a, seg_b, seg_face_off;
+    std::vector<int> seg_axis, seg_line, seg_lo, seg_len, seg_a, seg_b, seg_face_off, seg_grid;
     int nseg = 0;
     long long nskel_faces = 0;
     std::vector<int> xface_seg, yface_seg;   // segment of each x- / y-face, -1 off the skeleton
@@ -46,7 +48,9 @@ struct Plan {
         int o1 = 0;
     };
     std::vector<Node> nodes;
-    int root = -1, height = 0;
+    std::vector<int> roots;              // one per grid
+    std::vector<char> root_pinned;       // per node: root of an all-Neumann problem
+    int height = 0;
     std::vector<MergeDesc> merges;       // grouped by height (ascending)
     std::vector<int> level_first, level_count, level_max_g2, level_max_m;  // index by height-1
     std::vector<int> node_map, gamma_segs;
@@ -69,66 +73,101 @@ struct Plan {
 inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
 int make_plan(Plan& P) {
-    P.Nlx = ceil_div(P.nx, P.sx);
-    P.Nly = ceil_div(P.ny, P.sy);
-    P.nleaf = P.Nlx * P.Nly;
+    const int ngrid = (int)P.grids.size();
+    // per grid: leaf grid, offsets in the concatenated arrays
+    P.grid_Nlx.resize(ngrid);
+    P.grid_Nly.resize(ngrid);
+    P.grid_leaf0.resize(ngrid);
+    P.ncell = P.nxface = P.nyface = P.nbc = 0;
+    P.nleaf = 0;
+    for (int gi = 0; gi < ngrid; ++gi) {
+        GridDesc& G = P.grids[gi];
+        G.c0 = P.ncell;
+        G.fx0 = P.nxface;
+        G.fy0 = P.nyface;
+        G.b0 = P.nbc;
+        P.ncell += (long long)G.nx * G.ny;
+        P.nxface += (long long)(G.nx + 1) * G.ny;
+        P.nyface += (long long)G.nx * (G.ny + 1);
+        P.nbc += 2LL * (G.nx + G.ny);
+        P.grid_Nlx[gi] = ceil_div(G.nx, P.sx);
+        P.grid_Nly[gi] = ceil_div(G.ny, P.sy);
+        P.grid_leaf0[gi] = P.nleaf;
+        P.nleaf += P.grid_Nlx[gi] * P.grid_Nly[gi];
+    }
+    P.pure_neumann = ngrid == 1 && !(P.grids[0].bc[0] || P.grids[0].bc[1] || P.grids[0].bc[2] || P.grids[0].bc[3]);
     P.leaves.resize(P.nleaf);
+    std::vector<int> leaf_grid(P.nleaf);
     std::vector<int> xplus_first(P.nleaf, -1), yplus_first(P.nleaf, -1);
-    // leaves and the segments on their + sides
-    for (int J = 0; J < P.Nly; ++J)
-        for (int I = 0; I < P.Nlx; ++I) {
-            const int id = I + P.Nlx * J;
-            LeafDesc& L = P.leaves[id];
-            std::memset(&L, 0, sizeof(L));
-            L.i0 = I * P.sx;
-            L.j0 = J * P.sy;
-            L.w = std::min(P.sx, P.nx - L.i0);
-            L.h = std::min(P.sy, P.ny - L.j0);
-        }
-    for (int id = 0; id < P.nleaf; ++id) {
-        const int I = id % P.Nlx, J = id / P.Nlx;
-        const LeafDesc& L = P.leaves[id];
-        if (I + 1 < P.Nlx) {
-            xplus_first[id] = P.nseg;
-            for (int lo = 0; lo < L.h; lo += P.gy) {
-                P.seg_axis.push_back(0);
-                P.seg_line.push_back(L.i0 + L.w);
-                P.seg_lo.push_back(L.j0 + lo);
-                P.seg_len.push_back(std::min(P.gy, L.h - lo));
-                P.seg_a.push_back(id);
-                P.seg_b.push_back(id + 1);
-                ++P.nseg;
+    // leaves and the segments on their + sides, grid by grid (segment
+    // lines and positions are grid-local)
+    for (int gi = 0; gi < ngrid; ++gi) {
+        const GridDesc& G = P.grids[gi];
+        const int Nlx = P.grid_Nlx[gi], Nly = P.grid_Nly[gi], l0 = P.grid_leaf0[gi];
+        for (int J = 0; J < Nly; ++J)
+            for (int I = 0; I < Nlx; ++I) {
+                const int id = l0 + I + Nlx * J;
+                LeafDesc& L = P.leaves[id];
+                std::memset(&L, 0, sizeof(L));
+                L.i0 = I * P.sx;
+                L.j0 = J * P.sy;
+                L.w = std::min(P.sx, G.nx - L.i0);
+                L.h = std::min(P.sy, G.ny - L.j0);
+                L.grid = gi;
+                leaf_grid[id] = gi;
             }
-        }
-        if (J + 1 < P.Nly) {
-            yplus_first[id] = P.nseg;
-            for (int lo = 0; lo < L.w; lo += P.gx) {
-                P.seg_axis.push_back(1);
-                P.seg_line.push_back(L.j0 + L.h);
-                P.seg_lo.push_back(L.i0 + lo);
-                P.seg_len.push_back(std::min(P.gx, L.w - lo));
-                P.seg_a.push_back(id);
-                P.seg_b.push_back(id + P.Nlx);
-                ++P.nseg;
+        for (int J = 0; J < Nly; ++J)
+            for (int I = 0; I < Nlx; ++I) {
+                const int id = l0 + I + Nlx * J;
+                const LeafDesc& L = P.leaves[id];
+                if (I + 1 < Nlx) {
+                    xplus_first[id] = P.nseg;
+                    for (int lo = 0; lo < L.h; lo += P.gy) {
+                        P.seg_axis.push_back(0);
+                        P.seg_line.push_back(L.i0 + L.w);
+                        P.seg_lo.push_back(L.j0 + lo);
+                        P.seg_len.push_back(std::min(P.gy, L.h - lo));
+                        P.seg_a.push_back(id);
+                        P.seg_b.push_back(id + 1);
+                        P.seg_grid.push_back(gi);
+                        ++P.nseg;
+                    }
+                }
+                if (J + 1 < Nly) {
+                    yplus_first[id] = P.nseg;
+                    for (int lo = 0; lo < L.w; lo += P.gx) {
+                        P.seg_axis.push_back(1);
+                        P.seg_line.push_back(L.j0 + L.h);
+                        P.seg_lo.push_back(L.i0 + lo);
+                        P.seg_len.push_back(std::min(P.gx, L.w - lo));
+                        P.seg_a.push_back(id);
+                        P.seg_b.push_back(id + Nlx);
+                        P.seg_grid.push_back(gi);
+                        ++P.nseg;
+                    }
+                }
             }
-        }
     }
     P.seg_face_off.resize(P.nseg + 1);
     P.seg_face_off[0] = 0;
     for (int t = 0; t < P.nseg; ++t) P.seg_face_off[t + 1] = P.seg_face_off[t] + P.seg_len[t];
     P.nskel_faces = P.seg_face_off[P.nseg];
-    P.xface_seg.assign((size_t)(P.nx + 1) * P.ny, -1);
-    P.yface_seg.assign((size_t)P.nx * (P.ny + 1), -1);
+    P.xface_seg.assign((size_t)P.nxface, -1);
+    P.yface_seg.assign((size_t)P.nyface, -1);
     for (int t = 0; t < P.nseg; ++t) {
+        const GridDesc& G = P.grids[P.seg_grid[t]];
         for (int e = 0; e < P.seg_len[t]; ++e) {
             const int k = P.seg_lo[t] + e;
-            if (P.seg_axis[t] == 0) P.xface_seg[(size_t)P.seg_line[t] + (size_t)(P.nx + 1) * k] = t;
-            else P.yface_seg[(size_t)k + (size_t)P.nx * P.seg_line[t]] = t;
+            if (P.seg_axis[t] == 0)
+                P.xface_seg[(size_t)G.fx0 + (size_t)P.seg_line[t] + (size_t)(G.nx + 1) * k] = t;
+            else
+                P.yface_seg[(size_t)G.fy0 + (size_t)k + (size_t)G.nx * P.seg_line[t]] = t;
         }
     }
     // leaf segment lists: x-, x+, y-, y+ sides
     for (int id = 0; id < P.nleaf; ++id) {
-        const int I = id % P.Nlx, J = id / P.Nlx;
+        const int gi = leaf_grid[id], Nlx = P.grid_Nlx[gi], local = id - P.grid_leaf0[gi];
+        const int I = local % Nlx, J = local / Nlx;
         LeafDesc& L = P.leaves[id];
         L.seg_off = (int)P.leaf_segs.size();
         const int nx_side = ceil_div(L.h, P.gy), ny_side = ceil_div(L.w, P.gx);
@@ -141,16 +180,17 @@ int make_plan(Plan& P) {
         };
         add_side(0, I > 0 ? xplus_first[id - 1] : -1, nx_side);
         add_side(1, xplus_first[id], nx_side);
-        add_side(2, J > 0 ? yplus_first[id - P.Nlx] : -1, ny_side);
+        add_side(2, J > 0 ? yplus_first[id - Nlx] : -1, ny_side);
         add_side(3, yplus_first[id], ny_side);
         L.m = cnt;
         P.max_m_leaf = std::max(P.max_m_leaf, cnt);
     }
-    // tree by recursive bisection of the leaf box
+    // one tree per grid, by recursive bisection of its leaf box
     P.nodes.resize(P.nleaf);
     for (int id = 0; id < P.nleaf; ++id) {
         Plan::Node& nd = P.nodes[id];
-        const int I = id % P.Nlx, J = id / P.Nlx;
+        const int gi = leaf_grid[id], Nlx = P.grid_Nlx[gi], local = id - P.grid_leaf0[gi];
+        const int I = local % Nlx, J = local / Nlx;
         nd.box[0] = I; nd.box[1] = I + 1; nd.box[2] = J; nd.box[3] = J + 1;
         nd.leaf = id;
         const LeafDesc& L = P.leaves[id];
@@ -158,9 +198,10 @@ int make_plan(Plan& P) {
     }
     struct Rec {
         Plan& P;
+        int l0, Nlx;
         int build(int I0, int I1, int J0, int J1) {
             const int nxl = I1 - I0, nyl = J1 - J0;
-            if (nxl == 1 && nyl == 1) return I0 + P.Nlx * J0;
+            if (nxl == 1 && nyl == 1) return l0 + I0 + Nlx * J0;
             int c1, c2;
             if (nxl >= nyl) {
                 const int mid = I0 + (nxl + 1) / 2;
@@ -206,9 +247,17 @@ int make_plan(Plan& P) {
             P.nodes[c2].parent = id;
             return id;
         }
-    } rec{P};
-    P.root = rec.build(0, P.Nlx, 0, P.Nly);
-    P.height = P.nodes[P.root].height;
+    };
+    P.height = 0;
+    P.roots.clear();
+    for (int gi = 0; gi < ngrid; ++gi) {
+        Rec rec{P, P.grid_leaf0[gi], P.grid_Nlx[gi]};
+        const int root = rec.build(0, P.grid_Nlx[gi], 0, P.grid_Nly[gi]);
+        P.roots.push_back(root);
+        P.height = std::max(P.height, P.nodes[root].height);
+    }
+    P.root_pinned.assign(P.nodes.size(), 0);
+    if (P.pure_neumann) P.root_pinned[P.roots[0]] = 1;
     // storage offsets per node
     const int nnode = (int)P.nodes.size();
     P.node_R_off.resize(nnode);
@@ -301,7 +350,7 @@ int make_plan(Plan& P) {
             P.node_map.insert(P.node_map.end(), nd.map.begin(), nd.map.end());
             D.gamma_off = (int)P.gamma_segs.size();
             P.gamma_segs.insert(P.gamma_segs.end(), nd.gamma.begin(), nd.gamma.end());
-            D.pinned = (v == P.root && P.pure_neumann) ? 1 : 0;
+            D.pinned = P.root_pinned[v];
             D.R_off = P.node_R_off[v];
             D.R1_off = P.node_R_off[nd.c1];
             D.R2_off = P.node_R_off[nd.c2];
@@ -356,7 +405,7 @@ int make_plan(Plan& P) {
             P.phase_build[MRCM_PHASE_MERGE_R] += md * (md + 1.0) * gd;
         }
     }
-    const double ncell = (double)P.nx * P.ny, nface = (double)(P.nx + 1) * P.ny + (double)P.nx * (P.ny + 1);
+    const double ncell = (double)P.ncell, nface = (double)(P.nxface + P.nyface);
     P.residual_flops = 8.0 * ncell + 8.0 * (double)P.nskel_faces;
     P.finish_flops = 3.0 * nface + 2.0 * ncell;
     return MRCM_OK;
@@ -571,34 +620,51 @@ const char* mrcm_error_string(int code) {
     }
 }
 
-static int validate(const mrcm_grid* g, const int sub_cells[3], const int seg_cells[3],
-                    const int bc_type[6]) {
-    if (!g || !sub_cells || !seg_cells || !bc_type) return MRCM_ERR_INVALID_ARG;
-    if (g->dim == 3) return MRCM_ERR_UNSUPPORTED;
-    if (g->dim != 2) return MRCM_ERR_INVALID_ARG;
-    if (g->n[0] < 1 || g->n[1] < 1 || !(g->L[0] > 0) || !(g->L[1] > 0)) return MRCM_ERR_INVALID_ARG;
-    if ((long long)g->n[0] * g->n[1] > (1LL << 31)) return MRCM_ERR_INVALID_ARG;
-    for (int s = 0; s < 4; ++s)
-        if (bc_type[s] != MRCM_BC_NEUMANN && bc_type[s] != MRCM_BC_DIRICHLET) return MRCM_ERR_INVALID_ARG;
+// count grids g[k] with boundary types bc_type[6 k .. 6 k + 5]
+static int validate(int count, const mrcm_grid* g, const int sub_cells[3], const int seg_cells[3],
+                    const int* bc_type) {
+    if (count < 1 || !g || !sub_cells || !seg_cells || !bc_type) return MRCM_ERR_INVALID_ARG;
+    long long cells = 0, faces = 0;
+    bool all_neumann = false;
+    for (int k = 0; k < count; ++k) {
+        const mrcm_grid& G = g[k];
+        if (G.dim == 3) return MRCM_ERR_UNSUPPORTED;
+        if (G.dim != 2) return MRCM_ERR_INVALID_ARG;
+        if (G.n[0] < 1 || G.n[1] < 1 || !(G.L[0] > 0) || !(G.L[1] > 0)) return MRCM_ERR_INVALID_ARG;
+        cells += (long long)G.n[0] * G.n[1];
+        faces += 2LL * G.n[0] * G.n[1] + G.n[0] + G.n[1];
+        const int* bc = bc_type + 6 * k;
+        for (int s = 0; s < 4; ++s)
+            if (bc[s] != MRCM_BC_NEUMANN && bc[s] != MRCM_BC_DIRICHLET) return MRCM_ERR_INVALID_ARG;
+        all_neumann |= !(bc[0] || bc[1] || bc[2] || bc[3]);
+    }
+    // every index of the workspace stays below 2^31 (32-bit index arithmetic)
+    if (cells > (1LL << 31) || faces > (1LL << 31)) return MRCM_ERR_INVALID_ARG;
     for (int d = 0; d < 2; ++d) {
         if (sub_cells[d] < 1 || seg_cells[d] < 1) return MRCM_ERR_INVALID_ARG;
         if (sub_cells[d] > kMaxLeafSide) return MRCM_ERR_SHAPE;
         if (seg_cells[d] > sub_cells[d] || sub_cells[d] % seg_cells[d] != 0) return MRCM_ERR_SHAPE;
     }
+    // all-Neumann problems (zero-mean pressure) only as a context of their own
+    if (all_neumann && count > 1) return MRCM_ERR_UNSUPPORTED;
     return MRCM_OK;
 }
 
-static void fill_plan_inputs(Plan& P, const mrcm_grid* g, const int sub[3], const int seg[3],
-                             double alpha, const int bc_type[6]) {
-    P.nx = g->n[0];
-    P.ny = g->n[1];
-    P.hx = g->L[0] / g->n[0];
-    P.hy = g->L[1] / g->n[1];
+static void fill_plan_inputs(Plan& P, int count, const mrcm_grid* g, const int sub[3], const int seg[3],
+                             double alpha, const int* bc_type) {
+    P.grids.assign(count, GridDesc{});
+    for (int k = 0; k < count; ++k) {
+        GridDesc& G = P.grids[k];
+        std::memset(&G, 0, sizeof(G));
+        G.nx = g[k].n[0];
+        G.ny = g[k].n[1];
+        G.hx = g[k].L[0] / g[k].n[0];
+        G.hy = g[k].L[1] / g[k].n[1];
+        for (int s = 0; s < 4; ++s) G.bc[s] = bc_type[6 * k + s];
+    }
     P.alpha = alpha;
     P.sx = sub[0]; P.sy = sub[1];
     P.gx = seg[0]; P.gy = seg[1];
-    for (int s = 0; s < 4; ++s) P.bc[s] = bc_type[s];
-    P.pure_neumann = !(P.bc[0] || P.bc[1] || P.bc[2] || P.bc[3]);
 }
 
 static int plan_value(const Plan& P, int what, long long* value) {
@@ -613,6 +679,8 @@ static int plan_value(const Plan& P, int what, long long* value) {
         case MRCM_Q_LEAF_FLOPS: *value = P.leaf_flops; break;
         case MRCM_Q_MODEL_BUILD_FLOPS: *value = (long long)P.model_build; break;
         case MRCM_Q_MODEL_SWEEP_FLOPS: *value = (long long)P.model_sweep; break;
+        case MRCM_Q_GRIDS: *value = (long long)P.grids.size(); break;
+        case MRCM_Q_CELLS: *value = P.ncell; break;
         default: return MRCM_ERR_INVALID_ARG;
     }
     return MRCM_OK;
@@ -621,18 +689,18 @@ static int plan_value(const Plan& P, int what, long long* value) {
 int mrcm_plan_query(const mrcm_grid* g, const int sub_cells[3], const int seg_cells[3],
                     const int bc_type[6], int what, long long* value) {
     if (!value) return MRCM_ERR_INVALID_ARG;
-    TRY(validate(g, sub_cells, seg_cells, bc_type));
+    TRY(validate(1, g, sub_cells, seg_cells, bc_type));
     if (what == MRCM_Q_WORKSPACE_BYTES) { *value = 0; return MRCM_OK; }
     Plan P;
-    fill_plan_inputs(P, g, sub_cells, seg_cells, 1.0, bc_type);
+    fill_plan_inputs(P, 1, g, sub_cells, seg_cells, 1.0, bc_type);
     TRY(make_plan(P));
     return plan_value(P, what, value);
 }
 
-static int setup_impl(mrcm_ctx* c, const mrcm_grid* g, const double* K_dev, const int sub[3],
-                      const int seg[3], double alpha, const int bc_type[6], int precision, void* stream) {
+static int setup_impl(mrcm_ctx* c, int count, const mrcm_grid* g, const double* K_dev, const int sub[3],
+                      const int seg[3], double alpha, const int* bc_type, int precision, void* stream) {
     Plan& P = c->P;
-    fill_plan_inputs(P, g, sub, seg, alpha, bc_type);
+    fill_plan_inputs(P, count, g, sub, seg, alpha, bc_type);
     c->stream = static_cast<cudaStream_t>(stream);
     TRYC(cudaGetDevice(&c->device));
     TRY(make_plan(P));
@@ -641,12 +709,14 @@ static int setup_impl(mrcm_ctx* c, const mrcm_grid* g, const double* K_dev, cons
     v.mixed = precision == MRCM_MIXED ? 1 : 0;
     c->precision = precision;
     if (v.mixed) c->refine_steps = kMixedRefineDefault;
-    v.nx = P.nx; v.ny = P.ny; v.hx = P.hx; v.hy = P.hy; v.alpha = P.alpha;
-    for (int s = 0; s < 4; ++s) v.bc[s] = P.bc[s];
+    v.alpha = P.alpha;
+    v.ncell = P.ncell; v.nxface = P.nxface; v.nyface = P.nyface; v.nbc = P.nbc;
+    v.ngrid = (int)P.grids.size();
+    TRY(upload(c, &v.grids, P.grids));
     v.nleaf = P.nleaf; v.nseg = P.nseg;
     v.sx = P.sx; v.sy = P.sy; v.gx = P.gx; v.gy = P.gy;
-    const long long ncell = (long long)P.nx * P.ny;
-    const long long nxf = (long long)(P.nx + 1) * P.ny, nyf = (long long)P.nx * (P.ny + 1);
+    const long long ncell = P.ncell;
+    const long long nxf = P.nxface, nyf = P.nyface;
     TRY(dev_alloc(c, &c->K, ncell));
     v.K = c->K;
     TRY(dev_alloc(c, &v.rx, ncell));
@@ -664,6 +734,7 @@ static int setup_impl(mrcm_ctx* c, const mrcm_grid* g, const double* K_dev, cons
     TRY(upload(c, &v.seg_a, P.seg_a));
     TRY(upload(c, &v.seg_b, P.seg_b));
     TRY(upload(c, &v.seg_face_off, P.seg_face_off));
+    TRY(upload(c, &v.seg_grid, P.seg_grid));
     TRY(upload(c, &v.xface_seg, P.xface_seg));
     TRY(upload(c, &v.yface_seg, P.yface_seg));
     TRY(dev_alloc(c, &v.seg_lam_dd, 2LL * P.nseg));
@@ -736,17 +807,25 @@ static int setup_impl(mrcm_ctx* c, const mrcm_grid* g, const double* K_dev, cons
 int mrcm_setup(mrcm_ctx** out, const mrcm_grid* g, const double* K_dev, const int sub_cells[3],
                const int seg_cells[3], double alpha, const int bc_type[6], int precision,
                void* cuda_stream) {
+    return mrcm_setup_batch(out, 1, g, bc_type, K_dev, sub_cells, seg_cells, alpha, precision, cuda_stream);
+}
+
+int mrcm_setup_batch(mrcm_ctx** out, int count, const mrcm_grid* grids, const int* bc_types, const double* K_dev,
+                     const int sub_cells[3], const int seg_cells[3], double alpha, int precision,
+                     void* cuda_stream) {
     if (!out) return MRCM_ERR_INVALID_ARG;
     *out = nullptr;
     if (!K_dev) return MRCM_ERR_INVALID_ARG;
-    TRY(validate(g, sub_cells, seg_cells, bc_type));
+    const mrcm_grid* g = grids;
+    const int* bc_type = bc_types;
+    TRY(validate(count, g, sub_cells, seg_cells, bc_type));
     if (precision != MRCM_FP64 && precision != MRCM_MIXED && precision != MRCM_SURROGATE)
         return MRCM_ERR_INVALID_ARG;
     if (precision == MRCM_SURROGATE) return MRCM_ERR_UNSUPPORTED;
     if (!(alpha > 0) || !std::isfinite(alpha)) return MRCM_ERR_INVALID_ARG;
     mrcm_ctx* c = new (std::nothrow) mrcm_ctx();
     if (!c) return MRCM_ERR_OOM;
-    int rc = setup_impl(c, g, K_dev, sub_cells, seg_cells, alpha, bc_type, precision, cuda_stream);
+    int rc = setup_impl(c, count, g, K_dev, sub_cells, seg_cells, alpha, bc_type, precision, cuda_stream);
     if (rc != MRCM_OK) {
         mrcm_destroy(c);
         return rc;
@@ -757,7 +836,7 @@ int mrcm_setup(mrcm_ctx** out, const mrcm_grid* g, const double* K_dev, const in
 
 int mrcm_set_permeability(mrcm_ctx* c, const double* K_dev) {
     if (!c || !K_dev) return MRCM_ERR_INVALID_ARG;
-    TRYC(cudaMemcpyAsync(c->K, K_dev, sizeof(double) * (size_t)c->P.nx * c->P.ny, cudaMemcpyDefault,
+    TRYC(cudaMemcpyAsync(c->K, K_dev, sizeof(double) * (size_t)c->P.ncell, cudaMemcpyDefault,
                          c->stream));
     c->built = false;
     c->solved = false;

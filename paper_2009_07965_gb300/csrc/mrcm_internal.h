@@ -25,11 +25,27 @@ constexpr long long kDefaultSpinLimit = 5000000;
 // |sum q - sum |e| g_N| <= kCompatTol (sum |q| + sum |e| |g_N|).
 constexpr double kCompatTol = 1e-14;
 
+// One grid of a context: a context holds one problem, or a batch of
+// independent problems (realisations) whose leaves, segments and merge
+// trees are planned together and whose arrays are concatenated grid after
+// grid (cells x fastest within a grid; x-faces, y-faces and boundary values
+// likewise).
+struct GridDesc {
+    int nx, ny;        // cells
+    double hx, hy;     // cell size
+    int bc[4];         // side types x-, x+, y-, y+ (1: Dirichlet)
+    long long c0;      // first cell of the grid in the cell arrays
+    long long fx0;     // first x-face ((nx+1) ny of them)
+    long long fy0;     // first y-face (nx (ny+1))
+    long long b0;      // first boundary value (2 (nx + ny))
+};
+
 // Geometry of one leaf, uploaded once by mrcm_setup.
 struct LeafDesc {
-    int i0, j0;        // first cell
+    int i0, j0;        // first cell (within its grid)
     int w, h;          // size in cells (<= 16)
     int m;             // interface segments of the leaf
+    int grid;          // the grid it belongs to
     int side_off[4];   // local index of the first segment of side x-, x+, y-,
                        // y+ (-1 when the side lies on the domain boundary)
     int seg_off;       // offset of the leaf's segment ids in leaf_segs
@@ -61,13 +77,14 @@ struct MergeDesc {
 
 // Device-side view of the plan and workspace.
 struct DevView {
-    int nx, ny;
-    double hx, hy, alpha;
-    int bc[4];
+    double alpha;
+    long long ncell, nxface, nyface, nbc;   // totals over the grids
+    int ngrid;
+    const GridDesc* grids;
     int nleaf, nseg;
     int sx, sy, gx, gy;
     // inputs copied / derived
-    const double* K;        // nx*ny
+    const double* K;        // ncell
     double* rx;             // nx*ny half-cell resistances hx / (2 K)
     double* ry;             //                               hy / (2 K)
     double* seg_beta;       // nseg
@@ -79,6 +96,7 @@ struct DevView {
     // segment geometry
     const int* seg_axis; const int* seg_line; const int* seg_lo; const int* seg_len;
     const int* seg_a; const int* seg_b; const int* seg_face_off;
+    const int* seg_grid;          // grid of each segment (line and lo are grid-local)
     const long long* seg_lam_a;   // offset in lam of segment t in the leaf on side a
     const long long* seg_lam_b;   //                                   ... side b
     const int* xface_seg;         // (nx+1)*ny: segment of each x-face, -1 off the skeleton
@@ -121,23 +139,20 @@ struct DevView {
 };
 
 #ifdef __CUDACC__
-// Global segment id of the skeleton face (axis, line, k): line is the face
-// index along the normal, k the cell index along the face.  The segment is
-// listed on the + side of the leaf below the line.
-__device__ __forceinline__ int skeleton_segment(const DevView& v, int axis, int line, int k) {
-    const int nlx = (v.nx + v.sx - 1) / v.sx;
-    int leaf, side, pos;
-    if (axis == 0) {
-        leaf = (line / v.sx - 1) + nlx * (k / v.sy);
-        side = 1;
-        pos = (k - v.leaves[leaf].j0) / v.gy;
-    } else {
-        leaf = (k / v.sx) + nlx * (line / v.sy - 1);
-        side = 3;
-        pos = (k - v.leaves[leaf].i0) / v.gx;
+// The grid holding entry x of the concatenated cell (KIND 0), x-face (1) or
+// y-face (2) arrays: binary search over the grids' first entries (one grid:
+// no search).
+template <int KIND>
+__device__ __forceinline__ int grid_of(const DevView& v, long long x) {
+    int lo = 0, hi = v.ngrid - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        const GridDesc& G = v.grids[mid];
+        const long long o = KIND == 0 ? G.c0 : (KIND == 1 ? G.fx0 : G.fy0);
+        if (o <= x) lo = mid;
+        else hi = mid - 1;
     }
-    const LeafDesc& L = v.leaves[leaf];
-    return v.leaf_segs[L.seg_off + L.side_off[side] + pos];
+    return lo;
 }
 
 // Double-double arithmetic: TwoSum (Knuth) and FMA-based TwoProd are
@@ -233,14 +248,6 @@ template <> __device__ __forceinline__ float* leaf_L<float>(const DevView& v) { 
 template <class T> __device__ __forceinline__ T* leaf_Z(const DevView& v);
 template <> __device__ __forceinline__ double* leaf_Z<double>(const DevView& v) { return v.leafZ; }
 template <> __device__ __forceinline__ float* leaf_Z<float>(const DevView& v) { return v.leafZ32; }
-
-// x-face (i, j) / y-face (i, j) lies on the skeleton
-__device__ __forceinline__ bool x_skeleton(const DevView& v, int i) {
-    return i > 0 && i < v.nx && i % v.sx == 0;
-}
-__device__ __forceinline__ bool y_skeleton(const DevView& v, int j) {
-    return j > 0 && j < v.ny && j % v.sy == 0;
-}
 #endif
 
 // MRCM_OK for cudaSuccess; otherwise records e as the calling thread's last
