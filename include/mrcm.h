@@ -471,6 +471,84 @@ enum {
 };
 int mrcm_probe_peak(int kind, double seconds, double* tflops, void* cuda_stream);
 
+/*
+ * Learned basis surrogate (the learned part of the grown form; the paper
+ * computes every basis by a local solve).  A leaf's basis responses, Eqs.
+ * (11Hhatbasisa)/(11Hhatbasisb), are the fields psi_s = A^-1 B e_s (cell
+ * pressures for a unit Robin datum on segment s, local Robin problem of Eq.
+ * 11.2-12.2), and its Robin-to-flux map is R = B^T psi - W.  A small
+ * convolutional network predicts the 16 fields of a full interior 16 x 16
+ * leaf from its permeability patch; a residual gate keeps a prediction only
+ * where ||A psi_s - B e_s|| / ||B e_s|| <= tau for every s, and the plain
+ * local solve stands for every other leaf.
+ *
+ * Leaf lists are device int arrays of leaf ids (out-of-range ids, and leaves
+ * with more than 16 segments, make the call return MRCM_ERR_INVALID_ARG);
+ * contexts whose leaves have more than 16 segments return
+ * MRCM_ERR_UNSUPPORTED.  Every call synchronises the context's stream.
+ *
+ * mrcm_interior_leaves -- ids (host, up to cap) of the full interior leaves
+ *   (16 x 16 cells, 4 segments per side, no side on the domain boundary);
+ *   returns their number (host only).
+ * mrcm_leaf_fields -- psi_dev[item][256][16] (float; cell i + 16 j, then
+ *   segment: the network's output layout) of the listed leaves from the
+ *   built basis (training targets).
+ * mrcm_leaf_patches -- x_dev[item][18][18][16] (bf16, NHWC): channel 0 =
+ *   (log K - its mean over the leaf) / 2 on the leaf and a one-cell halo,
+ *   channel 1 = log10(alpha) / 3, others 0 (network inputs).
+ * mrcm_leaf_gate -- res_dev[item] (double) = max over s of the relative
+ *   residual of predicted fields psi_dev (float, layout of
+ *   mrcm_leaf_fields), in FP64.
+ * mrcm_leaf_apply -- for the items with res <= tau: R = B^T psi - W
+ *   (symmetrised) replaces the leaf's map; accepted_dev[item] = 1 for them,
+ *   0 for the others; then the merges are rebuilt (mrcm_solve uses the new
+ *   maps, the leaf factors are unchanged).
+ */
+int mrcm_interior_leaves(const mrcm_ctx* ctx, int* ids, int cap);
+int mrcm_leaf_fields(mrcm_ctx* ctx, const int* ids_dev, int count, float* psi_dev);
+int mrcm_leaf_patches(mrcm_ctx* ctx, const int* ids_dev, int count, void* x_dev);
+int mrcm_leaf_gate(mrcm_ctx* ctx, const int* ids_dev, int count, const float* psi_dev, double* res_dev);
+int mrcm_leaf_apply(mrcm_ctx* ctx, const int* ids_dev, int count, const float* psi_dev, const double* res_dev,
+                    double tau, int* accepted_dev);
+
+/*
+ * The network's kernels (no context; device buffers; asynchronous on
+ * `stream`).  Activations are bf16 NHWC [item][y][x][c], weights bf16
+ * [cout][ky][kx][cin], biases and gradients float.  Every output is 16 x 16.
+ *
+ * mrcm_cnn_conv_forward -- y = act(conv3x3(x, w) + b) on the tensor cores
+ *   (mma.sync m16n8k16, BF16 operands, FP32 accumulation): pad = 0 takes an
+ *   18 x 18 input ('valid'), pad = 1 a 16 x 16 input with a zero border
+ *   ('same'); relu != 0 applies max(., 0); writes y_bf16 and / or y_f32
+ *   (either may be NULL, not both); b may be NULL.  Shapes (cin, cout, pad):
+ *   (16, 32, 0), (16, 32, 1), (32, 32, 1), (32, 16, 1); others return
+ *   MRCM_ERR_UNSUPPORTED.
+ * mrcm_cnn_conv_wgrad -- dw[cout][9 cin] += sum over items and pixels of
+ *   dy x im2col(x), db[cout] += sum of dy (db may be NULL); shapes (16, 32,
+ *   0), (32, 32, 1), (32, 16, 1).
+ * mrcm_cnn_flip_weights -- w2[cin][ky][kx][cout] = w[cout][2-ky][2-kx][cin]:
+ *   the forward kernel on w2 (cin and cout swapped, pad 1) computes the
+ *   input gradient of a 'same' convolution.
+ * mrcm_cnn_relu_grad -- dpre (bf16) = dpost (float) where y > 0 (mask != 0;
+ *   y the layer's bf16 output), else 0; mask == 0 copies.
+ * mrcm_cnn_mse_grad -- loss 0.5 sum (pred - target)^2 / count added into
+ *   *loss (device float); dpred = (pred - target) / count.  pred and target
+ *   float [count][16][16][16] (NHWC).
+ * mrcm_cnn_adam -- one Adam step (step >= 1) on float parameters p with
+ *   gradient g and moments m1, m2; p_bf16 (may be NULL) receives the bf16
+ *   copy.
+ */
+int mrcm_cnn_conv_forward(const void* x, int count, int cin, int cout, int pad, int relu, const void* w,
+                          const float* b, void* y_bf16, float* y_f32, void* stream);
+int mrcm_cnn_conv_wgrad(const void* x, const void* dy, int count, int cin, int cout, int pad, float* dw,
+                        float* db, void* stream);
+int mrcm_cnn_flip_weights(const void* w, int cout, int cin, void* w2, void* stream);
+int mrcm_cnn_relu_grad(const float* dpost, const void* y, long long n, int mask, void* dpre, void* stream);
+int mrcm_cnn_mse_grad(const float* pred, const float* target, int count, float* dpred, float* loss,
+                      void* stream);
+int mrcm_cnn_adam(float* p, const float* g, float* m1, float* m2, void* p_bf16, long long n, float lr,
+                  float beta1, float beta2, float eps, int step, void* stream);
+
 /* mrcm_destroy -- free all device and host resources (NULL is a no-op). */
 void mrcm_destroy(mrcm_ctx* ctx);
 

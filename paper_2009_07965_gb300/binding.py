@@ -28,7 +28,10 @@ EXPORTS = ["mrcm_setup", "mrcm_setup_batch", "mrcm_plan_query", "mrcm_set_permea
            "mrcm_last_cuda_error",
            "mrcm_merge_pair_noalloc", "mrcm_set_refinement", "mrcm_residual_history", "mrcm_phase_flops",
            "mrcm_group_times", "mrcm_check_reciprocal", "mrcm_set_wait_limit",
-           "mrcm_probe_peak", "mrcm_set_mixed_split", "mrcm_autotune", "mrcm_tune_info"]
+           "mrcm_probe_peak", "mrcm_set_mixed_split", "mrcm_autotune", "mrcm_tune_info",
+           "mrcm_interior_leaves", "mrcm_leaf_fields", "mrcm_leaf_patches", "mrcm_leaf_gate", "mrcm_leaf_apply",
+           "mrcm_cnn_conv_forward", "mrcm_cnn_conv_wgrad", "mrcm_cnn_flip_weights", "mrcm_cnn_relu_grad",
+           "mrcm_cnn_mse_grad", "mrcm_cnn_adam"]
 PHASES = ["coef", "leaf_build", "merge_small", "gj_sweep", "merge_form", "merge_x", "merge_r",
           "leaf_particular", "tree_up", "tree_down", "leaf_pressure", "residual", "finish"]
 # kernel family behind each phase (for reports)
@@ -106,6 +109,29 @@ def _lib():
         lib.mrcm_check_reciprocal.restype = I
         lib.mrcm_set_refinement.argtypes = [P, I, I]
         lib.mrcm_set_refinement.restype = I
+        LL, F = ctypes.c_longlong, ctypes.c_float
+        lib.mrcm_interior_leaves.argtypes = [P, IP, I]
+        lib.mrcm_interior_leaves.restype = I
+        lib.mrcm_leaf_fields.argtypes = [P, P, I, P]
+        lib.mrcm_leaf_fields.restype = I
+        lib.mrcm_leaf_patches.argtypes = [P, P, I, P]
+        lib.mrcm_leaf_patches.restype = I
+        lib.mrcm_leaf_gate.argtypes = [P, P, I, P, P]
+        lib.mrcm_leaf_gate.restype = I
+        lib.mrcm_leaf_apply.argtypes = [P, P, I, P, P, D, P]
+        lib.mrcm_leaf_apply.restype = I
+        lib.mrcm_cnn_conv_forward.argtypes = [P, I, I, I, I, I, P, P, P, P, P]
+        lib.mrcm_cnn_conv_forward.restype = I
+        lib.mrcm_cnn_conv_wgrad.argtypes = [P, P, I, I, I, I, P, P, P]
+        lib.mrcm_cnn_conv_wgrad.restype = I
+        lib.mrcm_cnn_flip_weights.argtypes = [P, I, I, P, P]
+        lib.mrcm_cnn_flip_weights.restype = I
+        lib.mrcm_cnn_relu_grad.argtypes = [P, P, LL, I, P, P]
+        lib.mrcm_cnn_relu_grad.restype = I
+        lib.mrcm_cnn_mse_grad.argtypes = [P, P, I, P, P, P]
+        lib.mrcm_cnn_mse_grad.restype = I
+        lib.mrcm_cnn_adam.argtypes = [P, P, P, P, P, LL, F, F, F, F, I, P]
+        lib.mrcm_cnn_adam.restype = I
         lib.mrcm_autotune.argtypes = [P, I]
         lib.mrcm_autotune.restype = I
         lib.mrcm_tune_info.argtypes = [P, I, IP]
@@ -291,6 +317,61 @@ def mrcm_probe_peak(kind, seconds=0.3, stream=None):
     _check(_lib().mrcm_probe_peak(PROBES[kind] if isinstance(kind, str) else int(kind), float(seconds),
                                   ctypes.byref(out), stream), "mrcm_probe_peak")
     return out.value
+
+
+def mrcm_interior_leaves(ctx):
+    """Ids of the full interior leaves (host list)."""
+    n = _lib().mrcm_interior_leaves(ctx, None, 0)
+    _check(min(n, 0), "mrcm_interior_leaves")
+    buf = (ctypes.c_int * max(n, 1))()
+    _lib().mrcm_interior_leaves(ctx, buf, n)
+    return list(buf)[:n]
+
+
+def mrcm_leaf_fields(ctx, ids, psi):
+    _check(_lib().mrcm_leaf_fields(ctx, _ptr(ids), int(ids.numel()), _ptr(psi)), "mrcm_leaf_fields")
+
+
+def mrcm_leaf_patches(ctx, ids, x):
+    _check(_lib().mrcm_leaf_patches(ctx, _ptr(ids), int(ids.numel()), _ptr(x)), "mrcm_leaf_patches")
+
+
+def mrcm_leaf_gate(ctx, ids, psi, res):
+    _check(_lib().mrcm_leaf_gate(ctx, _ptr(ids), int(ids.numel()), _ptr(psi), _ptr(res)), "mrcm_leaf_gate")
+
+
+def mrcm_leaf_apply(ctx, ids, psi, res, tau, accepted):
+    _check(_lib().mrcm_leaf_apply(ctx, _ptr(ids), int(ids.numel()), _ptr(psi), _ptr(res), float(tau),
+                                  _ptr(accepted)), "mrcm_leaf_apply")
+
+
+def mrcm_cnn_conv_forward(x, count, cin, cout, pad, relu, w, b, y_bf16=None, y_f32=None, stream=None):
+    _check(_lib().mrcm_cnn_conv_forward(_ptr(x), int(count), cin, cout, pad, 1 if relu else 0, _ptr(w), _ptr(b),
+                                        _ptr(y_bf16), _ptr(y_f32), stream), "mrcm_cnn_conv_forward")
+
+
+def mrcm_cnn_conv_wgrad(x, dy, count, cin, cout, pad, dw, db=None, stream=None):
+    _check(_lib().mrcm_cnn_conv_wgrad(_ptr(x), _ptr(dy), int(count), cin, cout, pad, _ptr(dw), _ptr(db), stream),
+           "mrcm_cnn_conv_wgrad")
+
+
+def mrcm_cnn_flip_weights(w, cout, cin, w2, stream=None):
+    _check(_lib().mrcm_cnn_flip_weights(_ptr(w), cout, cin, _ptr(w2), stream), "mrcm_cnn_flip_weights")
+
+
+def mrcm_cnn_relu_grad(dpost, y, n, mask, dpre, stream=None):
+    _check(_lib().mrcm_cnn_relu_grad(_ptr(dpost), _ptr(y), int(n), 1 if mask else 0, _ptr(dpre), stream),
+           "mrcm_cnn_relu_grad")
+
+
+def mrcm_cnn_mse_grad(pred, target, count, dpred, loss, stream=None):
+    _check(_lib().mrcm_cnn_mse_grad(_ptr(pred), _ptr(target), int(count), _ptr(dpred), _ptr(loss), stream),
+           "mrcm_cnn_mse_grad")
+
+
+def mrcm_cnn_adam(p, g, m1, m2, p_bf16, n, lr, beta1, beta2, eps, step, stream=None):
+    _check(_lib().mrcm_cnn_adam(_ptr(p), _ptr(g), _ptr(m1), _ptr(m2), _ptr(p_bf16), int(n), float(lr), float(beta1),
+                                float(beta2), float(eps), int(step), stream), "mrcm_cnn_adam")
 
 
 def mrcm_autotune(ctx, reps=3):

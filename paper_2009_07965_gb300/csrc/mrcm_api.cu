@@ -844,21 +844,22 @@ int mrcm_set_permeability(mrcm_ctx* c, const double* K_dev) {
     return MRCM_OK;
 }
 
-// The launch sequence of mrcm_build_basis (no synchronisation).
-static int enqueue_build(mrcm_ctx* c, int& launches) {
+// The launch sequence of mrcm_build_basis (no synchronisation); with
+// merges_only the leaf maps already in place are merged again.
+static int enqueue_build(mrcm_ctx* c, int& launches, bool merges_only = false) {
     const Plan& P = c->P;
     const DevView& v = c->v;
     cudaStream_t s = c->stream;
     launches = 0;
     TRYC(cudaMemsetAsync(v.status, 0, sizeof(int), s));
-    {
+    if (!merges_only) {
         PhaseScope ps(c, MRCM_PHASE_COEF);
         TRYC(launch_check_K(v, s)); ++launches;
         TRYC(launch_cell_resist(v, s)); ++launches;
         TRYC(launch_seg_beta(v, s)); launches += P.nseg > 0;
         TRYC(launch_face_coef(v, s)); ++launches;
     }
-    {
+    if (!merges_only) {
         PhaseScope ps(c, MRCM_PHASE_LEAF_BUILD);
         TRYC(launch_leaf_build(v, P.max_m_leaf, s)); ++launches;
     }
@@ -1068,6 +1069,110 @@ int mrcm_set_wait_limit(mrcm_ctx* c, long long polls) {
     c->build_exec = c->solve_exec = nullptr;
     c->solve_key[0] = nullptr;
     return MRCM_OK;
+}
+
+// ---- learned basis surrogate ----------------------------------------------
+int mrcm_interior_leaves(const mrcm_ctx* c, int* ids, int cap) {
+    if (!c || cap < 0 || (cap > 0 && !ids)) return MRCM_ERR_INVALID_ARG;
+    int n = 0;
+    for (int id = 0; id < c->P.nleaf; ++id) {
+        const LeafDesc& L = c->P.leaves[id];
+        if (L.w != kMaxLeafSide || L.h != kMaxLeafSide || L.m != 16) continue;
+        if (L.side_off[0] < 0 || L.side_off[1] < 0 || L.side_off[2] < 0 || L.side_off[3] < 0) continue;
+        if (n < cap) ids[n] = id;
+        ++n;
+    }
+    return n;
+}
+
+static int surrogate_ready(mrcm_ctx* c, const int* ids, int count) {
+    if (!c || !ids || count < 0) return MRCM_ERR_INVALID_ARG;
+    if (c->P.max_m_leaf > 16) return MRCM_ERR_UNSUPPORTED;
+    return MRCM_OK;
+}
+
+int mrcm_leaf_fields(mrcm_ctx* c, const int* ids, int count, float* psi) {
+    TRY(surrogate_ready(c, ids, count));
+    if (!psi) return MRCM_ERR_INVALID_ARG;
+    if (!c->built) return MRCM_ERR_NOT_BUILT;
+    TRYC(cudaMemsetAsync(c->v.status, 0, sizeof(int), c->stream));
+    TRYC(launch_leaf_fields(c->v, ids, count, psi, c->stream));
+    return read_status(c);
+}
+
+int mrcm_leaf_patches(mrcm_ctx* c, const int* ids, int count, void* x) {
+    TRY(surrogate_ready(c, ids, count));
+    if (!x) return MRCM_ERR_INVALID_ARG;
+    TRYC(cudaMemsetAsync(c->v.status, 0, sizeof(int), c->stream));
+    TRYC(launch_leaf_patches(c->v, ids, count, x, c->stream));
+    return read_status(c);
+}
+
+int mrcm_leaf_gate(mrcm_ctx* c, const int* ids, int count, const float* psi, double* res) {
+    TRY(surrogate_ready(c, ids, count));
+    if (!psi || !res) return MRCM_ERR_INVALID_ARG;
+    TRYC(cudaMemsetAsync(c->v.status, 0, sizeof(int), c->stream));
+    TRYC(launch_leaf_gate(c->v, ids, count, psi, res, c->stream));
+    return read_status(c);
+}
+
+int mrcm_leaf_apply(mrcm_ctx* c, const int* ids, int count, const float* psi, const double* res, double tau,
+                    int* accepted) {
+    TRY(surrogate_ready(c, ids, count));
+    if (!psi || !res || !accepted) return MRCM_ERR_INVALID_ARG;
+    if (!c->built) return MRCM_ERR_NOT_BUILT;
+    TRYC(cudaMemsetAsync(c->v.status, 0, sizeof(int), c->stream));
+    TRYC(launch_leaf_apply(c->v, ids, count, psi, res, tau, accepted, c->stream));
+    TRY(read_status(c));
+    // the merged maps above the changed leaves
+    c->built = false;
+    c->solved = false;
+    int launches = 0;
+    TRY(enqueue_build(c, launches, true));
+    TRY(read_status(c));
+    c->built = true;
+    return MRCM_OK;
+}
+
+int mrcm_cnn_conv_forward(const void* x, int count, int cin, int cout, int pad, int relu, const void* w,
+                          const float* b, void* y_bf16, float* y_f32, void* stream) {
+    if (!x || !w || count < 0 || (!y_bf16 && !y_f32)) return MRCM_ERR_INVALID_ARG;
+    if (count == 0) return MRCM_OK;
+    const cudaError_t e = launch_conv_fwd(x, count, cin, cout, pad, relu, w, b, y_bf16, y_f32,
+                                          static_cast<cudaStream_t>(stream));
+    return e == cudaErrorInvalidValue ? MRCM_ERR_UNSUPPORTED : cuda_err(e);
+}
+
+int mrcm_cnn_conv_wgrad(const void* x, const void* dy, int count, int cin, int cout, int pad, float* dw, float* db,
+                        void* stream) {
+    if (!x || !dy || !dw || count < 0) return MRCM_ERR_INVALID_ARG;
+    if (count == 0) return MRCM_OK;
+    const cudaError_t e = launch_conv_wgrad(x, dy, count, cin, cout, pad, dw, db, static_cast<cudaStream_t>(stream));
+    return e == cudaErrorInvalidValue ? MRCM_ERR_UNSUPPORTED : cuda_err(e);
+}
+
+int mrcm_cnn_flip_weights(const void* w, int cout, int cin, void* w2, void* stream) {
+    if (!w || !w2 || cout < 1 || cin < 1) return MRCM_ERR_INVALID_ARG;
+    return cuda_err(launch_flip_weights(w, cout, cin, w2, static_cast<cudaStream_t>(stream)));
+}
+
+int mrcm_cnn_relu_grad(const float* dpost, const void* y, long long n, int mask, void* dpre, void* stream) {
+    if (!dpost || !dpre || n < 0 || (mask && !y)) return MRCM_ERR_INVALID_ARG;
+    if (n == 0) return MRCM_OK;
+    return cuda_err(launch_relu_grad(dpost, y, n, mask, dpre, static_cast<cudaStream_t>(stream)));
+}
+
+int mrcm_cnn_mse_grad(const float* pred, const float* target, int count, float* dpred, float* loss, void* stream) {
+    if (!pred || !target || !dpred || !loss || count < 1) return MRCM_ERR_INVALID_ARG;
+    return cuda_err(launch_mse_grad(pred, target, count, dpred, loss, static_cast<cudaStream_t>(stream)));
+}
+
+int mrcm_cnn_adam(float* p, const float* g, float* m1, float* m2, void* p_bf16, long long n, float lr, float beta1,
+                  float beta2, float eps, int step, void* stream) {
+    if (!p || !g || !m1 || !m2 || n < 0 || step < 1) return MRCM_ERR_INVALID_ARG;
+    if (n == 0) return MRCM_OK;
+    return cuda_err(launch_adam(p, g, m1, m2, p_bf16, n, lr, beta1, beta2, eps, step,
+                                static_cast<cudaStream_t>(stream)));
 }
 
 int mrcm_set_refinement(mrcm_ctx* c, int steps, int check) {

@@ -280,6 +280,25 @@ cudaError_t launch_residual(const DevView& v, const double* q, const double* bc_
 // fluxes are formed in plain FP64
 cudaError_t launch_face_fluxes(const DevView& v, const double* bc_val, double* p, double* Fx,
                                double* Fy, double* iface, bool plain, cudaStream_t s);
+// Learned basis surrogate (kernels_surrogate.cu): leaf lists are device
+// arrays of leaf ids (each checked; leaves with more than 16 segments are
+// refused); fields are float [item][16][256], patches bf16 [item][18][18][16].
+cudaError_t launch_leaf_fields(const DevView& v, const int* ids, int count, float* psi, cudaStream_t s);
+cudaError_t launch_leaf_patches(const DevView& v, const int* ids, int count, void* x, cudaStream_t s);
+cudaError_t launch_leaf_gate(const DevView& v, const int* ids, int count, const float* psi, double* res,
+                             cudaStream_t s);
+cudaError_t launch_leaf_apply(const DevView& v, const int* ids, int count, const float* psi, const double* res,
+                              double tau, int* accepted, cudaStream_t s);
+cudaError_t launch_conv_fwd(const void* x, int count, int cin, int cout, int pad, int relu, const void* w,
+                            const float* b, void* ybf, float* yf, cudaStream_t s);
+cudaError_t launch_conv_wgrad(const void* x, const void* dy, int count, int cin, int cout, int pad, float* dw,
+                              float* db, cudaStream_t s);
+cudaError_t launch_flip_weights(const void* w, int cout, int cin, void* w2, cudaStream_t s);
+cudaError_t launch_relu_grad(const float* dpost, const void* y, long long n, int mask, void* dpre, cudaStream_t s);
+cudaError_t launch_mse_grad(const float* pred, const float* target, int count, float* dpred, float* loss,
+                            cudaStream_t s);
+cudaError_t launch_adam(float* p, const float* g, float* m1, float* m2, void* pbf, long long n, float lr, float b1,
+                        float b2, float eps, int t, cudaStream_t s);
 // all-Neumann data: sets kStatusInconsistent unless the sources balance the
 // boundary outflow to kCompatTol (double-double sums; scratch in v.red)
 cudaError_t launch_compat_check(const DevView& v, const double* q, const double* bc_val, cudaStream_t s);
