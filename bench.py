@@ -91,6 +91,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision measurement")
     ap.add_argument("--no-autotune", action="store_true", help="keep the built-in launch-shape heuristics")
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-surrogate measurement")
     ap.add_argument("--refine", type=int, default=0,
                     help="iterative-refinement steps per solve in the timed steps (0: the paper's single "
                          "pass; its distance to the refined solution is checked in the same run)")
@@ -376,6 +377,72 @@ def time_mixed(mr, prob, q, bcv, stream, flush, args, split, ref_fp64, wl, rank)
                 phases_ms={k: v / args.steps for k, v in phases.items() if v > 0})
 
 
+def time_surrogate(mr, solver, wl, args):
+    """The learned basis surrogate at this workload: trained on the GPU (the
+    library's BF16 kernels) on basis fields the plain method computes for
+    seeded fields of the workload's statistics, then applied to the
+    workload's interior leaves through the residual gate."""
+    import numpy as np
+    import torch
+    import inputs
+    from paper_2009_07965_gb300.surrogate import BasisSurrogate
+    dev = torch.device("cuda", 0)
+    n = wl["n"]
+    xs, ys = [], []
+    for r in range(4):                              # 1024^2 windows with the workload's cell size
+        prob = inputs.darcy_problem(1024, 1024, Lx=1024 / n, sigma2=wl["sigma2"], corr=wl["corr"],
+                                    seed=50000 + r, bc="quarter_five_spot")
+        s = mr.Solver(torch.from_numpy(prob.K).to(dev), prob.Lx, prob.Ly, prob.sub, prob.seg, prob.alpha,
+                      prob.bc_type)
+        s.build_basis()
+        idt = torch.tensor(mr.mrcm_interior_leaves(s.ctx), dtype=torch.int32, device=dev)
+        x = torch.empty((idt.numel(), 18, 18, 16), dtype=torch.bfloat16, device=dev)
+        y = torch.empty((idt.numel(), 256, 16), dtype=torch.float32, device=dev)
+        mr.mrcm_leaf_patches(s.ctx, idt, x)
+        mr.mrcm_leaf_fields(s.ctx, idt, y)
+        xs.append(x)
+        ys.append(y.view(-1, 16, 16, 16))
+        s.close()
+    x, y = torch.cat(xs), torch.cat(ys)
+    train_leaves = int(x.shape[0])
+    net = BasisSurrogate(device=dev, seed=0)
+    g = torch.Generator(device="cpu").manual_seed(0)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    losses, steps, batch = [], 500, 256
+    ev0.record()
+    for it in range(steps):
+        idx = torch.randint(0, x.shape[0], (batch,), generator=g).to(dev)
+        losses.append(net.train_step(x[idx].contiguous(), y[idx].contiguous(), lr=2e-3))
+    ev1.record()
+    ev1.synchronize()
+    train_ms = ev0.elapsed_time(ev1) / steps
+    del x, y, xs, ys
+    # inference and the gate on the workload's interior leaves
+    idt = torch.tensor(mr.mrcm_interior_leaves(solver.ctx), dtype=torch.int32, device=dev)
+    torch.cuda.synchronize()
+    ev0.record()
+    psi = net.predict(solver.ctx, idt)
+    ev1.record()
+    ev1.synchronize()
+    infer_ms = ev0.elapsed_time(ev1)
+    res = torch.empty(idt.numel(), dtype=torch.float64, device=dev)
+    ev0.record()
+    mr.mrcm_leaf_gate(solver.ctx, idt, psi, res)
+    ev1.record()
+    ev1.synchronize()
+    gate_ms = ev0.elapsed_time(ev1)
+    r = res.cpu().numpy()
+    del psi
+    torch.cuda.empty_cache()
+    return dict(train_set_leaves=train_leaves, train_steps=steps,
+                train_batch=batch, train_ms_per_step=train_ms, loss_first=float(np.mean(losses[:10])),
+                loss_last=float(np.mean(losses[-10:])), interior_leaves=int(idt.numel()),
+                infer_ms=infer_ms, gate_ms=gate_ms, median_residual=float(np.median(r)),
+                accepted_at_tau_1e_4=float(np.mean(r <= 1e-4)), accepted_at_tau_1e_2=float(np.mean(r <= 1e-2)),
+                note=("inference + gate time against the plain leaf build of the same step (phases.leaf_build); "
+                      "rejected leaves keep the plain local solve"))
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -516,6 +583,9 @@ def run_ours(args):
         ev1.synchronize()
         ref_ms.append(ev0.elapsed_time(ev1))
     mr.mrcm_set_refinement(solver.ctx, args.refine)
+    surrogate = None
+    if not args.no_surrogate and world == 1:
+        surrogate = time_surrogate(mr, solver, wl, args)
     mixed = {}
     if not args.no_mixed:
         # free the FP64 form's workspace first (two 4096^2 contexts fit, but
@@ -601,6 +671,7 @@ def run_ours(args):
         refined_step=dict(refine_steps=1, ms_per_step=sum(ref_ms) / len(ref_ms),
                           value=cells * world / (sum(ref_ms) / len(ref_ms) / 1e3)),
         mixed=mixed or None,
+        surrogate=surrogate,
         cpu_baseline=cpu,
     )
     print(json.dumps(line), flush=True)
