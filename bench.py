@@ -320,7 +320,7 @@ def run_probe_only():
                           fp64_nominal_tflops=FP64_NOMINAL_TFLOPS)), flush=True)
 
 
-def time_mixed(mr, prob, q, bcv, stream, flush, args, split, ref_fp64, wl, rank):
+def time_mixed(mr, prob, q, bcv, stream, flush, args, split, ref_fp64, wl, rank, refine=3):
     """The mixed form (FP32 leaves and lower merges, FP64 top merges, refined
     with double-double residuals): ms per build + solve, its accuracy
     against the refined FP64 result and the oracle's samples, and its phase
@@ -334,7 +334,7 @@ def time_mixed(mr, prob, q, bcv, stream, flush, args, split, ref_fp64, wl, rank)
                       precision=mr.binding.MRCM_MIXED)
     if split is not None:
         mr.mrcm_set_mixed_split(s.ctx, split)
-    mr.mrcm_set_refinement(s.ctx, 3)
+    mr.mrcm_set_refinement(s.ctx, refine)
     mr.mrcm_enable_timing(s.ctx, True)
 
     def step():
@@ -360,7 +360,7 @@ def time_mixed(mr, prob, q, bcv, stream, flush, args, split, ref_fp64, wl, rank)
         for k, v in mr.mrcm_phase_times(s.ctx).items():
             phases[k] += v
     out = [x.cpu().numpy().copy() for x in (s.p, s.Fx, s.Fy)]
-    mr.mrcm_set_refinement(s.ctx, 3, check=True)
+    mr.mrcm_set_refinement(s.ctx, refine, check=True)
     s.solve(q, bcv)
     hist = mr.mrcm_residual_history(s.ctx)
     rel = {name: float(np.linalg.norm(a - b) / np.linalg.norm(b))
@@ -370,7 +370,7 @@ def time_mixed(mr, prob, q, bcv, stream, flush, args, split, ref_fp64, wl, rank)
     del K
     torch.cuda.empty_cache()
     step_ms = sum(ms) / len(ms)
-    return dict(ms_per_step=step_ms, value=prob.nx * prob.ny / (step_ms / 1e3), refine_steps=3,
+    return dict(ms_per_step=step_ms, value=prob.nx * prob.ny / (step_ms / 1e3), refine_steps=refine,
                 fp32_merges_up_to_2g=(split if split is not None else 512),
                 rel_l2_vs_fp64_refined=rel, vs_oracle_samples=vs_oracle, residual_history=hist,
                 within_tolerance=bool(max(rel.values()) <= 1e-8), tolerance=1e-8,
@@ -590,8 +590,12 @@ def run_ours(args):
     if not args.no_mixed:
         # free the FP64 form's workspace first (two 4096^2 contexts fit, but
         # the timing should not share L2 with a resident second workspace)
-        for split, name in ((None, "mixed"), (1 << 30, "mixed_all_fp32")):
-            mixed[name] = time_mixed(mr, prob, q, bcv, stream, flush, args, split, refined, wl, rank)
+        # three refinement steps (the form's default), and the steps this
+        # field needs to reach the metric's 1e-8 (the residual contracts by
+        # ~0.3 per step here)
+        for split, name, refine in ((None, "mixed", 3), (1 << 30, "mixed_all_fp32", 3),
+                                    (None, "mixed_to_1e-8", 12)):
+            mixed[name] = time_mixed(mr, prob, q, bcv, stream, flush, args, split, refined, wl, rank, refine)
 
     ph = {k: v / args.steps for k, v in phases.items()}          # ms per step
     pf = mr.mrcm_phase_flops(solver.ctx)                          # flops per step
