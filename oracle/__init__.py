@@ -19,4 +19,5 @@ Modules (each function cites the passage of the paper it follows):
   refine     double-double residual of Eqs. 11.2-14.2 and iterative
              refinement of the discrete solution
   dd         double-double helpers (TwoSum, Dekker's TwoProd)
+  cnn        the surrogate network's 3 x 3 convolutions and their gradients
 """

@@ -5,7 +5,8 @@ and the residual gate with the plain local solve as fallback.
 - Basis fields psi_s = A^-1 B e_s of interior leaves against the oracle's
   local solves (Eqs. 11Hhatbasisa/b), to float accuracy.
 - Convolution forward, weight gradient and input gradient (forward kernel
-  on flipped weights) against numpy FP32 on the same BF16-rounded operands.
+  on flipped weights) against the oracle's FP64 arithmetic (oracle.cnn) on
+  the same BF16-rounded operands.
 - Training with the library's kernels lowers the loss.
 - The gate accepts exact fields and refuses wrong ones; with accepted exact
   fields the solution equals the plain one to float accuracy; with a trained
@@ -17,6 +18,7 @@ import numpy as np
 import pytest
 
 import inputs
+from oracle.cnn import conv3x3, conv3x3_wgrad, conv3x3_xgrad
 from oracle.geometry import Decomposition
 from oracle.local import LeafProblem
 from oracle.mrcm import solve_mrcm
@@ -29,21 +31,6 @@ SHAPES = [(16, 32, 0), (16, 32, 1), (32, 32, 1), (32, 16, 1)]
 def _bf16(a):
     import torch
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(torch.bfloat16)
-
-
-def _conv_ref(x, w, b, pad):
-    """NHWC 3 x 3 convolution in FP32: x [n, h, w, cin], w [cout, 3, 3, cin]."""
-    if pad:
-        x = np.pad(x, ((0, 0), (1, 1), (1, 1), (0, 0)))
-    ho = x.shape[1] - 2
-    out = np.zeros((x.shape[0], ho, ho, w.shape[0]), dtype=np.float64)
-    for ky in range(3):
-        for kx in range(3):
-            out += np.einsum("nhwc,oc->nhwo", x[:, ky:ky + ho, kx:kx + ho, :].astype(np.float64),
-                             w[:, ky, kx, :].astype(np.float64))
-    if b is not None:
-        out += b
-    return out
 
 
 def _leaf_key_perm(mr, ctx, dec, lp, leaf):
@@ -92,7 +79,7 @@ def test_conv_forward_matches_cpu_reference(mrcm_lib, cin, cout, pad):
     ybf = torch.empty((n, 16, 16, cout), dtype=torch.bfloat16, device="cuda")
     for relu in (False, True):
         mr.mrcm_cnn_conv_forward(xb.cuda(), n, cin, cout, pad, relu, wb.cuda(), torch.from_numpy(b).cuda(), ybf, y)
-        ref = _conv_ref(xb.float().numpy(), wb.float().numpy(), b, pad)
+        ref = conv3x3(xb.float().numpy(), wb.float().numpy(), b, pad)
         if relu:
             ref = np.maximum(ref, 0.0)
         assert rel(y.cpu().numpy(), ref) < 1e-5, (relu, rel(y.cpu().numpy(), ref))
@@ -111,28 +98,16 @@ def test_conv_gradients_match_cpu_reference(mrcm_lib, cin, cout, pad):
     dw = torch.zeros((cout, 3, 3, cin), dtype=torch.float32, device="cuda")
     db = torch.zeros(cout, dtype=torch.float32, device="cuda")
     mr.mrcm_cnn_conv_wgrad(xb.cuda(), dyb.cuda(), n, cin, cout, pad, dw, db)
-    x = xb.float().numpy()
-    dy = dyb.float().numpy().astype(np.float64)
-    xp = np.pad(x, ((0, 0), (1, 1), (1, 1), (0, 0))) if pad else x
-    ref = np.zeros((cout, 3, 3, cin))
-    for ky in range(3):
-        for kx in range(3):
-            ref[:, ky, kx, :] = np.einsum("nhwo,nhwc->oc", dy, xp[:, ky:ky + 16, kx:kx + 16, :].astype(np.float64))
+    ref, ref_db = conv3x3_wgrad(xb.float().numpy(), dyb.float().numpy(), pad)
     assert rel(dw.cpu().numpy(), ref) < 1e-5, rel(dw.cpu().numpy(), ref)
-    assert rel(db.cpu().numpy(), dy.sum(axis=(0, 1, 2))) < 1e-5
+    assert rel(db.cpu().numpy(), ref_db) < 1e-5
     if pad:
         # input gradient: the forward kernel on flipped weights
         w2 = torch.empty((cin, 3, 3, cout), dtype=torch.bfloat16, device="cuda")
         mr.mrcm_cnn_flip_weights(wb.cuda(), cout, cin, w2)
         dx = torch.empty((n, 16, 16, cin), dtype=torch.float32, device="cuda")
         mr.mrcm_cnn_conv_forward(dyb.cuda(), n, cout, cin, 1, False, w2, None, None, dx)
-        w = wb.float().numpy().astype(np.float64)
-        dyp = np.pad(dy, ((0, 0), (1, 1), (1, 1), (0, 0)))
-        ref_dx = np.zeros((n, 16, 16, cin))
-        for ky in range(3):
-            for kx in range(3):
-                # dX[u] = sum dY[u + 1 - ky] W[ky]
-                ref_dx += np.einsum("nhwo,oc->nhwc", dyp[:, 2 - ky:18 - ky, 2 - kx:18 - kx, :], w[:, ky, kx, :])
+        ref_dx = conv3x3_xgrad(dyb.float().numpy(), wb.float().numpy())
         assert rel(dx.cpu().numpy(), ref_dx) < 1e-5, rel(dx.cpu().numpy(), ref_dx)
 
 
