@@ -155,7 +155,6 @@ __device__ __forceinline__ void leaf_build_body(const DevView& v, LeafBuildSmem<
     const int w = WF ? WF : L.w, n = WF ? WF * WF : L.w * L.h, m = L.m, W2 = w + 2;
     T* Lg = leaf_L<T>(v) + L.L_off;          // n x 16 multipliers
     T* Dg = Lg + (long long)n * kLeafThreads;   // n reciprocal pivots
-    T* LTg = Dg + n;                         // n x 16 multipliers by row
     T* Zg = leaf_Z<T>(v) + L.Z_off;          // n x m, column-major (local segment order)
 
     // Columns of B ordered by their first nonzero row: column q of Z stays
@@ -215,7 +214,6 @@ __device__ __forceinline__ void leaf_build_body(const DevView& v, LeafBuildSmem<
             const T l = S.win[sl][1 + t] * rcp;
             S.lcol[t] = l;
             Lg[(long long)k * kLeafThreads + t] = l;
-            LTg[(long long)(k + 1 + t) * kLeafThreads + t] = l;
         }
         if (t == 0) Dg[k] = rcp;
         for (int q = t; q < ck; q += kLeafThreads) {
@@ -462,14 +460,15 @@ __device__ __forceinline__ void leaf_pressure_body(const DevView& v, bool accumu
     }
     __syncwarp(mask);
     // backward sweep L^T p = y in place, right-looking from the last row,
-    // on the row layout of L (row k: L[k][k-1-t] at LTg[16 k + t], contiguous);
-    // the multipliers stream through a register ring kSweepAhead steps ahead
-    const TS* LTg = Dg + n;
+    // reading row k of L from the column layout (L[k][k-1-t] is multiplier t
+    // of column k-1-t, at Lg[16 (k-1-t) + t]: a diagonal of the layout, whose
+    // lines the next steps read again from L1); the multipliers stream
+    // through a register ring kSweepAhead steps ahead
     double ring[kSweepAhead];
 #pragma unroll
     for (int d = 0; d < kSweepAhead; ++d) {
         const int k = n - 1 - d;
-        ring[d] = (k >= 1 && t < min(w, k)) ? LTg[(long long)k * kLeafThreads + t] : 0.0;
+        ring[d] = (k >= 1 && t < min(w, k)) ? Lg[(long long)(k - 1 - t) * kLeafThreads + t] : 0.0;
     }
     for (int k0 = n - 1; k0 >= 0; k0 -= kSweepAhead) {
 #pragma unroll
@@ -478,7 +477,7 @@ __device__ __forceinline__ void leaf_pressure_body(const DevView& v, bool accumu
             if (k < 0) break;
             const double lk = ring[d];
             const int kn = k - kSweepAhead;
-            ring[d] = (kn >= 1 && t < min(w, kn)) ? LTg[(long long)kn * kLeafThreads + t] : 0.0;
+            ring[d] = (kn >= 1 && t < min(w, kn)) ? Lg[(long long)(kn - 1 - t) * kLeafThreads + t] : 0.0;
             const double pk = S.y[k];
             if (t < min(w, k)) S.y[k - 1 - t] = fma(-lk, pk, S.y[k - 1 - t]);   // entry L[k][k-1-t]
             __syncwarp(mask);

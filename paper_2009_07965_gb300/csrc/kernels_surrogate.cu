@@ -53,7 +53,6 @@ __global__ void __launch_bounds__(128) leaf_fields_kernel(DevView v, const int* 
     const int w = L.w, n = L.w * L.h, m = L.m;
     const TS* Lg = leaf_L<TS>(v) + L.L_off;
     const TS* Dg = Lg + (long long)n * kLeafThreads;
-    const TS* LTg = Dg + n;
     const TS* Zg = leaf_Z<TS>(v) + L.Z_off;
     double* y = ys[slot];
     for (int s = 0; s < m; ++s) {
@@ -61,7 +60,7 @@ __global__ void __launch_bounds__(128) leaf_fields_kernel(DevView v, const int* 
         __syncwarp(mask);
         for (int k = n - 1; k >= 1; --k) {
             const double pk = y[k];
-            if (t < min(w, k)) y[k - 1 - t] = fma(-(double)LTg[(long long)k * kLeafThreads + t], pk, y[k - 1 - t]);
+            if (t < min(w, k)) y[k - 1 - t] = fma(-(double)Lg[(long long)(k - 1 - t) * kLeafThreads + t], pk, y[k - 1 - t]);
             __syncwarp(mask);
         }
         for (int k = t; k < n; k += kLeafThreads) psi[((long long)item * (kS * kS) + k) * 16 + s] = (float)y[k];

@@ -273,7 +273,7 @@ int make_plan(Plan& P) {
         LeafDesc& L = P.leaves[id];
         const long long n = (long long)L.w * L.h;
         L.L_off = P.nL;
-        P.nL += n * (2 * kLeafThreads + 1);
+        P.nL += n * (kLeafThreads + 1);
         L.Z_off = P.nZ;
         P.nZ += n * L.m;
         L.zb_off = P.nzb;

@@ -49,9 +49,8 @@ struct LeafDesc {
     int side_off[4];   // local index of the first segment of side x-, x+, y-,
                        // y+ (-1 when the side lies on the domain boundary)
     int seg_off;       // offset of the leaf's segment ids in leaf_segs
-    long long L_off;   // band factor: n x 16 multipliers by column (step k: rows k+1..k+16),
-                       // n reciprocal pivots, n x 16 multipliers by row (row k: columns
-                       // k-1..k-16) for the transposed sweep
+    long long L_off;   // band factor: n x 16 multipliers by column (step k: rows
+                       // k+1..k+16), then n reciprocal pivots
     long long Z_off;   // Z = L^-1 B: n rows x m
     long long zb_off;  // particular forward solve: n values
     long long R_off;   // node R (m x m) of the leaf
