@@ -286,8 +286,11 @@ __device__ __forceinline__ void leaf_build_body(const DevView& v, LeafBuildSmem<
         Rg[idx] = val;
     }}
 
+// Residency: the FP64 full-leaf variant holds 31 KB of shared memory per
+// CTA, so 7 CTAs fit an SM; the register cap keeps all 7 resident (one wave
+// of 1064 CTAs covers the 4096 leaves of a 1024^2 grid).
 template <int MMAX, int LPB, class T>
-__global__ void __launch_bounds__(kLeafThreads * LPB)
+__global__ void __launch_bounds__(kLeafThreads * LPB, MMAX == 16 ? (sizeof(T) == 8 ? 7 : 8) : 1)
 leaf_build_kernel(DevView v) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int t = threadIdx.x & (kLeafThreads - 1);
