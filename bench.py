@@ -613,19 +613,21 @@ def run_ours(args):
                      model="(2/3) N^3 per blocked interface system (LU count)")
         model["frac_model"] = model["achieved_model"] / peak
     build_ms = sum(ph[k] for k in ("coef", "leaf_build", "merge_small", "gj_sweep", "merge_form", "merge_x",
-                                   "merge_r"))
+                                   "merge_r", "root_factor"))
     model_build = mr.mrcm_query(solver.ctx, "MODEL_BUILD_FLOPS")
     basis = dict(ms=build_ms, model_gflop=model_build / 1e9,
                  model_tflops=model_build / (build_ms / 1e3) / 1e12,
                  frac_model=model_build / (build_ms / 1e3) / 1e12 / peak,
                  model="banded-Cholesky leaves + LU merges (MRCM_Q_MODEL_BUILD_FLOPS)")
     # per tree height of the build: the launch groups in order
-    heights = []
+    heights, by_kernel = [], []
     for name, ms in groups:
-        if name in ("merge_small", "gj_sweep"):
+        if name in ("merge_small", "gj_sweep", "root_factor"):
             heights.append(ms)                  # a new tree height starts
+            by_kernel.append({name: round(ms, 4)})
         elif name in ("merge_x", "merge_r") and heights:
             heights[-1] += ms
+            by_kernel[-1][name] = round(ms, 4)
     heights = [round(h, 4) for h in heights]
     if rank != 0:
         return
@@ -662,6 +664,7 @@ def run_ours(args):
         peaks_measured_tflops=peaks,
         basis_build=basis,
         merge_ms_per_height=heights,
+        merge_ms_per_height_by_kernel=by_kernel,
         autotuned_shapes=tuned,
         phases=table,
         gflop_per_step=sum(pf.values()) / 1e9,

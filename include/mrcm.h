@@ -250,7 +250,10 @@ enum {
     MRCM_PHASE_LEAF_PRESSURE = 10, /* leaf pressures, interface unknowns (solve)    */
     MRCM_PHASE_RESIDUAL = 11,      /* refinement residuals (solve)                  */
     MRCM_PHASE_FINISH = 12,        /* mean shift and face fluxes (solve)            */
-    MRCM_PHASE_COUNT = 13
+    MRCM_PHASE_ROOT_FACTOR = 13,   /* blocked merges of a root level in the factor
+                                      form: block LDL^T of the quasi-definite form
+                                      (mrcm_set_root_form)                         */
+    MRCM_PHASE_COUNT = 14
 };
 
 /*
@@ -302,6 +305,29 @@ int mrcm_set_wait_limit(mrcm_ctx* ctx, long long polls);
  * context), MRCM_ERR_CUDA.
  */
 int mrcm_set_mixed_split(mrcm_ctx* ctx, int max_g2_fp32);
+
+/*
+ * mrcm_set_root_form -- how the interface system of a tree's root is kept
+ * (Algorithm 1's top merge: the root has no outer segments, so the build
+ * needs neither X nor a merged map there, only the means to solve for
+ * lambda_gamma in every solve pass, Section 3.2).
+ * MRCM_ROOT_FACTOR: the block LDL^T factor T = Lt Dt Lt^T of the
+ * quasi-definite form (16-wide diagonal blocks, inverted with the same
+ * sign-checked elimination as the inverse), about a third of the
+ * inversion's flops; each solve pass then runs two block triangular sweeps
+ * on it (64-row blocks, each waiting only for the blocks it depends on).
+ * MRCM_ROOT_INVERSE: the explicit inverse, as at every other blocked height;
+ * each solve pass then applies it as a matrix-vector product.
+ * MRCM_ROOT_AUTO (the default): the factor for root systems of 2g >= 1024,
+ * the inverse below (there both eliminations are bound by the same chain of
+ * pivot blocks and the product is the shorter solve).
+ * Applies to tree heights with 2g > 32 whose nodes all lack outer segments.
+ * Both forms solve the same equations (to rounding).  Invalidates the basis
+ * (call mrcm_build_basis again).  Errors: MRCM_ERR_INVALID_ARG,
+ * MRCM_ERR_CUDA.
+ */
+enum { MRCM_ROOT_FACTOR = 0, MRCM_ROOT_INVERSE = 1, MRCM_ROOT_AUTO = 2 };
+int mrcm_set_root_form(mrcm_ctx* ctx, int form);
 
 /*
  * mrcm_autotune -- picks the launch shapes of every blocked merge level by

@@ -13,6 +13,7 @@ LIB_PATH = os.path.join(HERE, "libmrcm.so")
 
 MRCM_BC_NEUMANN, MRCM_BC_DIRICHLET = 0, 1
 MRCM_FP64, MRCM_MIXED, MRCM_SURROGATE = 0, 1, 2
+MRCM_ROOT_FACTOR, MRCM_ROOT_INVERSE, MRCM_ROOT_AUTO = 0, 1, 2
 ERRORS = {0: "MRCM_OK", -1: "MRCM_ERR_INVALID_ARG", -2: "MRCM_ERR_SHAPE", -3: "MRCM_ERR_BAD_K",
           -4: "MRCM_ERR_NOT_BUILT", -5: "MRCM_ERR_SINGULAR", -6: "MRCM_ERR_CUDA",
           -7: "MRCM_ERR_OOM", -8: "MRCM_ERR_TIMEOUT", -9: "MRCM_ERR_UNSUPPORTED"}
@@ -28,12 +29,12 @@ EXPORTS = ["mrcm_setup", "mrcm_setup_batch", "mrcm_plan_query", "mrcm_set_permea
            "mrcm_last_cuda_error",
            "mrcm_merge_pair_noalloc", "mrcm_set_refinement", "mrcm_residual_history", "mrcm_phase_flops",
            "mrcm_group_times", "mrcm_check_reciprocal", "mrcm_set_wait_limit",
-           "mrcm_probe_peak", "mrcm_set_mixed_split", "mrcm_autotune", "mrcm_tune_info",
+           "mrcm_probe_peak", "mrcm_set_mixed_split", "mrcm_set_root_form", "mrcm_autotune", "mrcm_tune_info",
            "mrcm_interior_leaves", "mrcm_leaf_fields", "mrcm_leaf_patches", "mrcm_leaf_gate", "mrcm_leaf_apply",
            "mrcm_cnn_conv_forward", "mrcm_cnn_conv_wgrad", "mrcm_cnn_flip_weights", "mrcm_cnn_relu_grad",
            "mrcm_cnn_mse_grad", "mrcm_cnn_adam"]
 PHASES = ["coef", "leaf_build", "merge_small", "gj_sweep", "merge_form", "merge_x", "merge_r",
-          "leaf_particular", "tree_up", "tree_down", "leaf_pressure", "residual", "finish"]
+          "leaf_particular", "tree_up", "tree_down", "leaf_pressure", "residual", "finish", "root_factor"]
 # kernel family behind each phase (for reports)
 PHASE_KERNELS = {"coef": "face_coef_kernel", "leaf_build": "leaf_build_kernel",
                  "merge_small": "merge_small_kernel", "gj_sweep": "gj_sweep_kernel",
@@ -41,7 +42,7 @@ PHASE_KERNELS = {"coef": "face_coef_kernel", "leaf_build": "leaf_build_kernel",
                  "merge_r": "merge_rupdate_kernel", "leaf_particular": "leaf_particular_kernel",
                  "tree_up": "tree_up_kernel", "tree_down": "tree_down_kernel",
                  "leaf_pressure": "leaf_pressure_kernel", "residual": "residual_cells/segments_kernel",
-                 "finish": "face_flux_kernel"}
+                 "finish": "face_flux_kernel", "root_factor": "ldl_sweep_kernel"}
 
 
 class MrcmError(RuntimeError):
@@ -138,6 +139,8 @@ def _lib():
         lib.mrcm_tune_info.restype = I
         lib.mrcm_set_mixed_split.argtypes = [P, I]
         lib.mrcm_set_mixed_split.restype = I
+        lib.mrcm_set_root_form.argtypes = [P, I]
+        lib.mrcm_set_root_form.restype = I
         lib.mrcm_probe_peak.argtypes = [I, D, ctypes.POINTER(ctypes.c_double), P]
         lib.mrcm_probe_peak.restype = I
         lib.mrcm_set_wait_limit.argtypes = [P, ctypes.c_longlong]
@@ -386,6 +389,11 @@ def mrcm_tune_info(ctx, height):
 
 def mrcm_set_mixed_split(ctx, max_g2_fp32):
     _check(_lib().mrcm_set_mixed_split(ctx, int(max_g2_fp32)), "mrcm_set_mixed_split")
+
+
+def mrcm_set_root_form(ctx, form):
+    """MRCM_ROOT_FACTOR (0), MRCM_ROOT_INVERSE (1) or MRCM_ROOT_AUTO (2, default); the basis must be rebuilt."""
+    _check(_lib().mrcm_set_root_form(ctx, int(form)), "mrcm_set_root_form")
 
 
 def mrcm_set_wait_limit(ctx, polls):

@@ -47,6 +47,12 @@
 // lambda_gamma = X lambda_o + W (-rbar_gamma).  Iterative refinement
 // (kernels_refine.cu) absorbs the rounding of an inverse-based solve.
 //
+// A root (no outer segments: no X, no merged map) may be kept as a block
+// LDL^T factor of T instead (a third of the inversion's flops; by default
+// for 2g >= 1024, mrcm_set_root_form); its solve passes then run block
+// triangular sweeps (ldl_sweep_kernel and the factor-form branches of
+// tree_up_kernel / tree_down_kernel).
+//
 // Storage: W column-major per node (entry (r, c) at c*2g + r); X column-major
 // (2g x m).  Two launch shapes.  Levels with 2g <= 32: one group of 2g (padded
 // to a power of two) lanes per node does the whole merge in registers
@@ -65,6 +71,7 @@ constexpr int kGJTile = 32;       // output tile of the blocked update (kGJTile^
 constexpr int kSmallMax = 32;     // largest 2g merged by the per-node register kernel
 constexpr int kRTile = 32;       // R update tile
 constexpr double kTinyPivot = 1e-14;   // pivots of the scaled form are O(1)
+constexpr double kRsqrt2 = 0.70710678118654752440;   // 1 / sqrt(2), the sum / difference transform
 
 struct NodeRefs {
     int g, g2, m, o1, m1, m2;
@@ -984,6 +991,330 @@ __global__ void __launch_bounds__(256) gj_sweep_kernel(DevView v, int first, int
     __syncthreads();
     if (tid == 0 && s_bad) atomicOr(v.status, kStatusSingular);
 }
+// (row, column) of entry r of a row-packed lower triangle
+__device__ __forceinline__ void tri_rc(int r, int& a, int& b) {
+    a = (int)((sqrtf(8.0f * r + 1.0f) - 1.0f) * 0.5f);
+    while ((a + 1) * (a + 2) / 2 <= r) ++a;
+    while (a * (a + 1) / 2 > r) --a;
+    b = r - a * (a + 1) / 2;
+}
+
+// ---------------------------------------------------------------------------
+// Factor form of a root interface system (a level whose nodes have no outer
+// segments: only lambda_gamma = -M^-1 rbar_gamma is ever needed, no X and no
+// merged map).  The same blocked elimination as the sweep above, restricted
+// to the trailing part: at block step k only entries with both indices past
+// K are updated, which is a block LDL^T factorisation
+//     T = Lt Dt Lt^T,  Lt unit block-lower (identity kGJ x kGJ diagonal
+//     blocks),  Dt = blockdiag(A_KK) (the Schur complements met at the steps),
+// with Lt(x, K) = u_x^T (u_x = A_KK^-1 c_x^T as above) and Dt_K^-1 = P_K.
+// About N^3 / 3 flops instead of the N^3 of the inversion.  On exit the
+// node's W storage holds, on and below the diagonal, Lt below the diagonal
+// blocks and P_K = Dt_K^-1 in them (lower triangles; P_K is symmetric); a
+// solve is then T^-1 b = Lt^-T P Lt^-1 b (two block triangular sweeps,
+// tree_up / tree_down).  The quasi-definite T needs no pivot search here
+// either: the diagonal blocks are inverted by gj_invert_block with its sign
+// tests.
+
+// Tile of rank r among the lower tiles (ti >= tj) of the trailing triangle
+// of tiles [t0, tiles) at a block step: the tiles of column tk (the one that
+// holds the next block K1, as columns) first, so that their c, which the u
+// items wait for, come in early; then the others in row order.  tk - t0 is
+// 0 or 1 (K, kGJ wide, starts in tile t0; K1 follows it); tkc = 0 when no
+// node of the level has a next block (then plain row order).
+__device__ __forceinline__ void ldl_trailing_tile(int r, int t0, int tiles, int tk, bool col_first, int& ti,
+                                                  int& tj) {
+    const int n = tiles - t0;
+    int a, b;
+    if (!col_first) {
+        tri_rc(r, a, b);
+        ti = t0 + a;
+        tj = t0 + b;
+        return;
+    }
+    const int kp = tk - t0;                       // 0 or 1
+    if (r < n - kp) {                             // column tk, rows tk .. tiles-1
+        ti = tk + r;
+        tj = tk;
+        return;
+    }
+    r -= n - kp;
+    if (kp == 0) {                                // the rest: columns t0+1 .. (a triangle of n-1)
+        tri_rc(r, a, b);
+        ti = t0 + 1 + a;
+        tj = t0 + 1 + b;
+        return;
+    }
+    if (r < n) {                                  // column t0 (holds K), all its rows
+        ti = t0 + r;
+        tj = t0;
+        return;
+    }
+    tri_rc(r - n, a, b);                          // columns t0+2 .. (a triangle of n-2)
+    ti = t0 + 2 + a;
+    tj = t0 + 2 + b;
+}
+
+// Tile items of the node whose c of the next block a u item waits for, summed
+// over the block steps 0..step (each step: the tiles of column tk from row tk
+// down, tiles_n - tk of them, tk = (step + 1) / 2 with kGJ = kGJTile / 2).
+__device__ __forceinline__ unsigned int ldl_cready_target(int step, int tiles_n) {
+    static_assert(2 * kGJ == kGJTile, "two blocks per tile");
+    const unsigned int s1 = (unsigned int)step + 1u;
+    return s1 * (unsigned int)tiles_n - (s1 * s1) / 4u;
+}
+
+// Block step k of the factorisation for one (node, lower output tile (ti >=
+// tj) with columns reaching K): entries with both indices past K get
+// A_ij - c_i . u_j (the next diagonal block K1 x K1 is left to
+// gj_next_diag_item), the block column K below K gets Lt = u^T, the diagonal
+// block K gets P_K; c of step k + 1 is written for the indices below K1.
+template <class T>
+__device__ void ldl_step_item(const DevView& v, const MergeDesc& D, int slot, int ti, int tj, int step,
+                              T* scratch, int nmax, GJSmem<T>& S) {
+    const int N = 2 * D.g;
+    const int k0 = step * kGJ, nb = min(kGJ, N - k0);
+    const int k1 = k0 + kGJ, nb1 = k1 < N ? min(kGJ, N - k1) : 0;
+    const int r0 = ti * kGJTile, c0 = tj * kGJTile;
+    T* A = gj_work<T>(v) + D.W_off;
+    T* sc = gj_scratch(scratch, slot, nmax);
+    const T* Pg = gj_P(sc, step);
+    const T* cv = gj_cvec(sc, step, nmax);
+    const T* uv = gj_uvec(sc, step, nmax);
+    T* cn = gj_cvec(sc, step + 1, nmax);
+    const int tid = threadIdx.x;
+    const int tr = (tid % 16) * 2, tc = (tid / 16) * 2;
+    const int kend = k0 + nb;                     // first index past K
+    T old[2][2];
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+        const int j = c0 + tc + b;
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            const int i = r0 + tr + a;
+            old[a][b] = (j < N && i < N && i >= j && j >= kend) ? ldcg(A + (long long)j * N + i) : (T)0;
+        }
+    }
+    for (int idx = tid; idx < kGJTile * kGJ; idx += 256) {
+        const int xl = idx / kGJ, cc = idx % kGJ;
+        const int xi = r0 + xl, xj = c0 + xl;
+        const bool okc = cc < nb;
+        S.Cr[xl][cc] = (okc && xi < N && xi >= kend) ? ldcg(cv + (long long)xi * kGJ + cc) : (T)0;
+        S.Ur[xl][cc] = (okc && xi < N && xi >= kend) ? ldcg(uv + (long long)xi * kGJ + cc) : (T)0;
+        S.Uc[xl][cc] = (okc && xj < N && xj >= kend) ? ldcg(uv + (long long)xj * kGJ + cc) : (T)0;
+    }
+    __syncthreads();
+    T acc[2][2] = {{0, 0}, {0, 0}};
+#pragma unroll
+    for (int cc = 0; cc < kGJ; ++cc) {
+        const T l0 = S.Cr[tr][cc], l1 = S.Cr[tr + 1][cc];
+        const T u0 = S.Uc[tc][cc], u1 = S.Uc[tc + 1][cc];
+        acc[0][0] = fma(l0, u0, acc[0][0]);
+        acc[0][1] = fma(l0, u1, acc[0][1]);
+        acc[1][0] = fma(l1, u0, acc[1][0]);
+        acc[1][1] = fma(l1, u1, acc[1][1]);
+    }
+    const bool k1cols = nb1 > 0 && k1 >= c0 && k1 < c0 + kGJTile;
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+        const int j = c0 + tc + b;
+        if (j >= N || j < k0) continue;           // eliminated columns hold Lt already
+        const bool jK = j < kend;
+        const bool jK1 = j >= k1 && j < k1 + nb1;
+        T* col = A + (long long)j * N;
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            const int i = r0 + tr + a;
+            if (i >= N || i < j) continue;
+            const bool iK = i < kend;
+            const bool iK1 = i >= k1 && i < k1 + nb1;
+            T val;
+            if (iK && jK) {
+                val = ldcg(Pg + (i - k0) * kGJ + (j - k0));     // P_K = Dt_K^-1
+            } else if (jK) {
+                val = S.Ur[tr + a][j - k0];                     // Lt(i, K) = u_i^T
+            } else if (iK1 && jK1) {
+                continue;                                       // the next diagonal block
+            } else {
+                val = old[a][b] - acc[a][b];
+            }
+            col[i] = val;
+            if (jK1 && !iK1) cn[(long long)i * kGJ + (j - k1)] = val;   // c_i = A(i, K1), i past K1
+        }
+    }
+    if (k1cols) {
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) atomicAdd(gj_cready(sc, nmax), 1u);
+    }
+    __syncthreads();
+}
+
+// u of step k + 1 for one (node, run of indices [x0, x0 + len) past K1):
+// u_x = P_(k+1) c_x^T once P_(k+1) is published and every tile of column tk
+// has written its c.  Returns false when a wait timed out.
+template <class T>
+__device__ bool ldl_u_item(const DevView& v, const MergeDesc& D, int slot, int x0, int len, int step,
+                           T* scratch, int nmax, GJSmem<T>& S) {
+    const int N = 2 * D.g;
+    const int k1 = (step + 1) * kGJ, nb1 = min(kGJ, N - k1);
+    const int tiles_n = (N + kGJTile - 1) / kGJTile;
+    T* sc = gj_scratch(scratch, slot, nmax);
+    const T* Pn = gj_P(sc, step + 1);
+    const T* cn = gj_cvec(sc, step + 1, nmax);
+    T* un = gj_uvec(sc, step + 1, nmax);
+    const int tid = threadIdx.x;
+    const int o = tid >> 1, half = tid & 1;
+    const int xl = o / kGJ, rr = o % kGJ;
+    if (!wait_flag(gj_cready(sc, nmax), ldl_cready_target(step, tiles_n), v.status, v.spin_limit)) return false;
+    auto stage_c = [&](int xs) {
+        for (int idx = tid; idx < kUChunk * kGJ; idx += 256) {
+            const int yl = idx / kGJ, cc = idx % kGJ, y = xs + yl;
+            const bool ok = y < N && y >= k1 + nb1 && cc < nb1;
+            S.Cr[yl][cc] = ok ? ldcg(cn + (long long)y * kGJ + cc) : (T)0;
+        }
+    };
+    stage_c(x0);
+    if (!wait_flag(gj_flag(sc, nmax), (unsigned int)(step + 1), v.status, v.spin_limit)) return false;
+    for (int idx = tid; idx < kGJ * kGJ; idx += 256) S.Ps[idx / kGJ][idx % kGJ] = ldcg(Pn + idx);
+    for (int xs = x0; xs < x0 + len; xs += kUChunk) {
+        if (xs != x0) stage_c(xs);
+        __syncthreads();
+        const int x = xs + xl;
+        T a0 = 0, a1 = 0;
+#pragma unroll
+        for (int cc = half * (kGJ / 2); cc < (half + 1) * (kGJ / 2); cc += 2) {
+            a0 = fma(S.Ps[rr][cc], S.Cr[xl][cc], a0);
+            a1 = fma(S.Ps[rr][cc + 1], S.Cr[xl][cc + 1], a1);
+        }
+        T sum = a0 + a1;
+        sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+        if (half == 0 && x < N && x >= k1 + nb1 && rr < nb1) un[(long long)x * kGJ + rr] = sum;
+        __syncthreads();
+    }
+    return true;
+}
+
+// The factorisation of one root level in one cooperative launch: T of every
+// node, P_0, c and u of block 0, then per block step the next diagonal
+// blocks, the trailing tiles (column tk first) and the u of the next step
+// past K1, with a grid barrier after each step.  T: the arithmetic of the
+// level (double; float for an FP32 level of the mixed form, which factors in
+// the FP32 work array and stores Lt and P in double at the end).
+template <class T>
+__global__ void __launch_bounds__(256) ldl_sweep_kernel(DevView v, int first, int count, int nmax, T* scratch,
+                                                        unsigned int* counter) {
+    __shared__ GJSmem<T> S;
+    __shared__ int s_bad;
+    __shared__ double red[8];
+    extern __shared__ __align__(16) double scl[];           // 2g scalings (form)
+    const int tiles = (nmax + kGJTile - 1) / kGJTile;
+    const int nsteps = (nmax + kGJ - 1) / kGJ;
+    const int tid = threadIdx.x;
+    unsigned int round = 0;
+    if (tid == 0) s_bad = 0;
+    __syncthreads();
+    {
+        const long long per = (long long)nmax * nmax, run = level_run(per, count);
+        const long long runs = (per + run - 1) / run;
+        for (long long item = blockIdx.x; item < count * runs; item += gridDim.x) {
+            const int q = (int)(item / runs);
+            const long long e0 = (item % runs) * run;
+            const MergeDesc D = v.merges[first + q];
+            const long long nT = 4LL * D.g * D.g;
+            if (e0 >= nT) continue;                                  // uniform per CTA
+            form_item<T>(v, D, e0, min(e0 + run, nT), scl, red);
+        }
+    }
+    if (!grid_barrier(counter, round, v.status, v.spin_limit)) return;
+    for (int q = blockIdx.x; q < count; q += gridDim.x) {
+        const MergeDesc D = v.merges[first + q];
+        const int N = 2 * D.g, nb = min(kGJ, N);
+        const T* A = gj_work<T>(v) + D.W_off;
+        for (int idx = tid; idx < kGJ * kGJ; idx += 256) {
+            const int pr = idx % kGJ, pc = idx / kGJ;
+            S.Ps[pr][pc] = (pr < nb && pc < nb) ? ldcg(A + (long long)pc * N + pr) : (pr == pc ? (T)1 : (T)0);
+        }
+        __syncthreads();
+        if (!gj_invert_block(S.Ps, S.Pt, S.rp, S.tt, nb, D.g)) s_bad = 1;
+        T* sc = gj_scratch(scratch, q, nmax);
+        T* P0 = gj_P(sc, 0);
+        for (int idx = tid; idx < kGJ * kGJ; idx += 256) P0[idx] = S.Ps[idx / kGJ][idx % kGJ];
+        if (tid == 0) {
+            *gj_flag(sc, nmax) = 0u;
+            *gj_cready(sc, nmax) = 0u;
+        }
+        __syncthreads();
+    }
+    if (!grid_barrier(counter, round, v.status, v.spin_limit)) return;
+    for (int item = blockIdx.x; item < count * tiles; item += gridDim.x) {
+        const int q = item / tiles, x0 = (item % tiles) * kGJTile;
+        const MergeDesc D = v.merges[first + q];
+        if (x0 >= 2 * D.g) continue;                         // uniform per CTA
+        gj_first_cu_item(v, D, q, x0, scratch, nmax, S);
+    }
+    if (!grid_barrier(counter, round, v.status, v.spin_limit)) return;
+    for (int step = 0; step < nsteps; ++step) {
+        const int k0 = step * kGJ;
+        const int t0 = k0 / kGJTile;                          // tile column holding K
+        const int tk = (k0 + kGJ) / kGJTile;                  // tile column holding K1
+        const bool col_first = k0 + kGJ < nmax;
+        const int n = tiles - t0;
+        const int ntri = n * (n + 1) / 2;
+        const int tkc = col_first ? tiles - tk : 0;           // column-tk tiles per node
+        for (int item = blockIdx.x; item < count * (1 + ntri); item += gridDim.x) {
+            if (item < count) {
+                const MergeDesc D = v.merges[first + item];
+                if (k0 + kGJ >= 2 * D.g) continue;
+                if (!gj_next_diag_item(v, D, item, step, scratch, nmax, S)) s_bad = 1;
+                continue;
+            }
+            const int it = item - count;
+            int q, r;
+            if (it < count * tkc) { q = it / tkc; r = it % tkc; }
+            else { q = (it - count * tkc) / (ntri - tkc); r = tkc + (it - count * tkc) % (ntri - tkc); }
+            int ti, tj;
+            ldl_trailing_tile(r, t0, tiles, tk, col_first, ti, tj);
+            const MergeDesc D = v.merges[first + q];
+            if (k0 >= 2 * D.g || ti * kGJTile >= 2 * D.g) continue;
+            ldl_step_item(v, D, q, ti, tj, step, scratch, nmax, S);
+        }
+        // u of step + 1 past the next block, spread over all CTAs
+        const int xs0 = k0 + 2 * kGJ;                         // first index past K1
+        if (xs0 < nmax) {
+            const int span = nmax - xs0;
+            const int per = (count * span + (int)gridDim.x - 1) / (int)gridDim.x;
+            const int ulen = max(kUChunk, (per + kUChunk - 1) / kUChunk * kUChunk);
+            const int uchunks = (span + ulen - 1) / ulen;
+            for (int item = blockIdx.x; item < count * uchunks; item += gridDim.x) {
+                const int q = item / uchunks, x0 = xs0 + (item % uchunks) * ulen;
+                const MergeDesc D = v.merges[first + q];
+                if (xs0 >= 2 * D.g || x0 >= 2 * D.g) continue;       // nothing past K1 in this node
+                if (!ldl_u_item(v, D, q, x0, min(ulen, 2 * D.g - x0), step, scratch, nmax, S)) return;
+            }
+        }
+        if (!grid_barrier(counter, round, v.status, v.spin_limit)) return;
+    }
+    // an FP32 level: Lt and P (on and below the diagonal) into the double storage
+    if (sizeof(T) != sizeof(double)) {
+        for (long long item = blockIdx.x; item < (long long)count * tiles * tiles; item += gridDim.x) {
+            const int q = (int)(item / ((long long)tiles * tiles));
+            const int rem = (int)(item % ((long long)tiles * tiles));
+            const int ti = rem % tiles, tj = rem / tiles;
+            const MergeDesc D = v.merges[first + q];
+            const int N = 2 * D.g;
+            if (ti < tj || ti * kGJTile >= N) continue;
+            const T* A = gj_work<T>(v) + D.W_off;
+            double* Wd = v.W + D.W_off;
+            for (int idx = tid; idx < kGJTile * kGJTile; idx += 256) {
+                const int i = ti * kGJTile + idx % kGJTile, j = tj * kGJTile + idx / kGJTile;
+                if (i < N && j < N && i >= j) Wd[(long long)j * N + i] = (double)ldcg(A + (long long)j * N + i);
+            }
+        }
+    }
+    __syncthreads();
+    if (tid == 0 && s_bad) atomicOr(v.status, kStatusSingular);
+}
 
 
 // X = -W C with C = blockdiag(R^a_go, R^b_go): column j < o1 uses the first
@@ -1126,9 +1457,191 @@ __global__ void __launch_bounds__(256) merge_rupdate_kernel(DevView v, int first
     }
 }
 
-// Solve phase, bottom-up: the node's particular fluxes
-// rbar = rbar_o + X^T rbar_gamma (Eqs. particular.1-2 with M symmetric); one
-// warp per output, lanes split the sum over gamma.
+// ---------------------------------------------------------------------------
+// Block triangular sweeps with the factor Lt of a root level, in blocks of
+// kSolveBlock unknowns (kSolveBlock / kGJ factor blocks), left-looking: the
+// item of block K (one CTA) forms its right-hand side, subtracts the
+// products with the blocks it depends on as each of them is published
+// (a flag per block, bounded waits), solves its diagonal part of Lt
+// (identity kGJ blocks, full kGJ x kGJ blocks below them: kSolveBlock / kGJ
+// dependent sub-steps) and publishes its own unknowns.  Items run in the
+// order of the dependencies (forward: K ascending; backward: K descending)
+// over the CTAs of a cooperative launch, so an item only waits for items
+// that come earlier in that order, and the chain is one block's products
+// and its small solve per block instead of a grid barrier.
+constexpr int kSolveBlock = kTriBlock;
+constexpr int kSolveSub = kSolveBlock / kGJ;
+constexpr int kSolvePairs = kSolveSub * (kSolveSub - 1) / 2;
+static_assert(kSolveSub == 4, "four factor blocks per solve block");
+
+struct TriSmem {
+    double Ls[kSolvePairs][kGJ][kGJ + 1];   // the blocks (b, a), b > a, of the diagonal part
+    double rhs[kSolveBlock];
+    double sol[kSolveBlock];
+    double dep[kSolveBlock];                // unknowns of the block being subtracted
+    double part[4][kSolveBlock];
+};
+// pair index of the sub-block (b, a), b > a
+__device__ __forceinline__ int tri_pair(int b, int a) { return b * (b - 1) / 2 + a; }
+
+// Stages the diagonal part of Lt for the block [s0, s0 + kSolveBlock) of a
+// node (rows past N read as 0).
+__device__ __forceinline__ void tri_stage_diag(const double* Wn, int N, int s0, TriSmem& S) {
+    for (int idx = threadIdx.x; idx < kSolvePairs * kGJ * kGJ; idx += 256) {
+        const int pr = idx / (kGJ * kGJ), e = idx % (kGJ * kGJ), rr = e % kGJ, cc = e / kGJ;
+        int b = 1;
+        while (tri_pair(b + 1, 0) <= pr) ++b;
+        const int a = pr - tri_pair(b, 0);
+        const int row = s0 + b * kGJ + rr, col = s0 + a * kGJ + cc;
+        S.Ls[pr][rr][cc] = row < N ? __ldcg(Wn + (long long)col * N + row) : 0.0;
+    }
+}
+
+// Publishes a block's unknowns: the stores, a fence, then the flag.
+__device__ __forceinline__ void tri_publish(unsigned int* flag) {
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) atomicExch(flag, 1u);
+}
+
+// Forward item: y_K = Lt_KK^-1 (rhat_K - sum_{J<K} Lt_KJ y_J) for block K of
+// one node of a root level; rhat = Q^T S rbar_gamma is formed here from the
+// children's particular fluxes; y goes to out (v.fwd).  Returns false when
+// a wait timed out.
+__device__ bool tri_forward_item(const DevView& v, const MergeDesc& D, int K, unsigned int* flags,
+                                 TriSmem& S) {
+    const int tid = threadIdx.x, N = 2 * D.g, g = D.g, s0 = K * kSolveBlock;
+    const int nbk = min(kSolveBlock, N - s0);
+    const double* Wn = v.W + D.W_off;
+    double* out = v.fwd + 2LL * D.gamma_off;
+    if (tid < kSolveBlock) {
+        double r = 0.0;
+        if (tid < nbk) {
+            const int x = s0 + tid, i = x < g ? x : x - g;
+            const NodeRefs Nr = node_refs(v, D);
+            const double ra = __ldcg(v.rbar + D.r1_off + Nr.gpos1[i]);
+            const double rb = __ldcg(v.rbar + D.r2_off + Nr.gpos2[i]);
+            const double sc = kRsqrt2 / sqrt(gamma_D(v, D, i));
+            r = x < g ? sc * (rb - ra) : sc * (ra + rb);
+        }
+        S.rhs[tid] = r;
+    }
+    tri_stage_diag(Wn, N, s0, S);
+    const int rr = tid % kSolveBlock, grp = tid / kSolveBlock;
+    for (int J = 0; J < K; ++J) {
+        // this thread's entries of Lt_KJ are loaded before the wait (they do
+        // not depend on it), so the chain holds only the products
+        double lt[kGJ];
+        const double* col = Wn + (long long)(J * kSolveBlock + grp * kGJ) * N + s0 + rr;
+#pragma unroll
+        for (int jj = 0; jj < kGJ; ++jj) lt[jj] = rr < nbk ? __ldcg(col + (long long)jj * N) : 0.0;
+        if (!wait_flag(flags + J, 1u, v.status, v.spin_limit)) return false;
+        if (tid < kSolveBlock) S.dep[tid] = __ldcg(out + J * kSolveBlock + tid);
+        __syncthreads();
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+#pragma unroll
+        for (int jj = 0; jj < kGJ; jj += 4) {
+            a0 = fma(lt[jj], S.dep[grp * kGJ + jj], a0);
+            a1 = fma(lt[jj + 1], S.dep[grp * kGJ + jj + 1], a1);
+            a2 = fma(lt[jj + 2], S.dep[grp * kGJ + jj + 2], a2);
+            a3 = fma(lt[jj + 3], S.dep[grp * kGJ + jj + 3], a3);
+        }
+        S.part[grp][rr] = (a0 + a1) + (a2 + a3);
+        __syncthreads();
+        if (tid < kSolveBlock) S.rhs[tid] -= (S.part[0][tid] + S.part[1][tid]) + (S.part[2][tid] + S.part[3][tid]);
+    }
+    __syncthreads();
+    if (tid < kGJ) S.sol[tid] = S.rhs[tid];
+    __syncthreads();
+    const int sr = tid / kGJ, p = tid % kGJ;
+    for (int b = 1; b < kSolveSub; ++b) {
+        double acc = 0.0;
+        for (int a = 0; a < b; ++a) acc = fma(S.Ls[tri_pair(b, a)][sr][p], S.sol[a * kGJ + p], acc);
+#pragma unroll
+        for (int w = kGJ / 2; w > 0; w >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, w, kGJ);
+        if (p == 0) S.sol[b * kGJ + sr] = S.rhs[b * kGJ + sr] - acc;
+        __syncthreads();
+    }
+    if (tid < nbk) out[s0 + tid] = S.sol[tid];
+    tri_publish(flags + K);
+    __syncthreads();
+    return true;
+}
+
+// Backward item: x_K = Lt_KK^-T (z_K - sum_{J>K} Lt_JK^T x_J) with z = P y
+// (the inverse diagonal blocks of the factor on the forward result, formed
+// here); x goes to out (rgam).  Returns false when a wait timed out.
+__device__ bool tri_backward_item(const DevView& v, const MergeDesc& D, int K, unsigned int* flags,
+                                  TriSmem& S) {
+    const int tid = threadIdx.x, N = 2 * D.g, s0 = K * kSolveBlock;
+    const int nbk = min(kSolveBlock, N - s0), nblk = (N + kSolveBlock - 1) / kSolveBlock;
+    const double* Wn = v.W + D.W_off;
+    const double* y = v.fwd + 2LL * D.gamma_off;
+    double* out = v.rgam + 2LL * D.gamma_off;
+    if (tid < kSolveBlock) {
+        double z = 0.0;
+        if (tid < nbk) {
+            const int r = s0 + tid, k0 = r - r % kGJ, nb = min(kGJ, N - k0);
+            for (int cc = 0; cc < nb; ++cc) {
+                const int col = k0 + cc;
+                const double pv = r >= col ? Wn[(long long)col * N + r] : Wn[(long long)r * N + col];
+                z = fma(pv, __ldcg(y + col), z);
+            }
+        }
+        S.rhs[tid] = z;
+    }
+    tri_stage_diag(Wn, N, s0, S);
+    // kGJ lanes over the rows of block J, one column of block K per lane group
+    const int lane = tid % kGJ, cg = tid / kGJ;           // 16 column groups
+    for (int J = nblk - 1; J > K; --J) {
+        const int nbj = min(kSolveBlock, N - J * kSolveBlock);
+        // this thread's entries of Lt_JK (4 columns x 4 rows), loaded before
+        // the wait
+        double lt[kSolveBlock / 16][kSolveBlock / kGJ];
+#pragma unroll
+        for (int c4 = 0; c4 < kSolveBlock / 16; ++c4) {
+            const int cc = cg + 16 * c4;
+            const double* col = Wn + (long long)(s0 + cc) * N + J * kSolveBlock;
+#pragma unroll
+            for (int r4 = 0; r4 < kSolveBlock / kGJ; ++r4) {
+                const int ii = lane + r4 * kGJ;
+                lt[c4][r4] = (cc < nbk && ii < nbj) ? __ldcg(col + ii) : 0.0;
+            }
+        }
+        if (!wait_flag(flags + J, 1u, v.status, v.spin_limit)) return false;
+        if (tid < kSolveBlock) S.dep[tid] = tid < nbj ? __ldcg(out + J * kSolveBlock + tid) : 0.0;
+        __syncthreads();
+#pragma unroll
+        for (int c4 = 0; c4 < kSolveBlock / 16; ++c4) {
+            const int cc = cg + 16 * c4;
+            double acc = 0.0;
+#pragma unroll
+            for (int r4 = 0; r4 < kSolveBlock / kGJ; ++r4) acc = fma(lt[c4][r4], S.dep[lane + r4 * kGJ], acc);
+#pragma unroll
+            for (int w = kGJ / 2; w > 0; w >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, w, kGJ);
+            if (lane == 0) S.part[0][cc] = acc;
+        }
+        __syncthreads();
+        if (tid < kSolveBlock) S.rhs[tid] -= S.part[0][tid];
+    }
+    __syncthreads();
+    if (tid < kGJ) S.sol[(kSolveSub - 1) * kGJ + tid] = S.rhs[(kSolveSub - 1) * kGJ + tid];
+    __syncthreads();
+    const int sc = tid / kGJ, p = tid % kGJ;
+    for (int b = kSolveSub - 2; b >= 0; --b) {
+        double acc = 0.0;
+        for (int a = b + 1; a < kSolveSub; ++a) acc = fma(S.Ls[tri_pair(a, b)][p][sc], S.sol[a * kGJ + p], acc);
+#pragma unroll
+        for (int w = kGJ / 2; w > 0; w >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, w, kGJ);
+        if (p == 0) S.sol[b * kGJ + sc] = S.rhs[b * kGJ + sc] - acc;
+        __syncthreads();
+    }
+    if (tid < nbk) out[s0 + tid] = S.sol[tid];
+    tri_publish(flags + K);
+    __syncthreads();
+    return true;
+}
+
 // ---------------------------------------------------------------------------
 // Solve-phase tree sweeps (Algorithm 1's upward pass of the particular
 // fluxes and its downward pass of the interface unknowns), every tree height
@@ -1161,6 +1674,7 @@ __device__ __forceinline__ void prefetch_range_l2(const void* p, long long bytes
 // children into rgam, a grid barrier, then the dot products on contiguous
 // rgam (no dependent gathers inside them).
 __global__ void __launch_bounds__(256) tree_up_kernel(DevView v, TreeLevels L, unsigned int* counter) {
+    __shared__ TriSmem TS;
     const int tid = threadIdx.x, lane = tid & 31;
     const long long stride = (long long)gridDim.x * 256;
     const long long t0 = (long long)blockIdx.x * 256 + tid;
@@ -1175,6 +1689,22 @@ __global__ void __launch_bounds__(256) tree_up_kernel(DevView v, TreeLevels L, u
     for (int h = 0; h < L.height; ++h) {
         const int first = L.first[h], count = L.count[h], g2max = L.g2[h], mmax = L.m[h];
         if (count == 0) continue;                           // uniform over the grid
+        if (L.form[h]) {
+            // a root level in the factor form (no outer segments): y =
+            // Lt^-1 Q^T S rbar_gamma into fwd, block by block (left-looking)
+            const int nsb = (g2max + kSolveBlock - 1) / kSolveBlock;
+            unsigned int* fl = v.tri_flags;
+            for (long long t = t0; t < (long long)count * nsb; t += stride) fl[t] = 0u;
+            if (!grid_barrier(counter, round, v.status, v.spin_limit)) return;
+            for (int item = blockIdx.x; item < count * nsb; item += gridDim.x) {
+                const int K = item / count, q = item % count;
+                const MergeDesc D = v.merges[first + q];
+                if (K * kSolveBlock >= 2 * D.g) continue;                  // uniform per CTA
+                if (!tri_forward_item(v, D, K, fl + (long long)q * nsb, TS)) return;
+            }
+            if (h + 1 < L.height && !grid_barrier(counter, round, v.status, v.spin_limit)) return;
+            continue;
+        }
         for (long long t = t0; t < (long long)count * g2max; t += stride) {
             int q, k;
             udivmod(t, g2max, q, k);
@@ -1243,6 +1773,7 @@ __global__ void __launch_bounds__(256) tree_up_kernel(DevView v, TreeLevels L, u
 constexpr int kDownTerms = 8;
 __global__ void __launch_bounds__(256) tree_down_kernel(DevView v, TreeLevels L, double* scratch,
                                                         unsigned int* counter) {
+    __shared__ TriSmem TS;
     const int tid = threadIdx.x;
     const long long stride = (long long)gridDim.x * 256;
     const long long t0 = (long long)blockIdx.x * 256 + tid;
@@ -1250,6 +1781,38 @@ __global__ void __launch_bounds__(256) tree_down_kernel(DevView v, TreeLevels L,
     for (int h = L.height - 1; h >= 0; --h) {
         const int first = L.first[h], count = L.count[h], g2max = L.g2[h], mmax = L.m[h], nkc = L.nkc[h];
         if (count == 0) continue;                           // uniform over the grid
+        if (L.form[h]) {
+            // a root level in the factor form: x = Lt^-T P y (P: the inverse
+            // diagonal blocks of the factor, y from the up sweep) into rgam,
+            // block by block from the last, then lambda_gamma = -S Q x to the
+            // children
+            const int nsb = (g2max + kSolveBlock - 1) / kSolveBlock;
+            unsigned int* fl = v.tri_flags + v.tri_flag_n;
+            for (long long t = t0; t < (long long)count * nsb; t += stride) fl[t] = 0u;
+            if (!grid_barrier(counter, round, v.status, v.spin_limit)) return;
+            for (int item = blockIdx.x; item < count * nsb; item += gridDim.x) {
+                const int K = nsb - 1 - item / count, q = item % count;
+                const MergeDesc D = v.merges[first + q];
+                if (K * kSolveBlock >= 2 * D.g) continue;                  // uniform per CTA
+                if (!tri_backward_item(v, D, K, fl + (long long)q * nsb, TS)) return;
+            }
+            if (!grid_barrier(counter, round, v.status, v.spin_limit)) return;
+            const int gmax = g2max / 2;
+            for (long long t = t0; t < (long long)count * gmax; t += stride) {
+                int q, i;
+                udivmod(t, gmax, q, i);
+                const MergeDesc D = v.merges[first + q];
+                if (i >= D.g) continue;
+                const NodeRefs N = node_refs(v, D);
+                const double* x = v.rgam + 2LL * D.gamma_off;
+                const double xd = __ldcg(x + i), xs = __ldcg(x + D.g + i);
+                const double sc = kRsqrt2 / sqrt(gamma_D(v, D, i));
+                v.lam[D.r1_off + N.gpos1[i]] = sc * (xd - xs);
+                v.lam[D.r2_off + N.gpos2[i]] = -(sc * (xd + xs));
+            }
+            if (h > 0 && !grid_barrier(counter, round, v.status, v.spin_limit)) return;
+            continue;
+        }
         const int kc_len = L.kcl[h];
         const long long rows = (long long)count * nkc * g2max;
         // the rows, then the children's outer lambda (copied from the node),
@@ -1355,7 +1918,7 @@ size_t merge_scratch_doubles(int count, int max_g2, int max_m) {
 }
 
 // phase ids (include/mrcm.h)
-enum { kPhMergeSmall = 2, kPhGjSweep = 3, kPhMergeForm = 4, kPhMergeX = 5, kPhMergeR = 6 };
+enum { kPhMergeSmall = 2, kPhGjSweep = 3, kPhMergeForm = 4, kPhMergeX = 5, kPhMergeR = 6, kPhRootFactor = 13 };
 
 struct HookScope {
     const PhaseHook& h;
@@ -1381,8 +1944,9 @@ static cudaError_t launch_small(const DevView& v, int first, int count, int max_
 // CTA shape runs it, so the tuner may pick any of them.
 template <class F>
 static cudaError_t sweep_launch(const DevView& v, int first, int count, int max_g2, double* scratch, void* barrier,
-                                int sms, int per_sm, cudaStream_t s) {
+                                int sms, int per_sm, bool factor, cudaStream_t s) {
     cudaError_t e;
+    const void* kern = factor ? (const void*)ldl_sweep_kernel<F> : (const void*)gj_sweep_kernel<F>;
     // Default one CTA per SM (the padded dynamic shared memory keeps a
     // second one off): the CTAs that invert the next diagonal blocks, which
     // lie on the sequential chain of the sweep, then own their SM's FP64
@@ -1394,8 +1958,7 @@ static cudaError_t sweep_launch(const DevView& v, int first, int count, int max_
     if (per_sm >= 2) {
         dyn = std::max<size_t>((size_t)max_g2 * sizeof(double), 16);
         int fit = 0;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, gj_sweep_kernel<F>, 256, dyn)) != cudaSuccess)
-            return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, kern, 256, dyn)) != cudaSuccess) return e;
         if (fit < per_sm) {
             per_sm = fit >= 2 ? fit : 1;
             if (per_sm == 1) dyn = kSweepSmemPad;
@@ -1411,7 +1974,7 @@ static cudaError_t sweep_launch(const DevView& v, int first, int count, int max_
     int f = first, c = count, n = max_g2;
     F* scr = reinterpret_cast<F*>(scratch);
     void* args[] = {&vv, &f, &c, &n, &scr, &bar};
-    return cudaLaunchCooperativeKernel((const void*)gj_sweep_kernel<F>, dim3(grid), dim3(256), args, dyn, s);
+    return cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(256), args, dyn, s);
 }
 template <class F>
 static cudaError_t x_launch(const DevView& v, int first, int count, int max_g2, int max_m, int sms, int rows,
@@ -1448,7 +2011,15 @@ static cudaError_t device_sms(int* sms) {
 }
 
 template <class F>
-static cudaError_t launch_merge_build_t(const DevView& v, int first, int count, int max_g2, int max_m,
+static cudaError_t sweep_attributes() {
+    cudaError_t e = cudaFuncSetAttribute(gj_sweep_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kSweepSmemPad);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(ldl_sweep_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSweepSmemPad);
+}
+
+template <class F>
+static cudaError_t launch_merge_build_t(const DevView& v, int first, int count, int max_g2, int max_m, bool factor,
                                         const MergeTune& tune, double* scratch, void* barrier, cudaStream_t s,
                                         int* launches, const PhaseHook& hook) {
     if (count == 0) return cudaSuccess;
@@ -1458,18 +2029,17 @@ static cudaError_t launch_merge_build_t(const DevView& v, int first, int count, 
     // captured build makes them once)
     int sms = 0;
     if ((e = device_sms(&sms)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(gj_sweep_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  kSweepSmemPad)) != cudaSuccess)
-        return e;
+    if ((e = sweep_attributes<F>()) != cudaSuccess) return e;
     if (!merge_level_blocked(count, max_g2, max_m)) {
         HookScope hs(hook, kPhMergeSmall);
         e = launch_small<F>(v, first, count, max_g2, max_m, s);
         ++*launches;
         return e;
     }
+    factor = factor && max_m == 0;
     {
-        HookScope hs(hook, kPhGjSweep);
-        e = sweep_launch<F>(v, first, count, max_g2, scratch, barrier, sms, tune.sweep_per_sm, s);
+        HookScope hs(hook, factor ? kPhRootFactor : kPhGjSweep);
+        e = sweep_launch<F>(v, first, count, max_g2, scratch, barrier, sms, tune.sweep_per_sm, factor, s);
         ++*launches;
         if (e != cudaSuccess) return e;
     }
@@ -1489,12 +2059,13 @@ static cudaError_t launch_merge_build_t(const DevView& v, int first, int count, 
 }
 
 cudaError_t launch_merge_build(const DevView& v, int first, int count, int max_g2, int max_m, bool fp32,
-                               const MergeTune& tune, double* scratch, void* barrier, cudaStream_t s, int* launches,
-                               const PhaseHook& hook) {
+                               bool factor, const MergeTune& tune, double* scratch, void* barrier, cudaStream_t s,
+                               int* launches, const PhaseHook& hook) {
     if (fp32)
-        return launch_merge_build_t<float>(v, first, count, max_g2, max_m, tune, scratch, barrier, s, launches,
-                                           hook);
-    return launch_merge_build_t<double>(v, first, count, max_g2, max_m, tune, scratch, barrier, s, launches, hook);
+        return launch_merge_build_t<float>(v, first, count, max_g2, max_m, factor, tune, scratch, barrier, s,
+                                           launches, hook);
+    return launch_merge_build_t<double>(v, first, count, max_g2, max_m, factor, tune, scratch, barrier, s, launches,
+                                        hook);
 }
 
 // Times fn (one launch, already valid to repeat) `reps` times on s with
@@ -1516,16 +2087,15 @@ static cudaError_t best_time(cudaStream_t s, int reps, cudaEvent_t e0, cudaEvent
 }
 
 template <class F>
-static cudaError_t tune_level_t(const DevView& v, int first, int count, int max_g2, int max_m, double* scratch,
-                                void* barrier, cudaStream_t s, int reps, MergeTune* out) {
+static cudaError_t tune_level_t(const DevView& v, int first, int count, int max_g2, int max_m, bool factor,
+                                double* scratch, void* barrier, cudaStream_t s, int reps, MergeTune* out) {
     *out = MergeTune{};
     if (count == 0 || !merge_level_blocked(count, max_g2, max_m)) return cudaSuccess;
     int sms = 0;
     cudaError_t e;
     if ((e = device_sms(&sms)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(gj_sweep_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  kSweepSmemPad)) != cudaSuccess)
-        return e;
+    if ((e = sweep_attributes<F>()) != cudaSuccess) return e;
+    factor = factor && max_m == 0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if ((e = cudaEventCreate(&e0)) != cudaSuccess) return e;
     if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
@@ -1536,7 +2106,7 @@ static cudaError_t tune_level_t(const DevView& v, int first, int count, int max_
     for (int per_sm : {1, 2, 3}) {
         float t = 0.f;
         e = best_time(s, reps, e0, e1, [&] {
-            return sweep_launch<F>(v, first, count, max_g2, scratch, barrier, sms, per_sm, s);
+            return sweep_launch<F>(v, first, count, max_g2, scratch, barrier, sms, per_sm, factor, s);
         }, &t);
         if (e != cudaSuccess) break;
         if (t < best) { best = t; out->sweep_per_sm = per_sm; }
@@ -1565,10 +2135,10 @@ static cudaError_t tune_level_t(const DevView& v, int first, int count, int max_
     return e;
 }
 
-cudaError_t tune_merge_level(const DevView& v, int first, int count, int max_g2, int max_m, bool fp32,
+cudaError_t tune_merge_level(const DevView& v, int first, int count, int max_g2, int max_m, bool fp32, bool factor,
                              double* scratch, void* barrier, cudaStream_t s, int reps, MergeTune* out) {
-    if (fp32) return tune_level_t<float>(v, first, count, max_g2, max_m, scratch, barrier, s, reps, out);
-    return tune_level_t<double>(v, first, count, max_g2, max_m, scratch, barrier, s, reps, out);
+    if (fp32) return tune_level_t<float>(v, first, count, max_g2, max_m, factor, scratch, barrier, s, reps, out);
+    return tune_level_t<double>(v, first, count, max_g2, max_m, factor, scratch, barrier, s, reps, out);
 }
 
 cudaError_t tree_grid(int* grid) {

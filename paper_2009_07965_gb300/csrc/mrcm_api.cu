@@ -67,6 +67,11 @@ struct Plan {
     double model_build = 0, model_sweep = 0;
     double phase_build[MRCM_PHASE_COUNT] = {};   // per build call
     double phase_pass[MRCM_PHASE_COUNT] = {};    // per solve pass
+    // the above count root levels in the inverse form; where a root level
+    // takes the factor form these differences are added: [0] every root
+    // level (MRCM_ROOT_FACTOR), [1] the levels MRCM_ROOT_AUTO factors
+    double root_build[2][MRCM_PHASE_COUNT] = {}, root_pass[2][MRCM_PHASE_COUNT] = {};
+    double root_merge[2] = {}, root_solve[2] = {}, root_model_sweep[2] = {};
     double residual_flops = 0, finish_flops = 0;
 };
 
@@ -401,6 +406,23 @@ int make_plan(Plan& P) {
             P.merge_flops += (long long)(sym - node_inv_flops[q]);
             P.model_sweep += 2.0 / 3.0 * N * N * N;
             P.phase_build[MRCM_PHASE_GJ_SWEEP] += sym;
+            if (P.level_max_m[h - 1] == 0) {
+                // factor form of a root level: the rank-one count of the
+                // trailing updates, N (N^2 - 1) / 3; solve passes: the
+                // forward sweep (N^2), the inverse diagonal blocks (2 kGJ N)
+                // and the backward sweep (N^2) instead of the product (2 N^2)
+                const double fac = N * (N * N - 1.0) / 3.0;
+                for (int a = 0; a < 2; ++a) {
+                    if (a == 1 && P.level_max_g2[h - 1] < kRootFactorMinG2) continue;
+                    P.root_build[a][MRCM_PHASE_GJ_SWEEP] -= sym;
+                    P.root_build[a][MRCM_PHASE_ROOT_FACTOR] += fac;
+                    P.root_merge[a] += fac - sym;
+                    P.root_model_sweep[a] -= 2.0 / 3.0 * N * N * N;
+                    P.root_pass[a][MRCM_PHASE_TREE_UP] += N * N;
+                    P.root_pass[a][MRCM_PHASE_TREE_DOWN] += N * N + 2.0 * kMergeBlock * N - 2.0 * N * N;
+                    P.root_solve[a] += 2.0 * kMergeBlock * N;
+                }
+            }
             P.phase_build[MRCM_PHASE_MERGE_X] += 2.0 * N * gd * md;
             P.phase_build[MRCM_PHASE_MERGE_R] += md * (md + 1.0) * gd;
         }
@@ -436,6 +458,7 @@ struct mrcm_ctx {
     Plan P;
     int precision = MRCM_FP64;
     int mixed_split = kMixedSplitDefault;
+    int root_form = MRCM_ROOT_AUTO;       // mrcm_set_root_form
     std::vector<MergeTune> tune;          // per tree height (mrcm_autotune); empty: heuristics
     cudaStream_t stream = nullptr;
     int device = 0;
@@ -667,18 +690,24 @@ static void fill_plan_inputs(Plan& P, int count, const mrcm_grid* g, const int s
     P.gx = seg[0]; P.gy = seg[1];
 }
 
-static int plan_value(const Plan& P, int what, long long* value) {
+// which set of root-level flop differences applies to a root form: -1 none
+static int root_set(int form) { return form == MRCM_ROOT_FACTOR ? 0 : (form == MRCM_ROOT_AUTO ? 1 : -1); }
+
+static int plan_value(const Plan& P, int what, long long* value, int form = MRCM_ROOT_AUTO) {
+    const int a = root_set(form);
+    const double f = a >= 0 ? 1.0 : 0.0;
+    const int ai = a >= 0 ? a : 0;
     switch (what) {
         case MRCM_Q_LEAVES: *value = P.nleaf; break;
         case MRCM_Q_SEGMENTS: *value = P.nseg; break;
         case MRCM_Q_LEVELS: *value = P.height; break;
         case MRCM_Q_NODES: *value = (long long)P.nodes.size(); break;
         case MRCM_Q_MAX_GAMMA: *value = P.max_g2; break;
-        case MRCM_Q_BUILD_FLOPS: *value = P.leaf_flops + P.merge_flops; break;
-        case MRCM_Q_SOLVE_FLOPS: *value = P.solve_flops; break;  // one solve pass
+        case MRCM_Q_BUILD_FLOPS: *value = P.leaf_flops + P.merge_flops + (long long)(f * P.root_merge[ai]); break;
+        case MRCM_Q_SOLVE_FLOPS: *value = P.solve_flops + (long long)(f * P.root_solve[ai]); break;  // one pass
         case MRCM_Q_LEAF_FLOPS: *value = P.leaf_flops; break;
         case MRCM_Q_MODEL_BUILD_FLOPS: *value = (long long)P.model_build; break;
-        case MRCM_Q_MODEL_SWEEP_FLOPS: *value = (long long)P.model_sweep; break;
+        case MRCM_Q_MODEL_SWEEP_FLOPS: *value = (long long)(P.model_sweep + f * P.root_model_sweep[ai]); break;
         case MRCM_Q_GRIDS: *value = (long long)P.grids.size(); break;
         case MRCM_Q_CELLS: *value = P.ncell; break;
         default: return MRCM_ERR_INVALID_ARG;
@@ -695,6 +724,20 @@ int mrcm_plan_query(const mrcm_grid* g, const int sub_cells[3], const int seg_ce
     fill_plan_inputs(P, 1, g, sub_cells, seg_cells, 1.0, bc_type);
     TRY(make_plan(P));
     return plan_value(P, what, value);
+}
+
+// Whether height h (1-based) keeps the factor of its interface systems: a
+// blocked level whose nodes have no outer segments (roots), in the factor
+// form of the context.
+static bool level_factor(const mrcm_ctx* c, int h) {
+    const Plan& P = c->P;
+    if (c->root_form == MRCM_ROOT_INVERSE || P.level_max_m[h - 1] != 0 ||
+        !merge_level_blocked(P.level_count[h - 1], P.level_max_g2[h - 1], P.level_max_m[h - 1]))
+        return false;
+    return c->root_form == MRCM_ROOT_FACTOR || P.level_max_g2[h - 1] >= kRootFactorMinG2;
+}
+static void set_tree_forms(mrcm_ctx* c) {
+    for (int h = 1; h <= c->P.height; ++h) c->tree.form[h - 1] = level_factor(c, h) ? 1 : 0;
 }
 
 static int setup_impl(mrcm_ctx* c, int count, const mrcm_grid* g, const double* K_dev, const int sub[3],
@@ -790,6 +833,17 @@ static int setup_impl(mrcm_ctx* c, int count, const mrcm_grid* g, const double* 
             T.m[h - 1] = P.level_max_m[h - 1];
         }
         TRY(dev_alloc(c, &v.rgam, std::max<long long>(2 * (long long)P.gamma_segs.size(), 1)));
+        TRY(dev_alloc(c, &v.fwd, std::max<long long>(2 * (long long)P.gamma_segs.size(), 1)));
+        // flags of the triangular sweeps: per node of a level that may take
+        // the factor form, one per solve block
+        long long nflag = 1;
+        for (int h = 1; h <= P.height; ++h)
+            if (P.level_max_m[h - 1] == 0)
+                nflag = std::max(nflag, (long long)P.level_count[h - 1] *
+                                            ((P.level_max_g2[h - 1] + kTriBlock - 1) / kTriBlock));
+        v.tri_flag_n = nflag;
+        TRY(dev_alloc(c, &v.tri_flags, 2 * nflag));
+        set_tree_forms(c);
         TRYC(tree_grid(&c->tree_grid));
         const long long need = tree_plan_chunks(T, c->tree_grid);
         TRY(dev_alloc(c, &c->tree_scratch, std::max(need, 1LL)));
@@ -869,8 +923,8 @@ static int enqueue_build(mrcm_ctx* c, int& launches, bool merges_only = false) {
             const bool fp32 = v.mixed && P.level_max_g2[h - 1] <= c->mixed_split;
             const MergeTune tune = c->tune.empty() ? MergeTune{} : c->tune[h - 1];
             TRYC(launch_merge_build(v, P.level_first[h - 1], P.level_count[h - 1], P.level_max_g2[h - 1],
-                                    P.level_max_m[h - 1], fp32, tune, c->gj_scratch, c->gj_barrier, s, &launches,
-                                    hook));
+                                    P.level_max_m[h - 1], fp32, level_factor(c, h), tune, c->gj_scratch,
+                                    c->gj_barrier, s, &launches, hook));
         }
     }
     return MRCM_OK;
@@ -981,7 +1035,9 @@ int mrcm_solve(mrcm_ctx* c, const double* q_dev, const double* bc_val_dev, doubl
     if (!c->built) return MRCM_ERR_NOT_BUILT;
     if (!q_dev || !bc_val_dev || !p_dev || !Fx_dev || !Fy_dev || Fz_dev) return MRCM_ERR_INVALID_ARG;
     // keep the build's event pairs, reuse the solve's
-    while (c->ev_used > 0 && c->ev_phase[c->ev_used - 1] >= MRCM_PHASE_LEAF_PART) --c->ev_used;
+    while (c->ev_used > 0 && c->ev_phase[c->ev_used - 1] >= MRCM_PHASE_LEAF_PART &&
+           c->ev_phase[c->ev_used - 1] <= MRCM_PHASE_FINISH)
+        --c->ev_used;
     const int ev_begin = c->ev_used;
     const void* key[8] = {q_dev, bc_val_dev, p_dev, Fx_dev, Fy_dev, iface_dev,
                           reinterpret_cast<const void*>((long long)(c->refine_steps * 2 + c->refine_check) + 1),
@@ -1023,8 +1079,8 @@ int mrcm_autotune(mrcm_ctx* c, int reps) {
     for (int h = 1; h <= P.height; ++h) {
         const bool fp32 = c->v.mixed && P.level_max_g2[h - 1] <= c->mixed_split;
         TRYC(tune_merge_level(c->v, P.level_first[h - 1], P.level_count[h - 1], P.level_max_g2[h - 1],
-                              P.level_max_m[h - 1], fp32, c->gj_scratch, c->gj_barrier, c->stream, reps,
-                              &tune[h - 1]));
+                              P.level_max_m[h - 1], fp32, level_factor(c, h), c->gj_scratch, c->gj_barrier,
+                              c->stream, reps, &tune[h - 1]));
     }
     TRY(read_status(c));
     c->tune = tune;
@@ -1054,6 +1110,24 @@ int mrcm_set_mixed_split(mrcm_ctx* c, int max_g2_fp32) {
     TRYC(cudaStreamSynchronize(c->stream));
     if (c->build_exec) cudaGraphExecDestroy(c->build_exec);
     c->build_exec = nullptr;
+    return MRCM_OK;
+}
+
+int mrcm_set_root_form(mrcm_ctx* c, int form) {
+    if (!c || (form != MRCM_ROOT_FACTOR && form != MRCM_ROOT_INVERSE && form != MRCM_ROOT_AUTO))
+        return MRCM_ERR_INVALID_ARG;
+    if (form == c->root_form) return MRCM_OK;
+    TRYC(cudaStreamSynchronize(c->stream));
+    c->root_form = form;
+    c->built = false;
+    c->solved = false;
+    set_tree_forms(c);
+    // both captured graphs hold the old form (the build's launches, the
+    // solve sweeps' level table)
+    if (c->build_exec) cudaGraphExecDestroy(c->build_exec);
+    if (c->solve_exec) cudaGraphExecDestroy(c->solve_exec);
+    c->build_exec = c->solve_exec = nullptr;
+    c->solve_key[0] = nullptr;
     return MRCM_OK;
 }
 
@@ -1203,7 +1277,7 @@ int mrcm_query(const mrcm_ctx* c, int what, long long* value) {
         case MRCM_Q_KERNEL_LAUNCHES_BUILD: *value = c->launches_build; return MRCM_OK;
         case MRCM_Q_KERNEL_LAUNCHES_SOLVE: *value = c->launches_solve; return MRCM_OK;
         case MRCM_Q_GRAPH_REPLAYS: *value = c->graph_replays; return MRCM_OK;
-        default: return plan_value(c->P, what, value);
+        default: return plan_value(c->P, what, value, c->root_form);
     }
 }
 
@@ -1315,8 +1389,12 @@ int mrcm_group_times(mrcm_ctx* c, int* phase, double* ms, int cap) {
 int mrcm_phase_flops(const mrcm_ctx* c, double* flops) {
     if (!c || !flops) return MRCM_ERR_INVALID_ARG;
     const Plan& P = c->P;
-    const double passes = 1.0 + c->refine_steps;
-    for (int p = 0; p < MRCM_PHASE_COUNT; ++p) flops[p] = P.phase_build[p] + passes * P.phase_pass[p];
+    const int a = root_set(c->root_form);
+    const double passes = 1.0 + c->refine_steps, f = a >= 0 ? 1.0 : 0.0;
+    const int ai = a >= 0 ? a : 0;
+    for (int p = 0; p < MRCM_PHASE_COUNT; ++p)
+        flops[p] = P.phase_build[p] + f * P.root_build[ai][p] +
+                   passes * (P.phase_pass[p] + f * P.root_pass[ai][p]);
     flops[MRCM_PHASE_RESIDUAL] = (c->refine_steps + (c->refine_check ? 1 : 0)) * P.residual_flops;
     flops[MRCM_PHASE_FINISH] = P.finish_flops;
     return MRCM_OK;

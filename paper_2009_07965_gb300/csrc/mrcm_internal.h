@@ -70,7 +70,8 @@ struct MergeDesc {
     int pinned;        // 1: root of an all-Neumann problem (P of gamma[0] = 0)
     long long R_off, R1_off, R2_off;   // node / children R
     long long r_off, r1_off, r2_off;   // node / children rbar (and lambda)
-    long long W_off;   // 2g x 2g inverse W = M^-1 (column-major)
+    long long W_off;   // 2g x 2g inverse W = M^-1 (column-major), or the factor of
+                       // a factor-form root level
     long long X_off;   // 2g x m coefficients X = -M^-1 C (column-major)
 };
 
@@ -120,8 +121,15 @@ struct DevView {
     double* rgam;       // per merge, rbar of its 2g gamma unknowns gathered from
                         // the children (at 2 * gamma_off), written by the up sweep
     double* lam;        // node Robin data (top-down)
+    double* fwd;        // per merge of a factor-form root level (2g at 2 * gamma_off):
+                        // y = Lt^-1 rhat of the up sweep
+    unsigned int* tri_flags;   // block flags of the factor form's triangular sweeps:
+    long long tri_flag_n;      // tri_flag_n for the forward sweep, then as many backward
     double* X;
-    double* W;          // explicit inverses of the interface matrices (W_off layout)
+    double* W;          // per merge (W_off layout): the explicit inverse of the
+                        // interface matrix, or for a factor-form root level its
+                        // block LDL^T factor (Lt below the diagonal blocks, their
+                        // inverses in them; on and below the diagonal)
     float* W32;         // FP32 work array of the mixed form's blocked levels (W_off layout)
     double* segP;       // refined interface unknowns P_t, U_t (high parts)
     double* segU;
@@ -320,19 +328,26 @@ struct MergeTune {
     int sweep_per_sm = 0, x_rows = 0, r_tile = 0;
 };
 // fp32: the mixed form's FP32 arithmetic for this level (T of the blocked
-// sweep in v.W32; W, X and R stored in double either way)
+// sweep in v.W32; W, X and R stored in double either way).  factor: a
+// blocked level without outer segments (a root level) keeps the block
+// LDL^T factor of its interface system instead of the inverse.
 cudaError_t launch_merge_build(const DevView& v, int first, int count, int max_g2, int max_m, bool fp32,
-                               const MergeTune& tune, double* scratch, void* barrier, cudaStream_t s, int* launches,
-                               const PhaseHook& hook);
+                               bool factor, const MergeTune& tune, double* scratch, void* barrier, cudaStream_t s,
+                               int* launches, const PhaseHook& hook);
 // Times every launch shape of one blocked level (its children's maps must
 // be built: the launches are repeated and recompute the same numbers) and
 // returns the fastest per launch; `reps` timed runs each.
-cudaError_t tune_merge_level(const DevView& v, int first, int count, int max_g2, int max_m, bool fp32,
+cudaError_t tune_merge_level(const DevView& v, int first, int count, int max_g2, int max_m, bool fp32, bool factor,
                              double* scratch, void* barrier, cudaStream_t s, int reps, MergeTune* out);
 constexpr size_t kMergeBarrierBytes = 64;
 bool merge_level_blocked(int count, int max_g2, int max_m);
 size_t merge_scratch_doubles(int count, int max_g2, int max_m);
 constexpr int kMergeBlock = 16;      // block size of the blocked Gauss-Jordan sweep (flop model)
+constexpr int kTriBlock = 64;        // solve blocks of the factor form's triangular sweeps
+// MRCM_ROOT_AUTO factors root systems from this 2g on: below it the root's
+// elimination is bound by its sequential chain of pivot blocks (the same
+// length in both forms), and the inverse's solve passes are the shorter.
+constexpr int kRootFactorMinG2 = 1024;
 
 // The merge levels of the tree for the fused up / down sweeps of the solve
 // (passed by value as a kernel argument; index h - 1 for height h).
@@ -342,6 +357,7 @@ struct TreeLevels {
     int first[kMaxTreeLevels], count[kMaxTreeLevels], g2[kMaxTreeLevels], m[kMaxTreeLevels];
     int nkc[kMaxTreeLevels];   // down sweep: term chunks per row, a power of two (1: no partial sums)
     int kcl[kMaxTreeLevels];   // down sweep: terms per chunk (a multiple of 8)
+    int form[kMaxTreeLevels];  // 1: a root level in the factor form (block triangular sweeps)
     // extents of the static data the sweeps read (prefetched into L2)
     long long x_len, w_len;    // doubles of X and W
     long long n_merges, map_len;
