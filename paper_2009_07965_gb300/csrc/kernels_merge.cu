@@ -69,6 +69,7 @@ namespace {
 constexpr int kGJ = kMergeBlock; // block size of the blocked Gauss-Jordan sweep
 constexpr int kGJTile = 32;       // output tile of the blocked update (kGJTile^2 per CTA)
 constexpr int kSmallMax = 32;     // largest 2g merged by the per-node register kernel
+constexpr int kNodeMax = 128;     // largest 2g inverted by the per-node kernel of the blocked path
 constexpr int kRTile = 32;       // R update tile
 constexpr double kTinyPivot = 1e-14;   // pivots of the scaled form are O(1)
 constexpr double kRsqrt2 = 0.70710678118654752440;   // 1 / sqrt(2), the sum / difference transform
@@ -997,6 +998,98 @@ __device__ __forceinline__ void tri_rc(int r, int& a, int& b) {
     while ((a + 1) * (a + 2) / 2 <= r) ++a;
     while (a * (a + 1) / 2 > r) --a;
     b = r - a * (a + 1) / 2;
+}
+
+// ---------------------------------------------------------------------------
+// Per-node inversion for levels of many mid-sized systems (32 < 2g <= 128,
+// at least as many nodes as SMs): one CTA per node holds the lower triangle
+// of T in shared memory (row-packed) and runs the Gauss-Jordan elimination
+// of merge_small on it, a rank-one step per pivot (warp 0 forms the pivot's
+// reciprocal, the pivot test and the scaled pivot row and column; every
+// thread then updates its kept entries in place), then back-forms W into
+// global memory.  No grid barriers, no global round trips of T: at these
+// sizes the cooperative blocked sweep spends most of its time on its
+// per-step synchronisation.  X and R follow with merge_x / merge_rupdate.
+// NMAX: largest 2g of the instantiation; F: the arithmetic (double, or
+// float for the mixed form's FP32 levels; W is stored in double).
+template <int NMAX>
+struct NodeTri {
+    static constexpr int kTri = NMAX * (NMAX + 1) / 2;
+    static constexpr int kPer = (kTri + 255) / 256;    // kept entries per thread
+};
+template <int NMAX, class F>
+__global__ void __launch_bounds__(256) gj_node_kernel(DevView v, int first) {
+    constexpr int kPer = NodeTri<NMAX>::kPer;
+    extern __shared__ __align__(16) unsigned char nsm_raw[];
+    F* T = reinterpret_cast<F*>(nsm_raw);                               // row-packed lower triangle
+    __shared__ F xcol[NMAX], vrow[NMAX];
+    __shared__ double scl[NMAX];                                        // D^1/2 (g), D^-1/2 (g)
+    __shared__ double red[8];
+    __shared__ int s_bad;
+    const MergeDesc D = v.merges[first + blockIdx.x];
+    const NodeRefs Nr = node_refs(v, D);
+    const int g = D.g, n = 2 * g, ntri = n * (n + 1) / 2;
+    const int tid = threadIdx.x;
+    if (tid == 0) s_bad = 0;
+    const double sum = stage_gamma_scalings(v, D, scl, red);
+    const double inv_sum = (D.pinned && sum > 0.0) ? 1.0 / sum : 0.0;
+    // the thread's entries (r, c), r >= c, packed as r << 16 | c
+    int rc[kPer];
+#pragma unroll
+    for (int e = 0; e < kPer; ++e) {
+        const int idx = tid + e * 256;
+        int r = 0, c = 0;
+        if (idx < ntri) tri_rc(idx, r, c);
+        rc[e] = (r << 16) | c;
+    }
+#pragma unroll
+    for (int e = 0; e < kPer; ++e) {
+        const int idx = tid + e * 256;
+        if (idx >= ntri) break;
+        const int r = rc[e] >> 16, c = rc[e] & 0xffff;
+        const int i = r < g ? r : r - g, j = c < g ? c : c - g;
+        T[idx] = (F)t_entry(Nr, r, c, scl[g + i], scl[g + j], scl[i], scl[j], inv_sum);
+    }
+    // Gauss-Jordan without pivoting (d rows first: positive pivots, then
+    // negative); kept entries r >= c; after step k an entry of an eliminated
+    // and a remaining index is antisymmetric: a_rk = -T(k, r) for r < k.
+    for (int k = 0; k < n; ++k) {
+        __syncthreads();
+        if (tid < 32) {
+            const F p = T[k * (k + 1) / 2 + k];
+            const F rp = rcp_nr(p);
+            for (int c = tid; c < n; c += 32) {
+                // a_kc (row k) and -a_ck (column k) from the kept triangle
+                const F akc = c == k ? (F)1 : (c < k ? T[k * (k + 1) / 2 + c] : T[c * (c + 1) / 2 + k]);
+                vrow[c] = akc * rp;
+                xcol[c] = c == k ? (F)1 : (c > k ? neg_bits(T[c * (c + 1) / 2 + k]) : T[k * (k + 1) / 2 + c]);
+            }
+            if (tid == 0 && !pivot_ok_bits(p, k < g)) s_bad = 1;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < kPer; ++e) {
+            const int idx = tid + e * 256;
+            if (idx >= ntri) break;
+            const int r = rc[e] >> 16, c = rc[e] & 0xffff;
+            const F y = (r == k || c == k) ? (F)0 : T[idx];
+            T[idx] = fma(xcol[r], vrow[c], y);
+        }
+    }
+    __syncthreads();
+    if (tid == 0 && s_bad) atomicOr(v.status, kStatusSingular);
+    // W = D^-1/2 Q T^-1 Q^T D^-1/2, column-major, from the symmetric T^-1
+    double* Wg = v.W + D.W_off;
+    auto tinv = [&](int r, int c) -> F { return r >= c ? T[r * (r + 1) / 2 + c] : T[c * (c + 1) / 2 + r]; };
+    for (int idx = tid; idx < g * g; idx += 256) {
+        const int i = idx % g, j = idx / g;
+        const F zdd = tinv(i, j), zds = tinv(i, g + j), zsd = tinv(g + i, j), zss = tinv(g + i, g + j);
+        const F sc = (F)(0.5 * scl[g + i] * scl[g + j]);
+        Wg[(long long)j * n + i] = (double)((zdd - zds - zsd + zss) * sc);
+        Wg[(long long)(g + j) * n + i] = (double)((zss + zsd - zds - zdd) * sc);
+        Wg[(long long)j * n + g + i] = (double)((zss + zds - zsd - zdd) * sc);
+        Wg[(long long)(g + j) * n + g + i] = (double)((zdd + zds + zsd + zss) * sc);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1976,6 +2069,29 @@ static cudaError_t sweep_launch(const DevView& v, int first, int count, int max_
     void* args[] = {&vv, &f, &c, &n, &scr, &bar};
     return cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(256), args, dyn, s);
 }
+// A blocked level of many mid-sized systems takes the per-node inversion
+// (gj_node_kernel): one CTA per node keeps every SM busy without the
+// sweep's per-step grid barriers.  A fixed rule (not a tuning choice, so
+// that tuned launch shapes keep the bits of the result).
+static bool node_level(int count, int max_g2, int sms) { return max_g2 <= kNodeMax && count >= sms; }
+template <class F>
+static cudaError_t node_launch(const DevView& v, int first, int count, int max_g2, cudaStream_t s) {
+    cudaError_t e;
+    if (max_g2 <= 64) {
+        const size_t sm = sizeof(F) * NodeTri<64>::kTri;
+        if ((e = cudaFuncSetAttribute(gj_node_kernel<64, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) !=
+            cudaSuccess)
+            return e;
+        gj_node_kernel<64, F><<<count, 256, sm, s>>>(v, first);
+    } else {
+        const size_t sm = sizeof(F) * NodeTri<kNodeMax>::kTri;
+        if ((e = cudaFuncSetAttribute(gj_node_kernel<kNodeMax, F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)sm)) != cudaSuccess)
+            return e;
+        gj_node_kernel<kNodeMax, F><<<count, 256, sm, s>>>(v, first);
+    }
+    return cudaGetLastError();
+}
 template <class F>
 static cudaError_t x_launch(const DevView& v, int first, int count, int max_g2, int max_m, int sms, int rows,
                             cudaStream_t s) {
@@ -2039,7 +2155,10 @@ static cudaError_t launch_merge_build_t(const DevView& v, int first, int count, 
     factor = factor && max_m == 0;
     {
         HookScope hs(hook, factor ? kPhRootFactor : kPhGjSweep);
-        e = sweep_launch<F>(v, first, count, max_g2, scratch, barrier, sms, tune.sweep_per_sm, factor, s);
+        if (!factor && node_level(count, max_g2, sms))
+            e = node_launch<F>(v, first, count, max_g2, s);
+        else
+            e = sweep_launch<F>(v, first, count, max_g2, scratch, barrier, sms, tune.sweep_per_sm, factor, s);
         ++*launches;
         if (e != cudaSuccess) return e;
     }
@@ -2104,6 +2223,7 @@ static cudaError_t tune_level_t(const DevView& v, int first, int count, int max_
     }
     float best = 1e30f;
     for (int per_sm : {1, 2, 3}) {
+        if (!factor && node_level(count, max_g2, sms)) break;        // the per-node kernel: no shape to pick
         float t = 0.f;
         e = best_time(s, reps, e0, e1, [&] {
             return sweep_launch<F>(v, first, count, max_g2, scratch, barrier, sms, per_sm, factor, s);
