@@ -342,7 +342,7 @@ struct LeafSolveSmem {
 
 // Depth of the register ring that prefetches the band multipliers of the
 // sweeps (rows streamed from HBM ahead of the sequential elimination chain).
-constexpr int kSweepAhead = 8;
+constexpr int kSweepAhead = 16;
 
 // Body of the particular solve for one leaf; NF, WF > 0 fix the row count
 // and the band width at compile time (the full kMaxLeafSide^2 leaf: the
@@ -382,21 +382,33 @@ __device__ __forceinline__ void leaf_particular_body(const DevView& v, const dou
     }
     for (int k = t; k < n; k += kLeafThreads) zb[k] = S.y[k];
     // y = D^-1 zbar ; rbar = Z^T y  (= B^T A^-1 bbar): the 16 lanes share
-    // every column of Z (consecutive rows, coalesced) and reduce by shuffles
-    for (int k = t; k < n; k += kLeafThreads) S.y[k] *= (double)Dg[k];
-    __syncwarp(mask);
+    // every column of Z (consecutive rows, coalesced) and reduce by shuffles;
+    // the lane's y stay in registers and all of its kRows loads of a column
+    // are in flight together
+    constexpr int kRows = kMaxLeafSide * kMaxLeafSide / kLeafThreads;
+    double yv[kRows];
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+        const int k = t + r * kLeafThreads;
+        yv[r] = k < n ? S.y[k] * (double)Dg[k] : 0.0;
+    }
     double* rb = v.rbar + L.r_off;
     for (int s = 0; s < m; ++s) {
         const TS* zc = Zg + (long long)s * n;
-        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-        int k = t;
-        for (; k + 3 * kLeafThreads < n; k += 4 * kLeafThreads) {
-            a0 = fma((double)zc[k], S.y[k], a0);
-            a1 = fma((double)zc[k + kLeafThreads], S.y[k + kLeafThreads], a1);
-            a2 = fma((double)zc[k + 2 * kLeafThreads], S.y[k + 2 * kLeafThreads], a2);
-            a3 = fma((double)zc[k + 3 * kLeafThreads], S.y[k + 3 * kLeafThreads], a3);
+        double zv[kRows];
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) {
+            const int k = t + r * kLeafThreads;
+            zv[r] = k < n ? (double)zc[k] : 0.0;
         }
-        for (; k < n; k += kLeafThreads) a0 = fma((double)zc[k], S.y[k], a0);
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+#pragma unroll
+        for (int r = 0; r < kRows; r += 4) {
+            a0 = fma(zv[r], yv[r], a0);
+            a1 = fma(zv[r + 1], yv[r + 1], a1);
+            a2 = fma(zv[r + 2], yv[r + 2], a2);
+            a3 = fma(zv[r + 3], yv[r + 3], a3);
+        }
         double acc = (a0 + a1) + (a2 + a3);
 #pragma unroll
         for (int o = kLeafThreads / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(mask, acc, o);
