@@ -769,6 +769,19 @@ __device__ bool grid_barrier(unsigned int* counter, unsigned int& round, int* st
     return s_ok != 0;
 }
 
+// Next item of a dynamically distributed loop: thread 0 takes a ticket from
+// the launch's work counter (work; zeroed with the barrier counter before
+// the launch) and the CTA reads it.  The tickets of one loop run from base;
+// every CTA leaves the loop at its first ticket past the loop's items, so a
+// loop of n items consumes n + gridDim.x tickets (the next loop's base).
+__device__ __forceinline__ int grab_item(unsigned int* work, unsigned int base, int* s_item) {
+    if (threadIdx.x == 0) *s_item = (int)(atomicAdd(work, 1u) - base);
+    __syncthreads();
+    const int item = *s_item;
+    __syncthreads();
+    return item;
+}
+
 // Lower tile of rank r among the tiles of one node at a block step: the
 // tiles outside block row / column tk (the one holding K1), in row order,
 // then the tk ones.
@@ -872,9 +885,11 @@ template <class T>
 __global__ void __launch_bounds__(256) gj_sweep_kernel(DevView v, int first, int count, int nmax, T* scratch,
                                                        unsigned int* counter) {
     __shared__ GJSmem<T> S;
-    __shared__ int s_bad;
+    __shared__ int s_bad, s_item;
     __shared__ double red[8];
     extern __shared__ __align__(16) double scl[];           // 2g scalings (form / back-form)
+    unsigned int* work = counter + 1;                       // ticket counter of the tile loops
+    unsigned int wbase = 0;
     const int tiles = (nmax + kGJTile - 1) / kGJTile;
     const int nlower = tiles * (tiles + 1) / 2;
     const int nsteps = (nmax + kGJ - 1) / kGJ;
@@ -926,7 +941,16 @@ __global__ void __launch_bounds__(256) gj_sweep_kernel(DevView v, int first, int
     for (int step = 0; step < nsteps; ++step) {
         const int k0 = step * kGJ;
         const int tk = (k0 + kGJ) / kGJTile;                  // tile index of the next block
-        for (int item = blockIdx.x; item < count * (1 + nlower); item += gridDim.x) {
+        // the diagonal items first, then the tiles; with several items per
+        // CTA they are handed out as CTAs come free (a tile takes the same
+        // time on any CTA, and a fixed share per CTA left some SMs a tile
+        // behind the others at every step), with about one per CTA in a
+        // fixed order (a ticket would only add its latency)
+        const int nitems = count * (1 + nlower);
+        const bool dyn = nitems >= 2 * (int)gridDim.x;
+        for (int it0 = blockIdx.x;; it0 += gridDim.x) {
+            const int item = dyn ? grab_item(work, wbase, &s_item) : it0;
+            if (item >= nitems) break;
             if (item < count) {
                 const MergeDesc D = v.merges[first + item];
                 if (k0 + kGJ >= 2 * D.g) continue;
@@ -947,6 +971,7 @@ __global__ void __launch_bounds__(256) gj_sweep_kernel(DevView v, int first, int
             if (k0 >= 2 * D.g || ti * kGJTile >= 2 * D.g) continue;
             gj_step_item(v, D, q, ti, tj, step, scratch, nmax, S);
         }
+        if (dyn) wbase += (unsigned int)nitems + gridDim.x;
         // u of step + 1 for every index outside the next block, spread over
         // all CTAs once their tiles are done
         // (runs sized so that one round of items covers the level)
@@ -1298,9 +1323,11 @@ template <class T>
 __global__ void __launch_bounds__(256) ldl_sweep_kernel(DevView v, int first, int count, int nmax, T* scratch,
                                                         unsigned int* counter) {
     __shared__ GJSmem<T> S;
-    __shared__ int s_bad;
+    __shared__ int s_bad, s_item;
     __shared__ double red[8];
     extern __shared__ __align__(16) double scl[];           // 2g scalings (form)
+    unsigned int* work = counter + 1;                       // ticket counter of the tile loops
+    unsigned int wbase = 0;
     const int tiles = (nmax + kGJTile - 1) / kGJTile;
     const int nsteps = (nmax + kGJ - 1) / kGJ;
     const int tid = threadIdx.x;
@@ -1355,7 +1382,13 @@ __global__ void __launch_bounds__(256) ldl_sweep_kernel(DevView v, int first, in
         const int n = tiles - t0;
         const int ntri = n * (n + 1) / 2;
         const int tkc = col_first ? tiles - tk : 0;           // column-tk tiles per node
-        for (int item = blockIdx.x; item < count * (1 + ntri); item += gridDim.x) {
+        const int nitems = count * (1 + ntri);
+        // handed out as CTAs come free at every step: the trailing triangle
+        // shrinks, and its last steps gain most from the balance
+        const bool dyn = true;
+        for (int it0 = blockIdx.x;; it0 += gridDim.x) {
+            const int item = dyn ? grab_item(work, wbase, &s_item) : it0;
+            if (item >= nitems) break;
             if (item < count) {
                 const MergeDesc D = v.merges[first + item];
                 if (k0 + kGJ >= 2 * D.g) continue;
@@ -1372,6 +1405,7 @@ __global__ void __launch_bounds__(256) ldl_sweep_kernel(DevView v, int first, in
             if (k0 >= 2 * D.g || ti * kGJTile >= 2 * D.g) continue;
             ldl_step_item(v, D, q, ti, tj, step, scratch, nmax, S);
         }
+        if (dyn) wbase += (unsigned int)nitems + gridDim.x;
         // u of step + 1 past the next block, spread over all CTAs
         const int xs0 = k0 + 2 * kGJ;                         // first index past K1
         if (xs0 < nmax) {
@@ -2061,7 +2095,8 @@ static cudaError_t sweep_launch(const DevView& v, int first, int count, int max_
     const long long items = (long long)count * (1 + tiles * (tiles + 1) / 2);
     int grid = (int)std::min<long long>(items, (long long)sms * per_sm);
     grid = grid < 1 ? 1 : grid;
-    if ((e = cudaMemsetAsync(barrier, 0, sizeof(unsigned int), s)) != cudaSuccess) return e;
+    // the grid barrier's arrival counter and the tile loops' ticket counter
+    if ((e = cudaMemsetAsync(barrier, 0, 2 * sizeof(unsigned int), s)) != cudaSuccess) return e;
     unsigned int* bar = reinterpret_cast<unsigned int*>(barrier);
     DevView vv = v;
     int f = first, c = count, n = max_g2;
