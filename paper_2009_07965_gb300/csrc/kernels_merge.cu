@@ -145,17 +145,20 @@ template <> __device__ __forceinline__ float* gj_work<float>(const DevView& v) {
 // into W (column-major), then X = -W B and R = R_oo + B^T X with B = C
 // compacted to g x m (row k: gamma segment k of the child owning column j).
 // Shared layout: T[g2*g2], Wc[g2*g2], Bs[g*mstride], Xs[g2*mstride].
-constexpr int kSmallThreads = 256;
-constexpr int kSmallTri = (kSmallMax * (kSmallMax + 1) / 2 + kSmallThreads - 1) / kSmallThreads;   // kept T entries per thread
+constexpr int kSmallThreads = 256;      // CTA size for 2g up to kSmallMax (smaller systems: fewer)
 // Body of the per-node merge; G2F > 0 fixes 2g at compile time (the sizes of
 // a uniform tree's lower levels: its loops and the T index arithmetic then
 // fold), 0 reads it from the descriptor.
 // F: the arithmetic of the merge (double; float for the FP32 levels of the
 // mixed form); the scalings, W, X and R are stored in double.
-template <int G2F, class F>
+// NT: threads of the CTA (64 for 2g <= 8, 128 for 2g <= 16, else 256: the
+// smallest systems keep every thread busy and more nodes resident per SM).
+template <int G2F, class F, int NT>
 __device__ __forceinline__ void merge_small_body(const DevView& v, const MergeDesc& D, const NodeRefs& N, int mstride,
                                                  F* sm, double* sd, double* sq, F* vrow,
                                                  double& s_inv_sum, int& s_bad) {
+    constexpr int kG2Max = G2F ? G2F : (NT >= 256 ? kSmallMax : NT / 8);   // the launch's largest 2g
+    constexpr int kSmallTri = (kG2Max * (kG2Max + 1) / 2 + NT - 1) / NT;     // kept T entries per thread
     const int g2 = G2F ? G2F : N.g2, g = g2 / 2, m = N.m, o1 = N.o1;
     const int tid = threadIdx.x;
     F* T = sm;
@@ -178,14 +181,14 @@ __device__ __forceinline__ void merge_small_body(const DevView& v, const MergeDe
         }
     }
     __syncthreads();
-    for (int idx = tid; idx < g2 * g2; idx += kSmallThreads) {
+    for (int idx = tid; idx < g2 * g2; idx += NT) {
         const int r = idx / g2, c = idx % g2, i = r < g ? r : r - g, j = c < g ? c : c - g;
         T[idx] = (F)t_entry(N, r, c, sd[i], sd[j], sq[i], sq[j], s_inv_sum);
     }
     for (int k = 0; k < g; ++k) {
         const double* ra = N.R1 + N.gpos1[k] * N.m1;
         const double* rb = N.R2 + N.gpos2[k] * N.m2;
-        for (int j = tid; j < m; j += kSmallThreads)
+        for (int j = tid; j < m; j += NT)
             Bs[k * mstride + j] = (F)(j < o1 ? ra[N.opos1[j]] : rb[N.opos2[j - o1]]);
     }
     // Gauss-Jordan on T (d rows first: positive pivots, then negative).  T
@@ -200,7 +203,7 @@ __device__ __forceinline__ void merge_small_body(const DevView& v, const MergeDe
     int er[kSmallTri], ec[kSmallTri];
 #pragma unroll
     for (int e = 0; e < kSmallTri; ++e) {
-        const int idx = tid + e * kSmallThreads;
+        const int idx = tid + e * NT;
         int r = (int)((sqrtf(8.0f * idx + 1.0f) - 1.0f) * 0.5f);
         while ((r + 1) * (r + 2) / 2 <= idx) ++r;
         while (r * (r + 1) / 2 > idx) --r;
@@ -224,7 +227,7 @@ __device__ __forceinline__ void merge_small_body(const DevView& v, const MergeDe
         F nv[kSmallTri];
 #pragma unroll
         for (int e = 0; e < kSmallTri; ++e) {
-            const int idx = tid + e * kSmallThreads;
+            const int idx = tid + e * NT;
             if (idx >= ntri) break;
             const int r = er[e], c = ec[e];
             const F xr = r == k ? (F)1 : (r > k ? neg_bits(T[r * g2 + k]) : T[k * g2 + r]);
@@ -234,7 +237,7 @@ __device__ __forceinline__ void merge_small_body(const DevView& v, const MergeDe
         __syncthreads();
 #pragma unroll
         for (int e = 0; e < kSmallTri; ++e) {
-            const int idx = tid + e * kSmallThreads;
+            const int idx = tid + e * NT;
             if (idx >= ntri) break;
             T[er[e] * g2 + ec[e]] = nv[e];
         }
@@ -243,7 +246,7 @@ __device__ __forceinline__ void merge_small_body(const DevView& v, const MergeDe
     if (tid == 0 && s_bad) atomicOr(v.status, kStatusSingular);
     // W = D^-1/2 Q T^-1 Q^T D^-1/2 (column-major Wc); T^-1 symmetric, kept
     // in the lower triangle
-    for (int idx = tid; idx < g * g; idx += kSmallThreads) {
+    for (int idx = tid; idx < g * g; idx += NT) {
         const int i = idx % g, j = idx / g;
         const F zdd = i >= j ? T[i * g2 + j] : T[j * g2 + i];
         const F zds = T[(g + j) * g2 + i];           // (d_i, s_j) = (s_j, d_i)
@@ -257,10 +260,10 @@ __device__ __forceinline__ void merge_small_body(const DevView& v, const MergeDe
     }
     __syncthreads();
     double* Wg = v.W + D.W_off;
-    for (int idx = tid; idx < g2 * g2; idx += kSmallThreads) Wg[idx] = (double)Wc[idx];
+    for (int idx = tid; idx < g2 * g2; idx += NT) Wg[idx] = (double)Wc[idx];
     // X = -W B (columns of side a use W's a columns)
     double* Xg = v.X + D.X_off;
-    for (int idx = tid; idx < g2 * m; idx += kSmallThreads) {
+    for (int idx = tid; idx < g2 * m; idx += NT) {
         const int r = idx % g2, j = idx / g2;
         const F* wc = Wc + (j < o1 ? 0 : g) * g2 + r;
         F acc0 = 0, acc1 = 0;
@@ -279,7 +282,7 @@ __device__ __forceinline__ void merge_small_body(const DevView& v, const MergeDe
     // symmetric (R_oo - B^T W B), so the lower triangle is formed and mirrored
     double* Rp = v.R + D.R_off;
     const int mtri = m * (m + 1) / 2;
-    for (int idx = tid; idx < mtri; idx += kSmallThreads) {
+    for (int idx = tid; idx < mtri; idx += NT) {
         int i = (int)((sqrtf(8.0f * idx + 1.0f) - 1.0f) * 0.5f);
         while ((i + 1) * (i + 2) / 2 <= idx) ++i;
         while (i * (i + 1) / 2 > idx) --i;
@@ -301,8 +304,8 @@ __device__ __forceinline__ void merge_small_body(const DevView& v, const MergeDe
         Rp[(long long)j * m + i] = val;
     }}
 
-template <class F>
-__global__ void __launch_bounds__(kSmallThreads) merge_small_kernel(DevView v, int first, int mstride) {
+template <class F, int NT>
+__global__ void __launch_bounds__(NT) merge_small_kernel(DevView v, int first, int mstride) {
     extern __shared__ __align__(16) unsigned char sm_raw[];
     F* sm = reinterpret_cast<F*>(sm_raw);
     __shared__ double sd[kSmallMax / 2], sq[kSmallMax / 2];
@@ -311,12 +314,12 @@ __global__ void __launch_bounds__(kSmallThreads) merge_small_kernel(DevView v, i
     __shared__ int s_bad;
     const MergeDesc D = v.merges[first + blockIdx.x];
     const NodeRefs N = node_refs(v, D);
-    switch (N.g2) {                                       // uniform per CTA
-        case 8: merge_small_body<8, F>(v, D, N, mstride, sm, sd, sq, vrow, s_inv_sum, s_bad); break;
-        case 16: merge_small_body<16, F>(v, D, N, mstride, sm, sd, sq, vrow, s_inv_sum, s_bad); break;
-        case 32: merge_small_body<32, F>(v, D, N, mstride, sm, sd, sq, vrow, s_inv_sum, s_bad); break;
-        default: merge_small_body<0, F>(v, D, N, mstride, sm, sd, sq, vrow, s_inv_sum, s_bad); break;
-    }
+    // uniform per CTA; a launch with NT threads holds systems up to 2g = NT / 8
+    // (NT = 256: up to kSmallMax)
+    if (N.g2 == 8) merge_small_body<8, F, NT>(v, D, N, mstride, sm, sd, sq, vrow, s_inv_sum, s_bad);
+    else if (NT >= 128 && N.g2 == 16) merge_small_body<16, F, NT>(v, D, N, mstride, sm, sd, sq, vrow, s_inv_sum, s_bad);
+    else if (NT >= 256 && N.g2 == 32) merge_small_body<32, F, NT>(v, D, N, mstride, sm, sd, sq, vrow, s_inv_sum, s_bad);
+    else merge_small_body<0, F, NT>(v, D, N, mstride, sm, sd, sq, vrow, s_inv_sum, s_bad);
 }
 
 // ---------------------------------------------------------------------------
@@ -2058,11 +2061,15 @@ template <class F>
 static cudaError_t launch_small(const DevView& v, int first, int count, int max_g2, int max_m, cudaStream_t s) {
     const int mstride = max_m | 1;          // odd: rows of B and X start in different banks
     const size_t sm = small_smem(max_g2, max_m);
-    cudaError_t e = cudaFuncSetAttribute(merge_small_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kSmallSmemMax);
-    if (e != cudaSuccess) return e;
-    merge_small_kernel<F><<<count, kSmallThreads, sm, s>>>(v, first, mstride);
-    return cudaGetLastError();
+    auto go = [&](auto kern, int nt) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmallSmemMax);
+        if (e != cudaSuccess) return e;
+        kern<<<count, nt, sm, s>>>(v, first, mstride);
+        return cudaGetLastError();
+    };
+    if (max_g2 <= 8) return go(merge_small_kernel<F, 64>, 64);
+    if (max_g2 <= 16) return go(merge_small_kernel<F, 128>, 128);
+    return go(merge_small_kernel<F, kSmallThreads>, kSmallThreads);
 }
 
 // The three launches of a blocked level, each with its tuning choice (0:
