@@ -332,7 +332,7 @@ int mrcm_set_root_form(mrcm_ctx* ctx, int form);
 /*
  * mrcm_autotune -- picks the launch shapes of every blocked merge level by
  * timing them on this device: CTAs per SM of the cooperative Gauss-Jordan
- * sweep (1, 2 or 3), rows of X per CTA (32 or 64), side of an R tile (16 or
+ * sweep (1 to 4), rows of X per CTA (32 or 64), side of an R tile (16 or
  * 32); each candidate is run `reps` times (1..100) on the context's stream
  * and the fastest kept per launch and tree height.  Every shape computes the
  * same numbers, so the basis stays valid; later builds use the choices (the

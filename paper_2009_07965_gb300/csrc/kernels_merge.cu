@@ -885,7 +885,7 @@ __device__ __forceinline__ long long level_run(long long per_node, int count) {
 // T: the arithmetic of the level (double; float for the FP32 levels of the
 // mixed form, which sweep the FP32 work array and write W in double).
 template <class T>
-__global__ void __launch_bounds__(256) gj_sweep_kernel(DevView v, int first, int count, int nmax, T* scratch,
+__global__ void __launch_bounds__(256, 4) gj_sweep_kernel(DevView v, int first, int count, int nmax, T* scratch,
                                                        unsigned int* counter) {
     __shared__ GJSmem<T> S;
     __shared__ int s_bad, s_item;
@@ -1323,7 +1323,7 @@ __device__ bool ldl_u_item(const DevView& v, const MergeDesc& D, int slot, int x
 // level (double; float for an FP32 level of the mixed form, which factors in
 // the FP32 work array and stores Lt and P in double at the end).
 template <class T>
-__global__ void __launch_bounds__(256) ldl_sweep_kernel(DevView v, int first, int count, int nmax, T* scratch,
+__global__ void __launch_bounds__(256, 4) ldl_sweep_kernel(DevView v, int first, int count, int nmax, T* scratch,
                                                         unsigned int* counter) {
     __shared__ GJSmem<T> S;
     __shared__ int s_bad, s_item;
@@ -1783,6 +1783,7 @@ __device__ bool tri_backward_item(const DevView& v, const MergeDesc& D, int K, u
 // lane has about kUpTerms terms (FP64 products are costly per warp
 // instruction: they are spread thin, and padded ones are avoided).
 constexpr int kUpTerms = 4;
+constexpr long long kTreePrefetchMax = 64LL << 20;   // half the L2
 __device__ __forceinline__ int tree_up_lanes(int g2) {
     int l = 1;
     while (l < 32 && l * kUpTerms < g2) l <<= 1;
@@ -1809,13 +1810,17 @@ __global__ void __launch_bounds__(256) tree_up_kernel(DevView v, TreeLevels L, u
     const long long stride = (long long)gridDim.x * 256;
     const long long t0 = (long long)blockIdx.x * 256 + tid;
     unsigned int round = 0;
-    // The static data of both sweeps (descriptors, index maps, X, W: tens of
-    // MB at most) into L2 first, in the order of use: each height is a short
-    // chain of dependent loads, and cold misses would set its pace.
+    // The static data of both sweeps (descriptors, index maps, X, W) into L2
+    // first, in the order of use, when it fits there with room to spare: each
+    // height is then a short chain of dependent loads, and cold misses would
+    // set its pace.  Larger trees (X and W of a 4096^2 field: ~1 GB) would
+    // only stream W through L2 ahead of a sweep that does not read it.
     prefetch_range_l2(v.merges, L.n_merges * (long long)sizeof(MergeDesc), t0, stride);
     prefetch_range_l2(v.node_map, L.map_len * (long long)sizeof(int), t0, stride);
-    prefetch_range_l2(v.X, L.x_len * (long long)sizeof(double), t0, stride);
-    prefetch_range_l2(v.W, L.w_len * (long long)sizeof(double), t0, stride);
+    if ((L.x_len + L.w_len) * (long long)sizeof(double) <= kTreePrefetchMax) {
+        prefetch_range_l2(v.X, L.x_len * (long long)sizeof(double), t0, stride);
+        prefetch_range_l2(v.W, L.w_len * (long long)sizeof(double), t0, stride);
+    }
     for (int h = 0; h < L.height; ++h) {
         const int first = L.first[h], count = L.count[h], g2max = L.g2[h], mmax = L.m[h];
         if (count == 0) continue;                           // uniform over the grid
@@ -2264,7 +2269,7 @@ static cudaError_t tune_level_t(const DevView& v, int first, int count, int max_
         return e;
     }
     float best = 1e30f;
-    for (int per_sm : {1, 2, 3}) {
+    for (int per_sm : {1, 2, 3, 4}) {
         if (!factor && node_level(count, max_g2, sms)) break;        // the per-node kernel: no shape to pick
         float t = 0.f;
         e = best_time(s, reps, e0, e1, [&] {

@@ -322,7 +322,7 @@ struct PhaseHook {
 // max_m) values; barrier: kMergeBarrierBytes of device memory (reset by the
 // call); *launches is increased by the number of kernels launched
 // Launch shapes of one blocked merge level (0 everywhere: the built-in
-// heuristic).  sweep_per_sm: CTAs per SM of the cooperative sweep (1-3);
+// heuristic).  sweep_per_sm: CTAs per SM of the cooperative sweep (1-4);
 // x_rows: rows of X per CTA (32, 64); r_tile: side of an R tile (16, 32).
 struct MergeTune {
     int sweep_per_sm = 0, x_rows = 0, r_tile = 0;
