@@ -1030,7 +1030,7 @@ __device__ __forceinline__ void tri_rc(int r, int& a, int& b) {
 
 // ---------------------------------------------------------------------------
 // Per-node inversion for levels of many mid-sized systems (32 < 2g <= 128,
-// at least as many nodes as SMs): one CTA per node holds the lower triangle
+// at least half as many nodes as SMs): one CTA per node holds the lower triangle
 // of T in shared memory (row-packed) and runs the Gauss-Jordan elimination
 // of merge_small on it, a rank-one step per pivot (warp 0 forms the pivot's
 // reciprocal, the pivot test and the scaled pivot row and column; every
@@ -2117,10 +2117,11 @@ static cudaError_t sweep_launch(const DevView& v, int first, int count, int max_
     return cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(256), args, dyn, s);
 }
 // A blocked level of many mid-sized systems takes the per-node inversion
-// (gj_node_kernel): one CTA per node keeps every SM busy without the
-// sweep's per-step grid barriers.  A fixed rule (not a tuning choice, so
-// that tuned launch shapes keep the bits of the result).
-static bool node_level(int count, int max_g2, int sms) { return max_g2 <= kNodeMax && count >= sms; }
+// (gj_node_kernel): one CTA per node, no per-step grid barriers; from half
+// as many nodes as SMs on, a node's whole elimination on one SM is shorter
+// than the sweep's chain of block steps over the level.  A fixed rule (not
+// a tuning choice, so that tuned launch shapes keep the bits of the result).
+static bool node_level(int count, int max_g2, int sms) { return max_g2 <= kNodeMax && 2 * count >= sms; }
 template <class F>
 static cudaError_t node_launch(const DevView& v, int first, int count, int max_g2, cudaStream_t s) {
     cudaError_t e;
