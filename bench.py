@@ -84,6 +84,29 @@ TRAFFIC_PER_LAUNCH = {
 }
 
 
+def time_copies(stream, *pairs, reps=3):
+    """The step's host<->device copies alone (dst, src pairs; pinned host
+    buffers), best of `reps`: ms and GB/s per direction."""
+    import torch
+    out = {}
+    for name, sel in (("h2d", lambda d: d.is_cuda), ("d2h", lambda d: not d.is_cuda)):
+        ps = [(d, s) for d, s in pairs if sel(d)]
+        nbytes = sum(d.numel() * d.element_size() for d, _ in ps)
+        best = None
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            with torch.cuda.stream(stream):
+                for d, s in ps:
+                    d.copy_(s, non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            t = e0.elapsed_time(e1)
+            best = t if best is None else min(best, t)
+        out[name] = dict(ms=best, gb_per_s=nbytes / (best / 1e3) / 1e9)
+    return out
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -558,6 +581,7 @@ def run_ours(args):
     e2e_value, _ = job_throughput(sum(e2e_ms), cells, args.steps, world, dev)
     h2d = (K_h.numel() + q_h.numel() + bc_h.numel()) * 8
     d2h = (p_h.numel() + fx_h.numel() + fy_h.numel()) * 8
+    copies = time_copies(stream, (K_d, K_h), (q_d, q_h), (bc_d, bc_h), (p_h, pd), (fx_h, fxd), (fy_h, fyd))
     solver.solve(q, bcv, want_iface=True)
     torch.cuda.synchronize(dev)
     balance = mass_balance(solver, q)
@@ -671,7 +695,8 @@ def run_ours(args):
         autotuned_shapes=tuned,
         phases=table,
         gflop_per_step=sum(pf.values()) / 1e9,
-        e2e=dict(value=e2e_value, unit="cells/s", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
+        e2e=dict(value=e2e_value, unit="cells/s", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h,
+                 copies_alone=copies),
         gpu_launches=launches * args.steps,
         clocks=clocks,
         check=dict(mass_balance=balance, refine_steps=args.refine, rel_l2_vs_refined=rel,
