@@ -237,7 +237,8 @@ enum {
     MRCM_PHASE_LEAF_BUILD = 1,     /* leaf factorisation and Robin-to-flux maps     */
     MRCM_PHASE_MERGE_SMALL = 2,    /* whole merges of small interface systems       */
     MRCM_PHASE_GJ_SWEEP = 3,       /* blocked merges: Gauss-Jordan inversion of the
-                                      quasi-definite form                           */
+                                      quasi-definite form (the cooperative sweep, or
+                                      one system per CTA for many mid-sized ones)  */
     MRCM_PHASE_MERGE_FORM = 4,     /* blocked merges: the quasi-definite form of the
                                       interface matrix and its back transform; now
                                       done inside the sweep's launch (timed as
@@ -343,7 +344,9 @@ int mrcm_set_root_form(mrcm_ctx* ctx, int form);
  * mrcm_tune_info -- the choices for tree height `height` (1 = the leaves'
  * parents): out[0] CTAs per SM of the sweep, out[1] X rows, out[2] R tile;
  * 0 where the built-in heuristic applies (before mrcm_autotune, and on
- * heights merged by the small-system kernel).
+ * heights merged by the small-system kernel); out[0] is also 0 on heights
+ * inverted one system per CTA (2g <= 128 with at least one node per two
+ * SMs: a fixed rule, no launch shape to choose).
  */
 int mrcm_autotune(mrcm_ctx* ctx, int reps);
 int mrcm_tune_info(const mrcm_ctx* ctx, int height, int out[3]);
