@@ -44,6 +44,7 @@ struct LeafBuildSmem {
     int order[MMAX];                     // ordered column q -> local segment
     int pos[MMAX];                       // local segment -> ordered column
     int start[MMAX];                     // first row with a nonzero, per ordered column
+    double dg[kLeafThreads];             // diagonal entries of the next rows to enter (row % 16)
 };
 
 // (row, col) of entry idx of a lower triangle stored row by row.
@@ -85,18 +86,29 @@ __device__ __forceinline__ void cell_robin_segments(const DevView& v, const Leaf
     sn = (j == L.h - 1 && L.side_off[3] >= 0) ? L.side_off[3] + i / v.gx : -1;
 }
 
+// Diagonal entry of row `row` of the leaf matrix: the sum of the cell's face
+// coefficients.
+__device__ __forceinline__ double row_diag(const DevView& v, const LeafDesc& L, int row) {
+    const CellFaces f = cell_faces(v, L, row % L.w, row / L.w);
+    return (f.w_ + f.e_) + (f.s_ + f.n_);
+}
+
+// Row `row` of the band into the window and its Robin columns into zw.  The
+// diagonal entry comes from S.dg (formed 16 rows at a time, one row per
+// lane: an FP64 instruction costs a whole warp's issue however few lanes it
+// uses), or is formed here when `fresh` (the rows before the elimination).
 template <int MMAX, class T>
 __device__ __forceinline__ void init_row(const DevView& v, const LeafDesc& L, LeafBuildSmem<MMAX, T>& S,
-                                         int row, int t) {
+                                         int row, int t, bool fresh) {
     const int w = L.w, m = L.m;
     const int i = row % w, j = row / w;
     const int slot = row % (w + 2);
     const CellFaces f = cell_faces(v, L, i, j);
     for (int o = t; o <= w; o += kLeafThreads) {
         double a = 0.0;
-        if (o == 0) a = (f.w_ + f.e_) + (f.s_ + f.n_);
-        if (o == 1 && i > 0) a = -f.tx;
-        if (o == w && j > 0) a = -f.ty;   // w == 1: the y neighbour sits at offset 1
+        if (o == 0) a = fresh ? (f.w_ + f.e_) + (f.s_ + f.n_) : S.dg[row % kLeafThreads];
+        if (o == 1 && i > 0) a = neg_bits(f.tx);
+        if (o == w && j > 0) a = neg_bits(f.ty);   // w == 1: the y neighbour sits at offset 1
         S.win[slot][o] = (T)a;
     }
     int sw, se, ss, sn;
@@ -178,7 +190,7 @@ __device__ __forceinline__ void leaf_build_body(const DevView& v, LeafBuildSmem<
 
     for (int idx = t; idx < m * (MMAX + 1); idx += kLeafThreads) S.R[idx / (MMAX + 1)][idx % (MMAX + 1)] = (T)0;
     const int first = min(w, n - 1);
-    for (int r = 0; r <= first; ++r) init_row(v, L, S, r, t);
+    for (int r = 0; r <= first; ++r) init_row(v, L, S, r, t, true);
     __syncwarp(mask);
 
     // per-thread index patterns of the two triangles (band update: rows a >=
@@ -200,6 +212,12 @@ __device__ __forceinline__ void leaf_build_body(const DevView& v, LeafBuildSmem<
     int ck = 0;                      // active ordered columns
     int sk = 0;                      // window slot of row k (k mod W2)
     for (int k = 0; k < n; ++k) {
+        // diagonals of the rows entering the window in steps k .. k + 15 (read
+        // after the warp barrier of phase A)
+        if ((k & (kLeafThreads - 1)) == 0) {
+            const int r = k + w + 1 + t;
+            if (r < n) S.dg[r % kLeafThreads] = row_diag(v, L, r);
+        }
         while (ck < m && S.start[ck] <= k) ++ck;
         const int s1 = sk + 1 == W2 ? 0 : sk + 1;        // slot of row k + 1
         // ---- phase A: pivot, multipliers, row k of Z -------------------------
@@ -270,7 +288,7 @@ __device__ __forceinline__ void leaf_build_body(const DevView& v, LeafBuildSmem<
                 S.R[r][c] = fma(S.zk[r], S.uk[c], S.R[r][c]);
             }
         }
-        if (k + w + 1 < n) init_row(v, L, S, k + w + 1, t);
+        if (k + w + 1 < n) init_row(v, L, S, k + w + 1, t, false);
         __syncwarp(mask);
         sk = s1;
     }
