@@ -346,11 +346,11 @@ def run_probe_only():
                           fp64_nominal_tflops=FP64_NOMINAL_TFLOPS)), flush=True)
 
 
-def time_mixed(mr, prob, q, bcv, stream, flush, args, split, ref_fp64, wl, rank, refine=3):
-    """The mixed form (FP32 leaves and lower merges, FP64 top merges, refined
-    with double-double residuals): ms per build + solve, its accuracy
-    against the refined FP64 result and the oracle's samples, and its phase
-    times."""
+def time_mixed(mr, prob, q, bcv, stream, flush, args, split, ref_fp64, wl, rank, refine=3, leaves32=False):
+    """The mixed form (merges up to the split in FP32 -- every one by default
+    --, leaves in FP64 or, with leaves32, in FP32; refined with double-double
+    residuals): ms per build + solve, its accuracy against the refined FP64
+    result and the oracle's samples, and its phase times."""
     import numpy as np
     import torch
     dev = q.device
@@ -360,6 +360,7 @@ def time_mixed(mr, prob, q, bcv, stream, flush, args, split, ref_fp64, wl, rank,
                       precision=mr.binding.MRCM_MIXED)
     if split is not None:
         mr.mrcm_set_mixed_split(s.ctx, split)
+    mr.mrcm_set_mixed_leaves(s.ctx, 1 if leaves32 else 0)
     mr.mrcm_set_refinement(s.ctx, refine)
     mr.mrcm_enable_timing(s.ctx, True)
 
@@ -397,7 +398,7 @@ def time_mixed(mr, prob, q, bcv, stream, flush, args, split, ref_fp64, wl, rank,
     torch.cuda.empty_cache()
     step_ms = sum(ms) / len(ms)
     return dict(ms_per_step=step_ms, value=prob.nx * prob.ny / (step_ms / 1e3), refine_steps=refine,
-                fp32_merges_up_to_2g=(split if split is not None else 512),
+                fp32_merges_up_to_2g=(split if split is not None else "all"), fp32_leaves=bool(leaves32),
                 rel_l2_vs_fp64_refined=rel, vs_oracle_samples=vs_oracle, residual_history=hist,
                 within_tolerance=bool(max(rel.values()) <= 1e-8), tolerance=1e-8,
                 phases_ms={k: v / args.steps for k, v in phases.items() if v > 0})
@@ -615,14 +616,14 @@ def run_ours(args):
         surrogate = time_surrogate(mr, solver, wl, args)
     mixed = {}
     if not args.no_mixed:
-        # free the FP64 form's workspace first (two 4096^2 contexts fit, but
-        # the timing should not share L2 with a resident second workspace)
-        # three refinement steps (the form's default), and the steps this
-        # field needs to reach the metric's 1e-8 (the residual contracts by
-        # ~0.3 per step here)
-        for split, name, refine in ((None, "mixed", 3), (1 << 30, "mixed_all_fp32", 3),
-                                    (None, "mixed_to_1e-8", 12)):
-            mixed[name] = time_mixed(mr, prob, q, bcv, stream, flush, args, split, refined, wl, rank, refine)
+        # the form's defaults (FP64 leaves, every merge in FP32, three
+        # refinement steps), the FP64 top merges kept, and FP32 leaves with
+        # the steps they need at this field to reach the metric's 1e-8 (the
+        # residual then contracts by only ~0.3 per step)
+        for split, name, refine, leaves32 in ((None, "mixed", 3, False), (512, "mixed_fp64_top_merges", 3, False),
+                                              (None, "mixed_fp32_leaves_to_1e-8", 12, True)):
+            mixed[name] = time_mixed(mr, prob, q, bcv, stream, flush, args, split, refined, wl, rank, refine,
+                                     leaves32)
 
     ph = {k: v / args.steps for k, v in phases.items()}          # ms per step
     pf = mr.mrcm_phase_flops(solver.ctx)                          # flops per step

@@ -91,16 +91,16 @@ enum {
  *   bc_type    per side (x-, x+, y-, y+, z-, z+): MRCM_BC_NEUMANN or
  *              MRCM_BC_DIRICHLET (z entries ignored in 2D).  All-Neumann
  *              problems are solved with zero-mean pressure.
- *   precision  MRCM_FP64: every step in FP64.  MRCM_MIXED: the leaf
- *              factorisations, the multi-right-hand-side basis solves and
- *              the merges of interface systems up to 2g = 512
- *              (mrcm_set_mixed_split) in FP32; the coefficients, the top
- *              merges, the solve passes, the residuals (double-double) and
- *              the fluxes in FP64; mrcm_solve then refines 3 times by
- *              default (mrcm_set_refinement), which brings the result to
- *              the FP64 form's accuracy when the FP32 factors contract the
- *              error (Wilkinson's iterative refinement).  MRCM_SURROGATE
- *              returns MRCM_ERR_UNSUPPORTED.
+ *   precision  MRCM_FP64: every step in FP64.  MRCM_MIXED: the merges
+ *              (their blocked eliminations and products; by default every
+ *              one, mrcm_set_mixed_split) in FP32, and optionally the leaf
+ *              factorisations and basis solves (mrcm_set_mixed_leaves; FP64
+ *              by default); the coefficients, the solve passes, the
+ *              residuals (double-double) and the fluxes in FP64; mrcm_solve
+ *              then refines 3 times by default (mrcm_set_refinement), which
+ *              brings the result near the FP64 form's accuracy when the FP32
+ *              factors contract the error (Wilkinson's iterative
+ *              refinement).  MRCM_SURROGATE returns MRCM_ERR_UNSUPPORTED.
  *   cuda_stream  cudaStream_t to run on (NULL = legacy default stream)
  * The context allocates and owns all device workspace.
  */
@@ -298,14 +298,26 @@ int mrcm_set_wait_limit(mrcm_ctx* ctx, long long polls);
 
 /*
  * mrcm_set_mixed_split -- mixed form only: merges whose interface system
- * has 2g <= max_g2_fp32 run in FP32, larger ones in FP64 (default 512; 0:
- * every merge in FP64; a value at least the largest 2g: every merge in
- * FP32).  The paper has no counterpart (its arithmetic is FP64 throughout).
+ * has 2g <= max_g2_fp32 run in FP32, larger ones in FP64 (default 2^30,
+ * every merge in FP32; 0: every merge in FP64).  The paper has no counterpart (its arithmetic is FP64 throughout).
  * Invalidates the basis (call mrcm_build_basis again).  Errors:
  * MRCM_ERR_INVALID_ARG (negative), MRCM_ERR_UNSUPPORTED (not a mixed
  * context), MRCM_ERR_CUDA.
  */
 int mrcm_set_mixed_split(mrcm_ctx* ctx, int max_g2_fp32);
+
+/*
+ * mrcm_set_mixed_leaves -- mixed form only: fp32 = 1 keeps the leaf
+ * factorisations and their stored factors in FP32, fp32 = 0 (the default)
+ * in FP64 (then only the merges up to the split run in FP32; their errors
+ * are not amplified by the interface systems above as much as the leaf
+ * maps' are, and the refinement converges in fewer steps).  The paper has no
+ * counterpart.  A mixed context holds both sets of leaf arrays.  Invalidates
+ * the basis (call mrcm_build_basis again).  Errors: MRCM_ERR_INVALID_ARG
+ * (fp32 not 0 or 1), MRCM_ERR_UNSUPPORTED (not a mixed context),
+ * MRCM_ERR_CUDA.
+ */
+int mrcm_set_mixed_leaves(mrcm_ctx* ctx, int fp32);
 
 /*
  * mrcm_set_root_form -- how the interface system of a tree's root is kept

@@ -29,7 +29,7 @@ EXPORTS = ["mrcm_setup", "mrcm_setup_batch", "mrcm_plan_query", "mrcm_set_permea
            "mrcm_last_cuda_error",
            "mrcm_merge_pair_noalloc", "mrcm_set_refinement", "mrcm_residual_history", "mrcm_phase_flops",
            "mrcm_group_times", "mrcm_check_reciprocal", "mrcm_set_wait_limit",
-           "mrcm_probe_peak", "mrcm_set_mixed_split", "mrcm_set_root_form", "mrcm_autotune", "mrcm_tune_info",
+           "mrcm_probe_peak", "mrcm_set_mixed_split", "mrcm_set_mixed_leaves", "mrcm_set_root_form", "mrcm_autotune", "mrcm_tune_info",
            "mrcm_interior_leaves", "mrcm_leaf_fields", "mrcm_leaf_patches", "mrcm_leaf_gate", "mrcm_leaf_apply",
            "mrcm_cnn_conv_forward", "mrcm_cnn_conv_wgrad", "mrcm_cnn_flip_weights", "mrcm_cnn_relu_grad",
            "mrcm_cnn_mse_grad", "mrcm_cnn_adam"]
@@ -141,6 +141,8 @@ def _lib():
         lib.mrcm_set_mixed_split.restype = I
         lib.mrcm_set_root_form.argtypes = [P, I]
         lib.mrcm_set_root_form.restype = I
+        lib.mrcm_set_mixed_leaves.argtypes = [P, I]
+        lib.mrcm_set_mixed_leaves.restype = I
         lib.mrcm_probe_peak.argtypes = [I, D, ctypes.POINTER(ctypes.c_double), P]
         lib.mrcm_probe_peak.restype = I
         lib.mrcm_set_wait_limit.argtypes = [P, ctypes.c_longlong]
@@ -389,6 +391,11 @@ def mrcm_tune_info(ctx, height):
 
 def mrcm_set_mixed_split(ctx, max_g2_fp32):
     _check(_lib().mrcm_set_mixed_split(ctx, int(max_g2_fp32)), "mrcm_set_mixed_split")
+
+
+def mrcm_set_mixed_leaves(ctx, fp32):
+    """Mixed form: leaf factors in FP32 (1) or FP64 (0, default); the basis must be rebuilt."""
+    _check(_lib().mrcm_set_mixed_leaves(ctx, int(fp32)), "mrcm_set_mixed_leaves")
 
 
 def mrcm_set_root_form(ctx, form):

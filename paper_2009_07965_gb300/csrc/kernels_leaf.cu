@@ -630,14 +630,14 @@ static cudaError_t launch_leaf_build_t(const DevView& v, int max_m, cudaStream_t
 }
 
 cudaError_t launch_leaf_build(const DevView& v, int max_m, cudaStream_t s) {
-    return v.mixed ? launch_leaf_build_t<float>(v, max_m, s) : launch_leaf_build_t<double>(v, max_m, s);
+    return v.leaf32 ? launch_leaf_build_t<float>(v, max_m, s) : launch_leaf_build_t<double>(v, max_m, s);
 }
 
 cudaError_t launch_leaf_particular(const DevView& v, const double* q, const double* bc_val,
                                    bool with_sadj, cudaStream_t s) {
     constexpr int LPB = 8;
     const int grid = (v.nleaf + LPB - 1) / LPB;
-    if (v.mixed)
+    if (v.leaf32)
         leaf_particular_kernel<LPB, float><<<grid, kLeafThreads * LPB, 0, s>>>(v, q, bc_val, with_sadj);
     else
         leaf_particular_kernel<LPB, double><<<grid, kLeafThreads * LPB, 0, s>>>(v, q, bc_val, with_sadj);
@@ -647,7 +647,7 @@ cudaError_t launch_leaf_particular(const DevView& v, const double* q, const doub
 cudaError_t launch_leaf_pressure(const DevView& v, bool accumulate, cudaStream_t s) {
     constexpr int LPB = 8;
     const int grid = (v.nleaf + LPB - 1) / LPB;
-    if (v.mixed)
+    if (v.leaf32)
         leaf_pressure_kernel<LPB, float><<<grid, kLeafThreads * LPB, 0, s>>>(v, accumulate);
     else
         leaf_pressure_kernel<LPB, double><<<grid, kLeafThreads * LPB, 0, s>>>(v, accumulate);

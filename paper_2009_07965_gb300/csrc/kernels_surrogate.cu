@@ -441,7 +441,7 @@ __global__ void __launch_bounds__(kS * kS) leaf_apply_kernel(DevView v, const in
 
 cudaError_t launch_leaf_fields(const DevView& v, const int* ids, int count, float* psi, cudaStream_t s) {
     if (count <= 0) return cudaSuccess;
-    if (v.mixed)
+    if (v.leaf32)
         leaf_fields_kernel<float><<<(count + 7) / 8, 128, 0, s>>>(v, ids, count, psi);
     else
         leaf_fields_kernel<double><<<(count + 7) / 8, 128, 0, s>>>(v, ids, count, psi);

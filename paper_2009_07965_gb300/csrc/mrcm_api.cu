@@ -445,14 +445,15 @@ int mrcm::cuda_status(cudaError_t e) {
     return MRCM_ERR_CUDA;
 }
 
-// Refinement steps of the mixed form by default: each step contracts the
-// error by about the condition of the FP32 leaf factors times the FP32
-// rounding unit, so three reach the FP64 rounding level on the workloads.
+// Refinement steps of the mixed form by default: with FP64 leaf factors and
+// FP32 merges each step contracts the residual ~60 times at 4096^2, so three
+// reach ~1e-9 against the FP64 solution.
 constexpr int kMixedRefineDefault = 3;
 
 // Largest interface system 2g merged in FP32 by default in the mixed form:
-// the levels above stay FP64 (their conditioning grows with the contrast).
-constexpr int kMixedSplitDefault = 512;
+// every one (the FP32 merges' errors are small beside the contraction; FP32
+// leaf factors are what slowed the refinement at 4096^2: 0.3 per step).
+constexpr int kMixedSplitDefault = 1 << 30;
 
 struct mrcm_ctx {
     Plan P;
@@ -750,6 +751,7 @@ static int setup_impl(mrcm_ctx* c, int count, const mrcm_grid* g, const double* 
     if (P.pure_neumann && P.nleaf == 1) return MRCM_ERR_UNSUPPORTED;
     DevView& v = c->v;
     v.mixed = precision == MRCM_MIXED ? 1 : 0;
+    v.leaf32 = 0;                  // the mixed form's leaves in FP64 unless mrcm_set_mixed_leaves(1)
     c->precision = precision;
     if (v.mixed) c->refine_steps = kMixedRefineDefault;
     v.alpha = P.alpha;
@@ -789,8 +791,9 @@ static int setup_impl(mrcm_ctx* c, int count, const mrcm_grid* g, const double* 
     TRY(upload(c, &v.node_map, P.node_map));
     TRY(upload(c, &v.gamma_segs, P.gamma_segs));
     // leaf factors in the precision of the form (FP32 in the mixed form)
-    TRY(dev_alloc(c, &v.leafL, v.mixed ? 1 : P.nL));
-    TRY(dev_alloc(c, &v.leafZ, v.mixed ? 1 : P.nZ));
+    // (the mixed form holds both precisions: mrcm_set_mixed_leaves switches)
+    TRY(dev_alloc(c, &v.leafL, P.nL));
+    TRY(dev_alloc(c, &v.leafZ, P.nZ));
     TRY(dev_alloc(c, &v.leafL32, v.mixed ? P.nL : 1));
     TRY(dev_alloc(c, &v.leafZ32, v.mixed ? P.nZ : 1));
     TRY(dev_alloc(c, &v.leafzb, P.nzb));
@@ -1110,6 +1113,22 @@ int mrcm_set_mixed_split(mrcm_ctx* c, int max_g2_fp32) {
     TRYC(cudaStreamSynchronize(c->stream));
     if (c->build_exec) cudaGraphExecDestroy(c->build_exec);
     c->build_exec = nullptr;
+    return MRCM_OK;
+}
+
+int mrcm_set_mixed_leaves(mrcm_ctx* c, int fp32) {
+    if (!c || (fp32 != 0 && fp32 != 1)) return MRCM_ERR_INVALID_ARG;
+    if (!c->v.mixed) return MRCM_ERR_UNSUPPORTED;
+    if (fp32 == c->v.leaf32) return MRCM_OK;
+    TRYC(cudaStreamSynchronize(c->stream));
+    c->v.leaf32 = fp32;
+    c->built = false;
+    c->solved = false;
+    // both captured graphs launch the leaf kernels of the old precision
+    if (c->build_exec) cudaGraphExecDestroy(c->build_exec);
+    if (c->solve_exec) cudaGraphExecDestroy(c->solve_exec);
+    c->build_exec = c->solve_exec = nullptr;
+    c->solve_key[0] = nullptr;
     return MRCM_OK;
 }
 

@@ -114,7 +114,8 @@ struct DevView {
     double* leafZ;      // Z per leaf
     float* leafL32;     // the same in FP32 (mixed precision: leaf work in FP32)
     float* leafZ32;
-    int mixed;          // 1: leaf factors and the merges of FP32 levels in FP32
+    int mixed;          // 1: the mixed form (the merges of FP32 levels in FP32)
+    int leaf32;         // 1: leaf factors in FP32 (the mixed form's default; mrcm_set_mixed_leaves)
     double* leafzb;     // particular forward solves
     double* R;          // node maps (leaves and internal nodes)
     double* rbar;       // node particular fluxes

