@@ -97,10 +97,11 @@ enum {
  *              factorisations and basis solves (mrcm_set_mixed_leaves; FP64
  *              by default); the coefficients, the solve passes, the
  *              residuals (double-double) and the fluxes in FP64; mrcm_solve
- *              then refines 3 times by default (mrcm_set_refinement), which
- *              brings the result near the FP64 form's accuracy when the FP32
- *              factors contract the error (Wilkinson's iterative
- *              refinement).  MRCM_SURROGATE returns MRCM_ERR_UNSUPPORTED.
+ *              then refines 3 times by default (mrcm_set_refinement) with
+ *              FP64 residuals (mrcm_set_residual), which brings the result
+ *              near the FP64 form's accuracy when the FP32 factors contract
+ *              the error (Wilkinson's iterative refinement).
+ *              MRCM_SURROGATE returns MRCM_ERR_UNSUPPORTED.
  *   cuda_stream  cudaStream_t to run on (NULL = legacy default stream)
  * The context allocates and owns all device workspace.
  */
@@ -278,8 +279,16 @@ enum {
  * mrcm_residual_history -- out[k] (host) = max |residual| of the k-th
  * evaluation in the last mrcm_solve (cell balances, Eq. 13.2 and 14.2 rows,
  * unscaled); returns the number of evaluations (>= 0) or an error code.
+ *
+ * mrcm_set_residual -- dd = 1: the refinement residuals in double-double
+ * (the FP64 form's default: refinement to the FP64 rounding level); dd = 0:
+ * in plain FP64, about six times fewer FP64 operations (the mixed form's
+ * default: enough for its 1e-8 target, the refined result then stalls near
+ * the plain FP64 solve's accuracy).  Takes effect at the next mrcm_solve.
+ * Errors: MRCM_ERR_INVALID_ARG.
  */
 int mrcm_set_refinement(mrcm_ctx* ctx, int steps, int check);
+int mrcm_set_residual(mrcm_ctx* ctx, int dd);
 
 /*
  * mrcm_set_wait_limit -- polls after which a bounded wait between the CTAs

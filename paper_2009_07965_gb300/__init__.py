@@ -7,7 +7,7 @@ from .binding import (mrcm_setup, mrcm_setup_batch, mrcm_plan_query, mrcm_set_pe
                       mrcm_query, mrcm_node_info, mrcm_node_segments, mrcm_segment_info,
                       mrcm_node_operator, mrcm_destroy, mrcm_error_string, mrcm_enable_timing, mrcm_use_graphs,
                       mrcm_last_cuda_error,
-                      mrcm_phase_times, mrcm_merge_pair_noalloc, mrcm_set_refinement,
+                      mrcm_phase_times, mrcm_merge_pair_noalloc, mrcm_set_refinement, mrcm_set_residual,
                       mrcm_residual_history, mrcm_phase_flops, mrcm_group_times, mrcm_check_reciprocal, mrcm_set_wait_limit, mrcm_probe_peak, mrcm_set_mixed_split, mrcm_set_mixed_leaves, mrcm_set_root_form, mrcm_autotune, mrcm_tune_info,
                       mrcm_interior_leaves, mrcm_leaf_fields, mrcm_leaf_patches, mrcm_leaf_gate, mrcm_leaf_apply,
                       mrcm_cnn_conv_forward, mrcm_cnn_conv_wgrad, mrcm_cnn_flip_weights, mrcm_cnn_relu_grad,
@@ -19,7 +19,7 @@ __all__ = ["mrcm_setup", "mrcm_setup_batch", "mrcm_plan_query", "mrcm_set_permea
            "mrcm_node_info", "mrcm_node_segments", "mrcm_segment_info", "mrcm_node_operator",
            "mrcm_destroy", "mrcm_error_string", "mrcm_enable_timing", "mrcm_phase_times", "mrcm_use_graphs",
            "mrcm_last_cuda_error",
-           "mrcm_merge_pair_noalloc", "mrcm_set_refinement", "mrcm_residual_history", "mrcm_phase_flops",
+           "mrcm_merge_pair_noalloc", "mrcm_set_refinement", "mrcm_set_residual", "mrcm_residual_history", "mrcm_phase_flops",
            "mrcm_group_times", "mrcm_check_reciprocal", "mrcm_set_wait_limit", "mrcm_probe_peak", "mrcm_set_mixed_split", "mrcm_set_mixed_leaves", "mrcm_set_root_form", "mrcm_autotune", "mrcm_tune_info",
            "mrcm_interior_leaves", "mrcm_leaf_fields", "mrcm_leaf_patches", "mrcm_leaf_gate", "mrcm_leaf_apply",
            "mrcm_cnn_conv_forward", "mrcm_cnn_conv_wgrad", "mrcm_cnn_flip_weights", "mrcm_cnn_relu_grad",

@@ -27,8 +27,8 @@ EXPORTS = ["mrcm_setup", "mrcm_setup_batch", "mrcm_plan_query", "mrcm_set_permea
            "mrcm_node_info", "mrcm_node_segments", "mrcm_segment_info", "mrcm_node_operator",
            "mrcm_destroy", "mrcm_error_string", "mrcm_enable_timing", "mrcm_phase_times", "mrcm_use_graphs",
            "mrcm_last_cuda_error",
-           "mrcm_merge_pair_noalloc", "mrcm_set_refinement", "mrcm_residual_history", "mrcm_phase_flops",
-           "mrcm_group_times", "mrcm_check_reciprocal", "mrcm_set_wait_limit",
+           "mrcm_merge_pair_noalloc", "mrcm_set_refinement", "mrcm_set_residual", "mrcm_residual_history",
+           "mrcm_phase_flops", "mrcm_group_times", "mrcm_check_reciprocal", "mrcm_set_wait_limit",
            "mrcm_probe_peak", "mrcm_set_mixed_split", "mrcm_set_mixed_leaves", "mrcm_set_root_form", "mrcm_autotune", "mrcm_tune_info",
            "mrcm_interior_leaves", "mrcm_leaf_fields", "mrcm_leaf_patches", "mrcm_leaf_gate", "mrcm_leaf_apply",
            "mrcm_cnn_conv_forward", "mrcm_cnn_conv_wgrad", "mrcm_cnn_flip_weights", "mrcm_cnn_relu_grad",
@@ -110,6 +110,8 @@ def _lib():
         lib.mrcm_check_reciprocal.restype = I
         lib.mrcm_set_refinement.argtypes = [P, I, I]
         lib.mrcm_set_refinement.restype = I
+        lib.mrcm_set_residual.argtypes = [P, I]
+        lib.mrcm_set_residual.restype = I
         LL, F = ctypes.c_longlong, ctypes.c_float
         lib.mrcm_interior_leaves.argtypes = [P, IP, I]
         lib.mrcm_interior_leaves.restype = I
@@ -311,6 +313,11 @@ def mrcm_check_reciprocal(x, out=None):
 
 def mrcm_set_refinement(ctx, steps, check=False):
     _check(_lib().mrcm_set_refinement(ctx, int(steps), 1 if check else 0), "mrcm_set_refinement")
+
+
+def mrcm_set_residual(ctx, dd):
+    """Refinement residuals in double-double (1; FP64 form default) or FP64 (0; mixed form default)."""
+    _check(_lib().mrcm_set_residual(ctx, 1 if dd else 0), "mrcm_set_residual")
 
 
 PROBES = dict(DFMA=0, DMMA=1, FFMA=2, TF32=3, BF16=4, DFMA_DMMA=5)

@@ -152,6 +152,89 @@ __global__ void __launch_bounds__(128) residual_segments_kernel(DevView v, int s
     block_record_max(v.res_max + step, fmax(fabs(E13), fabs(E14)));
 }
 
+// The same residuals in plain FP64 (the state's pairs rounded to double):
+// three operations per face instead of nineteen.  Enough for refinement to
+// a tolerance well above the FP64 rounding level (the mixed form's 1e-8);
+// refinement to the rounding level itself needs the double-double kernels.
+__global__ void __launch_bounds__(256) residual_cells_fp64_kernel(DevView v, const double* __restrict__ q,
+                                                                  const double* __restrict__ bc_val, int step) {
+    const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    double e = 0.0;
+    if (c < v.ncell) {
+        const GridDesc& G = v.grids[grid_of<0>(v, c)];
+        int i, j;
+        udivmod(c - G.c0, G.nx, j, i);
+        const double pc = v.p_hi[c] + v.p_lo[c];
+        const long long fx = G.fx0 + i + (long long)(G.nx + 1) * j;
+        const long long fy = G.fy0 + i + (long long)G.nx * j;
+        const long long b0 = G.b0;
+        // outward flux of the cell through one face
+        auto face = [&](int dirichlet, bool boundary, int seg, bool lower, double coef, double area, long long nb,
+                        long long bc_index) -> double {
+            if (boundary) {
+                const double g = bc_val[bc_index];
+                return dirichlet ? coef * (pc - g) : area * g;
+            }
+            if (seg >= 0) {
+                const double2 l = v.seg_lam_dd[2 * seg + (lower ? 0 : 1)];
+                return coef * (pc - (l.x + l.y));
+            }
+            return coef * (pc - (v.p_hi[nb] + v.p_lo[nb]));
+        };
+        double E = -q[c];
+        E += face(G.bc[0], i == 0, i > 0 ? v.xface_seg[fx] : -1, false, v.cxU[fx], G.hy, c - 1, b0 + j);
+        E += face(G.bc[1], i == G.nx - 1, i < G.nx - 1 ? v.xface_seg[fx + 1] : -1, true, v.cxL[fx + 1], G.hy, c + 1,
+                  b0 + G.ny + j);
+        E += face(G.bc[2], j == 0, j > 0 ? v.yface_seg[fy] : -1, false, v.cyU[fy], G.hx, c - G.nx,
+                  b0 + 2 * G.ny + i);
+        E += face(G.bc[3], j == G.ny - 1, j < G.ny - 1 ? v.yface_seg[fy + G.nx] : -1, true, v.cyL[fy + G.nx], G.hx,
+                  c + G.nx, b0 + 2 * G.ny + G.nx + i);
+        e = E;
+        v.rcell[c] = -e;
+    }
+    block_record_max(v.res_max + step, e);
+}
+
+__global__ void __launch_bounds__(128) residual_segments_fp64_kernel(DevView v, int step) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    double E13 = 0.0, E14 = 0.0;
+    if (t < v.nseg) {
+        const int axis = v.seg_axis[t], line = v.seg_line[t], lo = v.seg_lo[t], len = v.seg_len[t];
+        const GridDesc& G = v.grids[v.seg_grid[t]];
+        const double2 l2a = v.seg_lam_dd[2 * t], l2b = v.seg_lam_dd[2 * t + 1];
+        const double la = l2a.x + l2a.y, lb = l2b.x + l2b.y;
+        double Fa = 0.0, Fb = 0.0;
+        for (int e = 0; e < len; ++e) {
+            long long ca, cb, f;
+            double ra, rb;
+            if (axis == 0) {
+                const int j = lo + e;
+                ca = G.c0 + (long long)j * G.nx + line - 1;
+                cb = ca + 1;
+                f = G.fx0 + line + (long long)(G.nx + 1) * j;
+                ra = v.cxL[f];
+                rb = v.cxU[f];
+            } else {
+                const int i = lo + e;
+                ca = G.c0 + (long long)(line - 1) * G.nx + i;
+                cb = ca + G.nx;
+                f = G.fy0 + i + (long long)G.nx * line;
+                ra = v.cyL[f];
+                rb = v.cyU[f];
+            }
+            Fa += ra * ((v.p_hi[ca] + v.p_lo[ca]) - la);
+            Fb += rb * ((v.p_hi[cb] + v.p_lo[cb]) - lb);
+        }
+        const double length = len * (axis == 0 ? G.hy : G.hx);
+        const double two_u = 2.0 * length * (v.segU[t] + v.segU_lo[t]);
+        E13 = Fa + Fb;
+        E14 = (Fa - Fb) - two_u;
+        v.sadj[v.seg_lam_a[t]] = -0.5 * (E13 + E14);
+        v.sadj[v.seg_lam_b[t]] = -0.5 * (E13 - E14);
+    }
+    block_record_max(v.res_max + step, fmax(fabs(E13), fabs(E14)));
+}
+
 // P = (lambda^a + lambda^b) / 2, U = (lambda^b - lambda^a) / (2 beta) into the
 // refined state (set, or added in double-double), then the state's Robin
 // data lambda^a = P - beta U, lambda^b = P + beta U in double-double.
@@ -181,7 +264,7 @@ __global__ void lam_to_PU_kernel(DevView v, bool accumulate) {
 // state, each formed in double-double and rounded once.  Skeleton faces: the
 // one-sided F^a = rho^a (p_a - lambda^a), F^b = -(rho^b (p_b - lambda^b))
 // and their mean.
-template <bool kPlain>
+template <int kMode>
 __global__ void face_flux_kernel(DevView v, const double* __restrict__ bc_val, double* __restrict__ p,
                                  double* __restrict__ Fx, double* __restrict__ Fy, double* __restrict__ iface) {
     const long long nxf = v.nxface, nyf = v.nyface;
@@ -204,26 +287,30 @@ __global__ void face_flux_kernel(DevView v, const double* __restrict__ bc_val, d
     const long long ca = axis == 0 ? cb - 1 : cb - G.nx;
     const double area = axis == 0 ? G.hy : G.hx;
     const double* bv = bc_val + G.b0;
-    if (kPlain) {
-        // state without low parts (no refinement step): plain FP64
+    // kMode 1: a state without low parts (no refinement step), plain FP64;
+    // 2: a refined state rounded to FP64, plain FP64 (refinement to a
+    // tolerance above the rounding level: FP64 residuals); 0: the state's
+    // double-double pairs in double-double arithmetic
+    auto pres = [&](long long c) -> double { return kMode == 2 ? v.p_hi[c] + v.p_lo[c] : v.p_hi[c]; };
+    if (kMode != 0) {
         if (line == 0) {
             const double g = bv[axis == 0 ? k : 2 * G.ny + k];
-            F = G.bc[2 * axis] ? -(cU[fl] * (v.p_hi[cb] - g)) : -(area * g);
+            F = G.bc[2 * axis] ? -(cU[fl] * (pres(cb) - g)) : -(area * g);
         } else if (line == nline) {
             const double g = bv[axis == 0 ? G.ny + k : 2 * G.ny + G.nx + k];
-            F = G.bc[2 * axis + 1] ? cL[fl] * (v.p_hi[ca] - g) : area * g;
+            F = G.bc[2 * axis + 1] ? cL[fl] * (pres(ca) - g) : area * g;
         } else {
             const int t = axis == 0 ? v.xface_seg[fl] : v.yface_seg[fl];
             if (t >= 0) {
                 const double2 la = v.seg_lam_dd[2 * t], lb = v.seg_lam_dd[2 * t + 1];
-                const double da = cL[fl] * (v.p_hi[ca] - (la.x + la.y));
-                const double db = cU[fl] * (v.p_hi[cb] - (lb.x + lb.y));
+                const double da = cL[fl] * (pres(ca) - (la.x + la.y));
+                const double db = cU[fl] * (pres(cb) - (lb.x + lb.y));
                 fa = da;
                 fb = -db;
                 F = 0.5 * (da - db);
                 skel = true;
             } else {
-                F = cL[fl] * (v.p_hi[ca] - v.p_hi[cb]);
+                F = cL[fl] * (pres(ca) - pres(cb));
             }
         }
     } else if (line == 0) {
@@ -348,10 +435,16 @@ cudaError_t launch_compat_check(const DevView& v, const double* q, const double*
 cudaError_t launch_residual(const DevView& v, const double* q, const double* bc_val, int step,
                             cudaStream_t s) {
     const long long n = v.ncell;
-    residual_cells_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(v, q, bc_val, step);
+    if (v.res_dd)
+        residual_cells_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(v, q, bc_val, step);
+    else
+        residual_cells_fp64_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(v, q, bc_val, step);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || v.nseg == 0) return e;
-    residual_segments_kernel<<<(v.nseg + 127) / 128, 128, 0, s>>>(v, step);
+    if (v.res_dd)
+        residual_segments_kernel<<<(v.nseg + 127) / 128, 128, 0, s>>>(v, step);
+    else
+        residual_segments_fp64_kernel<<<(v.nseg + 127) / 128, 128, 0, s>>>(v, step);
     return cudaGetLastError();
 }
 
@@ -365,9 +458,11 @@ cudaError_t launch_face_fluxes(const DevView& v, const double* bc_val, double* p
                                double* Fy, double* iface, bool plain, cudaStream_t s) {
     const long long nf = v.nxface + v.nyface;
     if (plain)
-        face_flux_kernel<true><<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(v, bc_val, p, Fx, Fy, iface);
+        face_flux_kernel<1><<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(v, bc_val, p, Fx, Fy, iface);
+    else if (!v.res_dd)
+        face_flux_kernel<2><<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(v, bc_val, p, Fx, Fy, iface);
     else
-        face_flux_kernel<false><<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(v, bc_val, p, Fx, Fy, iface);
+        face_flux_kernel<0><<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(v, bc_val, p, Fx, Fy, iface);
     return cudaGetLastError();
 }
 

@@ -752,6 +752,7 @@ static int setup_impl(mrcm_ctx* c, int count, const mrcm_grid* g, const double* 
     DevView& v = c->v;
     v.mixed = precision == MRCM_MIXED ? 1 : 0;
     v.leaf32 = 0;                  // the mixed form's leaves in FP64 unless mrcm_set_mixed_leaves(1)
+    v.res_dd = v.mixed ? 0 : 1;    // FP64 residuals suffice for the mixed form's tolerance
     c->precision = precision;
     if (v.mixed) c->refine_steps = kMixedRefineDefault;
     v.alpha = P.alpha;
@@ -1023,7 +1024,7 @@ static int enqueue_solve(mrcm_ctx* c, const double* q_dev, const double* bc_val_
     {
         PhaseScope ps(c, MRCM_PHASE_FINISH);
         if (P.pure_neumann) {
-            TRYC(launch_mean_shift(v, steps == 0, s));
+            TRYC(launch_mean_shift(v, steps == 0 || !v.res_dd, s));
             launches += 2;
         }
         TRYC(launch_face_fluxes(v, bc_val_dev, p_dev, Fx_dev, Fy_dev, iface_dev, steps == 0, s));
@@ -1043,7 +1044,8 @@ int mrcm_solve(mrcm_ctx* c, const double* q_dev, const double* bc_val_dev, doubl
         --c->ev_used;
     const int ev_begin = c->ev_used;
     const void* key[8] = {q_dev, bc_val_dev, p_dev, Fx_dev, Fy_dev, iface_dev,
-                          reinterpret_cast<const void*>((long long)(c->refine_steps * 2 + c->refine_check) + 1),
+                          reinterpret_cast<const void*>(
+                              (long long)((c->refine_steps * 2 + c->refine_check) * 2 + c->v.res_dd) + 1),
                           reinterpret_cast<const void*>((long long)(c->timing ? 2 : 1) + 4 * (long long)ev_begin)};
     int launches = 0;
     if (c->solve_exec == nullptr || std::memcmp(key, c->solve_key, sizeof(key)) != 0) {
@@ -1272,6 +1274,12 @@ int mrcm_set_refinement(mrcm_ctx* c, int steps, int check) {
     if (!c || steps < 0 || steps > kMaxRefine) return MRCM_ERR_INVALID_ARG;
     c->refine_steps = steps;
     c->refine_check = check ? 1 : 0;
+    return MRCM_OK;
+}
+
+int mrcm_set_residual(mrcm_ctx* c, int dd) {
+    if (!c || (dd != 0 && dd != 1)) return MRCM_ERR_INVALID_ARG;
+    c->v.res_dd = dd;              // the solve graph is keyed by it
     return MRCM_OK;
 }
 

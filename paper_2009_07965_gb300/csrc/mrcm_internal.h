@@ -115,7 +115,8 @@ struct DevView {
     float* leafL32;     // the same in FP32 (mixed precision: leaf work in FP32)
     float* leafZ32;
     int mixed;          // 1: the mixed form (the merges of FP32 levels in FP32)
-    int leaf32;         // 1: leaf factors in FP32 (the mixed form's default; mrcm_set_mixed_leaves)
+    int leaf32;         // 1: leaf factors in FP32 (mixed form, mrcm_set_mixed_leaves)
+    int res_dd;         // 1: refinement residuals in double-double, 0: in FP64 (mrcm_set_residual)
     double* leafzb;     // particular forward solves
     double* R;          // node maps (leaves and internal nodes)
     double* rbar;       // node particular fluxes

@@ -19,7 +19,7 @@ TOL_MIXED = 1e-8
 KEYS = ("p", "Fx", "Fy", "Fa_x", "Fb_x", "Fa_y", "Fb_y")
 
 
-def _mixed_solve(prob, split=None, refine=None, stream=None, leaves32=None):
+def _mixed_solve(prob, split=None, refine=None, stream=None, leaves32=None, residual_dd=None):
     import torch
     import paper_2009_07965_gb300 as mr
     s = mr.Solver(torch.from_numpy(prob.K).cuda(), prob.Lx, prob.Ly, prob.sub, prob.seg, prob.alpha,
@@ -28,6 +28,8 @@ def _mixed_solve(prob, split=None, refine=None, stream=None, leaves32=None):
         mr.mrcm_set_mixed_split(s.ctx, split)
     if leaves32 is not None:
         mr.mrcm_set_mixed_leaves(s.ctx, leaves32)
+    if residual_dd is not None:
+        mr.mrcm_set_residual(s.ctx, residual_dd)
     if refine is not None:
         mr.mrcm_set_refinement(s.ctx, refine, check=True)
     else:
@@ -107,6 +109,8 @@ def test_mixed_with_fp64_leaves(mrcm_lib):
     o = solve_mrcm(prob, refine=3)
     _check(_mixed_solve(prob, leaves32=0, split=512), o)
     _check(_mixed_solve(prob, leaves32=0), o)
+    # double-double residuals instead of the form's FP64 ones
+    _check(_mixed_solve(prob, leaves32=0, residual_dd=1), o)
     small = inputs.config_64()
     s64 = mr.Solver(torch.from_numpy(small.K).cuda(), small.Lx, small.Ly, small.sub, small.seg, small.alpha,
                     small.bc_type)
