@@ -96,7 +96,7 @@ enum {
  *              one, mrcm_set_mixed_split) in FP32, and optionally the leaf
  *              factorisations and basis solves (mrcm_set_mixed_leaves; FP64
  *              by default); the coefficients, the solve passes, the
- *              residuals (double-double) and the fluxes in FP64; mrcm_solve
+ *              residuals and the fluxes in FP64; mrcm_solve
  *              then refines 3 times by default (mrcm_set_refinement) with
  *              FP64 residuals (mrcm_set_residual), which brings the result
  *              near the FP64 form's accuracy when the FP32 factors contract
