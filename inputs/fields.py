@@ -60,3 +60,36 @@ def lognormal_permeability(nx, ny, hx, hy, sigma2, corr, seed):
     """K = exp(sigma * xi) on an ny x nx grid (x fastest when flattened)."""
     xi, _ = gaussian_random_field(nx, ny, hx, hy, corr, seed)
     return np.exp(np.sqrt(sigma2) * xi)
+
+
+def gaussian_random_field_3d(n, h, corr, seed):
+    """Zero-mean unit-variance field on an nz x ny x nx cell-centred grid.
+
+    n = (nx, ny, nz), h = (hx, hy, hz), corr = (lx, ly, lz) correlation
+    lengths of C(d) = exp(-sqrt(sum_d (d_d / l_d)^2)); the same circulant
+    embedding as the 2D generator, one axis more.  Returns (xi, clipped)."""
+    sizes = [_fft_size(2 * n[d] + int(np.ceil(corr[d] / h[d]))) for d in range(3)]
+    r2 = 0.0
+    for d in range(3):
+        i = np.arange(sizes[d])
+        dist = np.minimum(i, sizes[d] - i) * h[d] / corr[d]
+        shape = [1, 1, 1]
+        shape[2 - d] = sizes[d]            # array axes are (z, y, x)
+        r2 = r2 + (dist ** 2).reshape(shape)
+    c = np.exp(-np.sqrt(r2))
+    lam = np.real(np.fft.fftn(c))
+    neg = lam < 0
+    clipped = float(-lam[neg].sum() / np.abs(lam).sum()) if neg.any() else 0.0
+    lam = np.where(neg, 0.0, lam)
+    rng = np.random.default_rng(seed)
+    shape = lam.shape
+    z = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    w = np.sqrt(lam / lam.size) * z
+    xi = np.real(np.fft.fftn(w))[:n[2], :n[1], :n[0]]
+    return np.ascontiguousarray(xi, dtype=np.float64), clipped
+
+
+def lognormal_permeability_3d(n, h, sigma2, corr, seed):
+    """K = exp(sigma * xi) on an nz x ny x nx grid (x fastest when flattened)."""
+    xi, _ = gaussian_random_field_3d(n, h, corr, seed)
+    return np.exp(np.sqrt(sigma2) * xi)

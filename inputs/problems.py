@@ -136,3 +136,101 @@ def ensemble_member(r, nmin=250, nmax=1000, seed0=4000):
     sigma2 = float(rng.uniform(1.0, 4.0))
     return darcy_problem(nx, ny, sigma2=sigma2, corr=0.05, seed=seed0 + r, bc="left_right", alpha=1.0,
                          Lx=1.0, Ly=1.0, name=f"ensemble{r}-{nx}x{ny}")
+
+
+@dataclass
+class Problem3D:
+    """A 3D Cartesian grid on [0, Lx] x [0, Ly] x [0, Lz] with nx x ny x nz
+    cells.  Layouts (float64, x fastest, then y, then z):
+      K, q     : (nz, ny, nx)
+      bc_type  : (x-, x+, y-, y+, z-, z+), NEUMANN or DIRICHLET
+      bc_val   : the six sides' face values concatenated in that order; the
+                 x sides hold (nz, ny) faces, the y sides (nz, nx), the z
+                 sides (ny, nx), each flattened with its first listed index
+                 slowest.
+    sub / seg are the leaf shape and the interface patch shape in cells per
+    axis (a patch on an x-normal interface spans seg[1] x seg[2] faces)."""
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    Lx: float
+    Ly: float
+    Lz: float
+    K: np.ndarray
+    q: np.ndarray
+    bc_type: tuple
+    bc_val: np.ndarray
+    sub: tuple = (16, 16, 16)
+    seg: tuple = (4, 4, 4)
+    alpha: float = 1.0
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n(self):
+        return (self.nx, self.ny, self.nz)
+
+    @property
+    def h(self):
+        return (self.Lx / self.nx, self.Ly / self.ny, self.Lz / self.nz)
+
+    @property
+    def pure_neumann(self):
+        return all(t == NEUMANN for t in self.bc_type)
+
+    def side_shape(self, side):
+        """Face array shape of a boundary side (see bc_val)."""
+        nx, ny, nz = self.n
+        return ((nz, ny), (nz, ny), (nz, nx), (nz, nx), (ny, nx), (ny, nx))[side]
+
+    def bc_slices(self):
+        out, off = {}, 0
+        for s in range(6):
+            a, b = self.side_shape(s)
+            out[s] = slice(off, off + a * b)
+            off += a * b
+        return out
+
+
+def darcy_problem_3d(nx, ny, nz, *, sigma2=2.0, corr=(0.2, 0.2, 0.05), seed=0,
+                     bc="left_right", alpha=1.0, sub=(16, 16, 16), seg=(4, 4, 4),
+                     L=None, K=None, name=None):
+    """bc = "left_right": p = 1 on x = 0, p = 0 on x = Lx, no-flow on the
+    other four sides, no source (the paper's 3D setup, Section 5.1).
+    bc = "quarter_five_spot": no-flow everywhere, q = +1 in cell (0, 0, 0)
+    and -1 in the opposite corner cell.  L defaults to cubic cells with
+    Lx = 1.  sigma2 = 0 gives K = 1."""
+    from .fields import lognormal_permeability_3d
+    if L is None:
+        L = (1.0, ny / nx, nz / nx)
+    h = (L[0] / nx, L[1] / ny, L[2] / nz)
+    if K is None:
+        if sigma2 == 0.0:
+            K = np.ones((nz, ny, nx))
+        else:
+            K = lognormal_permeability_3d((nx, ny, nz), h, sigma2, corr, seed)
+    K = np.ascontiguousarray(np.asarray(K, dtype=np.float64).reshape(nz, ny, nx))
+    q = np.zeros((nz, ny, nx))
+    nb = 2 * (ny * nz + nx * nz + nx * ny)
+    val = np.zeros(nb)
+    if bc == "left_right":
+        types = (DIRICHLET, DIRICHLET, NEUMANN, NEUMANN, NEUMANN, NEUMANN)
+        val[0:ny * nz] = 1.0
+    elif bc == "quarter_five_spot":
+        types = (NEUMANN,) * 6
+        q[0, 0, 0] = 1.0
+        q[nz - 1, ny - 1, nx - 1] = -1.0
+    else:
+        raise ValueError(f"unknown bc preset {bc!r}")
+    return Problem3D(name or f"{nx}x{ny}x{nz}-{bc}", nx, ny, nz, L[0], L[1], L[2], K, q, types,
+                     val, tuple(sub), tuple(seg), float(alpha),
+                     dict(sigma2=sigma2, corr=tuple(corr), seed=seed, bc=bc))
+
+
+def config_3d(nx=256, ny=256, nz=64):
+    """256 x 256 x 64 cubic cells on [0,1] x [0,1] x [0,0.25], log-normal K
+    with sigma^2 = 2 and correlation lengths (0.2, 0.2, 0.05), p = 1 at
+    x = 0 / p = 0 at x = 1, no-flow elsewhere; 16^3 leaves, 4 x 4 face
+    patches, alpha = 1."""
+    return darcy_problem_3d(nx, ny, nz, sigma2=2.0, corr=(0.2, 0.2, 0.05), seed=3000,
+                            bc="left_right", alpha=1.0, name=f"box{nx}x{ny}x{nz}-lr")

@@ -111,6 +111,14 @@ class LeafProblem:
         self.neu_sign = np.array([f[3] for f in fn])
         self._lu = None
 
+    def block(self, arr):
+        """The leaf's block of a cell array (None passes through)."""
+        return None if arr is None else arr[self.j0:self.j1, self.i0:self.i1]
+
+    def place(self, out, vals):
+        """Writes the leaf's cell values into a cell array."""
+        out[self.j0:self.j1, self.i0:self.i1] = np.asarray(vals).reshape(self.h, self.w)
+
     def solve(self, lam, with_data, source=None, want_faces=True):
         """Solve the local problem for Robin data lam (one value per segment
         of the leaf, in self.segs order) with or without the source and

@@ -64,11 +64,15 @@ class GlobalMRCM:
     """Steps 1-3 for arbitrary data: source per cell, external boundary data
     on or off, and right-hand sides of the Eq. (13.2) / (14.2) rows."""
 
-    def __init__(self, prob):
+    def __init__(self, prob, dec=None, leaf_cls=None):
+        # dec / leaf_cls: another decomposition and local problem with the
+        # same interface (the 3D ones of oracle.mrcm3d); the assembly below
+        # only sees segment lists
         self.prob = prob
-        self.dec = dec = Decomposition(prob)
+        self.dec = dec = dec if dec is not None else Decomposition(prob)
         self.nseg = nseg = len(dec.segments)
-        self.leaves = [LeafProblem(dec, lf["id"]) for lf in dec.leaves]
+        leaf_cls = leaf_cls or LeafProblem
+        self.leaves = [leaf_cls(dec, lf["id"]) for lf in dec.leaves]
         self.lams, self.traces = [], []
         rows, cols, vals = [], [], []
         for lp in self.leaves:
@@ -108,7 +112,7 @@ class GlobalMRCM:
         parts = []
         for lp in self.leaves:
             i = lp.leaf["id"]
-            src = None if source is None else source[lp.j0:lp.j1, lp.i0:lp.i1]
+            src = lp.block(source)
             _, part, _ = lp.solve(np.zeros(len(lp.segs)), with_data=with_bc, source=src,
                                   want_faces=False)
             parts.append(src)
@@ -126,13 +130,13 @@ class GlobalMRCM:
         X = self.lu.solve(b) if nseg > 0 else np.zeros(0)
         U, P = X[:nseg], X[nseg:]
         # Eq. (final): pressures as the MMBF combination plus the particular part
-        p = np.zeros((prob.ny, prob.nx))
+        p = np.zeros(prob.K.shape)
         for lp, lam, src in zip(self.leaves, self.lams, parts):
             m = len(lp.segs)
             coef = np.array([U[t] for t in lp.segs] + [P[t] for t in lp.segs])
             ph, _, _ = lp.solve(lam, with_data=False, want_faces=False)
             pp, _, _ = lp.solve(np.zeros(m), with_data=with_bc, source=src, want_faces=False)
-            p[lp.j0:lp.j1, lp.i0:lp.i1] = (ph @ coef + pp).reshape(lp.h, lp.w)
+            lp.place(p, ph @ coef + pp)
         return p, U, P
 
 
