@@ -13,7 +13,7 @@ from .binding import (mrcm_setup, mrcm_setup_batch, mrcm_plan_query, mrcm_set_pe
                       mrcm_cnn_conv_forward, mrcm_cnn_conv_wgrad, mrcm_cnn_flip_weights, mrcm_cnn_relu_grad,
                       mrcm_cnn_mse_grad, mrcm_cnn_adam, PROBES, MrcmError, PHASES, PHASE_KERNELS,
                       EXPORTS, LIB_PATH)
-from .solver import Solver, BatchSolver
+from .solver import Solver, Solver3D, BatchSolver
 
 __all__ = ["mrcm_setup", "mrcm_setup_batch", "mrcm_plan_query", "mrcm_set_permeability", "mrcm_build_basis", "mrcm_solve", "mrcm_query",
            "mrcm_node_info", "mrcm_node_segments", "mrcm_segment_info", "mrcm_node_operator",
@@ -23,4 +23,4 @@ __all__ = ["mrcm_setup", "mrcm_setup_batch", "mrcm_plan_query", "mrcm_set_permea
            "mrcm_group_times", "mrcm_check_reciprocal", "mrcm_set_wait_limit", "mrcm_probe_peak", "mrcm_set_mixed_split", "mrcm_set_mixed_leaves", "mrcm_set_root_form", "mrcm_autotune", "mrcm_tune_info",
            "mrcm_interior_leaves", "mrcm_leaf_fields", "mrcm_leaf_patches", "mrcm_leaf_gate", "mrcm_leaf_apply",
            "mrcm_cnn_conv_forward", "mrcm_cnn_conv_wgrad", "mrcm_cnn_flip_weights", "mrcm_cnn_relu_grad",
-           "mrcm_cnn_mse_grad", "mrcm_cnn_adam", "PROBES", "MrcmError", "PHASE_KERNELS", "PHASES", "EXPORTS", "LIB_PATH", "Solver", "BatchSolver"]
+           "mrcm_cnn_mse_grad", "mrcm_cnn_adam", "PROBES", "MrcmError", "PHASE_KERNELS", "PHASES", "EXPORTS", "LIB_PATH", "Solver", "Solver3D", "BatchSolver"]

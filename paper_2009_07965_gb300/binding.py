@@ -184,7 +184,10 @@ def _ints(vals, n):
 
 def mrcm_setup(n, L, K, sub_cells=(16, 16), seg_cells=(4, 4), alpha=1.0,
                bc_type=(1, 1, 0, 0), precision=MRCM_FP64, stream=0):
-    g = mrcm_grid(2, (ctypes.c_int * 3)(n[0], n[1], 1), (ctypes.c_double * 3)(L[0], L[1], 1.0))
+    """n = (nx, ny) or (nx, ny, nz) cells, L the physical size per axis."""
+    dim = len(n)
+    g = mrcm_grid(dim, (ctypes.c_int * 3)(n[0], n[1], n[2] if dim == 3 else 1),
+                  (ctypes.c_double * 3)(L[0], L[1], L[2] if dim == 3 else 1.0))
     ctx = ctypes.c_void_p()
     _check(_lib().mrcm_setup(ctypes.byref(ctx), ctypes.byref(g), _ptr(K), _ints(sub_cells, 3),
                              _ints(seg_cells, 3), float(alpha), _ints(bc_type, 6), int(precision),
@@ -212,7 +215,9 @@ def mrcm_setup_batch(ns, Ls, bc_types, K, sub_cells=(16, 16), seg_cells=(4, 4), 
 
 
 def mrcm_plan_query(n, L, sub_cells, seg_cells, bc_type, what):
-    g = mrcm_grid(2, (ctypes.c_int * 3)(n[0], n[1], 1), (ctypes.c_double * 3)(L[0], L[1], 1.0))
+    dim = len(n)
+    g = mrcm_grid(dim, (ctypes.c_int * 3)(n[0], n[1], n[2] if dim == 3 else 1),
+                  (ctypes.c_double * 3)(L[0], L[1], L[2] if dim == 3 else 1.0))
     v = ctypes.c_longlong()
     key = Q[what] if isinstance(what, str) else int(what)
     _check(_lib().mrcm_plan_query(ctypes.byref(g), _ints(sub_cells, 3), _ints(seg_cells, 3),

@@ -15,7 +15,8 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libmrcm.so")
 BUILD_DIR = os.path.join(ROOT, "_build")
 SOURCES = ["mrcm_api.cu", "kernels_setup.cu", "kernels_leaf.cu", "kernels_merge.cu",
-           "kernels_noalloc.cu", "kernels_refine.cu", "kernels_probe.cu", "kernels_surrogate.cu"]
+           "kernels_noalloc.cu", "kernels_refine.cu", "kernels_probe.cu", "kernels_surrogate.cu",
+           "kernels_3d.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 

@@ -1,0 +1,483 @@
+// The 3D path: Robin and face coefficients, the leaf blocks' local Robin
+// problems and their solve-phase passes, and the face fluxes.
+//
+// arXiv 2009.07965 runs its experiments in 3D (Section 5.1): box subdomains,
+// rectangular interfaces cut into patches of H-bar (Section 4).  The Robin
+// coefficient of a segment t is Eq. (robin.beta) with K_eff from Eq.
+// (permeff): Keff_t = mean over the faces of t of 2 K_a K_b / (K_a + K_b),
+// beta_t = alpha Hbar_t / Keff_t with Hbar_t = sqrt(|t|) (the patch side of
+// a square patch), and the Robin coupling D_t = |t| / (2 beta_t).
+//
+// Leaves.  The grid is tiled by blocks of the patch shape (at most 64
+// cells), so a patch between two subdomains is exactly the shared side of
+// two blocks.  Inside a subdomain every face between two blocks is its own
+// segment: with one unknown pair per fine face the Robin coupling reproduces
+// the two-point flux exactly, whatever beta (the one-face-segment property of
+// Eqs. 11.2-14.2), so merging the blocks of a subdomain solves its local
+// Robin problems exactly -- a nested dissection of the subdomain by the same
+// merges that couple subdomains.  A block's local problem (Eqs. 11.2-12.2,
+// lumped RT0) is p = A^-1 (bbar + B lambda), its Robin-to-flux map
+// R = B^T A^-1 B - W, W_s = sum of rho over the faces of s; with the
+// Cholesky factor A = L L^T and Z = L^-1 B: R = Z^T Z - W, rbar = Z^T L^-1
+// bbar and p = L^-T (L^-1 bbar + Z lambda).
+//
+// Mapping: one CTA per block for the factorisation (the dense 64 x 64 A and
+// Z in shared memory), one warp per block for the solve-phase passes.
+#include "mrcm_internal.h"
+
+#include <algorithm>
+
+namespace mrcm {
+namespace {
+
+constexpr int kBuild3Threads = 128;
+constexpr int kSolve3Warps = 4;          // blocks (one warp each) per CTA in the solve passes
+
+__device__ __forceinline__ long long cell3(const Grid3& G, int i, int j, int k) {
+    return ((long long)k * G.ny + j) * G.nx + i;
+}
+__device__ __forceinline__ long long xface3(const Grid3& G, int i, int j, int k) {
+    return ((long long)k * G.ny + j) * (G.nx + 1) + i;
+}
+__device__ __forceinline__ long long yface3(const Grid3& G, int i, int j, int k) {
+    return ((long long)k * (G.ny + 1) + j) * G.nx + i;
+}
+__device__ __forceinline__ long long zface3(const Grid3& G, int i, int j, int k) {
+    return ((long long)k * G.ny + j) * G.nx + i;
+}
+__device__ __forceinline__ double area3(const Grid3& G, int d) {
+    return d == 0 ? G.hy * G.hz : (d == 1 ? G.hx * G.hz : G.hx * G.hy);
+}
+__device__ __forceinline__ double hnorm3(const Grid3& G, int d) {
+    return d == 0 ? G.hx : (d == 1 ? G.hy : G.hz);
+}
+
+// beta_t and D_t of every segment (faces: v outer along the second
+// tangential axis, u inner along the first).
+__global__ void seg_beta3_kernel(DevView v) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= v.nseg) return;
+    const Grid3& G = v.g3;
+    const int d = v.seg_axis[t], line = v.seg_line[t];
+    const int lo1 = v.seg_lo[t], len1 = v.seg_len[t], lo2 = v.seg_lo2[t], len2 = v.seg_len2[t];
+    const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+    double sum = 0.0;
+    for (int w = lo2; w < lo2 + len2; ++w)
+        for (int u = lo1; u < lo1 + len1; ++u) {
+            int pos[3];
+            pos[d] = line; pos[t1] = u; pos[t2] = w;
+            const double kb = v.K[cell3(G, pos[0], pos[1], pos[2])];
+            pos[d] = line - 1;
+            const double ka = v.K[cell3(G, pos[0], pos[1], pos[2])];
+            sum += 2.0 * ka * kb / (ka + kb);
+        }
+    const int nf = len1 * len2;
+    const double keff = sum / nf;
+    const double area = nf * area3(G, d);
+    const double beta = v.alpha * sqrt(area) / keff;
+    v.seg_beta[t] = beta;
+    v.seg_D[t] = area / (2.0 * beta);
+}
+
+// Face coefficients seen from the lower (cL) and the upper (cU) cell:
+// interior T = |e| / (r_a + r_b), skeleton rho = |e| / (r_c + beta_t),
+// Dirichlet tau = 2 K_c |e| / h, Neumann 0 (r_c = h / (2 K_c)).
+__global__ void face_coef3_kernel(DevView v) {
+    const Grid3& G = v.g3;
+    const long long total = v.nxface + v.nyface + v.nzface;
+    for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < total;
+         f += (long long)gridDim.x * blockDim.x) {
+        int d, i, j, k;
+        long long fl;
+        double *cL, *cU;
+        const int* fseg;
+        if (f < v.nxface) {
+            d = 0; fl = f; cL = v.cxL; cU = v.cxU; fseg = v.xface_seg;
+            i = (int)(fl % (G.nx + 1)); const long long r = fl / (G.nx + 1); j = (int)(r % G.ny); k = (int)(r / G.ny);
+        } else if (f < v.nxface + v.nyface) {
+            d = 1; fl = f - v.nxface; cL = v.cyL; cU = v.cyU; fseg = v.yface_seg;
+            i = (int)(fl % G.nx); const long long r = fl / G.nx; j = (int)(r % (G.ny + 1)); k = (int)(r / (G.ny + 1));
+        } else {
+            d = 2; fl = f - v.nxface - v.nyface; cL = v.czL; cU = v.czU; fseg = v.zface_seg;
+            i = (int)(fl % G.nx); const long long r = fl / G.nx; j = (int)(r % G.ny); k = (int)(r / G.ny);
+        }
+        const int n_d = d == 0 ? G.nx : (d == 1 ? G.ny : G.nz);
+        const int pos = d == 0 ? i : (d == 1 ? j : k);
+        const double area = area3(G, d), hn = hnorm3(G, d);
+        const long long cu = pos < n_d ? cell3(G, i, j, k) : -1;
+        const long long cl = pos > 0 ? cell3(G, i - (d == 0), j - (d == 1), k - (d == 2)) : -1;
+        double vl = 0.0, vu = 0.0;
+        if (cl < 0) {
+            if (G.bc[2 * d]) vu = 2.0 * v.K[cu] * area / hn;
+        } else if (cu < 0) {
+            if (G.bc[2 * d + 1]) vl = 2.0 * v.K[cl] * area / hn;
+        } else {
+            const double ra = hn / (2.0 * v.K[cl]), rb = hn / (2.0 * v.K[cu]);
+            const int t = fseg[fl];
+            if (t >= 0) {
+                const double beta = v.seg_beta[t];
+                vl = area / (ra + beta);
+                vu = area / (rb + beta);
+            } else {
+                vl = vu = area / (ra + rb);
+            }
+        }
+        cL[fl] = vl;
+        cU[fl] = vu;
+    }
+}
+
+// The six faces of local cell (ii, jj, kk) of block B: the coefficient seen
+// from the cell, whether the face couples to a cell of the block, and the
+// local segment of a skeleton face (-1 otherwise).
+struct Face3Info {
+    double c;
+    int nb;       // local neighbour cell, -1 when the face is not inside the block
+    int seg;      // local segment, -1 when not a skeleton face
+    int bside;    // domain boundary side (0..5), -1 otherwise
+};
+
+__device__ __forceinline__ Face3Info block_face(const DevView& v, const LeafDesc3& B, int ii, int jj, int kk,
+                                                int side) {
+    const Grid3& G = v.g3;
+    const int d = side >> 1, up = side & 1;
+    const int loc[3] = {ii, jj, kk};
+    const int w0 = B.w[0], w1 = B.w[1];
+    const int gi = B.i0 + ii, gj = B.j0 + jj, gk = B.k0 + kk;
+    long long f;
+    const double* cf;
+    if (d == 0) {
+        f = xface3(G, gi + up, gj, gk);
+        cf = up ? v.cxL : v.cxU;
+    } else if (d == 1) {
+        f = yface3(G, gi, gj + up, gk);
+        cf = up ? v.cyL : v.cyU;
+    } else {
+        f = zface3(G, gi, gj, gk + up);
+        cf = up ? v.czL : v.czU;
+    }
+    Face3Info r;
+    r.c = cf[f];
+    r.nb = -1;
+    r.seg = -1;
+    r.bside = -1;
+    const int p = loc[d] + (up ? 1 : -1);
+    if (p >= 0 && p < B.w[d]) {
+        int q[3] = {ii, jj, kk};
+        q[d] = p;
+        r.nb = (q[2] * w1 + q[1]) * w0 + q[0];
+        return r;
+    }
+    if (B.side_off[side] < 0) {
+        r.bside = side;
+        return r;
+    }
+    // face index on the side: v outer along the second tangential axis
+    const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+    r.seg = B.side_off[side] + (B.side_fine[side] ? loc[t2] * B.w[t1] + loc[t1] : 0);
+    return r;
+}
+
+struct Leaf3Smem {
+    double A[kLeaf3Cells][kLeaf3Cells + 1];   // A, then its Cholesky factor (lower)
+    double Z[kLeaf3Segs][kLeaf3Cells + 1];    // B, then Z = L^-1 B (one row per segment)
+    double W[kLeaf3Segs];
+    int start[kLeaf3Segs];                    // first nonzero row of each column of B
+};
+
+__global__ void __launch_bounds__(kBuild3Threads) leaf3_build_kernel(DevView v) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Leaf3Smem& S = *reinterpret_cast<Leaf3Smem*>(smem_raw);
+    const int leaf = blockIdx.x;
+    const int tid = threadIdx.x;
+    const LeafDesc3 B = v.leaves3[leaf];
+    const int n = B.w[0] * B.w[1] * B.w[2], m = B.m;
+    for (int e = tid; e < kLeaf3Cells * (kLeaf3Cells + 1); e += kBuild3Threads) (&S.A[0][0])[e] = 0.0;
+    for (int e = tid; e < kLeaf3Segs * (kLeaf3Cells + 1); e += kBuild3Threads) (&S.Z[0][0])[e] = 0.0;
+    __syncthreads();
+    // assembly, one cell per thread: diagonal in the order x-, x+, y-, y+, z-, z+
+    for (int c = tid; c < n; c += kBuild3Threads) {
+        const int ii = c % B.w[0], jj = (c / B.w[0]) % B.w[1], kk = c / (B.w[0] * B.w[1]);
+        double diag = 0.0;
+        for (int side = 0; side < 6; ++side) {
+            const Face3Info F = block_face(v, B, ii, jj, kk, side);
+            diag += F.c;
+            if (F.nb >= 0) S.A[c][F.nb] = -F.c;
+            else if (F.seg >= 0) S.Z[F.seg][c] = F.c;
+        }
+        S.A[c][c] = diag;
+    }
+    __syncthreads();
+    for (int s = tid; s < m; s += kBuild3Threads) {
+        double w = 0.0;
+        int st = n;
+        for (int c = 0; c < n; ++c) {
+            w += S.Z[s][c];
+            if (st == n && S.Z[s][c] != 0.0) st = c;
+        }
+        S.W[s] = w;
+        S.start[s] = st;
+    }
+    // Cholesky A = L L^T, right-looking over the lower triangle
+    bool bad = false;
+    for (int k = 0; k < n; ++k) {
+        __syncthreads();
+        const double akk = S.A[k][k];
+        bad |= !(akk > 0.0);
+        const double lkk = sqrt(akk), rl = 1.0 / lkk;
+        const int len = n - 1 - k;
+        for (int e = tid; e < len * len; e += kBuild3Threads) {
+            const int r = e / len, q = e % len;
+            if (q <= r) {
+                const int i = k + 1 + r, j = k + 1 + q;
+                S.A[i][j] -= S.A[i][k] * S.A[j][k] / akk;
+            }
+        }
+        __syncthreads();
+        if (tid == 0) S.A[k][k] = lkk;
+        for (int i = k + 1 + tid; i < n; i += kBuild3Threads) S.A[i][k] *= rl;
+    }
+    __syncthreads();
+    if (bad && tid == 0) atomicOr(v.status, kStatusSingular);
+    // Z = L^-1 B, one column (segment) per thread, from its first nonzero row
+    for (int s = tid; s < m; s += kBuild3Threads) {
+        for (int k = S.start[s]; k < n; ++k) {
+            const double zk = S.Z[s][k] / S.A[k][k];
+            S.Z[s][k] = zk;
+            for (int i = k + 1; i < n; ++i) S.Z[s][i] = fma(-S.A[i][k], zk, S.Z[s][i]);
+        }
+    }
+    __syncthreads();
+    // R = Z^T Z - W (symmetric, both halves written)
+    double* Rg = v.R + B.R_off;
+    const int npair = m * (m + 1) / 2;
+    for (int e = tid; e < npair; e += kBuild3Threads) {
+        int r = (int)((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
+        while ((r + 1) * (r + 2) / 2 <= e) ++r;
+        while (r * (r + 1) / 2 > e) --r;
+        const int q = e - r * (r + 1) / 2;
+        const int k0 = max(S.start[r], S.start[q]);
+        double acc = 0.0;
+        for (int k = k0; k < n; ++k) acc = fma(S.Z[r][k], S.Z[q][k], acc);
+        if (r == q) acc -= S.W[r];
+        Rg[(long long)r * m + q] = acc;
+        Rg[(long long)q * m + r] = acc;
+    }
+    // the factor (column-major, 1 / L_kk on the diagonal) and Z for the solve
+    double* Lg = v.leafL + B.L_off;
+    for (int e = tid; e < n * n; e += kBuild3Threads) {
+        const int k = e / n, i = e % n;      // column k, row i
+        Lg[e] = i > k ? S.A[i][k] : (i == k ? 1.0 / S.A[k][k] : 0.0);
+    }
+    double* Zg = v.leafZ + B.Z_off;
+    for (int e = tid; e < m * n; e += kBuild3Threads) Zg[e] = S.Z[e / n][e % n];
+}
+
+// Boundary value of the face of global cell (gi, gj, gk) on domain side s.
+__device__ __forceinline__ double bc_value3(const Grid3& G, const double* bc_val, int s, int gi, int gj, int gk) {
+    const long long sx = (long long)G.ny * G.nz, sy = (long long)G.nx * G.nz, sz = (long long)G.nx * G.ny;
+    long long o;
+    if (s < 2) o = (s ? sx : 0) + (long long)gk * G.ny + gj;
+    else if (s < 4) o = 2 * sx + (s == 3 ? sy : 0) + (long long)gk * G.nx + gi;
+    else o = 2 * sx + 2 * sy + (s == 5 ? sz : 0) + (long long)gj * G.nx + gi;
+    return bc_val[o];
+}
+
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// Particular solve of each block: zbar = L^-1 bbar (bbar: the source and
+// the external boundary data, Eqs. addu / addp) and rbar = Z^T zbar.
+__global__ void __launch_bounds__(32 * kSolve3Warps)
+leaf3_particular_kernel(DevView v, const double* __restrict__ q, const double* __restrict__ bc_val) {
+    __shared__ double ys[kSolve3Warps][kLeaf3Cells];
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    const int leaf = blockIdx.x * kSolve3Warps + wi;
+    if (leaf >= v.nleaf) return;            // uniform over the warp
+    const LeafDesc3 B = v.leaves3[leaf];
+    const Grid3& G = v.g3;
+    const int n = B.w[0] * B.w[1] * B.w[2], m = B.m;
+    const double* Lg = v.leafL + B.L_off;
+    const double* Zg = v.leafZ + B.Z_off;
+    double* y = ys[wi];
+    for (int c = lane; c < n; c += 32) {
+        const int ii = c % B.w[0], jj = (c / B.w[0]) % B.w[1], kk = c / (B.w[0] * B.w[1]);
+        const int gi = B.i0 + ii, gj = B.j0 + jj, gk = B.k0 + kk;
+        double b = q[cell3(G, gi, gj, gk)];
+        for (int side = 0; side < 6; ++side) {
+            const Face3Info F = block_face(v, B, ii, jj, kk, side);
+            if (F.bside < 0) continue;
+            const double g = bc_value3(G, bc_val, side, gi, gj, gk);
+            if (G.bc[side]) b += F.c * g;
+            else b -= area3(G, side >> 1) * g;
+        }
+        y[c] = b;
+    }
+    __syncwarp();
+    for (int k = 0; k < n; ++k) {
+        const double yk = y[k] * Lg[(long long)k * n + k];
+        __syncwarp();
+        if (lane == 0) y[k] = yk;
+        for (int i = k + 1 + lane; i < n; i += 32) y[i] = fma(-Lg[(long long)k * n + i], yk, y[i]);
+        __syncwarp();
+    }
+    double* zb = v.leafzb + B.zb_off;
+    for (int c = lane; c < n; c += 32) zb[c] = y[c];
+    double* rb = v.rbar + B.r_off;
+    for (int s = 0; s < m; ++s) {
+        double acc = 0.0;
+        for (int k = lane; k < n; k += 32) acc = fma(Zg[(long long)s * n + k], y[k], acc);
+        acc = warp_sum(acc);
+        if (lane == 0) rb[s] = acc;
+    }
+}
+
+// Final pressures of each block: p = L^-T (zbar + Z lambda), written into the
+// cell state (p_hi, p_lo = 0).
+__global__ void __launch_bounds__(32 * kSolve3Warps) leaf3_pressure_kernel(DevView v) {
+    __shared__ double ys[kSolve3Warps][kLeaf3Cells];
+    __shared__ double ls[kSolve3Warps][kLeaf3Segs];
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    const int leaf = blockIdx.x * kSolve3Warps + wi;
+    if (leaf >= v.nleaf) return;
+    const LeafDesc3 B = v.leaves3[leaf];
+    const Grid3& G = v.g3;
+    const int n = B.w[0] * B.w[1] * B.w[2], m = B.m;
+    const double* Lg = v.leafL + B.L_off;
+    const double* Zg = v.leafZ + B.Z_off;
+    const double* zb = v.leafzb + B.zb_off;
+    double* y = ys[wi];
+    double* lam = ls[wi];
+    for (int s = lane; s < m; s += 32) lam[s] = v.lam[B.r_off + s];
+    __syncwarp();
+    for (int c = lane; c < n; c += 32) {
+        double acc = zb[c];
+        for (int s = 0; s < m; ++s) acc = fma(Zg[(long long)s * n + c], lam[s], acc);
+        y[c] = acc;
+    }
+    __syncwarp();
+    // L^T p = y, left-looking from the last row: p_k = (y_k - sum_{i>k} L_ik p_i) / L_kk
+    for (int k = n - 1; k >= 0; --k) {
+        double part = 0.0;
+        for (int i = k + 1 + lane; i < n; i += 32) part = fma(Lg[(long long)k * n + i], y[i], part);
+        part = warp_sum(part);
+        const double pk = (y[k] - part) * Lg[(long long)k * n + k];
+        __syncwarp();
+        if (lane == 0) y[k] = pk;
+        __syncwarp();
+    }
+    for (int c = lane; c < n; c += 32) {
+        const int ii = c % B.w[0], jj = (c / B.w[0]) % B.w[1], kk = c / (B.w[0] * B.w[1]);
+        const long long gc = cell3(G, B.i0 + ii, B.j0 + jj, B.k0 + kk);
+        v.p_hi[gc] = y[c];
+        v.p_lo[gc] = 0.0;
+    }
+}
+
+// Cell pressures and face fluxes (+axis sign); on the skeleton the mean of
+// the two one-sided values rho (p_c - lambda) of the blocks on either side.
+__global__ void face_flux3_kernel(DevView v, const double* __restrict__ bc_val, double* __restrict__ p,
+                                  double* __restrict__ Fx, double* __restrict__ Fy, double* __restrict__ Fz) {
+    const Grid3& G = v.g3;
+    const long long nf = v.nxface + v.nyface + v.nzface;
+    for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < nf + v.ncell;
+         f += (long long)gridDim.x * blockDim.x) {
+        if (f >= nf) {
+            const long long c = f - nf;
+            p[c] = v.p_hi[c] + v.p_lo[c];
+            continue;
+        }
+        int d, i, j, k;
+        long long fl;
+        const double *cL, *cU;
+        const int* fseg;
+        double* out;
+        if (f < v.nxface) {
+            d = 0; fl = f; cL = v.cxL; cU = v.cxU; fseg = v.xface_seg; out = Fx;
+            i = (int)(fl % (G.nx + 1)); const long long r = fl / (G.nx + 1); j = (int)(r % G.ny); k = (int)(r / G.ny);
+        } else if (f < v.nxface + v.nyface) {
+            d = 1; fl = f - v.nxface; cL = v.cyL; cU = v.cyU; fseg = v.yface_seg; out = Fy;
+            i = (int)(fl % G.nx); const long long r = fl / G.nx; j = (int)(r % (G.ny + 1)); k = (int)(r / (G.ny + 1));
+        } else {
+            d = 2; fl = f - v.nxface - v.nyface; cL = v.czL; cU = v.czU; fseg = v.zface_seg; out = Fz;
+            i = (int)(fl % G.nx); const long long r = fl / G.nx; j = (int)(r % G.ny); k = (int)(r / G.ny);
+        }
+        const int n_d = d == 0 ? G.nx : (d == 1 ? G.ny : G.nz);
+        const int pos = d == 0 ? i : (d == 1 ? j : k);
+        const double area = area3(G, d);
+        double F;
+        if (pos == 0) {
+            const double pb = v.p_hi[cell3(G, i, j, k)] + v.p_lo[cell3(G, i, j, k)];
+            const double g = bc_value3(G, bc_val, 2 * d, i, j, k);
+            F = G.bc[2 * d] ? -(cU[fl] * (pb - g)) : -(area * g);
+        } else {
+            const int ai = i - (d == 0), aj = j - (d == 1), ak = k - (d == 2);
+            const long long ca = cell3(G, ai, aj, ak);
+            const double pa = v.p_hi[ca] + v.p_lo[ca];
+            if (pos == n_d) {
+                const double g = bc_value3(G, bc_val, 2 * d + 1, ai, aj, ak);
+                F = G.bc[2 * d + 1] ? cL[fl] * (pa - g) : area * g;
+            } else {
+                const long long cb = cell3(G, i, j, k);
+                const double pb = v.p_hi[cb] + v.p_lo[cb];
+                const int t = fseg[fl];
+                if (t >= 0) {
+                    const double fa = cL[fl] * (pa - v.lam[v.seg_lam_a[t]]);
+                    const double fb = -(cU[fl] * (pb - v.lam[v.seg_lam_b[t]]));
+                    F = 0.5 * (fa + fb);
+                } else {
+                    F = cL[fl] * (pa - pb);
+                }
+            }
+        }
+        out[fl] = F;
+    }
+}
+
+inline unsigned grid_for(long long n, int threads) {
+    long long b = (n + threads - 1) / threads;
+    if (b > 152LL * 16) b = 152LL * 16;
+    return (unsigned)std::max(b, 1LL);
+}
+
+}  // namespace
+
+cudaError_t launch_coef3(const DevView& v, cudaStream_t s) {
+    if (v.nseg > 0) seg_beta3_kernel<<<(v.nseg + 127) / 128, 128, 0, s>>>(v);
+    face_coef3_kernel<<<grid_for(v.nxface + v.nyface + v.nzface, 256), 256, 0, s>>>(v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_leaf3_build(const DevView& v, cudaStream_t s) {
+    const int bytes = (int)sizeof(Leaf3Smem);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(leaf3_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    leaf3_build_kernel<<<v.nleaf, kBuild3Threads, bytes, s>>>(v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_leaf3_particular(const DevView& v, const double* q, const double* bc_val, cudaStream_t s) {
+    leaf3_particular_kernel<<<(v.nleaf + kSolve3Warps - 1) / kSolve3Warps, 32 * kSolve3Warps, 0, s>>>(v, q, bc_val);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_leaf3_pressure(const DevView& v, cudaStream_t s) {
+    leaf3_pressure_kernel<<<(v.nleaf + kSolve3Warps - 1) / kSolve3Warps, 32 * kSolve3Warps, 0, s>>>(v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_face_fluxes3(const DevView& v, const double* bc_val, double* p, double* Fx, double* Fy,
+                                double* Fz, cudaStream_t s) {
+    const long long n = v.nxface + v.nyface + v.nzface + v.ncell;
+    face_flux3_kernel<<<grid_for(n, 256), 256, 0, s>>>(v, bc_val, p, Fx, Fy, Fz);
+    return cudaGetLastError();
+}
+
+}  // namespace mrcm

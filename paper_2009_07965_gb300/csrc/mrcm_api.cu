@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <map>
 #include <unordered_map>
 #include <vector>
 
@@ -73,9 +74,75 @@ struct Plan {
     double root_build[2][MRCM_PHASE_COUNT] = {}, root_pass[2][MRCM_PHASE_COUNT] = {};
     double root_merge[2] = {}, root_solve[2] = {}, root_model_sweep[2] = {};
     double residual_flops = 0, finish_flops = 0;
+    // 3D contexts: the grid, the blocks (leaves), the second tangential
+    // extent of each segment and the z-face map
+    int dim = 2;
+    Grid3 g3{};
+    int sz = 0, gz = 0;
+    std::vector<LeafDesc3> leaves3;
+    std::vector<int> seg_lo2, seg_len2, zface_seg;
+    long long nzface = 0;
 };
 
 inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+// A tree node merging c1 and c2 (c1 on side a of every gamma segment): gamma =
+// the segments the two share; the node's outer segments are c1's others,
+// then c2's, and the node map records where each sits in the children.
+int add_merge_node(Plan& P, int c1, int c2, const int box[4]) {
+    Plan::Node nd;
+    for (int k = 0; k < 4; ++k) nd.box[k] = box[k];
+    nd.c1 = c1; nd.c2 = c2;
+    nd.height = 1 + std::max(P.nodes[c1].height, P.nodes[c2].height);
+    const std::vector<int>& s1 = P.nodes[c1].segs;
+    const std::vector<int>& s2 = P.nodes[c2].segs;
+    std::unordered_map<int, int> pos2;
+    for (int k = 0; k < (int)s2.size(); ++k) pos2[s2[k]] = k;
+    std::vector<int> gpos1, gpos2, opos1, opos2;
+    std::vector<char> in_gamma2(s2.size(), 0);
+    for (int k = 0; k < (int)s1.size(); ++k) {
+        auto it = pos2.find(s1[k]);
+        if (it != pos2.end()) {
+            nd.gamma.push_back(s1[k]);
+            gpos1.push_back(k);
+            gpos2.push_back(it->second);
+            in_gamma2[it->second] = 1;
+        } else {
+            opos1.push_back(k);
+            nd.segs.push_back(s1[k]);
+        }
+    }
+    nd.o1 = (int)opos1.size();
+    for (int k = 0; k < (int)s2.size(); ++k)
+        if (!in_gamma2[k]) { opos2.push_back(k); nd.segs.push_back(s2[k]); }
+    nd.map = gpos1;
+    nd.map.insert(nd.map.end(), gpos2.begin(), gpos2.end());
+    nd.map.insert(nd.map.end(), opos1.begin(), opos1.end());
+    nd.map.insert(nd.map.end(), opos2.begin(), opos2.end());
+    const int id = (int)P.nodes.size();
+    P.nodes.push_back(nd);
+    P.nodes[c1].parent = id;
+    P.nodes[c2].parent = id;
+    return id;
+}
+
+// Root pins and the storage offsets of every node's R and rbar.
+void finish_tree(Plan& P) {
+    P.root_pinned.assign(P.nodes.size(), 0);
+    if (P.pure_neumann) P.root_pinned[P.roots[0]] = 1;
+    const int nnode = (int)P.nodes.size();
+    P.node_R_off.resize(nnode);
+    P.node_r_off.resize(nnode);
+    for (int v = 0; v < nnode; ++v) {
+        const long long m = (long long)P.nodes[v].segs.size();
+        P.node_R_off[v] = P.nR;
+        P.nR += m * m;
+        P.node_r_off[v] = P.nr;
+        P.nr += m;
+    }
+}
+
+void finish_merges(Plan& P);
 
 int make_plan(Plan& P) {
     const int ngrid = (int)P.grids.size();
@@ -217,40 +284,8 @@ int make_plan(Plan& P) {
                 c1 = build(I0, I1, J0, mid);
                 c2 = build(I0, I1, mid, J1);
             }
-            Plan::Node nd;
-            nd.box[0] = I0; nd.box[1] = I1; nd.box[2] = J0; nd.box[3] = J1;
-            nd.c1 = c1; nd.c2 = c2;
-            nd.height = 1 + std::max(P.nodes[c1].height, P.nodes[c2].height);
-            const std::vector<int>& s1 = P.nodes[c1].segs;
-            const std::vector<int>& s2 = P.nodes[c2].segs;
-            std::unordered_map<int, int> pos2;
-            for (int k = 0; k < (int)s2.size(); ++k) pos2[s2[k]] = k;
-            std::vector<int> gpos1, gpos2, opos1, opos2;
-            std::vector<char> in_gamma2(s2.size(), 0);
-            for (int k = 0; k < (int)s1.size(); ++k) {
-                auto it = pos2.find(s1[k]);
-                if (it != pos2.end()) {
-                    nd.gamma.push_back(s1[k]);
-                    gpos1.push_back(k);
-                    gpos2.push_back(it->second);
-                    in_gamma2[it->second] = 1;
-                } else {
-                    opos1.push_back(k);
-                    nd.segs.push_back(s1[k]);
-                }
-            }
-            nd.o1 = (int)opos1.size();
-            for (int k = 0; k < (int)s2.size(); ++k)
-                if (!in_gamma2[k]) { opos2.push_back(k); nd.segs.push_back(s2[k]); }
-            nd.map = gpos1;
-            nd.map.insert(nd.map.end(), gpos2.begin(), gpos2.end());
-            nd.map.insert(nd.map.end(), opos1.begin(), opos1.end());
-            nd.map.insert(nd.map.end(), opos2.begin(), opos2.end());
-            const int id = (int)P.nodes.size();
-            P.nodes.push_back(nd);
-            P.nodes[c1].parent = id;
-            P.nodes[c2].parent = id;
-            return id;
+            const int box[4] = {I0, I1, J0, J1};
+            return add_merge_node(P, c1, c2, box);
         }
     };
     P.height = 0;
@@ -261,19 +296,7 @@ int make_plan(Plan& P) {
         P.roots.push_back(root);
         P.height = std::max(P.height, P.nodes[root].height);
     }
-    P.root_pinned.assign(P.nodes.size(), 0);
-    if (P.pure_neumann) P.root_pinned[P.roots[0]] = 1;
-    // storage offsets per node
-    const int nnode = (int)P.nodes.size();
-    P.node_R_off.resize(nnode);
-    P.node_r_off.resize(nnode);
-    for (int v = 0; v < nnode; ++v) {
-        const long long m = (long long)P.nodes[v].segs.size();
-        P.node_R_off[v] = P.nR;
-        P.nR += m * m;
-        P.node_r_off[v] = P.nr;
-        P.nr += m;
-    }
+    finish_tree(P);
     for (int id = 0; id < P.nleaf; ++id) {
         LeafDesc& L = P.leaves[id];
         const long long n = (long long)L.w * L.h;
@@ -328,6 +351,17 @@ int make_plan(Plan& P) {
             else P.seg_lam_b[t] = L.r_off + k;
         }
     }
+    finish_merges(P);
+    const double ncell = (double)P.ncell, nface = (double)(P.nxface + P.nyface);
+    P.residual_flops = 8.0 * ncell + 8.0 * (double)P.nskel_faces;
+    P.finish_flops = 3.0 * nface + 2.0 * ncell;
+    return MRCM_OK;
+}
+
+// The merge descriptors grouped by tree height, their storage, and the flop
+// counts of the merges and of the solve's tree sweeps.
+void finish_merges(Plan& P) {
+    const int nnode = (int)P.nodes.size();
     // merges grouped by height
     std::vector<double> node_lu_flops, node_inv_flops, node_prod_flops;
     std::vector<std::vector<int>> by_h(P.height + 1);
@@ -427,9 +461,209 @@ int make_plan(Plan& P) {
             P.phase_build[MRCM_PHASE_MERGE_R] += md * (md + 1.0) * gd;
         }
     }
-    const double ncell = (double)P.ncell, nface = (double)(P.nxface + P.nyface);
-    P.residual_flops = 8.0 * ncell + 8.0 * (double)P.nskel_faces;
-    P.finish_flops = 3.0 * nface + 2.0 * ncell;
+}
+
+
+// First row of each column of B of a 3D block (local cells x fastest; the
+// local segment of a skeleton face as the leaf kernel numbers it).
+void leaf3_starts(const LeafDesc3& B, std::vector<int>& start) {
+    const int n = B.w[0] * B.w[1] * B.w[2];
+    start.assign(B.m, n);
+    for (int c = 0; c < n; ++c) {
+        const int loc[3] = {c % B.w[0], (c / B.w[0]) % B.w[1], c / (B.w[0] * B.w[1])};
+        for (int side = 0; side < 6; ++side) {
+            const int d = side >> 1, up = side & 1;
+            const int p = loc[d] + (up ? 1 : -1);
+            if ((p >= 0 && p < B.w[d]) || B.side_off[side] < 0) continue;
+            const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+            const int s = B.side_off[side] + (B.side_fine[side] ? loc[t2] * B.w[t1] + loc[t1] : 0);
+            start[s] = std::min(start[s], c);
+        }
+    }
+}
+
+// The 3D plan.  Blocks of the patch shape (seg cells per axis) tile the grid;
+// a face between two blocks of one subdomain (sub cells per axis) is a
+// segment of its own, the side shared by blocks of two subdomains is one
+// patch.  One tree by recursive bisection of the block box (the axis with
+// the most blocks, ties x, y, z; the lower half takes ceil(count / 2)).
+int make_plan3d(Plan& P) {
+    const Grid3& G = P.g3;
+    const int b[3] = {P.gx, P.gy, P.gz};
+    const int sub[3] = {P.sx, P.sy, P.sz};
+    const int n[3] = {G.nx, G.ny, G.nz};
+    int Nb[3];
+    for (int d = 0; d < 3; ++d) Nb[d] = n[d] / b[d];
+    P.ncell = (long long)G.nx * G.ny * G.nz;
+    P.nxface = (long long)(G.nx + 1) * G.ny * G.nz;
+    P.nyface = (long long)G.nx * (G.ny + 1) * G.nz;
+    P.nzface = (long long)G.nx * G.ny * (G.nz + 1);
+    P.nbc = 2LL * ((long long)G.ny * G.nz + (long long)G.nx * G.nz + (long long)G.nx * G.ny);
+    P.pure_neumann = !(G.bc[0] || G.bc[1] || G.bc[2] || G.bc[3] || G.bc[4] || G.bc[5]);
+    P.nleaf = Nb[0] * Nb[1] * Nb[2];
+    P.leaves3.assign(P.nleaf, LeafDesc3{});
+    const int stride[3] = {1, Nb[0], Nb[0] * Nb[1]};
+    auto tang = [](int d, int& t1, int& t2) { t1 = d == 0 ? 1 : 0; t2 = d == 2 ? 1 : 2; };
+    std::vector<int> plus_first(3 * (size_t)P.nleaf, -1), plus_fine(3 * (size_t)P.nleaf, 0);
+    for (int id = 0; id < P.nleaf; ++id) {
+        const int idx[3] = {id % Nb[0], (id / Nb[0]) % Nb[1], id / (Nb[0] * Nb[1])};
+        LeafDesc3& B = P.leaves3[id];
+        std::memset(&B, 0, sizeof(B));
+        B.i0 = idx[0] * b[0]; B.j0 = idx[1] * b[1]; B.k0 = idx[2] * b[2];
+        for (int d = 0; d < 3; ++d) B.w[d] = b[d];
+        for (int d = 0; d < 3; ++d) {
+            if (idx[d] + 1 >= Nb[d]) continue;
+            const bool fine = (idx[d] * b[d]) / sub[d] == ((idx[d] + 1) * b[d]) / sub[d];
+            int t1, t2;
+            tang(d, t1, t2);
+            const int base[3] = {B.i0, B.j0, B.k0};
+            plus_first[3 * (size_t)id + d] = P.nseg;
+            plus_fine[3 * (size_t)id + d] = fine ? 1 : 0;
+            auto add = [&](int lo1, int len1, int lo2, int len2) {
+                P.seg_axis.push_back(d);
+                P.seg_line.push_back(base[d] + b[d]);
+                P.seg_lo.push_back(lo1);
+                P.seg_len.push_back(len1);
+                P.seg_lo2.push_back(lo2);
+                P.seg_len2.push_back(len2);
+                P.seg_a.push_back(id);
+                P.seg_b.push_back(id + stride[d]);
+                P.seg_grid.push_back(0);
+                ++P.nseg;
+            };
+            if (fine) {
+                for (int w = 0; w < b[t2]; ++w)
+                    for (int u = 0; u < b[t1]; ++u) add(base[t1] + u, 1, base[t2] + w, 1);
+            } else {
+                add(base[t1], b[t1], base[t2], b[t2]);
+            }
+        }
+    }
+    P.seg_face_off.resize(P.nseg + 1);
+    P.seg_face_off[0] = 0;
+    for (int t = 0; t < P.nseg; ++t) P.seg_face_off[t + 1] = P.seg_face_off[t] + P.seg_len[t] * P.seg_len2[t];
+    P.nskel_faces = P.seg_face_off[P.nseg];
+    P.xface_seg.assign((size_t)P.nxface, -1);
+    P.yface_seg.assign((size_t)P.nyface, -1);
+    P.zface_seg.assign((size_t)P.nzface, -1);
+    for (int t = 0; t < P.nseg; ++t) {
+        const int d = P.seg_axis[t];
+        int t1, t2;
+        tang(d, t1, t2);
+        for (int w = P.seg_lo2[t]; w < P.seg_lo2[t] + P.seg_len2[t]; ++w)
+            for (int u = P.seg_lo[t]; u < P.seg_lo[t] + P.seg_len[t]; ++u) {
+                int pos[3];
+                pos[d] = P.seg_line[t]; pos[t1] = u; pos[t2] = w;
+                const long long i = pos[0], j = pos[1], k = pos[2];
+                if (d == 0) P.xface_seg[(size_t)((k * G.ny + j) * (G.nx + 1) + i)] = t;
+                else if (d == 1) P.yface_seg[(size_t)((k * (G.ny + 1) + j) * G.nx + i)] = t;
+                else P.zface_seg[(size_t)((k * G.ny + j) * G.nx + i)] = t;
+            }
+    }
+    // block segment lists: sides x-, x+, y-, y+, z-, z+
+    for (int id = 0; id < P.nleaf; ++id) {
+        const int idx[3] = {id % Nb[0], (id / Nb[0]) % Nb[1], id / (Nb[0] * Nb[1])};
+        LeafDesc3& B = P.leaves3[id];
+        B.seg_off = (int)P.leaf_segs.size();
+        int cnt = 0;
+        for (int side = 0; side < 6; ++side) {
+            const int d = side >> 1, up = side & 1;
+            int t1, t2;
+            tang(d, t1, t2);
+            const int owner = up ? id : (idx[d] > 0 ? id - stride[d] : -1);
+            const int first = owner >= 0 ? plus_first[3 * (size_t)owner + d] : -1;
+            if (first < 0) { B.side_off[side] = -1; B.side_fine[side] = 0; continue; }
+            const int fine = plus_fine[3 * (size_t)owner + d];
+            const int count = fine ? b[t1] * b[t2] : 1;
+            B.side_off[side] = cnt;
+            B.side_fine[side] = fine;
+            for (int k = 0; k < count; ++k) P.leaf_segs.push_back(first + k);
+            cnt += count;
+        }
+        B.m = cnt;
+        P.max_m_leaf = std::max(P.max_m_leaf, cnt);
+    }
+    // tree
+    P.nodes.assign(P.nleaf, Plan::Node{});
+    for (int id = 0; id < P.nleaf; ++id) {
+        Plan::Node& nd = P.nodes[id];
+        const int I = id % Nb[0], J = (id / Nb[0]) % Nb[1];
+        nd.box[0] = I; nd.box[1] = I + 1; nd.box[2] = J; nd.box[3] = J + 1;
+        nd.leaf = id;
+        const LeafDesc3& B = P.leaves3[id];
+        nd.segs.assign(P.leaf_segs.begin() + B.seg_off, P.leaf_segs.begin() + B.seg_off + B.m);
+    }
+    struct Rec3 {
+        Plan& P;
+        const int* stride;
+        int build(const int lo[3], const int hi[3]) {
+            int d = 0;
+            for (int a = 1; a < 3; ++a)
+                if (hi[a] - lo[a] > hi[d] - lo[d]) d = a;
+            if (hi[d] - lo[d] == 1) return lo[0] * stride[0] + lo[1] * stride[1] + lo[2] * stride[2];
+            const int mid = lo[d] + (hi[d] - lo[d] + 1) / 2;
+            int h1[3] = {hi[0], hi[1], hi[2]}, l2[3] = {lo[0], lo[1], lo[2]};
+            h1[d] = mid;
+            l2[d] = mid;
+            const int c1 = build(lo, h1);
+            const int c2 = build(l2, hi);
+            const int box[4] = {lo[0], hi[0], lo[1], hi[1]};
+            return add_merge_node(P, c1, c2, box);
+        }
+    };
+    {
+        Rec3 rec{P, stride};
+        const int lo[3] = {0, 0, 0};
+        const int root = rec.build(lo, Nb);
+        P.roots.assign(1, root);
+        P.height = P.nodes[root].height;
+    }
+    finish_tree(P);
+    // block storage and flop counts (Cholesky, Z from each column's first
+    // nonzero row, the lower triangle of Z^T Z from each pair's later start)
+    std::map<std::vector<int>, long long> flop_cache;
+    std::vector<int> start;
+    for (int id = 0; id < P.nleaf; ++id) {
+        LeafDesc3& B = P.leaves3[id];
+        const long long nn = (long long)B.w[0] * B.w[1] * B.w[2], m = B.m;
+        B.L_off = P.nL; P.nL += nn * nn;
+        B.Z_off = P.nZ; P.nZ += nn * m;
+        B.zb_off = P.nzb; P.nzb += nn;
+        B.R_off = P.node_R_off[id];
+        B.r_off = P.node_r_off[id];
+        std::vector<int> key(B.side_off, B.side_off + 6);
+        key.insert(key.end(), B.side_fine, B.side_fine + 6);
+        auto it = flop_cache.find(key);
+        long long f;
+        if (it != flop_cache.end()) {
+            f = it->second;
+        } else {
+            leaf3_starts(B, start);
+            f = 0;
+            for (long long k = 0; k < nn; ++k) f += 1 + (nn - 1 - k) + (nn - 1 - k) * (nn - k);
+            for (int s = 0; s < m; ++s) f += (nn - start[s]) * (nn - start[s]);   // 1 + 2 (n-1-k) per row
+            for (int r = 0; r < m; ++r)
+                for (int q = 0; q <= r; ++q) f += 2 * (nn - std::max(start[r], start[q]));
+            flop_cache[key] = f;
+        }
+        P.leaf_flops += f;
+        P.model_build += (double)f;
+        P.solve_flops += 2 * nn * nn + 4 * nn * m;
+        P.phase_pass[MRCM_PHASE_LEAF_PART] += (double)(nn * nn + 2 * nn * m);
+        P.phase_pass[MRCM_PHASE_LEAF_PRESSURE] += (double)(nn * nn + 2 * nn * m);
+    }
+    P.seg_lam_a.assign(P.nseg, -1);
+    P.seg_lam_b.assign(P.nseg, -1);
+    for (int id = 0; id < P.nleaf; ++id) {
+        const LeafDesc3& B = P.leaves3[id];
+        for (int k = 0; k < B.m; ++k) {
+            const int t = P.leaf_segs[B.seg_off + k];
+            if (P.seg_a[t] == id) P.seg_lam_a[t] = B.r_off + k;
+            else P.seg_lam_b[t] = B.r_off + k;
+        }
+    }
+    finish_merges(P);
+    P.finish_flops = 3.0 * (double)(P.nxface + P.nyface + P.nzface) + (double)P.ncell;
     return MRCM_OK;
 }
 
@@ -644,15 +878,57 @@ const char* mrcm_error_string(int code) {
     }
 }
 
+// A 3D grid: blocks of the patch shape (at most kLeaf3Cells cells, at most
+// 16 faces per side) that tile the subdomains, which tile the grid; at least
+// one Dirichlet side.
+static int validate3(const mrcm_grid& G, const int sub[3], const int seg[3], const int* bc) {
+    long long cells = 1;
+    for (int d = 0; d < 3; ++d) {
+        if (G.n[d] < 1 || !(G.L[d] > 0) || sub[d] < 1 || seg[d] < 1) return MRCM_ERR_INVALID_ARG;
+        cells *= G.n[d];
+    }
+    bool dirichlet = false;
+    for (int s = 0; s < 6; ++s) {
+        if (bc[s] != MRCM_BC_NEUMANN && bc[s] != MRCM_BC_DIRICHLET) return MRCM_ERR_INVALID_ARG;
+        dirichlet |= bc[s] == MRCM_BC_DIRICHLET;
+    }
+    if (4 * cells + 3LL * G.n[0] * G.n[1] > (1LL << 31)) return MRCM_ERR_INVALID_ARG;
+    for (int d = 0; d < 3; ++d)
+        if (sub[d] % seg[d] != 0 || G.n[d] % sub[d] != 0) return MRCM_ERR_SHAPE;
+    if (seg[0] * seg[1] * seg[2] > kLeaf3Cells) return MRCM_ERR_SHAPE;
+    for (int d = 0; d < 3; ++d) {
+        const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+        if (seg[t1] * seg[t2] > kLeaf3Segs / 6) return MRCM_ERR_SHAPE;
+    }
+    if (!dirichlet) return MRCM_ERR_UNSUPPORTED;
+    return MRCM_OK;
+}
+
+static void fill_plan_inputs3(Plan& P, const mrcm_grid& g, const int sub[3], const int seg[3], double alpha,
+                              const int* bc) {
+    P.dim = 3;
+    P.g3.nx = g.n[0]; P.g3.ny = g.n[1]; P.g3.nz = g.n[2];
+    P.g3.hx = g.L[0] / g.n[0]; P.g3.hy = g.L[1] / g.n[1]; P.g3.hz = g.L[2] / g.n[2];
+    for (int s = 0; s < 6; ++s) P.g3.bc[s] = bc[s];
+    P.grids.assign(1, GridDesc{});
+    std::memset(&P.grids[0], 0, sizeof(GridDesc));
+    P.grids[0].nx = g.n[0];
+    P.grids[0].ny = g.n[1];
+    P.alpha = alpha;
+    P.sx = sub[0]; P.sy = sub[1]; P.sz = sub[2];
+    P.gx = seg[0]; P.gy = seg[1]; P.gz = seg[2];
+}
+
 // count grids g[k] with boundary types bc_type[6 k .. 6 k + 5]
 static int validate(int count, const mrcm_grid* g, const int sub_cells[3], const int seg_cells[3],
                     const int* bc_type) {
     if (count < 1 || !g || !sub_cells || !seg_cells || !bc_type) return MRCM_ERR_INVALID_ARG;
+    for (int k = 0; k < count; ++k)
+        if (g[k].dim == 3) return count == 1 ? validate3(g[0], sub_cells, seg_cells, bc_type) : MRCM_ERR_UNSUPPORTED;
     long long cells = 0, faces = 0;
     bool all_neumann = false;
     for (int k = 0; k < count; ++k) {
         const mrcm_grid& G = g[k];
-        if (G.dim == 3) return MRCM_ERR_UNSUPPORTED;
         if (G.dim != 2) return MRCM_ERR_INVALID_ARG;
         if (G.n[0] < 1 || G.n[1] < 1 || !(G.L[0] > 0) || !(G.L[1] > 0)) return MRCM_ERR_INVALID_ARG;
         cells += (long long)G.n[0] * G.n[1];
@@ -722,8 +998,13 @@ int mrcm_plan_query(const mrcm_grid* g, const int sub_cells[3], const int seg_ce
     TRY(validate(1, g, sub_cells, seg_cells, bc_type));
     if (what == MRCM_Q_WORKSPACE_BYTES) { *value = 0; return MRCM_OK; }
     Plan P;
-    fill_plan_inputs(P, 1, g, sub_cells, seg_cells, 1.0, bc_type);
-    TRY(make_plan(P));
+    if (g->dim == 3) {
+        fill_plan_inputs3(P, *g, sub_cells, seg_cells, 1.0, bc_type);
+        TRY(make_plan3d(P));
+    } else {
+        fill_plan_inputs(P, 1, g, sub_cells, seg_cells, 1.0, bc_type);
+        TRY(make_plan(P));
+    }
     return plan_value(P, what, value);
 }
 
@@ -739,6 +1020,133 @@ static bool level_factor(const mrcm_ctx* c, int h) {
 }
 static void set_tree_forms(mrcm_ctx* c) {
     for (int h = 1; h <= c->P.height; ++h) c->tree.form[h - 1] = level_factor(c, h) ? 1 : 0;
+}
+
+// Workspace of the merges and of the fused solve sweeps (both forms, 2D and
+// 3D): Gauss-Jordan scratch and barrier words, the sweep levels, the factor
+// form's flags and the sweep plan.
+static int setup_tree(mrcm_ctx* c) {
+    const Plan& P = c->P;
+    DevView& v = c->v;
+    {
+        size_t nscr = 1;
+        for (int h = 1; h <= P.height; ++h)
+            nscr = std::max(nscr, merge_scratch_doubles(P.level_count[h - 1], P.level_max_g2[h - 1],
+                                                        P.level_max_m[h - 1]));
+        TRY(dev_alloc(c, &c->gj_scratch, (long long)nscr));
+        TRY(dev_alloc(c, &c->gj_barrier, (long long)(kMergeBarrierBytes / sizeof(unsigned long long))));
+    }
+    {
+        if (P.height > kMaxTreeLevels) return MRCM_ERR_UNSUPPORTED;
+        TreeLevels& T = c->tree;
+        T.height = P.height;
+        T.x_len = P.nX;
+        T.w_len = P.nW;
+        T.n_merges = (long long)P.merges.size();
+        T.map_len = (long long)P.node_map.size();
+        for (int h = 1; h <= P.height; ++h) {
+            T.first[h - 1] = P.level_first[h - 1];
+            T.count[h - 1] = P.level_count[h - 1];
+            T.g2[h - 1] = P.level_max_g2[h - 1];
+            T.m[h - 1] = P.level_max_m[h - 1];
+        }
+        TRY(dev_alloc(c, &v.rgam, std::max<long long>(2 * (long long)P.gamma_segs.size(), 1)));
+        TRY(dev_alloc(c, &v.fwd, std::max<long long>(2 * (long long)P.gamma_segs.size(), 1)));
+        // flags of the triangular sweeps: per node of a level that may take
+        // the factor form, one per solve block
+        long long nflag = 1;
+        for (int h = 1; h <= P.height; ++h)
+            if (P.level_max_m[h - 1] == 0)
+                nflag = std::max(nflag, (long long)P.level_count[h - 1] *
+                                            ((P.level_max_g2[h - 1] + kTriBlock - 1) / kTriBlock));
+        v.tri_flag_n = nflag;
+        TRY(dev_alloc(c, &v.tri_flags, 2 * nflag));
+        set_tree_forms(c);
+        TRYC(tree_grid(&c->tree_grid));
+        const long long need = tree_plan_chunks(T, c->tree_grid);
+        TRY(dev_alloc(c, &c->tree_scratch, std::max(need, 1LL)));
+    }
+    return MRCM_OK;
+}
+
+static int setup3_impl(mrcm_ctx* c, const mrcm_grid* g, const double* K_dev, const int sub[3], const int seg[3],
+                       double alpha, const int* bc_type, int precision, void* stream) {
+    if (precision != MRCM_FP64) return MRCM_ERR_UNSUPPORTED;
+    Plan& P = c->P;
+    fill_plan_inputs3(P, *g, sub, seg, alpha, bc_type);
+    c->stream = static_cast<cudaStream_t>(stream);
+    TRYC(cudaGetDevice(&c->device));
+    TRY(make_plan3d(P));
+    DevView& v = c->v;
+    v.dim = 3;
+    v.g3 = P.g3;
+    v.mixed = 0;
+    v.leaf32 = 0;
+    v.res_dd = 1;
+    c->precision = precision;
+    c->refine_steps = 0;           // the 3D path solves in one pass
+    v.alpha = P.alpha;
+    v.ncell = P.ncell; v.nxface = P.nxface; v.nyface = P.nyface; v.nzface = P.nzface; v.nbc = P.nbc;
+    v.ngrid = 1;
+    TRY(upload(c, &v.grids, P.grids));
+    v.nleaf = P.nleaf; v.nseg = P.nseg;
+    v.sx = P.sx; v.sy = P.sy; v.gx = P.gx; v.gy = P.gy;
+    TRY(dev_alloc(c, &c->K, P.ncell));
+    v.K = c->K;
+    TRY(dev_alloc(c, &v.rx, 1));
+    TRY(dev_alloc(c, &v.ry, 1));
+    TRY(dev_alloc(c, &v.seg_beta, std::max(P.nseg, 1)));
+    TRY(dev_alloc(c, &v.seg_D, std::max(P.nseg, 1)));
+    TRY(dev_alloc(c, &v.cxL, P.nxface));
+    TRY(dev_alloc(c, &v.cxU, P.nxface));
+    TRY(dev_alloc(c, &v.cyL, P.nyface));
+    TRY(dev_alloc(c, &v.cyU, P.nyface));
+    TRY(dev_alloc(c, &v.czL, P.nzface));
+    TRY(dev_alloc(c, &v.czU, P.nzface));
+    TRY(upload(c, &v.seg_axis, P.seg_axis));
+    TRY(upload(c, &v.seg_line, P.seg_line));
+    TRY(upload(c, &v.seg_lo, P.seg_lo));
+    TRY(upload(c, &v.seg_len, P.seg_len));
+    TRY(upload(c, &v.seg_lo2, P.seg_lo2));
+    TRY(upload(c, &v.seg_len2, P.seg_len2));
+    TRY(upload(c, &v.seg_a, P.seg_a));
+    TRY(upload(c, &v.seg_b, P.seg_b));
+    TRY(upload(c, &v.seg_face_off, P.seg_face_off));
+    TRY(upload(c, &v.seg_grid, P.seg_grid));
+    TRY(upload(c, &v.xface_seg, P.xface_seg));
+    TRY(upload(c, &v.yface_seg, P.yface_seg));
+    TRY(upload(c, &v.zface_seg, P.zface_seg));
+    TRY(dev_alloc(c, &v.seg_lam_dd, 1));
+    TRY(upload(c, &v.seg_lam_a, P.seg_lam_a));
+    TRY(upload(c, &v.seg_lam_b, P.seg_lam_b));
+    TRY(upload(c, &v.leaves3, P.leaves3));
+    TRY(upload(c, &v.leaf_segs, P.leaf_segs));
+    TRY(upload(c, &v.merges, P.merges));
+    TRY(upload(c, &v.node_map, P.node_map));
+    TRY(upload(c, &v.gamma_segs, P.gamma_segs));
+    TRY(dev_alloc(c, &v.leafL, P.nL));
+    TRY(dev_alloc(c, &v.leafZ, std::max(P.nZ, 1LL)));
+    TRY(dev_alloc(c, &v.leafL32, 1));
+    TRY(dev_alloc(c, &v.leafZ32, 1));
+    TRY(dev_alloc(c, &v.leafzb, P.nzb));
+    TRY(dev_alloc(c, &v.R, std::max(P.nR, 1LL)));
+    TRY(dev_alloc(c, &v.rbar, std::max(P.nr, 1LL)));
+    TRY(dev_alloc(c, &v.lam, std::max(P.nr, 1LL)));
+    TRY(dev_alloc(c, &v.X, std::max(P.nX, 1LL)));
+    TRY(dev_alloc(c, &v.W, std::max(P.nW, 1LL)));
+    TRY(dev_alloc(c, &v.W32, 1));
+    TRY(dev_alloc(c, &v.p_hi, P.ncell));
+    TRY(dev_alloc(c, &v.p_lo, P.ncell));
+    TRY(dev_alloc(c, &v.sadj, std::max(P.nr, 1LL)));
+    TRY(dev_alloc(c, &v.res_max, kMaxRefine + 1));
+    TRY(dev_alloc(c, &v.red, 1024));
+    TRY(setup_tree(c));
+    TRY(dev_alloc(c, &v.status, 4));
+    v.spin_limit = kDefaultSpinLimit;
+    TRYC(cudaMemcpyAsync(c->K, K_dev, sizeof(double) * P.ncell, cudaMemcpyDefault, c->stream));
+    TRYC(cudaMemsetAsync(v.status, 0, sizeof(int), c->stream));
+    TRYC(cudaStreamSynchronize(c->stream));
+    return MRCM_OK;
 }
 
 static int setup_impl(mrcm_ctx* c, int count, const mrcm_grid* g, const double* K_dev, const int sub[3],
@@ -814,44 +1222,7 @@ static int setup_impl(mrcm_ctx* c, int count, const mrcm_grid* g, const double* 
     TRY(dev_alloc(c, &v.sadj, P.nr));
     TRY(dev_alloc(c, &v.res_max, kMaxRefine + 1));
     TRY(dev_alloc(c, &v.red, 1024));
-    {
-        size_t nscr = 1;
-        for (int h = 1; h <= P.height; ++h)
-            nscr = std::max(nscr, merge_scratch_doubles(P.level_count[h - 1], P.level_max_g2[h - 1],
-                                                        P.level_max_m[h - 1]));
-        TRY(dev_alloc(c, &c->gj_scratch, (long long)nscr));
-        TRY(dev_alloc(c, &c->gj_barrier, (long long)(kMergeBarrierBytes / sizeof(unsigned long long))));
-    }
-    {
-        if (P.height > kMaxTreeLevels) return MRCM_ERR_UNSUPPORTED;
-        TreeLevels& T = c->tree;
-        T.height = P.height;
-        T.x_len = P.nX;
-        T.w_len = P.nW;
-        T.n_merges = (long long)P.merges.size();
-        T.map_len = (long long)P.node_map.size();
-        for (int h = 1; h <= P.height; ++h) {
-            T.first[h - 1] = P.level_first[h - 1];
-            T.count[h - 1] = P.level_count[h - 1];
-            T.g2[h - 1] = P.level_max_g2[h - 1];
-            T.m[h - 1] = P.level_max_m[h - 1];
-        }
-        TRY(dev_alloc(c, &v.rgam, std::max<long long>(2 * (long long)P.gamma_segs.size(), 1)));
-        TRY(dev_alloc(c, &v.fwd, std::max<long long>(2 * (long long)P.gamma_segs.size(), 1)));
-        // flags of the triangular sweeps: per node of a level that may take
-        // the factor form, one per solve block
-        long long nflag = 1;
-        for (int h = 1; h <= P.height; ++h)
-            if (P.level_max_m[h - 1] == 0)
-                nflag = std::max(nflag, (long long)P.level_count[h - 1] *
-                                            ((P.level_max_g2[h - 1] + kTriBlock - 1) / kTriBlock));
-        v.tri_flag_n = nflag;
-        TRY(dev_alloc(c, &v.tri_flags, 2 * nflag));
-        set_tree_forms(c);
-        TRYC(tree_grid(&c->tree_grid));
-        const long long need = tree_plan_chunks(T, c->tree_grid);
-        TRY(dev_alloc(c, &c->tree_scratch, std::max(need, 1LL)));
-    }
+    TRY(setup_tree(c));
     TRY(dev_alloc(c, &v.status, 4));
     v.spin_limit = kDefaultSpinLimit;
     TRYC(cudaMemcpyAsync(c->K, K_dev, sizeof(double) * ncell, cudaMemcpyDefault, c->stream));
@@ -883,7 +1254,9 @@ int mrcm_setup_batch(mrcm_ctx** out, int count, const mrcm_grid* grids, const in
     if (!(alpha > 0) || !std::isfinite(alpha)) return MRCM_ERR_INVALID_ARG;
     mrcm_ctx* c = new (std::nothrow) mrcm_ctx();
     if (!c) return MRCM_ERR_OOM;
-    int rc = setup_impl(c, count, g, K_dev, sub_cells, seg_cells, alpha, bc_type, precision, cuda_stream);
+    int rc = g[0].dim == 3
+                 ? setup3_impl(c, g, K_dev, sub_cells, seg_cells, alpha, bc_type, precision, cuda_stream)
+                 : setup_impl(c, count, g, K_dev, sub_cells, seg_cells, alpha, bc_type, precision, cuda_stream);
     if (rc != MRCM_OK) {
         mrcm_destroy(c);
         return rc;
@@ -910,14 +1283,22 @@ static int enqueue_build(mrcm_ctx* c, int& launches, bool merges_only = false) {
     cudaStream_t s = c->stream;
     launches = 0;
     TRYC(cudaMemsetAsync(v.status, 0, sizeof(int), s));
-    if (!merges_only) {
+    if (!merges_only && P.dim == 3) {
+        {
+            PhaseScope ps(c, MRCM_PHASE_COEF);
+            TRYC(launch_check_K(v, s)); ++launches;
+            TRYC(launch_coef3(v, s)); launches += 1 + (P.nseg > 0);
+        }
+        PhaseScope ps(c, MRCM_PHASE_LEAF_BUILD);
+        TRYC(launch_leaf3_build(v, s)); ++launches;
+    } else if (!merges_only) {
         PhaseScope ps(c, MRCM_PHASE_COEF);
         TRYC(launch_check_K(v, s)); ++launches;
         TRYC(launch_cell_resist(v, s)); ++launches;
         TRYC(launch_seg_beta(v, s)); launches += P.nseg > 0;
         TRYC(launch_face_coef(v, s)); ++launches;
     }
-    if (!merges_only) {
+    if (!merges_only && P.dim != 3) {
         PhaseScope ps(c, MRCM_PHASE_LEAF_BUILD);
         TRYC(launch_leaf_build(v, P.max_m_leaf, s)); ++launches;
     }
@@ -972,7 +1353,9 @@ static int solve_pass(mrcm_ctx* c, const double* q, const double* bc, bool with_
     cudaStream_t s = c->stream;
     {
         PhaseScope ps(c, MRCM_PHASE_LEAF_PART);
-        TRYC(launch_leaf_particular(v, q, bc, with_sadj, s)); ++launches;
+        if (P.dim == 3) TRYC(launch_leaf3_particular(v, q, bc, s));
+        else TRYC(launch_leaf_particular(v, q, bc, with_sadj, s));
+        ++launches;
     }
     if (P.height > 0) {
         {
@@ -986,15 +1369,19 @@ static int solve_pass(mrcm_ctx* c, const double* q, const double* bc, bool with_
     }
     {
         PhaseScope ps(c, MRCM_PHASE_LEAF_PRESSURE);
-        TRYC(launch_leaf_pressure(v, accumulate, s)); ++launches;
-        TRYC(launch_lam_to_PU(v, accumulate, s)); launches += P.nseg > 0;
+        if (P.dim == 3) {
+            TRYC(launch_leaf3_pressure(v, s)); ++launches;
+        } else {
+            TRYC(launch_leaf_pressure(v, accumulate, s)); ++launches;
+            TRYC(launch_lam_to_PU(v, accumulate, s)); launches += P.nseg > 0;
+        }
     }
     return MRCM_OK;
 }
 
 // The launch sequence of mrcm_solve (no synchronisation).
 static int enqueue_solve(mrcm_ctx* c, const double* q_dev, const double* bc_val_dev, double* p_dev, double* Fx_dev,
-                         double* Fy_dev, double* iface_dev, int& launches) {
+                         double* Fy_dev, double* Fz_dev, double* iface_dev, int& launches) {
     const Plan& P = c->P;
     const DevView& v = c->v;
     cudaStream_t s = c->stream;
@@ -1027,7 +1414,8 @@ static int enqueue_solve(mrcm_ctx* c, const double* q_dev, const double* bc_val_
             TRYC(launch_mean_shift(v, steps == 0 || !v.res_dd, s));
             launches += 2;
         }
-        TRYC(launch_face_fluxes(v, bc_val_dev, p_dev, Fx_dev, Fy_dev, iface_dev, steps == 0, s));
+        if (P.dim == 3) TRYC(launch_face_fluxes3(v, bc_val_dev, p_dev, Fx_dev, Fy_dev, Fz_dev, s));
+        else TRYC(launch_face_fluxes(v, bc_val_dev, p_dev, Fx_dev, Fy_dev, iface_dev, steps == 0, s));
         ++launches;
     }
     return MRCM_OK;
@@ -1037,20 +1425,22 @@ int mrcm_solve(mrcm_ctx* c, const double* q_dev, const double* bc_val_dev, doubl
                double* Fy_dev, double* Fz_dev, double* iface_dev) {
     if (!c) return MRCM_ERR_INVALID_ARG;
     if (!c->built) return MRCM_ERR_NOT_BUILT;
-    if (!q_dev || !bc_val_dev || !p_dev || !Fx_dev || !Fy_dev || Fz_dev) return MRCM_ERR_INVALID_ARG;
+    if (!q_dev || !bc_val_dev || !p_dev || !Fx_dev || !Fy_dev) return MRCM_ERR_INVALID_ARG;
+    // Fz and only Fz in 3D; the interface unknowns are a 2D output
+    if (c->P.dim == 3 ? (!Fz_dev || iface_dev) : (Fz_dev != nullptr)) return MRCM_ERR_INVALID_ARG;
     // keep the build's event pairs, reuse the solve's
     while (c->ev_used > 0 && c->ev_phase[c->ev_used - 1] >= MRCM_PHASE_LEAF_PART &&
            c->ev_phase[c->ev_used - 1] <= MRCM_PHASE_FINISH)
         --c->ev_used;
     const int ev_begin = c->ev_used;
-    const void* key[8] = {q_dev, bc_val_dev, p_dev, Fx_dev, Fy_dev, iface_dev,
+    const void* key[8] = {q_dev, bc_val_dev, p_dev, Fx_dev, Fy_dev, c->P.dim == 3 ? Fz_dev : iface_dev,
                           reinterpret_cast<const void*>(
                               (long long)((c->refine_steps * 2 + c->refine_check) * 2 + c->v.res_dd) + 1),
                           reinterpret_cast<const void*>((long long)(c->timing ? 2 : 1) + 4 * (long long)ev_begin)};
     int launches = 0;
     if (c->solve_exec == nullptr || std::memcmp(key, c->solve_key, sizeof(key)) != 0) {
         if (capture_graph(c, &c->solve_exec, [&] {
-                return enqueue_solve(c, q_dev, bc_val_dev, p_dev, Fx_dev, Fy_dev, iface_dev, launches);
+                return enqueue_solve(c, q_dev, bc_val_dev, p_dev, Fx_dev, Fy_dev, Fz_dev, iface_dev, launches);
             })) {
             std::memcpy(c->solve_key, key, sizeof(key));
             c->solve_ev_begin = ev_begin;
@@ -1067,7 +1457,7 @@ int mrcm_solve(mrcm_ctx* c, const double* q_dev, const double* bc_val_dev, doubl
         ++c->graph_replays;
     } else {
         c->ev_used = ev_begin;
-        TRY(enqueue_solve(c, q_dev, bc_val_dev, p_dev, Fx_dev, Fy_dev, iface_dev, launches));
+        TRY(enqueue_solve(c, q_dev, bc_val_dev, p_dev, Fx_dev, Fy_dev, Fz_dev, iface_dev, launches));
         c->launches_solve = launches;
     }
     c->hist_count = c->refine_steps + (c->refine_check ? 1 : 0);
@@ -1169,6 +1559,7 @@ int mrcm_set_wait_limit(mrcm_ctx* c, long long polls) {
 // ---- learned basis surrogate ----------------------------------------------
 int mrcm_interior_leaves(const mrcm_ctx* c, int* ids, int cap) {
     if (!c || cap < 0 || (cap > 0 && !ids)) return MRCM_ERR_INVALID_ARG;
+    if (c->P.dim == 3) return MRCM_ERR_UNSUPPORTED;
     int n = 0;
     for (int id = 0; id < c->P.nleaf; ++id) {
         const LeafDesc& L = c->P.leaves[id];
@@ -1182,7 +1573,7 @@ int mrcm_interior_leaves(const mrcm_ctx* c, int* ids, int cap) {
 
 static int surrogate_ready(mrcm_ctx* c, const int* ids, int count) {
     if (!c || !ids || count < 0) return MRCM_ERR_INVALID_ARG;
-    if (c->P.max_m_leaf > 16) return MRCM_ERR_UNSUPPORTED;
+    if (c->P.dim == 3 || c->P.max_m_leaf > 16) return MRCM_ERR_UNSUPPORTED;
     return MRCM_OK;
 }
 
@@ -1272,6 +1663,7 @@ int mrcm_cnn_adam(float* p, const float* g, float* m1, float* m2, void* p_bf16, 
 
 int mrcm_set_refinement(mrcm_ctx* c, int steps, int check) {
     if (!c || steps < 0 || steps > kMaxRefine) return MRCM_ERR_INVALID_ARG;
+    if (c->P.dim == 3 && (steps > 0 || check)) return MRCM_ERR_UNSUPPORTED;
     c->refine_steps = steps;
     c->refine_check = check ? 1 : 0;
     return MRCM_OK;

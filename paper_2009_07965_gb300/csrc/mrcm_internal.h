@@ -57,6 +57,40 @@ struct LeafDesc {
     long long r_off;   // node rbar / lambda (m values each, separate arrays)
 };
 
+// A 3D grid (one problem per 3D context): arrays are x fastest, then y,
+// then z.  Faces: x-faces (k ny + j)(nx + 1) + i, y-faces (k (ny + 1) + j)
+// nx + i, z-faces (k ny + j) nx + i with k in [0, nz].  Boundary values per
+// side x-, x+, y-, y+, z-, z+ concatenated, the x sides (nz, ny), the y
+// sides (nz, nx), the z sides (ny, nx), first index slowest.
+struct Grid3 {
+    int nx, ny, nz;
+    double hx, hy, hz;
+    int bc[6];                  // side types (1: Dirichlet)
+};
+
+// Largest leaf block of the 3D path (cells) and its segment count: a
+// seg_x x seg_y x seg_z block of at most 64 cells, at most 16 faces per side.
+constexpr int kLeaf3Cells = 64;
+constexpr int kLeaf3Segs = 96;
+
+// One 3D leaf block.  The blocks tile the grid with the interface patch shape,
+// so a patch between two subdomains is the whole shared side of two blocks;
+// inside a subdomain every face between two blocks is a segment of its own
+// (a fine-face interface, on which the Robin coupling is exact for any beta).
+struct LeafDesc3 {
+    int i0, j0, k0;             // first cell
+    int w[3];                   // cells per axis
+    int m;                      // segments of the block
+    int seg_off;                // offset of its segment ids in leaf_segs
+    int side_off[6];            // local index of the first segment of side x-, x+,
+                                // y-, y+, z-, z+ (-1: the side is on the domain boundary)
+    int side_fine[6];           // 1: one segment per face; 0: one patch for the side
+    long long L_off;            // n x n: L below the diagonal (row-major), 1/d on it
+    long long Z_off;            // Z = L^-1 B: m columns of n
+    long long zb_off;           // particular forward solve: n values
+    long long R_off, r_off;     // node R (m x m) and rbar / lambda (m)
+};
+
 // One internal tree node (a merge of two children).
 struct MergeDesc {
     int node;          // node id
@@ -145,6 +179,17 @@ struct DevView {
     unsigned long long* res_max;  // max |residual| per refinement step (double bits)
     int* status;        // device status word
     long long spin_limit;         // polls of a bounded inter-CTA wait (mrcm_set_wait_limit)
+    // 3D contexts (dim == 3): the grid, the blocks, the z-faces and the second
+    // tangential extent of each segment (seg_lo / seg_len hold the first)
+    int dim;
+    Grid3 g3;
+    long long nzface;
+    const LeafDesc3* leaves3;
+    const int* zface_seg;         // segment of each z-face, -1 off the skeleton
+    const int* seg_lo2;
+    const int* seg_len2;
+    double* czL;                  // z-face coefficients seen from the lower / upper cell
+    double* czU;
 };
 
 #ifdef __CUDACC__
@@ -292,6 +337,14 @@ cudaError_t launch_face_fluxes(const DevView& v, const double* bc_val, double* p
 // Learned basis surrogate (kernels_surrogate.cu): leaf lists are device
 // arrays of leaf ids (each checked; leaves with more than 16 segments are
 // refused); fields are float [item][16][256], patches bf16 [item][18][18][16].
+// The 3D path (kernels_3d.cu): coefficients, the leaf blocks' local Robin
+// problems, their solve-phase passes and the face fluxes.
+cudaError_t launch_coef3(const DevView& v, cudaStream_t s);
+cudaError_t launch_leaf3_build(const DevView& v, cudaStream_t s);
+cudaError_t launch_leaf3_particular(const DevView& v, const double* q, const double* bc_val, cudaStream_t s);
+cudaError_t launch_leaf3_pressure(const DevView& v, cudaStream_t s);
+cudaError_t launch_face_fluxes3(const DevView& v, const double* bc_val, double* p, double* Fx, double* Fy,
+                                double* Fz, cudaStream_t s);
 cudaError_t launch_leaf_fields(const DevView& v, const int* ids, int count, float* psi, cudaStream_t s);
 cudaError_t launch_leaf_patches(const DevView& v, const int* ids, int count, void* x, cudaStream_t s);
 cudaError_t launch_leaf_gate(const DevView& v, const int* ids, int count, const float* psi, double* res,

@@ -63,6 +63,56 @@ class Solver:
             pass
 
 
+class Solver3D:
+    """Recursive MRCM solver for one 3D grid (FP64): blocks of the patch
+    shape seg, subdomains sub, one patch per seg-sized side between
+    subdomains.
+
+    K: (nz, ny, nx) float64 CUDA tensor.  bc_type: (x-, x+, y-, y+, z-, z+)
+    with at least one Dirichlet side.  solve() returns p (nz, ny, nx), Fx
+    (nz, ny, nx+1), Fy (nz, ny+1, nx), Fz (nz+1, ny, nx).
+    """
+
+    def __init__(self, K, L=(1.0, 1.0, 1.0), sub=(16, 16, 16), seg=(4, 4, 4), alpha=1.0,
+                 bc_type=(1, 1, 0, 0, 0, 0), stream=None):
+        if not (K.is_cuda and K.dtype == torch.float64 and K.dim() == 3):
+            raise TypeError("K must be a 3D float64 CUDA tensor")
+        self.nz, self.ny, self.nx = K.shape
+        self.stream = stream if stream is not None else torch.cuda.current_stream(K.device)
+        self.device = K.device
+        self.ctx = B.mrcm_setup((self.nx, self.ny, self.nz), L, K.contiguous(), sub, seg, alpha,
+                                bc_type, B.MRCM_FP64, self.stream.cuda_stream)
+        dev, nx, ny, nz = self.device, self.nx, self.ny, self.nz
+        self.p = torch.empty(nz, ny, nx, dtype=torch.float64, device=dev)
+        self.Fx = torch.empty(nz, ny, nx + 1, dtype=torch.float64, device=dev)
+        self.Fy = torch.empty(nz, ny + 1, nx, dtype=torch.float64, device=dev)
+        self.Fz = torch.empty(nz + 1, ny, nx, dtype=torch.float64, device=dev)
+
+    def set_permeability(self, K):
+        B.mrcm_set_permeability(self.ctx, K.contiguous())
+
+    def build_basis(self):
+        B.mrcm_build_basis(self.ctx)
+
+    def solve(self, q, bc_val):
+        B.mrcm_solve(self.ctx, q.contiguous(), bc_val.contiguous(), self.p, self.Fx, self.Fy, self.Fz, None)
+        return self.p, self.Fx, self.Fy, self.Fz
+
+    def query(self, what):
+        return B.mrcm_query(self.ctx, what)
+
+    def close(self):
+        if self.ctx:
+            B.mrcm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class BatchSolver:
     """One context for several independent problems (mrcm_setup_batch): the
     build and every solve run all of them together, one launch per tree

@@ -82,9 +82,11 @@ def test_setup_rejects_bad_shapes_without_a_device(mrcm_lib):
 
 
 def test_unsupported_requests_are_refused_before_any_device_work(mrcm_lib):
-    # 3D grids and the surrogate precision are reserved by the ABI; the call
-    # returns MRCM_ERR_UNSUPPORTED after validating its host arguments and
-    # before touching the device (the permeability pointer is never read)
+    # The surrogate precision, the mixed form in 3D, all-Neumann 3D problems
+    # and 3D batches are refused with MRCM_ERR_UNSUPPORTED, 3D shapes that the
+    # blocks cannot tile with MRCM_ERR_SHAPE, after validating the host
+    # arguments and before touching the device (the permeability pointer is
+    # never read)
     import ctypes
     from paper_2009_07965_gb300 import binding as B
     lib = B._lib()
@@ -92,11 +94,45 @@ def test_unsupported_requests_are_refused_before_any_device_work(mrcm_lib):
     fake_K = ctypes.c_void_p(16)
     sub, seg, bc = B._ints((16, 16, 16), 3), B._ints((4, 4, 4), 3), B._ints((1, 1, 0, 0, 0, 0), 6)
     g3 = B.mrcm_grid(3, (ctypes.c_int * 3)(64, 64, 64), (ctypes.c_double * 3)(1.0, 1.0, 1.0))
-    assert lib.mrcm_setup(ctypes.byref(ctx), ctypes.byref(g3), fake_K, sub, seg, 1.0, bc, B.MRCM_FP64,
+    assert lib.mrcm_setup(ctypes.byref(ctx), ctypes.byref(g3), fake_K, sub, seg, 1.0, bc, B.MRCM_MIXED,
                           None) == -9
+    neumann = B._ints((0, 0, 0, 0, 0, 0), 6)
+    assert lib.mrcm_setup(ctypes.byref(ctx), ctypes.byref(g3), fake_K, sub, seg, 1.0, neumann, B.MRCM_FP64,
+                          None) == -9
+    two = (B.mrcm_grid * 2)(g3, g3)
+    bc2 = B._ints((1, 1, 0, 0, 0, 0) * 2, 12)
+    assert lib.mrcm_setup_batch(ctypes.byref(ctx), 2, two, bc2, fake_K, sub, seg, 1.0, B.MRCM_FP64,
+                                None) == -9
+    ragged = B.mrcm_grid(3, (ctypes.c_int * 3)(64, 64, 40), (ctypes.c_double * 3)(1.0, 1.0, 1.0))
+    assert lib.mrcm_setup(ctypes.byref(ctx), ctypes.byref(ragged), fake_K, sub, seg, 1.0, bc, B.MRCM_FP64,
+                          None) == -2
+    flat = B._ints((8, 8, 1), 3)
+    assert lib.mrcm_setup(ctypes.byref(ctx), ctypes.byref(g3), fake_K, sub, flat, 1.0, bc, B.MRCM_FP64,
+                          None) == -2
     assert not ctx.value
     g2 = B.mrcm_grid(2, (ctypes.c_int * 3)(64, 64, 1), (ctypes.c_double * 3)(1.0, 1.0, 1.0))
     assert lib.mrcm_setup(ctypes.byref(ctx), ctypes.byref(g2), fake_K, sub, seg, 1.0, bc, B.MRCM_SURROGATE,
                           None) == -9
     assert lib.mrcm_setup(ctypes.byref(ctx), ctypes.byref(g2), fake_K, sub, seg, 1.0, bc, 7, None) == -1
     assert not ctx.value
+
+
+def test_plan_of_the_3d_box_workload(mrcm_lib):
+    # 256 x 256 x 64 cells, 16^3 subdomains, 4 x 4 patches: 64 x 64 x 16
+    # blocks of 4^3 cells; a face between blocks of one subdomain is one
+    # segment, the side between blocks of two subdomains one patch; the
+    # bisection tree has log2(65536) = 16 levels
+    Nb, Ns = (64, 64, 16), (16, 16, 4)
+    segs = 0
+    for d in range(3):
+        others = Nb[0] * Nb[1] * Nb[2] // Nb[d]
+        patch_sides = (Ns[d] - 1) * others
+        fine_sides = (Nb[d] - 1) * others - patch_sides
+        segs += patch_sides + 16 * fine_sides
+    q = lambda what: mrcm_lib.mrcm_plan_query((256, 256, 64), (1.0, 1.0, 0.25), (16, 16, 16), (4, 4, 4),
+                                               (1, 1, 0, 0, 0, 0), what)
+    assert q("LEAVES") == 64 * 64 * 16
+    assert q("SEGMENTS") == segs
+    assert q("LEVELS") == 16
+    assert q("NODES") == 2 * 64 * 64 * 16 - 1
+    assert q("CELLS") == 256 * 256 * 64

@@ -1,0 +1,105 @@
+"""3D parity: the CUDA path (blocks of the patch shape merged into 16^3
+subdomains by fine-face Robin couplings, subdomains coupled by patches)
+against the 3D oracle (direct local solves of each subdomain and the global
+interface system), FP64, rel-L2 <= 1e-10 in p, Fx, Fy, Fz.
+
+At the full 256 x 256 x 64 size, where the oracle would take too long, the
+test checks what holds at any size: the net inflow equals the net outflow,
+every subdomain is balanced (the patch-integrated fluxes of its two sides
+agree, Eq. 13.2), and every cell away from the subdomain boundaries is
+conservative (its faces are exact fine-face couplings)."""
+import numpy as np
+import pytest
+
+import inputs
+from conftest import rel
+
+pytestmark = pytest.mark.gpu
+
+
+def _solve(prob, torch):
+    from paper_2009_07965_gb300 import Solver3D
+    dev = torch.device("cuda:0")
+    K = torch.from_numpy(prob.K).to(dev)
+    s = Solver3D(K, L=(prob.Lx, prob.Ly, prob.Lz), sub=prob.sub, seg=prob.seg, alpha=prob.alpha,
+                 bc_type=prob.bc_type)
+    s.build_basis()
+    q = torch.from_numpy(prob.q).to(dev)
+    g = torch.from_numpy(prob.bc_val).to(dev)
+    p, Fx, Fy, Fz = s.solve(q, g)
+    torch.cuda.synchronize()
+    out = dict(p=p.cpu().numpy(), Fx=Fx.cpu().numpy(), Fy=Fy.cpu().numpy(), Fz=Fz.cpu().numpy())
+    s.close()
+    return out
+
+
+CASES = [
+    # (n, sub, seg, L, sigma2, corr, seed, alpha)
+    ((32, 32, 16), (16, 16, 16), (4, 4, 4), None, 2.0, (0.2, 0.2, 0.05), 1, 1.0),
+    ((16, 24, 16), (8, 8, 8), (4, 4, 2), None, 2.0, (0.3, 0.3, 0.1), 2, 1.0),
+    ((24, 16, 12), (8, 8, 4), (2, 4, 2), (1.0, 0.5, 0.25), 3.0, (0.2, 0.2, 0.2), 3, 3.0),
+    ((16, 16, 16), (4, 4, 4), (4, 4, 4), None, 2.0, (0.3, 0.3, 0.3), 4, 0.5),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "x".join(map(str, c[0])) + "-seg" + "".join(map(str, c[2])))
+def test_3d_matches_the_oracle(case, mrcm_lib):
+    import torch
+    from oracle.mrcm3d import solve_mrcm3d
+    n, sub, seg, L, s2, corr, seed, alpha = case
+    prob = inputs.darcy_problem_3d(*n, sigma2=s2, corr=corr, seed=seed, bc="left_right", sub=sub,
+                                   seg=seg, alpha=alpha, L=L)
+    g, o = _solve(prob, torch), solve_mrcm3d(prob)
+    for key in ("p", "Fx", "Fy", "Fz"):
+        assert rel(g[key], o[key]) < 1e-10, (key, rel(g[key], o[key]))
+
+
+def test_3d_one_face_patches_equal_the_fine_solution(mrcm_lib):
+    # single-cell blocks and one-face patches: every coupling is exact
+    import torch
+    from oracle.mrcm3d import solve_fine3d
+    prob = inputs.darcy_problem_3d(12, 8, 8, sigma2=2.0, corr=(0.3, 0.3, 0.3), seed=6, bc="left_right",
+                                   sub=(2, 2, 2), seg=(1, 1, 1), alpha=1.0)
+    g, f = _solve(prob, torch), solve_fine3d(prob)
+    for key in ("p", "Fx", "Fy", "Fz"):
+        assert rel(g[key], f[key]) < 1e-10, key
+
+
+def test_3d_box_workload_conservation(mrcm_lib):
+    # the 256 x 256 x 64 workload of the benchmark, on its own inputs
+    import torch
+    prob = inputs.config_3d()
+    g = _solve(prob, torch)
+    Fx, Fy, Fz, q = g["Fx"], g["Fy"], g["Fz"], prob.q
+    inflow, outflow = Fx[:, :, 0].sum(), Fx[:, :, -1].sum()
+    assert inflow > 0 and abs(inflow - outflow) < 1e-10 * inflow
+    assert np.abs(Fy[:, 0, :]).max() == 0 and np.abs(Fz[0]).max() == 0
+    s = 16
+    div = np.diff(Fx, axis=2) + np.diff(Fy, axis=1) + np.diff(Fz, axis=0) - q
+    scale = np.abs(Fx).max()
+    # cells with no face on a subdomain boundary
+    inner = np.zeros(q.shape, dtype=bool)
+    idx = [np.arange(m) % s for m in q.shape]
+    kk, jj, ii = np.meshgrid(*idx, indexing="ij")
+    inner = (ii > 0) & (ii < s - 1) & (jj > 0) & (jj < s - 1) & (kk > 0) & (kk < s - 1)
+    assert np.abs(div[inner]).max() < 1e-10 * scale
+    # every subdomain: net outflow = its source (zero)
+    nz, ny, nx = q.shape
+    for k0 in range(0, nz, s):
+        for j0 in range(0, ny, s):
+            for i0 in range(0, nx, s):
+                net = (Fx[k0:k0 + s, j0:j0 + s, i0 + s].sum() - Fx[k0:k0 + s, j0:j0 + s, i0].sum()
+                       + Fy[k0:k0 + s, j0 + s, i0:i0 + s].sum() - Fy[k0:k0 + s, j0, i0:i0 + s].sum()
+                       + Fz[k0 + s, j0:j0 + s, i0:i0 + s].sum() - Fz[k0, j0:j0 + s, i0:i0 + s].sum())
+                assert abs(net) < 1e-10 * inflow
+
+
+def test_3d_refinement_request_is_refused(mrcm_lib):
+    import torch
+    from paper_2009_07965_gb300 import Solver3D, MrcmError, mrcm_set_refinement
+    prob = inputs.darcy_problem_3d(16, 16, 16, sigma2=1.0, seed=1, sub=(8, 8, 8), seg=(4, 4, 4))
+    s = Solver3D(torch.from_numpy(prob.K).cuda(), sub=prob.sub, seg=prob.seg)
+    with pytest.raises(MrcmError) as e:
+        mrcm_set_refinement(s.ctx, 1, 0)
+    assert e.value.code == -9
+    s.close()
