@@ -63,6 +63,13 @@ WORKLOADS = {
               "left / p=0 right, no-flow top and bottom, 16x16 leaves truncated at each grid's edges, 4-cell "
               "segments, alpha=1; one batched context (mrcm_setup_batch), FP64"),
         golden=None),
+    "box3d": dict(
+        kind="box3d",
+        desc=("box3d-lr: 256x256x64 cubic cells on [0,1]x[0,1]x[0,0.25], log-normal K sigma^2=2 with "
+              "correlation lengths (0.2, 0.2, 0.05) (seed 3000), p=1 at x=0 / p=0 at x=1, no-flow elsewhere, "
+              "16^3 subdomains (1024), 4x4-face patches, alpha=1; blocks of 4^3 cells merged by fine-face "
+              "couplings inside each subdomain, FP64"),
+        golden=None),
     "square1024": dict(
         n=1024, sigma2=4.0, corr=0.05, seed=2000,
         desc=("square1024-qfs: 1024x1024 cells, log-normal K sigma^2=4 corr 0.05 (seed 2000), "
@@ -914,6 +921,178 @@ def run_ensemble(args):
     b.close()
 
 
+def run_box3d(args):
+    """The 3D workload: one 256 x 256 x 64 problem (16^3 subdomains, 4 x 4
+    patches) built and solved per step."""
+    import numpy as np
+    import torch
+    import inputs
+    wl = WORKLOADS[args.workload]
+    prob = inputs.config_3d()                         # before any CUDA call
+    import paper_2009_07965_gb300 as mr
+    from paper_2009_07965_gb300 import build as build_mod
+    rank, world, local = dist_env()
+    if world > 1:
+        raise SystemExit("the 3D workload runs on one GPU")
+    build_mod.build()
+    dev = torch.device("cuda", 0)
+    peaks = probe_peaks()
+    stream = torch.cuda.Stream(dev)
+    K = torch.from_numpy(prob.K).to(dev)
+    with torch.cuda.stream(stream):
+        sol = mr.Solver3D(K, L=(prob.Lx, prob.Ly, prob.Lz), sub=prob.sub, seg=prob.seg, alpha=prob.alpha,
+                          bc_type=prob.bc_type, stream=stream)
+    mr.mrcm_enable_timing(sol.ctx, True)
+    q = torch.from_numpy(prob.q).to(dev)
+    bcv = torch.from_numpy(prob.bc_val).to(dev)
+    cells = prob.nx * prob.ny * prob.nz
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        sol.build_basis()
+        sol.solve(q, bcv)
+
+    for _ in range(args.warmup):
+        step()
+    tuned = None
+    if not args.no_autotune:
+        mr.mrcm_autotune(sol.ctx, 3)
+        tuned = {h: mr.mrcm_tune_info(sol.ctx, h) for h in range(1, mr.mrcm_query(sol.ctx, "LEVELS") + 1)}
+        tuned = {h: t for h, t in tuned.items() if any(t.values())}
+        step()
+    torch.cuda.synchronize(dev)
+    props = torch.cuda.get_device_properties(dev)
+    uuid = getattr(props, "uuid", None)
+    uuid = f"GPU-{uuid}" if uuid is not None and not str(uuid).startswith("GPU-") else uuid
+    sampler = ClockSampler(uuid)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    step_ms = []
+    phases = {k: 0.0 for k in mr.PHASES}
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+        ev0.record(stream)
+        step()
+        ev1.record(stream)
+        ev1.synchronize()
+        step_ms.append(ev0.elapsed_time(ev1))
+        for k, v in mr.mrcm_phase_times(sol.ctx).items():
+            phases[k] += v
+    clocks = sampler.stop()
+    launches = mr.mrcm_query(sol.ctx, "KERNEL_LAUNCHES_BUILD") + mr.mrcm_query(sol.ctx, "KERNEL_LAUNCHES_SOLVE")
+    value, total_ms = job_throughput(sum(step_ms), cells, args.steps, 1, dev)
+    # end to end from pinned host buffers
+    K_h, q_h, bc_h = K.cpu().pin_memory(), q.cpu().pin_memory(), bcv.cpu().pin_memory()
+    outs_h = [torch.empty_like(t, device="cpu").pin_memory() for t in (sol.p, sol.Fx, sol.Fy, sol.Fz)]
+    K_d, q_d, bc_d = torch.empty_like(K), torch.empty_like(q), torch.empty_like(bcv)
+    e2e_ms = []
+    for it in range(args.warmup + args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+        ev0.record(stream)
+        with torch.cuda.stream(stream):
+            K_d.copy_(K_h, non_blocking=True)
+            q_d.copy_(q_h, non_blocking=True)
+            bc_d.copy_(bc_h, non_blocking=True)
+        mr.mrcm_set_permeability(sol.ctx, K_d)
+        sol.build_basis()
+        outs = sol.solve(q_d, bc_d)
+        with torch.cuda.stream(stream):
+            for h, d in zip(outs_h, outs):
+                h.copy_(d, non_blocking=True)
+        ev1.record(stream)
+        ev1.synchronize()
+        if it >= args.warmup:
+            e2e_ms.append(ev0.elapsed_time(ev1))
+    e2e_value, _ = job_throughput(sum(e2e_ms), cells, args.steps, 1, dev)
+    h2d = (K_h.numel() + q_h.numel() + bc_h.numel()) * 8
+    d2h = sum(h.numel() for h in outs_h) * 8
+    pf = mr.mrcm_phase_flops(sol.ctx)
+    # properties that hold at any size: net inflow = net outflow, every
+    # subdomain balanced (patch-integrated fluxes agree on both sides)
+    p_, Fx, Fy, Fz = (t.cpu().numpy() for t in sol.solve(q, bcv))
+    inflow, outflow = float(Fx[:, :, 0].sum()), float(Fx[:, :, -1].sum())
+    sd = 16
+    nets = (Fx[:, :, sd::sd].reshape(prob.nz // sd, sd, prob.ny // sd, sd, -1).sum(axis=(1, 3))
+            - Fx[:, :, 0:-1:sd].reshape(prob.nz // sd, sd, prob.ny // sd, sd, -1).sum(axis=(1, 3)))
+    nets = nets + (Fy[:, sd::sd, :].reshape(prob.nz // sd, sd, -1, prob.nx // sd, sd).sum(axis=(1, 4))
+                   - Fy[:, 0:-1:sd, :].reshape(prob.nz // sd, sd, -1, prob.nx // sd, sd).sum(axis=(1, 4)))
+    nets = nets + (Fz[sd::sd].reshape(-1, prob.ny // sd, sd, prob.nx // sd, sd).sum(axis=(2, 4))
+                   - Fz[0:-1:sd].reshape(-1, prob.ny // sd, sd, prob.nx // sd, sd).sum(axis=(2, 4)))
+    balance = dict(inflow=inflow, rel_inflow_minus_outflow=abs(inflow - outflow) / inflow,
+                   max_rel_subdomain_imbalance=float(np.abs(nets).max() / inflow))
+    ph = {k: v / args.steps for k, v in phases.items()}
+    dom = max(mr.PHASES, key=lambda k: ph[k])
+    achieved = pf[dom] / (ph[dom] / 1e3) / 1e12
+    peak = peaks["DFMA"]
+    cpu = None if args.no_cpu_baseline else time_box3d_oracle()
+    line = dict(
+        metric=METRIC, value=value, unit="cells/s", n_gpus=1, steps=args.steps, warmup=args.warmup,
+        ms_per_step=total_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
+        data="synthetic",
+        config=dict(workload=wl["desc"], cells=cells, leaves=mr.mrcm_query(sol.ctx, "LEAVES"),
+                    segments=mr.mrcm_query(sol.ctx, "SEGMENTS"), levels=mr.mrcm_query(sol.ctx, "LEVELS"),
+                    l2="inputs larger than L2; L2 also flushed between timed steps", parallelism="one context"),
+        roofline=dict(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
+                      traffic=None, kernel=mr.PHASE_KERNELS[dom], phase=dom,
+                      share=ph[dom] / (total_ms / args.steps),
+                      peak_source="measured in this run: FP64 FMA probe (mrcm_probe_peak DFMA), of measured",
+                      peak_nominal=FP64_NOMINAL_TFLOPS),
+        peaks_measured_tflops=peaks,
+        autotuned_shapes=tuned,
+        gflop_per_step=sum(pf.values()) / 1e9,
+        phases={k: dict(ms=ph[k], gflop=pf[k] / 1e9, tflops=(pf[k] / (ph[k] / 1e3) / 1e12) if ph[k] > 0 else None)
+                for k in mr.PHASES},
+        e2e=dict(value=e2e_value, unit="cells/s", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
+        gpu_launches=launches * args.steps,
+        clocks=clocks,
+        check=dict(balance=balance, tolerance=1e-10,
+                   within_tolerance=bool(max(balance["rel_inflow_minus_outflow"],
+                                             balance["max_rel_subdomain_imbalance"]) <= 1e-10),
+                   parity="tests/test_gpu_3d.py: rel-L2 <= 1e-10 against the 3D oracle up to 32x32x16"),
+        cpu_baseline=cpu,
+    )
+    print(json.dumps(line), flush=True)
+    sol.close()
+
+
+BOX3D_ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import inputs
+from oracle.mrcm3d import solve_mrcm3d
+prob = inputs.darcy_problem_3d(32, 32, 32, sigma2=2.0, corr=(0.2, 0.2, 0.05), seed=3000 + {r},
+                               bc="left_right", L=(0.125, 0.125, 0.125))
+t = time.perf_counter()
+solve_mrcm3d(prob)
+print(json.dumps(dict(times=[time.perf_counter() - t], cells=prob.nx * prob.ny * prob.nz)))
+"""
+
+
+def time_box3d_oracle():
+    """The 3D oracle on the host cores: one process per core, each solving a
+    32^3-cell window (8 subdomains) with the workload's cell size and field
+    statistics."""
+    procs = host_cores()
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    ps = [subprocess.Popen([sys.executable, "-c", BOX3D_ORACLE_SNIPPET.format(root=ROOT, r=k)], env=env,
+                           stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True) for k in range(procs)]
+    res = []
+    for p in ps:
+        out, err = p.communicate(timeout=1800)
+        if p.returncode:
+            return dict(value=None, unit="cells/s", cores=procs, kind="oracle", error=err[-300:])
+        res.append(json.loads(out.strip().splitlines()[-1]))
+    slowest = max(r["times"][0] for r in res)
+    cells = sum(r["cells"] for r in res)
+    return dict(value=cells / slowest, unit="cells/s", cores=procs, kind="oracle",
+                single_core_value=sum(r["cells"] / r["times"][0] for r in res) / len(res),
+                sample=(f"3D oracle O2 on {procs} concurrent processes (one per host core), each solving a "
+                        f"32x32x32-cell window (8 subdomains of 16^3) with the workload's cell size and field "
+                        f"statistics; value = their cells / the slowest solve time"))
+
+
 ENSEMBLE_ORACLE_SNIPPET = r"""
 import json, sys, time
 sys.path.insert(0, {root!r})
@@ -958,6 +1137,8 @@ def main():
         run_profile_step(args)
     elif args.impl == "reference":
         run_reference(args)
+    elif WORKLOADS[args.workload].get("kind") == "box3d" and args.impl != "reference":
+        run_box3d(args)
     elif WORKLOADS[args.workload].get("kind") == "ensemble":
         run_ensemble(args)
     else:

@@ -21,8 +21,9 @@
 // Cholesky factor A = L L^T and Z = L^-1 B: R = Z^T Z - W, rbar = Z^T L^-1
 // bbar and p = L^-T (L^-1 bbar + Z lambda).
 //
-// Mapping: one CTA per block for the factorisation (the dense 64 x 64 A and
-// Z in shared memory), one warp per block for the solve-phase passes.
+// Mapping: one CTA per block for the factorisation (A and Z in shared
+// memory; the banded Cholesky step and the forward solve of every column of Z
+// advance together), one warp per block for the solve-phase passes.
 #include "mrcm_internal.h"
 
 #include <algorithm>
@@ -218,36 +219,40 @@ __global__ void __launch_bounds__(kBuild3Threads) leaf3_build_kernel(DevView v) 
         S.W[s] = w;
         S.start[s] = st;
     }
-    // Cholesky A = L L^T, right-looking over the lower triangle
+    // Cholesky A = L L^T, right-looking; cells are x fastest, so the factor
+    // keeps A's half-bandwidth bw = w_x w_y.  Step k scales column k of L and
+    // row k of Z (both final then), then updates the band triangle below it
+    // and rows k+1..k+bw of every column of Z = L^-1 B that has started (its
+    // first nonzero row at or above k).  The triangle goes first to the
+    // threads that hold no column of Z.  1 / L_kk is kept on the diagonal.
+    const int bw = B.w[0] * B.w[1];
     bool bad = false;
     for (int k = 0; k < n; ++k) {
         __syncthreads();
         const double akk = S.A[k][k];
         bad |= !(akk > 0.0);
-        const double lkk = sqrt(akk), rl = 1.0 / lkk;
-        const int len = n - 1 - k;
-        for (int e = tid; e < len * len; e += kBuild3Threads) {
-            const int r = e / len, q = e % len;
-            if (q <= r) {
-                const int i = k + 1 + r, j = k + 1 + q;
-                S.A[i][j] -= S.A[i][k] * S.A[j][k] / akk;
-            }
-        }
+        const double rl = 1.0 / sqrt(akk);
+        const int len = min(bw, n - 1 - k);
+        for (int i = k + 1 + tid; i <= k + len; i += kBuild3Threads) S.A[i][k] *= rl;
+        for (int q = tid; q < m; q += kBuild3Threads) S.Z[q][k] *= rl;
         __syncthreads();
-        if (tid == 0) S.A[k][k] = lkk;
-        for (int i = k + 1 + tid; i < n; i += kBuild3Threads) S.A[i][k] *= rl;
+        if (tid == 0) S.A[k][k] = rl;
+        const int ntri = len * (len + 1) / 2;
+        for (int e = (tid - m + kBuild3Threads) % kBuild3Threads; e < ntri; e += kBuild3Threads) {
+            int r = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
+            while ((r + 1) * (r + 2) / 2 <= e) ++r;
+            while (r * (r + 1) / 2 > e) --r;
+            const int i = k + 1 + r, j = k + 1 + (e - r * (r + 1) / 2);
+            S.A[i][j] = fma(-S.A[i][k], S.A[j][k], S.A[i][j]);
+        }
+        for (int q = tid; q < m; q += kBuild3Threads) {
+            if (S.start[q] > k) continue;
+            const double zk = S.Z[q][k];
+            for (int r = 1; r <= len; ++r) S.Z[q][k + r] = fma(-S.A[k + r][k], zk, S.Z[q][k + r]);
+        }
     }
     __syncthreads();
     if (bad && tid == 0) atomicOr(v.status, kStatusSingular);
-    // Z = L^-1 B, one column (segment) per thread, from its first nonzero row
-    for (int s = tid; s < m; s += kBuild3Threads) {
-        for (int k = S.start[s]; k < n; ++k) {
-            const double zk = S.Z[s][k] / S.A[k][k];
-            S.Z[s][k] = zk;
-            for (int i = k + 1; i < n; ++i) S.Z[s][i] = fma(-S.A[i][k], zk, S.Z[s][i]);
-        }
-    }
-    __syncthreads();
     // R = Z^T Z - W (symmetric, both halves written)
     double* Rg = v.R + B.R_off;
     const int npair = m * (m + 1) / 2;
@@ -267,7 +272,7 @@ __global__ void __launch_bounds__(kBuild3Threads) leaf3_build_kernel(DevView v) 
     double* Lg = v.leafL + B.L_off;
     for (int e = tid; e < n * n; e += kBuild3Threads) {
         const int k = e / n, i = e % n;      // column k, row i
-        Lg[e] = i > k ? S.A[i][k] : (i == k ? 1.0 / S.A[k][k] : 0.0);
+        Lg[e] = (i > k && i <= k + bw) || i == k ? S.A[i][k] : 0.0;
     }
     double* Zg = v.leafZ + B.Z_off;
     for (int e = tid; e < m * n; e += kBuild3Threads) Zg[e] = S.Z[e / n][e % n];
@@ -302,6 +307,7 @@ leaf3_particular_kernel(DevView v, const double* __restrict__ q, const double* _
     const int n = B.w[0] * B.w[1] * B.w[2], m = B.m;
     const double* Lg = v.leafL + B.L_off;
     const double* Zg = v.leafZ + B.Z_off;
+    const int bw = B.w[0] * B.w[1];
     double* y = ys[wi];
     for (int c = lane; c < n; c += 32) {
         const int ii = c % B.w[0], jj = (c / B.w[0]) % B.w[1], kk = c / (B.w[0] * B.w[1]);
@@ -321,7 +327,8 @@ leaf3_particular_kernel(DevView v, const double* __restrict__ q, const double* _
         const double yk = y[k] * Lg[(long long)k * n + k];
         __syncwarp();
         if (lane == 0) y[k] = yk;
-        for (int i = k + 1 + lane; i < n; i += 32) y[i] = fma(-Lg[(long long)k * n + i], yk, y[i]);
+        const int iend = min(n - 1, k + bw);
+        for (int i = k + 1 + lane; i <= iend; i += 32) y[i] = fma(-Lg[(long long)k * n + i], yk, y[i]);
         __syncwarp();
     }
     double* zb = v.leafzb + B.zb_off;
@@ -349,6 +356,7 @@ __global__ void __launch_bounds__(32 * kSolve3Warps) leaf3_pressure_kernel(DevVi
     const double* Lg = v.leafL + B.L_off;
     const double* Zg = v.leafZ + B.Z_off;
     const double* zb = v.leafzb + B.zb_off;
+    const int bw = B.w[0] * B.w[1];
     double* y = ys[wi];
     double* lam = ls[wi];
     for (int s = lane; s < m; s += 32) lam[s] = v.lam[B.r_off + s];
@@ -362,7 +370,8 @@ __global__ void __launch_bounds__(32 * kSolve3Warps) leaf3_pressure_kernel(DevVi
     // L^T p = y, left-looking from the last row: p_k = (y_k - sum_{i>k} L_ik p_i) / L_kk
     for (int k = n - 1; k >= 0; --k) {
         double part = 0.0;
-        for (int i = k + 1 + lane; i < n; i += 32) part = fma(Lg[(long long)k * n + i], y[i], part);
+        const int iend = min(n - 1, k + bw);
+        for (int i = k + 1 + lane; i <= iend; i += 32) part = fma(Lg[(long long)k * n + i], y[i], part);
         part = warp_sum(part);
         const double pk = (y[k] - part) * Lg[(long long)k * n + k];
         __syncwarp();

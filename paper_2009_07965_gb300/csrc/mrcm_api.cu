@@ -619,8 +619,9 @@ int make_plan3d(Plan& P) {
         P.height = P.nodes[root].height;
     }
     finish_tree(P);
-    // block storage and flop counts (Cholesky, Z from each column's first
-    // nonzero row, the lower triangle of Z^T Z from each pair's later start)
+    // block storage and flop counts (banded Cholesky, Z from each column's
+    // first nonzero row within the band, the lower triangle of Z^T Z from
+    // each pair's later start)
     std::map<std::vector<int>, long long> flop_cache;
     std::vector<int> start;
     for (int id = 0; id < P.nleaf; ++id) {
@@ -640,17 +641,23 @@ int make_plan3d(Plan& P) {
         } else {
             leaf3_starts(B, start);
             f = 0;
-            for (long long k = 0; k < nn; ++k) f += 1 + (nn - 1 - k) + (nn - 1 - k) * (nn - k);
-            for (int s = 0; s < m; ++s) f += (nn - start[s]) * (nn - start[s]);   // 1 + 2 (n-1-k) per row
+            const long long bw = (long long)B.w[0] * B.w[1];
+            for (long long k = 0; k < nn; ++k) {
+                const long long len = std::min(bw, nn - 1 - k);
+                f += 2 + len + len * (len + 1);                  // 1/sqrt, column scale, band triangle
+                for (int s = 0; s < m; ++s)
+                    if (start[s] <= k) f += 1 + 2 * len;         // row scale and band update of Z
+            }
             for (int r = 0; r < m; ++r)
                 for (int q = 0; q <= r; ++q) f += 2 * (nn - std::max(start[r], start[q]));
             flop_cache[key] = f;
         }
         P.leaf_flops += f;
         P.model_build += (double)f;
-        P.solve_flops += 2 * nn * nn + 4 * nn * m;
-        P.phase_pass[MRCM_PHASE_LEAF_PART] += (double)(nn * nn + 2 * nn * m);
-        P.phase_pass[MRCM_PHASE_LEAF_PRESSURE] += (double)(nn * nn + 2 * nn * m);
+        const long long bwn = (long long)B.w[0] * B.w[1] * nn;
+        P.solve_flops += 4 * bwn + 4 * nn * m;
+        P.phase_pass[MRCM_PHASE_LEAF_PART] += (double)(2 * bwn + 2 * nn * m);
+        P.phase_pass[MRCM_PHASE_LEAF_PRESSURE] += (double)(2 * bwn + 2 * nn * m);
     }
     P.seg_lam_a.assign(P.nseg, -1);
     P.seg_lam_b.assign(P.nseg, -1);
