@@ -1026,13 +1026,57 @@ def run_box3d(args):
     dom = max(mr.PHASES, key=lambda k: ph[k])
     achieved = pf[dom] / (ph[dom] / 1e3) / 1e12
     peak = peaks["DFMA"]
+    plan = {w: mr.mrcm_query(sol.ctx, w.upper()) for w in ("leaves", "segments", "levels")}
+    sol.close()
+    del K_d, q_d, bc_d, outs_h
+    # the mixed form: FP32 merges (every one, or those up to 2g = 512: the
+    # merges inside the subdomains, the patch-level ones above in FP64), FP64
+    # blocks, three refinement steps with FP64 residuals; error against the
+    # FP64 solution of this run
+    ref = dict(p=p_, Fx=Fx, Fy=Fy, Fz=Fz)
+    mixed = {}
+    for name, split in (("mixed", 1 << 30), ("mixed_fp64_patch_merges", 512)):
+        with torch.cuda.stream(stream):
+            ms = mr.Solver3D(K, L=(prob.Lx, prob.Ly, prob.Lz), sub=prob.sub, seg=prob.seg, alpha=prob.alpha,
+                             bc_type=prob.bc_type, stream=stream, precision=mr.binding.MRCM_MIXED)
+        mr.mrcm_set_mixed_split(ms.ctx, split)
+        mr.mrcm_enable_timing(ms.ctx, True)
+
+        def mstep():
+            ms.build_basis()
+            ms.solve(q, bcv)
+
+        for _ in range(args.warmup):
+            mstep()
+        if not args.no_autotune:
+            mr.mrcm_autotune(ms.ctx, 3)
+            mstep()
+        mms, mph = [], {k: 0.0 for k in mr.PHASES}
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)
+            ev0.record(stream)
+            mstep()
+            ev1.record(stream)
+            ev1.synchronize()
+            mms.append(ev0.elapsed_time(ev1))
+            for k, v in mr.mrcm_phase_times(ms.ctx).items():
+                mph[k] += v
+        outm = [t.cpu().numpy() for t in ms.solve(q, bcv)]
+        err = {key: float(np.linalg.norm(a - ref[key]) / np.linalg.norm(ref[key]))
+               for key, a in zip(("p", "Fx", "Fy", "Fz"), outm)}
+        mval, mtot = job_throughput(sum(mms), cells, args.steps, 1, dev)
+        mixed[name] = dict(ms_per_step=mtot / args.steps, value=mval, fp32_merges_up_to_2g=split if split < (1 << 30) else "all",
+                           refine_steps=3, rel_l2_vs_fp64=err, residual_history=mr.mrcm_residual_history(ms.ctx),
+                           tolerance=1e-8, within_tolerance=bool(max(err.values()) <= 1e-8),
+                           phases_ms={k: v / args.steps for k, v in mph.items() if v > 0})
+        ms.close()
     cpu = None if args.no_cpu_baseline else time_box3d_oracle()
     line = dict(
         metric=METRIC, value=value, unit="cells/s", n_gpus=1, steps=args.steps, warmup=args.warmup,
         ms_per_step=total_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
         data="synthetic",
-        config=dict(workload=wl["desc"], cells=cells, leaves=mr.mrcm_query(sol.ctx, "LEAVES"),
-                    segments=mr.mrcm_query(sol.ctx, "SEGMENTS"), levels=mr.mrcm_query(sol.ctx, "LEVELS"),
+        config=dict(workload=wl["desc"], cells=cells, **plan,
                     l2="inputs larger than L2; L2 also flushed between timed steps", parallelism="one context"),
         roofline=dict(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
                       traffic=None, kernel=mr.PHASE_KERNELS[dom], phase=dom,
@@ -1051,10 +1095,10 @@ def run_box3d(args):
                    within_tolerance=bool(max(balance["rel_inflow_minus_outflow"],
                                              balance["max_rel_subdomain_imbalance"]) <= 1e-10),
                    parity="tests/test_gpu_3d.py: rel-L2 <= 1e-10 against the 3D oracle up to 32x32x16"),
+        mixed=mixed,
         cpu_baseline=cpu,
     )
     print(json.dumps(line), flush=True)
-    sol.close()
 
 
 BOX3D_ORACLE_SNIPPET = r"""

@@ -297,7 +297,8 @@ __device__ __forceinline__ double warp_sum(double x) {
 // Particular solve of each block: zbar = L^-1 bbar (bbar: the source and
 // the external boundary data, Eqs. addu / addp) and rbar = Z^T zbar.
 __global__ void __launch_bounds__(32 * kSolve3Warps)
-leaf3_particular_kernel(DevView v, const double* __restrict__ q, const double* __restrict__ bc_val) {
+leaf3_particular_kernel(DevView v, const double* __restrict__ q, const double* __restrict__ bc_val,
+                        bool with_sadj) {
     __shared__ double ys[kSolve3Warps][kLeaf3Cells];
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
     const int leaf = blockIdx.x * kSolve3Warps + wi;
@@ -313,7 +314,7 @@ leaf3_particular_kernel(DevView v, const double* __restrict__ q, const double* _
         const int ii = c % B.w[0], jj = (c / B.w[0]) % B.w[1], kk = c / (B.w[0] * B.w[1]);
         const int gi = B.i0 + ii, gj = B.j0 + jj, gk = B.k0 + kk;
         double b = q[cell3(G, gi, gj, gk)];
-        for (int side = 0; side < 6; ++side) {
+        for (int side = 0; side < 6 && bc_val; ++side) {
             const Face3Info F = block_face(v, B, ii, jj, kk, side);
             if (F.bside < 0) continue;
             const double g = bc_value3(G, bc_val, side, gi, gj, gk);
@@ -338,13 +339,15 @@ leaf3_particular_kernel(DevView v, const double* __restrict__ q, const double* _
         double acc = 0.0;
         for (int k = lane; k < n; k += 32) acc = fma(Zg[(long long)s * n + k], y[k], acc);
         acc = warp_sum(acc);
-        if (lane == 0) rb[s] = acc;
+        // a right-hand side sigma of the segment's interface row (refinement)
+        // acts as rbar - sigma
+        if (lane == 0) rb[s] = with_sadj ? acc - v.sadj[B.r_off + s] : acc;
     }
 }
 
 // Final pressures of each block: p = L^-T (zbar + Z lambda), written into the
 // cell state (p_hi, p_lo = 0).
-__global__ void __launch_bounds__(32 * kSolve3Warps) leaf3_pressure_kernel(DevView v) {
+__global__ void __launch_bounds__(32 * kSolve3Warps) leaf3_pressure_kernel(DevView v, bool accumulate) {
     __shared__ double ys[kSolve3Warps][kLeaf3Cells];
     __shared__ double ls[kSolve3Warps][kLeaf3Segs];
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
@@ -381,13 +384,122 @@ __global__ void __launch_bounds__(32 * kSolve3Warps) leaf3_pressure_kernel(DevVi
     for (int c = lane; c < n; c += 32) {
         const int ii = c % B.w[0], jj = (c / B.w[0]) % B.w[1], kk = c / (B.w[0] * B.w[1]);
         const long long gc = cell3(G, B.i0 + ii, B.j0 + jj, B.k0 + kk);
-        v.p_hi[gc] = y[c];
-        v.p_lo[gc] = 0.0;
+        if (accumulate) {
+            const DD x = dd_add(DD{v.p_hi[gc], v.p_lo[gc]}, DD{y[c], 0.0});
+            v.p_hi[gc] = x.h;
+            v.p_lo[gc] = x.l;
+        } else {
+            v.p_hi[gc] = y[c];
+            v.p_lo[gc] = 0.0;
+        }
     }
 }
 
-// Cell pressures and face fluxes (+axis sign); on the skeleton the mean of
-// the two one-sided values rho (p_c - lambda) of the blocks on either side.
+__device__ __forceinline__ void block_max3(unsigned long long* slot, double x) {
+    __shared__ double wmax[32];
+    double a = fabs(x);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = a;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double b = threadIdx.x < (blockDim.x >> 5) ? wmax[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+        // non-negative doubles order like their bit patterns
+        if (threadIdx.x == 0 && b > 0.0) atomicMax(slot, (unsigned long long)__double_as_longlong(b));
+    }
+}
+
+// Refinement residuals in FP64 of the discrete equations (Eqs. 11.2-14.2
+// with lumped RT0) at the current state (p_hi + p_lo, the segments' Robin
+// data lambda^a = P - beta U, lambda^b = P + beta U): cell balances
+// E_c = sum of outward fluxes - q_c, rcell = -E_c.
+__global__ void __launch_bounds__(256) residual3_cells_kernel(DevView v, const double* __restrict__ q,
+                                                              const double* __restrict__ bc_val, int step) {
+    const Grid3& G = v.g3;
+    const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    double e = 0.0;
+    if (c < v.ncell) {
+        const int i = (int)(c % G.nx);
+        const long long r = c / G.nx;
+        const int j = (int)(r % G.ny), k = (int)(r / G.ny);
+        const double pc = v.p_hi[c] + v.p_lo[c];
+        double E = -q[c];
+        for (int side = 0; side < 6; ++side) {
+            const int d = side >> 1, up = side & 1;
+            const int pos = d == 0 ? i : (d == 1 ? j : k);
+            const int nd = d == 0 ? G.nx : (d == 1 ? G.ny : G.nz);
+            long long f;
+            const double* cf;
+            const int* fs;
+            if (d == 0) { f = xface3(G, i + up, j, k); cf = up ? v.cxL : v.cxU; fs = v.xface_seg; }
+            else if (d == 1) { f = yface3(G, i, j + up, k); cf = up ? v.cyL : v.cyU; fs = v.yface_seg; }
+            else { f = zface3(G, i, j, k + up); cf = up ? v.czL : v.czU; fs = v.zface_seg; }
+            const double coef = cf[f];
+            if (up ? pos == nd - 1 : pos == 0) {
+                const double g = bc_value3(G, bc_val, side, i, j, k);
+                E += G.bc[side] ? coef * (pc - g) : area3(G, d) * g;
+                continue;
+            }
+            const int t = fs[f];
+            if (t >= 0) {
+                const double2 l = v.seg_lam_dd[2 * t + (up ? 0 : 1)];
+                E += coef * (pc - (l.x + l.y));
+            } else {
+                const long long nb = c + (up ? 1 : -1) * (d == 0 ? 1LL : (d == 1 ? (long long)G.nx : (long long)G.nx * G.ny));
+                E += coef * (pc - (v.p_hi[nb] + v.p_lo[nb]));
+            }
+        }
+        e = E;
+        v.rcell[c] = -E;
+    }
+    block_max3(v.res_max + step, e);
+}
+
+// Segment residuals: E13 = F^a + F^b (Eq. 13.2), E14 = F^a - F^b - 2 |t| U
+// (Eq. 14.2, divided by beta), outward integrated fluxes of the two sides;
+// they enter the correction solve as right-hand sides of the two interface
+// rows of the segment.
+__global__ void __launch_bounds__(128) residual3_segments_kernel(DevView v, int step) {
+    const Grid3& G = v.g3;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    double E13 = 0.0, E14 = 0.0;
+    if (t < v.nseg) {
+        const int d = v.seg_axis[t], line = v.seg_line[t];
+        const int lo1 = v.seg_lo[t], len1 = v.seg_len[t], lo2 = v.seg_lo2[t], len2 = v.seg_len2[t];
+        const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+        const double2 l2a = v.seg_lam_dd[2 * t], l2b = v.seg_lam_dd[2 * t + 1];
+        const double la = l2a.x + l2a.y, lb = l2b.x + l2b.y;
+        const double* cL = d == 0 ? v.cxL : (d == 1 ? v.cyL : v.czL);
+        const double* cU = d == 0 ? v.cxU : (d == 1 ? v.cyU : v.czU);
+        double Fa = 0.0, Fb = 0.0;
+        for (int w = lo2; w < lo2 + len2; ++w)
+            for (int u = lo1; u < lo1 + len1; ++u) {
+                int pos[3];
+                pos[d] = line; pos[t1] = u; pos[t2] = w;
+                const long long cb = cell3(G, pos[0], pos[1], pos[2]);
+                const long long f = d == 0 ? xface3(G, pos[0], pos[1], pos[2])
+                                           : (d == 1 ? yface3(G, pos[0], pos[1], pos[2]) : zface3(G, pos[0], pos[1], pos[2]));
+                pos[d] = line - 1;
+                const long long ca = cell3(G, pos[0], pos[1], pos[2]);
+                Fa += cL[f] * ((v.p_hi[ca] + v.p_lo[ca]) - la);
+                Fb += cU[f] * ((v.p_hi[cb] + v.p_lo[cb]) - lb);
+            }
+        const double area = len1 * len2 * area3(G, d);
+        const double two_u = 2.0 * area * (v.segU[t] + v.segU_lo[t]);
+        E13 = Fa + Fb;
+        E14 = (Fa - Fb) - two_u;
+        v.sadj[v.seg_lam_a[t]] = -0.5 * (E13 + E14);
+        v.sadj[v.seg_lam_b[t]] = -0.5 * (E13 - E14);
+    }
+    block_max3(v.res_max + step, fmax(fabs(E13), fabs(E14)));
+}
+
+// Cell pressures and face fluxes (+axis sign) from the state (p_hi + p_lo,
+// the segments' Robin data of the interface unknowns); on the skeleton the
+// mean of the two one-sided values rho (p_c - lambda) of the blocks on either
+// side.
 __global__ void face_flux3_kernel(DevView v, const double* __restrict__ bc_val, double* __restrict__ p,
                                   double* __restrict__ Fx, double* __restrict__ Fy, double* __restrict__ Fz) {
     const Grid3& G = v.g3;
@@ -434,8 +546,9 @@ __global__ void face_flux3_kernel(DevView v, const double* __restrict__ bc_val, 
                 const double pb = v.p_hi[cb] + v.p_lo[cb];
                 const int t = fseg[fl];
                 if (t >= 0) {
-                    const double fa = cL[fl] * (pa - v.lam[v.seg_lam_a[t]]);
-                    const double fb = -(cU[fl] * (pb - v.lam[v.seg_lam_b[t]]));
+                    const double2 la = v.seg_lam_dd[2 * t], lb = v.seg_lam_dd[2 * t + 1];
+                    const double fa = cL[fl] * (pa - (la.x + la.y));
+                    const double fb = -(cU[fl] * (pb - (lb.x + lb.y)));
                     F = 0.5 * (fa + fb);
                 } else {
                     F = cL[fl] * (pa - pb);
@@ -472,13 +585,23 @@ cudaError_t launch_leaf3_build(const DevView& v, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_leaf3_particular(const DevView& v, const double* q, const double* bc_val, cudaStream_t s) {
-    leaf3_particular_kernel<<<(v.nleaf + kSolve3Warps - 1) / kSolve3Warps, 32 * kSolve3Warps, 0, s>>>(v, q, bc_val);
+cudaError_t launch_leaf3_particular(const DevView& v, const double* q, const double* bc_val, bool with_sadj,
+                                    cudaStream_t s) {
+    leaf3_particular_kernel<<<(v.nleaf + kSolve3Warps - 1) / kSolve3Warps, 32 * kSolve3Warps, 0, s>>>(
+        v, q, bc_val, with_sadj);
     return cudaGetLastError();
 }
 
-cudaError_t launch_leaf3_pressure(const DevView& v, cudaStream_t s) {
-    leaf3_pressure_kernel<<<(v.nleaf + kSolve3Warps - 1) / kSolve3Warps, 32 * kSolve3Warps, 0, s>>>(v);
+cudaError_t launch_leaf3_pressure(const DevView& v, bool accumulate, cudaStream_t s) {
+    leaf3_pressure_kernel<<<(v.nleaf + kSolve3Warps - 1) / kSolve3Warps, 32 * kSolve3Warps, 0, s>>>(v, accumulate);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual3(const DevView& v, const double* q, const double* bc_val, int step, cudaStream_t s) {
+    residual3_cells_kernel<<<(unsigned)((v.ncell + 255) / 256), 256, 0, s>>>(v, q, bc_val, step);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || v.nseg == 0) return e;
+    residual3_segments_kernel<<<(v.nseg + 127) / 128, 128, 0, s>>>(v, step);
     return cudaGetLastError();
 }
 

@@ -1078,7 +1078,7 @@ static int setup_tree(mrcm_ctx* c) {
 
 static int setup3_impl(mrcm_ctx* c, const mrcm_grid* g, const double* K_dev, const int sub[3], const int seg[3],
                        double alpha, const int* bc_type, int precision, void* stream) {
-    if (precision != MRCM_FP64) return MRCM_ERR_UNSUPPORTED;
+    if (precision != MRCM_FP64 && precision != MRCM_MIXED) return MRCM_ERR_UNSUPPORTED;
     Plan& P = c->P;
     fill_plan_inputs3(P, *g, sub, seg, alpha, bc_type);
     c->stream = static_cast<cudaStream_t>(stream);
@@ -1087,11 +1087,11 @@ static int setup3_impl(mrcm_ctx* c, const mrcm_grid* g, const double* K_dev, con
     DevView& v = c->v;
     v.dim = 3;
     v.g3 = P.g3;
-    v.mixed = 0;
-    v.leaf32 = 0;
-    v.res_dd = 1;
+    v.mixed = precision == MRCM_MIXED ? 1 : 0;
+    v.leaf32 = 0;                  // 3D blocks are factored in FP64
+    v.res_dd = 0;                  // 3D refinement residuals in FP64
     c->precision = precision;
-    c->refine_steps = 0;           // the 3D path solves in one pass
+    c->refine_steps = v.mixed ? kMixedRefineDefault : 0;
     v.alpha = P.alpha;
     v.ncell = P.ncell; v.nxface = P.nxface; v.nyface = P.nyface; v.nzface = P.nzface; v.nbc = P.nbc;
     v.ngrid = 1;
@@ -1123,7 +1123,7 @@ static int setup3_impl(mrcm_ctx* c, const mrcm_grid* g, const double* K_dev, con
     TRY(upload(c, &v.xface_seg, P.xface_seg));
     TRY(upload(c, &v.yface_seg, P.yface_seg));
     TRY(upload(c, &v.zface_seg, P.zface_seg));
-    TRY(dev_alloc(c, &v.seg_lam_dd, 1));
+    TRY(dev_alloc(c, &v.seg_lam_dd, 2LL * std::max(P.nseg, 1)));
     TRY(upload(c, &v.seg_lam_a, P.seg_lam_a));
     TRY(upload(c, &v.seg_lam_b, P.seg_lam_b));
     TRY(upload(c, &v.leaves3, P.leaves3));
@@ -1141,9 +1141,14 @@ static int setup3_impl(mrcm_ctx* c, const mrcm_grid* g, const double* K_dev, con
     TRY(dev_alloc(c, &v.lam, std::max(P.nr, 1LL)));
     TRY(dev_alloc(c, &v.X, std::max(P.nX, 1LL)));
     TRY(dev_alloc(c, &v.W, std::max(P.nW, 1LL)));
-    TRY(dev_alloc(c, &v.W32, 1));
+    TRY(dev_alloc(c, &v.W32, v.mixed ? std::max(P.nW, 1LL) : 1));
+    TRY(dev_alloc(c, &v.segP, std::max(P.nseg, 1)));
+    TRY(dev_alloc(c, &v.segU, std::max(P.nseg, 1)));
+    TRY(dev_alloc(c, &v.segP_lo, std::max(P.nseg, 1)));
+    TRY(dev_alloc(c, &v.segU_lo, std::max(P.nseg, 1)));
     TRY(dev_alloc(c, &v.p_hi, P.ncell));
     TRY(dev_alloc(c, &v.p_lo, P.ncell));
+    TRY(dev_alloc(c, &v.rcell, P.ncell));
     TRY(dev_alloc(c, &v.sadj, std::max(P.nr, 1LL)));
     TRY(dev_alloc(c, &v.res_max, kMaxRefine + 1));
     TRY(dev_alloc(c, &v.red, 1024));
@@ -1360,7 +1365,7 @@ static int solve_pass(mrcm_ctx* c, const double* q, const double* bc, bool with_
     cudaStream_t s = c->stream;
     {
         PhaseScope ps(c, MRCM_PHASE_LEAF_PART);
-        if (P.dim == 3) TRYC(launch_leaf3_particular(v, q, bc, s));
+        if (P.dim == 3) TRYC(launch_leaf3_particular(v, q, bc, with_sadj, s));
         else TRYC(launch_leaf_particular(v, q, bc, with_sadj, s));
         ++launches;
     }
@@ -1377,7 +1382,8 @@ static int solve_pass(mrcm_ctx* c, const double* q, const double* bc, bool with_
     {
         PhaseScope ps(c, MRCM_PHASE_LEAF_PRESSURE);
         if (P.dim == 3) {
-            TRYC(launch_leaf3_pressure(v, s)); ++launches;
+            TRYC(launch_leaf3_pressure(v, accumulate, s)); ++launches;
+            TRYC(launch_lam_to_PU(v, accumulate, s)); launches += P.nseg > 0;
         } else {
             TRYC(launch_leaf_pressure(v, accumulate, s)); ++launches;
             TRYC(launch_lam_to_PU(v, accumulate, s)); launches += P.nseg > 0;
@@ -1406,13 +1412,15 @@ static int enqueue_solve(mrcm_ctx* c, const double* q_dev, const double* bc_val_
     for (int it = 0; it < steps; ++it) {
         {
             PhaseScope ps(c, MRCM_PHASE_RESIDUAL);
-            TRYC(launch_residual(v, q_dev, bc_val_dev, it, s));
+            if (P.dim == 3) TRYC(launch_residual3(v, q_dev, bc_val_dev, it, s));
+            else TRYC(launch_residual(v, q_dev, bc_val_dev, it, s));
             launches += 1 + (P.nseg > 0);
         }
         TRY(solve_pass(c, v.rcell, nullptr, true, true, launches));
     }
     if (c->refine_check) {
-        TRYC(launch_residual(v, q_dev, bc_val_dev, steps, s));
+        if (P.dim == 3) TRYC(launch_residual3(v, q_dev, bc_val_dev, steps, s));
+        else TRYC(launch_residual(v, q_dev, bc_val_dev, steps, s));
         launches += 1 + (P.nseg > 0);
     }
     {
@@ -1517,7 +1525,7 @@ int mrcm_set_mixed_split(mrcm_ctx* c, int max_g2_fp32) {
 
 int mrcm_set_mixed_leaves(mrcm_ctx* c, int fp32) {
     if (!c || (fp32 != 0 && fp32 != 1)) return MRCM_ERR_INVALID_ARG;
-    if (!c->v.mixed) return MRCM_ERR_UNSUPPORTED;
+    if (!c->v.mixed || (c->P.dim == 3 && fp32)) return MRCM_ERR_UNSUPPORTED;
     if (fp32 == c->v.leaf32) return MRCM_OK;
     TRYC(cudaStreamSynchronize(c->stream));
     c->v.leaf32 = fp32;
@@ -1670,7 +1678,6 @@ int mrcm_cnn_adam(float* p, const float* g, float* m1, float* m2, void* p_bf16, 
 
 int mrcm_set_refinement(mrcm_ctx* c, int steps, int check) {
     if (!c || steps < 0 || steps > kMaxRefine) return MRCM_ERR_INVALID_ARG;
-    if (c->P.dim == 3 && (steps > 0 || check)) return MRCM_ERR_UNSUPPORTED;
     c->refine_steps = steps;
     c->refine_check = check ? 1 : 0;
     return MRCM_OK;
@@ -1678,6 +1685,7 @@ int mrcm_set_refinement(mrcm_ctx* c, int steps, int check) {
 
 int mrcm_set_residual(mrcm_ctx* c, int dd) {
     if (!c || (dd != 0 && dd != 1)) return MRCM_ERR_INVALID_ARG;
+    if (c->P.dim == 3 && dd) return MRCM_ERR_UNSUPPORTED;   // 3D residuals are FP64 only
     c->v.res_dd = dd;              // the solve graph is keyed by it
     return MRCM_OK;
 }

@@ -341,8 +341,10 @@ cudaError_t launch_face_fluxes(const DevView& v, const double* bc_val, double* p
 // problems, their solve-phase passes and the face fluxes.
 cudaError_t launch_coef3(const DevView& v, cudaStream_t s);
 cudaError_t launch_leaf3_build(const DevView& v, cudaStream_t s);
-cudaError_t launch_leaf3_particular(const DevView& v, const double* q, const double* bc_val, cudaStream_t s);
-cudaError_t launch_leaf3_pressure(const DevView& v, cudaStream_t s);
+cudaError_t launch_leaf3_particular(const DevView& v, const double* q, const double* bc_val, bool with_sadj,
+                                    cudaStream_t s);
+cudaError_t launch_leaf3_pressure(const DevView& v, bool accumulate, cudaStream_t s);
+cudaError_t launch_residual3(const DevView& v, const double* q, const double* bc_val, int step, cudaStream_t s);
 cudaError_t launch_face_fluxes3(const DevView& v, const double* bc_val, double* p, double* Fx, double* Fy,
                                 double* Fz, cudaStream_t s);
 cudaError_t launch_leaf_fields(const DevView& v, const int* ids, int count, float* psi, cudaStream_t s);

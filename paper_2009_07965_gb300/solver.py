@@ -64,9 +64,10 @@ class Solver:
 
 
 class Solver3D:
-    """Recursive MRCM solver for one 3D grid (FP64): blocks of the patch
-    shape seg, subdomains sub, one patch per seg-sized side between
-    subdomains.
+    """Recursive MRCM solver for one 3D grid: blocks of the patch shape seg,
+    subdomains sub, one patch per seg-sized side between subdomains.
+    precision: MRCM_FP64, or MRCM_MIXED (FP32 merges, FP64 blocks and
+    refinement).
 
     K: (nz, ny, nx) float64 CUDA tensor.  bc_type: (x-, x+, y-, y+, z-, z+)
     with at least one Dirichlet side.  solve() returns p (nz, ny, nx), Fx
@@ -74,14 +75,14 @@ class Solver3D:
     """
 
     def __init__(self, K, L=(1.0, 1.0, 1.0), sub=(16, 16, 16), seg=(4, 4, 4), alpha=1.0,
-                 bc_type=(1, 1, 0, 0, 0, 0), stream=None):
+                 bc_type=(1, 1, 0, 0, 0, 0), stream=None, precision=B.MRCM_FP64):
         if not (K.is_cuda and K.dtype == torch.float64 and K.dim() == 3):
             raise TypeError("K must be a 3D float64 CUDA tensor")
         self.nz, self.ny, self.nx = K.shape
         self.stream = stream if stream is not None else torch.cuda.current_stream(K.device)
         self.device = K.device
         self.ctx = B.mrcm_setup((self.nx, self.ny, self.nz), L, K.contiguous(), sub, seg, alpha,
-                                bc_type, B.MRCM_FP64, self.stream.cuda_stream)
+                                bc_type, precision, self.stream.cuda_stream)
         dev, nx, ny, nz = self.device, self.nx, self.ny, self.nz
         self.p = torch.empty(nz, ny, nx, dtype=torch.float64, device=dev)
         self.Fx = torch.empty(nz, ny, nx + 1, dtype=torch.float64, device=dev)

@@ -17,18 +17,25 @@ from conftest import rel
 pytestmark = pytest.mark.gpu
 
 
-def _solve(prob, torch):
-    from paper_2009_07965_gb300 import Solver3D
+def _solve(prob, torch, precision=None, split=None, refine=None):
+    from paper_2009_07965_gb300 import Solver3D, mrcm_set_mixed_split, mrcm_set_refinement
+    import paper_2009_07965_gb300.binding as B
     dev = torch.device("cuda:0")
     K = torch.from_numpy(prob.K).to(dev)
     s = Solver3D(K, L=(prob.Lx, prob.Ly, prob.Lz), sub=prob.sub, seg=prob.seg, alpha=prob.alpha,
-                 bc_type=prob.bc_type)
+                 bc_type=prob.bc_type, precision=B.MRCM_FP64 if precision is None else precision)
+    if split is not None:
+        mrcm_set_mixed_split(s.ctx, split)
+    if refine is not None:
+        mrcm_set_refinement(s.ctx, refine, 0)
     s.build_basis()
     q = torch.from_numpy(prob.q).to(dev)
     g = torch.from_numpy(prob.bc_val).to(dev)
     p, Fx, Fy, Fz = s.solve(q, g)
     torch.cuda.synchronize()
     out = dict(p=p.cpu().numpy(), Fx=Fx.cpu().numpy(), Fy=Fy.cpu().numpy(), Fz=Fz.cpu().numpy())
+    from paper_2009_07965_gb300 import mrcm_residual_history
+    out["hist"] = mrcm_residual_history(s.ctx)
     s.close()
     return out
 
@@ -94,12 +101,54 @@ def test_3d_box_workload_conservation(mrcm_lib):
                 assert abs(net) < 1e-10 * inflow
 
 
-def test_3d_refinement_request_is_refused(mrcm_lib):
+def test_3d_settings_it_lacks_are_refused(mrcm_lib):
+    # double-double residuals and FP32 block factors are 2D-only
     import torch
-    from paper_2009_07965_gb300 import Solver3D, MrcmError, mrcm_set_refinement
+    from paper_2009_07965_gb300 import Solver3D, MrcmError, mrcm_set_residual, mrcm_set_mixed_leaves
+    import paper_2009_07965_gb300.binding as B
     prob = inputs.darcy_problem_3d(16, 16, 16, sigma2=1.0, seed=1, sub=(8, 8, 8), seg=(4, 4, 4))
-    s = Solver3D(torch.from_numpy(prob.K).cuda(), sub=prob.sub, seg=prob.seg)
+    s = Solver3D(torch.from_numpy(prob.K).cuda(), sub=prob.sub, seg=prob.seg, precision=B.MRCM_MIXED)
     with pytest.raises(MrcmError) as e:
-        mrcm_set_refinement(s.ctx, 1, 0)
+        mrcm_set_residual(s.ctx, 1)
+    assert e.value.code == -9
+    with pytest.raises(MrcmError) as e:
+        mrcm_set_mixed_leaves(s.ctx, 1)
     assert e.value.code == -9
     s.close()
+
+
+MIXED = [CASES[0], CASES[1], CASES[2]]
+
+
+@pytest.mark.parametrize("split", [1 << 30, 64])
+@pytest.mark.parametrize("case", MIXED, ids=lambda c: "x".join(map(str, c[0])) + "-seg" + "".join(map(str, c[2])))
+def test_3d_mixed_form_matches_the_oracle(case, split, mrcm_lib):
+    # FP32 merges (all of them, or those up to 2g = 64), FP64 blocks, three
+    # refinement steps with FP64 residuals: rel-L2 <= 1e-8
+    import torch
+    from oracle.mrcm3d import solve_mrcm3d
+    import paper_2009_07965_gb300.binding as B
+    n, sub, seg, L, s2, corr, seed, alpha = case
+    prob = inputs.darcy_problem_3d(*n, sigma2=s2, corr=corr, seed=seed, bc="left_right", sub=sub,
+                                   seg=seg, alpha=alpha, L=L)
+    g = _solve(prob, torch, precision=B.MRCM_MIXED, split=split)
+    o = solve_mrcm3d(prob)
+    for key in ("p", "Fx", "Fy", "Fz"):
+        assert rel(g[key], o[key]) < 1e-8, (key, rel(g[key], o[key]))
+    hist = g["hist"]
+    assert len(hist) == 3 and hist[-1] < 1e-3 * hist[0]
+
+
+def test_3d_fp64_refinement_keeps_the_solution(mrcm_lib):
+    # refining the FP64 form changes the single pass only at its rounding
+    # level
+    import torch
+    from oracle.mrcm3d import solve_mrcm3d
+    n, sub, seg, L, s2, corr, seed, alpha = CASES[0]
+    prob = inputs.darcy_problem_3d(*n, sigma2=s2, corr=corr, seed=seed, bc="left_right", sub=sub,
+                                   seg=seg, alpha=alpha, L=L)
+    a, b = _solve(prob, torch), _solve(prob, torch, refine=2)
+    o = solve_mrcm3d(prob)
+    for key in ("p", "Fx", "Fy", "Fz"):
+        assert rel(b[key], a[key]) < 1e-11, key
+        assert rel(b[key], o[key]) < 1e-10, key
