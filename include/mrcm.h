@@ -43,7 +43,7 @@ extern "C" {
 typedef struct mrcm_ctx mrcm_ctx; /* opaque, owned by the library */
 
 typedef struct {
-    int dim;       /* 2; 3 is reserved and returns MRCM_ERR_UNSUPPORTED */
+    int dim;       /* 2 or 3 */
     int n[3];      /* cells per axis (n[2] ignored in 2D) */
     double L[3];   /* domain extent per axis; h_d = L[d] / n[d] */
 } mrcm_grid;
@@ -55,7 +55,10 @@ enum {
     MRCM_OK = 0,
     MRCM_ERR_INVALID_ARG = -1, /* null pointer, bad size, alpha <= 0, ...  */
     MRCM_ERR_SHAPE = -2,       /* segment does not divide the leaf side, or
-                                  leaf larger than 16x16 cells              */
+                                  leaf larger than 16x16 cells; in 3D: the
+                                  patch shape does not tile the leaves or
+                                  the leaves the grid, or a patch-shaped
+                                  block exceeds 64 cells or 16 faces a side */
     MRCM_ERR_BAD_K = -3,       /* a permeability is <= 0 or not finite      */
     MRCM_ERR_NOT_BUILT = -4,   /* mrcm_solve before mrcm_build_basis         */
     MRCM_ERR_SINGULAR = -5,    /* zero / tiny pivot, or a pivot of the wrong
@@ -64,9 +67,10 @@ enum {
     MRCM_ERR_CUDA = -6,        /* a CUDA runtime call failed                 */
     MRCM_ERR_OOM = -7,         /* device allocation failed                   */
     MRCM_ERR_TIMEOUT = -8,     /* a bounded device wait gave up              */
-    MRCM_ERR_UNSUPPORTED = -9  /* valid request not implemented (3D, mixed
-                                  precision, surrogate, single-leaf pure
-                                  Neumann)                                  */
+    MRCM_ERR_UNSUPPORTED = -9  /* valid request not implemented (surrogate,
+                                  single-leaf pure Neumann; in 3D: batches,
+                                  all-Neumann problems, FP32 leaves,
+                                  double-double residuals)                  */
 };
 
 /*
@@ -81,11 +85,26 @@ enum {
  * scale H-bar).  The hierarchy bisects the box of leaves along the axis with
  * more leaves (x on ties), the lower half taking ceil(count/2).
  *
+ * 3D (g->dim = 3; Section 5.1 runs its experiments on boxes): the leaves
+ * are sub_cells boxes that must tile the grid, every interface between two
+ * leaves is cut into patches of seg_cells[t1] x seg_cells[t2] faces (t1 <
+ * t2 the tangential axes), each with beta_t = alpha sqrt(|t|) / Keff_t
+ * (sqrt(|t|) the patch side, Eqs. robin.beta / permeff).  The leaves' local
+ * Robin problems are solved by the same recursive merges: the grid is tiled
+ * by blocks of the patch shape (at most 64 cells, at most 16 faces a side),
+ * every face between two blocks of one leaf is a segment of its own (on
+ * which the Robin coupling is exact for any beta) and the side between
+ * blocks of two leaves is one patch; one tree bisects the box of blocks
+ * along the axis with the most blocks (x, y, z on ties).  At least one side
+ * must be Dirichlet; one problem per context.
+ *
  *   out        receives the new context (NULL on failure)
- *   g          grid; g->dim must be 2
- *   K_dev      device array, n[0]*n[1] permeabilities (> 0); copied, the
- *              caller may free it when the call returns
- *   sub_cells  leaf shape in cells, each in [1, 16]
+ *   g          grid; g->dim 2 or 3
+ *   K_dev      device array, n[0]*n[1] (3D: n[0]*n[1]*n[2]) permeabilities
+ *              (> 0), x fastest; copied, the caller may free it when the
+ *              call returns
+ *   sub_cells  leaf shape in cells, each in [1, 16] (3D: any multiple of the
+ *              patch shape that divides n)
  *   seg_cells  segment length in cells; must divide sub_cells per axis
  *   alpha      dimensionless Robin parameter of Eq. (robin.beta), > 0
  *   bc_type    per side (x-, x+, y-, y+, z-, z+): MRCM_BC_NEUMANN or
@@ -100,7 +119,8 @@ enum {
  *              then refines 3 times by default (mrcm_set_refinement) with
  *              FP64 residuals (mrcm_set_residual), which brings the result
  *              near the FP64 form's accuracy when the FP32 factors contract
- *              the error (Wilkinson's iterative refinement).
+ *              the error (Wilkinson's iterative refinement).  In 3D the
+ *              blocks are always factored in FP64.
  *              MRCM_SURROGATE returns MRCM_ERR_UNSUPPORTED.
  *   cuda_stream  cudaStream_t to run on (NULL = legacy default stream)
  * The context allocates and owns all device workspace.
@@ -174,17 +194,21 @@ int mrcm_build_basis(mrcm_ctx* ctx);
  *              compatible data: |sum q - sum |e| g_N| <= 1e-14 (sum |q| +
  *              sum |e| |g_N|), both sums evaluated in double-double on the
  *              device; otherwise the call returns MRCM_ERR_INVALID_ARG
- *   bc_val_dev 2*(n[0]+n[1]) boundary values (layout in the header comment)
- *   p_dev      out: n[0]*n[1] cell pressures
- *   Fx_dev     out: (n[0]+1)*n[1] x-face fluxes; skeleton faces hold the
- *              mean of the two one-sided values
- *   Fy_dev     out: n[0]*(n[1]+1) y-face fluxes
- *   Fz_dev     must be NULL in 2D
+ *   bc_val_dev 2*(n[0]+n[1]) boundary values (layout in the header comment);
+ *              3D: the six sides x-, x+, y-, y+, z-, z+ concatenated, the x
+ *              sides n[2]*n[1] values, the y sides n[2]*n[0], the z sides
+ *              n[1]*n[0], each with its first listed index slowest
+ *   p_dev      out: n[0]*n[1] (3D: n[0]*n[1]*n[2]) cell pressures
+ *   Fx_dev     out: (n[0]+1)*n[1] x-face fluxes (3D: (n[0]+1)*n[1]*n[2]);
+ *              skeleton faces hold the mean of the two one-sided values
+ *   Fy_dev     out: n[0]*(n[1]+1) y-face fluxes (3D: n[0]*(n[1]+1)*n[2])
+ *   Fz_dev     must be NULL in 2D; in 3D required, n[0]*n[1]*(n[2]+1)
+ *              z-face fluxes
  *   iface_dev  optional out (NULL to skip): one-sided fluxes, 2*((n[0]+1)*n[1]
  *              + n[0]*(n[1]+1)) values laid out as [Fa_x, Fb_x, Fa_y, Fb_y],
  *              each face-shaped like Fx / Fy; side a is the lower-coordinate
  *              leaf, side b the upper one, both in the +axis direction; off
- *              the skeleton both equal the face flux.
+ *              the skeleton both equal the face flux.  Must be NULL in 3D.
  * Errors: MRCM_ERR_NOT_BUILT, MRCM_ERR_INVALID_ARG, MRCM_ERR_TIMEOUT,
  * MRCM_ERR_CUDA.
  */
@@ -194,7 +218,7 @@ int mrcm_solve(mrcm_ctx* ctx, const double* q_dev, const double* bc_val_dev,
 
 /* Keys of mrcm_query. */
 enum {
-    MRCM_Q_LEAVES = 0,        /* number of leaves                            */
+    MRCM_Q_LEAVES = 0,        /* number of leaves (3D: patch-shaped blocks)   */
     MRCM_Q_SEGMENTS = 1,      /* number of interface segments                */
     MRCM_Q_LEVELS = 2,        /* tree height (merge steps from leaf to root) */
     MRCM_Q_NODES = 3,         /* tree nodes, leaves included                 */
@@ -284,8 +308,9 @@ enum {
  * (the FP64 form's default: refinement to the FP64 rounding level); dd = 0:
  * in plain FP64, about six times fewer FP64 operations (the mixed form's
  * default: enough for its 1e-8 target, the refined result then stalls near
- * the plain FP64 solve's accuracy).  Takes effect at the next mrcm_solve.
- * Errors: MRCM_ERR_INVALID_ARG.
+ * the plain FP64 solve's accuracy; the only choice in 3D).  Takes effect at
+ * the next mrcm_solve.
+ * Errors: MRCM_ERR_INVALID_ARG, MRCM_ERR_UNSUPPORTED (dd = 1 in 3D).
  */
 int mrcm_set_refinement(mrcm_ctx* ctx, int steps, int check);
 int mrcm_set_residual(mrcm_ctx* ctx, int dd);
@@ -323,8 +348,8 @@ int mrcm_set_mixed_split(mrcm_ctx* ctx, int max_g2_fp32);
  * maps' are, and the refinement converges in fewer steps).  The paper has no
  * counterpart.  A mixed context holds both sets of leaf arrays.  Invalidates
  * the basis (call mrcm_build_basis again).  Errors: MRCM_ERR_INVALID_ARG
- * (fp32 not 0 or 1), MRCM_ERR_UNSUPPORTED (not a mixed context),
- * MRCM_ERR_CUDA.
+ * (fp32 not 0 or 1), MRCM_ERR_UNSUPPORTED (not a mixed context, or fp32 = 1
+ * in 3D), MRCM_ERR_CUDA.
  */
 int mrcm_set_mixed_leaves(mrcm_ctx* ctx, int fp32);
 
