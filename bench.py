@@ -122,6 +122,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="square4096", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--box-n", type=int, nargs=3, default=(256, 256, 64), metavar=("NX", "NY", "NZ"),
+                    help="cells of the box3d workload (multiples of 16; the field keeps its statistics)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision measurement")
     ap.add_argument("--no-autotune", action="store_true", help="keep the built-in launch-shape heuristics")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-surrogate measurement")
@@ -928,7 +930,7 @@ def run_box3d(args):
     import torch
     import inputs
     wl = WORKLOADS[args.workload]
-    prob = inputs.config_3d()                         # before any CUDA call
+    prob = inputs.config_3d(*args.box_n)              # before any CUDA call
     import paper_2009_07965_gb300 as mr
     from paper_2009_07965_gb300 import build as build_mod
     rank, world, local = dist_env()
@@ -1035,7 +1037,7 @@ def run_box3d(args):
     # FP64 solution of this run
     ref = dict(p=p_, Fx=Fx, Fy=Fy, Fz=Fz)
     mixed = {}
-    for name, split in (("mixed", 1 << 30), ("mixed_fp64_patch_merges", 512)):
+    for name, split in (() if args.no_mixed else (("mixed", 1 << 30), ("mixed_fp64_patch_merges", 512))):
         with torch.cuda.stream(stream):
             ms = mr.Solver3D(K, L=(prob.Lx, prob.Ly, prob.Lz), sub=prob.sub, seg=prob.seg, alpha=prob.alpha,
                              bc_type=prob.bc_type, stream=stream, precision=mr.binding.MRCM_MIXED)
@@ -1076,7 +1078,9 @@ def run_box3d(args):
         metric=METRIC, value=value, unit="cells/s", n_gpus=1, steps=args.steps, warmup=args.warmup,
         ms_per_step=total_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
         data="synthetic",
-        config=dict(workload=wl["desc"], cells=cells, **plan,
+        config=dict(workload=wl["desc"] if tuple(args.box_n) == (256, 256, 64)
+                    else wl["desc"].replace("256x256x64", "x".join(map(str, args.box_n))) + " (reduced box)",
+                    cells=cells, **plan,
                     l2="inputs larger than L2; L2 also flushed between timed steps", parallelism="one context"),
         roofline=dict(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
                       traffic=None, kernel=mr.PHASE_KERNELS[dom], phase=dom,

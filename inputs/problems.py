@@ -231,6 +231,7 @@ def config_3d(nx=256, ny=256, nz=64):
     """256 x 256 x 64 cubic cells on [0,1] x [0,1] x [0,0.25], log-normal K
     with sigma^2 = 2 and correlation lengths (0.2, 0.2, 0.05), p = 1 at
     x = 0 / p = 0 at x = 1, no-flow elsewhere; 16^3 leaves, 4 x 4 face
-    patches, alpha = 1."""
+    patches, alpha = 1.  Other sizes keep the cell size h = 1/256."""
     return darcy_problem_3d(nx, ny, nz, sigma2=2.0, corr=(0.2, 0.2, 0.05), seed=3000,
-                            bc="left_right", alpha=1.0, name=f"box{nx}x{ny}x{nz}-lr")
+                            bc="left_right", alpha=1.0, L=(nx / 256, ny / 256, nz / 256),
+                            name=f"box{nx}x{ny}x{nz}-lr")
