@@ -181,22 +181,36 @@ __device__ __forceinline__ Face3Info block_face(const DevView& v, const LeafDesc
 
 struct Leaf3Smem {
     double A[kLeaf3Cells][kLeaf3Cells + 1];   // A, then its Cholesky factor (lower)
-    double Z[kLeaf3Segs][kLeaf3Cells + 1];    // B, then Z = L^-1 B (one row per segment)
-    double W[kLeaf3Segs];
-    int start[kLeaf3Segs];                    // first nonzero row of each column of B
+    double Z[kLeaf3Segs][kLeaf3Cells + 1];    // B, then Z = L^-1 B, columns ordered by first row
+    double W[kLeaf3Segs];                     // sum of rho per ordered column
+    int first[kLeaf3Segs];                    // first nonzero row of B per local segment
+    int start[kLeaf3Segs];                    // ... per ordered column (ascending)
+    int order[kLeaf3Segs];                    // ordered column -> local segment
+    int rank[kLeaf3Segs];                     // local segment -> ordered column
+    int act[kLeaf3Cells];                     // columns started at or above row k
 };
 
+// The factorisation of each block, one CTA per block.  Columns of Z are
+// ordered by their first nonzero row, so the columns a step updates are a
+// prefix, and every step's work (the band triangle of the Cholesky update,
+// then one item per started column and band row) is spread evenly over the
+// threads: an FP64 instruction costs a whole warp's issue whatever its mask,
+// so the kernel avoids lanes that idle inside a busy warp.  R = Z^T Z - W
+// gives each warp one ordered row r (its pairs run from the row's first
+// nonzero, the later of the two), its lanes the columns q <= r.
 __global__ void __launch_bounds__(kBuild3Threads) leaf3_build_kernel(DevView v) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Leaf3Smem& S = *reinterpret_cast<Leaf3Smem*>(smem_raw);
     const int leaf = blockIdx.x;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const LeafDesc3 B = v.leaves3[leaf];
     const int n = B.w[0] * B.w[1] * B.w[2], m = B.m;
     for (int e = tid; e < kLeaf3Cells * (kLeaf3Cells + 1); e += kBuild3Threads) (&S.A[0][0])[e] = 0.0;
     for (int e = tid; e < kLeaf3Segs * (kLeaf3Cells + 1); e += kBuild3Threads) (&S.Z[0][0])[e] = 0.0;
+    for (int q = tid; q < m; q += kBuild3Threads) S.first[q] = n;
     __syncthreads();
-    // assembly, one cell per thread: diagonal in the order x-, x+, y-, y+, z-, z+
+    // assembly of A (one cell per thread: diagonal in the order x-, x+, y-,
+    // y+, z-, z+) and the first row of every column of B
     for (int c = tid; c < n; c += kBuild3Threads) {
         const int ii = c % B.w[0], jj = (c / B.w[0]) % B.w[1], kk = c / (B.w[0] * B.w[1]);
         double diag = 0.0;
@@ -204,28 +218,46 @@ __global__ void __launch_bounds__(kBuild3Threads) leaf3_build_kernel(DevView v) 
             const Face3Info F = block_face(v, B, ii, jj, kk, side);
             diag += F.c;
             if (F.nb >= 0) S.A[c][F.nb] = -F.c;
-            else if (F.seg >= 0) S.Z[F.seg][c] = F.c;
+            else if (F.seg >= 0) atomicMin(&S.first[F.seg], c);
         }
         S.A[c][c] = diag;
     }
     __syncthreads();
-    for (int s = tid; s < m; s += kBuild3Threads) {
-        double w = 0.0;
-        int st = n;
-        for (int c = 0; c < n; ++c) {
-            w += S.Z[s][c];
-            if (st == n && S.Z[s][c] != 0.0) st = c;
+    for (int q = tid; q < m; q += kBuild3Threads) {
+        int r = 0;
+        for (int t = 0; t < m; ++t)
+            r += S.first[t] < S.first[q] || (S.first[t] == S.first[q] && t < q);
+        S.rank[q] = r;
+        S.order[r] = q;
+    }
+    __syncthreads();
+    for (int c = tid; c < n; c += kBuild3Threads) {
+        const int ii = c % B.w[0], jj = (c / B.w[0]) % B.w[1], kk = c / (B.w[0] * B.w[1]);
+        for (int side = 0; side < 6; ++side) {
+            const Face3Info F = block_face(v, B, ii, jj, kk, side);
+            if (F.nb < 0 && F.seg >= 0) S.Z[S.rank[F.seg]][c] = F.c;
         }
-        S.W[s] = w;
-        S.start[s] = st;
+    }
+    for (int q = tid; q < m; q += kBuild3Threads) S.start[q] = S.first[S.order[q]];
+    __syncthreads();
+    for (int q = tid; q < m; q += kBuild3Threads) {
+        double w = 0.0;
+        for (int c = S.start[q]; c < n; ++c) w += S.Z[q][c];
+        S.W[q] = w;
+    }
+    for (int k = tid; k < n; k += kBuild3Threads) {
+        int a = 0;
+        while (a < m && S.start[a] <= k) ++a;
+        S.act[k] = a;
     }
     // Cholesky A = L L^T, right-looking; cells are x fastest, so the factor
     // keeps A's half-bandwidth bw = w_x w_y.  Step k scales column k of L and
-    // row k of Z (both final then), then updates the band triangle below it
-    // and rows k+1..k+bw of every column of Z = L^-1 B that has started (its
-    // first nonzero row at or above k).  The triangle goes first to the
-    // threads that hold no column of Z.  1 / L_kk is kept on the diagonal.
+    // row k of the started columns of Z (both final then), then updates the
+    // band triangle below it and rows k+1..k+bw of those columns.  1 / L_kk
+    // is kept on the diagonal.
     const int bw = B.w[0] * B.w[1];
+    int lb = 0;
+    while ((1 << lb) < bw) ++lb;                       // items per column: 2^lb >= bw band rows
     bool bad = false;
     for (int k = 0; k < n; ++k) {
         __syncthreads();
@@ -233,40 +265,43 @@ __global__ void __launch_bounds__(kBuild3Threads) leaf3_build_kernel(DevView v) 
         bad |= !(akk > 0.0);
         const double rl = 1.0 / sqrt(akk);
         const int len = min(bw, n - 1 - k);
+        const int a = S.act[k];
         for (int i = k + 1 + tid; i <= k + len; i += kBuild3Threads) S.A[i][k] *= rl;
-        for (int q = tid; q < m; q += kBuild3Threads) S.Z[q][k] *= rl;
+        for (int q = tid; q < a; q += kBuild3Threads) S.Z[q][k] *= rl;
         __syncthreads();
         if (tid == 0) S.A[k][k] = rl;
         const int ntri = len * (len + 1) / 2;
-        for (int e = (tid - m + kBuild3Threads) % kBuild3Threads; e < ntri; e += kBuild3Threads) {
-            int r = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
-            while ((r + 1) * (r + 2) / 2 <= e) ++r;
-            while (r * (r + 1) / 2 > e) --r;
-            const int i = k + 1 + r, j = k + 1 + (e - r * (r + 1) / 2);
-            S.A[i][j] = fma(-S.A[i][k], S.A[j][k], S.A[i][j]);
-        }
-        for (int q = tid; q < m; q += kBuild3Threads) {
-            if (S.start[q] > k) continue;
-            const double zk = S.Z[q][k];
-            for (int r = 1; r <= len; ++r) S.Z[q][k + r] = fma(-S.A[k + r][k], zk, S.Z[q][k + r]);
+        const int nitem = ntri + (a << lb);
+        for (int e = tid; e < nitem; e += kBuild3Threads) {
+            if (e < ntri) {
+                int r = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
+                while ((r + 1) * (r + 2) / 2 <= e) ++r;
+                while (r * (r + 1) / 2 > e) --r;
+                const int i = k + 1 + r, j = k + 1 + (e - r * (r + 1) / 2);
+                S.A[i][j] = fma(-S.A[i][k], S.A[j][k], S.A[i][j]);
+            } else {
+                const int e2 = e - ntri, q = e2 >> lb, r = (e2 & ((1 << lb) - 1)) + 1;
+                if (r <= len) S.Z[q][k + r] = fma(-S.A[k + r][k], S.Z[q][k], S.Z[q][k + r]);
+            }
         }
     }
     __syncthreads();
     if (bad && tid == 0) atomicOr(v.status, kStatusSingular);
-    // R = Z^T Z - W (symmetric, both halves written)
+    // R = Z^T Z - W (symmetric, both halves written, at the local segments)
     double* Rg = v.R + B.R_off;
-    const int npair = m * (m + 1) / 2;
-    for (int e = tid; e < npair; e += kBuild3Threads) {
-        int r = (int)((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
-        while ((r + 1) * (r + 2) / 2 <= e) ++r;
-        while (r * (r + 1) / 2 > e) --r;
-        const int q = e - r * (r + 1) / 2;
-        const int k0 = max(S.start[r], S.start[q]);
-        double acc = 0.0;
-        for (int k = k0; k < n; ++k) acc = fma(S.Z[r][k], S.Z[q][k], acc);
-        if (r == q) acc -= S.W[r];
-        Rg[(long long)r * m + q] = acc;
-        Rg[(long long)q * m + r] = acc;
+    for (int r = warp; r < m; r += kBuild3Threads / 32) {
+        const int k0 = S.start[r], sr = S.order[r];
+        for (int qb = 0; qb <= r; qb += 32) {
+            const int q = min(qb + lane, r);
+            double acc = 0.0;
+            for (int k = k0; k < n; ++k) acc = fma(S.Z[r][k], S.Z[q][k], acc);
+            if (qb + lane <= r) {
+                const int sq = S.order[q];
+                if (q == r) acc -= S.W[r];
+                Rg[(long long)sr * m + sq] = acc;
+                Rg[(long long)sq * m + sr] = acc;
+            }
+        }
     }
     // the factor (column-major, 1 / L_kk on the diagonal) and Z for the solve
     double* Lg = v.leafL + B.L_off;
@@ -275,7 +310,10 @@ __global__ void __launch_bounds__(kBuild3Threads) leaf3_build_kernel(DevView v) 
         Lg[e] = (i > k && i <= k + bw) || i == k ? S.A[i][k] : 0.0;
     }
     double* Zg = v.leafZ + B.Z_off;
-    for (int e = tid; e < m * n; e += kBuild3Threads) Zg[e] = S.Z[e / n][e % n];
+    for (int e = tid; e < m * n; e += kBuild3Threads) {
+        const int q = e / n, k = e % n;
+        Zg[(long long)S.order[q] * n + k] = S.Z[q][k];
+    }
 }
 
 // Boundary value of the face of global cell (gi, gj, gk) on domain side s.
