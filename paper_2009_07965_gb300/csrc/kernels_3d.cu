@@ -113,14 +113,15 @@ __global__ void face_coef3_kernel(DevView v) {
         } else if (cu < 0) {
             if (G.bc[2 * d + 1]) vl = 2.0 * v.K[cl] * area / hn;
         } else {
-            const double ra = hn / (2.0 * v.K[cl]), rb = hn / (2.0 * v.K[cu]);
+            // quotients as products with a reciprocal within an ulp (rcp_nr)
+            const double ra = hn * rcp_nr(2.0 * v.K[cl]), rb = hn * rcp_nr(2.0 * v.K[cu]);
             const int t = fseg[fl];
             if (t >= 0) {
                 const double beta = v.seg_beta[t];
-                vl = area / (ra + beta);
-                vu = area / (rb + beta);
+                vl = area * rcp_nr(ra + beta);
+                vu = area * rcp_nr(rb + beta);
             } else {
-                vl = vu = area / (ra + rb);
+                vl = vu = area * rcp_nr(ra + rb);
             }
         }
         cL[fl] = vl;

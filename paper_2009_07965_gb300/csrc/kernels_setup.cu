@@ -11,8 +11,11 @@
 //     interior face:   T   = |e| / (r_a + r_b)                 (both sides)
 //     skeleton face:   rho = |e| / (r_c + beta_t)              (Eq. 11.2, lumped)
 //     Dirichlet face:  tau = 2 K_c |e| / h,   Neumann face: 0.
-// Each coefficient is evaluated in this exact order (no fused operations),
-// so that the discrete system is defined to the last bit.
+// Each coefficient is evaluated in this order (no fused operations); the
+// quotients of the cell and interior / skeleton face terms are products with
+// a reciprocal within an ulp (rcp_nr: an FP64 division costs about ten FP64
+// instructions on this part, and these kernels are bound by them), so the
+// discrete system agrees with the plain quotients to a few ulps.
 #include "mrcm_internal.h"
 
 namespace mrcm {
@@ -36,9 +39,9 @@ __global__ void cell_resist_kernel(DevView v) {
     const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (c >= v.ncell) return;
     const GridDesc& G = v.grids[grid_of<0>(v, c)];
-    const double k2 = 2.0 * v.K[c];
-    v.rx[c] = G.hx / k2;
-    v.ry[c] = G.hy / k2;
+    const double rk = rcp_nr(2.0 * v.K[c]);
+    v.rx[c] = G.hx * rk;
+    v.ry[c] = G.hy * rk;
 }
 
 __global__ void seg_beta_kernel(DevView v) {
@@ -85,10 +88,10 @@ __global__ void face_coef_kernel(DevView v) {
             const int t = v.xface_seg[f];
             if (t >= 0) {
                 const double beta = v.seg_beta[t];
-                cl = area / (ra + beta);
-                cu = area / (rb + beta);
+                cl = area * rcp_nr(ra + beta);
+                cu = area * rcp_nr(rb + beta);
             } else {
-                cl = cu = area / (ra + rb);
+                cl = cu = area * rcp_nr(ra + rb);
             }
         }
         v.cxL[f] = cl;
@@ -112,10 +115,10 @@ __global__ void face_coef_kernel(DevView v) {
             const int t = v.yface_seg[f];
             if (t >= 0) {
                 const double beta = v.seg_beta[t];
-                cl = area / (ra + beta);
-                cu = area / (rb + beta);
+                cl = area * rcp_nr(ra + beta);
+                cu = area * rcp_nr(rb + beta);
             } else {
-                cl = cu = area / (ra + rb);
+                cl = cu = area * rcp_nr(ra + rb);
             }
         }
         v.cyL[f] = cl;
