@@ -152,3 +152,25 @@ def test_3d_fp64_refinement_keeps_the_solution(mrcm_lib):
     for key in ("p", "Fx", "Fy", "Fz"):
         assert rel(b[key], a[key]) < 1e-11, key
         assert rel(b[key], o[key]) < 1e-10, key
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_3d_every_side_and_source_against_the_oracle(precision, mrcm_lib):
+    # Dirichlet on x-, y+ and z+, nonzero Neumann fluxes on x+, y- and z-, a
+    # random source: every side's boundary-value block is read at its own
+    # face positions (a transposed or shifted index fails here)
+    import torch
+    from oracle.mrcm3d import solve_mrcm3d
+    import paper_2009_07965_gb300.binding as B
+    from inputs.problems import DIRICHLET, NEUMANN
+    prob = inputs.darcy_problem_3d(16, 12, 20, sigma2=2.0, corr=(0.3, 0.2, 0.2), seed=9, bc="left_right",
+                                   sub=(8, 4, 4), seg=(4, 2, 2), alpha=1.5, L=(1.0, 0.5, 1.0))
+    prob.bc_type = (DIRICHLET, NEUMANN, NEUMANN, DIRICHLET, NEUMANN, DIRICHLET)
+    rng = np.random.default_rng(17)
+    prob.bc_val = rng.uniform(-1.0, 1.0, prob.bc_val.shape)
+    prob.q = rng.uniform(-0.01, 0.01, prob.q.shape)
+    prec = B.MRCM_FP64 if precision == "fp64" else B.MRCM_MIXED
+    g, o = _solve(prob, torch, precision=prec), solve_mrcm3d(prob)
+    tol = 1e-10 if precision == "fp64" else 1e-8
+    for key in ("p", "Fx", "Fy", "Fz"):
+        assert rel(g[key], o[key]) < tol, (key, rel(g[key], o[key]))
