@@ -613,13 +613,10 @@ cudaError_t launch_coef3(const DevView& v, cudaStream_t s) {
 }
 
 cudaError_t launch_leaf3_build(const DevView& v, cudaStream_t s) {
+    // set on every launch (a host call; the attribute belongs to the current device)
     const int bytes = (int)sizeof(Leaf3Smem);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(leaf3_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    cudaError_t e = cudaFuncSetAttribute(leaf3_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
     leaf3_build_kernel<<<v.nleaf, kBuild3Threads, bytes, s>>>(v);
     return cudaGetLastError();
 }
