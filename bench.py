@@ -1033,8 +1033,8 @@ def run_box3d(args):
     del K_d, q_d, bc_d, outs_h
     # the mixed form: FP32 merges (every one, or those up to 2g = 512: the
     # merges inside the subdomains, the patch-level ones above in FP64), FP64
-    # blocks, three refinement steps with FP64 residuals; error against the
-    # FP64 solution of this run
+    # blocks, the default refinement (two steps) with FP64 residuals; error
+    # against the FP64 solution of this run
     ref = dict(p=p_, Fx=Fx, Fy=Fy, Fz=Fz)
     mixed = {}
     for name, split in (() if args.no_mixed else (("mixed", 1 << 30), ("mixed_fp64_patch_merges", 512))):
@@ -1069,7 +1069,8 @@ def run_box3d(args):
                for key, a in zip(("p", "Fx", "Fy", "Fz"), outm)}
         mval, mtot = job_throughput(sum(mms), cells, args.steps, 1, dev)
         mixed[name] = dict(ms_per_step=mtot / args.steps, value=mval, fp32_merges_up_to_2g=split if split < (1 << 30) else "all",
-                           refine_steps=3, rel_l2_vs_fp64=err, residual_history=mr.mrcm_residual_history(ms.ctx),
+                           refine_steps=len(mr.mrcm_residual_history(ms.ctx)), rel_l2_vs_fp64=err,
+                           residual_history=mr.mrcm_residual_history(ms.ctx),
                            tolerance=1e-8, within_tolerance=bool(max(err.values()) <= 1e-8),
                            phases_ms={k: v / args.steps for k, v in mph.items() if v > 0})
         ms.close()

@@ -116,7 +116,7 @@ enum {
  *              factorisations and basis solves (mrcm_set_mixed_leaves; FP64
  *              by default); the coefficients, the solve passes, the
  *              residuals and the fluxes in FP64; mrcm_solve
- *              then refines 3 times by default (mrcm_set_refinement) with
+ *              then refines 3 times by default (2 in 3D; mrcm_set_refinement) with
  *              FP64 residuals (mrcm_set_residual), which brings the result
  *              near the FP64 form's accuracy when the FP32 factors contract
  *              the error (Wilkinson's iterative refinement).  In 3D the

@@ -123,8 +123,8 @@ MIXED = [CASES[0], CASES[1], CASES[2]]
 @pytest.mark.parametrize("split", [1 << 30, 64])
 @pytest.mark.parametrize("case", MIXED, ids=lambda c: "x".join(map(str, c[0])) + "-seg" + "".join(map(str, c[2])))
 def test_3d_mixed_form_matches_the_oracle(case, split, mrcm_lib):
-    # FP32 merges (all of them, or those up to 2g = 64), FP64 blocks, three
-    # refinement steps with FP64 residuals: rel-L2 <= 1e-8
+    # FP32 merges (all of them, or those up to 2g = 64), FP64 blocks, the
+    # default two refinement steps with FP64 residuals: rel-L2 <= 1e-8
     import torch
     from oracle.mrcm3d import solve_mrcm3d
     import paper_2009_07965_gb300.binding as B
@@ -136,7 +136,7 @@ def test_3d_mixed_form_matches_the_oracle(case, split, mrcm_lib):
     for key in ("p", "Fx", "Fy", "Fz"):
         assert rel(g[key], o[key]) < 1e-8, (key, rel(g[key], o[key]))
     hist = g["hist"]
-    assert len(hist) == 3 and hist[-1] < 1e-3 * hist[0]
+    assert len(hist) == 2 and hist[-1] < 1e-2 * hist[0]
 
 
 def test_3d_fp64_refinement_keeps_the_solution(mrcm_lib):
