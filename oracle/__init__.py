@@ -20,4 +20,6 @@ Modules (each function cites the passage of the paper it follows):
              refinement of the discrete solution
   dd         double-double helpers (TwoSum, Dekker's TwoProd)
   cnn        the surrogate network's 3 x 3 convolutions and their gradients
+  mrcm3d     the 3D counterparts (Section 5.1): fine solve, box leaves,
+             interface patches, local Robin problems and O2 over patches
 """
