@@ -84,9 +84,9 @@ CPU_WINDOW = 256
 # from one ncu capture of this bench (dram__bytes_read.sum +
 # dram__bytes_write.sum).  A family missing here reports traffic null.
 TRAFFIC_PER_LAUNCH = {
-    ("square4096", "gj_sweep"): dict(bytes=15.7e6, source="ncu capture of one profiled step "
-                                     "(profiles/dram_traffic_square4096.md), mean over its 7 launches"),
-    ("square4096", "leaf_build"): dict(bytes=5805.7e6, source="ncu capture of one profiled step "
+    ("square4096", "gj_sweep"): dict(bytes=16.1e6, source="ncu capture of one profiled step "
+                                     "(profiles/dram_traffic_square4096.md), mean over its 6 launches"),
+    ("square4096", "leaf_build"): dict(bytes=5820.5e6, source="ncu capture of one profiled step "
                                        "(profiles/dram_traffic_square4096.md)"),
 }
 
