@@ -174,3 +174,15 @@ def test_3d_every_side_and_source_against_the_oracle(precision, mrcm_lib):
     tol = 1e-10 if precision == "fp64" else 1e-8
     for key in ("p", "Fx", "Fy", "Fz"):
         assert rel(g[key], o[key]) < tol, (key, rel(g[key], o[key]))
+
+
+def test_3d_single_leaf_nested_dissection_is_the_fine_solution(mrcm_lib):
+    # one 16^3 leaf and no patches: the merges of its 64 blocks over one-face
+    # segments must give the fine two-point-flux solution itself
+    import torch
+    from oracle.mrcm3d import solve_fine3d
+    prob = inputs.darcy_problem_3d(16, 16, 16, sigma2=3.0, corr=(0.2, 0.2, 0.1), seed=21, bc="left_right",
+                                   sub=(16, 16, 16), seg=(4, 4, 4), alpha=1.0)
+    g, f = _solve(prob, torch), solve_fine3d(prob)
+    for key in ("p", "Fx", "Fy", "Fz"):
+        assert rel(g[key], f[key]) < 1e-10, (key, rel(g[key], f[key]))
