@@ -208,7 +208,8 @@ int mrcm_build_basis(mrcm_ctx* ctx);
  *              + n[0]*(n[1]+1)) values laid out as [Fa_x, Fb_x, Fa_y, Fb_y],
  *              each face-shaped like Fx / Fy; side a is the lower-coordinate
  *              leaf, side b the upper one, both in the +axis direction; off
- *              the skeleton both equal the face flux.  Must be NULL in 3D.
+ *              the skeleton both equal the face flux.  3D: 2*(number of x-,
+ *              y- and z-faces) values, [Fa_x, Fb_x, Fa_y, Fb_y, Fa_z, Fb_z].
  * Errors: MRCM_ERR_NOT_BUILT, MRCM_ERR_INVALID_ARG, MRCM_ERR_TIMEOUT,
  * MRCM_ERR_CUDA.
  */

@@ -538,9 +538,11 @@ __global__ void __launch_bounds__(128) residual3_segments_kernel(DevView v, int 
 // Cell pressures and face fluxes (+axis sign) from the state (p_hi + p_lo,
 // the segments' Robin data of the interface unknowns); on the skeleton the
 // mean of the two one-sided values rho (p_c - lambda) of the blocks on either
-// side.
+// side.  iface (optional): the one-sided values [Fa_x, Fb_x, Fa_y, Fb_y,
+// Fa_z, Fb_z], side a the lower block, both equal to F off the skeleton.
 __global__ void face_flux3_kernel(DevView v, const double* __restrict__ bc_val, double* __restrict__ p,
-                                  double* __restrict__ Fx, double* __restrict__ Fy, double* __restrict__ Fz) {
+                                  double* __restrict__ Fx, double* __restrict__ Fy, double* __restrict__ Fz,
+                                  double* __restrict__ iface) {
     const Grid3& G = v.g3;
     const long long nf = v.nxface + v.nyface + v.nzface;
     for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < nf + v.ncell;
@@ -568,7 +570,8 @@ __global__ void face_flux3_kernel(DevView v, const double* __restrict__ bc_val, 
         const int n_d = d == 0 ? G.nx : (d == 1 ? G.ny : G.nz);
         const int pos = d == 0 ? i : (d == 1 ? j : k);
         const double area = area3(G, d);
-        double F;
+        double F, fa1 = 0.0, fb1 = 0.0;
+        bool skel = false;
         if (pos == 0) {
             const double pb = v.p_hi[cell3(G, i, j, k)] + v.p_lo[cell3(G, i, j, k)];
             const double g = bc_value3(G, bc_val, 2 * d, i, j, k);
@@ -589,12 +592,22 @@ __global__ void face_flux3_kernel(DevView v, const double* __restrict__ bc_val, 
                     const double fa = cL[fl] * (pa - (la.x + la.y));
                     const double fb = -(cU[fl] * (pb - (lb.x + lb.y)));
                     F = 0.5 * (fa + fb);
+                    fa1 = fa;
+                    fb1 = fb;
+                    skel = true;
                 } else {
                     F = cL[fl] * (pa - pb);
                 }
             }
         }
         out[fl] = F;
+        if (iface) {
+            // block of this axis: Fa at 2 (faces of the earlier axes), Fb after it
+            const long long nd = d == 0 ? v.nxface : (d == 1 ? v.nyface : v.nzface);
+            const long long base = 2 * (d == 0 ? 0 : (d == 1 ? v.nxface : v.nxface + v.nyface));
+            iface[base + fl] = skel ? fa1 : F;
+            iface[base + nd + fl] = skel ? fb1 : F;
+        }
     }
 }
 
@@ -642,9 +655,9 @@ cudaError_t launch_residual3(const DevView& v, const double* q, const double* bc
 }
 
 cudaError_t launch_face_fluxes3(const DevView& v, const double* bc_val, double* p, double* Fx, double* Fy,
-                                double* Fz, cudaStream_t s) {
+                                double* Fz, double* iface, cudaStream_t s) {
     const long long n = v.nxface + v.nyface + v.nzface + v.ncell;
-    face_flux3_kernel<<<grid_for(n, 256), 256, 0, s>>>(v, bc_val, p, Fx, Fy, Fz);
+    face_flux3_kernel<<<grid_for(n, 256), 256, 0, s>>>(v, bc_val, p, Fx, Fy, Fz, iface);
     return cudaGetLastError();
 }
 

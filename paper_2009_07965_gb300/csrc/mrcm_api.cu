@@ -737,7 +737,7 @@ struct mrcm_ctx {
     bool build_timing = false;
     int build_ev_used = 0;
     cudaGraphExec_t solve_exec = nullptr;
-    const void* solve_key[8] = {};
+    const void* solve_key[9] = {};
     int solve_ev_begin = 0, solve_ev_used = 0, solve_launches = 0;
 };
 
@@ -1433,7 +1433,7 @@ static int enqueue_solve(mrcm_ctx* c, const double* q_dev, const double* bc_val_
             TRYC(launch_mean_shift(v, steps == 0 || !v.res_dd, s));
             launches += 2;
         }
-        if (P.dim == 3) TRYC(launch_face_fluxes3(v, bc_val_dev, p_dev, Fx_dev, Fy_dev, Fz_dev, s));
+        if (P.dim == 3) TRYC(launch_face_fluxes3(v, bc_val_dev, p_dev, Fx_dev, Fy_dev, Fz_dev, iface_dev, s));
         else TRYC(launch_face_fluxes(v, bc_val_dev, p_dev, Fx_dev, Fy_dev, iface_dev, steps == 0, s));
         ++launches;
     }
@@ -1445,14 +1445,14 @@ int mrcm_solve(mrcm_ctx* c, const double* q_dev, const double* bc_val_dev, doubl
     if (!c) return MRCM_ERR_INVALID_ARG;
     if (!c->built) return MRCM_ERR_NOT_BUILT;
     if (!q_dev || !bc_val_dev || !p_dev || !Fx_dev || !Fy_dev) return MRCM_ERR_INVALID_ARG;
-    // Fz and only Fz in 3D; the interface unknowns are a 2D output
-    if (c->P.dim == 3 ? (!Fz_dev || iface_dev) : (Fz_dev != nullptr)) return MRCM_ERR_INVALID_ARG;
+    // Fz in 3D only
+    if (c->P.dim == 3 ? !Fz_dev : (Fz_dev != nullptr)) return MRCM_ERR_INVALID_ARG;
     // keep the build's event pairs, reuse the solve's
     while (c->ev_used > 0 && c->ev_phase[c->ev_used - 1] >= MRCM_PHASE_LEAF_PART &&
            c->ev_phase[c->ev_used - 1] <= MRCM_PHASE_FINISH)
         --c->ev_used;
     const int ev_begin = c->ev_used;
-    const void* key[8] = {q_dev, bc_val_dev, p_dev, Fx_dev, Fy_dev, c->P.dim == 3 ? Fz_dev : iface_dev,
+    const void* key[9] = {q_dev, bc_val_dev, p_dev, Fx_dev, Fy_dev, iface_dev, Fz_dev,
                           reinterpret_cast<const void*>(
                               (long long)((c->refine_steps * 2 + c->refine_check) * 2 + c->v.res_dd) + 1),
                           reinterpret_cast<const void*>((long long)(c->timing ? 2 : 1) + 4 * (long long)ev_begin)};

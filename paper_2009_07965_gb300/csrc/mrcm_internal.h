@@ -346,7 +346,7 @@ cudaError_t launch_leaf3_particular(const DevView& v, const double* q, const dou
 cudaError_t launch_leaf3_pressure(const DevView& v, bool accumulate, cudaStream_t s);
 cudaError_t launch_residual3(const DevView& v, const double* q, const double* bc_val, int step, cudaStream_t s);
 cudaError_t launch_face_fluxes3(const DevView& v, const double* bc_val, double* p, double* Fx, double* Fy,
-                                double* Fz, cudaStream_t s);
+                                double* Fz, double* iface, cudaStream_t s);
 cudaError_t launch_leaf_fields(const DevView& v, const int* ids, int count, float* psi, cudaStream_t s);
 cudaError_t launch_leaf_patches(const DevView& v, const int* ids, int count, void* x, cudaStream_t s);
 cudaError_t launch_leaf_gate(const DevView& v, const int* ids, int count, const float* psi, double* res,

@@ -95,9 +95,22 @@ class Solver3D:
     def build_basis(self):
         B.mrcm_build_basis(self.ctx)
 
-    def solve(self, q, bc_val):
-        B.mrcm_solve(self.ctx, q.contiguous(), bc_val.contiguous(), self.p, self.Fx, self.Fy, self.Fz, None)
+    def solve(self, q, bc_val, want_iface=False):
+        if want_iface and getattr(self, "iface", None) is None:
+            n = self.Fx.numel() + self.Fy.numel() + self.Fz.numel()
+            self.iface = torch.empty(2 * n, dtype=torch.float64, device=self.device)
+        B.mrcm_solve(self.ctx, q.contiguous(), bc_val.contiguous(), self.p, self.Fx, self.Fy, self.Fz,
+                     self.iface if want_iface else None)
         return self.p, self.Fx, self.Fy, self.Fz
+
+    def iface_parts(self):
+        """The one-sided flux output as Fa_x, Fb_x, Fa_y, Fb_y, Fa_z, Fb_z."""
+        out, off = [], 0
+        for F in (self.Fx, self.Fy, self.Fz):
+            n = F.numel()
+            out += [self.iface[off:off + n].view(F.shape), self.iface[off + n:off + 2 * n].view(F.shape)]
+            off += 2 * n
+        return tuple(out)
 
     def query(self, what):
         return B.mrcm_query(self.ctx, what)

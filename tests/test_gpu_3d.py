@@ -186,3 +186,24 @@ def test_3d_single_leaf_nested_dissection_is_the_fine_solution(mrcm_lib):
     g, f = _solve(prob, torch), solve_fine3d(prob)
     for key in ("p", "Fx", "Fy", "Fz"):
         assert rel(g[key], f[key]) < 1e-10, (key, rel(g[key], f[key]))
+
+
+def test_3d_one_sided_fluxes_against_the_oracle(mrcm_lib):
+    # both one-sided skeleton fluxes (side a the lower block), FP64
+    import torch
+    from oracle.mrcm3d import solve_mrcm3d
+    from paper_2009_07965_gb300 import Solver3D
+    n, sub, seg, L, s2, corr, seed, alpha = CASES[1]
+    prob = inputs.darcy_problem_3d(*n, sigma2=s2, corr=corr, seed=seed, bc="left_right", sub=sub,
+                                   seg=seg, alpha=alpha, L=L)
+    dev = torch.device("cuda:0")
+    s = Solver3D(torch.from_numpy(prob.K).to(dev), L=(prob.Lx, prob.Ly, prob.Lz), sub=prob.sub, seg=prob.seg,
+                 alpha=prob.alpha, bc_type=prob.bc_type)
+    s.build_basis()
+    s.solve(torch.from_numpy(prob.q).to(dev), torch.from_numpy(prob.bc_val).to(dev), want_iface=True)
+    torch.cuda.synchronize()
+    parts = [t.cpu().numpy() for t in s.iface_parts()]
+    o = solve_mrcm3d(prob)
+    for name, g in zip(("Fa_x", "Fb_x", "Fa_y", "Fb_y", "Fa_z", "Fb_z"), parts):
+        assert rel(g, o[name]) < 1e-10, (name, rel(g, o[name]))
+    s.close()
