@@ -69,8 +69,7 @@ enum {
     MRCM_ERR_TIMEOUT = -8,     /* a bounded device wait gave up              */
     MRCM_ERR_UNSUPPORTED = -9  /* valid request not implemented (surrogate,
                                   single-leaf pure Neumann; in 3D: batches,
-                                  all-Neumann problems, FP32 leaves,
-                                  double-double residuals)                  */
+                                  FP32 leaves, double-double residuals)     */
 };
 
 /*
@@ -95,8 +94,8 @@ enum {
  * every face between two blocks of one leaf is a segment of its own (on
  * which the Robin coupling is exact for any beta) and the side between
  * blocks of two leaves is one patch; one tree bisects the box of blocks
- * along the axis with the most blocks (x, y, z on ties).  At least one side
- * must be Dirichlet; one problem per context.
+ * along the axis with the most blocks (x, y, z on ties).  One problem per
+ * context.
  *
  *   out        receives the new context (NULL on failure)
  *   g          grid; g->dim 2 or 3

@@ -377,7 +377,17 @@ __global__ void __launch_bounds__(256) compat_partial_kernel(DevView v, const do
         if (i < n) {
             x = {val, 0.0};
         } else {
-            const double area = i - n < 2LL * G.ny ? G.hy : G.hx;
+            // face area of the boundary value's side (2D: x sides, then y
+            // sides; 3D: x, y, z sides of ny nz, nx nz, nx ny faces each)
+            double area;
+            const long long b = i - n;
+            if (v.dim == 3) {
+                const Grid3& H = v.g3;
+                const long long sx = (long long)H.ny * H.nz, sy = (long long)H.nx * H.nz;
+                area = b < 2 * sx ? H.hy * H.hz : (b < 2 * sx + 2 * sy ? H.hx * H.hz : H.hx * H.hy);
+            } else {
+                area = b < 2LL * G.ny ? G.hy : G.hx;
+            }
             x = dd_neg(dd_two_prod(area, val));
         }
         acc = dd_add(acc, x);

@@ -890,19 +890,15 @@ const char* mrcm_error_string(int code) {
 }
 
 // A 3D grid: blocks of the patch shape (at most kLeaf3Cells cells, at most
-// 16 faces per side) that tile the subdomains, which tile the grid; at least
-// one Dirichlet side.
+// 16 faces per side) that tile the subdomains, which tile the grid.
 static int validate3(const mrcm_grid& G, const int sub[3], const int seg[3], const int* bc) {
     long long cells = 1;
     for (int d = 0; d < 3; ++d) {
         if (G.n[d] < 1 || !(G.L[d] > 0) || sub[d] < 1 || seg[d] < 1) return MRCM_ERR_INVALID_ARG;
         cells *= G.n[d];
     }
-    bool dirichlet = false;
-    for (int s = 0; s < 6; ++s) {
+    for (int s = 0; s < 6; ++s)
         if (bc[s] != MRCM_BC_NEUMANN && bc[s] != MRCM_BC_DIRICHLET) return MRCM_ERR_INVALID_ARG;
-        dirichlet |= bc[s] == MRCM_BC_DIRICHLET;
-    }
     if (4 * cells + 3LL * G.n[0] * G.n[1] > (1LL << 31)) return MRCM_ERR_INVALID_ARG;
     for (int d = 0; d < 3; ++d)
         if (sub[d] % seg[d] != 0 || G.n[d] % sub[d] != 0) return MRCM_ERR_SHAPE;
@@ -911,7 +907,6 @@ static int validate3(const mrcm_grid& G, const int sub[3], const int seg[3], con
         const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
         if (seg[t1] * seg[t2] > kLeaf3Segs / 6) return MRCM_ERR_SHAPE;
     }
-    if (!dirichlet) return MRCM_ERR_UNSUPPORTED;
     return MRCM_OK;
 }
 
@@ -1088,6 +1083,7 @@ static int setup3_impl(mrcm_ctx* c, const mrcm_grid* g, const double* K_dev, con
     c->stream = static_cast<cudaStream_t>(stream);
     TRYC(cudaGetDevice(&c->device));
     TRY(make_plan3d(P));
+    if (P.pure_neumann && P.nleaf == 1) return MRCM_ERR_UNSUPPORTED;
     DevView& v = c->v;
     v.dim = 3;
     v.g3 = P.g3;

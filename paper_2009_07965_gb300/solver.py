@@ -70,7 +70,7 @@ class Solver3D:
     refinement).
 
     K: (nz, ny, nx) float64 CUDA tensor.  bc_type: (x-, x+, y-, y+, z-, z+)
-    with at least one Dirichlet side.  solve() returns p (nz, ny, nx), Fx
+    (all Neumann: zero-mean pressure).  solve() returns p (nz, ny, nx), Fx
     (nz, ny, nx+1), Fy (nz, ny+1, nx), Fz (nz+1, ny, nx).
     """
 

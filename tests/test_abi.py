@@ -82,7 +82,7 @@ def test_setup_rejects_bad_shapes_without_a_device(mrcm_lib):
 
 
 def test_unsupported_requests_are_refused_before_any_device_work(mrcm_lib):
-    # The surrogate precision (2D and 3D), all-Neumann 3D problems
+    # The surrogate precision (2D and 3D)
     # and 3D batches are refused with MRCM_ERR_UNSUPPORTED, 3D shapes that the
     # blocks cannot tile with MRCM_ERR_SHAPE, after validating the host
     # arguments and before touching the device (the permeability pointer is
@@ -95,9 +95,6 @@ def test_unsupported_requests_are_refused_before_any_device_work(mrcm_lib):
     sub, seg, bc = B._ints((16, 16, 16), 3), B._ints((4, 4, 4), 3), B._ints((1, 1, 0, 0, 0, 0), 6)
     g3 = B.mrcm_grid(3, (ctypes.c_int * 3)(64, 64, 64), (ctypes.c_double * 3)(1.0, 1.0, 1.0))
     assert lib.mrcm_setup(ctypes.byref(ctx), ctypes.byref(g3), fake_K, sub, seg, 1.0, bc, B.MRCM_SURROGATE,
-                          None) == -9
-    neumann = B._ints((0, 0, 0, 0, 0, 0), 6)
-    assert lib.mrcm_setup(ctypes.byref(ctx), ctypes.byref(g3), fake_K, sub, seg, 1.0, neumann, B.MRCM_FP64,
                           None) == -9
     two = (B.mrcm_grid * 2)(g3, g3)
     bc2 = B._ints((1, 1, 0, 0, 0, 0) * 2, 12)

@@ -207,3 +207,38 @@ def test_3d_one_sided_fluxes_against_the_oracle(mrcm_lib):
     for name, g in zip(("Fa_x", "Fb_x", "Fa_y", "Fb_y", "Fa_z", "Fb_z"), parts):
         assert rel(g, o[name]) < 1e-10, (name, rel(g, o[name]))
     s.close()
+
+
+@pytest.mark.parametrize("case,precision", [(CASES[0], "fp64"), (CASES[2], "fp64"), (CASES[1], "mixed")],
+                         ids=["32x32x16-fp64", "24x16x12-fp64", "16x24x16-mixed"])
+def test_3d_all_neumann_quarter_five_spot(case, precision, mrcm_lib):
+    # no-flow on every side, +1 / -1 in opposite corner cells: the pinned
+    # root, the data check and the zero-mean shift in 3D
+    import torch
+    from oracle.mrcm3d import solve_mrcm3d
+    import paper_2009_07965_gb300.binding as B
+    n, sub, seg, L, s2, corr, seed, alpha = case
+    prob = inputs.darcy_problem_3d(*n, sigma2=s2, corr=corr, seed=seed, bc="quarter_five_spot", sub=sub,
+                                   seg=seg, alpha=alpha, L=L)
+    prec = B.MRCM_FP64 if precision == "fp64" else B.MRCM_MIXED
+    g, o = _solve(prob, torch, precision=prec), solve_mrcm3d(prob)
+    tol = 1e-10 if precision == "fp64" else 1e-8
+    assert abs(g["p"].mean()) < 1e-12 * np.abs(g["p"]).max()
+    for key in ("p", "Fx", "Fy", "Fz"):
+        assert rel(g[key], o[key]) < tol, (key, rel(g[key], o[key]))
+
+
+def test_3d_incompatible_neumann_data_is_refused(mrcm_lib):
+    import torch
+    from paper_2009_07965_gb300 import Solver3D, MrcmError
+    prob = inputs.darcy_problem_3d(16, 16, 16, sigma2=1.0, seed=3, bc="quarter_five_spot", sub=(8, 8, 8),
+                                   seg=(4, 4, 4))
+    dev = torch.device("cuda:0")
+    s = Solver3D(torch.from_numpy(prob.K).to(dev), sub=prob.sub, seg=prob.seg, bc_type=prob.bc_type)
+    s.build_basis()
+    q = prob.q.copy()
+    q[0, 0, 0] = 2.0                      # sources no longer balance the (zero) boundary flux
+    with pytest.raises(MrcmError) as e:
+        s.solve(torch.from_numpy(q).to(dev), torch.from_numpy(prob.bc_val).to(dev))
+    assert e.value.code == -1
+    s.close()
