@@ -229,17 +229,24 @@ def run_reference(args):
     times = []
     value_steps = []
     ensemble = wl.get("kind") == "ensemble"
+    box = wl.get("kind") == "box3d"
     if ensemble:
         probs = ensemble_inputs(wl, count=wl["count"])
         order = sorted(range(len(probs)), key=lambda k: probs[k].nx * probs[k].ny)[:procs]
         cells = sum(probs[k].nx * probs[k].ny for k in order)
         sample = "the smallest members of the ensemble, one per host core"
+    elif box:
+        cells = 32 * 32 * 32 * procs
+        sample = f"{procs} x 32x32x32-cell windows per step (8 leaves of 16^3 each, the workload's cell size)"
     else:
         cells = CPU_WINDOW * CPU_WINDOW * procs
         sample = f"{procs} x {CPU_WINDOW}x{CPU_WINDOW} windows per step"
     for it in range(args.warmup + args.steps):
         if ensemble:
             v = time_ensemble_oracle(wl, probs)["value"]
+            wall = cells / v
+        elif box:
+            v = time_box3d_oracle()["value"]
             wall = cells / v
         else:
             v, _, wall = time_oracle_parallel(wl, 1, procs)
@@ -253,7 +260,7 @@ def run_reference(args):
                 data="synthetic", impl="reference",
                 config=dict(workload=wl["desc"], sample=sample),
                 cpu_baseline=dict(value=value, unit="cells/s", cores=procs, kind="oracle",
-                                  sample=sample if ensemble else oracle_sample_desc(wl, procs, 1)),
+                                  sample=sample if (ensemble or box) else oracle_sample_desc(wl, procs, 1)),
                 e2e=dict(value=value, unit="cells/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
 
