@@ -189,6 +189,8 @@ struct Leaf3Smem {
     int order[kLeaf3Segs];                    // ordered column -> local segment
     int rank[kLeaf3Segs];                     // local segment -> ordered column
     int act[kLeaf3Cells];                     // columns started at or above row k
+    double rl[kLeaf3Cells];                   // 1 / L_kk, formed once per pivot
+    int bad;                                  // a pivot that is not positive
 };
 
 // The factorisation of each block, one CTA per block.  Columns of Z are
@@ -256,15 +258,22 @@ __global__ void __launch_bounds__(kBuild3Threads) leaf3_build_kernel(DevView v) 
     // row k of the started columns of Z (both final then), then updates the
     // band triangle below it and rows k+1..k+bw of those columns.  1 / L_kk
     // is kept on the diagonal.
+    // The reciprocal 1 / L_kk is formed once per pivot (an FP64 square root
+    // and division cost about twenty FP64 instructions, per warp that runs
+    // them): pivot k + 1 receives its last update at step k, as entry 0 of
+    // that step's band triangle, and the thread that makes it forms the next
+    // reciprocal there; the barrier that opens the next step publishes it.
     const int bw = B.w[0] * B.w[1];
     int lb = 0;
     while ((1 << lb) < bw) ++lb;                       // items per column: 2^lb >= bw band rows
-    bool bad = false;
+    if (tid == 0) {
+        const double a00 = S.A[0][0];
+        S.bad = !(a00 > 0.0);
+        S.rl[0] = 1.0 / sqrt(a00);
+    }
     for (int k = 0; k < n; ++k) {
         __syncthreads();
-        const double akk = S.A[k][k];
-        bad |= !(akk > 0.0);
-        const double rl = 1.0 / sqrt(akk);
+        const double rl = S.rl[k];
         const int len = min(bw, n - 1 - k);
         const int a = S.act[k];
         for (int i = k + 1 + tid; i <= k + len; i += kBuild3Threads) S.A[i][k] *= rl;
@@ -279,7 +288,12 @@ __global__ void __launch_bounds__(kBuild3Threads) leaf3_build_kernel(DevView v) 
                 while ((r + 1) * (r + 2) / 2 <= e) ++r;
                 while (r * (r + 1) / 2 > e) --r;
                 const int i = k + 1 + r, j = k + 1 + (e - r * (r + 1) / 2);
-                S.A[i][j] = fma(-S.A[i][k], S.A[j][k], S.A[i][j]);
+                const double a = fma(-S.A[i][k], S.A[j][k], S.A[i][j]);
+                S.A[i][j] = a;
+                if (e == 0) {                      // pivot k + 1, final now
+                    if (!(a > 0.0)) S.bad = 1;
+                    S.rl[k + 1] = 1.0 / sqrt(a);
+                }
             } else {
                 const int e2 = e - ntri, q = e2 >> lb, r = (e2 & ((1 << lb) - 1)) + 1;
                 if (r <= len) S.Z[q][k + r] = fma(-S.A[k + r][k], S.Z[q][k], S.Z[q][k + r]);
@@ -287,7 +301,7 @@ __global__ void __launch_bounds__(kBuild3Threads) leaf3_build_kernel(DevView v) 
         }
     }
     __syncthreads();
-    if (bad && tid == 0) atomicOr(v.status, kStatusSingular);
+    if (S.bad && tid == 0) atomicOr(v.status, kStatusSingular);
     // R = Z^T Z - W (symmetric, both halves written, at the local segments)
     double* Rg = v.R + B.R_off;
     for (int r = warp; r < m; r += kBuild3Threads / 32) {
